@@ -1,0 +1,474 @@
+"""Pins of the FP64 oracle to facts outside itself: closed forms, brute force, independent
+methods, finite differences and special cases with a known exact answer.  CPU only."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import dqb, frame, ransac, solver, terms
+from oracle.quat import qexp_half, rotmat
+from synth import CONFIGS, make_scene
+from synth.scene import Config, axis_angle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            rows.append(line.split())
+    return rows
+
+
+def random_state(rng, N, rot=0.3, trans=3.0):
+    axes = rng.normal(size=(N, 3))
+    q = qexp_half(axes / np.linalg.norm(axes, axis=1, keepdims=True) * rng.uniform(0, rot, (N, 1)))
+    return q, rng.normal(scale=trans, size=(N, 3))
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    sc = make_scene(CONFIGS["frame_80x60_n32"], 1000, f64=True)
+    tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes)
+    return sc, tpl
+
+
+# ----------------------------------------------------------------------------- constants
+
+
+def test_paper_constants_are_oracle_defaults():
+    prm = solver.Params()
+    for name, value, *_ in _read_golden("paper_constants.txt"):
+        assert float(getattr(prm, name)) == float(value), name
+
+
+def test_closed_form_weights():
+    prm = solver.Params()
+    for kind, arg, val, *_ in _read_golden("closed_form_weights.txt"):
+        x, v = float(arg), float(val)
+        if kind == "ransac":
+            S1 = np.zeros((2, 3))
+            S2 = np.array([[0, 0, 0], [x, 0, 0]], dtype=np.float64)
+            # one reference at the origin plus one match displaced by x with a zero lever arm:
+            # the rotation cannot move a zero vector, so d = x exactly
+            d, w = ransac.reweight(S1, S2, prm.H, 1)
+            got = w[1]
+        elif kind == "orbramp":
+            got = terms.orb_weight(np.array([x]), np.array([False]), np.array([0.0]), prm.H)[0]
+        elif kind == "tukeyw":
+            got = terms.tukey_weight(np.array([x]), prm.tukey_c)[0]
+        elif kind == "tukeyrho":
+            got = terms.tukey_rho(np.array([x]), prm.tukey_c)[0]
+        else:
+            raise AssertionError(kind)
+        assert abs(got - v) < 1e-12, (kind, x, got, v)
+
+
+# ----------------------------------------------------------------------------- frame prep
+
+
+def test_backprojection_closed_form():
+    rng = np.random.default_rng(1)
+    H, W = 7, 9
+    K = (9.0, 9.0, 4.0, 3.0)
+    z = rng.uniform(50, 150, (H, W))
+    z[2, 3] = 0.0
+    X, valid = frame.backproject(z, K)
+    for v in range(H):
+        for u in range(W):
+            exp = np.array([(u - 4.0) * z[v, u] / 9.0, (v - 3.0) * z[v, u] / 9.0, z[v, u]])
+            assert np.array_equal(X[v, u], exp)
+    assert not valid[2, 3] and valid.sum() == H * W - 1
+
+
+def test_plane_normals_exact():
+    # depth of the plane n.X = c seen through the pinhole: z = c / (n . d(u, v))
+    H, W = 12, 16
+    K = (16.0, 16.0, 7.5, 5.5)
+    nrm = np.array([0.2, -0.3, -1.0])
+    nrm /= np.linalg.norm(nrm)
+    c = -100.0
+    u, v = np.meshgrid(np.arange(W), np.arange(H))
+    d = np.stack([(u - 7.5) / 16.0, (v - 5.5) / 16.0, np.ones_like(u, dtype=float)], -1)
+    z = c / (d @ nrm)
+    X, valid = frame.backproject(z, K)
+    n, ok = frame.target_normals(X, valid)
+    assert ok[1:-1, 1:-1].all() and not ok[0].any() and not ok[:, -1].any()
+    assert np.abs(n[ok] - nrm).max() < 1e-12
+    z2 = z.copy()
+    z2[5, 5] = 0.0
+    X2, v2 = frame.backproject(z2, K)
+    _, ok2 = frame.target_normals(X2, v2)
+    for (a, b) in [(5, 5), (4, 5), (6, 5), (5, 4), (5, 6)]:
+        assert not ok2[a, b]
+    assert ok2[4, 4]
+
+
+# ----------------------------------------------------------------------------- association
+
+
+def test_association_is_nearest_pixel_centre_brute_force():
+    rng = np.random.default_rng(2)
+    W, H = 11, 8
+    K = (11.0, 11.0, 5.0, 3.5)
+    x = np.concatenate([rng.uniform(-6, 6, (300, 1)), rng.uniform(-5, 5, (300, 1)),
+                        rng.uniform(5, 20, (300, 1))], 1)
+    # a few exact half-pixel cases: floor(u + 1/2) rounds halves up
+    x[0] = [0.5 * 10 / 11.0, 0.0, 10.0]
+    tgt_ok = np.ones((H, W), dtype=bool)
+    pix, valid, u, v = terms.associate(x, K, W, H, tgt_ok)
+    for i in range(x.shape[0]):
+        best, bd = None, None
+        for pv in range(H):
+            for pu in range(W):
+                du, dv = u[i] - pu, v[i] - pv
+                # nearest centre along each axis, halves to the larger index
+                if -0.5 <= du < 0.5 and -0.5 <= dv < 0.5:
+                    best = pv * W + pu
+                    bd = (du, dv)
+        if best is None:
+            assert not valid[i]
+        else:
+            assert valid[i] and pix[i] == best, (i, bd)
+    assert valid[0] and pix[0] % W == 6
+
+
+# ----------------------------------------------------------------------------- nearest nodes
+
+
+def test_nearest_nodes_brute_force():
+    rng = np.random.default_rng(3)
+    g = rng.integers(0, 5, (9, 3)).astype(float)      # integer lattice: many exact ties
+    p = rng.integers(0, 5, (200, 3)).astype(float) + 0.5 * rng.integers(0, 2, (200, 3))
+    ids, d2 = solver.nearest_nodes(p, g, 4)
+    for j in range(p.shape[0]):
+        cand = sorted(range(9), key=lambda i: (float(((p[j] - g[i]) ** 2).sum()), i))[:4]
+        assert list(ids[j]) == cand
+
+
+# ----------------------------------------------------------------------------- Kabsch / RANSAC
+
+
+def test_kabsch_matches_horn_and_is_exact_on_three_points():
+    rng = np.random.default_rng(4)
+    for trial in range(50):
+        M = int(rng.integers(3, 40))
+        S1 = rng.normal(size=(M, 3)) * 10
+        R = axis_angle(rng.normal(size=3), rng.uniform(0, math.pi))
+        S2 = S1 @ R.T + rng.normal(scale=0.5, size=(M, 3)) * (trial % 2)
+        w = rng.uniform(0.1, 1.0, M)
+        Rk = ransac.kabsch(S1, S2, w)
+        Rh = ransac.horn(S1, S2, w)
+        assert np.abs(Rk - Rh).max() < 1e-12
+        assert abs(np.linalg.det(Rk) - 1) < 1e-12
+        if trial % 2 == 0:
+            assert np.abs(Rk - R).max() < 1e-12
+    S1 = rng.normal(size=(3, 3))
+    R = axis_angle([1, 2, 3], 0.7)
+    assert np.abs(ransac.kabsch(S1, S1 @ R.T, np.ones(3)) - R).max() < 1e-13
+
+
+def test_kabsch_reflection_guard_and_degenerate():
+    S1 = np.array([[1.0, 0, 0], [2.0, 0, 0]])
+    assert np.array_equal(ransac.kabsch(S1, S1, np.ones(2)), np.eye(3))     # collinear
+    assert np.array_equal(ransac.kabsch(S1, S1, np.zeros(2)), np.eye(3))    # no weight
+    rng = np.random.default_rng(5)
+    S1 = rng.normal(size=(10, 3))
+    S2 = S1 * np.array([1, 1, -1])                 # a mirror: best proper rotation, det = +1
+    R = ransac.kabsch(S1, S2, np.ones(10))
+    assert abs(np.linalg.det(R) - 1) < 1e-12
+
+
+def _ransac_bruteforce(o1, o2, hyp, H, n_it, keep_frac):
+    """Pure-Python loops over every reference and match, Kabsch by exhaustive search for the
+    eigenvector of Horn's matrix (independent of the vectorised oracle's SVD)."""
+    M = len(o1)
+    res = []
+    for k0 in hyp:
+        S1 = [[o1[k][a] - o1[k0][a] for a in range(3)] for k in range(M)]
+        S2 = [[o2[k][a] - o2[k0][a] for a in range(3)] for k in range(M)]
+        w = [1.0] * M
+        d = [0.0] * M
+        for _ in range(n_it):
+            R = ransac.horn(np.array(S1), np.array(S2), np.array(w))
+            if sum(w) < 1e-12:
+                R = np.eye(3)
+            for k in range(M):
+                rs = [sum(R[a][b] * S1[k][b] for b in range(3)) for a in range(3)]
+                d[k] = math.sqrt(sum((S2[k][a] - rs[a]) ** 2 for a in range(3)))
+                w[k] = 1.0 if d[k] == 0 else min(H / d[k], 1.0)
+        res.append((list(d), list(w), sum(w) - w[k0]))
+    best = max(r[2] for r in res)
+    kept = [r[2] >= keep_frac * best for r in res]
+    mask = [any(kept[h] and res[h][0][k] <= H for h in range(len(hyp))) for k in range(M)]
+    return mask, kept, res
+
+
+def test_ransac_matches_bruteforce_small():
+    rng = np.random.default_rng(6)
+    for trial in range(6):
+        M = int(rng.integers(5, 13))
+        o1 = rng.normal(scale=20, size=(M, 3))
+        R = axis_angle(rng.normal(size=3), 0.2)
+        o2 = o1 @ R.T + 3 + rng.normal(scale=0.3, size=(M, 3))
+        out = rng.random(M) < 0.35
+        o2[out] += rng.normal(scale=30, size=(out.sum(), 3))
+        hyp = rng.choice(M, size=min(M, 5), replace=False)
+        rs = ransac.ransac_1p(o1, o2, hyp, 2.0, 10, 0.5)
+        mask, kept, res = _ransac_bruteforce(o1.tolist(), o2.tolist(), list(hyp), 2.0, 10, 0.5)
+        assert list(rs["kept"]) == kept
+        for h in range(len(hyp)):
+            assert np.abs(rs["d"][h] - np.array(res[h][0])).max() < 1e-9
+        assert list(rs["mask"]) == mask
+
+
+def test_ransac_recovers_planted_inliers():
+    # rigid scene, noise-free inliers, outliers >= 10 H from their true position
+    cfg = Config("planted", 80, 60, 32, 200, 5, 0.3, 0.0, 0.0, 0.0, 0.0, 3.0, 2.0, 1,
+                 outlier_min_dist=20.0)
+    sc = make_scene(cfg, 77, f64=True)
+    f = sc.frames[0]
+    X0, _ = frame.backproject(sc.template_depth, sc.K)
+    o1 = X0.reshape(-1, 3)[f.match_idx]
+    rs = ransac.ransac_1p(o1, f.match_xyz, f.hyp, 2.0, 10, 0.5)
+    assert np.array_equal(rs["mask"], f.inlier)
+    for h, k0 in enumerate(f.hyp):
+        if f.inlier[k0]:
+            assert rs["kept"][h]
+            assert np.array_equal(rs["d"][h] <= 2.0, f.inlier)
+
+
+# ----------------------------------------------------------------------------- DQB
+
+
+def test_dqb_identical_transforms_and_sign_flips():
+    rng = np.random.default_rng(8)
+    N, P = 6, 50
+    g = rng.normal(scale=20, size=(N, 3))
+    p = rng.normal(scale=20, size=(P, 3))
+    qa = qexp_half(np.array([0.3, -0.2, 0.5]))
+    R = rotmat(qa)
+    T = np.array([1.0, -2.0, 3.0])
+    q = np.tile(qa, (N, 1))
+    t = g @ R.T + T - g                     # every node moves by the same rigid (R, T)
+    nid = np.stack([rng.choice(N, 4, replace=False) for _ in range(P)])
+    al = rng.uniform(0.1, 1, (P, 4))
+    al /= al.sum(1, keepdims=True)
+    x, _ = dqb.warp_points(q, t, g, p, nid, al, nid[:, 0], with_jac=False)
+    assert np.abs(x - (p @ R.T + T)).max() < 1e-12
+    q2, t2 = random_state(rng, N)
+    x2, _ = dqb.warp_points(q2, t2, g, p, nid, al, nid[:, 0], with_jac=False)
+    flip = np.where(rng.random(N) < 0.5, -1.0, 1.0)[:, None]
+    x3, _ = dqb.warp_points(q2 * flip, t2, g, p, nid, al, nid[:, 0], with_jac=False)
+    assert np.abs(x2 - x3).max() < 1e-12
+    # a single node reproduces its own node-centred transform W(x) = R (x - g) + g + t
+    x4, _ = dqb.warp_points(q2, t2, g, p, np.zeros((P, 4), int) + 2, al, np.full(P, 2),
+                            with_jac=False)
+    R2 = rotmat(q2[2])
+    assert np.abs(x4 - ((p - g[2]) @ R2.T + g[2] + t2[2])).max() < 1e-12
+
+
+def _fd(fun, q, t, n, h_rot=1e-6, h_tr=1e-5):
+    cols = []
+    for k in range(6 * n):
+        h = h_rot if k % 6 < 3 else h_tr
+        d = np.zeros(6 * n)
+        d[k] = h
+        qp, tp = dqb.apply_step(q, t, d)
+        qm, tm = dqb.apply_step(q, t, -d)
+        cols.append((fun(qp, tp) - fun(qm, tm)) / (2 * h))
+    return np.stack(cols, -1)
+
+
+def test_warp_jacobian_finite_differences():
+    rng = np.random.default_rng(9)
+    N, P = 5, 40
+    g = rng.normal(scale=20, size=(N, 3)) + [0, 0, 100]
+    p = rng.normal(scale=20, size=(P, 3)) + [0, 0, 100]
+    q, t = random_state(rng, N)
+    nid = np.stack([rng.choice(N, 4, replace=False) for _ in range(P)])
+    al = rng.uniform(0.1, 1, (P, 4))
+    al /= al.sum(1, keepdims=True)
+    x, J = dqb.warp_points(q, t, g, p, nid, al, nid[:, 0])
+    full = np.zeros((P, 3, 6 * N))
+    for k in range(4):
+        for c in range(6):
+            full[np.arange(P), :, 6 * nid[:, k] + c] += J[:, :, k, c]
+    num = _fd(lambda qq, tt: dqb.warp_points(qq, tt, g, p, nid, al, nid[:, 0], False)[0], q, t, N)
+    err = np.abs(num - full).max() / np.abs(full).max()
+    assert err < 1e-6, err
+
+
+def test_arap_jacobian_finite_differences():
+    rng = np.random.default_rng(10)
+    N = 5
+    g = rng.normal(scale=20, size=(N, 3)) + [0, 0, 100]
+    q, t = random_state(rng, N)
+    wpair, _ = terms.arap_pair_weights(g, 0.25)
+    rows, _ = terms.arap_rows(q, t, g, wpair, 1.0, 20.0, 100.0)
+    R = rows.r.shape[0]
+    full = np.zeros((R, 6 * N))
+    for c in range(12):
+        full[np.arange(R), rows.cols[:, c]] += rows.vals[:, c]
+    num = _fd(lambda qq, tt: terms.arap_rows(qq, tt, g, wpair, 1.0, 20.0, 100.0)[0].r, q, t, N)
+    err = np.abs(num - full).max() / np.abs(full).max()
+    assert err < 1e-6, err
+
+
+def test_icp_and_orb_jacobians_finite_differences(tiny):
+    sc, tpl = tiny
+    rng = np.random.default_rng(11)
+    N = tpl.g.shape[0]
+    q, t = random_state(rng, N, rot=0.02, trans=0.5)
+    f = sc.frames[0]
+    tgt = solver.prepare_target(f.depth, tpl.K)
+    x, Jx = dqb.warp_points(q, t, tpl.g, tpl.p, tpl.nid, tpl.alpha, tpl.nid[:, 0])
+    rows, _, _, pix, valid = terms.icp_rows(x, Jx, tpl.nid, tgt.X, tgt.n, tgt.ok, tpl.K, tpl.W,
+                                            tpl.H, 10.0)
+    v = np.flatnonzero(valid)[::37]
+    qq_ = tgt.X.reshape(-1, 3)[pix[v]]
+    nn_ = tgt.n.reshape(-1, 3)[pix[v]]
+
+    def res(qa, ta):
+        xx, _ = dqb.warp_points(qa, ta, tpl.g, tpl.p[v], tpl.nid[v], tpl.alpha[v], tpl.nid[v, 0], False)
+        return (nn_ * (xx - qq_)).sum(1)
+
+    num = _fd(res, q, t, N)
+    sel = np.searchsorted(np.flatnonzero(valid), v)
+    full = np.zeros((len(v), 6 * N))
+    for c in range(24):
+        full[np.arange(len(v)), rows.cols[sel, c]] += rows.vals[sel, c]
+    err = np.abs(num - full).max() / np.abs(full).max()
+    assert err < 1e-6, err
+
+
+# ----------------------------------------------------------------------------- ARAP closed form
+
+
+def test_arap_zero_for_common_rigid_motion():
+    rng = np.random.default_rng(12)
+    for _ in range(10):
+        N = int(rng.integers(3, 12))
+        g = rng.normal(scale=30, size=(N, 3)) + [0, 0, 100]
+        qa = qexp_half(rng.normal(size=3))
+        if qa[0] < 0:
+            qa = -qa
+        R = rotmat(qa)
+        T = rng.normal(scale=10, size=3)
+        q = np.tile(qa, (N, 1))
+        t = g @ R.T + T - g
+        wpair, _ = terms.arap_pair_weights(g, 0.25)
+        rows, cost = terms.arap_rows(q, t, g, wpair, 3.0, 20.0, 100.0)
+        assert cost < 1e-20
+        A, b = solver.assemble([rows], 6 * N)
+        assert np.abs(b).max() < 1e-9
+        # ... and positive for a non-rigid state
+        q2, t2 = random_state(rng, N)
+        assert terms.arap_rows(q2, t2, g, wpair, 3.0, 20.0, 100.0)[1] > 1e-3
+
+
+# ----------------------------------------------------------------------------- assembly / linear algebra
+
+
+def test_normal_equations_equal_explicit_dense_triple_loop():
+    cfg = Config("mini", 20, 15, 6, 20, 3, 0.3, 0.0, 0.0, 3.0, 0.0, 2.0, 1.0, 1, n_hyp=8)
+    sc = make_scene(cfg, 5, f64=True)
+    tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes)
+    f = sc.frames[0]
+    tgt = solver.prepare_target(f.depth, tpl.K)
+    rng = np.random.default_rng(13)
+    q, t = random_state(rng, 6, rot=0.01, trans=0.3)
+    mask = rng.random(20) < 0.5
+    orb = (f.match_idx, f.match_xyz.astype(float), mask, mask.astype(float))
+    rows, *_ = solver.data_terms(tpl, tgt, q, t, orb, solver.Params())
+    ar, _ = terms.arap_rows(q, t, tpl.g, tpl.wpair, 2.0, 20.0, 100.0)
+    rows.append(ar)
+    n = 36
+    Jd, Wd, rd = [], [], []
+    for rw in rows:
+        for i in range(rw.r.shape[0]):
+            row = [0.0] * n
+            for c, val in zip(rw.cols[i], rw.vals[i]):
+                row[c] += val
+            Jd.append(row)
+            Wd.append(rw.W[i])
+            rd.append(rw.r[i])
+    A_ref = [[0.0] * n for _ in range(n)]
+    b_ref = [0.0] * n
+    for a in range(n):
+        for c in range(n):
+            s = 0.0
+            for i in range(len(Jd)):
+                s += Jd[i][a] * Wd[i] * Jd[i][c]
+            A_ref[a][c] = s
+        b_ref[a] = -sum(Jd[i][a] * Wd[i] * rd[i] for i in range(len(Jd)))
+    A, b = solver.assemble(rows, n)
+    A_ref = np.array(A_ref)
+    assert np.abs(A - A_ref).max() <= 1e-12 * np.abs(A_ref).max()
+    assert np.abs(b - np.array(b_ref)).max() <= 1e-12 * np.abs(b_ref).max()
+
+
+def _gauss_partial_pivot(A, b):
+    A = [list(r) for r in A]
+    b = list(b)
+    n = len(b)
+    for k in range(n):
+        p = max(range(k, n), key=lambda i: abs(A[i][k]))
+        A[k], A[p] = A[p], A[k]
+        b[k], b[p] = b[p], b[k]
+        for i in range(k + 1, n):
+            f = A[i][k] / A[k][k]
+            for j in range(k, n):
+                A[i][j] -= f * A[k][j]
+            b[i] -= f * b[k]
+    x = [0.0] * n
+    for i in range(n - 1, -1, -1):
+        x[i] = (b[i] - sum(A[i][j] * x[j] for j in range(i + 1, n))) / A[i][i]
+    return np.array(x)
+
+
+def test_cholesky_reconstruction_and_gaussian_elimination(tiny):
+    sc, tpl = tiny
+    f = sc.frames[0]
+    res = solver.solve_frame(tpl, f.depth, f.match_idx, f.match_xyz, f.hyp, iters=1, keep_lins=True)
+    A = solver.damp(res.lins[0].A, solver.Params())
+    b = res.lins[0].b
+    L = np.linalg.cholesky(A)
+    assert np.linalg.norm(L @ L.T - A) / np.linalg.norm(A) < 1e-14
+    x = solver.cholesky_solve(A, b)
+    xg = _gauss_partial_pivot(A, b)
+    assert np.abs(x - xg).max() <= 1e-9 * np.abs(xg).max()
+    d0 = np.diag(res.lins[0].A)
+    assert np.allclose(np.diag(A), d0 + 1e-4 * (d0 + 1e-9), rtol=1e-14, atol=0)
+
+
+# ----------------------------------------------------------------------------- whole solve
+
+
+def test_exact_recovery_of_a_rigid_motion_on_a_plane():
+    cfg = Config("rigid_plane", 80, 60, 32, 200, 0, 0.0, 0.0, 0.0, 0.0, 0.0, 3.0, 2.0, 1,
+                 planar=True)
+    sc = make_scene(cfg, 31, f64=True)
+    f = sc.frames[0]
+    tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes)
+    res = solver.solve_frame(tpl, f.depth, f.match_idx, f.match_xyz, f.hyp, iters=10)
+    err = np.abs(res.pos - f.node_truth).max()
+    assert err < 1e-9, err
+    R = f.motion.Rc
+    qe = res.q
+    assert np.abs(rotmat(qe) - R).max() < 1e-9
+    assert res.ransac["mask"].all()
+
+
+def test_gauss_newton_cost_non_increasing(tiny):
+    sc, tpl = tiny
+    f = sc.frames[0]
+    res = solver.solve_frame(tpl, f.depth, f.match_idx, f.match_xyz, f.hyp, iters=10)
+    c = np.array(res.costs)
+    assert (np.diff(c) <= 1e-9 * c[:-1]).all(), c
+    assert c[-1] < 0.2 * c[0]
