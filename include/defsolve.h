@@ -1,0 +1,205 @@
+/*
+ * defsolve — per-frame non-rigid surface deformation solve on one GB300 (sm_103a).
+ *
+ * C ABI of the library libdefsolve.so. The operation is the deformation recovery of
+ * Zhou & Jagadeesan, "Real-time Surface Deformation Recovery from Stereo Videos":
+ *   - a depth template is deformed by sparse control points, each carrying a rigid warp W_i
+ *     (Section 2: dual-quaternion warp, template points follow the interpolation of their
+ *     neighbouring control points);
+ *   - the warps minimise f_ICP + w_ORB f_ORB + w_ARAP f_ARAP (Eq. 1): point-to-plane ICP with
+ *     Tukey weights from projective association (Section 2), feature matches weighted by
+ *     1-point RANSAC + reweighting (Section 2.1, Eq. 2-4) and dense all-pairs ARAP
+ *     (Section 2.2, Eq. 5-6);
+ *   - by damped Gauss-Newton over every control point's rotation and translation, solving the
+ *     normal equations with a Cholesky factorisation (Section 2, LM + Cholesky).
+ *
+ * Conventions shared by every call:
+ *   - Images are row-major H x W, pixel (u, v) at index v * W + u, pixel centres at integer
+ *     coordinates. Camera frame x right, y down, z forward; units are millimetres.
+ *   - Input pointers may be host (pageable or pinned) or device pointers; the library copies
+ *     them with cudaMemcpyAsync(cudaMemcpyDefault) on the handle's stream. Pageable host input
+ *     is copied before the call returns; pinned host or device input must stay valid and
+ *     unchanged until the handle's stream reaches the copy (any ds_get_* call, or a stream
+ *     synchronisation, guarantees that).
+ *   - Output pointers are caller-allocated host or device memory; every ds_get_* call
+ *     synchronises the handle's stream before it returns.
+ *   - The handle owns all of its device memory; calls on one handle must not run
+ *     concurrently from several host threads. Distinct handles are independent.
+ *   - Every call returns a ds_status; nothing aborts the process. A CUDA error is returned as
+ *     DS_ERR_CUDA and leaves the handle usable only for ds_destroy.
+ */
+#ifndef DEFSOLVE_H
+#define DEFSOLVE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DS_OK = 0,
+  DS_ERR_ARG = 1,       /* a null pointer, a size out of range, an index outside the image  */
+  DS_ERR_OOM = 2,       /* a device allocation failed                                       */
+  DS_ERR_BAD_INPUT = 3, /* non-finite depth or match coordinates                             */
+  DS_ERR_NOT_SPD = 4,   /* a Cholesky pivot <= 0 even after the damping retries              */
+  DS_ERR_STATE = 5,     /* call order violated (e.g. solve before submit_frame)              */
+  DS_ERR_TIMEOUT = 6,   /* a bounded device-side wait gave up                                */
+  DS_ERR_CUDA = 7       /* any other CUDA runtime error                                      */
+} ds_status;
+
+/* Precision of the normal-equation solve. Residuals, Jacobians and J^T W J are FP32 in every
+ * mode; the state is kept in FP64. */
+typedef enum {
+  DS_PREC_FP64 = 0,        /* FP64 Cholesky + FP64 triangular solves + refinement steps whose
+                              residual b - A x is accumulated in FP64 against the FP32 matrix */
+  DS_PREC_FP32 = 1,        /* plain: FP32 Cholesky and solves, no refinement                   */
+  DS_PREC_FP32_REFINE = 2  /* FP32 Cholesky, FP64 residual refinement steps                   */
+} ds_precision;
+
+#define DS_MAX_ITERS 64
+#define DS_MAX_HYP 64
+
+typedef struct ds_ctx* ds_handle;
+
+typedef struct {
+  float fx, fy, cx, cy; /* pinhole intrinsics, shared by the template and every frame */
+} ds_intrinsics;
+
+/* Method parameters. ds_default_params() fills the paper's values where it gives them
+ * (w_orb = 10 after Eq. 1; w_angle = 20 and w_rot = 100 after Eq. 5; 10 reweighting iterations
+ * and 30 references in Section 2.1) and the library's readings elsewhere. */
+typedef struct {
+  double w_orb;             /* weight of f_ORB in Eq. 1                                          */
+  double w_angle;           /* weight of f_angle in Eq. 5                                        */
+  double w_rot;             /* weight of f_rotation in Eq. 5                                     */
+  double w_arap0;           /* w_ARAP = w_arap0 * (sum ICP weights + w_orb * sum ORB weights) / N */
+  double H_mm;              /* threshold H of Eq. 4 (also the 5H ramp of the ORB weights)        */
+  double tukey_c_mm;        /* Tukey constant of the ICP term                                    */
+  double sigma_blend_scale; /* blend sigma = scale * mean nearest-neighbour node spacing         */
+  double sigma_arap_scale;  /* ARAP pair sigma = scale * node bounding-box diagonal              */
+  double lambda;            /* damping: A + lambda (diag(A) + eps_damp)                          */
+  double eps_damp;
+  double keep_frac;         /* a RANSAC reference is kept iff its score >= keep_frac * best      */
+  int32_t n_hyp;            /* number of RANSAC references (<= DS_MAX_HYP)                       */
+  int32_t n_reweight;       /* reweighting iterations per reference                              */
+  int32_t n_nearest;        /* control points blended per template point; must be 4             */
+  int32_t precision;        /* ds_precision                                                      */
+  int32_t refine_steps;     /* refinement steps in DS_PREC_FP64 / DS_PREC_FP32_REFINE (0..4)     */
+  int32_t use_graph;        /* 1: replay the GN loop as a CUDA graph (default), 0: plain launches */
+} ds_params;
+
+/* Per-solve statistics (filled by ds_solve when its `out` is not NULL). */
+typedef struct {
+  int32_t iters;                  /* iterations run                                          */
+  int32_t n_inliers;              /* preselected matches                                     */
+  int32_t n_kept;                 /* kept RANSAC references                                  */
+  int32_t n_icp_valid_last;       /* valid ICP associations at the last linearisation        */
+  double w_arap;                  /* the frame's w_ARAP                                       */
+  double cost[DS_MAX_ITERS];      /* Eq. 1 at each linearisation point                        */
+  double cost_icp[DS_MAX_ITERS];
+  double cost_orb[DS_MAX_ITERS];
+  double cost_arap[DS_MAX_ITERS];
+} ds_solve_stats;
+
+/* Fills *p with the defaults listed above. */
+void ds_default_params(ds_params* p);
+
+/* Creates a handle from a template depth map (Section 2: the template is generated from the
+ * first frame). depth_hw: H x W FP32 depths in mm, <= 0 or non-finite = no surface.
+ * W, H in [8, 4096]. p may be NULL (defaults). cuda_stream: the cudaStream_t to run on, or
+ * NULL for a stream owned by the handle. On success *out receives the handle.
+ * Errors: DS_ERR_ARG, DS_ERR_BAD_INPUT (NaN/inf depth), DS_ERR_OOM, DS_ERR_CUDA. */
+int ds_create_template(const float* depth_hw, int32_t W, int32_t H, ds_intrinsics K,
+                       const ds_params* p, void* cuda_stream, ds_handle* out);
+
+/* Places N control points at template pixels pixel_index[0..N) (Section 2: sparse control
+ * points on the template); g_i is the template point at that pixel. Builds the blend tables
+ * (4 nearest control points by 3D distance, Gaussian weights) and resets every warp to the
+ * identity. N in [5, 2048]; every index must be a distinct valid template pixel.
+ * Errors: DS_ERR_ARG, DS_ERR_OOM, DS_ERR_CUDA. */
+int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N);
+
+/* Submits one live frame: depth_hw (H x W FP32, same size as the template; <= 0 = no data),
+ * M feature matches (match_tmpl_idx[k] = template pixel of match k, match_xyz[3k..3k+2] = its
+ * live 3D point), and hyp_list[0..n_hyp) = the reference match ids of the 1-point RANSAC
+ * (Section 2.1). Runs the frame preparation (live points and normals) and the RANSAC
+ * preselection on the handle's stream. M in [0, 65536]; with M == 0 hyp_list may be NULL.
+ * Host-memory indices are checked before the call returns. Device-memory indices are checked
+ * on the device without a host synchronisation: an out-of-range template pixel or reference id
+ * is replaced by 0 before any kernel reads it, and the next synchronising call (ds_solve with
+ * stats, any ds_get_*) returns DS_ERR_ARG. Non-finite depth or match coordinates are reported
+ * the same way as DS_ERR_BAD_INPUT.
+ * Errors: DS_ERR_ARG, DS_ERR_BAD_INPUT, DS_ERR_STATE (no control points), DS_ERR_CUDA. */
+int ds_submit_frame(ds_handle h, const float* depth_hw, const int32_t* match_tmpl_idx,
+                    const float* match_xyz, int32_t M, const int32_t* hyp_list);
+
+/* Runs `iters` damped Gauss-Newton iterations (1..DS_MAX_ITERS) of Eq. 1 on the submitted
+ * frame, starting from the current warps (warm start). Asynchronous unless `out` is not NULL,
+ * in which case the stream is synchronised and *out filled.
+ * Errors: DS_ERR_ARG, DS_ERR_STATE (no frame), DS_ERR_NOT_SPD, DS_ERR_CUDA. */
+int ds_solve(ds_handle h, int32_t iters, ds_solve_stats* out);
+
+/* Solves n handles, each with its own submitted frame, `iters` iterations each; the work of
+ * all handles is issued before any of them is waited on. Equivalent to ds_solve on each. */
+int ds_solve_batch(ds_handle* hs, int32_t n, int32_t iters);
+
+/* Copies the current warps out: q_N4 (w, x, y, z per node), t_N3, and the control-point
+ * positions p_i = W_i(g_i) = g_i + t_i (Eq. 6 notation) into pos_N3. Any pointer may be NULL. */
+int ds_get_deformation(ds_handle h, float* q_N4, float* t_N3, float* pos_N3);
+
+/* FP64 copy of the warps (q_N4, t_N3); either may be NULL. */
+int ds_get_deformation64(ds_handle h, double* q_N4, double* t_N3);
+
+/* Overwrites the warps (resume / warm start from a saved state). q rows are normalised. */
+int ds_set_deformation(ds_handle h, const float* q_N4, const float* t_N3);
+
+/* RANSAC results of the last submitted frame: bits[ceil(M/32)] preselection mask (bit k of
+ * word k/32), w_M[M] match weights (max over kept references), kept_bits (bit h = reference h
+ * kept), score_nh[n_hyp] (sum of weights of each reference). Any pointer may be NULL. */
+int ds_get_inlier_mask(ds_handle h, uint32_t* bits);
+int ds_get_ransac(ds_handle h, float* w_M, uint32_t* kept_bits, double* score_nh);
+
+/* Eq. 1 cost at the last linearisation point of the last solve. */
+int ds_get_cost(ds_handle h, double* F);
+
+/* Inspection of intermediate results, for tests and tracing. */
+/* Blend table in template pixel order for the P valid template pixels (ascending pixel index):
+ * pix_P, node ids nid_P4 (nearest first) and weights alpha_P4. Any pointer may be NULL.
+ * *P_out receives P. */
+int ds_get_blend_table(ds_handle h, int32_t* P_out, int32_t* pix_P, int32_t* nid_P4,
+                       float* alpha_P4);
+/* Live points (x, y, z, valid) and normals (nx, ny, nz, 0) of the last frame, H*W*4 floats. */
+int ds_get_frame_points(ds_handle h, float* pts4, float* nrm4);
+/* Linearises Eq. 1 at the current warps without stepping: the undamped normal equations
+ * A_nn (full symmetric, n = 6N, row-major), b_n = -J^T W r, and cost3 = {ICP, ORB, ARAP}.
+ * If w_arap_in > 0 it is used as w_ARAP; otherwise the per-frame rule sets it from this state.
+ * *w_arap_out (may be NULL) receives the w_ARAP used. */
+int ds_linearize(ds_handle h, double w_arap_in, double* A_nn, double* b_n, double* cost3,
+                 double* w_arap_out);
+
+/* Tracing. When on (set before the next ds_solve), the solve records CUDA events on the handle's
+ * stream around each phase of every iteration (inside the captured graph). ds_get_phase_times
+ * synchronises and returns the summed milliseconds of the last solve per phase:
+ * ms4[0] linearisation (ICP, ORB, dense ARAP and assembly), ms4[1] Cholesky factorisation,
+ * ms4[2] triangular solves and refinement, ms4[3] state update.
+ * ds_get_counters returns the number of kernels the handle has launched so far (graph kernel
+ * nodes count once per replay). */
+int ds_set_tracing(ds_handle h, int32_t on);
+int ds_get_phase_times(ds_handle h, double* ms4);
+int ds_get_counters(ds_handle h, int64_t* kernels_launched);
+
+/* Releases everything the handle owns. NULL is accepted. */
+int ds_destroy(ds_handle h);
+
+/* Static description of a status code. */
+const char* ds_status_str(int status);
+
+/* Library build identification (sm_103a build flags and version). */
+const char* ds_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DEFSOLVE_H */

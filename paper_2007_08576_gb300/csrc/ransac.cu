@@ -1,0 +1,356 @@
+// 1-point RANSAC + reweighting inlier preselection (Section 2.1, Eq. 2-4).
+//
+// One CTA per reference match k0. The CTA rectifies both 3D match sets to k0 (Eq. 2) into
+// shared memory (FP64, 56 B per match: S1, S2, w), then alternates n_reweight times
+//   R <- rotation maximising sum_k w_k S2(k)^T R S1(k)        (Eq. 3, weighted)
+//   d_k = |S2(k) - R S1(k)|,  w_k = min(H / d_k, 1)            (Eq. 4)
+// The rotation is Horn's unit quaternion: the eigenvector of the largest eigenvalue of the 4x4
+// symmetric matrix built from M = sum_k w_k S1(k) S2(k)^T. The largest eigenvalue is found by
+// Newton's method on the characteristic polynomial from a Gershgorin upper bound (monotone for
+// a polynomial with real roots), the eigenvector as the dominant column of the adjugate of
+// N - lambda I. A fit is degenerate (R = I) if sum w < 1e-12 or the two largest eigenvalues are
+// within 2e-12 |M|_F of each other.
+// After the last update the CTA writes its score sum_{k != k0} w_k, a bitset of d_k <= H
+// (warp ballots) and its weights; a second kernel keeps references whose score is at least
+// keep_frac times the best and combines them (mask = OR, weight = max).
+// Everything that decides a mask bit is FP64.
+#include <math.h>
+
+#include "ds_internal.cuh"
+
+namespace ds {
+
+static constexpr int kRansacThreads = 256;
+
+__device__ __forceinline__ double det3(double a, double b, double c, double d, double e, double f,
+                                       double g, double h, double i) {
+  return a * (e * i - f * h) - b * (d * i - f * g) + c * (d * h - e * g);
+}
+
+// Rotation matrix (row-major) from M[a][b] = sum w S1_a S2_b. Returns false if degenerate.
+__device__ bool horn_rotation(const double* M, double wsum, double* R) {
+  double Sxx = M[0], Sxy = M[1], Sxz = M[2];
+  double Syx = M[3], Syy = M[4], Syz = M[5];
+  double Szx = M[6], Szy = M[7], Szz = M[8];
+  double fro = 0.0;
+  for (int i = 0; i < 9; ++i) fro += M[i] * M[i];
+  fro = sqrt(fro);
+  if (!(wsum >= 1e-12) || !(fro > 0.0)) return false;
+  double N[4][4] = {{Sxx + Syy + Szz, Syz - Szy, Szx - Sxz, Sxy - Syx},
+                    {Syz - Szy, Sxx - Syy - Szz, Sxy + Syx, Szx + Sxz},
+                    {Szx - Sxz, Sxy + Syx, -Sxx + Syy - Szz, Syz + Szy},
+                    {Sxy - Syx, Szx + Sxz, Syz + Szy, -Sxx - Syy + Szz}};
+  // det(lambda I - N) = lambda^4 + e2 lambda^2 - e3 lambda + e4 (N is traceless)
+  double e2 = 0.0;
+  for (int i = 0; i < 4; ++i)
+    for (int j = i + 1; j < 4; ++j) e2 += N[i][i] * N[j][j] - N[i][j] * N[i][j];
+  double e3 = 0.0;
+  for (int skip = 0; skip < 4; ++skip) {
+    int r[3], c = 0;
+    for (int i = 0; i < 4; ++i)
+      if (i != skip) r[c++] = i;
+    e3 += det3(N[r[0]][r[0]], N[r[0]][r[1]], N[r[0]][r[2]], N[r[1]][r[0]], N[r[1]][r[1]],
+               N[r[1]][r[2]], N[r[2]][r[0]], N[r[2]][r[1]], N[r[2]][r[2]]);
+  }
+  double e4 = 0.0;
+  for (int j = 0; j < 4; ++j) {
+    int c[3], k = 0;
+    for (int i = 0; i < 4; ++i)
+      if (i != j) c[k++] = i;
+    double m = det3(N[1][c[0]], N[1][c[1]], N[1][c[2]], N[2][c[0]], N[2][c[1]], N[2][c[2]],
+                    N[3][c[0]], N[3][c[1]], N[3][c[2]]);
+    e4 += ((j & 1) ? -1.0 : 1.0) * N[0][j] * m;
+  }
+  // Newton from a Gershgorin bound
+  double lam = -INFINITY;
+  for (int i = 0; i < 4; ++i) {
+    double r = N[i][i];
+    for (int j = 0; j < 4; ++j)
+      if (j != i) r += fabs(N[i][j]);
+    lam = fmax(lam, r);
+  }
+  for (int it = 0; it < 100; ++it) {
+    double l2 = lam * lam;
+    double p = (l2 + e2) * l2 - e3 * lam + e4;
+    double dp = 4.0 * l2 * lam + 2.0 * e2 * lam - e3;
+    if (!(dp > 0.0)) break;
+    double step = p / dp;
+    double nl = lam - step;
+    if (!(nl < lam)) break;
+    lam = nl;
+    if (step <= 1e-16 * fabs(lam)) break;
+  }
+  // deflate: p(x) / (x - lam) = x^3 + c2 x^2 + c1 x + c0, largest root by Newton from lam
+  double c2 = lam, c1 = e2 + lam * lam, c0 = -e3 + lam * c1;
+  double mu = lam;
+  for (int it = 0; it < 100; ++it) {
+    double p = ((mu + c2) * mu + c1) * mu + c0;
+    double dp = (3.0 * mu + 2.0 * c2) * mu + c1;
+    if (!(dp > 0.0)) break;
+    double step = p / dp;
+    double nm = mu - step;
+    if (!(nm < mu)) break;
+    mu = nm;
+    if (step <= 1e-16 * fabs(mu) + 1e-300) break;
+  }
+  if (!(lam - mu > 2e-12 * fro)) return false;
+  // adjugate of A = N - lam I: choose the largest diagonal cofactor, take its column
+  double A[4][4];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) A[i][j] = N[i][j] - (i == j ? lam : 0.0);
+  double best = -1.0;
+  int jb = 0;
+  for (int j = 0; j < 4; ++j) {
+    int r[3], k = 0;
+    for (int i = 0; i < 4; ++i)
+      if (i != j) r[k++] = i;
+    double m = fabs(det3(A[r[0]][r[0]], A[r[0]][r[1]], A[r[0]][r[2]], A[r[1]][r[0]],
+                         A[r[1]][r[1]], A[r[1]][r[2]], A[r[2]][r[0]], A[r[2]][r[1]],
+                         A[r[2]][r[2]]));
+    if (m > best) {
+      best = m;
+      jb = j;
+    }
+  }
+  double q[4];
+  {
+    int cols[3], k = 0;
+    for (int i = 0; i < 4; ++i)
+      if (i != jb) cols[k++] = i;
+    for (int i = 0; i < 4; ++i) {
+      int rows[3], kk = 0;
+      for (int t = 0; t < 4; ++t)
+        if (t != i) rows[kk++] = t;
+      // cofactor C_{i, jb}: delete row i, column jb (A symmetric, so this is column jb of adj)
+      double m = det3(A[rows[0]][cols[0]], A[rows[0]][cols[1]], A[rows[0]][cols[2]],
+                      A[rows[1]][cols[0]], A[rows[1]][cols[1]], A[rows[1]][cols[2]],
+                      A[rows[2]][cols[0]], A[rows[2]][cols[1]], A[rows[2]][cols[2]]);
+      q[i] = (((i + jb) & 1) ? -1.0 : 1.0) * m;
+    }
+  }
+  double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  if (!(qn > 0.0)) return false;
+  double w = q[0] / qn, x = q[1] / qn, y = q[2] / qn, z = q[3] / qn;
+  R[0] = 1 - 2 * (y * y + z * z);
+  R[1] = 2 * (x * y - w * z);
+  R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z);
+  R[4] = 1 - 2 * (x * x + z * z);
+  R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y);
+  R[7] = 2 * (y * z + w * x);
+  R[8] = 1 - 2 * (x * x + y * y);
+  return true;
+}
+
+// FP64 template point at pixel j, ((u - cx) z) / fx with single roundings.
+__device__ __forceinline__ void tmpl_point64(const float* depth0, int W, double fx, double fy,
+                                             double cx, double cy, int j, double* o) {
+  int u = j % W, v = j / W;
+  double z = (double)depth0[j];
+  o[0] = __ddiv_rn(__dmul_rn(__dsub_rn((double)u, cx), z), fx);
+  o[1] = __ddiv_rn(__dmul_rn(__dsub_rn((double)v, cy), z), fy);
+  o[2] = z;
+}
+
+template <int NV>
+__device__ __forceinline__ void block_sum(double* v, double* red /* NV * 32 */) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double x = v[i];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    v[i] = x;
+  }
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) red[i * 32 + warp] = v[i];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double x = 0.0;
+    for (int w = 0; w < nw; ++w) x += red[i * 32 + w];  // fixed order
+    v[i] = x;
+  }
+  __syncthreads();
+}
+
+__global__ __launch_bounds__(kRansacThreads) void k_ransac_hyp(
+    const float* __restrict__ depth0, int W, double fx, double fy, double cx, double cy,
+    const int* __restrict__ midx, const float* __restrict__ mxyz, int M,
+    const int* __restrict__ hyp, int n_reweight, double H, int use_smem,
+    double* __restrict__ scratch, uint32_t* __restrict__ hbits, float* __restrict__ hw,
+    double* __restrict__ score) {
+  extern __shared__ double sm[];
+  __shared__ double red[10 * 32];
+  __shared__ double sR[9];
+  const int h = blockIdx.x;
+  const int k0 = hyp[h];
+  double* S = use_smem ? sm : scratch + (size_t)h * 7 * M;
+  double* S1x = S;
+  double* S1y = S + M;
+  double* S1z = S + 2 * M;
+  double* S2x = S + 3 * M;
+  double* S2y = S + 4 * M;
+  double* S2z = S + 5 * M;
+  double* w = S + 6 * M;
+  double r1[3], r2[3];
+  tmpl_point64(depth0, W, fx, fy, cx, cy, midx[k0], r1);
+  r2[0] = (double)mxyz[3 * k0 + 0];
+  r2[1] = (double)mxyz[3 * k0 + 1];
+  r2[2] = (double)mxyz[3 * k0 + 2];
+  for (int k = threadIdx.x; k < M; k += blockDim.x) {
+    double o1[3];
+    tmpl_point64(depth0, W, fx, fy, cx, cy, midx[k], o1);
+    S1x[k] = o1[0] - r1[0];
+    S1y[k] = o1[1] - r1[1];
+    S1z[k] = o1[2] - r1[2];
+    S2x[k] = (double)mxyz[3 * k + 0] - r2[0];
+    S2y[k] = (double)mxyz[3 * k + 1] - r2[1];
+    S2z[k] = (double)mxyz[3 * k + 2] - r2[2];
+    w[k] = 1.0;
+  }
+  __syncthreads();
+  const int words = (M + 31) / 32;
+  for (int it = 0; it < n_reweight; ++it) {
+    double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k = threadIdx.x; k < M; k += blockDim.x) {
+      double wk = w[k];
+      double a0 = wk * S1x[k], a1 = wk * S1y[k], a2 = wk * S1z[k];
+      double b0 = S2x[k], b1 = S2y[k], b2 = S2z[k];
+      acc[0] += a0 * b0;
+      acc[1] += a0 * b1;
+      acc[2] += a0 * b2;
+      acc[3] += a1 * b0;
+      acc[4] += a1 * b1;
+      acc[5] += a1 * b2;
+      acc[6] += a2 * b0;
+      acc[7] += a2 * b1;
+      acc[8] += a2 * b2;
+      acc[9] += wk;
+    }
+    block_sum<10>(acc, red);
+    if (threadIdx.x == 0) {
+      double R[9];
+      if (!horn_rotation(acc, acc[9], R)) {
+        for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0) ? 1.0 : 0.0;
+      }
+      for (int i = 0; i < 9; ++i) sR[i] = R[i];
+    }
+    __syncthreads();
+    double R0 = sR[0], R1 = sR[1], R2 = sR[2], R3 = sR[3], R4 = sR[4], R5 = sR[5], R6 = sR[6],
+           R7 = sR[7], R8 = sR[8];
+    const bool last = it == n_reweight - 1;
+    double sc = 0.0;
+    // warp-uniform trip count so that every lane reaches the ballot
+    for (int base = (threadIdx.x & ~31); base < M; base += blockDim.x) {
+      int k = base + (threadIdx.x & 31);
+      bool inl = false;
+      if (k < M) {
+        double x = S1x[k], y = S1y[k], z = S1z[k];
+        double e0 = S2x[k] - (R0 * x + R1 * y + R2 * z);
+        double e1 = S2y[k] - (R3 * x + R4 * y + R5 * z);
+        double e2 = S2z[k] - (R6 * x + R7 * y + R8 * z);
+        double d = sqrt(e0 * e0 + e1 * e1 + e2 * e2);
+        double wk = d > 0.0 ? fmin(H / d, 1.0) : 1.0;
+        w[k] = wk;
+        if (last) {
+          inl = d <= H;
+          hw[(size_t)h * M + k] = (float)wk;
+          if (k != k0) sc += wk;
+        }
+      }
+      if (last) {
+        uint32_t bits = __ballot_sync(0xffffffffu, inl);
+        if ((threadIdx.x & 31) == 0) hbits[(size_t)h * words + base / 32] = bits;
+      }
+    }
+    if (last) {
+      double v[1] = {sc};
+      block_sum<1>(v, red);
+      if (threadIdx.x == 0) score[h] = v[0];
+    }
+    __syncthreads();
+  }
+}
+
+// Keep references with score >= keep_frac * best; mask = OR of kept bitsets, weight = max of
+// kept weights. One CTA.
+__global__ void k_ransac_combine(const uint32_t* __restrict__ hbits, const float* __restrict__ hw,
+                                 const double* __restrict__ score, int n_hyp, int M,
+                                 double keep_frac, uint32_t* __restrict__ mask,
+                                 float* __restrict__ what, uint32_t* __restrict__ kept,
+                                 int* __restrict__ counts) {
+  __shared__ uint32_t skept[2];
+  __shared__ int sin;
+  if (threadIdx.x == 0) {
+    double best = -INFINITY;
+    for (int h = 0; h < n_hyp; ++h) best = fmax(best, score[h]);
+    uint32_t k0 = 0, k1 = 0;
+    int nk = 0;
+    for (int h = 0; h < n_hyp; ++h)
+      if (score[h] >= keep_frac * best) {
+        if (h < 32)
+          k0 |= 1u << h;
+        else
+          k1 |= 1u << (h - 32);
+        ++nk;
+      }
+    skept[0] = k0;
+    skept[1] = k1;
+    kept[0] = k0;
+    kept[1] = k1;
+    counts[1] = nk;
+    sin = 0;
+  }
+  __syncthreads();
+  const int words = (M + 31) / 32;
+  int local = 0;
+  for (int wd = threadIdx.x; wd < words; wd += blockDim.x) {
+    uint32_t m = 0;
+    for (int h = 0; h < n_hyp; ++h)
+      if ((skept[h >> 5] >> (h & 31)) & 1u) m |= hbits[(size_t)h * words + wd];
+    if (wd == words - 1 && (M & 31)) m &= (1u << (M & 31)) - 1u;
+    mask[wd] = m;
+    local += __popc(m);
+  }
+  for (int k = threadIdx.x; k < M; k += blockDim.x) {
+    float b = 0.f;
+    for (int h = 0; h < n_hyp; ++h)
+      if ((skept[h >> 5] >> (h & 31)) & 1u) b = fmaxf(b, hw[(size_t)h * M + k]);
+    what[k] = b;
+  }
+  atomicAdd(&sin, local);
+  __syncthreads();
+  if (threadIdx.x == 0) counts[0] = sin;
+}
+
+int ransac_smem_bytes(int M) { return 7 * (int)sizeof(double) * M; }
+
+void launch_ransac(const float* depth0, int W, ds_intrinsics K, const int* midx,
+                   const float* mxyz, int M, const int* hyp, int n_hyp, int n_reweight, double H,
+                   double keep_frac, double* scratch, uint32_t* hbits, float* hw, double* score,
+                   uint32_t* mask, float* what, uint32_t* kept, int* counts, cudaStream_t s) {
+  if (M <= 0 || n_hyp <= 0) return;
+  int sm = ransac_smem_bytes(M);
+  int use_smem = sm <= 220 * 1024;
+  if (use_smem) {
+    static bool attr_done = false;
+    if (!attr_done) {
+      cudaFuncSetAttribute(k_ransac_hyp, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+      attr_done = true;
+    }
+  } else {
+    sm = 0;
+  }
+  k_ransac_hyp<<<n_hyp, kRansacThreads, sm, s>>>(depth0, W, K.fx, K.fy, K.cx, K.cy, midx, mxyz,
+                                                 M, hyp, n_reweight, H, use_smem, scratch, hbits,
+                                                 hw, score);
+  ++g_launches;
+  k_ransac_combine<<<1, 256, 0, s>>>(hbits, hw, score, n_hyp, M, keep_frac, mask, what, kept,
+                                     counts);
+  ++g_launches;
+}
+
+}  // namespace ds

@@ -1,0 +1,709 @@
+// The three terms of Eq. 1 and the assembly of the damped normal equations.
+//
+// Unknowns: 6 per control point, (dtheta, dt), node-major. A step moves node i by
+// q_i <- exp(dtheta_i / 2) (x) q_i, t_i <- t_i + dt_i; the node's rigid map is
+// W_i(x) = R_i (x - g_i) + g_i + t_i, i.e. the dual quaternion (q_i, 1/2 (0, T_i) (x) q_i) with
+// T_i = g_i + t_i - R_i g_i (Section 2, dual-quaternion warps).
+//
+// Point terms (ICP, ORB) warp a template point p by dual-quaternion blending of its 4 nodes:
+// b = sum_k alpha_k s_k dq_k (s_k aligns each quaternion with the nearest node's),
+// x' = y(b) / |b_r|^2 with y = vec(b_r (x) (0,p) (x) b_r*) + 2 vec(b_d (x) b_r*).
+// For a direction n, h = d(n . x')/db is evaluated in closed form, and the Jacobian of n . x'
+// with respect to node k's (dtheta, dt) is alpha_k s_k times
+//   dtheta: 1/2 f_v - 1/4 e_w T_k + 1/2 e_v x (R_k g_k + T_k / 2),   dt: 1/2 e_v
+// with f = h_r (x) q_k*, e = h_d (x) q_k*.
+//
+// ICP (Section 2): r = n_q . (x' - q) at the pixel the warped point projects to (nearest
+// pixel centre), Tukey IRLS weight (1 - (r/c)^2)^2; only the normal-direction distance counts.
+// ORB (Section 2.1): r = x'(j_k) - o2_k, weight w_ORB * omega_k, omega_k = RANSAC weight of a
+// preselected match, else clamp(1 - |r| / (5H), 0, 1).
+// ARAP (Section 2.2, Eq. 5-6): all ordered pairs of control points, closed-form J^T W J blocks.
+//
+// Accumulation: the ICP and ORB passes add their 6x6 blocks into a block-sparse table (one
+// entry per node pair that shares a template point) and their gradients into a vector; the
+// ARAP pass writes every lower block of A exactly once, adding the data blocks, the damping
+// lambda (diag + eps) and b = -(J^T W r).
+#include <math.h>
+
+#include "ds_internal.cuh"
+
+namespace ds {
+
+struct Q {
+  float w, x, y, z;
+};
+struct V {
+  float x, y, z;
+};
+
+__device__ __forceinline__ Q q4(float4 a) { return {a.x, a.y, a.z, a.w}; }
+__device__ __forceinline__ V v3(float4 a) { return {a.x, a.y, a.z}; }
+__device__ __forceinline__ Q qmul(Q a, Q b) {
+  return {a.w * b.w - a.x * b.x - a.y * b.y - a.z * b.z,
+          a.w * b.x + a.x * b.w + a.y * b.z - a.z * b.y,
+          a.w * b.y - a.x * b.z + a.y * b.w + a.z * b.x,
+          a.w * b.z + a.x * b.y - a.y * b.x + a.z * b.w};
+}
+__device__ __forceinline__ Q qconj(Q a) { return {a.w, -a.x, -a.y, -a.z}; }
+__device__ __forceinline__ float qdot(Q a, Q b) {
+  return a.w * b.w + a.x * b.x + a.y * b.y + a.z * b.z;
+}
+__device__ __forceinline__ float dot(V a, V b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V cross(V a, V b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ V add(V a, V b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V sub(V a, V b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V mul(V a, float s) { return {a.x * s, a.y * s, a.z * s}; }
+
+// ----------------------------------------------------------------------------- node update
+
+// FP64 state step and the FP32 node tables of the next linearisation. x == nullptr: no step.
+// Thread 0 also records the linearisation's costs into hist[it] and clears the accumulators.
+__global__ void k_node_update(const double* __restrict__ x, int N, double* __restrict__ q64,
+                              double* __restrict__ t64, const double* __restrict__ g64,
+                              const double* __restrict__ gc, NodeGPU* __restrict__ node,
+                              PairNode* __restrict__ pn) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double qw = q64[4 * i], qx = q64[4 * i + 1], qy = q64[4 * i + 2], qz = q64[4 * i + 3];
+  double tx = t64[3 * i], ty = t64[3 * i + 1], tz = t64[3 * i + 2];
+  if (x) {
+    double a = x[6 * i], b = x[6 * i + 1], c = x[6 * i + 2];
+    double th = sqrt(a * a + b * b + c * c);
+    double ew, sf;
+    if (th > 0.0) {
+      ew = cos(0.5 * th);
+      sf = sin(0.5 * th) / th;
+    } else {
+      ew = 1.0;
+      sf = 0.5;
+    }
+    double ex = sf * a, ey = sf * b, ez = sf * c;
+    // (ew, e) (x) q
+    double nw = ew * qw - ex * qx - ey * qy - ez * qz;
+    double nx = ew * qx + ex * qw + ey * qz - ez * qy;
+    double ny = ew * qy - ex * qz + ey * qw + ez * qx;
+    double nz = ew * qz + ex * qy - ey * qx + ez * qw;
+    double nn = 1.0 / sqrt(nw * nw + nx * nx + ny * ny + nz * nz);
+    if (nw < 0) nn = -nn;
+    qw = nw * nn;
+    qx = nx * nn;
+    qy = ny * nn;
+    qz = nz * nn;
+    tx += x[6 * i + 3];
+    ty += x[6 * i + 4];
+    tz += x[6 * i + 5];
+    q64[4 * i] = qw;
+    q64[4 * i + 1] = qx;
+    q64[4 * i + 2] = qy;
+    q64[4 * i + 3] = qz;
+    t64[3 * i] = tx;
+    t64[3 * i + 1] = ty;
+    t64[3 * i + 2] = tz;
+  }
+  double R[9] = {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy),
+                 2 * (qx * qy + qw * qz),     1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx),
+                 2 * (qx * qz - qw * qy),     2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)};
+  double gx = g64[3 * i], gy = g64[3 * i + 1], gz = g64[3 * i + 2];
+  double Rgx = R[0] * gx + R[1] * gy + R[2] * gz;
+  double Rgy = R[3] * gx + R[4] * gy + R[5] * gz;
+  double Rgz = R[6] * gx + R[7] * gy + R[8] * gz;
+  double Tx = gx + tx - Rgx, Ty = gy + ty - Rgy, Tz = gz + tz - Rgz;
+  // d = 1/2 (0, T) (x) q
+  double dw = 0.5 * (-Tx * qx - Ty * qy - Tz * qz);
+  double dx = 0.5 * (Tx * qw + Ty * qz - Tz * qy);
+  double dy = 0.5 * (-Tx * qz + Ty * qw + Tz * qx);
+  double dz = 0.5 * (Tx * qy - Ty * qx + Tz * qw);
+  NodeGPU nd;
+  nd.q = make_float4((float)qw, (float)qx, (float)qy, (float)qz);
+  nd.d = make_float4((float)dw, (float)dx, (float)dy, (float)dz);
+  nd.T = make_float4((float)Tx, (float)Ty, (float)Tz, 0.f);
+  nd.w = make_float4((float)(Rgx + 0.5 * Tx), (float)(Rgy + 0.5 * Ty), (float)(Rgz + 0.5 * Tz),
+                     0.f);
+  node[i] = nd;
+  PairNode p;
+  double cxg = gx - gc[0], cyg = gy - gc[1], czg = gz - gc[2];
+  p.q = nd.q;
+  p.g = make_float4((float)cxg, (float)cyg, (float)czg, 0.f);
+  p.p = make_float4((float)(cxg + tx), (float)(cyg + ty), (float)(czg + tz), 0.f);
+  p.R0 = make_float4((float)R[0], (float)R[1], (float)R[2], 0.f);
+  p.R1 = make_float4((float)R[3], (float)R[4], (float)R[5], 0.f);
+  p.R2 = make_float4((float)R[6], (float)R[7], (float)R[8], 0.f);
+  pn[i] = p;
+}
+
+void launch_node_update(const double* x, int N, double* q64, double* t64, const double* g64,
+                        const double* gc, NodeGPU* node, PairNode* pn, cudaStream_t s) {
+  k_node_update<<<(N + 127) / 128, 128, 0, s>>>(x, N, q64, t64, g64, gc, node, pn);
+  ++g_launches;
+}
+
+// ----------------------------------------------------------------------------- blending
+
+struct Blend {
+  Q br, bd;      // blended dual quaternion (unnormalised)
+  float inv_s;   // 1 / |b_r|^2
+  V x;           // warped point
+  float sgn[4];  // sign alignment per slot
+};
+
+__device__ __forceinline__ void blend_point(const NodeGPU* __restrict__ node, const int* nid,
+                                            const float* alpha, int near, V p, Blend& B,
+                                            NodeGPU* nd) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) nd[k] = node[nid[k]];
+  Q qn = q4(nd[near].q);
+  Q br = {0, 0, 0, 0}, bd = {0, 0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    Q qk = q4(nd[k].q), dk = q4(nd[k].d);
+    float s = qdot(qk, qn) >= 0.f ? 1.f : -1.f;
+    B.sgn[k] = s;
+    float a = alpha[k] * s;
+    br.w += a * qk.w;
+    br.x += a * qk.x;
+    br.y += a * qk.y;
+    br.z += a * qk.z;
+    bd.w += a * dk.w;
+    bd.x += a * dk.x;
+    bd.y += a * dk.y;
+    bd.z += a * dk.z;
+  }
+  V bv = {br.x, br.y, br.z}, dv = {bd.x, bd.y, bd.z};
+  float bw = br.w, dw = bd.w;
+  float s = bw * bw + dot(bv, bv);
+  // rotation part (bw^2 - |bv|^2) p + 2 (bv.p) bv + 2 bw (bv x p)
+  V y = add(add(mul(p, bw * bw - dot(bv, bv)), mul(bv, 2.f * dot(bv, p))),
+            mul(cross(bv, p), 2.f * bw));
+  // translation part 2 (bw dv - dw bv + bv x dv)
+  y = add(y, mul(sub(sub(mul(dv, bw), mul(bv, dw)), mul(cross(dv, bv), 1.f)), 2.f));
+  B.br = br;
+  B.bd = bd;
+  B.inv_s = 1.f / s;
+  B.x = mul(y, B.inv_s);
+}
+
+// h = d(n . x') / db for a direction n (8 entries: b_r then b_d).
+__device__ __forceinline__ void dir_grad(V n, V p, const Blend& B, float* h) {
+  V bv = {B.br.x, B.br.y, B.br.z}, dv = {B.bd.x, B.bd.y, B.bd.z};
+  float bw = B.br.w, dw = B.bd.w;
+  float np = dot(n, p), nbv = dot(n, bv), bvp = dot(bv, p), nx = dot(n, B.x);
+  float g0 = 2.f * bw * np + 2.f * dot(n, cross(bv, p)) + 2.f * dot(n, dv);
+  V gv = add(add(mul(bv, -2.f * np), mul(add(mul(p, nbv), mul(n, bvp)), 2.f)),
+             add(mul(cross(p, n), 2.f * bw), add(mul(n, -2.f * dw), mul(cross(dv, n), 2.f))));
+  float gdw = -2.f * nbv;
+  V gdv = add(mul(n, 2.f * bw), mul(cross(n, bv), 2.f));
+  float is = B.inv_s, t = 2.f * nx;
+  h[0] = (g0 - t * bw) * is;
+  h[1] = (gv.x - t * bv.x) * is;
+  h[2] = (gv.y - t * bv.y) * is;
+  h[3] = (gv.z - t * bv.z) * is;
+  h[4] = gdw * is;
+  h[5] = gdv.x * is;
+  h[6] = gdv.y * is;
+  h[7] = gdv.z * is;
+}
+
+// Jacobian (6) of n . x' w.r.t. one node's (dtheta, dt), scaled by `scale`.
+__device__ __forceinline__ void slot_jac(const float* h, const NodeGPU& nd, float scale,
+                                         float* J) {
+  Q qc = qconj(q4(nd.q));
+  Q f = qmul({h[0], h[1], h[2], h[3]}, qc);
+  Q e = qmul({h[4], h[5], h[6], h[7]}, qc);
+  V ev = {e.x, e.y, e.z};
+  V ew = cross(ev, v3(nd.w));
+  V T = v3(nd.T);
+  J[0] = scale * (0.5f * f.x - 0.25f * e.w * T.x + 0.5f * ew.x);
+  J[1] = scale * (0.5f * f.y - 0.25f * e.w * T.y + 0.5f * ew.y);
+  J[2] = scale * (0.5f * f.z - 0.25f * e.w * T.z + 0.5f * ew.z);
+  J[3] = scale * 0.5f * ev.x;
+  J[4] = scale * 0.5f * ev.y;
+  J[5] = scale * 0.5f * ev.z;
+}
+
+// ----------------------------------------------------------------------------- ICP
+
+// One thread per template point (points sorted by their node quadruple, so that a segment of
+// consecutive points shares the same 4 nodes). Each CTA reduces the sqrt-weighted Jacobians of
+// its tile per segment in shared memory and adds the segment's 10 blocks and gradient into
+// the block table with one atomic per entry.
+__global__ __launch_bounds__(kTile) void k_icp(
+    const float4* __restrict__ tp, const float4* __restrict__ tw,
+    const int4* __restrict__ segnodes, const int* __restrict__ segbp, int P,
+    const NodeGPU* __restrict__ node, const float4* __restrict__ tgt_pt,
+    const float4* __restrict__ tgt_nrm, int W, int H, float fx, float fy, float cx, float cy,
+    float c, float* __restrict__ blk, float* __restrict__ gdata, double* __restrict__ acc) {
+  __shared__ float sJ[kTile][25];
+  __shared__ int sSeg[kTile];
+  __shared__ int sStart[kTile + 1];
+  __shared__ int sWarpCnt[kTile / 32 + 1];
+  __shared__ float sRed[3][kTile / 32];
+  const int tid = threadIdx.x;
+  const int base = blockIdx.x * kTile;
+  const int len = min(kTile, P - base);
+  const int pidx = base + tid;
+  float Jt[24];
+#pragma unroll
+  for (int i = 0; i < 24; ++i) Jt[i] = 0.f;
+  float rt = 0.f, rho = 0.f, wv = 0.f, nv = 0.f;
+  int seg = -1;
+  if (tid < len) {
+    float4 a = tp[pidx];
+    int bits = __float_as_int(a.w);
+    seg = bits >> 2;
+    int near = bits & 3;
+    int4 nn = segnodes[seg];
+    float4 al = tw[pidx];
+    int nid[4] = {nn.x, nn.y, nn.z, nn.w};
+    float alp[4] = {al.x, al.y, al.z, al.w};
+    V p = {a.x, a.y, a.z};
+    Blend B;
+    NodeGPU nd[4];
+    blend_point(node, nid, alp, near, p, B, nd);
+    V x = B.x;
+    if (x.z > 0.f) {
+      float u = fx * x.x / x.z + cx;
+      float v = fy * x.y / x.z + cy;
+      float pu = floorf(u + 0.5f), pv = floorf(v + 0.5f);
+      if (pu >= 0.f && pu < (float)W && pv >= 0.f && pv < (float)H) {
+        int pix = (int)pv * W + (int)pu;
+        float4 q = tgt_pt[pix];
+        if (q.w > 0.f) {
+          float4 n4 = tgt_nrm[pix];
+          V n = {n4.x, n4.y, n4.z};
+          float r = dot(n, sub(x, {q.x, q.y, q.z}));
+          nv = 1.f;
+          float cc6 = c * c * (1.f / 6.f);
+          if (fabsf(r) < c) {
+            float uu = r / c;
+            float sig = 1.f - uu * uu;
+            wv = sig * sig;
+            rho = cc6 * (1.f - sig * sig * sig);
+            float h[8];
+            dir_grad(n, p, B, h);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) slot_jac(h, nd[k], alp[k] * B.sgn[k] * sig, &Jt[6 * k]);
+            rt = sig * r;
+          } else {
+            rho = cc6;
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 24; ++i) sJ[tid][i] = Jt[i];
+  sJ[tid][24] = rt;
+  sSeg[tid] = seg;
+  // cost / weight / count reduction
+  {
+    float v0 = rho, v1 = wv, v2 = nv;
+    for (int o = 16; o > 0; o >>= 1) {
+      v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+      v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+      v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+    }
+    if ((tid & 31) == 0) {
+      sRed[0][tid >> 5] = v0;
+      sRed[1][tid >> 5] = v1;
+      sRed[2][tid >> 5] = v2;
+    }
+  }
+  __syncthreads();
+  // segment starts within the tile (segments are contiguous because points are sorted)
+  bool start = tid < len && (tid == 0 || sSeg[tid] != sSeg[tid - 1]);
+  unsigned bal = __ballot_sync(0xffffffffu, start);
+  if ((tid & 31) == 0) sWarpCnt[tid >> 5] = __popc(bal);
+  if (tid == 0) {
+    double a0 = 0, a1 = 0, a2 = 0;
+    for (int w = 0; w < kTile / 32; ++w) {
+      a0 += sRed[0][w];
+      a1 += sRed[1][w];
+      a2 += sRed[2][w];
+    }
+    atomicAdd(&acc[ACC_COST_ICP], a0);
+    atomicAdd(&acc[ACC_WSUM_ICP], a1);
+    atomicAdd(&acc[ACC_NVALID], a2);
+  }
+  __syncthreads();
+  if (start) {
+    int off = 0;
+    for (int w = 0; w < (tid >> 5); ++w) off += sWarpCnt[w];
+    off += __popc(bal & ((1u << (tid & 31)) - 1u));
+    sStart[off] = tid;
+  }
+  int nseg = 0;
+  for (int w = 0; w < kTile / 32; ++w) nseg += sWarpCnt[w];
+  if (tid == 0) sStart[nseg] = len;
+  __syncthreads();
+  for (int si = 0; si < nseg; ++si) {
+    const int lo = sStart[si], hi = sStart[si + 1];
+    const int sg = sSeg[lo];
+    for (int o = tid; o < kOuts; o += kTile) {
+      float s = 0.f;
+      if (o < 360) {
+        int k = o / 36, e = o % 36;
+        int ai = 6 * kSlotPairI(k) + e / 6, bj = 6 * kSlotPairJ(k) + e % 6;
+        for (int pp = lo; pp < hi; ++pp) s += sJ[pp][ai] * sJ[pp][bj];
+        if (s != 0.f) atomicAdd(&blk[(size_t)segbp[sg * 10 + k] * 36 + e], s);
+      } else {
+        int a = o - 360;
+        for (int pp = lo; pp < hi; ++pp) s += sJ[pp][a] * sJ[pp][24];
+        if (s != 0.f) {
+          int4 nn = segnodes[sg];
+          int nd = (a / 6 == 0) ? nn.x : (a / 6 == 1) ? nn.y : (a / 6 == 2) ? nn.z : nn.w;
+          atomicAdd(&gdata[6 * nd + a % 6], s);
+        }
+      }
+    }
+  }
+}
+
+void launch_icp(const float4* tp, const float4* tw, const int4* segnodes, const int* segbp,
+                int P, const NodeGPU* node, const float4* tgt_pt, const float4* tgt_nrm,
+                int W, int H, ds_intrinsics K, float c, float* blk, float* gdata, double* acc,
+                cudaStream_t s) {
+  if (P <= 0) return;
+  k_icp<<<(P + kTile - 1) / kTile, kTile, 0, s>>>(tp, tw, segnodes, segbp, P, node, tgt_pt,
+                                                  tgt_nrm, W, H, K.fx, K.fy, K.cx, K.cy, c, blk,
+                                                  gdata, acc);
+  ++g_launches;
+}
+
+// ----------------------------------------------------------------------------- ORB
+
+__global__ __launch_bounds__(128) void k_orb(
+    const int* __restrict__ midx, const float* __restrict__ mxyz, int M,
+    const int* __restrict__ rank, const float4* __restrict__ tp, const float4* __restrict__ tw,
+    const int4* __restrict__ segnodes, const int* __restrict__ segbp,
+    const NodeGPU* __restrict__ node, const uint32_t* __restrict__ mask,
+    const float* __restrict__ what, float H, float w_orb, float* __restrict__ blk,
+    float* __restrict__ gdata, double* __restrict__ acc) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  float cost = 0.f, wsum = 0.f;
+  if (k < M) {
+    int sp = rank[midx[k]];
+    if (sp >= 0) {
+      float4 a = tp[sp];
+      int bits = __float_as_int(a.w);
+      int seg = bits >> 2, near = bits & 3;
+      int4 nn = segnodes[seg];
+      float4 al = tw[sp];
+      int nid[4] = {nn.x, nn.y, nn.z, nn.w};
+      float alp[4] = {al.x, al.y, al.z, al.w};
+      V p = {a.x, a.y, a.z};
+      Blend B;
+      NodeGPU nd[4];
+      blend_point(node, nid, alp, near, p, B, nd);
+      V r = sub(B.x, {mxyz[3 * k], mxyz[3 * k + 1], mxyz[3 * k + 2]});
+      float d = sqrtf(dot(r, r));
+      bool pre = (mask[k >> 5] >> (k & 31)) & 1u;
+      float om = pre ? what[k] : fminf(fmaxf(1.f - d / (5.f * H), 0.f), 1.f);
+      cost = 0.5f * w_orb * om * dot(r, r);
+      wsum = om;
+      float sig = sqrtf(w_orb * om);
+      if (sig > 0.f) {
+        float J[3][24];
+        const V ax[3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+#pragma unroll
+        for (int row = 0; row < 3; ++row) {
+          float h[8];
+          dir_grad(ax[row], p, B, h);
+#pragma unroll
+          for (int s = 0; s < 4; ++s) slot_jac(h, nd[s], alp[s] * B.sgn[s] * sig, &J[row][6 * s]);
+        }
+        float rr[3] = {sig * r.x, sig * r.y, sig * r.z};
+        for (int kk = 0; kk < 10; ++kk) {
+          int bp = segbp[seg * 10 + kk];
+          int ib = 6 * kSlotPairI(kk), jb = 6 * kSlotPairJ(kk);
+          for (int e = 0; e < 36; ++e) {
+            int ai = ib + e / 6, bj = jb + e % 6;
+            float v = J[0][ai] * J[0][bj] + J[1][ai] * J[1][bj] + J[2][ai] * J[2][bj];
+            if (v != 0.f) atomicAdd(&blk[(size_t)bp * 36 + e], v);
+          }
+        }
+        for (int a2 = 0; a2 < 24; ++a2) {
+          float v = J[0][a2] * rr[0] + J[1][a2] * rr[1] + J[2][a2] * rr[2];
+          int ndid = nid[a2 / 6];
+          if (v != 0.f) atomicAdd(&gdata[6 * ndid + a2 % 6], v);
+        }
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    cost += __shfl_xor_sync(0xffffffffu, cost, o);
+    wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+  }
+  if ((threadIdx.x & 31) == 0 && (cost != 0.f || wsum != 0.f)) {
+    atomicAdd(&acc[ACC_COST_ORB], (double)cost);
+    atomicAdd(&acc[ACC_WSUM_ORB], (double)wsum);
+  }
+}
+
+void launch_orb(const int* midx, const float* mxyz, int M, const int* rank, const float4* tp,
+                const float4* tw, const int4* segnodes, const int* segbp, const NodeGPU* node,
+                const uint32_t* mask, const float* what, float H, float w_orb, float* blk,
+                float* gdata, double* acc, cudaStream_t s) {
+  if (M <= 0) return;
+  k_orb<<<(M + 127) / 128, 128, 0, s>>>(midx, mxyz, M, rank, tp, tw, segnodes, segbp, node,
+                                        mask, what, H, w_orb, blk, gdata, acc);
+  ++g_launches;
+}
+
+// ----------------------------------------------------------------------------- ARAP + assembly
+
+template <typename T>
+__device__ __forceinline__ void store_out(T* p, float v) {
+  *p = (T)v;
+}
+
+// One CTA per block row i1. For every partner i2 != i1 the CTA evaluates both ordered pairs
+// (i1, i2) and (i2, i1) in closed form; with u = unit(R_a (g_b - g_a)), v = unit(p_b - p_a),
+// l = |p_b - p_a|, P = I - v v^T, r = q_b (x) q_a*, s = sign(q_a . q_b) and per-pair weights
+// W_l = w, W_a = w w_angle, W_r = w w_rot (w = w_ARAP exp(-|g_a - g_b|^2 / 2 sigma^2)):
+//   diag(i1)   += [[W_a (I - u u^T) + W_r/2 I, C], [C^T, 2 Tm]],  C = W_a [u]x P / l,
+//                 Tm = W_l v v^T + W_a P / l^2
+//   A(i1, i2)   = [[-s W_r / 2 (r_w I - [r_v]x), -C], [-C'^T, -2 Tm]]   (C' of the reverse pair)
+//   grad(i1)   += [-W_a u x v - s W_r r_v, -2 W_l (l - l0) v + W_a (P u - P u') / l]
+// (u' = unit(R_i2 (g_i1 - g_i2))). Only the lower blocks (i2 <= i1) are written.
+template <typename T>
+__global__ __launch_bounds__(256) void k_arap_assemble(
+    const PairNode* __restrict__ pn, int N, float inv2sig2, const int* __restrict__ rowptr,
+    const int* __restrict__ rowcol, const int* __restrict__ rowbp, const float* __restrict__ blk,
+    const float* __restrict__ gdata, double* __restrict__ acc, int first_iter, double w_arap0,
+    float w_orb, float w_angle, float w_rot, double lam, double eps, T* __restrict__ Afac,
+    float* __restrict__ Aref, double* __restrict__ b) {
+  extern __shared__ int smap[];
+  __shared__ float sRed[28][8];
+  const int i1 = blockIdx.x;
+  const int n = 6 * N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) smap[i] = -1;
+  __syncthreads();
+  for (int e = rowptr[i1] + threadIdx.x; e < rowptr[i1 + 1]; e += blockDim.x)
+    smap[rowcol[e]] = rowbp[e];
+  double wa64;
+  if (first_iter)
+    wa64 = w_arap0 * (acc[ACC_WSUM_ICP] + (double)w_orb * acc[ACC_WSUM_ORB]) / N;
+  else
+    wa64 = acc[ACC_W_ARAP];
+  __syncthreads();
+  if (first_iter && i1 == 0 && threadIdx.x == 0) acc[ACC_W_ARAP] = wa64;
+  const float wA = (float)wa64;
+  const PairNode me = pn[i1];
+  const Q q1 = q4(me.q);
+  const V g1 = v3(me.g), p1 = v3(me.p);
+  const V R1a = v3(me.R0), R1b = v3(me.R1), R1c = v3(me.R2);
+  // diag accumulators: theta-theta (sym 6: xx xy xz yy yz zz), theta-t (9), t-t (sym 6)
+  float Dtt[6] = {0, 0, 0, 0, 0, 0}, Dtx[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  float Dxx[6] = {0, 0, 0, 0, 0, 0}, G[6] = {0, 0, 0, 0, 0, 0}, cost = 0.f;
+  for (int i2 = threadIdx.x; i2 < N; i2 += blockDim.x) {
+    if (i2 == i1) continue;
+    const PairNode o = pn[i2];
+    const Q q2 = q4(o.q);
+    const V g2 = v3(o.g), p2 = v3(o.p);
+    V dg = sub(g2, g1);
+    float L0 = sqrtf(dot(dg, dg));
+    V e = sub(p2, p1);
+    float l = sqrtf(dot(e, e));
+    float il = 1.f / l;
+    V v = mul(e, il);
+    V a = {dot(R1a, dg), dot(R1b, dg), dot(R1c, dg)};
+    V u = mul(a, rsqrtf(dot(a, a)));
+    V mdg = {-dg.x, -dg.y, -dg.z};
+    V a2 = {dot(v3(o.R0), mdg), dot(v3(o.R1), mdg), dot(v3(o.R2), mdg)};
+    V u2 = mul(a2, rsqrtf(dot(a2, a2)));
+    Q r = qmul(q2, qconj(q1));
+    float qq = qdot(q1, q2);
+    float s = qq >= 0.f ? 1.f : -1.f;
+    float w = wA * __expf(-dot(dg, dg) * inv2sig2);
+    float Wl = w, Wa = w * w_angle, Wr = w * w_rot;
+    float rl = l - L0;
+    V ang = sub(u, v);
+    Q rot = {q1.w - s * q2.w, q1.x - s * q2.x, q1.y - s * q2.y, q1.z - s * q2.z};
+    cost += 0.5f * (Wl * rl * rl + Wa * dot(ang, ang) + Wr * qdot(rot, rot));
+    // C = W_a [u]x P / l with P = I - v v^T:  [u]x - (u x v) v^T
+    V uxv = cross(u, v);
+    float ca = Wa * il;
+    float C[9] = {ca * (0.f - uxv.x * v.x), ca * (-u.z - uxv.x * v.y), ca * (u.y - uxv.x * v.z),
+                  ca * (u.z - uxv.y * v.x), ca * (0.f - uxv.y * v.y), ca * (-u.x - uxv.y * v.z),
+                  ca * (-u.y - uxv.z * v.x), ca * (u.x - uxv.z * v.y), ca * (0.f - uxv.z * v.z)};
+    // Tm = W_l v v^T + W_a (I - v v^T) / l^2
+    float tb = Wa * il * il;
+    float tv = Wl - tb;
+    float Tm[6] = {tb + tv * v.x * v.x, tv * v.x * v.y, tv * v.x * v.z,
+                   tb + tv * v.y * v.y, tv * v.y * v.z, tb + tv * v.z * v.z};
+    // diag
+    float hr = 0.5f * Wr;
+    Dtt[0] += Wa * (1.f - u.x * u.x) + hr;
+    Dtt[1] += -Wa * u.x * u.y;
+    Dtt[2] += -Wa * u.x * u.z;
+    Dtt[3] += Wa * (1.f - u.y * u.y) + hr;
+    Dtt[4] += -Wa * u.y * u.z;
+    Dtt[5] += Wa * (1.f - u.z * u.z) + hr;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Dtx[i] += C[i];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) Dxx[i] += 2.f * Tm[i];
+    // gradient
+    V rv = {r.x, r.y, r.z};
+    G[0] += -Wa * uxv.x - s * Wr * rv.x;
+    G[1] += -Wa * uxv.y - s * Wr * rv.y;
+    G[2] += -Wa * uxv.z - s * Wr * rv.z;
+    V Pu = sub(u, mul(v, dot(v, u)));
+    V Pu2 = sub(u2, mul(v, dot(v, u2)));
+    V gt = add(mul(v, -2.f * Wl * rl), mul(sub(Pu, Pu2), Wa * il));
+    G[3] += gt.x;
+    G[4] += gt.y;
+    G[5] += gt.z;
+    if (i2 < i1) {
+      // off-diagonal block (rows: i1's theta,t; cols: i2's theta,t)
+      float O[36];
+      float hs = -0.5f * s * Wr;
+      // theta-theta: hs (r_w I - [r_v]x)
+      O[0 * 6 + 0] = hs * r.w;
+      O[0 * 6 + 1] = hs * r.z;
+      O[0 * 6 + 2] = -hs * r.y;
+      O[1 * 6 + 0] = -hs * r.z;
+      O[1 * 6 + 1] = hs * r.w;
+      O[1 * 6 + 2] = hs * r.x;
+      O[2 * 6 + 0] = hs * r.y;
+      O[2 * 6 + 1] = -hs * r.x;
+      O[2 * 6 + 2] = hs * r.w;
+      // theta-t: -C
+#pragma unroll
+      for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) O[rr * 6 + 3 + cc] = -C[rr * 3 + cc];
+      // t-theta: -C'^T, C' = W_a/l ([u2]x - (u2 x v) v^T)
+      V u2xv = cross(u2, v);
+      float Cp[9] = {ca * (0.f - u2xv.x * v.x), ca * (-u2.z - u2xv.x * v.y),
+                     ca * (u2.y - u2xv.x * v.z), ca * (u2.z - u2xv.y * v.x),
+                     ca * (0.f - u2xv.y * v.y), ca * (-u2.x - u2xv.y * v.z),
+                     ca * (-u2.y - u2xv.z * v.x), ca * (u2.x - u2xv.z * v.y),
+                     ca * (0.f - u2xv.z * v.z)};
+#pragma unroll
+      for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) O[(3 + rr) * 6 + cc] = -Cp[cc * 3 + rr];
+      // t-t: -2 Tm
+      O[3 * 6 + 3] = -2.f * Tm[0];
+      O[3 * 6 + 4] = -2.f * Tm[1];
+      O[3 * 6 + 5] = -2.f * Tm[2];
+      O[4 * 6 + 3] = -2.f * Tm[1];
+      O[4 * 6 + 4] = -2.f * Tm[3];
+      O[4 * 6 + 5] = -2.f * Tm[4];
+      O[5 * 6 + 3] = -2.f * Tm[2];
+      O[5 * 6 + 4] = -2.f * Tm[4];
+      O[5 * 6 + 5] = -2.f * Tm[5];
+      int bp = smap[i2];
+      if (bp >= 0) {
+        const float* db = blk + (size_t)bp * 36;
+#pragma unroll
+        for (int i = 0; i < 36; ++i) O[i] += db[i];
+      }
+#pragma unroll
+      for (int rr = 0; rr < 6; ++rr) {
+        T* row = Afac + (size_t)(6 * i1 + rr) * n + 6 * i2;
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) store_out(row + cc, O[rr * 6 + cc]);
+      }
+      if (Aref) {
+#pragma unroll
+        for (int rr = 0; rr < 6; ++rr) {
+          float* row = Aref + (size_t)(6 * i1 + rr) * n + 6 * i2;
+#pragma unroll
+          for (int cc = 0; cc < 6; ++cc) row[cc] = O[rr * 6 + cc];
+        }
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) {
+          float* row = Aref + (size_t)(6 * i2 + cc) * n + 6 * i1;
+#pragma unroll
+          for (int rr = 0; rr < 6; ++rr) row[rr] = O[rr * 6 + cc];
+        }
+      }
+    }
+  }
+  // block reduction of the 28 per-thread sums
+  float vals[28];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) vals[i] = Dtt[i];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) vals[6 + i] = Dtx[i];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) vals[15 + i] = Dxx[i];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) vals[21 + i] = G[i];
+  vals[27] = cost;
+#pragma unroll
+  for (int i = 0; i < 28; ++i) {
+    float x = vals[i];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    vals[i] = x;
+  }
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int i = 0; i < 28; ++i) sRed[i][warp] = vals[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t[28];
+    for (int i = 0; i < 28; ++i) {
+      float x = 0.f;
+      for (int w = 0; w < nw; ++w) x += sRed[i][w];
+      t[i] = x;
+    }
+    float D[36];
+    // theta-theta
+    D[0] = t[0]; D[1] = t[1]; D[2] = t[2];
+    D[6] = t[1]; D[7] = t[3]; D[8] = t[4];
+    D[12] = t[2]; D[13] = t[4]; D[14] = t[5];
+    // theta-t and t-theta
+    for (int rr = 0; rr < 3; ++rr)
+      for (int cc = 0; cc < 3; ++cc) {
+        D[rr * 6 + 3 + cc] = t[6 + rr * 3 + cc];
+        D[(3 + cc) * 6 + rr] = t[6 + rr * 3 + cc];
+      }
+    // t-t
+    D[21] = t[15]; D[22] = t[16]; D[23] = t[17];
+    D[27] = t[16]; D[28] = t[18]; D[29] = t[19];
+    D[33] = t[17]; D[34] = t[19]; D[35] = t[20];
+    int bp = smap[i1];
+    if (bp >= 0) {
+      const float* db = blk + (size_t)bp * 36;
+      for (int i = 0; i < 36; ++i) D[i] += db[i];
+    }
+    for (int j = 0; j < 6; ++j) D[j * 7] += (float)(lam * ((double)D[j * 7] + eps));
+    for (int rr = 0; rr < 6; ++rr)
+      for (int cc = 0; cc < 6; ++cc) {
+        store_out(Afac + (size_t)(6 * i1 + rr) * n + 6 * i1 + cc, D[rr * 6 + cc]);
+        if (Aref) Aref[(size_t)(6 * i1 + rr) * n + 6 * i1 + cc] = D[rr * 6 + cc];
+      }
+    for (int j = 0; j < 6; ++j) b[6 * i1 + j] = -((double)t[21 + j] + (double)gdata[6 * i1 + j]);
+    atomicAdd(&acc[ACC_COST_ARAP], (double)t[27]);
+  }
+}
+
+template <typename T>
+void launch_arap_assemble(const PairNode* pn, int N, float inv2sig2, const int* rowptr,
+                          const int* rowcol, const int* rowbp, const float* blk,
+                          const float* gdata, double* acc, bool first_iter, double w_arap0,
+                          float w_orb, float w_angle, float w_rot, double lam, double eps,
+                          T* Afac, float* Aref, double* b, cudaStream_t s) {
+  k_arap_assemble<T><<<N, 256, sizeof(int) * N, s>>>(pn, N, inv2sig2, rowptr, rowcol, rowbp,
+                                                     blk, gdata, acc, first_iter ? 1 : 0,
+                                                     w_arap0, w_orb, w_angle, w_rot, lam, eps,
+                                                     Afac, Aref, b);
+  ++g_launches;
+}
+
+template void launch_arap_assemble<float>(const PairNode*, int, float, const int*, const int*,
+                                          const int*, const float*, const float*, double*, bool,
+                                          double, float, float, float, double, double, float*,
+                                          float*, double*, cudaStream_t);
+template void launch_arap_assemble<double>(const PairNode*, int, float, const int*, const int*,
+                                           const int*, const float*, const float*, double*, bool,
+                                           double, float, float, float, double, double, double*,
+                                           float*, double*, cudaStream_t);
+
+}  // namespace ds

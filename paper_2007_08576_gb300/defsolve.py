@@ -1,0 +1,315 @@
+"""Python binding of libdefsolve (the C ABI in include/defsolve.h).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA kernels. Arrays
+may be numpy arrays (host memory) or torch CUDA tensors (device memory); both are passed to the
+library as plain pointers. The library must be built first (paper_2007_08576_gb300.build); a
+missing library raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libdefsolve.so")
+
+DS_OK, DS_ERR_ARG, DS_ERR_OOM, DS_ERR_BAD_INPUT, DS_ERR_NOT_SPD, DS_ERR_STATE, DS_ERR_TIMEOUT, \
+    DS_ERR_CUDA = range(8)
+DS_PREC_FP64, DS_PREC_FP32, DS_PREC_FP32_REFINE = 0, 1, 2
+DS_MAX_ITERS = 64
+DS_MAX_HYP = 64
+
+# every exported symbol of include/defsolve.h
+EXPORTS = [
+    "ds_default_params", "ds_create_template", "ds_set_control_points", "ds_submit_frame",
+    "ds_solve", "ds_solve_batch", "ds_get_deformation", "ds_get_deformation64",
+    "ds_set_deformation", "ds_get_inlier_mask", "ds_get_ransac", "ds_get_cost",
+    "ds_get_blend_table", "ds_get_frame_points", "ds_linearize", "ds_set_tracing",
+    "ds_get_phase_times", "ds_get_counters", "ds_destroy", "ds_status_str", "ds_version",
+]
+
+
+class DsIntrinsics(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float),
+                ("cy", ctypes.c_float)]
+
+
+class DsParams(ctypes.Structure):
+    _fields_ = [("w_orb", ctypes.c_double), ("w_angle", ctypes.c_double),
+                ("w_rot", ctypes.c_double), ("w_arap0", ctypes.c_double),
+                ("H_mm", ctypes.c_double), ("tukey_c_mm", ctypes.c_double),
+                ("sigma_blend_scale", ctypes.c_double), ("sigma_arap_scale", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("eps_damp", ctypes.c_double),
+                ("keep_frac", ctypes.c_double), ("n_hyp", ctypes.c_int32),
+                ("n_reweight", ctypes.c_int32), ("n_nearest", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32)]
+
+
+class DsSolveStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("n_inliers", ctypes.c_int32),
+                ("n_kept", ctypes.c_int32), ("n_icp_valid_last", ctypes.c_int32),
+                ("w_arap", ctypes.c_double), ("cost", ctypes.c_double * DS_MAX_ITERS),
+                ("cost_icp", ctypes.c_double * DS_MAX_ITERS),
+                ("cost_orb", ctypes.c_double * DS_MAX_ITERS),
+                ("cost_arap", ctypes.c_double * DS_MAX_ITERS)]
+
+
+class DsError(RuntimeError):
+    def __init__(self, fn, status):
+        self.status = status
+        super().__init__(f"{fn}: {status_str(status)} ({status})")
+
+
+_lib = None
+
+
+def lib(path: str | None = None):
+    """Load libdefsolve.so once; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libdefsolve.so not built ({p}); run paper_2007_08576_gb300.build.build()")
+    L = ctypes.CDLL(p)
+    vp, i32, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+    sig = {
+        "ds_default_params": (None, [ctypes.POINTER(DsParams)]),
+        "ds_create_template": (i32, [vp, i32, i32, DsIntrinsics, ctypes.POINTER(DsParams), vp,
+                                     ctypes.POINTER(vp)]),
+        "ds_set_control_points": (i32, [vp, vp, i32]),
+        "ds_submit_frame": (i32, [vp, vp, vp, vp, i32, vp]),
+        "ds_solve": (i32, [vp, i32, ctypes.POINTER(DsSolveStats)]),
+        "ds_solve_batch": (i32, [ctypes.POINTER(vp), i32, i32]),
+        "ds_get_deformation": (i32, [vp, vp, vp, vp]),
+        "ds_get_deformation64": (i32, [vp, vp, vp]),
+        "ds_set_deformation": (i32, [vp, vp, vp]),
+        "ds_get_inlier_mask": (i32, [vp, vp]),
+        "ds_get_ransac": (i32, [vp, vp, vp, vp]),
+        "ds_get_cost": (i32, [vp, ctypes.POINTER(f64)]),
+        "ds_get_blend_table": (i32, [vp, ctypes.POINTER(i32), vp, vp, vp]),
+        "ds_get_frame_points": (i32, [vp, vp, vp]),
+        "ds_linearize": (i32, [vp, f64, vp, vp, vp, ctypes.POINTER(f64)]),
+        "ds_set_tracing": (i32, [vp, i32]),
+        "ds_get_phase_times": (i32, [vp, vp]),
+        "ds_get_counters": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
+        "ds_destroy": (i32, [vp]),
+        "ds_status_str": (ctypes.c_char_p, [i32]),
+        "ds_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def status_str(status: int) -> str:
+    return lib().ds_status_str(int(status)).decode()
+
+
+def _check(fn, rc):
+    if rc != DS_OK:
+        raise DsError(fn, rc)
+
+
+def _ptr(x, dtype):
+    """Plain pointer of a contiguous numpy array or torch tensor of the given numpy dtype."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if x.dtype != dtype or not x.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"expected a C-contiguous {np.dtype(dtype)} array")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        import torch
+        tmap = {np.float32: torch.float32, np.float64: torch.float64, np.int32: torch.int32,
+                np.uint32: torch.uint32 if hasattr(torch, "uint32") else torch.int32}
+        if x.dtype != tmap[np.dtype(dtype).type] or not x.is_contiguous():
+            raise TypeError(f"expected a contiguous tensor of {np.dtype(dtype)}")
+        return x.data_ptr()
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def default_params(**kw) -> DsParams:
+    p = DsParams()
+    lib().ds_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, "lambda_" if k == "lambda" else k, v)
+    return p
+
+
+# ----------------------------------------------------------------------------- the C ABI
+
+
+def ds_create_template(depth_hw, W, H, K, params: DsParams | None = None, stream=None):
+    h = ctypes.c_void_p()
+    Kc = DsIntrinsics(*[float(k) for k in K])
+    rc = lib().ds_create_template(_ptr(depth_hw, np.float32), int(W), int(H), Kc,
+                                  ctypes.byref(params) if params is not None else None,
+                                  stream, ctypes.byref(h))
+    _check("ds_create_template", rc)
+    return h
+
+
+def ds_set_control_points(h, pixel_index, N=None):
+    N = len(pixel_index) if N is None else N
+    _check("ds_set_control_points", lib().ds_set_control_points(h, _ptr(pixel_index, np.int32), int(N)))
+
+
+def ds_submit_frame(h, depth_hw, match_tmpl_idx, match_xyz, M=None, hyp_list=None):
+    M = (len(match_tmpl_idx) if match_tmpl_idx is not None else 0) if M is None else M
+    rc = lib().ds_submit_frame(h, _ptr(depth_hw, np.float32), _ptr(match_tmpl_idx, np.int32),
+                               _ptr(match_xyz, np.float32), int(M), _ptr(hyp_list, np.int32))
+    _check("ds_submit_frame", rc)
+
+
+def ds_solve(h, iters, stats: bool = False):
+    st = DsSolveStats() if stats else None
+    rc = lib().ds_solve(h, int(iters), ctypes.byref(st) if st is not None else None)
+    _check("ds_solve", rc)
+    return st
+
+
+def ds_solve_batch(handles, iters):
+    arr = (ctypes.c_void_p * len(handles))(*[hh.value if isinstance(hh, ctypes.c_void_p) else hh
+                                             for hh in handles])
+    _check("ds_solve_batch", lib().ds_solve_batch(arr, len(handles), int(iters)))
+
+
+def ds_get_deformation(h, q_N4=None, t_N3=None, pos_N3=None):
+    rc = lib().ds_get_deformation(h, _ptr(q_N4, np.float32), _ptr(t_N3, np.float32),
+                                  _ptr(pos_N3, np.float32))
+    _check("ds_get_deformation", rc)
+
+
+def ds_get_deformation64(h, q_N4=None, t_N3=None):
+    _check("ds_get_deformation64",
+           lib().ds_get_deformation64(h, _ptr(q_N4, np.float64), _ptr(t_N3, np.float64)))
+
+
+def ds_set_deformation(h, q_N4, t_N3):
+    _check("ds_set_deformation",
+           lib().ds_set_deformation(h, _ptr(q_N4, np.float32), _ptr(t_N3, np.float32)))
+
+
+def ds_get_inlier_mask(h, bits):
+    _check("ds_get_inlier_mask", lib().ds_get_inlier_mask(h, _ptr(bits, np.uint32)))
+
+
+def ds_get_ransac(h, w_M=None, kept_bits=None, score_nh=None):
+    _check("ds_get_ransac", lib().ds_get_ransac(h, _ptr(w_M, np.float32),
+                                                _ptr(kept_bits, np.uint32),
+                                                _ptr(score_nh, np.float64)))
+
+
+def ds_get_cost(h) -> float:
+    F = ctypes.c_double()
+    _check("ds_get_cost", lib().ds_get_cost(h, ctypes.byref(F)))
+    return F.value
+
+
+def ds_get_blend_table(h, pix_P=None, nid_P4=None, alpha_P4=None) -> int:
+    P = ctypes.c_int32()
+    rc = lib().ds_get_blend_table(h, ctypes.byref(P), _ptr(pix_P, np.int32),
+                                  _ptr(nid_P4, np.int32), _ptr(alpha_P4, np.float32))
+    _check("ds_get_blend_table", rc)
+    return P.value
+
+
+def ds_get_frame_points(h, pts4=None, nrm4=None):
+    _check("ds_get_frame_points",
+           lib().ds_get_frame_points(h, _ptr(pts4, np.float32), _ptr(nrm4, np.float32)))
+
+
+def ds_linearize(h, w_arap_in=0.0, A_nn=None, b_n=None, cost3=None):
+    wo = ctypes.c_double()
+    rc = lib().ds_linearize(h, float(w_arap_in), _ptr(A_nn, np.float64), _ptr(b_n, np.float64),
+                            _ptr(cost3, np.float64), ctypes.byref(wo))
+    _check("ds_linearize", rc)
+    return wo.value
+
+
+def ds_set_tracing(h, on=True):
+    _check("ds_set_tracing", lib().ds_set_tracing(h, 1 if on else 0))
+
+
+def ds_get_phase_times(h):
+    ms = np.zeros(4, np.float64)
+    _check("ds_get_phase_times", lib().ds_get_phase_times(h, ms.ctypes.data))
+    return ms
+
+
+def ds_get_counters(h) -> int:
+    k = ctypes.c_int64()
+    _check("ds_get_counters", lib().ds_get_counters(h, ctypes.byref(k)))
+    return k.value
+
+
+def ds_destroy(h):
+    _check("ds_destroy", lib().ds_destroy(h))
+
+
+def ds_version() -> str:
+    return lib().ds_version().decode()
+
+
+# ----------------------------------------------------------------------------- convenience
+
+
+class Solver:
+    """One deformation stream: template + control points + per-frame solves (host arrays)."""
+
+    def __init__(self, template_depth, K, nodes, params: DsParams | None = None, stream=None):
+        H, W = template_depth.shape
+        self.W, self.H = W, H
+        self.h = ds_create_template(np.ascontiguousarray(template_depth, np.float32), W, H, K,
+                                    params, stream)
+        self.nodes = np.ascontiguousarray(nodes, np.int32)
+        self.N = len(self.nodes)
+        ds_set_control_points(self.h, self.nodes)
+        self.params = params
+
+    def submit(self, depth, match_idx, match_xyz, hyp):
+        self.M = len(match_idx)
+        ds_submit_frame(self.h, np.ascontiguousarray(depth, np.float32),
+                        np.ascontiguousarray(match_idx, np.int32),
+                        np.ascontiguousarray(match_xyz, np.float32).reshape(-1, 3),
+                        self.M, np.ascontiguousarray(hyp, np.int32))
+
+    def solve(self, iters=10, stats=True):
+        return ds_solve(self.h, iters, stats)
+
+    def deformation(self):
+        q = np.zeros((self.N, 4), np.float32)
+        t = np.zeros((self.N, 3), np.float32)
+        p = np.zeros((self.N, 3), np.float32)
+        ds_get_deformation(self.h, q, t, p)
+        return q, t, p
+
+    def deformation64(self):
+        q = np.zeros((self.N, 4), np.float64)
+        t = np.zeros((self.N, 3), np.float64)
+        ds_get_deformation64(self.h, q, t)
+        return q, t
+
+    def mask(self):
+        bits = np.zeros((self.M + 31) // 32, np.uint32)
+        ds_get_inlier_mask(self.h, bits)
+        k = np.arange(self.M)
+        return ((bits[k // 32] >> (k % 32).astype(np.uint32)) & 1).astype(bool)
+
+    def close(self):
+        if self.h is not None:
+            ds_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,300 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded
+inputs, element by element, at sizes the oracle finishes in seconds (several tiles, ragged
+tails) and at the full 320x240 / 256-node size the benchmark times."""
+import numpy as np
+import pytest
+
+from gpu_common import (BAND_MM, COST_RTOL, MID, POS_TOL_MM, gpu_frame, lib, oracle_params,
+                        ransac_listed, scene, unpack_bits)
+from oracle import frame as oframe
+from oracle import solver
+from synth import CONFIGS
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def d():
+    return lib()
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return scene(CONFIGS["frame_80x60_n32"], 1000)
+
+
+@pytest.fixture(scope="module")
+def mid():
+    return scene(MID, 4242)
+
+
+def _oracle(sc, fr, prm, iters=10, q0=None, t0=None):
+    tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes, prm)
+    res = solver.solve_frame(tpl, fr.depth, fr.match_idx, fr.match_xyz, fr.hyp, prm, iters,
+                             q0=q0, t0=t0)
+    return tpl, res
+
+
+# ----------------------------------------------------------------------------- set-up tables
+
+
+@pytest.mark.parametrize("which", ["tiny", "mid"])
+def test_blend_table_bit_exact(d, which, tiny, mid):
+    sc = tiny if which == "tiny" else mid
+    p = d.default_params()
+    s = d.Solver(sc.template_depth, sc.K, sc.nodes, p)
+    tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes, oracle_params(p))
+    P = d.ds_get_blend_table(s.h)
+    pix = np.zeros(P, np.int32)
+    nid = np.zeros((P, 4), np.int32)
+    al = np.zeros((P, 4), np.float32)
+    d.ds_get_blend_table(s.h, pix, nid, al)
+    assert np.array_equal(pix, tpl.pidx)
+    assert np.array_equal(nid, tpl.nid)          # index work: bit-exact
+    assert np.abs(al - tpl.alpha).max() < 1e-6   # FP32 rounding of FP64 weights
+    s.close()
+
+
+def test_frame_points_and_normals(d, mid):
+    sc = mid
+    fr = sc.frames[0]
+    p = d.default_params()
+    s = d.Solver(sc.template_depth, sc.K, sc.nodes, p)
+    s.submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+    pts = np.zeros((sc.H * sc.W, 4), np.float32)
+    nrm = np.zeros((sc.H * sc.W, 4), np.float32)
+    d.ds_get_frame_points(s.h, pts, nrm)
+    X, valid = oframe.backproject(fr.depth, sc.K)
+    n, ok = oframe.target_normals(X, valid)
+    assert np.array_equal(pts[:, 3] > 0, ok.reshape(-1))
+    okf = ok.reshape(-1)
+    assert np.abs(pts[okf, :3] - X.reshape(-1, 3)[okf]).max() < 1e-4      # mm
+    assert np.abs(nrm[okf, :3] - n.reshape(-1, 3)[okf]).max() < 1e-4
+    s.close()
+
+
+# ----------------------------------------------------------------------------- RANSAC
+
+
+@pytest.mark.parametrize("which", ["tiny", "mid", "full"])
+def test_ransac_mask_bit_exact(d, which, tiny, mid):
+    if which == "full":
+        sc = scene(CONFIGS["seq_320x240_n256"], 1000)
+    else:
+        sc = tiny if which == "tiny" else mid
+    fr = sc.frames[0]
+    p = d.default_params()
+    s = d.Solver(sc.template_depth, sc.K, sc.nodes, p)
+    s.submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+    M = len(fr.match_idx)
+    bits = np.zeros((M + 31) // 32, np.uint32)
+    d.ds_get_inlier_mask(s.h, bits)
+    w = np.zeros(M, np.float32)
+    kept = np.zeros(2, np.uint32)
+    score = np.zeros(p.n_hyp, np.float64)
+    d.ds_get_ransac(s.h, w, kept, score)
+    gmask = unpack_bits(bits, M)
+    gkept = unpack_bits(kept, p.n_hyp)
+    from oracle import ransac
+    X0, _ = oframe.backproject(sc.template_depth, sc.K)
+    rs = ransac.ransac_1p(X0.reshape(-1, 3)[fr.match_idx], fr.match_xyz, fr.hyp, p.H_mm,
+                          p.n_reweight, p.keep_frac)
+    listed, amb = ransac_listed(rs, p.H_mm)
+    assert np.array_equal(gkept[~amb], rs["kept"][~amb])
+    assert np.array_equal(gmask[~listed], rs["mask"][~listed]), np.flatnonzero(gmask != rs["mask"])
+    assert np.abs(score - rs["score"]).max() <= 1e-9 * np.abs(rs["score"]).max()
+    assert np.abs(w[~listed] - rs["what"][~listed]).max() < 1e-6
+    assert listed.sum() <= max(1, M // 100)
+    s.close()
+
+
+# ----------------------------------------------------------------------------- linearisation
+
+
+@pytest.mark.parametrize("which", ["tiny", "mid"])
+def test_normal_equations_match_oracle(d, which, tiny, mid):
+    sc = tiny if which == "tiny" else mid
+    fr = sc.frames[0]
+    p = d.default_params()
+    prm = oracle_params(p)
+    s = d.Solver(sc.template_depth, sc.K, sc.nodes, p)
+    s.submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+    n = 6 * len(sc.nodes)
+    A = np.zeros((n, n))
+    b = np.zeros(n)
+    c3 = np.zeros(3)
+    w_arap = d.ds_linearize(s.h, 0.0, A, b, c3)
+    tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes, prm)
+    tgt = solver.prepare_target(fr.depth, tpl.K)
+    from oracle import ransac
+    rs = ransac.ransac_1p(tpl.X0[fr.match_idx], fr.match_xyz, fr.hyp, prm.H, prm.n_reweight,
+                          prm.keep_frac)
+    orb = (fr.match_idx, fr.match_xyz.astype(np.float64), rs["mask"], rs["what"])
+    N = len(sc.nodes)
+    q = np.tile([1.0, 0, 0, 0], (N, 1))
+    t = np.zeros((N, 3))
+    lin, wo = solver.linearize(tpl, tgt, q, t, orb, None, prm)
+    assert abs(w_arap - wo) <= 1e-5 * wo
+    scale = np.abs(lin.A).max()
+    assert np.abs(A - lin.A).max() <= 2e-5 * scale, np.abs(A - lin.A).max() / scale
+    assert np.abs(b - lin.b).max() <= 2e-5 * np.abs(lin.b).max()
+    ref = np.array([lin.cost_icp, lin.cost_orb, lin.cost_arap])
+    # relative to the total: the ARAP cost is exactly 0 at the identity, FP32 leaves ~1e-9
+    assert np.all(np.abs(c3 - ref) <= COST_RTOL * ref.sum())
+    s.close()
+
+
+# ----------------------------------------------------------------------------- whole solves
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_solve_matches_oracle_tiny(d, tiny, prec):
+    sc = tiny
+    fr = sc.frames[0]
+    p = d.default_params(precision=prec)
+    prm = oracle_params(p)
+    s, st, q, t = gpu_frame(d, sc, fr, p)
+    tpl, res = _oracle(sc, fr, prm)
+    pos = tpl.g + t
+    err = np.abs(pos - res.pos).max()
+    assert err <= POS_TOL_MM, err
+    cost = np.array(st.cost[:10])
+    rel = np.abs(cost - np.array(res.costs)) / np.array(res.costs)
+    assert rel.max() <= COST_RTOL, rel
+    assert abs(st.w_arap - res.w_arap) <= 1e-6 * res.w_arap
+    s.close()
+
+
+def test_solve_matches_oracle_mid_ragged(d, mid):
+    sc = mid
+    fr = sc.frames[0]
+    p = d.default_params()
+    s, st, q, t = gpu_frame(d, sc, fr, p)
+    tpl, res = _oracle(sc, fr, oracle_params(p))
+    err = np.abs(tpl.g + t - res.pos).max()
+    assert err <= POS_TOL_MM, err
+    rel = np.abs(np.array(st.cost[:10]) - np.array(res.costs)) / np.array(res.costs)
+    assert rel.max() <= COST_RTOL, rel
+    s.close()
+
+
+def test_solve_matches_oracle_full_size_frame(d):
+    """The benchmark's workload size: 320x240 template, 256 nodes, 2000 matches."""
+    sc = scene(CONFIGS["seq_320x240_n256"], 1000)
+    fr = sc.frames[0]
+    p = d.default_params()
+    s, st, q, t = gpu_frame(d, sc, fr, p)
+    tpl, res = _oracle(sc, fr, oracle_params(p))
+    err = np.abs(tpl.g + t - res.pos).max()
+    assert err <= POS_TOL_MM, err
+    rel = np.abs(np.array(st.cost[:10]) - np.array(res.costs)) / np.array(res.costs)
+    assert rel.max() <= COST_RTOL, rel
+    s.close()
+
+
+def test_warm_started_sequence(d):
+    """Three consecutive frames, each warm-started from the previous result on both sides."""
+    from synth.scene import Config
+    cfg = Config("seq_120x90_n40", 120, 90, 40, 300, 8, 0.4, 0.5, 0.1, 8.0, 1.0, 0.3, 0.5, 3)
+    sc = scene(cfg, 77, n_frames=3)
+    p = d.default_params()
+    prm = oracle_params(p)
+    s = d.Solver(sc.template_depth, sc.K, sc.nodes, p)
+    tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes, prm)
+    q0 = t0 = None
+    for fr in sc.frames:
+        s.submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+        s.solve(10, stats=False)
+        res = solver.solve_frame(tpl, fr.depth, fr.match_idx, fr.match_xyz, fr.hyp, prm, 10,
+                                 q0=q0, t0=t0)
+        q0, t0 = res.q, res.t
+        _, t = s.deformation64()
+        assert np.abs(tpl.g + t - res.pos).max() <= POS_TOL_MM
+    s.close()
+
+
+def test_no_matches_frame(d, tiny):
+    sc = tiny
+    fr = sc.frames[0]
+    p = d.default_params()
+    prm = oracle_params(p)
+    s = d.Solver(sc.template_depth, sc.K, sc.nodes, p)
+    d.ds_submit_frame(s.h, fr.depth, None, None, 0, None)
+    st = d.ds_solve(s.h, 10, True)
+    _, t = s.deformation64()
+    tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes, prm)
+    res = solver.solve_frame(tpl, fr.depth, np.zeros(0, np.int32), np.zeros((0, 3)), [], prm, 10)
+    assert np.abs(tpl.g + t - res.pos).max() <= POS_TOL_MM
+    assert st.n_inliers == 0
+    s.close()
+
+
+def test_batch_equals_individual(d, tiny, mid):
+    p = d.default_params()
+    solvers = []
+    for sc in (tiny, mid, tiny):
+        s = d.Solver(sc.template_depth, sc.K, sc.nodes, p)
+        fr = sc.frames[0]
+        s.submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+        solvers.append(s)
+    d.ds_solve_batch([s.h for s in solvers], 10)
+    outs = [s.deformation64()[1] for s in solvers]
+    for s, sc, o in zip(solvers, (tiny, mid, tiny), outs):
+        s2, st, q, t = gpu_frame(d, sc, sc.frames[0], p)
+        assert np.abs(o - t).max() <= 1e-4
+        s2.close()
+        s.close()
+
+
+# ----------------------------------------------------------------------------- errors
+
+
+def test_error_codes(d, tiny):
+    sc = tiny
+    fr = sc.frames[0]
+    p = d.default_params()
+    s = d.Solver(sc.template_depth, sc.K, sc.nodes, p)
+    with pytest.raises(d.DsError) as e:
+        d.ds_solve(s.h, 10)
+    assert e.value.status == d.DS_ERR_STATE
+    bad = sc.nodes.copy()
+    bad[1] = bad[0]
+    with pytest.raises(d.DsError) as e:
+        d.ds_set_control_points(s.h, bad)
+    assert e.value.status == d.DS_ERR_ARG
+    with pytest.raises(d.DsError) as e:
+        d.ds_submit_frame(s.h, fr.depth, np.full(len(fr.match_idx), 10 ** 7, np.int32),
+                          fr.match_xyz, len(fr.match_idx), fr.hyp)
+    assert e.value.status == d.DS_ERR_ARG
+    dep = fr.depth.copy()
+    dep[3, 3] = np.nan
+    d.ds_submit_frame(s.h, dep, fr.match_idx, fr.match_xyz, len(fr.match_idx), fr.hyp)
+    with pytest.raises(d.DsError) as e:
+        d.ds_solve(s.h, 10, True)
+    assert e.value.status == d.DS_ERR_BAD_INPUT
+    tdep = sc.template_depth.copy()
+    tdep[0, 0] = np.inf
+    with pytest.raises(d.DsError) as e:
+        d.ds_create_template(tdep, sc.W, sc.H, sc.K)
+    assert e.value.status == d.DS_ERR_BAD_INPUT
+    s.close()
+
+
+def test_resume_from_saved_state(d, tiny):
+    """get_deformation / set_deformation round trip resumes the same trajectory."""
+    sc = tiny
+    fr = sc.frames[0]
+    p = d.default_params()
+    s, st, q, t = gpu_frame(d, sc, fr, p, iters=4)
+    qf, tf, _ = s.deformation()
+    s.submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+    s.solve(3, stats=False)
+    _, ta = s.deformation64()
+    s2 = d.Solver(sc.template_depth, sc.K, sc.nodes, p)
+    d.ds_set_deformation(s2.h, qf, tf)
+    s2.submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+    s2.solve(3, stats=False)
+    _, tb = s2.deformation64()
+    assert np.abs(ta - tb).max() <= 1e-4
+    s.close()
+    s2.close()
