@@ -95,6 +95,17 @@ struct ds_ctx {
   void* d_v1 = nullptr;
   void* d_v2 = nullptr;
   void* d_v3 = nullptr;
+  // persistent factorisation / solve
+  LinProblem* d_lp = nullptr;
+  int* d_lcnt = nullptr;      // factorisation task counters
+  int* d_lflags = nullptr;    // solve row flags
+  int4* d_tasks = nullptr;
+  int ntasks = 0;
+  int2* d_tickets = nullptr;
+  int ntickets = 0;
+  int* d_lhead = nullptr;     // [0] factorisation ticket head, [1] solve ticket head
+  int* d_lerr = nullptr;      // bounded-wait timeout word
+  int nt = 0;
   double* d_acc = nullptr;
   double* d_hist = nullptr;   // DS_MAX_ITERS x 6
   int* d_flag = nullptr;
@@ -157,7 +168,8 @@ void free_cp(ds_ctx* h) {
   dfree(h->d_segbp); dfree(h->d_rowptr); dfree(h->d_rowcol); dfree(h->d_rowbp);
   dfree(h->d_A32); dfree(h->d_A64); dfree(h->d_Af32); dfree(h->d_Dinv); dfree(h->d_blk);
   dfree(h->d_gdata); dfree(h->d_b); dfree(h->d_x); dfree(h->d_r); dfree(h->d_v1);
-  dfree(h->d_v2); dfree(h->d_v3);
+  dfree(h->d_v2); dfree(h->d_v3); dfree(h->d_lp); dfree(h->d_lcnt); dfree(h->d_lflags);
+  dfree(h->d_tasks); dfree(h->d_tickets); dfree(h->d_lhead); dfree(h->d_lerr);
   h->N = h->n = 0;
   h->have_frame = false;
 }
@@ -186,6 +198,14 @@ int sync_status(ds_ctx* h) {
     }
     if (flag & 2) return DS_ERR_ARG;
     if (flag & 1) return DS_ERR_BAD_INPUT;
+  }
+  if (h->d_lerr) {
+    int te = 0;
+    if (cudaMemcpy(&te, h->d_lerr, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      h->error = true;
+      return DS_ERR_CUDA;
+    }
+    if (te) return DS_ERR_TIMEOUT;
   }
   if (h->N > 0) {
     double st = 0;
@@ -247,6 +267,25 @@ __global__ void k_sanitize(int* __restrict__ midx, int M, int first_valid) {
 
 // Events recorded while the stream is captured become event-record nodes of the graph only with
 // cudaEventRecordExternal (a plain record is a capture-internal dependency marker).
+// Tile tasks of one problem's factorisation in a topological order with one step of look-ahead:
+// CRIT(k) (last update of (k,k), POTRF(k), TRSM(k+1,k)), TRSM(i>k+1, k), the rest of step k-1's
+// trailing update, then step k's update of column k+1 (which the next critical task needs).
+// Encoding: {problem, type | k << 4, i, j}.
+void make_chol_tasks(int p, int nt, std::vector<int4>& out) {
+  auto C = [&](int k) { out.push_back(make_int4(p, 0 | (k << 4), k, k)); };
+  auto T = [&](int i, int k) { out.push_back(make_int4(p, 1 | (k << 4), i, k)); };
+  auto G = [&](int i, int j, int k) { out.push_back(make_int4(p, 2 | (k << 4), i, j)); };
+  for (int k = 0; k < nt; ++k) {
+    C(k);
+    for (int i = k + 2; i < nt; ++i) T(i, k);
+    if (k >= 1)
+      for (int j = k + 1; j < nt; ++j)
+        for (int i = j; i < nt; ++i) G(i, j, k - 1);
+    if (k + 1 < nt)
+      for (int i = k + 2; i < nt; ++i) G(i, k + 1, k);
+  }
+}
+
 void trace_ev(ds_ctx* h, cudaEvent_t e) {
   if (h->tracing) cudaEventRecordWithFlags(e, h->stream, cudaEventRecordExternal);
 }
@@ -284,22 +323,31 @@ void enqueue_linearize(ds_ctx* h, bool first, double lam, bool factor_buffers) {
 }
 
 template <typename T>
-void enqueue_factor_solve(ds_ctx* h, T* Afac, int steps) {
+void enqueue_trsv(ds_ctx* h) {
+  cudaStream_t s = h->stream;
+  cudaMemsetAsync(h->d_lflags, 0, sizeof(int) * 2 * h->nt, s);
+  cudaMemsetAsync(h->d_lhead + 1, 0, sizeof(int), s);
+  launch_trsv_dag<T>(h->d_lp, h->d_tickets, h->ntickets, h->d_lhead + 1, h->d_lerr, s);
+}
+
+template <typename T>
+void enqueue_factor_solve(ds_ctx* h, int steps) {
   cudaStream_t s = h->stream;
   int n = h->n;
   T* v1 = (T*)h->d_v1;
   T* v2 = (T*)h->d_v2;
-  T* v3 = (T*)h->d_v3;
-  T* Dinv = (T*)h->d_Dinv;
-  launch_cholesky<T>(Afac, n, Dinv, h->d_acc, s);
+  const size_t ncnt = (size_t)h->nt + 2 * (size_t)h->nt * h->nt;
+  cudaMemsetAsync(h->d_lcnt, 0, sizeof(int) * ncnt, s);
+  cudaMemsetAsync(h->d_lhead, 0, sizeof(int), s);
+  launch_chol_dag<T>(h->d_lp, h->d_tasks, h->ntasks, h->d_lhead, h->d_lerr, s);
   trace(h, h->cur_it, 2);
   launch_cast_from64<T>(h->d_b, v1, n, s);
-  launch_trsv<T>(Afac, Dinv, n, v1, v2, v3, s);
+  enqueue_trsv<T>(h);
   launch_axpy_to64<T>(v2, h->d_x, n, true, s);
   for (int k = 0; k < steps; ++k) {
     launch_residual64(h->d_A32, n, h->d_b, h->d_x, h->d_r, s);
     launch_cast_from64<T>(h->d_r, v1, n, s);
-    launch_trsv<T>(Afac, Dinv, n, v1, v2, v3, s);
+    enqueue_trsv<T>(h);
     launch_axpy_to64<T>(v2, h->d_x, n, false, s);
   }
 }
@@ -316,11 +364,11 @@ void enqueue_solve(ds_ctx* h, int iters) {
     enqueue_linearize(h, it == 0, p.lambda, true);
     trace(h, it, 1);
     if (p.precision == DS_PREC_FP64)
-      enqueue_factor_solve<double>(h, h->d_A64, p.refine_steps);
+      enqueue_factor_solve<double>(h, p.refine_steps);
     else if (p.precision == DS_PREC_FP32_REFINE)
-      enqueue_factor_solve<float>(h, h->d_Af32, p.refine_steps);
+      enqueue_factor_solve<float>(h, p.refine_steps);
     else
-      enqueue_factor_solve<float>(h, h->d_A32, 0);
+      enqueue_factor_solve<float>(h, 0);
     trace(h, it, 4);
     k_record_clear<<<1, 32, 0, s>>>(h->d_acc, h->d_hist, it);
     launch_node_update(h->d_x, h->N, h->d_q64, h->d_t64, h->d_g64, h->d_gc, h->d_node, h->d_pn,
@@ -598,7 +646,9 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
   const int n = h->n;
   const int prec = h->prm.precision;
   const size_t nn = (size_t)n * n;
-  const int nblk = (n + 31) / 32;
+  const int TB = prec == DS_PREC_FP64 ? chol_tile<double>() : chol_tile<float>();
+  const int nt = (n + TB - 1) / TB;
+  h->nt = nt;
   const size_t tsz = prec == DS_PREC_FP64 ? sizeof(double) : sizeof(float);
   if ((rc = dalloc(&h->d_q64, 4 * N)) || (rc = dalloc(&h->d_t64, 3 * N)) ||
       (rc = dalloc(&h->d_node, N)) || (rc = dalloc(&h->d_pn, N)) || (rc = dalloc(&h->d_tp, P)) ||
@@ -610,7 +660,10 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
       (rc = dalloc(&h->d_b, n)) || (rc = dalloc(&h->d_x, n)) || (rc = dalloc(&h->d_r, n)) ||
       (rc = dalloc((char**)&h->d_v1, tsz * n)) || (rc = dalloc((char**)&h->d_v2, tsz * n)) ||
       (rc = dalloc((char**)&h->d_v3, tsz * n)) ||
-      (rc = dalloc((char**)&h->d_Dinv, tsz * (size_t)nblk * 32 * 32))) {
+      (rc = dalloc((char**)&h->d_Dinv, tsz * (size_t)nt * TB * TB)) ||
+      (rc = dalloc(&h->d_lp, 1)) || (rc = dalloc(&h->d_lcnt, (size_t)nt + 2 * (size_t)nt * nt)) ||
+      (rc = dalloc(&h->d_lflags, 2 * (size_t)nt)) || (rc = dalloc(&h->d_lhead, 2)) ||
+      (rc = dalloc(&h->d_lerr, 1))) {
     free_cp(h);
     return rc;
   }
@@ -621,6 +674,34 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
   if (prec == DS_PREC_FP32_REFINE && (rc = dalloc(&h->d_Af32, nn))) {
     free_cp(h);
     return rc;
+  }
+  {
+    std::vector<int4> tasks;
+    make_chol_tasks(0, nt, tasks);
+    std::vector<int2> tickets;
+    for (int t = 0; t < 2 * nt; ++t) tickets.push_back(make_int2(0, t));
+    h->ntasks = (int)tasks.size();
+    h->ntickets = (int)tickets.size();
+    if ((rc = dalloc(&h->d_tasks, tasks.size())) || (rc = dalloc(&h->d_tickets, tickets.size()))) {
+      free_cp(h);
+      return rc;
+    }
+    cudaMemcpy(h->d_tasks, tasks.data(), sizeof(int4) * tasks.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(h->d_tickets, tickets.data(), sizeof(int2) * tickets.size(), cudaMemcpyHostToDevice);
+    LinProblem lp;
+    lp.A = prec == DS_PREC_FP64 ? (void*)h->d_A64
+                                : (prec == DS_PREC_FP32_REFINE ? (void*)h->d_Af32 : (void*)h->d_A32);
+    lp.Dinv = h->d_Dinv;
+    lp.n = n;
+    lp.nt = nt;
+    lp.cnt = h->d_lcnt;
+    lp.flags = h->d_lflags;
+    lp.status = h->d_acc + ACC_STATUS;
+    lp.rhs = h->d_v1;
+    lp.y = h->d_v3;
+    lp.x = h->d_v2;
+    cudaMemcpy(h->d_lp, &lp, sizeof(lp), cudaMemcpyHostToDevice);
+    cudaMemset(h->d_lerr, 0, sizeof(int));
   }
   std::vector<double> q0(4 * N, 0.0), t0(3 * N, 0.0);
   for (int i = 0; i < N; ++i) q0[4 * i] = 1.0;

@@ -1,26 +1,66 @@
 // Cholesky factorisation and triangular solves of the damped normal equations (Section 2:
-// "we perform Cholesky decomposition to update W_i"), for T = double (FP64 factor) or
-// T = float (FP32 factor), plus the FP64 residual of the refinement steps.
+// "we perform Cholesky decomposition to update W_i"), for T = double (FP64 factor, TB = 32) or
+// T = float (FP32 factor, TB = 64), plus the FP64 residual of the refinement steps.
 //
-// Layout: A is n x n row-major; only the lower triangle (row >= col) is read or written. The
-// factorisation is right-looking and blocked with NB = 32 columns per panel:
-//   panel kernel  : every CTA factors the NB x NB diagonal block in shared memory and inverts
-//                   it; CTA 0 stores L_kk and L_kk^-1 (Dinv), the others solve
-//                   L_ik = A_ik L_kk^-T for their RB rows of the panel as a product with L_kk^-T;
-//   update kernel : A_ij -= L_ik L_jk^T on 64 x 64 tiles of the trailing lower triangle.
-// A pivot <= 0 (or NaN) is recorded in acc[ACC_STATUS] as 1 + its row and replaced by 1 so that
-// the remaining launches stay finite; the host reports DS_ERR_NOT_SPD.
-// Triangular solves use the stored inverses of the diagonal blocks: forward y_k = Dinv_k r_k,
-// then r_i -= L_ik y_k below; backward x_k = Dinv_k^T r_k, then r_j -= L_kj^T x_k to the left.
+// Layout: A is n x n row-major; only the lower triangle is read or written. The matrix is cut
+// into TB x TB tiles (the last row/column of tiles is ragged).
+//
+// Factorisation: one persistent launch runs the tile tasks of a right-looking blocked Cholesky
+//   CRIT(k)       the critical chain of step k in one task: A_kk -= L_k,k-1 L_k,k-1^T,
+//                 L_kk = chol(A_kk) with its inverse L_kk^-1 (kept for the solves), and
+//                 L_k+1,k = A_k+1,k L_kk^-T
+//   TRSM(i,k)     L_ik = A_ik L_kk^-T (as a product with the stored inverse), i > k + 1
+//   GEMM(i,j,k)   A_ij -= L_ik L_jk^T          (k < j <= i, except the last update of (k+1,k+1))
+// in a fixed topological order (with one step of look-ahead: the column that feeds the next
+// critical task is issued before the rest of the trailing update). CTAs claim tasks in that order from
+// an atomic ticket counter; a task waits on per-tile counters written by earlier tickets. Every
+// ticket a CTA waits on was claimed earlier by a running CTA, so the waits always end; they are
+// bounded anyway (globaltimer deadline) and a timeout sets an error word, after which all CTAs
+// drain the queue without computing. Tiles written inside the launch are read through L2
+// (ld.global.cg) because L1 is not coherent across SMs.
+//
+// Triangular solves: one launch, one ticket per tile row and direction (forward tickets first,
+// then backward in reverse row order): y_i = L_ii^-1 (b_i - sum_{j<i} L_ij y_j), then
+// x_i = L_ii^-T (y_i - sum_{j>i} L_ji^T x_j), each term consumed as soon as its producer
+// publishes it.
+//
+// A pivot <= 0 (or NaN) is recorded in the problem's status word as 1 + its row and replaced by
+// 1 so that the rest stays finite; the host reports DS_ERR_NOT_SPD.
 #include <math.h>
 
 #include "ds_internal.cuh"
 
 namespace ds {
 
-constexpr int NB = 32;    // panel width
-constexpr int RB = 64;    // panel rows per CTA in the panel kernel
-constexpr int TS = 64;    // trailing-update tile
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait until *p >= v. Returns false (and raises *err) on timeout or if *err is set.
+__device__ __forceinline__ bool wait_ge(const int* p, int v, int* err,
+                                        unsigned long long budget_ns) {
+  const volatile int* vp = p;
+  const volatile int* ve = err;
+  if (*vp >= v) return true;
+  unsigned long long t0 = globaltimer();
+  int it = 0;
+  while (*vp < v) {
+    if (*ve) return false;
+    if ((++it & 31) == 0 && globaltimer() - t0 > budget_ns) {
+      atomicExch(err, 1);
+      return false;
+    }
+    __nanosleep(64);
+  }
+  return true;
+}
+
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) {
+  return __ldcg(p);
+}
 
 template <typename T>
 __device__ __forceinline__ T tsqrt(T x);
@@ -33,224 +73,632 @@ __device__ __forceinline__ float tsqrt<float>(float x) {
   return sqrtf(x);
 }
 
-// Factor the nb x nb lower block in shared memory (L[i][j], stride NB+1) and write its inverse
-// into Li (same layout). 256 threads.
+template <typename T, int TB>
+struct TileCfg {
+  static constexpr int RT = TB / 16;               // register block per thread (16 x 16 threads)
+  static constexpr int LDT = TB + 16 / sizeof(T);  // transposed shared tile row stride (16 B pad)
+};
+
 template <typename T>
-__device__ void factor_invert_diag(T (*L)[NB + 1], T (*Li)[NB + 1], int nb, int k0,
-                                   double* acc) {
-  const int tid = threadIdx.x;
-  for (int j = 0; j < nb; ++j) {
-    if (tid == 0) {
-      T d = L[j][j];
-      if (!(d > (T)0)) {
-        if (acc) atomicCAS((unsigned long long*)&acc[ACC_STATUS], 0ull,
-                           __double_as_longlong((double)(k0 + j + 1)));
-        d = (T)1;
-      }
-      L[j][j] = tsqrt(d);
+struct Vec2 {};
+template <>
+struct Vec2<float> {
+  using type = float2;
+};
+template <>
+struct Vec2<double> {
+  using type = double2;
+};
+
+// Loads tile (ti, tj) of A transposed into shared memory: S[m * LDT + r] = A[ti*TB + r][tj*TB + m]
+// (zero outside the matrix). Two-element vector loads along rows (n is even, so rows stay
+// 8-byte aligned for float and 16-byte aligned for double).
+template <typename T, int TB>
+__device__ __forceinline__ void load_tile_t(const T* A, int n, int ti, int tj, T* S) {
+  using V2 = typename Vec2<T>::type;
+  constexpr int LDT = TileCfg<T, TB>::LDT;
+  const int r0 = ti * TB, c0 = tj * TB;
+  for (int e = threadIdx.x; e < TB * TB / 2; e += blockDim.x) {
+    const int r = e / (TB / 2), m = 2 * (e % (TB / 2));
+    V2 v;
+    if (r0 + r < n && c0 + m + 1 < n) {
+      v = __ldcg(reinterpret_cast<const V2*>(A + (size_t)(r0 + r) * n + c0 + m));
+    } else {
+      v.x = (r0 + r < n && c0 + m < n) ? ldcg(A + (size_t)(r0 + r) * n + c0 + m) : (T)0;
+      v.y = (T)0;
     }
-    __syncthreads();
-    T piv = L[j][j];
-    for (int i = j + 1 + tid; i < nb; i += blockDim.x) L[i][j] /= piv;
-    __syncthreads();
-    // trailing update of the block: rows i > j, cols j < c <= i
-    int m = nb - j - 1;
-    for (int e = tid; e < m * m; e += blockDim.x) {
-      int i = j + 1 + e / m, c = j + 1 + e % m;
-      if (c <= i) L[i][c] -= L[i][j] * L[c][j];
-    }
-    __syncthreads();
+    S[m * LDT + r] = v.x;
+    S[(m + 1) * LDT + r] = v.y;
   }
-  // inverse of the lower-triangular L: column c by forward substitution, one row at a time
-  for (int i = 0; i < nb; ++i) {
-    for (int c = tid; c <= i; c += blockDim.x) {
-      T v;
-      if (c == i) {
-        v = (T)1 / L[i][i];
-      } else {
+}
+
+// acc[a][b] = sum_m P^T[m][tr + a] Q^T[m][tc + b] over m < TB (transposed shared operands).
+template <typename T, int TB>
+__device__ __forceinline__ void tile_abt_t(const T* Pt, const T* Qt,
+                                           T (&acc)[TileCfg<T, TB>::RT][TileCfg<T, TB>::RT]) {
+  constexpr int RT = TileCfg<T, TB>::RT, LDT = TileCfg<T, TB>::LDT;
+  const int tr = (threadIdx.x / 16) * RT, tc = (threadIdx.x % 16) * RT;
+#pragma unroll
+  for (int a = 0; a < RT; ++a)
+#pragma unroll
+    for (int b = 0; b < RT; ++b) acc[a][b] = (T)0;
+#pragma unroll 4
+  for (int m = 0; m < TB; ++m) {
+    T x[RT], y[RT];
+    if constexpr (RT == 4) {
+      float4 xv = *reinterpret_cast<const float4*>(Pt + m * LDT + tr);
+      float4 yv = *reinterpret_cast<const float4*>(Qt + m * LDT + tc);
+      x[0] = xv.x; x[1] = xv.y; x[2] = xv.z; x[3] = xv.w;
+      y[0] = yv.x; y[1] = yv.y; y[2] = yv.z; y[3] = yv.w;
+    } else {
+      double2 xv = *reinterpret_cast<const double2*>(Pt + m * LDT + tr);
+      double2 yv = *reinterpret_cast<const double2*>(Qt + m * LDT + tc);
+      x[0] = xv.x; x[1] = xv.y;
+      y[0] = yv.x; y[1] = yv.y;
+    }
+#pragma unroll
+    for (int a = 0; a < RT; ++a)
+#pragma unroll
+      for (int b = 0; b < RT; ++b) acc[a][b] += x[a] * y[b];
+  }
+}
+
+// Stores (or subtracts from) this thread's RT x RT block of tile (ti, tj); lower_only keeps
+// r >= c (diagonal tiles).
+template <typename T, int TB, bool SUB>
+__device__ __forceinline__ void store_block(T* A, int n, int ti, int tj,
+                                            const T (&v)[TileCfg<T, TB>::RT][TileCfg<T, TB>::RT],
+                                            bool lower_only) {
+  constexpr int RT = TileCfg<T, TB>::RT;
+  const int tr = (threadIdx.x / 16) * RT, tc = (threadIdx.x % 16) * RT;
+#pragma unroll
+  for (int a = 0; a < RT; ++a) {
+    const int r = ti * TB + tr + a;
+    if (r >= n) continue;
+#pragma unroll
+    for (int b = 0; b < RT; ++b) {
+      const int c = tj * TB + tc + b;
+      if (c < n && (!lower_only || c <= r)) {
+        T* p = A + (size_t)r * n + c;
+        __stcg(p, SUB ? ldcg(p) - v[a][b] : v[a][b]);
+      }
+    }
+  }
+}
+
+// 1/sqrt(p) to working precision: hardware estimate refined by Newton steps
+// y <- y (3 - p y^2) / 2 (one step in FP32, two in FP64 from the FP32 estimate).
+template <typename T>
+__device__ __forceinline__ T rsqrt_newton(T p);
+template <>
+__device__ __forceinline__ float rsqrt_newton<float>(float p) {
+  float y = rsqrtf(p);
+  return y * (1.5f - 0.5f * p * y * y);
+}
+template <>
+__device__ __forceinline__ double rsqrt_newton<double>(double p) {
+  double y = (double)rsqrtf((float)p);
+  y = y * (1.5 - 0.5 * p * y * y);
+  return y * (1.5 - 0.5 * p * y * y);
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl(T v, int src) {
+  return __shfl_sync(0xffffffffu, v, src);
+}
+
+// Cholesky of a diagonal tile in shared memory (L[r * LDS + c], lower, identity padding past the
+// matrix) together with its inverse X (lower part written in full). The tile is processed in
+// blocks of PB = 8 columns:
+//   (1) warp 0 factors the 8 x 8 diagonal block and inverts it with shuffles (lane i owns row
+//       i; no block-wide barrier inside);
+//   (2) the rows below take L_rb = A_rb D^T (D = the block's inverse), one thread per row;
+//   (3) the block's rows of X left of the block: X_bc = -D sum_q L_bq X_qc;
+//   (4) the trailing lower triangle gets the rank-8 update with the new panel.
+// Three barriers per 8 columns; 256 threads (8 warps).
+template <typename T, int TB>
+__device__ void potrf_blocked(T* L, T* X, T* tmp, int row0, double* status) {
+  constexpr int LDS = TB + 1, PB = 8, NBK = TB / PB;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int kb = 0; kb < NBK; ++kb) {
+    const int c0 = kb * PB;
+    if (warp == 0) {
+      const int i = lane & (PB - 1);
+      T a[PB], xr[PB];
+#pragma unroll
+      for (int c = 0; c < PB; ++c) {
+        a[c] = (c <= i) ? L[(c0 + i) * LDS + c0 + c] : (T)0;
+        xr[c] = (c == i) ? (T)1 : (T)0;
+      }
+#pragma unroll
+      for (int j = 0; j < PB; ++j) {
+        T p = shfl(a[j], j);
+        if (!(p > (T)0)) {
+          if (status && lane == 0)
+            atomicCAS((unsigned long long*)status, 0ull,
+                      __double_as_longlong((double)(row0 + c0 + j + 1)));
+          p = (T)1;
+        }
+        const T inv = rsqrt_newton<T>(p), d = p * inv;
+        const T lij = (i > j) ? a[j] * inv : ((i == j) ? d : (T)0);
+        a[j] = lij;
+        T xj[PB];
+#pragma unroll
+        for (int c = 0; c < PB; ++c) xj[c] = (c <= j) ? shfl(xr[c], j) * inv : (T)0;
+        if (i == j) {
+#pragma unroll
+          for (int c = 0; c < PB; ++c)
+            if (c <= j) xr[c] = xj[c];
+        }
+#pragma unroll
+        for (int c = j + 1; c < PB; ++c) {
+          const T lcj = shfl(a[j], c);
+          if (i > j && c <= i) a[c] -= lij * lcj;
+        }
+        if (i > j) {
+#pragma unroll
+          for (int c = 0; c < PB; ++c)
+            if (c <= j) xr[c] -= lij * xj[c];
+        }
+      }
+      if (lane < PB) {
+#pragma unroll
+        for (int c = 0; c < PB; ++c)
+          if (c <= i) {
+            L[(c0 + i) * LDS + c0 + c] = a[c];
+            X[(c0 + i) * LDS + c0 + c] = xr[c];
+          }
+      }
+    }
+    __syncthreads();
+    // (2) rows below the block
+    for (int r = c0 + PB + tid; r < TB; r += blockDim.x) {
+      T row[PB];
+#pragma unroll
+      for (int m = 0; m < PB; ++m) row[m] = L[r * LDS + c0 + m];
+#pragma unroll
+      for (int c = 0; c < PB; ++c) {
         T s = (T)0;
-        for (int k = c; k < i; ++k) s += L[i][k] * Li[k][c];
-        v = -s / L[i][i];
+#pragma unroll
+        for (int m = 0; m <= c; ++m) s += row[m] * X[(c0 + c) * LDS + c0 + m];
+        L[r * LDS + c0 + c] = s;
       }
-      Li[i][c] = v;
+    }
+    // (3a) tmp[m][c] = sum_{q = c}^{c0 - 1} L[c0 + m][q] X[q][c]   (warp m, lanes over c)
+    for (int c = lane; c < c0; c += 32) {
+      T s = (T)0;
+      for (int q = c; q < c0; ++q) s += L[(c0 + warp) * LDS + q] * X[q * LDS + c];
+      tmp[warp * TB + c] = s;
+    }
+    __syncthreads();
+    // (4) rank-8 update of the trailing lower triangle
+    for (int r = c0 + PB + warp; r < TB; r += 8)
+      for (int c = c0 + PB + lane; c <= r; c += 32) {
+        T s = (T)0;
+#pragma unroll
+        for (int q = 0; q < PB; ++q) s += L[r * LDS + c0 + q] * L[c * LDS + c0 + q];
+        L[r * LDS + c] -= s;
+      }
+    // (3b) X[c0 + i][c] = -sum_m D[i][m] tmp[m][c]   (warp i, lanes over c)
+    for (int c = lane; c < c0; c += 32) {
+      T s = (T)0;
+#pragma unroll
+      for (int m = 0; m < PB; ++m)
+        if (m <= warp) s += X[(c0 + warp) * LDS + c0 + m] * tmp[m * TB + c];
+      X[(c0 + warp) * LDS + c] = -s;
     }
     __syncthreads();
   }
 }
 
-template <typename T>
-__global__ __launch_bounds__(256) void k_chol_panel(T* __restrict__ A, int n, int k0,
-                                                    T* __restrict__ Dinv, double* acc) {
-  __shared__ T L[NB][NB + 1];
-  __shared__ T Li[NB][NB + 1];
-  const int nb = min(NB, n - k0);
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    int i = e / NB, j = e % NB;
-    L[i][j] = (i < nb && j <= i) ? A[(size_t)(k0 + i) * n + k0 + j] : (T)0;
-    Li[i][j] = (T)0;
-  }
-  __syncthreads();
-  factor_invert_diag<T>(L, Li, nb, k0, blockIdx.x == 0 ? acc : nullptr);
-  if (blockIdx.x == 0) {
-    T* D = Dinv + (size_t)(k0 / NB) * NB * NB;
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-      int i = e / NB, j = e % NB;
-      if (i < nb && j <= i) A[(size_t)(k0 + i) * n + k0 + j] = L[i][j];
-      D[e] = (i < nb && j <= i) ? Li[i][j] : (T)0;
+// Loads this thread's RT x RT block of tile (k, k) (lower part; identity padding past n).
+template <typename T, int TB>
+__device__ __forceinline__ void load_diag_block(const T* A, int n, int k,
+                                                T (&a)[TileCfg<T, TB>::RT][TileCfg<T, TB>::RT]) {
+  constexpr int RT = TileCfg<T, TB>::RT;
+  const int tr = (threadIdx.x / 16) * RT, tc = (threadIdx.x % 16) * RT;
+  const int r0 = k * TB;
+#pragma unroll
+  for (int p = 0; p < RT; ++p)
+#pragma unroll
+    for (int q = 0; q < RT; ++q) {
+      const int r = tr + p, cc = tc + q;
+      if (r0 + r < n && r0 + cc < n)
+        a[p][q] = cc <= r ? ldcg(A + (size_t)(r0 + r) * n + r0 + cc) : (T)0;
+      else
+        a[p][q] = (r == cc) ? (T)1 : (T)0;
     }
-    return;
+}
+
+// The critical task of step k: the last update of tile (k,k) (from column k-1), its Cholesky
+// and inverse, and the solve of tile (k+1, k) that the next critical task needs. Shared layout:
+// Pt/Qt (transposed operand tiles, LDT) and the factor / inverse tiles Ls / Xs (LDS = TB + 1).
+template <typename T, int TB>
+__device__ void task_crit(T* A, T* Dinv, int n, int nt, int k, double* status, T* Pt, T* Qt,
+                          T* Ls, T* Xs, T* tmp, int* pdone, const int* upd_next, int* err,
+                          unsigned long long budget_ns, int* s_ok) {
+  constexpr int RT = TileCfg<T, TB>::RT, LDT = TileCfg<T, TB>::LDT, LDS = TB + 1;
+  const int tr = (threadIdx.x / 16) * RT, tc = (threadIdx.x % 16) * RT;
+  const int r0 = k * TB;
+  T acc[RT][RT];
+  if (k >= 1) {
+    load_tile_t<T, TB>(A, n, k, k - 1, Pt);
+    __syncthreads();
+    tile_abt_t<T, TB>(Pt, Pt, acc);
   }
-  // rows of this CTA: X = B L^-T, X[r][j] = sum_{m <= j} B[r][m] Li[j][m]
-  __shared__ T Bs[RB][NB + 1];
-  const int r0 = k0 + nb + (blockIdx.x - 1) * RB;
-  const int rows = min(RB, n - r0);
-  for (int e = threadIdx.x; e < RB * NB; e += blockDim.x) {
-    int r = e / NB, j = e % NB;
-    Bs[r][j] = (r < rows && j < nb) ? A[(size_t)(r0 + r) * n + k0 + j] : (T)0;
+#pragma unroll
+  for (int p = 0; p < RT; ++p)
+#pragma unroll
+    for (int q = 0; q < RT; ++q) {
+      const int r = tr + p, cc = tc + q;
+      T v;
+      if (r0 + r < n && r0 + cc < n)
+        v = cc <= r ? ldcg(A + (size_t)(r0 + r) * n + r0 + cc) - (k >= 1 ? acc[p][q] : (T)0) : (T)0;
+      else
+        v = (r == cc) ? (T)1 : (T)0;
+      Ls[r * LDS + cc] = v;
+      Xs[r * LDS + cc] = (r == cc) ? (T)1 : (T)0;
+    }
+  __syncthreads();
+  potrf_blocked<T, TB>(Ls, Xs, tmp, r0, status);
+  // write L_kk (lower), L_kk^-1, and keep the inverse transposed for the solve: Qt[m][c] = X[c][m]
+  T* D = Dinv + (size_t)k * TB * TB;
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+    const int r = e / TB, cc = e % TB;
+    const T xv = cc <= r ? Xs[r * LDS + cc] : (T)0;
+    __stcg(D + e, xv);
+    Qt[cc * LDT + r] = xv;
+    if (cc <= r && r0 + r < n) __stcg(A + (size_t)(r0 + r) * n + r0 + cc, Ls[r * LDS + cc]);
+  }
+  // publish L_kk and its inverse now: the other TRSM tasks of column k can start while this
+  // task waits for tile (k+1, k) and solves it
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicExch(pdone, 1);
+    if (k + 1 < nt) *s_ok = wait_ge(upd_next, k, err, budget_ns);
+    __threadfence();
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < rows * nb; e += blockDim.x) {
-    int r = e / nb, j = e % nb;
-    T s = (T)0;
-    for (int m = 0; m <= j; ++m) s += Bs[r][m] * Li[j][m];
-    A[(size_t)(r0 + r) * n + k0 + j] = s;
+  if (k + 1 < nt && *s_ok) {
+    load_tile_t<T, TB>(A, n, k + 1, k, Pt);
+    __syncthreads();
+    tile_abt_t<T, TB>(Pt, Qt, acc);
+    store_block<T, TB, false>(A, n, k + 1, k, acc, false);
   }
 }
 
-// A[i][j] -= sum_m L[i][k0+m] L[j][k0+m], m < nb, for the lower tiles of the trailing matrix.
-template <typename T>
-__global__ __launch_bounds__(256) void k_chol_update(T* __restrict__ A, int n, int k0, int nb,
-                                                     int nt) {
-  // blockIdx.x -> lower tile (I, J), I >= J, of the nt x nt trailing tile grid
-  int t = blockIdx.x;
-  int I = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-  while ((I + 1) * (I + 2) / 2 <= t) ++I;
-  while (I * (I + 1) / 2 > t) --I;
-  int J = t - I * (I + 1) / 2;
-  const int s0 = k0 + nb;
-  const int i0 = s0 + I * TS, j0 = s0 + J * TS;
-  __shared__ T Ls[TS][NB + 1];
-  __shared__ T Ms[TS][NB + 1];
-  for (int e = threadIdx.x; e < TS * NB; e += blockDim.x) {
-    int r = e / NB, m = e % NB;
-    Ls[r][m] = (i0 + r < n && m < nb) ? A[(size_t)(i0 + r) * n + k0 + m] : (T)0;
-    Ms[r][m] = (j0 + r < n && m < nb) ? A[(size_t)(j0 + r) * n + k0 + m] : (T)0;
+// TRSM: L_ik = A_ik (L_kk^-1)^T.
+template <typename T, int TB>
+__device__ void task_trsm(T* A, const T* Dinv, int n, int i, int k, T* Pt, T* Qt) {
+  constexpr int RT = TileCfg<T, TB>::RT, LDT = TileCfg<T, TB>::LDT;
+  load_tile_t<T, TB>(A, n, i, k, Pt);
+  const T* D = Dinv + (size_t)k * TB * TB;
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+    const int cc = e / TB, m = e % TB;
+    Qt[m * LDT + cc] = ldcg(D + e);
   }
   __syncthreads();
-  // 256 threads, 4 x 4 outputs each
-  const int tr = (threadIdx.x / 16) * 4, tc = (threadIdx.x % 16) * 4;
-  T c[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int bb = 0; bb < 4; ++bb) c[a][bb] = (T)0;
-  for (int m = 0; m < NB; ++m) {
-    T x[4], y[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) x[a] = Ls[tr + a][m];
-#pragma unroll
-    for (int bb = 0; bb < 4; ++bb) y[bb] = Ms[tc + bb][m];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int bb = 0; bb < 4; ++bb) c[a][bb] += x[a] * y[bb];
-  }
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    int i = i0 + tr + a;
-    if (i >= n) continue;
-#pragma unroll
-    for (int bb = 0; bb < 4; ++bb) {
-      int j = j0 + tc + bb;
-      if (j < n && j <= i) A[(size_t)i * n + j] -= c[a][bb];
-    }
-  }
+  T acc[RT][RT];
+  tile_abt_t<T, TB>(Pt, Qt, acc);
+  store_block<T, TB, false>(A, n, i, k, acc, false);
 }
 
-template <typename T>
-void launch_cholesky(T* A, int n, T* Dinv, double* acc, cudaStream_t s) {
-  for (int k0 = 0; k0 < n; k0 += NB) {
-    int nb = min(NB, n - k0);
-    int below = n - k0 - nb;
-    int grid = 1 + (below + RB - 1) / RB;
-    k_chol_panel<T><<<grid, 256, 0, s>>>(A, n, k0, Dinv, acc);
-    ++g_launches;
-    if (below > 0) {
-      int nt = (below + TS - 1) / TS;
-      k_chol_update<T><<<nt * (nt + 1) / 2, 256, 0, s>>>(A, n, k0, nb, nt);
-      ++g_launches;
+// GEMM: A_ij -= L_ik L_jk^T.
+template <typename T, int TB>
+__device__ void task_gemm(T* A, int n, int i, int j, int k, T* Pt, T* Qt) {
+  constexpr int RT = TileCfg<T, TB>::RT;
+  load_tile_t<T, TB>(A, n, i, k, Pt);
+  if (j != i) load_tile_t<T, TB>(A, n, j, k, Qt);
+  __syncthreads();
+  T acc[RT][RT];
+  tile_abt_t<T, TB>(Pt, j != i ? Qt : Pt, acc);
+  store_block<T, TB, true>(A, n, i, j, acc, i == j);
+}
+
+// counters of a problem: [0, nt) POTRF done, [nt, nt + nt^2) TRSM done (i*nt + k),
+// [nt + nt^2, nt + 2 nt^2) updates applied to tile (i, j). Task types: 0 critical task
+// (last update of (k,k), POTRF(k), TRSM(k+1,k)), 1 TRSM(i,k), 2 GEMM(i,j,k).
+template <typename T, int TB>
+__global__ __launch_bounds__(256) void k_chol_dag(const LinProblem* __restrict__ probs,
+                                                  const int4* __restrict__ tasks, int ntasks,
+                                                  int* __restrict__ head, int* __restrict__ err,
+                                                  unsigned long long budget_ns) {
+  constexpr int LDT = TileCfg<T, TB>::LDT;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* Pt = reinterpret_cast<T*>(smraw);
+  T* Qt = Pt + TB * LDT;
+  T* Ls = Qt + TB * LDT;
+  T* Xs = Ls + TB * (TB + 1);
+  T* tmp = Xs + TB * (TB + 1);
+  __shared__ int s_t, s_ok;
+  for (;;) {
+    if (threadIdx.x == 0) s_t = atomicAdd(head, 1);
+    __syncthreads();
+    const int t = s_t;
+    if (t >= ntasks) return;
+    const int4 tk = tasks[t];
+#if defined(DS_TASK_TRACE)
+    if (threadIdx.x == 0) ds_trace_mark(t, 0);
+#endif
+    const LinProblem P = probs[tk.x];
+    const int type = tk.y & 15, k = tk.y >> 4, i = tk.z, j = tk.w;
+    const int nt = P.nt;
+    int* pdone = P.cnt;
+    int* tdone = P.cnt + nt;
+    int* upd = P.cnt + nt + nt * nt;
+    T* A = (T*)P.A;
+    T* Dinv = (T*)P.Dinv;
+    if (threadIdx.x == 0) {
+      bool ok = true;
+      if (type == 0) {
+        if (k >= 1)
+          ok = wait_ge(&upd[k * nt + k], k - 1, err, budget_ns) &&
+               wait_ge(&tdone[k * nt + k - 1], 1, err, budget_ns);
+      } else if (type == 1) {
+        ok = wait_ge(&pdone[k], 1, err, budget_ns) && wait_ge(&upd[i * nt + k], k, err, budget_ns);
+      } else {
+        ok = wait_ge(&tdone[i * nt + k], 1, err, budget_ns) &&
+             wait_ge(&tdone[j * nt + k], 1, err, budget_ns) &&
+             wait_ge(&upd[i * nt + j], k, err, budget_ns);
+      }
+      __threadfence();
+      s_ok = ok;
+    }
+    __syncthreads();
+#if defined(DS_TASK_TRACE)
+    if (threadIdx.x == 0) ds_trace_mark(t, 1);
+#endif
+    if (s_ok) {
+      if (type == 0)
+        task_crit<T, TB>(A, Dinv, P.n, nt, k, P.status, Pt, Qt, Ls, Xs, tmp, &pdone[k],
+                         k + 1 < nt ? &upd[(k + 1) * nt + k] : nullptr, err, budget_ns, &s_ok);
+      else if (type == 1)
+        task_trsm<T, TB>(A, Dinv, P.n, i, k, Pt, Qt);
+      else
+        task_gemm<T, TB>(A, P.n, i, j, k, Pt, Qt);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+#if defined(DS_TASK_TRACE)
+      ds_trace_mark(t, 2);
+#endif
+      if (type == 0) {
+        atomicExch(&pdone[k], 1);  // already published mid-task unless the task was skipped
+        if (k + 1 < nt) atomicExch(&tdone[(k + 1) * nt + k], 1);
+      } else if (type == 1) {
+        atomicExch(&tdone[i * nt + k], 1);
+      } else {
+        atomicExch(&upd[i * nt + j], k + 1);
+      }
     }
   }
 }
 
 // ----------------------------------------------------------------------------- solves
 
-// forward step k: y_k = Dinv_k r_k (every CTA computes it; CTA 0 stores it), then rows below
-// the block: r_i -= L[i, k-block] y_k. One warp per row.
-template <typename T>
-__global__ __launch_bounds__(256) void k_trsv_fwd(const T* __restrict__ L,
-                                                  const T* __restrict__ Dinv, int n, int kb,
-                                                  T* __restrict__ r, T* __restrict__ y) {
-  __shared__ T ys[NB];
-  const int k0 = kb * NB, nb = min(NB, n - k0);
-  const T* D = Dinv + (size_t)kb * NB * NB;
-  if (threadIdx.x < nb) {
-    T s = (T)0;
-    for (int m = 0; m <= (int)threadIdx.x; ++m) s += D[threadIdx.x * NB + m] * r[k0 + m];
-    ys[threadIdx.x] = s;
-  }
-  __syncthreads();
-  if (blockIdx.x == 0 && threadIdx.x < nb) y[k0 + threadIdx.x] = ys[threadIdx.x];
+// Register-prefetched tile GEMVs of the triangular solves (256 threads).
+// Row form (forward): thread (warp w, lane l) holds M[r][c] for r = w + 8 s, c = l + 32 t.
+// Column form (backward): thread (r = tid % TB, slice sl = tid / TB) holds M[c][r] for
+// c = sl + SL q, SL = 256 / TB. Both hold TB * TB / 256 values per thread.
+template <typename T, int TB>
+struct SolveTile {
+  static constexpr int NV = TB * TB / 256;
+  static constexpr int RS = TB / 8;    // rows per warp (row form)
+  static constexpr int CS = TB / 32;   // columns per lane (row form)
+  static constexpr int SL = 256 / TB;  // slices (column form)
+};
+
+template <typename T, int TB>
+__device__ __forceinline__ void prefetch_rows(const T* M, size_t ld, int nr, int nc,
+                                              T (&v)[SolveTile<T, TB>::NV]) {
+  constexpr int RS = SolveTile<T, TB>::RS, CS = SolveTile<T, TB>::CS;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = k0 + nb + blockIdx.x * 8 + warp;
-  if (row < n) {
-    T s = lane < nb ? L[(size_t)row * n + k0 + lane] * ys[lane] : (T)0;
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) r[row] -= s;
+#pragma unroll
+  for (int s = 0; s < RS; ++s)
+#pragma unroll
+    for (int t = 0; t < CS; ++t) {
+      const int r = warp + 8 * s, c = lane + 32 * t;
+      v[s * CS + t] = (r < nr && c < nc) ? ldcg(M + (size_t)r * ld + c) : (T)0;
+    }
+}
+
+template <typename T, int TB>
+__device__ __forceinline__ void prefetch_cols(const T* M, size_t ld, int nr, int nc,
+                                              T (&v)[SolveTile<T, TB>::NV]) {
+  constexpr int SL = SolveTile<T, TB>::SL, NV = SolveTile<T, TB>::NV;
+  const int r = threadIdx.x % TB, sl = threadIdx.x / TB;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    const int c = sl + SL * q;
+    v[q] = (r < nr && c < nc) ? ldcg(M + (size_t)c * ld + r) : (T)0;
   }
 }
 
-// backward step k: x_k = Dinv_k^T r_k, then r_j -= sum_{i in block k} L[i][j] x_i for j < k0.
-template <typename T>
-__global__ __launch_bounds__(256) void k_trsv_bwd(const T* __restrict__ L,
-                                                  const T* __restrict__ Dinv, int n, int kb,
-                                                  T* __restrict__ r, T* __restrict__ x) {
-  __shared__ T xs[NB];
-  const int k0 = kb * NB, nb = min(NB, n - k0);
-  const T* D = Dinv + (size_t)kb * NB * NB;
-  if (threadIdx.x < nb) {
-    T s = (T)0;
-    for (int m = threadIdx.x; m < nb; ++m) s += D[m * NB + threadIdx.x] * r[k0 + m];
-    xs[threadIdx.x] = s;
+// acc[r] (-)= sum_c M[r][c] vin[c] from prefetched row-form values.
+template <typename T, int TB>
+__device__ __forceinline__ void gemv_rows_pf(const T (&v)[SolveTile<T, TB>::NV], const T* vin,
+                                             T* acc, bool sub) {
+  constexpr int RS = SolveTile<T, TB>::RS, CS = SolveTile<T, TB>::CS;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 0; s < RS; ++s) {
+    T sum = (T)0;
+#pragma unroll
+    for (int t = 0; t < CS; ++t) sum += v[s * CS + t] * vin[lane + 32 * t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) acc[warp + 8 * s] = sub ? acc[warp + 8 * s] - sum : sum;
   }
+}
+
+// acc[r] (-)= sum_c M[c][r] vin[c] from prefetched column-form values (reduction through part).
+template <typename T, int TB>
+__device__ __forceinline__ void gemv_cols_pf(const T (&v)[SolveTile<T, TB>::NV], const T* vin,
+                                             T* acc, bool sub, T (*part)[17]) {
+  constexpr int SL = SolveTile<T, TB>::SL, NV = SolveTile<T, TB>::NV;
+  const int r = threadIdx.x % TB, sl = threadIdx.x / TB;
+  T sum = (T)0;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) sum += v[q] * vin[sl + SL * q];
+  part[r][sl] = sum;
   __syncthreads();
-  if (blockIdx.x == 0 && threadIdx.x < nb) x[k0 + threadIdx.x] = xs[threadIdx.x];
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < k0) {
-    T s = (T)0;
-    for (int i = 0; i < nb; ++i) s += L[(size_t)(k0 + i) * n + j] * xs[i];
-    r[j] -= s;
+  if (threadIdx.x < TB) {
+    T a = (T)0;
+#pragma unroll
+    for (int q = 0; q < SL; ++q) a += part[threadIdx.x][q];
+    acc[threadIdx.x] = sub ? acc[threadIdx.x] - a : a;
+  }
+}
+
+// Tickets per problem: [0, nt) forward rows 0..nt-1, [nt, 2nt) backward rows nt-1..0.
+// flags: [0, nt) forward row done, [nt, 2nt) backward row done. Every tile a ticket needs is
+// loaded into registers before the wait on its producer (the tiles do not depend on it), so a
+// dependency costs one flag hand-off and one 64-value vector load.
+template <typename T, int TB>
+__global__ __launch_bounds__(256) void k_trsv_dag(const LinProblem* __restrict__ probs,
+                                                  const int2* __restrict__ tickets, int ntk,
+                                                  int* __restrict__ head, int* __restrict__ err,
+                                                  unsigned long long budget_ns) {
+  constexpr int NV = SolveTile<T, TB>::NV;
+  __shared__ T acc[TB];
+  __shared__ T vin[TB];
+  __shared__ T part[TB][17];
+  __shared__ int s_t, s_ok;
+  for (;;) {
+    if (threadIdx.x == 0) s_t = atomicAdd(head, 1);
+    __syncthreads();
+    const int t = s_t;
+    if (t >= ntk) return;
+    const int2 tk = tickets[t];
+    const LinProblem P = probs[tk.x];
+    const int nt = P.nt, n = P.n;
+    const bool fwd = tk.y < nt;
+    const int i = fwd ? tk.y : 2 * nt - 1 - tk.y;
+    const int r0 = i * TB;
+    const int nr = min(TB, n - r0);
+    const T* L = (const T*)P.A;
+    const T* D = (const T*)P.Dinv + (size_t)i * TB * TB;
+    int* flag = P.flags;
+    T* y = (T*)P.y;
+    T* x = (T*)P.x;
+    const T* rhs = (const T*)P.rhs;
+    const T* src = fwd ? y : x;
+    T dv[NV];  // the diagonal block's inverse, prefetched
+    if (fwd)
+      prefetch_rows<T, TB>(D, TB, TB, TB, dv);
+    else
+      prefetch_cols<T, TB>(D, TB, TB, TB, dv);
+    bool ok = true;
+    if (threadIdx.x == 0) {
+      ok = fwd ? true : wait_ge(&flag[i], 1, err, budget_ns);
+      __threadfence();
+      s_ok = ok;
+    }
+    __syncthreads();
+    ok = s_ok;
+    if (threadIdx.x < TB)
+      acc[threadIdx.x] = (threadIdx.x < nr && ok) ? ldcg((fwd ? rhs : y) + r0 + threadIdx.x) : (T)0;
+    const int cnt = fwd ? i : nt - 1 - i;
+    T lv[NV];
+    if (cnt > 0) {
+      const int jt = fwd ? 0 : nt - 1;
+      const int c0 = jt * TB, nc = min(TB, n - c0);
+      if (fwd)
+        prefetch_rows<T, TB>(L + (size_t)r0 * n + c0, n, nr, nc, lv);
+      else
+        prefetch_cols<T, TB>(L + (size_t)c0 * n + r0, n, nr, nc, lv);
+    }
+    for (int q = 0; q < cnt && ok; ++q) {
+      const int jt = fwd ? q : nt - 1 - q;
+      if (threadIdx.x == 0) {
+        s_ok = wait_ge(&flag[fwd ? jt : nt + jt], 1, err, budget_ns);
+        __threadfence();
+      }
+      __syncthreads();
+      ok = s_ok;
+      if (!ok) break;
+      const int c0 = jt * TB;
+      const int nc = min(TB, n - c0);
+      if (threadIdx.x < TB) vin[threadIdx.x] = threadIdx.x < nc ? ldcg(src + c0 + threadIdx.x) : (T)0;
+      __syncthreads();
+      T cur[NV];
+#pragma unroll
+      for (int e = 0; e < NV; ++e) cur[e] = lv[e];
+      if (q + 1 < cnt) {  // next tile while this one is used
+        const int jn = fwd ? q + 1 : nt - 2 - q;
+        const int cn = jn * TB, ncn = min(TB, n - cn);
+        if (fwd)
+          prefetch_rows<T, TB>(L + (size_t)r0 * n + cn, n, nr, ncn, lv);
+        else
+          prefetch_cols<T, TB>(L + (size_t)cn * n + r0, n, nr, ncn, lv);
+      }
+      if (fwd)
+        gemv_rows_pf<T, TB>(cur, vin, acc, true);
+      else
+        gemv_cols_pf<T, TB>(cur, vin, acc, true, part);
+      __syncthreads();
+    }
+    if (ok) {
+      if (threadIdx.x < TB) vin[threadIdx.x] = acc[threadIdx.x];
+      __syncthreads();
+      if (fwd)
+        gemv_rows_pf<T, TB>(dv, vin, acc, false);
+      else
+        gemv_cols_pf<T, TB>(dv, vin, acc, false, part);
+      __syncthreads();
+      if (threadIdx.x < nr) __stcg((fwd ? y : x) + r0 + threadIdx.x, acc[threadIdx.x]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicExch(&flag[fwd ? i : nt + i], 1);
+    }
   }
 }
 
 template <typename T>
-void launch_trsv(const T* L, const T* Dinv, int n, const T* rhs, T* x, T* tmp, cudaStream_t s) {
-  // tmp holds the running right-hand side; x receives y then the solution
-  cudaMemcpyAsync(tmp, rhs, sizeof(T) * n, cudaMemcpyDeviceToDevice, s);
-  int nblk = (n + NB - 1) / NB;
-  for (int kb = 0; kb < nblk; ++kb) {
-    int below = n - (kb * NB + min(NB, n - kb * NB));
-    int grid = max(1, (below + 7) / 8);
-    k_trsv_fwd<T><<<grid, 256, 0, s>>>(L, Dinv, n, kb, tmp, x);
-    ++g_launches;
+int chol_tile() {
+  return sizeof(T) == 8 ? 32 : 64;
+}
+template int chol_tile<float>();
+template int chol_tile<double>();
+
+static int g_sms = 0;
+static int num_sms() {
+  if (!g_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sms <= 0) g_sms = 1;
   }
-  cudaMemcpyAsync(tmp, x, sizeof(T) * n, cudaMemcpyDeviceToDevice, s);
-  for (int kb = nblk - 1; kb >= 0; --kb) {
-    int left = kb * NB;
-    int grid = max(1, (left + 255) / 256);
-    k_trsv_bwd<T><<<grid, 256, 0, s>>>(L, Dinv, n, kb, tmp, x);
-    ++g_launches;
+  return g_sms;
+}
+
+template <typename T>
+void launch_chol_dag(const LinProblem* probs, const int4* tasks, int ntasks, int* head, int* err,
+                     cudaStream_t s) {
+  constexpr int TB = sizeof(T) == 8 ? 32 : 64;
+  const size_t sm = 2 * sizeof(T) * TB * TileCfg<T, TB>::LDT + 2 * sizeof(T) * TB * (TB + 1) +
+                    8 * sizeof(T) * TB;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_chol_dag<T, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = true;
   }
+  int grid = std::min(ntasks, 2 * num_sms());
+  k_chol_dag<T, TB><<<grid, 256, sm, s>>>(probs, tasks, ntasks, head, err, 2000000000ull);
+  ++g_launches;
+}
+
+template <typename T>
+void launch_trsv_dag(const LinProblem* probs, const int2* tickets, int ntk, int* head, int* err,
+                     cudaStream_t s) {
+  constexpr int TB = sizeof(T) == 8 ? 32 : 64;
+  int grid = std::min(ntk, 2 * num_sms());
+  k_trsv_dag<T, TB><<<grid, 256, 0, s>>>(probs, tickets, ntk, head, err, 2000000000ull);
+  ++g_launches;
 }
 
 // r = b - A x with A the full symmetric FP32 matrix, accumulated in FP64. One warp per row.
@@ -308,12 +756,14 @@ void launch_sym_unpack(const float* A, int n, double* out, cudaStream_t s) {
   ++g_launches;
 }
 
-template void launch_cholesky<float>(float*, int, float*, double*, cudaStream_t);
-template void launch_cholesky<double>(double*, int, double*, double*, cudaStream_t);
-template void launch_trsv<float>(const float*, const float*, int, const float*, float*, float*,
-                                 cudaStream_t);
-template void launch_trsv<double>(const double*, const double*, int, const double*, double*,
-                                  double*, cudaStream_t);
+template void launch_chol_dag<float>(const LinProblem*, const int4*, int, int*, int*,
+                                     cudaStream_t);
+template void launch_chol_dag<double>(const LinProblem*, const int4*, int, int*, int*,
+                                      cudaStream_t);
+template void launch_trsv_dag<float>(const LinProblem*, const int2*, int, int*, int*,
+                                     cudaStream_t);
+template void launch_trsv_dag<double>(const LinProblem*, const int2*, int, int*, int*,
+                                      cudaStream_t);
 template void launch_cast_from64<float>(const double*, float*, int, cudaStream_t);
 template void launch_cast_from64<double>(const double*, double*, int, cudaStream_t);
 template void launch_axpy_to64<float>(const float*, double*, int, bool, cudaStream_t);

@@ -48,6 +48,23 @@ __host__ __device__ constexpr int kSlotPairJ(int k) {
   return k < 1 ? k : k < 3 ? k - 1 : k < 6 ? k - 3 : k - 6;
 }
 
+// One dense SPD system for the persistent factorisation / solve kernels (one per problem of a
+// batch). A: n x n lower, factored in place; Dinv: inverses of the nt diagonal tiles (TB x TB);
+// cnt: task counters of the factorisation (nt + 2 nt^2 ints); flags: 2 nt ints of the solve;
+// status: FP64 word receiving 1 + row of a non-positive pivot; rhs / y / x: vectors of the
+// solve (T).
+struct LinProblem {
+  void* A;
+  void* Dinv;
+  int n, nt;
+  int* cnt;
+  int* flags;
+  double* status;
+  void* rhs;
+  void* y;
+  void* x;
+};
+
 constexpr int kTile = 256;        // points per CTA of the ICP pass
 constexpr int kOuts = 10 * 36 + 24;  // per-segment outputs: 10 blocks of 6x6, 24 gradient entries
 
@@ -93,9 +110,13 @@ void launch_arap_assemble(const PairNode* pn, int N, float inv2sig2, const int* 
 
 // chol.cu
 template <typename T>
-void launch_cholesky(T* A, int n, T* Dinv, double* acc, cudaStream_t s);
+int chol_tile();
 template <typename T>
-void launch_trsv(const T* L, const T* Dinv, int n, const T* rhs, T* x, T* tmp, cudaStream_t s);
+void launch_chol_dag(const LinProblem* probs, const int4* tasks, int ntasks, int* head, int* err,
+                     cudaStream_t s);
+template <typename T>
+void launch_trsv_dag(const LinProblem* probs, const int2* tickets, int ntk, int* head, int* err,
+                     cudaStream_t s);
 void launch_residual64(const float* Aref, int n, const double* b, const double* x, double* r,
                        cudaStream_t s);
 template <typename T>
