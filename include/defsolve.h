@@ -140,8 +140,25 @@ int ds_submit_frame(ds_handle h, const float* depth_hw, const int32_t* match_tmp
  * Errors: DS_ERR_ARG, DS_ERR_STATE (no frame), DS_ERR_NOT_SPD, DS_ERR_CUDA. */
 int ds_solve(ds_handle h, int32_t iters, ds_solve_stats* out);
 
-/* Solves n handles, each with its own submitted frame, `iters` iterations each; the work of
- * all handles is issued before any of them is waited on. Equivalent to ds_solve on each. */
+/* Batched solves of uneven problems. A batch groups n handles (same precision and refinement
+ * steps, control points set) and runs the Gauss-Newton iterations of all of them together:
+ * every kernel launch of an iteration covers the work lists of all problems (ICP tiles, ORB
+ * matches, ARAP rows, factorisation tile tasks, solve tiles), and the iterations are captured
+ * once as a CUDA graph per iteration count. Handles keep their own stream for submit_frame and
+ * ds_get_*; the batch orders its work after the handles' pending work and the handles' later
+ * work after the batch. A handle may belong to several batches; a batch must not run while one
+ * of its handles is being solved elsewhere. cuda_stream: stream of the batch or NULL (owned).
+ * Errors: DS_ERR_ARG (empty, mixed precision, a handle without control points), DS_ERR_OOM. */
+typedef struct ds_batch_s* ds_batch;
+int ds_batch_create(const ds_handle* hs, int32_t n, void* cuda_stream, ds_batch* out);
+/* Runs `iters` iterations (1..DS_MAX_ITERS) on every handle of the batch; each handle must have
+ * a submitted frame. Asynchronous; results are read per handle (ds_get_*), and
+ * ds_batch_status synchronises the batch and reports DS_ERR_TIMEOUT / DS_ERR_NOT_SPD. */
+int ds_batch_solve(ds_batch b, int32_t iters);
+int ds_batch_status(ds_batch b);
+int ds_batch_destroy(ds_batch b);
+
+/* Convenience: a temporary batch over n handles, solved and synchronised. */
 int ds_solve_batch(ds_handle* hs, int32_t n, int32_t iters);
 
 /* Copies the current warps out: q_N4 (w, x, y, z per node), t_N3, and the control-point
@@ -184,7 +201,7 @@ int ds_linearize(ds_handle h, double w_arap_in, double* A_nn, double* b_n, doubl
  * ms4[0] linearisation (ICP, ORB, dense ARAP and assembly), ms4[1] Cholesky factorisation,
  * ms4[2] triangular solves and refinement, ms4[3] state update.
  * ds_get_counters returns the number of kernels the handle has launched so far (graph kernel
- * nodes count once per replay). */
+ * nodes count once per replay); with h == NULL, the number the whole library has launched. */
 int ds_set_tracing(ds_handle h, int32_t on);
 int ds_get_phase_times(ds_handle h, double* ms4);
 int ds_get_counters(ds_handle h, int64_t* kernels_launched);

@@ -1,20 +1,24 @@
 // C ABI of libdefsolve (declared in include/defsolve.h): handle life cycle, template and
-// control-point set-up, frame submission and the damped Gauss-Newton loop.
+// control-point set-up, frame submission, batched damped Gauss-Newton solves.
 //
 // Set-up (once per template / control-point set):
 //   * the template depth is back-projected in FP64; control points g_i are template points;
 //   * the blend table (4 nearest control points, Gaussian weights) is computed on the device;
 //   * the host sorts the valid template points by their node quadruple, so that points sharing
-//     the same 4 nodes are contiguous ("segments"), and enumerates the node pairs that share a
-//     point (the block-sparse pattern of the ICP and ORB contributions to A).
-// Per frame: copy-in, live points and normals, RANSAC preselection.
-// Per Gauss-Newton iteration: ICP + ORB accumulation, dense ARAP + assembly + damping,
-// Cholesky, triangular solves (+ FP64 refinement), state update. The whole loop of a solve is
-// captured once as a CUDA graph per iteration count and replayed.
+//     the same 4 nodes are contiguous ("segments"), enumerates the node pairs that share a point
+//     (the block-sparse pattern of the ICP and ORB contributions to A) and lists the tile tasks
+//     of the factorisation;
+//   * a device descriptor (ProbDesc) gathers every pointer and size the kernels need.
+// Per frame: copy-in, device-side index validation, live points and normals, RANSAC.
+// Per Gauss-Newton iteration (for every problem of a batch at once): counters reset, ICP, ORB,
+// dense ARAP + assembly + damping, persistent Cholesky, persistent solves (+ FP64 refinement),
+// state update. A single-handle solve is a batch of one. The iterations of a solve are captured
+// once as a CUDA graph per batch and iteration count and replayed.
 #include <math.h>
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <numeric>
 #include <unordered_map>
@@ -27,6 +31,31 @@ using namespace ds;
 namespace ds {
 thread_local int64_t g_launches = 0;
 }
+
+static std::atomic<int64_t> g_total_kernels{0};
+
+struct ds_batch_s {
+  std::vector<ds_ctx*> hs;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool fp64 = false;
+  int refine_steps = 0;
+  BatchTabs tabs{};
+  const ProbDesc** d_descs = nullptr;
+  int2* d_tab = nullptr;   // all work tables, back to back
+  int* d_words = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int g_iters = -1;
+  int64_t g_kernels = 0;
+  bool tracing = false;
+  cudaEvent_t ev[DS_MAX_ITERS][5] = {};
+  bool ev_made = false;
+  int cur_it = 0;
+  int last_iters = 0;
+  cudaEvent_t ev_done = nullptr;
+  std::vector<cudaEvent_t> ev_in;
+  bool error = false;
+};
 
 struct ds_ctx {
   int dev = 0;
@@ -95,43 +124,35 @@ struct ds_ctx {
   void* d_v1 = nullptr;
   void* d_v2 = nullptr;
   void* d_v3 = nullptr;
-  // persistent factorisation / solve
-  LinProblem* d_lp = nullptr;
   int* d_lcnt = nullptr;      // factorisation task counters
   int* d_lflags = nullptr;    // solve row flags
   int4* d_tasks = nullptr;
   int ntasks = 0;
-  int2* d_tickets = nullptr;
-  int ntickets = 0;
-  int* d_lhead = nullptr;     // [0] factorisation ticket head, [1] solve ticket head
-  int* d_lerr = nullptr;      // bounded-wait timeout word
   int nt = 0;
+  bool prec_fp64 = false;
   double* d_acc = nullptr;
   double* d_hist = nullptr;   // DS_MAX_ITERS x 6
   int* d_flag = nullptr;
-  // graph
-  cudaGraphExec_t gexec = nullptr;
-  int g_iters = -1;
-  int64_t g_kernels = 0;       // kernel nodes in the instantiated graph
-  int64_t kernels = 0;         // kernels launched so far
-  // tracing
+  // descriptor
+  ProbDesc hdesc{};
+  ProbDesc* d_desc = nullptr;
+  // the batch of one used by ds_solve
+  ds_batch_s* self = nullptr;
   bool tracing = false;
-  int cur_it = 0;
-  cudaEvent_t ev[DS_MAX_ITERS][5] = {};
-  bool ev_made = false;
+  int64_t kernels = 0;
   int last_iters = 0;
   bool error = false;
 };
 
 namespace {
 
-#define DS_TRY(expr)                                 \
-  do {                                               \
-    cudaError_t _e = (expr);                         \
-    if (_e != cudaSuccess) {                         \
+#define DS_TRY(expr)                                          \
+  do {                                                        \
+    cudaError_t _e = (expr);                                  \
+    if (_e != cudaSuccess) {                                  \
       if (_e == cudaErrorMemoryAllocation) return DS_ERR_OOM; \
-      return DS_ERR_CUDA;                            \
-    }                                                \
+      return DS_ERR_CUDA;                                     \
+    }                                                         \
   } while (0)
 
 template <typename T>
@@ -159,17 +180,25 @@ int copy_in(void* dst, const void* src, size_t bytes, cudaStream_t s) {
   return DS_OK;
 }
 
+void push_desc(ds_ctx* h) {
+  // staged from pageable memory: the copy has left hdesc when the call returns
+  cudaMemcpyAsync(h->d_desc, &h->hdesc, sizeof(ProbDesc), cudaMemcpyHostToDevice, h->stream);
+}
+
+void destroy_batch(ds_batch_s* b);
+
 void free_cp(ds_ctx* h) {
-  if (h->gexec) cudaGraphExecDestroy(h->gexec);
-  h->gexec = nullptr;
-  h->g_iters = -1;
+  if (h->self) {
+    destroy_batch(h->self);
+    h->self = nullptr;
+  }
   dfree(h->d_g64); dfree(h->d_gc); dfree(h->d_q64); dfree(h->d_t64); dfree(h->d_node);
   dfree(h->d_pn); dfree(h->d_tp); dfree(h->d_tw); dfree(h->d_rank); dfree(h->d_seg);
   dfree(h->d_segbp); dfree(h->d_rowptr); dfree(h->d_rowcol); dfree(h->d_rowbp);
   dfree(h->d_A32); dfree(h->d_A64); dfree(h->d_Af32); dfree(h->d_Dinv); dfree(h->d_blk);
   dfree(h->d_gdata); dfree(h->d_b); dfree(h->d_x); dfree(h->d_r); dfree(h->d_v1);
-  dfree(h->d_v2); dfree(h->d_v3); dfree(h->d_lp); dfree(h->d_lcnt); dfree(h->d_lflags);
-  dfree(h->d_tasks); dfree(h->d_tickets); dfree(h->d_lhead); dfree(h->d_lerr);
+  dfree(h->d_v2); dfree(h->d_v3); dfree(h->d_lcnt); dfree(h->d_lflags); dfree(h->d_tasks);
+  dfree(h->d_desc);
   h->N = h->n = 0;
   h->have_frame = false;
 }
@@ -182,6 +211,13 @@ int check_sticky(ds_ctx* h) {
     return DS_ERR_CUDA;
   }
   return DS_OK;
+}
+
+int batch_words_status(ds_batch_s* b) {
+  int te = 0;
+  if (cudaMemcpy(&te, b->d_words + 5, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return DS_ERR_CUDA;
+  return te ? DS_ERR_TIMEOUT : DS_OK;
 }
 
 int sync_status(ds_ctx* h) {
@@ -199,13 +235,9 @@ int sync_status(ds_ctx* h) {
     if (flag & 2) return DS_ERR_ARG;
     if (flag & 1) return DS_ERR_BAD_INPUT;
   }
-  if (h->d_lerr) {
-    int te = 0;
-    if (cudaMemcpy(&te, h->d_lerr, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
-      h->error = true;
-      return DS_ERR_CUDA;
-    }
-    if (te) return DS_ERR_TIMEOUT;
+  if (h->self) {
+    int rc = batch_words_status(h->self);
+    if (rc) return rc;
   }
   if (h->N > 0) {
     double st = 0;
@@ -217,25 +249,6 @@ int sync_status(ds_ctx* h) {
     if (st != 0.0) return DS_ERR_NOT_SPD;
   }
   return DS_OK;
-}
-
-__global__ void k_record_clear(double* acc, double* hist, int it) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double* hrow = hist + 6 * it;
-    hrow[0] = acc[ACC_COST_ICP] + acc[ACC_COST_ORB] + acc[ACC_COST_ARAP];
-    hrow[1] = acc[ACC_COST_ICP];
-    hrow[2] = acc[ACC_COST_ORB];
-    hrow[3] = acc[ACC_COST_ARAP];
-    hrow[4] = acc[ACC_NVALID];
-    hrow[5] = acc[ACC_W_ARAP];
-    for (int i = 0; i < ACC_W_ARAP; ++i) acc[i] = 0.0;
-  }
-}
-
-__global__ void k_clear_acc(double* acc, int keep_w) {
-  if (threadIdx.x < ACC_COUNT) {
-    if (!(keep_w && threadIdx.x == ACC_W_ARAP)) acc[threadIdx.x] = 0.0;
-  }
 }
 
 // Device-side check of the frame's indices: an out-of-range template pixel (or one without a
@@ -265,16 +278,14 @@ __global__ void k_sanitize(int* __restrict__ midx, int M, int first_valid) {
   if (i < M && midx[i] < 0) midx[i] = first_valid;
 }
 
-// Events recorded while the stream is captured become event-record nodes of the graph only with
-// cudaEventRecordExternal (a plain record is a capture-internal dependency marker).
 // Tile tasks of one problem's factorisation in a topological order with one step of look-ahead:
 // CRIT(k) (last update of (k,k), POTRF(k), TRSM(k+1,k)), TRSM(i>k+1, k), the rest of step k-1's
 // trailing update, then step k's update of column k+1 (which the next critical task needs).
-// Encoding: {problem, type | k << 4, i, j}.
-void make_chol_tasks(int p, int nt, std::vector<int4>& out) {
-  auto C = [&](int k) { out.push_back(make_int4(p, 0 | (k << 4), k, k)); };
-  auto T = [&](int i, int k) { out.push_back(make_int4(p, 1 | (k << 4), i, k)); };
-  auto G = [&](int i, int j, int k) { out.push_back(make_int4(p, 2 | (k << 4), i, j)); };
+// Encoding: {0, type | k << 4, i, j}.
+void make_chol_tasks(int nt, std::vector<int4>& out) {
+  auto C = [&](int k) { out.push_back(make_int4(0, 0 | (k << 4), k, k)); };
+  auto T = [&](int i, int k) { out.push_back(make_int4(0, 1 | (k << 4), i, k)); };
+  auto G = [&](int i, int j, int k) { out.push_back(make_int4(0, 2 | (k << 4), i, j)); };
   for (int k = 0; k < nt; ++k) {
     C(k);
     for (int i = k + 2; i < nt; ++i) T(i, k);
@@ -286,95 +297,216 @@ void make_chol_tasks(int p, int nt, std::vector<int4>& out) {
   }
 }
 
-void trace_ev(ds_ctx* h, cudaEvent_t e) {
-  if (h->tracing) cudaEventRecordWithFlags(e, h->stream, cudaEventRecordExternal);
+// Events recorded while the stream is captured become event-record nodes of the graph only with
+// cudaEventRecordExternal (a plain record is a capture-internal dependency marker).
+void trace(ds_batch_s* b, int it, int k) {
+  if (b->tracing) cudaEventRecordWithFlags(b->ev[it][k], b->stream, cudaEventRecordExternal);
 }
-void trace(ds_ctx* h, int it, int k) { trace_ev(h, h->ev[it][k]); }
 
-// One linearisation (ICP + ORB + ARAP + assembly) into the buffers of the handle's precision.
-void enqueue_linearize(ds_ctx* h, bool first, double lam, bool factor_buffers) {
-  cudaStream_t s = h->stream;
-  const ds_params& p = h->prm;
-  cudaMemsetAsync(h->d_blk, 0, sizeof(float) * 36 * (size_t)h->nbp, s);
-  cudaMemsetAsync(h->d_gdata, 0, sizeof(float) * h->n, s);
-  launch_icp(h->d_tp, h->d_tw, h->d_seg, h->d_segbp, h->P, h->d_node, h->d_tpts, h->d_tnrm, h->W,
-             h->H, h->K, (float)p.tukey_c_mm, h->d_blk, h->d_gdata, h->d_acc, s);
-  launch_orb(h->d_midx, h->d_mxyz, h->M, h->d_rank, h->d_tp, h->d_tw, h->d_seg, h->d_segbp,
-             h->d_node, h->d_rs_mask, h->d_rs_what, (float)p.H_mm, (float)p.w_orb, h->d_blk,
-             h->d_gdata, h->d_acc, s);
-  float inv2sig2 = (float)(1.0 / (2.0 * h->sigma_A * h->sigma_A));
-  if (factor_buffers && p.precision == DS_PREC_FP64) {
-    launch_arap_assemble<double>(h->d_pn, h->N, inv2sig2, h->d_rowptr, h->d_rowcol, h->d_rowbp,
-                                 h->d_blk, h->d_gdata, h->d_acc, first, p.w_arap0,
-                                 (float)p.w_orb, (float)p.w_angle, (float)p.w_rot, lam,
-                                 p.eps_damp, h->d_A64,
-                                 p.refine_steps > 0 ? h->d_A32 : nullptr, h->d_b, s);
-  } else if (factor_buffers && p.precision == DS_PREC_FP32_REFINE) {
-    launch_arap_assemble<float>(h->d_pn, h->N, inv2sig2, h->d_rowptr, h->d_rowcol, h->d_rowbp,
-                                h->d_blk, h->d_gdata, h->d_acc, first, p.w_arap0, (float)p.w_orb,
-                                (float)p.w_angle, (float)p.w_rot, lam, p.eps_damp, h->d_Af32,
-                                h->d_A32, h->d_b, s);
-  } else {
-    launch_arap_assemble<float>(h->d_pn, h->N, inv2sig2, h->d_rowptr, h->d_rowcol, h->d_rowbp,
-                                h->d_blk, h->d_gdata, h->d_acc, first, p.w_arap0, (float)p.w_orb,
-                                (float)p.w_angle, (float)p.w_rot, lam, p.eps_damp, h->d_A32,
-                                nullptr, h->d_b, s);
+// ----------------------------------------------------------------------------- batches
+
+void destroy_batch(ds_batch_s* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->ev_made)
+    for (int i = 0; i < DS_MAX_ITERS; ++i)
+      for (int k = 0; k < 5; ++k) cudaEventDestroy(b->ev[i][k]);
+  if (b->ev_done) cudaEventDestroy(b->ev_done);
+  for (auto e : b->ev_in) cudaEventDestroy(e);
+  dfree(b->d_descs);
+  dfree(b->d_tab);
+  dfree(b->d_words);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch_s** out) {
+  *out = nullptr;
+  if (n < 1) return DS_ERR_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!hs[i] || hs[i]->N == 0 || hs[i]->error) return DS_ERR_ARG;
+  const bool fp64 = hs[0]->prec_fp64;
+  const int prec = hs[0]->prm.precision;
+  const int steps = prec == DS_PREC_FP32 ? 0 : hs[0]->prm.refine_steps;
+  for (int i = 1; i < n; ++i) {
+    const int ps = hs[i]->prm.precision == DS_PREC_FP32 ? 0 : hs[i]->prm.refine_steps;
+    if (hs[i]->prec_fp64 != fp64 || (hs[i]->prm.precision == DS_PREC_FP32) != (prec == DS_PREC_FP32) ||
+        ps != steps)
+      return DS_ERR_ARG;
   }
+  ds_batch_s* b = new ds_batch_s();
+  b->hs.assign(hs, hs + n);
+  b->fp64 = fp64;
+  b->refine_steps = steps;
+  b->stream = stream;
+  b->own_stream = own;
+  std::vector<int2> icp, rows, nodes, vec, res;
+  int max_tasks = 0, max_nt = 0;
+  std::vector<const ProbDesc*> descs(n);
+  for (int p = 0; p < n; ++p) {
+    ds_ctx* h = hs[p];
+    descs[p] = h->d_desc;
+    for (int t = 0; t * kTile < h->P; ++t) icp.push_back(make_int2(p, t));
+    for (int i = 0; i < h->N; ++i) rows.push_back(make_int2(p, i));
+    for (int c = 0; c * 128 < h->N; ++c) nodes.push_back(make_int2(p, c));
+    for (int c = 0; c * 256 < h->n; ++c) vec.push_back(make_int2(p, c));
+    for (int c = 0; c * 8 < h->n; ++c) res.push_back(make_int2(p, c));
+    max_tasks = std::max(max_tasks, h->ntasks);
+    max_nt = std::max(max_nt, h->nt);
+  }
+  const size_t ntab = icp.size() + rows.size() + nodes.size() + vec.size() + res.size();
+  int rc;
+  if ((rc = dalloc(&b->d_descs, n)) || (rc = dalloc(&b->d_tab, ntab)) ||
+      (rc = dalloc(&b->d_words, 8))) {
+    destroy_batch(b);
+    return rc;
+  }
+  std::vector<int2> all;
+  all.reserve(ntab);
+  for (auto* v : {&icp, &rows, &nodes, &vec, &res}) all.insert(all.end(), v->begin(), v->end());
+  cudaMemcpy(b->d_descs, descs.data(), sizeof(void*) * n, cudaMemcpyHostToDevice);
+  cudaMemcpy(b->d_tab, all.data(), sizeof(int2) * ntab, cudaMemcpyHostToDevice);
+  cudaMemset(b->d_words, 0, sizeof(int) * 8);
+  BatchTabs& T = b->tabs;
+  T.d = b->d_descs;
+  T.P = n;
+  size_t off = 0;
+  T.icp = b->d_tab + off; T.n_icp = (int)icp.size(); off += icp.size();
+  T.rows = b->d_tab + off; T.n_rows = (int)rows.size(); off += rows.size();
+  T.nodes = b->d_tab + off; T.n_nodes = (int)nodes.size(); off += nodes.size();
+  T.vec = b->d_tab + off; T.n_vec = (int)vec.size(); off += vec.size();
+  T.res = b->d_tab + off; T.n_res = (int)res.size(); off += res.size();
+  T.orb_ctas = 16;
+  T.max_tasks = max_tasks;
+  T.max_nt = max_nt;
+  T.words = b->d_words;
+  if (cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming) != cudaSuccess) {
+    destroy_batch(b);
+    return DS_ERR_CUDA;
+  }
+  b->ev_in.resize(n, nullptr);
+  for (int p = 0; p < n; ++p)
+    if (cudaEventCreateWithFlags(&b->ev_in[p], cudaEventDisableTiming) != cudaSuccess) {
+      destroy_batch(b);
+      return DS_ERR_CUDA;
+    }
+  *out = b;
+  return DS_OK;
 }
 
 template <typename T>
-void enqueue_trsv(ds_ctx* h) {
-  cudaStream_t s = h->stream;
-  cudaMemsetAsync(h->d_lflags, 0, sizeof(int) * 2 * h->nt, s);
-  cudaMemsetAsync(h->d_lhead + 1, 0, sizeof(int), s);
-  launch_trsv_dag<T>(h->d_lp, h->d_tickets, h->ntickets, h->d_lhead + 1, h->d_lerr, s);
-}
-
-template <typename T>
-void enqueue_factor_solve(ds_ctx* h, int steps) {
-  cudaStream_t s = h->stream;
-  int n = h->n;
-  T* v1 = (T*)h->d_v1;
-  T* v2 = (T*)h->d_v2;
-  const size_t ncnt = (size_t)h->nt + 2 * (size_t)h->nt * h->nt;
-  cudaMemsetAsync(h->d_lcnt, 0, sizeof(int) * ncnt, s);
-  cudaMemsetAsync(h->d_lhead, 0, sizeof(int), s);
-  launch_chol_dag<T>(h->d_lp, h->d_tasks, h->ntasks, h->d_lhead, h->d_lerr, s);
-  trace(h, h->cur_it, 2);
-  launch_cast_from64<T>(h->d_b, v1, n, s);
-  enqueue_trsv<T>(h);
-  launch_axpy_to64<T>(v2, h->d_x, n, true, s);
-  for (int k = 0; k < steps; ++k) {
-    launch_residual64(h->d_A32, n, h->d_b, h->d_x, h->d_r, s);
-    launch_cast_from64<T>(h->d_r, v1, n, s);
-    enqueue_trsv<T>(h);
-    launch_axpy_to64<T>(v2, h->d_x, n, false, s);
+void enqueue_factor_solve(ds_batch_s* b) {
+  cudaStream_t s = b->stream;
+  const BatchTabs& B = b->tabs;
+  launch_chol_dag<T>(B, s);
+  trace(b, b->cur_it, 2);
+  launch_vec_in<T>(B, false, s);
+  launch_trsv_dag<T>(B, 1, s);
+  launch_vec_out<T>(B, true, s);
+  for (int k = 0; k < b->refine_steps; ++k) {
+    launch_residual64(B, s);
+    launch_vec_in<T>(B, true, s);
+    launch_trsv_dag<T>(B, 2 + k, s);
+    launch_vec_out<T>(B, false, s);
   }
 }
 
-void enqueue_solve(ds_ctx* h, int iters) {
-  cudaStream_t s = h->stream;
-  const ds_params& p = h->prm;
-  launch_node_update(nullptr, h->N, h->d_q64, h->d_t64, h->d_g64, h->d_gc, h->d_node, h->d_pn,
-                     s);
-  k_clear_acc<<<1, 32, 0, s>>>(h->d_acc, 0);
+void enqueue_solve(ds_batch_s* b, int iters) {
+  cudaStream_t s = b->stream;
+  const BatchTabs& B = b->tabs;
+  launch_iter_end(B, -1, false, s);  // node tables of the current state, accumulators cleared
   for (int it = 0; it < iters; ++it) {
-    h->cur_it = it;
-    trace(h, it, 0);
-    enqueue_linearize(h, it == 0, p.lambda, true);
-    trace(h, it, 1);
-    if (p.precision == DS_PREC_FP64)
-      enqueue_factor_solve<double>(h, p.refine_steps);
-    else if (p.precision == DS_PREC_FP32_REFINE)
-      enqueue_factor_solve<float>(h, p.refine_steps);
+    b->cur_it = it;
+    trace(b, it, 0);
+    launch_iter_begin(B, s);
+    launch_icp(B, s);
+    launch_orb(B, s);
+    if (b->fp64)
+      launch_arap_assemble<double>(B, it == 0, false, s);
     else
-      enqueue_factor_solve<float>(h, 0);
-    trace(h, it, 4);
-    k_record_clear<<<1, 32, 0, s>>>(h->d_acc, h->d_hist, it);
-    launch_node_update(h->d_x, h->N, h->d_q64, h->d_t64, h->d_g64, h->d_gc, h->d_node, h->d_pn,
-                       s);
+      launch_arap_assemble<float>(B, it == 0, false, s);
+    trace(b, it, 1);
+    if (b->fp64)
+      enqueue_factor_solve<double>(b);
+    else
+      enqueue_factor_solve<float>(b);
+    trace(b, it, 4);
+    launch_iter_end(B, it, true, s);
   }
-  trace(h, iters - 1, 3);
+  trace(b, iters - 1, 3);
+}
+
+int run_batch(ds_batch_s* b, int iters, bool use_graph) {
+  cudaStream_t s = b->stream;
+  // order after each handle's pending work (submit_frame on its own stream)
+  for (size_t p = 0; p < b->hs.size(); ++p) {
+    ds_ctx* h = b->hs[p];
+    if (h->stream != s) {
+      cudaEventRecord(b->ev_in[p], h->stream);
+      cudaStreamWaitEvent(s, b->ev_in[p], 0);
+    }
+  }
+  const int64_t before = g_launches;
+  int64_t launched = 0;
+  if (use_graph) {
+    if (!b->gexec || b->g_iters != iters) {
+      if (b->gexec) cudaGraphExecDestroy(b->gexec);
+      b->gexec = nullptr;
+      cudaGraph_t g;
+      if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        b->error = true;
+        return DS_ERR_CUDA;
+      }
+      enqueue_solve(b, iters);
+      if (cudaStreamEndCapture(s, &g) != cudaSuccess) {
+        cudaGetLastError();
+        b->error = true;
+        return DS_ERR_CUDA;
+      }
+      size_t nn = 0;
+      cudaGraphGetNodes(g, nullptr, &nn);
+      std::vector<cudaGraphNode_t> nodes(nn);
+      if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+      b->g_kernels = 0;
+      for (auto nd : nodes) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel)
+          ++b->g_kernels;
+      }
+      cudaError_t e = cudaGraphInstantiate(&b->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        b->gexec = nullptr;
+        b->error = true;
+        return DS_ERR_CUDA;
+      }
+      b->g_iters = iters;
+    }
+    if (cudaGraphLaunch(b->gexec, s) != cudaSuccess) {
+      b->error = true;
+      return DS_ERR_CUDA;
+    }
+    launched = b->g_kernels;
+  } else {
+    enqueue_solve(b, iters);
+    launched = g_launches - before;
+  }
+  g_total_kernels += launched;
+  b->last_iters = iters;
+  // each handle's later work follows the batch
+  cudaEventRecord(b->ev_done, s);
+  for (ds_ctx* h : b->hs) {
+    if (h->stream != s) cudaStreamWaitEvent(h->stream, b->ev_done, 0);
+    h->last_iters = iters;
+    h->kernels += launched;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    b->error = true;
+    return DS_ERR_CUDA;
+  }
+  return DS_OK;
 }
 
 bool valid_params(const ds_params& p) {
@@ -382,9 +514,11 @@ bool valid_params(const ds_params& p) {
          p.n_reweight <= 1000 && p.H_mm > 0 && p.tukey_c_mm > 0 && p.lambda >= 0 &&
          p.eps_damp >= 0 && p.keep_frac >= 0 && p.keep_frac <= 1 && p.sigma_blend_scale > 0 &&
          p.sigma_arap_scale > 0 && p.precision >= 0 && p.precision <= 2 && p.refine_steps >= 0 &&
-         p.refine_steps <= 4 && p.w_orb >= 0 && p.w_angle >= 0 && p.w_rot >= 0 &&
+         p.refine_steps <= 3 && p.w_orb >= 0 && p.w_angle >= 0 && p.w_rot >= 0 &&
          p.w_arap0 >= 0;
 }
+
+bool is_host_ptr(const void* p);
 
 }  // namespace
 
@@ -661,9 +795,8 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
       (rc = dalloc((char**)&h->d_v1, tsz * n)) || (rc = dalloc((char**)&h->d_v2, tsz * n)) ||
       (rc = dalloc((char**)&h->d_v3, tsz * n)) ||
       (rc = dalloc((char**)&h->d_Dinv, tsz * (size_t)nt * TB * TB)) ||
-      (rc = dalloc(&h->d_lp, 1)) || (rc = dalloc(&h->d_lcnt, (size_t)nt + 2 * (size_t)nt * nt)) ||
-      (rc = dalloc(&h->d_lflags, 2 * (size_t)nt)) || (rc = dalloc(&h->d_lhead, 2)) ||
-      (rc = dalloc(&h->d_lerr, 1))) {
+      (rc = dalloc(&h->d_lcnt, (size_t)nt + 2 * (size_t)nt * nt)) ||
+      (rc = dalloc(&h->d_lflags, 2 * (size_t)nt))) {
     free_cp(h);
     return rc;
   }
@@ -677,18 +810,64 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
   }
   {
     std::vector<int4> tasks;
-    make_chol_tasks(0, nt, tasks);
-    std::vector<int2> tickets;
-    for (int t = 0; t < 2 * nt; ++t) tickets.push_back(make_int2(0, t));
+    make_chol_tasks(nt, tasks);
     h->ntasks = (int)tasks.size();
-    h->ntickets = (int)tickets.size();
-    if ((rc = dalloc(&h->d_tasks, tasks.size())) || (rc = dalloc(&h->d_tickets, tickets.size()))) {
+    if ((rc = dalloc(&h->d_tasks, tasks.size()))) {
       free_cp(h);
       return rc;
     }
     cudaMemcpy(h->d_tasks, tasks.data(), sizeof(int4) * tasks.size(), cudaMemcpyHostToDevice);
-    cudaMemcpy(h->d_tickets, tickets.data(), sizeof(int2) * tickets.size(), cudaMemcpyHostToDevice);
-    LinProblem lp;
+  }
+  h->prec_fp64 = prec == DS_PREC_FP64;
+  {
+    ProbDesc& D = h->hdesc;
+    memset(&D, 0, sizeof(D));
+    D.W = h->W;
+    D.H = h->H;
+    D.P = P;
+    D.N = N;
+    D.n = n;
+    D.M = 0;
+    D.nbp = h->nbp;
+    D.fx = h->K.fx;
+    D.fy = h->K.fy;
+    D.cx = h->K.cx;
+    D.cy = h->K.cy;
+    D.tukey_c = (float)h->prm.tukey_c_mm;
+    D.H_mm = (float)h->prm.H_mm;
+    D.w_orb = (float)h->prm.w_orb;
+    D.w_angle = (float)h->prm.w_angle;
+    D.w_rot = (float)h->prm.w_rot;
+    D.inv2sig2 = (float)(1.0 / (2.0 * h->sigma_A * h->sigma_A));
+    D.w_arap0 = h->prm.w_arap0;
+    D.lam = h->prm.lambda;
+    D.eps = h->prm.eps_damp;
+    D.write_ref = (prec != DS_PREC_FP32 && h->prm.refine_steps > 0) ? 1 : 0;
+    D.tp = h->d_tp;
+    D.tw = h->d_tw;
+    D.seg = h->d_seg;
+    D.segbp = h->d_segbp;
+    D.rank = h->d_rank;
+    D.tpts = h->d_tpts;
+    D.tnrm = h->d_tnrm;
+    D.rowptr = h->d_rowptr;
+    D.rowcol = h->d_rowcol;
+    D.rowbp = h->d_rowbp;
+    D.g64 = h->d_g64;
+    D.gc = h->d_gc;
+    D.node = h->d_node;
+    D.pn = h->d_pn;
+    D.blk = h->d_blk;
+    D.gdata = h->d_gdata;
+    D.acc = h->d_acc;
+    D.hist = h->d_hist;
+    D.q64 = h->d_q64;
+    D.t64 = h->d_t64;
+    D.Aref = h->d_A32;
+    D.b = h->d_b;
+    D.x = h->d_x;
+    D.r = h->d_r;
+    LinProblem& lp = D.lp;
     lp.A = prec == DS_PREC_FP64 ? (void*)h->d_A64
                                 : (prec == DS_PREC_FP32_REFINE ? (void*)h->d_Af32 : (void*)h->d_A32);
     lp.Dinv = h->d_Dinv;
@@ -696,12 +875,17 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
     lp.nt = nt;
     lp.cnt = h->d_lcnt;
     lp.flags = h->d_lflags;
+    lp.tasks = h->d_tasks;
+    lp.ntasks = h->ntasks;
     lp.status = h->d_acc + ACC_STATUS;
     lp.rhs = h->d_v1;
     lp.y = h->d_v3;
     lp.x = h->d_v2;
-    cudaMemcpy(h->d_lp, &lp, sizeof(lp), cudaMemcpyHostToDevice);
-    cudaMemset(h->d_lerr, 0, sizeof(int));
+    if ((rc = dalloc(&h->d_desc, 1))) {
+      free_cp(h);
+      return rc;
+    }
+    push_desc(h);
   }
   std::vector<double> q0(4 * N, 0.0), t0(3 * N, 0.0);
   for (int i = 0; i < N; ++i) q0[4 * i] = 1.0;
@@ -719,8 +903,6 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
   if (h->d_A64) cudaMemset(h->d_A64, 0, sizeof(double) * nn);
   if (h->d_Af32) cudaMemset(h->d_Af32, 0, sizeof(float) * nn);
   cudaMemset(h->d_acc, 0, sizeof(double) * ACC_COUNT);
-  launch_node_update(nullptr, N, h->d_q64, h->d_t64, h->d_g64, h->d_gc, h->d_node, h->d_pn,
-                     h->stream);
   if (cudaStreamSynchronize(h->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
     h->error = true;
     return DS_ERR_CUDA;
@@ -728,7 +910,10 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
   return DS_OK;
 }
 
-static bool is_host_ptr(const void* p) {
+}  // extern "C"
+
+namespace {
+bool is_host_ptr(const void* p) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
@@ -736,6 +921,9 @@ static bool is_host_ptr(const void* p) {
   }
   return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
 }
+}  // namespace
+
+extern "C" {
 
 int ds_submit_frame(ds_handle h, const float* depth_hw, const int32_t* match_tmpl_idx,
                     const float* match_xyz, int32_t M, const int32_t* hyp_list) {
@@ -773,19 +961,17 @@ int ds_submit_frame(ds_handle h, const float* depth_hw, const int32_t* match_tmp
       return rc;
     }
     h->M_cap = cap;
-    if (h->gexec) {
-      cudaGraphExecDestroy(h->gexec);
-      h->gexec = nullptr;
-      h->g_iters = -1;
-    }
-  }
-  // a new M changes the captured graph's launch shapes
-  if (M != h->M && h->gexec) {
-    cudaGraphExecDestroy(h->gexec);
-    h->gexec = nullptr;
-    h->g_iters = -1;
   }
   h->M = M;
+  // the frame's match count and buffers, read by the kernels from the descriptor
+  if (h->hdesc.M != M || h->hdesc.midx != h->d_midx) {
+    h->hdesc.M = M;
+    h->hdesc.midx = h->d_midx;
+    h->hdesc.mxyz = h->d_mxyz;
+    h->hdesc.mask = h->d_rs_mask;
+    h->hdesc.what = h->d_rs_what;
+    push_desc(h);
+  }
   const int64_t launches0 = g_launches;
   if ((rc = copy_in(h->d_depth, depth_hw, sizeof(float) * npx, s))) return rc;
   if ((rc = copy_in(h->d_midx, match_tmpl_idx, sizeof(int) * M, s))) return rc;
@@ -838,73 +1024,86 @@ static int finish_solve(ds_handle h, int iters, ds_solve_stats* out) {
   return check_sticky(h);
 }
 
+static int ensure_self(ds_handle h) {
+  if (h->self) return DS_OK;
+  ds_ctx* one[1] = {h};
+  int rc = make_batch(one, 1, h->stream, false, &h->self);
+  if (rc) return rc;
+  h->self->tracing = h->tracing;
+  if (h->tracing) {
+    for (int i = 0; i < DS_MAX_ITERS; ++i)
+      for (int k = 0; k < 5; ++k) cudaEventCreate(&h->self->ev[i][k]);
+    h->self->ev_made = true;
+  }
+  return DS_OK;
+}
+
 int ds_solve(ds_handle h, int32_t iters, ds_solve_stats* out) {
   if (!h || iters < 1 || iters > DS_MAX_ITERS) return DS_ERR_ARG;
   if (h->N == 0 || !h->have_frame) return DS_ERR_STATE;
   if (h->error) return DS_ERR_CUDA;
-  cudaStream_t s = h->stream;
-  if (h->prm.use_graph) {
-    if (!h->gexec || h->g_iters != iters) {
-      if (h->gexec) cudaGraphExecDestroy(h->gexec);
-      h->gexec = nullptr;
-      cudaGraph_t g;
-      if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-        h->error = true;
-        return DS_ERR_CUDA;
-      }
-      enqueue_solve(h, iters);
-      if (cudaStreamEndCapture(s, &g) != cudaSuccess) {
-        cudaGetLastError();
-        h->error = true;
-        return DS_ERR_CUDA;
-      }
-      size_t nn = 0;
-      cudaGraphGetNodes(g, nullptr, &nn);
-      std::vector<cudaGraphNode_t> nodes(nn);
-      if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
-      h->g_kernels = 0;
-      for (auto nd : nodes) {
-        cudaGraphNodeType ty;
-        if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel)
-          ++h->g_kernels;
-      }
-      cudaError_t e = cudaGraphInstantiate(&h->gexec, g, 0);
-      cudaGraphDestroy(g);
-      if (e != cudaSuccess) {
-        h->gexec = nullptr;
-        h->error = true;
-        return DS_ERR_CUDA;
-      }
-      h->g_iters = iters;
-    }
-    if (cudaGraphLaunch(h->gexec, s) != cudaSuccess) {
-      h->error = true;
-      return DS_ERR_CUDA;
-    }
-    h->kernels += h->g_kernels;
-  } else {
-    int64_t before = g_launches;
-    enqueue_solve(h, iters);
-    h->kernels += g_launches - before;
-  }
-  h->last_iters = iters;
-  int rc = check_sticky(h);
+  int rc = ensure_self(h);
   if (rc) return rc;
+  rc = run_batch(h->self, iters, h->prm.use_graph != 0);
+  if (rc) {
+    h->error = true;
+    return rc;
+  }
   if (out) return finish_solve(h, iters, out);
   return DS_OK;
 }
 
-int ds_solve_batch(ds_handle* hs, int32_t n, int32_t iters) {
-  if (!hs || n < 0) return DS_ERR_ARG;
-  for (int i = 0; i < n; ++i) {
-    int rc = ds_solve(hs[i], iters, nullptr);
-    if (rc) return rc;
+int ds_batch_create(const ds_handle* hs, int32_t n, void* cuda_stream, ds_batch* out) {
+  if (!hs || !out || n < 1) return DS_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  bool own = false;
+  if (!s) {
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return DS_ERR_CUDA;
+    own = true;
   }
-  for (int i = 0; i < n; ++i) {
-    int rc = sync_status(hs[i]);
-    if (rc) return rc;
+  std::vector<ds_ctx*> v(hs, hs + n);
+  int rc = make_batch(v.data(), n, s, own, out);
+  if (rc && own) cudaStreamDestroy(s);
+  return rc;
+}
+
+int ds_batch_solve(ds_batch b, int32_t iters) {
+  if (!b || iters < 1 || iters > DS_MAX_ITERS) return DS_ERR_ARG;
+  if (b->error) return DS_ERR_CUDA;
+  for (ds_ctx* h : b->hs)
+    if (!h->have_frame || h->N == 0) return DS_ERR_STATE;
+  bool graph = true;
+  for (ds_ctx* h : b->hs) graph = graph && h->prm.use_graph;
+  return run_batch(b, iters, graph);
+}
+
+int ds_batch_status(ds_batch b) {
+  if (!b) return DS_ERR_ARG;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return DS_ERR_CUDA;
+  int rc = batch_words_status(b);
+  if (rc) return rc;
+  for (ds_ctx* h : b->hs) {
+    double st = 0;
+    cudaMemcpy(&st, h->d_acc + ACC_STATUS, sizeof(double), cudaMemcpyDeviceToHost);
+    if (st != 0.0) return DS_ERR_NOT_SPD;
   }
   return DS_OK;
+}
+
+int ds_batch_destroy(ds_batch b) {
+  destroy_batch(b);
+  return DS_OK;
+}
+
+int ds_solve_batch(ds_handle* hs, int32_t n, int32_t iters) {
+  if (!hs || n < 1) return DS_ERR_ARG;
+  ds_batch b = nullptr;
+  int rc = ds_batch_create(hs, n, nullptr, &b);
+  if (rc) return rc;
+  rc = ds_batch_solve(b, iters);
+  if (!rc) rc = ds_batch_status(b);
+  ds_batch_destroy(b);
+  return rc;
 }
 
 int ds_get_deformation(ds_handle h, float* q_N4, float* t_N3, float* pos_N3) {
@@ -1044,14 +1243,19 @@ int ds_linearize(ds_handle h, double w_arap_in, double* A_nn, double* b_n, doubl
   if (!h) return DS_ERR_ARG;
   if (h->N == 0 || !h->have_frame) return DS_ERR_STATE;
   if (h->error) return DS_ERR_CUDA;
+  int rc = ensure_self(h);
+  if (rc) return rc;
   cudaStream_t s = h->stream;
-  launch_node_update(nullptr, h->N, h->d_q64, h->d_t64, h->d_g64, h->d_gc, h->d_node, h->d_pn, s);
-  k_clear_acc<<<1, 32, 0, s>>>(h->d_acc, 0);
-  bool first = !(w_arap_in > 0);
-  if (!first) cudaMemcpyAsync(h->d_acc + ACC_W_ARAP, &w_arap_in, sizeof(double),
-                              cudaMemcpyHostToDevice, s);
-  enqueue_linearize(h, first, 0.0, false);
-  int rc = sync_status(h);
+  const BatchTabs& B = h->self->tabs;
+  launch_iter_end(B, -1, false, s);
+  const bool first = !(w_arap_in > 0);
+  if (!first)
+    cudaMemcpyAsync(h->d_acc + ACC_W_ARAP, &w_arap_in, sizeof(double), cudaMemcpyHostToDevice, s);
+  launch_iter_begin(B, s);
+  launch_icp(B, s);
+  launch_orb(B, s);
+  launch_arap_assemble<float>(B, first, true, s);
+  rc = sync_status(h);
   if (rc) return rc;
   double acc[ACC_COUNT];
   cudaMemcpy(acc, h->d_acc, sizeof(acc), cudaMemcpyDeviceToHost);
@@ -1072,26 +1276,16 @@ int ds_linearize(ds_handle h, double w_arap_in, double* A_nn, double* b_n, doubl
     dfree(tmp);
     if (e != cudaSuccess) return DS_ERR_ARG;
   }
-  // the captured graph and the next solve start from fresh accumulators
-  k_clear_acc<<<1, 32, 0, s>>>(h->d_acc, 0);
   return check_sticky(h);
 }
 
 int ds_set_tracing(ds_handle h, int32_t on) {
   if (!h) return DS_ERR_ARG;
   if (h->error) return DS_ERR_CUDA;
-  bool want = on != 0;
-  if (want && !h->ev_made) {
-    for (int i = 0; i < DS_MAX_ITERS; ++i)
-      for (int k = 0; k < 5; ++k)
-        if (cudaEventCreate(&h->ev[i][k]) != cudaSuccess) return DS_ERR_CUDA;
-    h->ev_made = true;
-  }
-  if (want != h->tracing && h->gexec) {
-    cudaStreamSynchronize(h->stream);
-    cudaGraphExecDestroy(h->gexec);
-    h->gexec = nullptr;
-    h->g_iters = -1;
+  const bool want = on != 0;
+  if (want != h->tracing && h->self) {
+    destroy_batch(h->self);  // the graph is re-captured with (or without) the events
+    h->self = nullptr;
   }
   h->tracing = want;
   return DS_OK;
@@ -1099,25 +1293,26 @@ int ds_set_tracing(ds_handle h, int32_t on) {
 
 int ds_get_phase_times(ds_handle h, double* ms4) {
   if (!h || !ms4) return DS_ERR_ARG;
-  if (!h->tracing || h->last_iters == 0) return DS_ERR_STATE;
+  if (!h->tracing || !h->self || h->self->last_iters == 0) return DS_ERR_STATE;
   int rc = sync_status(h);
   if (rc && rc != DS_ERR_NOT_SPD) return rc;
+  ds_batch_s* b = h->self;
   for (int k = 0; k < 4; ++k) ms4[k] = 0.0;
-  int it_n = h->last_iters;
+  const int it_n = b->last_iters;
   for (int it = 0; it < it_n; ++it) {
-    float a = 0, b = 0, c = 0, d = 0;
-    cudaError_t e = cudaEventElapsedTime(&a, h->ev[it][0], h->ev[it][1]);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, h->ev[it][1], h->ev[it][2]);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&c, h->ev[it][2], h->ev[it][4]);
+    float a = 0, bb = 0, c = 0, d = 0;
+    cudaError_t e = cudaEventElapsedTime(&a, b->ev[it][0], b->ev[it][1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&bb, b->ev[it][1], b->ev[it][2]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&c, b->ev[it][2], b->ev[it][4]);
     if (e == cudaSuccess)
-      e = cudaEventElapsedTime(&d, h->ev[it][4],
-                               it + 1 < it_n ? h->ev[it + 1][0] : h->ev[it_n - 1][3]);
+      e = cudaEventElapsedTime(&d, b->ev[it][4],
+                               it + 1 < it_n ? b->ev[it + 1][0] : b->ev[it_n - 1][3]);
     if (e != cudaSuccess) {
       cudaGetLastError();  // not a sticky error: the events were not recorded by this solve
       return DS_ERR_STATE;
     }
     ms4[0] += a;
-    ms4[1] += b;
+    ms4[1] += bb;
     ms4[2] += c;
     ms4[3] += d;
   }
@@ -1125,8 +1320,8 @@ int ds_get_phase_times(ds_handle h, double* ms4) {
 }
 
 int ds_get_counters(ds_handle h, int64_t* kernels_launched) {
-  if (!h || !kernels_launched) return DS_ERR_ARG;
-  *kernels_launched = h->kernels;
+  if (!kernels_launched) return DS_ERR_ARG;
+  *kernels_launched = h ? h->kernels : g_total_kernels.load();
   return DS_OK;
 }
 
@@ -1139,9 +1334,6 @@ int ds_destroy(ds_handle h) {
   dfree(h->d_rs_scratch); dfree(h->d_rs_hbits); dfree(h->d_rs_hw); dfree(h->d_rs_score);
   dfree(h->d_rs_mask); dfree(h->d_rs_what); dfree(h->d_rs_kept); dfree(h->d_rs_counts);
   dfree(h->d_acc); dfree(h->d_hist); dfree(h->d_flag);
-  if (h->ev_made)
-    for (int i = 0; i < DS_MAX_ITERS; ++i)
-      for (int k = 0; k < 5; ++k) cudaEventDestroy(h->ev[i][k]);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
   return DS_OK;

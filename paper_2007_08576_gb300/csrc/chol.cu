@@ -400,9 +400,9 @@ __device__ void task_gemm(T* A, int n, int i, int j, int k, T* Pt, T* Qt) {
 // [nt + nt^2, nt + 2 nt^2) updates applied to tile (i, j). Task types: 0 critical task
 // (last update of (k,k), POTRF(k), TRSM(k+1,k)), 1 TRSM(i,k), 2 GEMM(i,j,k).
 template <typename T, int TB>
-__global__ __launch_bounds__(256) void k_chol_dag(const LinProblem* __restrict__ probs,
-                                                  const int4* __restrict__ tasks, int ntasks,
-                                                  int* __restrict__ head, int* __restrict__ err,
+__global__ __launch_bounds__(256) void k_chol_dag(const ProbDesc* const* __restrict__ descs,
+                                                  int np, int nticket, int* __restrict__ head,
+                                                  int* __restrict__ err,
                                                   unsigned long long budget_ns) {
   constexpr int LDT = TileCfg<T, TB>::LDT;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -416,12 +416,18 @@ __global__ __launch_bounds__(256) void k_chol_dag(const LinProblem* __restrict__
     if (threadIdx.x == 0) s_t = atomicAdd(head, 1);
     __syncthreads();
     const int t = s_t;
-    if (t >= ntasks) return;
-    const int4 tk = tasks[t];
+    if (t >= nticket) return;
+    // ticket -> (problem, local task): problems interleaved round-robin
+    const LinProblem& P = descs[t % np]->lp;
+    const int local = t / np;
+    if (local >= P.ntasks) {
+      __syncthreads();
+      continue;
+    }
+    const int4 tk = P.tasks[local];
 #if defined(DS_TASK_TRACE)
     if (threadIdx.x == 0) ds_trace_mark(t, 0);
 #endif
-    const LinProblem P = probs[tk.x];
     const int type = tk.y & 15, k = tk.y >> 4, i = tk.z, j = tk.w;
     const int nt = P.nt;
     int* pdone = P.cnt;
@@ -557,8 +563,8 @@ __device__ __forceinline__ void gemv_cols_pf(const T (&v)[SolveTile<T, TB>::NV],
 // loaded into registers before the wait on its producer (the tiles do not depend on it), so a
 // dependency costs one flag hand-off and one 64-value vector load.
 template <typename T, int TB>
-__global__ __launch_bounds__(256) void k_trsv_dag(const LinProblem* __restrict__ probs,
-                                                  const int2* __restrict__ tickets, int ntk,
+__global__ __launch_bounds__(256) void k_trsv_dag(const ProbDesc* const* __restrict__ descs,
+                                                  int np, int nticket, int solve_id,
                                                   int* __restrict__ head, int* __restrict__ err,
                                                   unsigned long long budget_ns) {
   constexpr int NV = SolveTile<T, TB>::NV;
@@ -570,9 +576,13 @@ __global__ __launch_bounds__(256) void k_trsv_dag(const LinProblem* __restrict__
     if (threadIdx.x == 0) s_t = atomicAdd(head, 1);
     __syncthreads();
     const int t = s_t;
-    if (t >= ntk) return;
-    const int2 tk = tickets[t];
-    const LinProblem P = probs[tk.x];
+    if (t >= nticket) return;
+    const LinProblem& P = descs[t % np]->lp;
+    const int2 tk = make_int2(t % np, t / np);
+    if (tk.y >= 2 * P.nt) {
+      __syncthreads();
+      continue;
+    }
     const int nt = P.nt, n = P.n;
     const bool fwd = tk.y < nt;
     const int i = fwd ? tk.y : 2 * nt - 1 - tk.y;
@@ -592,7 +602,7 @@ __global__ __launch_bounds__(256) void k_trsv_dag(const LinProblem* __restrict__
       prefetch_cols<T, TB>(D, TB, TB, TB, dv);
     bool ok = true;
     if (threadIdx.x == 0) {
-      ok = fwd ? true : wait_ge(&flag[i], 1, err, budget_ns);
+      ok = fwd ? true : wait_ge(&flag[i], solve_id, err, budget_ns);
       __threadfence();
       s_ok = ok;
     }
@@ -613,7 +623,7 @@ __global__ __launch_bounds__(256) void k_trsv_dag(const LinProblem* __restrict__
     for (int q = 0; q < cnt && ok; ++q) {
       const int jt = fwd ? q : nt - 1 - q;
       if (threadIdx.x == 0) {
-        s_ok = wait_ge(&flag[fwd ? jt : nt + jt], 1, err, budget_ns);
+        s_ok = wait_ge(&flag[fwd ? jt : nt + jt], solve_id, err, budget_ns);
         __threadfence();
       }
       __syncthreads();
@@ -653,7 +663,7 @@ __global__ __launch_bounds__(256) void k_trsv_dag(const LinProblem* __restrict__
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
-      atomicExch(&flag[fwd ? i : nt + i], 1);
+      atomicExch(&flag[fwd ? i : nt + i], solve_id);
     }
   }
 }
@@ -677,8 +687,7 @@ static int num_sms() {
 }
 
 template <typename T>
-void launch_chol_dag(const LinProblem* probs, const int4* tasks, int ntasks, int* head, int* err,
-                     cudaStream_t s) {
+void launch_chol_dag(const BatchTabs& B, cudaStream_t s) {
   constexpr int TB = sizeof(T) == 8 ? 32 : 64;
   const size_t sm = 2 * sizeof(T) * TB * TileCfg<T, TB>::LDT + 2 * sizeof(T) * TB * (TB + 1) +
                     8 * sizeof(T) * TB;
@@ -687,59 +696,75 @@ void launch_chol_dag(const LinProblem* probs, const int4* tasks, int ntasks, int
     cudaFuncSetAttribute(k_chol_dag<T, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr = true;
   }
-  int grid = std::min(ntasks, 2 * num_sms());
-  k_chol_dag<T, TB><<<grid, 256, sm, s>>>(probs, tasks, ntasks, head, err, 2000000000ull);
+  const int nticket = B.P * B.max_tasks;
+  const int grid = std::min(nticket, 2 * num_sms());
+  k_chol_dag<T, TB><<<grid, 256, sm, s>>>(B.d, B.P, nticket, B.words + 0, B.words + 5,
+                                          2000000000ull);
   ++g_launches;
 }
 
 template <typename T>
-void launch_trsv_dag(const LinProblem* probs, const int2* tickets, int ntk, int* head, int* err,
-                     cudaStream_t s) {
+void launch_trsv_dag(const BatchTabs& B, int solve_id, cudaStream_t s) {
   constexpr int TB = sizeof(T) == 8 ? 32 : 64;
-  int grid = std::min(ntk, 2 * num_sms());
-  k_trsv_dag<T, TB><<<grid, 256, 0, s>>>(probs, tickets, ntk, head, err, 2000000000ull);
+  const int nticket = B.P * 2 * B.max_nt;
+  const int grid = std::min(nticket, 2 * num_sms());
+  k_trsv_dag<T, TB><<<grid, 256, 0, s>>>(B.d, B.P, nticket, solve_id, B.words + solve_id,
+                                          B.words + 5, 2000000000ull);
   ++g_launches;
 }
 
-// r = b - A x with A the full symmetric FP32 matrix, accumulated in FP64. One warp per row.
-__global__ __launch_bounds__(256) void k_residual64(const float* __restrict__ A, int n,
-                                                    const double* __restrict__ b,
-                                                    const double* __restrict__ x,
-                                                    double* __restrict__ r) {
-  const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+// rhs (T) = b or r (FP64), per (problem, 256-element chunk)
+template <typename T>
+__global__ void k_vec_in(const ProbDesc* const* __restrict__ descs, const int2* __restrict__ tab,
+                         int from_r) {
+  const int2 w = tab[blockIdx.x];
+  const ProbDesc& D = *descs[w.x];
+  const int i = w.y * 256 + threadIdx.x;
+  if (i < D.n) ((T*)D.lp.rhs)[i] = (T)(from_r ? D.r[i] : D.b[i]);
+}
+template <typename T>
+void launch_vec_in(const BatchTabs& B, bool from_r, cudaStream_t s) {
+  k_vec_in<T><<<B.n_vec, 256, 0, s>>>(B.d, B.vec, from_r ? 1 : 0);
+  ++g_launches;
+}
+
+// x (FP64) = or += solution (T)
+template <typename T>
+__global__ void k_vec_out(const ProbDesc* const* __restrict__ descs, const int2* __restrict__ tab,
+                          int assign) {
+  const int2 w = tab[blockIdx.x];
+  const ProbDesc& D = *descs[w.x];
+  const int i = w.y * 256 + threadIdx.x;
+  if (i < D.n) {
+    const double v = (double)((const T*)D.lp.x)[i];
+    D.x[i] = assign ? v : D.x[i] + v;
+  }
+}
+template <typename T>
+void launch_vec_out(const BatchTabs& B, bool assign, cudaStream_t s) {
+  k_vec_out<T><<<B.n_vec, 256, 0, s>>>(B.d, B.vec, assign ? 1 : 0);
+  ++g_launches;
+}
+
+// r = b - A x with A the full symmetric FP32 matrix, accumulated in FP64; one warp per row,
+// (problem, 8-row chunk) per CTA.
+__global__ __launch_bounds__(256) void k_residual64(const ProbDesc* const* __restrict__ descs,
+                                                    const int2* __restrict__ tab) {
+  const int2 w = tab[blockIdx.x];
+  const ProbDesc& D = *descs[w.x];
+  const int n = D.n;
+  const int row = w.y * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (row >= n) return;
-  const float* a = A + (size_t)row * n;
+  const float* a = D.Aref + (size_t)row * n;
+  const double* x = D.x;
   double s = 0.0;
   for (int j = lane; j < n; j += 32) s += (double)a[j] * x[j];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) r[row] = b[row] - s;
+  if (lane == 0) D.r[row] = D.b[row] - s;
 }
 
-void launch_residual64(const float* Aref, int n, const double* b, const double* x, double* r,
-                       cudaStream_t s) {
-  k_residual64<<<(n + 7) / 8, 256, 0, s>>>(Aref, n, b, x, r);
-  ++g_launches;
-}
-
-template <typename T>
-__global__ void k_cast_from64(const double* __restrict__ in, T* __restrict__ out, int n) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = (T)in[i];
-}
-template <typename T>
-void launch_cast_from64(const double* in, T* out, int n, cudaStream_t s) {
-  k_cast_from64<T><<<(n + 255) / 256, 256, 0, s>>>(in, out, n);
-  ++g_launches;
-}
-
-template <typename T>
-__global__ void k_axpy_to64(const T* __restrict__ d, double* __restrict__ x, int n, int assign) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) x[i] = assign ? (double)d[i] : x[i] + (double)d[i];
-}
-template <typename T>
-void launch_axpy_to64(const T* d, double* x, int n, bool assign, cudaStream_t s) {
-  k_axpy_to64<T><<<(n + 255) / 256, 256, 0, s>>>(d, x, n, assign ? 1 : 0);
+void launch_residual64(const BatchTabs& B, cudaStream_t s) {
+  k_residual64<<<B.n_res, 256, 0, s>>>(B.d, B.res);
   ++g_launches;
 }
 
@@ -756,17 +781,13 @@ void launch_sym_unpack(const float* A, int n, double* out, cudaStream_t s) {
   ++g_launches;
 }
 
-template void launch_chol_dag<float>(const LinProblem*, const int4*, int, int*, int*,
-                                     cudaStream_t);
-template void launch_chol_dag<double>(const LinProblem*, const int4*, int, int*, int*,
-                                      cudaStream_t);
-template void launch_trsv_dag<float>(const LinProblem*, const int2*, int, int*, int*,
-                                     cudaStream_t);
-template void launch_trsv_dag<double>(const LinProblem*, const int2*, int, int*, int*,
-                                      cudaStream_t);
-template void launch_cast_from64<float>(const double*, float*, int, cudaStream_t);
-template void launch_cast_from64<double>(const double*, double*, int, cudaStream_t);
-template void launch_axpy_to64<float>(const float*, double*, int, bool, cudaStream_t);
-template void launch_axpy_to64<double>(const double*, double*, int, bool, cudaStream_t);
+template void launch_chol_dag<float>(const BatchTabs&, cudaStream_t);
+template void launch_chol_dag<double>(const BatchTabs&, cudaStream_t);
+template void launch_trsv_dag<float>(const BatchTabs&, int, cudaStream_t);
+template void launch_trsv_dag<double>(const BatchTabs&, int, cudaStream_t);
+template void launch_vec_in<float>(const BatchTabs&, bool, cudaStream_t);
+template void launch_vec_in<double>(const BatchTabs&, bool, cudaStream_t);
+template void launch_vec_out<float>(const BatchTabs&, bool, cudaStream_t);
+template void launch_vec_out<double>(const BatchTabs&, bool, cudaStream_t);
 
 }  // namespace ds

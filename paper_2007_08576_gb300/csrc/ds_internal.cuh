@@ -50,27 +50,65 @@ __host__ __device__ constexpr int kSlotPairJ(int k) {
 
 // One dense SPD system for the persistent factorisation / solve kernels (one per problem of a
 // batch). A: n x n lower, factored in place; Dinv: inverses of the nt diagonal tiles (TB x TB);
-// cnt: task counters of the factorisation (nt + 2 nt^2 ints); flags: 2 nt ints of the solve;
-// status: FP64 word receiving 1 + row of a non-positive pivot; rhs / y / x: vectors of the
-// solve (T).
+// cnt: task counters of the factorisation (nt + 2 nt^2 ints); flags: 2 nt ints of the solves
+// (a row is done for solve s when its flag equals s); tasks: the problem's factorisation tasks
+// in topological order; status: FP64 word receiving 1 + row of a non-positive pivot; rhs / y /
+// x: vectors of the solve (T).
 struct LinProblem {
   void* A;
   void* Dinv;
   int n, nt;
   int* cnt;
   int* flags;
+  const int4* tasks;
+  int ntasks;
   double* status;
   void* rhs;
   void* y;
   void* x;
 };
 
+// Everything the per-iteration kernels need about one problem (one handle). Lives in device
+// memory; kernels read sizes that change per frame (M) from it, so captured graphs stay valid.
+struct ProbDesc {
+  int W, H, P, N, n, M, nbp;
+  float fx, fy, cx, cy;
+  float tukey_c, H_mm, w_orb, w_angle, w_rot, inv2sig2;
+  double w_arap0, lam, eps;
+  int write_ref;           // the refinement needs the FP32 system (full symmetric) besides the factor
+  const float4* tp;        // sorted template points (x, y, z, bits(seg << 2 | nearest slot))
+  const float4* tw;        // blend weights per sorted point (slot order)
+  const int4* seg;         // node quadruple of each segment (ascending ids)
+  const int* segbp;        // 10 block-pair ids per segment
+  const int* rank;         // template pixel -> sorted position, -1 if no point
+  const float4* tpts;      // live points (x, y, z, valid)
+  const float4* tnrm;      // live normals
+  const int* midx;
+  const float* mxyz;
+  const uint32_t* mask;
+  const float* what;
+  const int* rowptr;       // CSR of the block pairs by row
+  const int* rowcol;
+  const int* rowbp;
+  const double* g64;       // node positions (FP64)
+  const double* gc;        // node centroid
+  NodeGPU* node;
+  PairNode* pn;
+  float* blk;              // block-sparse data-term blocks (36 floats per pair)
+  float* gdata;            // data-term gradient
+  double* acc;             // ACC_* scalars
+  double* hist;            // DS_MAX_ITERS x 6
+  double* q64;
+  double* t64;
+  float* Aref;             // FP32 system (reference of the refinement, or the factor itself)
+  double* b;
+  double* x;
+  double* r;
+  LinProblem lp;
+};
+
 constexpr int kTile = 256;        // points per CTA of the ICP pass
 constexpr int kOuts = 10 * 36 + 24;  // per-segment outputs: 10 blocks of 6x6, 24 gradient entries
-
-// Kernels enqueued by this host thread (stream launches, including those recorded into a graph
-// under capture); the API layer reads differences of it.
-extern thread_local int64_t g_launches;
 
 // ----------------------------------------------------------------------------- launchers
 // frame.cu
@@ -89,40 +127,51 @@ void launch_ransac(const float* depth0, int W, ds_intrinsics K, const int* midx,
                    double keep_frac, double* scratch, uint32_t* hbits, float* hw, double* score,
                    uint32_t* mask, float* what, uint32_t* kept, int* counts, cudaStream_t s);
 
-// terms.cu
-void launch_node_update(const double* x, int N, double* q64, double* t64, const double* g64,
-                        const double* gc, NodeGPU* node, PairNode* pn, cudaStream_t s);
-void launch_icp(const float4* tp, const float4* tw, const int4* segnodes, const int* segbp,
-                int P, const NodeGPU* node, const float4* tgt_pt, const float4* tgt_nrm,
-                int W, int H, ds_intrinsics K, float c, float* blk, float* gdata, double* acc,
-                cudaStream_t s);
-void launch_orb(const int* midx, const float* mxyz, int M, const int* rank, const float4* tp,
-                const float4* tw, const int4* segnodes, const int* segbp, const NodeGPU* node,
-                const uint32_t* mask, const float* what, float H, float w_orb, float* blk,
-                float* gdata, double* acc, cudaStream_t s);
-// dense ARAP + assembly of A (lower blocks, damped) and b; T = float or double (factor type)
+// Work tables of a batch (device arrays of (problem, index) pairs) and its shared words.
+struct BatchTabs {
+  const ProbDesc* const* d;  // descriptor pointer per problem
+  int P;                     // problems
+  const int2* icp;           // (problem, 256-point tile)
+  int n_icp;
+  const int2* rows;          // (problem, node) of the dense ARAP pass
+  int n_rows;
+  const int2* nodes;         // (problem, 128-node chunk)
+  int n_nodes;
+  const int2* vec;           // (problem, 256-element chunk of the 6N vectors)
+  int n_vec;
+  const int2* res;           // (problem, 8-row chunk of the refinement residual)
+  int n_res;
+  int orb_ctas;              // CTAs per problem of the ORB pass (grid-stride over M)
+  int max_tasks;             // max factorisation tasks over the problems
+  int max_nt;                // max tile rows over the problems
+  int* words;                // [0] factorisation head, [1..4] solve heads, [5] timeout word
+};
+
+// terms.cu (batched over the problems of a BatchTabs)
+void launch_iter_begin(const BatchTabs& B, cudaStream_t s);
+void launch_icp(const BatchTabs& B, cudaStream_t s);
+void launch_orb(const BatchTabs& B, cudaStream_t s);
 template <typename T>
-void launch_arap_assemble(const PairNode* pn, int N, float inv2sig2, const int* rowptr,
-                          const int* rowcol, const int* rowbp, const float* blk,
-                          const float* gdata, double* acc, bool first_iter, double w_arap0,
-                          float w_orb, float w_angle, float w_rot, double lam, double eps,
-                          T* Afac, float* Aref, double* b, cudaStream_t s);
+void launch_arap_assemble(const BatchTabs& B, bool first, bool lin_only, cudaStream_t s);
+void launch_iter_end(const BatchTabs& B, int it, bool step, cudaStream_t s);
 
 // chol.cu
 template <typename T>
 int chol_tile();
 template <typename T>
-void launch_chol_dag(const LinProblem* probs, const int4* tasks, int ntasks, int* head, int* err,
-                     cudaStream_t s);
+void launch_chol_dag(const BatchTabs& B, cudaStream_t s);
 template <typename T>
-void launch_trsv_dag(const LinProblem* probs, const int2* tickets, int ntk, int* head, int* err,
-                     cudaStream_t s);
-void launch_residual64(const float* Aref, int n, const double* b, const double* x, double* r,
-                       cudaStream_t s);
+void launch_trsv_dag(const BatchTabs& B, int solve_id, cudaStream_t s);
+// vector steps of the solve: rhs = (T) b (k = 0) or (T) r (k > 0); x (=|+=) solution
 template <typename T>
-void launch_cast_from64(const double* in, T* out, int n, cudaStream_t s);
+void launch_vec_in(const BatchTabs& B, bool from_r, cudaStream_t s);
 template <typename T>
-void launch_axpy_to64(const T* d, double* x, int n, bool assign, cudaStream_t s);
+void launch_vec_out(const BatchTabs& B, bool assign, cudaStream_t s);
+void launch_residual64(const BatchTabs& B, cudaStream_t s);
 void launch_sym_unpack(const float* A, int n, double* out, cudaStream_t s);
+
+// Kernels enqueued by this host thread (stream launches, including those recorded into a graph
+// under capture); the API layer reads differences of it.
+extern thread_local int64_t g_launches;
 
 }  // namespace ds

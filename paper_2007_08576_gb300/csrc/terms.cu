@@ -58,17 +58,19 @@ __device__ __forceinline__ V mul(V a, float s) { return {a.x * s, a.y * s, a.z *
 
 // ----------------------------------------------------------------------------- node update
 
-// FP64 state step and the FP32 node tables of the next linearisation. x == nullptr: no step.
-// Thread 0 also records the linearisation's costs into hist[it] and clears the accumulators.
-__global__ void k_node_update(const double* __restrict__ x, int N, double* __restrict__ q64,
-                              double* __restrict__ t64, const double* __restrict__ g64,
-                              const double* __restrict__ gc, NodeGPU* __restrict__ node,
-                              PairNode* __restrict__ pn) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+// FP64 state step and the FP32 node tables of the next linearisation, one thread per node.
+// step: apply x (the Gauss-Newton step); it >= 0: the first CTA of each problem records the
+// linearisation's costs into hist[it]; the accumulators are cleared for the next linearisation
+// (it < 0, the start of a solve, also clears w_ARAP and the status word).
+__device__ void node_update(const ProbDesc& D, int i, bool step) {
+  const double* x = D.x;
+  double* q64 = D.q64;
+  double* t64 = D.t64;
+  const double* g64 = D.g64;
+  const double* gc = D.gc;
   double qw = q64[4 * i], qx = q64[4 * i + 1], qy = q64[4 * i + 2], qz = q64[4 * i + 3];
   double tx = t64[3 * i], ty = t64[3 * i + 1], tz = t64[3 * i + 2];
-  if (x) {
+  if (step) {
     double a = x[6 * i], b = x[6 * i + 1], c = x[6 * i + 2];
     double th = sqrt(a * a + b * b + c * c);
     double ew, sf;
@@ -121,7 +123,7 @@ __global__ void k_node_update(const double* __restrict__ x, int N, double* __res
   nd.T = make_float4((float)Tx, (float)Ty, (float)Tz, 0.f);
   nd.w = make_float4((float)(Rgx + 0.5 * Tx), (float)(Rgy + 0.5 * Ty), (float)(Rgz + 0.5 * Tz),
                      0.f);
-  node[i] = nd;
+  D.node[i] = nd;
   PairNode p;
   double cxg = gx - gc[0], cyg = gy - gc[1], czg = gz - gc[2];
   p.q = nd.q;
@@ -130,12 +132,55 @@ __global__ void k_node_update(const double* __restrict__ x, int N, double* __res
   p.R0 = make_float4((float)R[0], (float)R[1], (float)R[2], 0.f);
   p.R1 = make_float4((float)R[3], (float)R[4], (float)R[5], 0.f);
   p.R2 = make_float4((float)R[6], (float)R[7], (float)R[8], 0.f);
-  pn[i] = p;
+  D.pn[i] = p;
 }
 
-void launch_node_update(const double* x, int N, double* q64, double* t64, const double* g64,
-                        const double* gc, NodeGPU* node, PairNode* pn, cudaStream_t s) {
-  k_node_update<<<(N + 127) / 128, 128, 0, s>>>(x, N, q64, t64, g64, gc, node, pn);
+__global__ void k_iter_end(const ProbDesc* const* __restrict__ descs, const int2* __restrict__ tab,
+                           int it, int step) {
+  const int2 w = tab[blockIdx.x];
+  const ProbDesc& D = *descs[w.x];
+  if (w.y == 0 && threadIdx.x == 0) {
+    double* acc = D.acc;
+    if (it >= 0) {
+      double* hrow = D.hist + 6 * it;
+      hrow[0] = acc[ACC_COST_ICP] + acc[ACC_COST_ORB] + acc[ACC_COST_ARAP];
+      hrow[1] = acc[ACC_COST_ICP];
+      hrow[2] = acc[ACC_COST_ORB];
+      hrow[3] = acc[ACC_COST_ARAP];
+      hrow[4] = acc[ACC_NVALID];
+      hrow[5] = acc[ACC_W_ARAP];
+    }
+    const int upto = it < 0 ? ACC_COUNT : ACC_W_ARAP;
+    for (int k = 0; k < upto; ++k) acc[k] = 0.0;
+  }
+  const int i = w.y * 128 + threadIdx.x;
+  if (i < D.N) node_update(D, i, step != 0);
+}
+
+void launch_iter_end(const BatchTabs& B, int it, bool step, cudaStream_t s) {
+  k_iter_end<<<B.n_nodes, 128, 0, s>>>(B.d, B.nodes, it, step ? 1 : 0);
+  ++g_launches;
+}
+
+// Zeroes the data-term blocks / gradient and the factorisation / solve counters of every
+// problem, and the batch's ticket heads (not its timeout word).
+__global__ void k_iter_begin(const ProbDesc* const* __restrict__ descs, int* __restrict__ words) {
+  const ProbDesc& D = *descs[blockIdx.x];
+  const int nth = blockDim.x * gridDim.y;
+  const int t0 = blockIdx.y * blockDim.x + threadIdx.x;
+  float* blk = D.blk;
+  const int nb = 36 * D.nbp;
+  for (int e = t0; e < nb; e += nth) blk[e] = 0.f;
+  for (int e = t0; e < D.n; e += nth) D.gdata[e] = 0.f;
+  const int nt = D.lp.nt;
+  const int nc = nt + 2 * nt * nt;
+  for (int e = t0; e < nc; e += nth) D.lp.cnt[e] = 0;
+  for (int e = t0; e < 2 * nt; e += nth) D.lp.flags[e] = 0;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < 5) words[threadIdx.x] = 0;
+}
+
+void launch_iter_begin(const BatchTabs& B, cudaStream_t s) {
+  k_iter_begin<<<dim3(B.P, 8), 256, 0, s>>>(B.d, B.words);
   ++g_launches;
 }
 
@@ -228,19 +273,30 @@ __device__ __forceinline__ void slot_jac(const float* h, const NodeGPU& nd, floa
 // consecutive points shares the same 4 nodes). Each CTA reduces the sqrt-weighted Jacobians of
 // its tile per segment in shared memory and adds the segment's 10 blocks and gradient into
 // the block table with one atomic per entry.
-__global__ __launch_bounds__(kTile) void k_icp(
-    const float4* __restrict__ tp, const float4* __restrict__ tw,
-    const int4* __restrict__ segnodes, const int* __restrict__ segbp, int P,
-    const NodeGPU* __restrict__ node, const float4* __restrict__ tgt_pt,
-    const float4* __restrict__ tgt_nrm, int W, int H, float fx, float fy, float cx, float cy,
-    float c, float* __restrict__ blk, float* __restrict__ gdata, double* __restrict__ acc) {
+__global__ __launch_bounds__(kTile) void k_icp(const ProbDesc* const* __restrict__ descs,
+                                               const int2* __restrict__ tab) {
+  const int2 wk = tab[blockIdx.x];
+  const ProbDesc& D = *descs[wk.x];
+  const float4* __restrict__ tp = D.tp;
+  const float4* __restrict__ tw = D.tw;
+  const int4* __restrict__ segnodes = D.seg;
+  const int* __restrict__ segbp = D.segbp;
+  const int P = D.P;
+  const NodeGPU* __restrict__ node = D.node;
+  const float4* __restrict__ tgt_pt = D.tpts;
+  const float4* __restrict__ tgt_nrm = D.tnrm;
+  const int W = D.W, H = D.H;
+  const float fx = D.fx, fy = D.fy, cx = D.cx, cy = D.cy, c = D.tukey_c;
+  float* __restrict__ blk = D.blk;
+  float* __restrict__ gdata = D.gdata;
+  double* __restrict__ acc = D.acc;
   __shared__ float sJ[kTile][25];
   __shared__ int sSeg[kTile];
   __shared__ int sStart[kTile + 1];
   __shared__ int sWarpCnt[kTile / 32 + 1];
   __shared__ float sRed[3][kTile / 32];
   const int tid = threadIdx.x;
-  const int base = blockIdx.x * kTile;
+  const int base = wk.y * kTile;
   const int len = min(kTile, P - base);
   const int pidx = base + tid;
   float Jt[24];
@@ -360,27 +416,37 @@ __global__ __launch_bounds__(kTile) void k_icp(
   }
 }
 
-void launch_icp(const float4* tp, const float4* tw, const int4* segnodes, const int* segbp,
-                int P, const NodeGPU* node, const float4* tgt_pt, const float4* tgt_nrm,
-                int W, int H, ds_intrinsics K, float c, float* blk, float* gdata, double* acc,
-                cudaStream_t s) {
-  if (P <= 0) return;
-  k_icp<<<(P + kTile - 1) / kTile, kTile, 0, s>>>(tp, tw, segnodes, segbp, P, node, tgt_pt,
-                                                  tgt_nrm, W, H, K.fx, K.fy, K.cx, K.cy, c, blk,
-                                                  gdata, acc);
+void launch_icp(const BatchTabs& B, cudaStream_t s) {
+  if (B.n_icp <= 0) return;
+  k_icp<<<B.n_icp, kTile, 0, s>>>(B.d, B.icp);
   ++g_launches;
 }
 
 // ----------------------------------------------------------------------------- ORB
 
-__global__ __launch_bounds__(128) void k_orb(
-    const int* __restrict__ midx, const float* __restrict__ mxyz, int M,
-    const int* __restrict__ rank, const float4* __restrict__ tp, const float4* __restrict__ tw,
-    const int4* __restrict__ segnodes, const int* __restrict__ segbp,
-    const NodeGPU* __restrict__ node, const uint32_t* __restrict__ mask,
-    const float* __restrict__ what, float H, float w_orb, float* __restrict__ blk,
-    float* __restrict__ gdata, double* __restrict__ acc) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ __launch_bounds__(128) void k_orb(const ProbDesc* const* __restrict__ descs,
+                                             int ctas_per_problem) {
+  const ProbDesc& D = *descs[blockIdx.x / ctas_per_problem];
+  const int* __restrict__ midx = D.midx;
+  const float* __restrict__ mxyz = D.mxyz;
+  const int M = D.M;
+  const int* __restrict__ rank = D.rank;
+  const float4* __restrict__ tp = D.tp;
+  const float4* __restrict__ tw = D.tw;
+  const int4* __restrict__ segnodes = D.seg;
+  const int* __restrict__ segbp = D.segbp;
+  const NodeGPU* __restrict__ node = D.node;
+  const uint32_t* __restrict__ mask = D.mask;
+  const float* __restrict__ what = D.what;
+  const float H = D.H_mm, w_orb = D.w_orb;
+  float* __restrict__ blk = D.blk;
+  float* __restrict__ gdata = D.gdata;
+  double* __restrict__ acc = D.acc;
+  const int stride = ctas_per_problem * blockDim.x;
+  const int first = (blockIdx.x % ctas_per_problem) * blockDim.x + threadIdx.x;
+  const int rounds = (M + stride - 1) / stride;
+  for (int rd = 0; rd < rounds; ++rd) {
+  const int k = first + rd * stride;
   float cost = 0.f, wsum = 0.f;
   if (k < M) {
     int sp = rank[midx[k]];
@@ -439,15 +505,11 @@ __global__ __launch_bounds__(128) void k_orb(
     atomicAdd(&acc[ACC_COST_ORB], (double)cost);
     atomicAdd(&acc[ACC_WSUM_ORB], (double)wsum);
   }
+  }
 }
 
-void launch_orb(const int* midx, const float* mxyz, int M, const int* rank, const float4* tp,
-                const float4* tw, const int4* segnodes, const int* segbp, const NodeGPU* node,
-                const uint32_t* mask, const float* what, float H, float w_orb, float* blk,
-                float* gdata, double* acc, cudaStream_t s) {
-  if (M <= 0) return;
-  k_orb<<<(M + 127) / 128, 128, 0, s>>>(midx, mxyz, M, rank, tp, tw, segnodes, segbp, node,
-                                        mask, what, H, w_orb, blk, gdata, acc);
+void launch_orb(const BatchTabs& B, cudaStream_t s) {
+  k_orb<<<B.P * B.orb_ctas, 128, 0, s>>>(B.d, B.orb_ctas);
   ++g_launches;
 }
 
@@ -468,15 +530,29 @@ __device__ __forceinline__ void store_out(T* p, float v) {
 //   grad(i1)   += [-W_a u x v - s W_r r_v, -2 W_l (l - l0) v + W_a (P u - P u') / l]
 // (u' = unit(R_i2 (g_i1 - g_i2))). Only the lower blocks (i2 <= i1) are written.
 template <typename T>
-__global__ __launch_bounds__(256) void k_arap_assemble(
-    const PairNode* __restrict__ pn, int N, float inv2sig2, const int* __restrict__ rowptr,
-    const int* __restrict__ rowcol, const int* __restrict__ rowbp, const float* __restrict__ blk,
-    const float* __restrict__ gdata, double* __restrict__ acc, int first_iter, double w_arap0,
-    float w_orb, float w_angle, float w_rot, double lam, double eps, T* __restrict__ Afac,
-    float* __restrict__ Aref, double* __restrict__ b) {
+__global__ __launch_bounds__(256) void k_arap_assemble(const ProbDesc* const* __restrict__ descs,
+                                                       const int2* __restrict__ tab,
+                                                       int first_iter, int lin_only) {
+  const int2 wk = tab[blockIdx.x];
+  const ProbDesc& D = *descs[wk.x];
+  const PairNode* __restrict__ pn = D.pn;
+  const int N = D.N;
+  const float inv2sig2 = D.inv2sig2;
+  const int* __restrict__ rowptr = D.rowptr;
+  const int* __restrict__ rowcol = D.rowcol;
+  const int* __restrict__ rowbp = D.rowbp;
+  const float* __restrict__ blk = D.blk;
+  const float* __restrict__ gdata = D.gdata;
+  double* __restrict__ acc = D.acc;
+  const double w_arap0 = D.w_arap0, eps = D.eps;
+  const double lam = lin_only ? 0.0 : D.lam;
+  const float w_orb = D.w_orb, w_angle = D.w_angle, w_rot = D.w_rot;
+  T* __restrict__ Afac = lin_only ? (T*)D.Aref : (T*)D.lp.A;
+  float* __restrict__ Aref = (!lin_only && D.write_ref) ? D.Aref : nullptr;
+  double* __restrict__ b = D.b;
   extern __shared__ int smap[];
   __shared__ float sRed[28][8];
-  const int i1 = blockIdx.x;
+  const int i1 = wk.y;
   const int n = 6 * N;
   for (int i = threadIdx.x; i < N; i += blockDim.x) smap[i] = -1;
   __syncthreads();
@@ -685,25 +761,14 @@ __global__ __launch_bounds__(256) void k_arap_assemble(
 }
 
 template <typename T>
-void launch_arap_assemble(const PairNode* pn, int N, float inv2sig2, const int* rowptr,
-                          const int* rowcol, const int* rowbp, const float* blk,
-                          const float* gdata, double* acc, bool first_iter, double w_arap0,
-                          float w_orb, float w_angle, float w_rot, double lam, double eps,
-                          T* Afac, float* Aref, double* b, cudaStream_t s) {
-  k_arap_assemble<T><<<N, 256, sizeof(int) * N, s>>>(pn, N, inv2sig2, rowptr, rowcol, rowbp,
-                                                     blk, gdata, acc, first_iter ? 1 : 0,
-                                                     w_arap0, w_orb, w_angle, w_rot, lam, eps,
-                                                     Afac, Aref, b);
+void launch_arap_assemble(const BatchTabs& B, bool first, bool lin_only, cudaStream_t s) {
+  // dynamic shared memory: the node -> data block map of the row (N <= 2048 by the API)
+  const int sm = sizeof(int) * 2048;
+  k_arap_assemble<T><<<B.n_rows, 256, sm, s>>>(B.d, B.rows, first ? 1 : 0, lin_only ? 1 : 0);
   ++g_launches;
 }
 
-template void launch_arap_assemble<float>(const PairNode*, int, float, const int*, const int*,
-                                          const int*, const float*, const float*, double*, bool,
-                                          double, float, float, float, double, double, float*,
-                                          float*, double*, cudaStream_t);
-template void launch_arap_assemble<double>(const PairNode*, int, float, const int*, const int*,
-                                           const int*, const float*, const float*, double*, bool,
-                                           double, float, float, float, double, double, double*,
-                                           float*, double*, cudaStream_t);
+template void launch_arap_assemble<float>(const BatchTabs&, bool, bool, cudaStream_t);
+template void launch_arap_assemble<double>(const BatchTabs&, bool, bool, cudaStream_t);
 
 }  // namespace ds

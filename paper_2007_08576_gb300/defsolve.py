@@ -24,7 +24,8 @@ DS_MAX_HYP = 64
 # every exported symbol of include/defsolve.h
 EXPORTS = [
     "ds_default_params", "ds_create_template", "ds_set_control_points", "ds_submit_frame",
-    "ds_solve", "ds_solve_batch", "ds_get_deformation", "ds_get_deformation64",
+    "ds_solve", "ds_solve_batch", "ds_batch_create", "ds_batch_solve", "ds_batch_status",
+    "ds_batch_destroy", "ds_get_deformation", "ds_get_deformation64",
     "ds_set_deformation", "ds_get_inlier_mask", "ds_get_ransac", "ds_get_cost",
     "ds_get_blend_table", "ds_get_frame_points", "ds_linearize", "ds_set_tracing",
     "ds_get_phase_times", "ds_get_counters", "ds_destroy", "ds_status_str", "ds_version",
@@ -84,6 +85,10 @@ def lib(path: str | None = None):
         "ds_submit_frame": (i32, [vp, vp, vp, vp, i32, vp]),
         "ds_solve": (i32, [vp, i32, ctypes.POINTER(DsSolveStats)]),
         "ds_solve_batch": (i32, [ctypes.POINTER(vp), i32, i32]),
+        "ds_batch_create": (i32, [ctypes.POINTER(vp), i32, vp, ctypes.POINTER(vp)]),
+        "ds_batch_solve": (i32, [vp, i32]),
+        "ds_batch_status": (i32, [vp]),
+        "ds_batch_destroy": (i32, [vp]),
         "ds_get_deformation": (i32, [vp, vp, vp, vp]),
         "ds_get_deformation64": (i32, [vp, vp, vp]),
         "ds_set_deformation": (i32, [vp, vp, vp]),
@@ -176,9 +181,31 @@ def ds_solve(h, iters, stats: bool = False):
 
 
 def ds_solve_batch(handles, iters):
-    arr = (ctypes.c_void_p * len(handles))(*[hh.value if isinstance(hh, ctypes.c_void_p) else hh
-                                             for hh in handles])
-    _check("ds_solve_batch", lib().ds_solve_batch(arr, len(handles), int(iters)))
+    _check("ds_solve_batch", lib().ds_solve_batch(_handle_array(handles), len(handles), int(iters)))
+
+
+def _handle_array(handles):
+    return (ctypes.c_void_p * len(handles))(*[hh.value if isinstance(hh, ctypes.c_void_p) else hh
+                                              for hh in handles])
+
+
+def ds_batch_create(handles, stream=None):
+    b = ctypes.c_void_p()
+    _check("ds_batch_create", lib().ds_batch_create(_handle_array(handles), len(handles), stream,
+                                                    ctypes.byref(b)))
+    return b
+
+
+def ds_batch_solve(b, iters):
+    _check("ds_batch_solve", lib().ds_batch_solve(b, int(iters)))
+
+
+def ds_batch_status(b):
+    _check("ds_batch_status", lib().ds_batch_status(b))
+
+
+def ds_batch_destroy(b):
+    _check("ds_batch_destroy", lib().ds_batch_destroy(b))
 
 
 def ds_get_deformation(h, q_N4=None, t_N3=None, pos_N3=None):
@@ -244,7 +271,8 @@ def ds_get_phase_times(h):
     return ms
 
 
-def ds_get_counters(h) -> int:
+def ds_get_counters(h=None) -> int:
+    """Kernels launched by the handle so far (h None: by the whole library)."""
     k = ctypes.c_int64()
     _check("ds_get_counters", lib().ds_get_counters(h, ctypes.byref(k)))
     return k.value

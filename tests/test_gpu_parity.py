@@ -298,3 +298,73 @@ def test_resume_from_saved_state(d, tiny):
     assert np.abs(ta - tb).max() <= 1e-4
     s.close()
     s2.close()
+
+
+# ----------------------------------------------------------------------------- batches
+
+
+def test_batch_of_uneven_problems_matches_oracle(d, tiny, mid):
+    """One batch over problems of different template sizes, node counts and match counts: every
+    problem's result equals its own oracle solve."""
+    from synth.scene import Config
+    cfg3 = Config("seq_120x90_n40", 120, 90, 40, 300, 8, 0.4, 0.5, 0.1, 8.0, 1.0, 0.3, 0.5, 1)
+    scenes = [tiny, mid, scene(cfg3, 99), tiny]
+    p = d.default_params(precision=2)
+    solvers = []
+    for sc in scenes:
+        s = d.Solver(sc.template_depth, sc.K, sc.nodes, p)
+        fr = sc.frames[0]
+        s.submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+        solvers.append(s)
+    b = d.ds_batch_create([s.h for s in solvers])
+    d.ds_batch_solve(b, 10)
+    d.ds_batch_status(b)
+    for s, sc in zip(solvers, scenes):
+        _, t = s.deformation64()
+        fr = sc.frames[0]
+        tpl, res = _oracle(sc, fr, oracle_params(p))
+        assert np.abs(tpl.g + t - res.pos).max() <= POS_TOL_MM
+    # a second solve of the same batch (graph replay) on new frames continues from the warm start
+    for s, sc in zip(solvers, scenes):
+        fr = sc.frames[0]
+        s.submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+    d.ds_batch_solve(b, 3)
+    d.ds_batch_status(b)
+    d.ds_batch_destroy(b)
+    for s in solvers:
+        s.close()
+
+
+def test_batch_result_equals_alone(d, tiny, mid):
+    """Each problem's result is the same alone and inside a batch (within the parity
+    tolerance; the reduction order of the data-term atomics may differ)."""
+    p = d.default_params(precision=2)
+    alone = []
+    for sc in (tiny, mid):
+        s, st, q, t = gpu_frame(d, sc, sc.frames[0], p)
+        alone.append(t)
+        s.close()
+    solvers = []
+    for sc in (mid, tiny, mid):
+        s = d.Solver(sc.template_depth, sc.K, sc.nodes, p)
+        fr = sc.frames[0]
+        s.submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+        solvers.append(s)
+    d.ds_solve_batch([s.h for s in solvers], 10)
+    outs = [s.deformation64()[1] for s in solvers]
+    assert np.abs(outs[0] - alone[1]).max() <= 1e-4
+    assert np.abs(outs[1] - alone[0]).max() <= 1e-4
+    assert np.abs(outs[2] - alone[1]).max() <= 1e-4
+    for s in solvers:
+        s.close()
+
+
+def test_batch_rejects_mixed_precision(d, tiny):
+    sc = tiny
+    a = d.Solver(sc.template_depth, sc.K, sc.nodes, d.default_params(precision=0))
+    b = d.Solver(sc.template_depth, sc.K, sc.nodes, d.default_params(precision=1))
+    with pytest.raises(d.DsError) as e:
+        d.ds_batch_create([a.h, b.h])
+    assert e.value.status == d.DS_ERR_ARG
+    a.close()
+    b.close()
