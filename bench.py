@@ -1,18 +1,22 @@
 #!/usr/bin/env python3
 """Benchmark of the per-frame deformation solve on GB300.
 
-A step is one frame of the 320x240 / 256-control-point / 2000-match sequence workload: frame
-preparation, 1-point RANSAC preselection and 10 damped Gauss-Newton iterations (ICP + ORB +
-dense ARAP, assembly, Cholesky, solves, update), warm-started from the previous frame.
+Workload: concurrent streams of the 320x240 / 256-control-point / 2000-match sequence. A frame is
+frame preparation, 1-point RANSAC preselection and 10 damped Gauss-Newton iterations (ICP + ORB +
+dense ARAP, assembly, Cholesky, solves, update), warm-started from the stream's previous frame.
+A step is one frame of every one of S streams (default 32), solved as one batch in mixed
+precision (FP32 J^T J and factorisation, FP64 refinement residuals).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32|fp32_refine]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32_refine|fp32|fp64]
   python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
 
 Prints one JSON line (rank 0). `value` is frames/s with inputs resident in device memory,
 timed with CUDA events on the library's stream, L2 flushed before every step (outside the
-events). `e2e` is the same metric through the C ABI with pinned host buffers: host->device
-copy of the frame, the solve and the device->host read of the deformation, wall clock.
-Multi-GPU runs are independent replicas (one stream per rank, no collective on the data path).
+events). Next to it: the plain single-stream FP32 solve (the comparison the metric names), a
+served run with Poisson arrivals (continuous batching, p50/p99 latency), `e2e` (the same metric
+through the C ABI with pinned host buffers: host->device copies of the frames, the solve and the
+device->host read of the deformations, wall clock), the factorisation's roofline and clocks.
+Multi-GPU runs are independent replicas (one set of streams per rank, no collective).
 """
 from __future__ import annotations
 
@@ -34,6 +38,7 @@ ITERS = 10
 METRIC = "frames/s and p50/p99 frame latency vs plain GPU solve, at ≤1e-3 mm error"
 PREC = {"fp64": 0, "fp32": 1, "fp32_refine": 2}
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate per GPU (nominal)
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
 
 def _dist():
@@ -134,6 +139,12 @@ def measure_dgemm_tflops(torch, dev):
     return 2.0 * n ** 3 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12
 
 
+def _stats_ms(xs):
+    a = np.asarray(xs, dtype=np.float64)
+    return {"p50": round(float(np.percentile(a, 50)), 4), "p99": round(float(np.percentile(a, 99)), 4),
+            "mean": round(float(a.mean()), 4)}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -146,37 +157,51 @@ def run_gpu(args):
     from paper_2007_08576_gb300 import build
     build.build()
     from paper_2007_08576_gb300 import defsolve as d
+    from paper_2007_08576_gb300.serve import FrameIn, GpuEngine, Server, StreamSpec, poisson_schedule
 
-    K, W = args.steps, args.warmup
-    n_frames = max(2, min(K + W, args.max_frames))
-    sc = gen_frames(n_frames, 1000 + rank)
-    prm = d.default_params(precision=PREC[args.precision])
-    stream = torch.cuda.Stream(device=dev)
-    h = d.ds_create_template(sc.template_depth, sc.W, sc.H, sc.K, prm, stream.cuda_stream)
-    d.ds_set_control_points(h, sc.nodes)
-    N, M = len(sc.nodes), len(sc.frames[0].match_idx)
+    K, W, S = args.steps, args.warmup, args.streams
+    n_scenes = min(args.scenes, S)
+    F = args.frames
+    from synth import CONFIGS, make_scene
+    scenes = [make_scene(CONFIGS[WORKLOAD], 1000 + 100 * rank + k, n_frames=F) for k in range(n_scenes)]
+    N = len(scenes[0].nodes)
+    M = len(scenes[0].frames[0].match_idx)
     n = 6 * N
-    # device-resident inputs of every frame
-    dev_frames = [(torch.from_numpy(f.depth).to(dev), torch.from_numpy(f.match_idx).to(dev),
-                   torch.from_numpy(np.ascontiguousarray(f.match_xyz)).to(dev),
-                   torch.from_numpy(f.hyp).to(dev)) for f in sc.frames]
+    prec = PREC[args.precision]
+    stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
-    torch.cuda.synchronize()
+
+    def dev_frames(sc):
+        return [(torch.from_numpy(f.depth).to(dev), torch.from_numpy(f.match_idx).to(dev),
+                 torch.from_numpy(np.ascontiguousarray(f.match_xyz)).to(dev),
+                 torch.from_numpy(f.hyp).to(dev)) for f in sc.frames]
+
+    dframes = [dev_frames(sc) for sc in scenes]
+
+    # ---------------------------------------------------------------- batched mixed precision
+    prm = d.default_params(precision=prec)
+    handles = []
+    for j in range(S):
+        sc = scenes[j % n_scenes]
+        h = d.ds_create_template(sc.template_depth, sc.W, sc.H, sc.K, prm, stream.cuda_stream)
+        d.ds_set_control_points(h, sc.nodes)
+        handles.append(h)
+    batch = d.ds_batch_create(handles, stream.cuda_stream)
+    d.ds_batch_set_tracing(batch, True)
 
     def step(i):
-        dep, mi, mx, hy = dev_frames[i % len(dev_frames)]
-        d.ds_submit_frame(h, dep, mi, mx, M, hy)
-        d.ds_solve(h, ITERS, False)
+        for j, h in enumerate(handles):
+            dep, mi, mx, hy = dframes[j % n_scenes][i % F]
+            d.ds_submit_frame(h, dep, mi, mx, M, hy)
+        d.ds_batch_solve(batch, ITERS)
 
-    d.ds_set_tracing(h, True)
     for i in range(W):
         step(i)
     torch.cuda.synchronize()
-    # timed region: per-step CUDA events on the library's stream, L2 flushed outside them
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    k0 = d.ds_get_counters(h)
+    k0 = d.ds_get_counters(None)
     step_ms, phase = [], np.zeros(4)
     with ClockSampler(local) as clk:
         for i in range(K):
@@ -189,92 +214,149 @@ def run_gpu(args):
             e1.record(stream)
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
-            phase += d.ds_get_phase_times(h)
+            phase += d.ds_batch_phase_times(batch)
+    d.ds_batch_status(batch)
     torch.cuda.synchronize()
-    launches = d.ds_get_counters(h) - k0
+    launches = d.ds_get_counters(None) - k0
     total_s = sum(step_ms) * 1e-3
     if world > 1:
         t = torch.tensor([total_s], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_s = float(t.item())
-    value = world * K / total_s
-    lat = np.array(step_ms)
+    value = world * S * K / total_s
 
-    # end to end through the C ABI with pinned host buffers
-    pin = []
-    for f in sc.frames:
-        arrs = []
-        for a in (f.depth, f.match_idx, np.ascontiguousarray(f.match_xyz), f.hyp):
-            t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-            arrs.append(t.numpy())
-        pin.append(arrs)
-    out_q = torch.empty((N, 4), dtype=torch.float32).pin_memory().numpy()
-    out_t = torch.empty((N, 3), dtype=torch.float32).pin_memory().numpy()
-    out_p = torch.empty((N, 3), dtype=torch.float32).pin_memory().numpy()
-    d.ds_set_tracing(h, False)
+    # end to end through the C ABI: pinned host frames in, deformations out, every step
+    pin = [[[torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+             for a in (f.depth, f.match_idx, f.match_xyz, f.hyp)] for f in sc.frames] for sc in scenes]
+    outs = [[torch.empty(shape, dtype=torch.float32).pin_memory().numpy()
+             for shape in ((N, 4), (N, 3), (N, 3))] for _ in range(S)]
+    d.ds_batch_set_tracing(batch, False)
     e2e_s = []
     for i in range(W + K):
         with torch.cuda.stream(stream):
             flush.fill_(float(i))
         torch.cuda.synchronize()
-        dep, mi, mx, hy = pin[i % len(pin)]
         t0 = time.perf_counter()
-        d.ds_submit_frame(h, dep, mi, mx, M, hy)
-        d.ds_solve(h, ITERS, False)
-        d.ds_get_deformation(h, out_q, out_t, out_p)
-        t1 = time.perf_counter()
+        for j, h in enumerate(handles):
+            dep, mi, mx, hy = pin[j % n_scenes][i % F]
+            d.ds_submit_frame(h, dep, mi, mx, M, hy)
+        d.ds_batch_solve(batch, ITERS)
+        for j, h in enumerate(handles):
+            d.ds_get_deformation(h, *outs[j])
         if i >= W:
-            e2e_s.append(t1 - t0)
+            e2e_s.append(time.perf_counter() - t0)
     e2e_tot = sum(e2e_s)
     if world > 1:
         t = torch.tensor([e2e_tot], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_tot = float(t.item())
-    h2d = sc.frames[0].depth.nbytes + sc.frames[0].match_idx.nbytes + \
-        np.ascontiguousarray(sc.frames[0].match_xyz).nbytes + sc.frames[0].hyp.nbytes
-    d2h = out_q.nbytes + out_t.nbytes + out_p.nbytes
+    f0 = scenes[0].frames[0]
+    h2d = S * (f0.depth.nbytes + f0.match_idx.nbytes + np.ascontiguousarray(f0.match_xyz).nbytes +
+               f0.hyp.nbytes)
+    d2h = S * sum(o.nbytes for o in outs[0])
+    d.ds_batch_destroy(batch)
+    for h in handles:
+        d.ds_destroy(h)
 
-    # roofline of the dominant kernel: the Cholesky factorisation (FP64: DFMA-bound)
-    flops_per_factor = n ** 3 / 3.0
-    factor_ms = phase[1] / K                     # per frame (ITERS factorisations)
-    achieved = ITERS * flops_per_factor / (factor_ms * 1e-3) / 1e12
-    if args.precision == "fp64":
-        peak, unit, bound = FP64_NOMINAL_TFLOPS, "TFLOP/s", "alu"
+    # ---------------------------------------------------------------- plain single-stream FP32
+    pprm = d.default_params(precision=PREC["fp32"])
+    hp = d.ds_create_template(scenes[0].template_depth, scenes[0].W, scenes[0].H, scenes[0].K,
+                              pprm, stream.cuda_stream)
+    d.ds_set_control_points(hp, scenes[0].nodes)
+    plain_ms = []
+    for i in range(W + K):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(i))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dep, mi, mx, hy = dframes[0][i % F]
+        d.ds_submit_frame(hp, dep, mi, mx, M, hy)
+        d.ds_solve(hp, ITERS, False)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= W:
+            plain_ms.append(e0.elapsed_time(e1))
+    d.ds_destroy(hp)
+    plain_fps = 1e3 * len(plain_ms) / sum(plain_ms)
+
+    # ---------------------------------------------------------------- served, Poisson arrivals
+    served = None
+    if rank == 0 and args.served_frames > 0:
+        rng = np.random.default_rng(7)
+        rates = rng.uniform(15.0, 60.0, S)
+        srv = Server(GpuEngine(d.default_params(precision=prec)), budget_bytes=int(0.6 * torch.cuda.mem_get_info()[0]))
+        for j in range(S):
+            sc = scenes[j % n_scenes]
+            srv.open_stream(j, StreamSpec(sc.template_depth, sc.K, sc.nodes, max_matches=M))
+        sched = poisson_schedule(rng, rates, args.served_frames)
+        cnt = [0] * S
+        # warm the graph caches of the steady-state compositions with a few rounds
+        t_start = time.perf_counter()
+        for t_arr, s_id in sched:
+            now = time.perf_counter() - t_start
+            while now < t_arr:
+                srv.poll()
+                now = time.perf_counter() - t_start
+            f = scenes[s_id % n_scenes].frames[cnt[s_id] % F]
+            cnt[s_id] += 1
+            srv.submit(s_id, FrameIn(f.depth, f.match_idx, f.match_xyz, f.hyp),
+                       t_arrival=t_start + t_arr)
+            srv.poll()
+        srv.drain()
+        st = srv.stats()
+        served = {"streams": S, "rates_hz": [round(float(r), 1) for r in rates[:4]] + ["..."],
+                  "offered_frames_per_s": round(float(rates.sum()), 1),
+                  "frames": st["frames"], "frames_per_s": round(st["frames_per_s"], 2),
+                  "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
+                  "mean_batch": round(st["mean_batch"], 2), "batches": st["batches"]}
+        for j in range(S):
+            srv.close_stream(j)
+
+    # ---------------------------------------------------------------- roofline of the factorisation
+    flops_per_step = S * ITERS * n ** 3 / 3.0
+    factor_ms = phase[1] / K
+    achieved = flops_per_step / (factor_ms * 1e-3) / 1e12
+    if prec == 0:
+        peak, peak_src = FP64_NOMINAL_TFLOPS, "nominal GB300 FP64 rate"
     else:
-        peak, unit, bound = 72.0, "TFLOP/s", "alu"   # FP32 SIMT nominal (152 SM x 128 FMA x 2 x 1.85 GHz)
-    dgemm = measure_dgemm_tflops(torch, dev) if args.precision == "fp64" else None
+        peak, peak_src = FP32_SIMT_TFLOPS, "152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz"
+    dgemm = measure_dgemm_tflops(torch, dev) if prec == 0 else None
 
     result = None
     if rank == 0:
-        cpu = cpu_baseline(sc) if world == 1 and not args.no_cpu else None
+        cpu = cpu_baseline(scenes[0]) if world == 1 and not args.no_cpu else None
         result = {
             "metric": METRIC, "value": round(value, 3), "unit": "frames/s", "n_gpus": world,
             "steps": K, "warmup": W, "ms_per_step": round(float(total_s * 1e3 / K), 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp64": "f32 residuals/J^T J, f64 Cholesky+refine",
-                      "fp32": "f32", "fp32_refine": "f32 Cholesky, f64 refine"}[args.precision],
+                      "fp32": "f32", "fp32_refine": "f32 J^T J + Cholesky, f64 refine residuals"}[args.precision],
             "data": "synthetic (seeded heightfield + deformation + camera motion, ray-cast depth)",
             "config": {"workload": WORKLOAD, "template": "320x240", "control_points": N,
                        "matches": M, "gn_iters": ITERS, "precision": args.precision,
-                       "frames_cycled": len(sc.frames), "l2": "flushed (256 MB write) before each step",
-                       "parallelism": f"replicas x{world}"},
-            "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 4),
-                           "p99": round(float(np.percentile(lat, 99)), 4),
-                           "mean": round(float(lat.mean()), 4)},
-            "phase_ms_per_frame": {"linearize": round(phase[0] / K, 4), "factor": round(phase[1] / K, 4),
-                                   "solve_refine": round(phase[2] / K, 4), "update": round(phase[3] / K, 4)},
-            "e2e": {"value": round(world * K / e2e_tot, 3), "unit": "frames/s",
+                       "streams_per_batch": S, "distinct_scenes": n_scenes, "frames_per_scene": F,
+                       "step": f"one frame of each of {S} streams, one batched solve",
+                       "l2": "flushed (256 MB write) before each step", "parallelism": f"replicas x{world}"},
+            "latency_ms": _stats_ms(step_ms),
+            "plain_gpu_single_stream": {"precision": "fp32", "frames_per_s": round(plain_fps, 3),
+                                        "latency_ms": _stats_ms(plain_ms)},
+            "speedup_vs_plain": round(value / (world * plain_fps), 2),
+            "served": served,
+            "phase_ms_per_step": {"linearize": round(phase[0] / K, 4), "factor": round(phase[1] / K, 4),
+                                  "solve_refine": round(phase[2] / K, 4), "update": round(phase[3] / K, 4)},
+            "e2e": {"value": round(world * S * K / e2e_tot, 3), "unit": "frames/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
-            "roofline": {"bound": bound, "kernel": "Cholesky factorisation (panel + trailing update)",
-                         "achieved": round(achieved, 4), "peak": peak, "unit": unit,
+            "roofline": {"bound": "alu", "kernel": "k_chol_dag (persistent tile Cholesky, all problems)",
+                         "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
                          "frac": round(achieved / peak, 4), "traffic": None,
-                         "peak_source": "nominal GB300 FP64 rate" if args.precision == "fp64" else "nominal FP32 SIMT rate",
+                         "peak_source": peak_src,
+                         "algorithmic": "n^3/3 flop per factorisation, 10 per frame",
                          "dgemm_measured_tflops": round(dgemm, 4) if dgemm else None},
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
         }
-    d.ds_destroy(h)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -340,11 +422,14 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=list(PREC))
-    ap.add_argument("--max-frames", type=int, default=12, dest="max_frames")
+    ap.add_argument("--precision", default="fp32_refine", choices=list(PREC))
+    ap.add_argument("--streams", type=int, default=32, help="concurrent streams per batch")
+    ap.add_argument("--scenes", type=int, default=8, help="distinct seeded scenes behind them")
+    ap.add_argument("--frames", type=int, default=4, help="frames per scene (cycled)")
+    ap.add_argument("--served-frames", type=int, default=2000, dest="served_frames")
     ap.add_argument("--no-cpu", action="store_true", dest="no_cpu")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":

@@ -157,6 +157,10 @@ int ds_batch_create(const ds_handle* hs, int32_t n, void* cuda_stream, ds_batch*
 int ds_batch_solve(ds_batch b, int32_t iters);
 int ds_batch_status(ds_batch b);
 int ds_batch_destroy(ds_batch b);
+/* Phase tracing of a batch, as ds_set_tracing / ds_get_phase_times for a handle (summed over
+ * the last ds_batch_solve's iterations; the phases cover all problems of the batch). */
+int ds_batch_set_tracing(ds_batch b, int32_t on);
+int ds_batch_phase_times(ds_batch b, double* ms4);
 
 /* Convenience: a temporary batch over n handles, solved and synchronised. */
 int ds_solve_batch(ds_handle* hs, int32_t n, int32_t iters);

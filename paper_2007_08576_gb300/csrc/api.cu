@@ -1291,12 +1291,7 @@ int ds_set_tracing(ds_handle h, int32_t on) {
   return DS_OK;
 }
 
-int ds_get_phase_times(ds_handle h, double* ms4) {
-  if (!h || !ms4) return DS_ERR_ARG;
-  if (!h->tracing || !h->self || h->self->last_iters == 0) return DS_ERR_STATE;
-  int rc = sync_status(h);
-  if (rc && rc != DS_ERR_NOT_SPD) return rc;
-  ds_batch_s* b = h->self;
+static int batch_phase_times(ds_batch_s* b, double* ms4) {
   for (int k = 0; k < 4; ++k) ms4[k] = 0.0;
   const int it_n = b->last_iters;
   for (int it = 0; it < it_n; ++it) {
@@ -1317,6 +1312,40 @@ int ds_get_phase_times(ds_handle h, double* ms4) {
     ms4[3] += d;
   }
   return DS_OK;
+}
+
+int ds_get_phase_times(ds_handle h, double* ms4) {
+  if (!h || !ms4) return DS_ERR_ARG;
+  if (!h->tracing || !h->self || h->self->last_iters == 0) return DS_ERR_STATE;
+  int rc = sync_status(h);
+  if (rc && rc != DS_ERR_NOT_SPD) return rc;
+  return batch_phase_times(h->self, ms4);
+}
+
+int ds_batch_set_tracing(ds_batch b, int32_t on) {
+  if (!b) return DS_ERR_ARG;
+  const bool want = on != 0;
+  if (want && !b->ev_made) {
+    for (int i = 0; i < DS_MAX_ITERS; ++i)
+      for (int k = 0; k < 5; ++k)
+        if (cudaEventCreate(&b->ev[i][k]) != cudaSuccess) return DS_ERR_CUDA;
+    b->ev_made = true;
+  }
+  if (want != b->tracing && b->gexec) {
+    cudaStreamSynchronize(b->stream);
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    b->g_iters = -1;
+  }
+  b->tracing = want;
+  return DS_OK;
+}
+
+int ds_batch_phase_times(ds_batch b, double* ms4) {
+  if (!b || !ms4) return DS_ERR_ARG;
+  if (!b->tracing || b->last_iters == 0) return DS_ERR_STATE;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return DS_ERR_CUDA;
+  return batch_phase_times(b, ms4);
 }
 
 int ds_get_counters(ds_handle h, int64_t* kernels_launched) {

@@ -1,0 +1,280 @@
+"""Continuous-batching server for many concurrent deformation streams on one GPU.
+
+Each stream (one tissue surface seen by one camera) keeps its template, control points, blend
+tables, normal-equation buffers and warm-start deformation resident in device memory. Frames
+arrive asynchronously; every scheduler round (``poll``)
+
+  1. completes the batches whose GPU work has finished (results read to the host, futures
+     resolved, latency = result on the host - arrival),
+  2. admits waiting streams while the device-memory budget allows,
+  3. launches one batch over every admitted stream that has a queued frame and is not already in
+     flight (the streams' frames are submitted, then one batched Gauss-Newton solve covers all of
+     them).
+
+Several batches are in flight at once on their own CUDA streams (their stream sets are
+disjoint), so frames arriving while others are on the GPU are admitted into the next batch and
+their work overlaps on the device. Batch objects (and their captured graphs) are cached per
+stream composition.
+
+The engine is pluggable: ``GpuEngine`` drives libdefsolve; tests use a fake engine to check the
+host logic without a GPU.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+from concurrent.futures import Future
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class StreamSpec:
+    template_depth: np.ndarray      # (H, W) float32
+    K: tuple                        # fx, fy, cx, cy
+    nodes: np.ndarray               # (N,) int32 control-point pixels
+    max_matches: int = 4096
+
+
+@dataclasses.dataclass
+class FrameIn:
+    depth: np.ndarray
+    match_idx: np.ndarray
+    match_xyz: np.ndarray
+    hyp: np.ndarray
+
+
+@dataclasses.dataclass
+class Result:
+    q: np.ndarray                   # (N, 4)
+    t: np.ndarray                   # (N, 3)
+    pos: np.ndarray                 # (N, 3) control-point positions
+    latency_s: float
+    batch_size: int
+
+
+def stream_bytes(W: int, H: int, N: int, M: int, precision: int) -> int:
+    """Device bytes one stream holds (template, frame, blend tables, system buffers)."""
+    npx, n = W * H, 6 * N
+    nbp = 14 * N
+    b = npx * (4 + 24 + 4 + 4 + 16 + 16 + 4)            # depths, FP64 template, frame points
+    b += npx * (16 + 16 + 4)                            # sorted points, weights, rank
+    b += N * (8 * 7 + 64 + 96) + nbp * (36 * 4 + 12)    # state, node tables, data blocks
+    b += n * n * 4                                      # FP32 system
+    if precision == 0:
+        b += n * n * 8                                  # FP64 factor
+    elif precision == 2:
+        b += n * n * 4                                  # FP32 factor
+    b += n * (8 * 3 + 8 * 3 + 4)                        # vectors
+    tb = 32 if precision == 0 else 64
+    nt = (n + tb - 1) // tb
+    b += 4 * (nt + 2 * nt * nt) + 8 * nt * tb * tb
+    b += nt * (nt + 1) // 2 * 16 * 2                    # task list
+    b += M * (4 + 12 + 4 + 4) + M * 64 * (7 * 8 + 4)    # matches and RANSAC scratch
+    return int(b)
+
+
+class GpuEngine:
+    """libdefsolve behind the server: one handle per stream, one batch object per composition."""
+
+    def __init__(self, params=None, use_graph=True, cache=32):
+        import torch
+        from . import build, defsolve
+        build.build()
+        self.d = defsolve
+        self.torch = torch
+        self.params = params if params is not None else defsolve.default_params(precision=2)
+        self.params.use_graph = 1 if use_graph else 0
+        self.cache = collections.OrderedDict()
+        self.cache_cap = cache
+
+    @property
+    def precision(self):
+        return int(self.params.precision)
+
+    def create(self, spec: StreamSpec):
+        s = self.d.Solver(spec.template_depth, spec.K, spec.nodes, self.params)
+        return s
+
+    def destroy(self, s):
+        for key in [k for k in self.cache if id(s) in k]:
+            b, _, _ = self.cache.pop(key)
+            self.d.ds_batch_destroy(b)
+        s.close()
+
+    def submit(self, s, f: FrameIn):
+        s.submit(f.depth, f.match_idx, f.match_xyz, f.hyp)
+
+    def launch(self, solvers, iters):
+        key = tuple(sorted(id(s) for s in solvers))
+        if key in self.cache:
+            b, stream, ev = self.cache.pop(key)
+        else:
+            stream = self.torch.cuda.Stream()
+            b = self.d.ds_batch_create([s.h for s in solvers], stream.cuda_stream)
+            ev = None
+            while len(self.cache) >= self.cache_cap:
+                _, (ob, _, _) = self.cache.popitem(last=False)
+                self.d.ds_batch_destroy(ob)
+        self.d.ds_batch_solve(b, iters)
+        ev = self.torch.cuda.Event()
+        ev.record(stream)
+        self.cache[key] = (b, stream, ev)
+        return (key, ev)
+
+    def done(self, token) -> bool:
+        return token[1].query()
+
+    def read(self, s):
+        q, t, p = s.deformation()
+        return q, t, p
+
+
+class Server:
+    def __init__(self, engine, budget_bytes: int, iters: int = 10, max_batch: int = 64,
+                 clock=time.perf_counter):
+        self.engine = engine
+        self.budget = int(budget_bytes)
+        self.iters = iters
+        self.max_batch = max_batch
+        self.clock = clock
+        self.used = 0
+        self.streams = {}                 # sid -> dict(spec, solver, queue, busy, bytes)
+        self.waiting = collections.deque()  # sids waiting for admission
+        self.in_flight = []               # (token, [sid], [(future, t_arrival)])
+        self.latencies = []
+        self.completed = 0
+        self.t_first = None
+        self.t_last = None
+        self.batches = 0
+        self.batch_sizes = []
+
+    # -- streams
+    def open_stream(self, sid, spec: StreamSpec) -> bool:
+        """Registers a stream; returns True if it was admitted now, False if it waits for
+        device memory (its frames queue up meanwhile)."""
+        if sid in self.streams:
+            raise KeyError(f"stream {sid} already open")
+        H, W = spec.template_depth.shape
+        nbytes = stream_bytes(W, H, len(spec.nodes), spec.max_matches, self.engine.precision)
+        if nbytes > self.budget:
+            raise ValueError(f"stream {sid} needs {nbytes} B, more than the whole budget")
+        self.streams[sid] = dict(spec=spec, solver=None, queue=collections.deque(), busy=False,
+                                 bytes=nbytes)
+        self.waiting.append(sid)
+        self._admit()
+        return self.streams[sid]["solver"] is not None
+
+    def close_stream(self, sid):
+        st = self.streams[sid]
+        if st["busy"]:
+            raise RuntimeError(f"stream {sid} has a frame in flight")
+        for fut, _, _ in st["queue"]:
+            fut.cancel()
+        if st["solver"] is not None:
+            self.engine.destroy(st["solver"])
+            self.used -= st["bytes"]
+        else:
+            self.waiting.remove(sid)
+        del self.streams[sid]
+        self._admit()
+
+    def _admit(self):
+        while self.waiting:
+            sid = self.waiting[0]
+            st = self.streams[sid]
+            if self.used + st["bytes"] > self.budget:
+                break
+            self.waiting.popleft()
+            st["solver"] = self.engine.create(st["spec"])
+            self.used += st["bytes"]
+
+    # -- frames
+    def submit(self, sid, frame: FrameIn, t_arrival=None) -> Future:
+        fut = Future()
+        t = self.clock() if t_arrival is None else t_arrival
+        if self.t_first is None:
+            self.t_first = t
+        self.streams[sid]["queue"].append((fut, t, frame))
+        return fut
+
+    def poll(self) -> int:
+        """One scheduler round; returns the number of frames completed."""
+        n_done = 0
+        still = []
+        for token, sids, items in self.in_flight:
+            if self.engine.done(token):
+                now_batch = len(sids)
+                for sid, (fut, t_arr) in zip(sids, items):
+                    st = self.streams[sid]
+                    q, t, p = self.engine.read(st["solver"])
+                    now = self.clock()
+                    lat = now - t_arr
+                    self.latencies.append(lat)
+                    st["busy"] = False
+                    fut.set_result(Result(q, t, p, lat, now_batch))
+                    self.completed += 1
+                    self.t_last = now
+                    n_done += 1
+            else:
+                still.append((token, sids, items))
+        self.in_flight = still
+        self._admit()
+        ready = [sid for sid, st in self.streams.items()
+                 if st["solver"] is not None and not st["busy"] and st["queue"]]
+        ready = ready[: self.max_batch]
+        if ready:
+            solvers, items = [], []
+            for sid in ready:
+                st = self.streams[sid]
+                fut, t_arr, frame = st["queue"].popleft()
+                self.engine.submit(st["solver"], frame)
+                st["busy"] = True
+                solvers.append(st["solver"])
+                items.append((fut, t_arr))
+            token = self.engine.launch(solvers, self.iters)
+            self.in_flight.append((token, ready, items))
+            self.batches += 1
+            self.batch_sizes.append(len(ready))
+        return n_done
+
+    def pending(self) -> int:
+        return sum(len(st["queue"]) for st in self.streams.values()) + sum(
+            len(s) for _, s, _ in self.in_flight)
+
+    def drain(self, idle_sleep=0.0):
+        while self.pending():
+            if self.poll() == 0 and idle_sleep:
+                time.sleep(idle_sleep)
+
+    def stats(self) -> dict:
+        lat = np.array(self.latencies) if self.latencies else np.zeros(1)
+        span = (self.t_last - self.t_first) if self.completed and self.t_last else float("nan")
+        return {"frames": self.completed, "frames_per_s": self.completed / span if span else None,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "batches": self.batches,
+                "mean_batch": float(np.mean(self.batch_sizes)) if self.batch_sizes else 0.0,
+                "device_bytes": self.used}
+
+
+def poisson_schedule(rng: np.random.Generator, rates_hz, n_total: int):
+    """Merged arrival schedule of independent Poisson streams: list of (t, stream index), the
+    first n_total arrivals."""
+    events = []
+    horizon = 1.0
+    while True:
+        events = []
+        for s, r in enumerate(rates_hz):
+            t = 0.0
+            while True:
+                t += rng.exponential(1.0 / r)
+                if t > horizon:
+                    break
+                events.append((t, s))
+        if len(events) >= n_total:
+            break
+        horizon *= 2.0
+    events.sort()
+    return events[:n_total]

@@ -136,6 +136,8 @@ def raycast_template(hf: Heightfield, W: int, H: int, iters: int = 40):
     for _ in range(iters):
         z, zx, zy = hf.eval(lam * dx, lam * dy)
         f = lam - z
+        if np.abs(f).max() < 1e-12:
+            break
         df = 1.0 - (zx * dx + zy * dy)
         df = np.where(np.abs(df) < 0.2, np.sign(df + 1e-300) * 0.2, df)
         lam = lam - f / df
@@ -170,6 +172,8 @@ def render_target(hf: Heightfield, mo: Motion, W: int, H: int, iters: int = 12):
         det = np.where(np.abs(det) < 1e-12, 1e-12, det)
         ru = pu - up
         rv = pv - vp
+        if max(np.abs(ru).max(), np.abs(rv).max()) < 1e-10:
+            break
         x = x - (a22 * ru - a12 * rv) / det
         y = y - (-a21 * ru + a11 * rv) / det
     Y, _, _ = mo.surface(hf, x, y)

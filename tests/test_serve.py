@@ -1,0 +1,151 @@
+"""Serving loop: host logic on the CPU with a fake engine; on the GPU, each stream's results in
+the served mix equal the same stream solved alone."""
+import numpy as np
+import pytest
+
+from paper_2007_08576_gb300.serve import (FrameIn, Server, StreamSpec, poisson_schedule,
+                                          stream_bytes)
+
+
+class FakeEngine:
+    """Completes a launched batch after `delay` polls; 'solves' by counting frames."""
+
+    precision = 2
+
+    def __init__(self, delay=2):
+        self.delay = delay
+        self.launches = []
+        self.polls = 0
+        self.live = set()
+
+    def create(self, spec):
+        s = {"frames": 0, "spec": spec}
+        self.live.add(id(s))
+        return s
+
+    def destroy(self, s):
+        self.live.discard(id(s))
+
+    def submit(self, s, f):
+        s["frames"] += 1
+
+    def launch(self, solvers, iters):
+        tok = {"left": self.delay, "ids": [id(s) for s in solvers]}
+        self.launches.append(tok)
+        return tok
+
+    def done(self, tok):
+        tok["left"] -= 1
+        return tok["left"] < 0
+
+    def read(self, s):
+        N = len(s["spec"].nodes)
+        return np.zeros((N, 4)), np.full((N, 3), float(s["frames"])), np.zeros((N, 3))
+
+
+def _spec(W=80, H=60, N=32):
+    return StreamSpec(np.full((H, W), 100.0, np.float32), (W, W, (W - 1) / 2, (H - 1) / 2),
+                      np.arange(N, dtype=np.int32), max_matches=200)
+
+
+def _frame():
+    return FrameIn(None, None, None, None)
+
+
+def test_admission_by_memory_budget():
+    one = stream_bytes(80, 60, 32, 200, 2)
+    eng = FakeEngine()
+    srv = Server(eng, budget_bytes=int(2.5 * one))
+    assert srv.open_stream("a", _spec())
+    assert srv.open_stream("b", _spec())
+    assert not srv.open_stream("c", _spec())         # waits: budget holds two streams
+    assert srv.used == 2 * one and len(eng.live) == 2
+    fc = srv.submit("c", _frame())                  # queued while not admitted
+    srv.close_stream("a")                           # frees memory -> c admitted
+    assert srv.streams["c"]["solver"] is not None and srv.used == 2 * one
+    srv.drain()
+    assert fc.result().t[0, 0] == 1.0
+    with pytest.raises(ValueError):
+        Server(eng, budget_bytes=one // 2).open_stream("x", _spec())
+
+
+def test_continuous_batching_overlaps_and_keeps_order():
+    eng = FakeEngine(delay=3)
+    srv = Server(eng, budget_bytes=1 << 40)
+    for s in "abcd":
+        srv.open_stream(s, _spec())
+    f1 = [srv.submit(s, _frame()) for s in "ab"]
+    srv.poll()                                       # batch 1: a, b
+    assert eng.launches[-1]["ids"] and len(srv.in_flight) == 1
+    f2 = [srv.submit(s, _frame()) for s in "cd"] + [srv.submit("a", _frame())]
+    srv.poll()                                       # batch 2: c, d (a still busy)
+    assert len(srv.in_flight) == 2
+    ids2 = set(eng.launches[-1]["ids"])
+    assert ids2 == {id(srv.streams["c"]["solver"]), id(srv.streams["d"]["solver"])}
+    srv.drain()
+    assert all(f.done() for f in f1 + f2)
+    # stream a got its two frames in order (warm-start chain)
+    assert f1[0].result().t[0, 0] == 1.0 and f2[2].result().t[0, 0] == 2.0
+    st = srv.stats()
+    assert st["frames"] == 5 and st["batches"] >= 3 and st["p99_ms"] >= st["p50_ms"]
+
+
+def test_poisson_schedule():
+    rng = np.random.default_rng(0)
+    ev = poisson_schedule(rng, [15.0, 60.0], 200)
+    assert len(ev) == 200 and all(a[0] <= b[0] for a, b in zip(ev, ev[1:]))
+    counts = np.bincount([s for _, s in ev], minlength=2)
+    assert counts[1] > 2 * counts[0]                 # rate ratio 4
+
+
+@pytest.mark.gpu
+def test_served_results_equal_alone():
+    from gpu_common import lib
+    from paper_2007_08576_gb300.serve import GpuEngine
+    from synth import make_scene
+    from synth.scene import Config
+    d = lib()
+    cfgs = [Config("s80", 80, 60, 32, 200, 5, 0.3, 0.3, 0.0, 4.0, 1.0, 0.3, 0.5, 3),
+            Config("s120", 120, 90, 40, 300, 8, 0.4, 0.5, 0.1, 8.0, 1.0, 0.3, 0.5, 3),
+            Config("s150", 150, 110, 50, 333, 8, 0.35, 0.5, 0.05, 6.0, 1.0, 0.2, 0.5, 3)]
+    scenes = [make_scene(c, 500 + i, n_frames=3) for i, c in enumerate(cfgs)]
+    p = d.default_params(precision=2)
+    # alone: each stream's frames in order on its own handle
+    alone = []
+    for sc in scenes:
+        s = d.Solver(sc.template_depth, sc.K, sc.nodes, p)
+        outs = []
+        for f in sc.frames:
+            s.submit(f.depth, f.match_idx, f.match_xyz, f.hyp)
+            s.solve(10, stats=False)
+            outs.append(s.deformation()[2])
+        alone.append(outs)
+        s.close()
+    # served: Poisson arrivals, continuous batching
+    srv = Server(GpuEngine(d.default_params(precision=2)), budget_bytes=1 << 33)
+    for i, sc in enumerate(scenes):
+        srv.open_stream(i, StreamSpec(sc.template_depth, sc.K, sc.nodes, max_matches=400))
+    rng = np.random.default_rng(3)
+    sched = poisson_schedule(rng, [40.0, 25.0, 60.0], 9)
+    nxt = [0, 0, 0]
+    futs = {i: [] for i in range(3)}
+    for _, s in sched:
+        if nxt[s] >= 3:
+            continue
+        f = scenes[s].frames[nxt[s]]
+        futs[s].append(srv.submit(s, FrameIn(f.depth, f.match_idx, f.match_xyz, f.hyp)))
+        nxt[s] += 1
+        srv.poll()
+    for s in range(3):
+        while nxt[s] < 3:
+            f = scenes[s].frames[nxt[s]]
+            futs[s].append(srv.submit(s, FrameIn(f.depth, f.match_idx, f.match_xyz, f.hyp)))
+            nxt[s] += 1
+    srv.drain()
+    for s in range(3):
+        for k, fut in enumerate(futs[s]):
+            assert np.abs(fut.result().pos - alone[s][k]).max() <= 1e-4
+    st = srv.stats()
+    assert st["frames"] == 9
+    for i in range(3):
+        srv.close_stream(i)
