@@ -696,8 +696,13 @@ void launch_chol_dag(const BatchTabs& B, cudaStream_t s) {
     cudaFuncSetAttribute(k_chol_dag<T, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr = true;
   }
+  static int per_sm = 0;
+  if (!per_sm) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_dag<T, TB>, 256, sm);
+    per_sm = std::max(1, std::min(per_sm, 4));
+  }
   const int nticket = B.P * B.max_tasks;
-  const int grid = std::min(nticket, 2 * num_sms());
+  const int grid = std::min(nticket, per_sm * num_sms());
   k_chol_dag<T, TB><<<grid, 256, sm, s>>>(B.d, B.P, nticket, B.words + 0, B.words + 5,
                                           2000000000ull);
   ++g_launches;
@@ -706,8 +711,13 @@ void launch_chol_dag(const BatchTabs& B, cudaStream_t s) {
 template <typename T>
 void launch_trsv_dag(const BatchTabs& B, int solve_id, cudaStream_t s) {
   constexpr int TB = sizeof(T) == 8 ? 32 : 64;
+  static int per_sm = 0;
+  if (!per_sm) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trsv_dag<T, TB>, 256, 0);
+    per_sm = std::max(1, std::min(per_sm, 4));
+  }
   const int nticket = B.P * 2 * B.max_nt;
-  const int grid = std::min(nticket, 2 * num_sms());
+  const int grid = std::min(nticket, per_sm * num_sms());
   k_trsv_dag<T, TB><<<grid, 256, 0, s>>>(B.d, B.P, nticket, solve_id, B.words + solve_id,
                                           B.words + 5, 2000000000ull);
   ++g_launches;

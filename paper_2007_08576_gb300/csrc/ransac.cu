@@ -213,6 +213,7 @@ __global__ __launch_bounds__(kRansacThreads) void k_ransac_hyp(
   }
   __syncthreads();
   const int words = (M + 31) / 32;
+  const double H2 = H * H;
   for (int it = 0; it < n_reweight; ++it) {
     double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int k = threadIdx.x; k < M; k += blockDim.x) {
@@ -252,11 +253,20 @@ __global__ __launch_bounds__(kRansacThreads) void k_ransac_hyp(
         double e0 = S2x[k] - (R0 * x + R1 * y + R2 * z);
         double e1 = S2y[k] - (R3 * x + R4 * y + R5 * z);
         double e2 = S2z[k] - (R6 * x + R7 * y + R8 * z);
-        double d = sqrt(e0 * e0 + e1 * e1 + e2 * e2);
-        double wk = d > 0.0 ? fmin(H / d, 1.0) : 1.0;
+        // d <= H  <=>  d^2 <= H^2, and w = H / d = H rsqrt(d^2) when d > H: no FP64 sqrt or
+        // division (each costs tens of instructions on the FP64 pipe)
+        const double d2 = e0 * e0 + e1 * e1 + e2 * e2;
+        const bool within = d2 <= H2;
+        double wk = 1.0;
+        if (!within) {
+          double y0 = (double)rsqrtf((float)d2);
+          y0 = y0 * (1.5 - 0.5 * d2 * y0 * y0);
+          y0 = y0 * (1.5 - 0.5 * d2 * y0 * y0);
+          wk = fmin(H * y0, 1.0);
+        }
         w[k] = wk;
         if (last) {
-          inl = d <= H;
+          inl = within;
           hw[(size_t)h * M + k] = (float)wk;
           if (k != k0) sc += wk;
         }
@@ -276,7 +286,8 @@ __global__ __launch_bounds__(kRansacThreads) void k_ransac_hyp(
 }
 
 // Keep references with score >= keep_frac * best; mask = OR of kept bitsets, weight = max of
-// kept weights. One CTA.
+// kept weights. Every CTA derives the kept set from the scores itself and handles a slice of the
+// matches; CTA 0 also writes the kept bitset and the counts.
 __global__ void k_ransac_combine(const uint32_t* __restrict__ hbits, const float* __restrict__ hw,
                                  const double* __restrict__ score, int n_hyp, int M,
                                  double keep_frac, uint32_t* __restrict__ mask,
@@ -299,31 +310,36 @@ __global__ void k_ransac_combine(const uint32_t* __restrict__ hbits, const float
       }
     skept[0] = k0;
     skept[1] = k1;
-    kept[0] = k0;
-    kept[1] = k1;
-    counts[1] = nk;
+    if (blockIdx.x == 0) {
+      kept[0] = k0;
+      kept[1] = k1;
+      counts[1] = nk;
+    }
     sin = 0;
   }
   __syncthreads();
   const int words = (M + 31) / 32;
+  // this CTA: matches [blockIdx.x * 256, +256) = words [blockIdx.x * 8, +8)
   int local = 0;
-  for (int wd = threadIdx.x; wd < words; wd += blockDim.x) {
+  const int wd = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if ((threadIdx.x & 31) == 0 && wd < words) {
     uint32_t m = 0;
     for (int h = 0; h < n_hyp; ++h)
       if ((skept[h >> 5] >> (h & 31)) & 1u) m |= hbits[(size_t)h * words + wd];
     if (wd == words - 1 && (M & 31)) m &= (1u << (M & 31)) - 1u;
     mask[wd] = m;
-    local += __popc(m);
+    local = __popc(m);
   }
-  for (int k = threadIdx.x; k < M; k += blockDim.x) {
+  const int k = blockIdx.x * 256 + threadIdx.x;
+  if (k < M) {
     float b = 0.f;
     for (int h = 0; h < n_hyp; ++h)
       if ((skept[h >> 5] >> (h & 31)) & 1u) b = fmaxf(b, hw[(size_t)h * M + k]);
     what[k] = b;
   }
-  atomicAdd(&sin, local);
+  if (local) atomicAdd(&sin, local);
   __syncthreads();
-  if (threadIdx.x == 0) counts[0] = sin;
+  if (threadIdx.x == 0 && sin) atomicAdd(&counts[0], sin);
 }
 
 int ransac_smem_bytes(int M) { return 7 * (int)sizeof(double) * M; }
@@ -348,8 +364,9 @@ void launch_ransac(const float* depth0, int W, ds_intrinsics K, const int* midx,
                                                  M, hyp, n_reweight, H, use_smem, scratch, hbits,
                                                  hw, score);
   ++g_launches;
-  k_ransac_combine<<<1, 256, 0, s>>>(hbits, hw, score, n_hyp, M, keep_frac, mask, what, kept,
-                                     counts);
+  cudaMemsetAsync(counts, 0, sizeof(int), s);  // counts[0] is accumulated by every CTA
+  k_ransac_combine<<<(M + 255) / 256, 256, 0, s>>>(hbits, hw, score, n_hyp, M, keep_frac, mask,
+                                                     what, kept, counts);
   ++g_launches;
 }
 
