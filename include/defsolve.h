@@ -210,6 +210,29 @@ int ds_set_tracing(ds_handle h, int32_t on);
 int ds_get_phase_times(ds_handle h, double* ms4);
 int ds_get_counters(ds_handle h, int64_t* kernels_launched);
 
+/* 1-point RANSAC preselection without any allocation, for callers that cannot allocate device
+ * memory (for example a host process that runs inside a pre-sized memory pool, or a real-time
+ * loop where an allocation can block on a device-wide synchronisation). The paper has no
+ * counterpart; it computes exactly what ds_submit_frame's preselection computes (Section 2.1),
+ * into caller-provided device buffers.
+ * All pointers are device memory owned by the caller: depth0 (H x W template depth), the M match
+ * pixels and live points, the n_hyp reference ids; outputs mask_bits[ceil(M/32)], w_M[M],
+ * kept_bits[2], score_nh[n_hyp]. Limits: 1 <= M <= DS_NOALLOC_MAX_MATCHES, n_hyp <= DS_MAX_HYP.
+ * The working memory is one fixed array compiled into the library (about 1.1 MB, held on every
+ * device that loads the library until the process exits). The first call on a device looks up
+ * that array's device address; make that first call before any stream capture. All calls share
+ * the array: calls that overlap on the GPU (other streams, other threads) race and must not be
+ * issued. The call runs on cuda_stream (NULL: the legacy default stream) and synchronises it
+ * before returning. Errors: DS_ERR_ARG (sizes beyond the limits, a null or host pointer, an
+ * out-of-range match pixel or reference id — reported after the run, whose outputs then refer
+ * to the index 0 in place of the bad ones), DS_ERR_CUDA. */
+#define DS_NOALLOC_MAX_MATCHES 4000
+int ds_ransac_noalloc(const float* depth0, int32_t W, int32_t H, ds_intrinsics K,
+                      const int32_t* match_tmpl_idx, const float* match_xyz, int32_t M,
+                      const int32_t* hyp_list, int32_t n_hyp, int32_t n_reweight, double H_mm,
+                      double keep_frac, uint32_t* mask_bits, float* w_M, uint32_t* kept_bits,
+                      double* score_nh, void* cuda_stream);
+
 /* Releases everything the handle owns. NULL is accepted. */
 int ds_destroy(ds_handle h);
 

@@ -16,6 +16,8 @@
 // Everything that decides a mask bit is FP64.
 #include <math.h>
 
+#include <mutex>
+
 #include "ds_internal.cuh"
 
 namespace ds {
@@ -370,4 +372,120 @@ void launch_ransac(const float* depth0, int W, ds_intrinsics K, const int* midx,
   ++g_launches;
 }
 
+// ----------------------------------------------------------------------------- no-allocation entry
+
+// Scratch of ds_ransac_noalloc: a file-scope device array, so the entry point never allocates.
+// Limits: M <= DS_NOALLOC_MAX_MATCHES matches (the shared-memory path of the kernel, no global
+// staging), n_hyp <= DS_MAX_HYP references. Layout (256-byte aligned sections): per-reference
+// bitsets, per-reference weights, validated copies of the match and reference indices, the
+// match count word and the invalid-index flag.
+namespace {
+constexpr int kNaWords = (DS_NOALLOC_MAX_MATCHES + 31) / 32;
+constexpr size_t kNaAlign(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t kNaBits = 0;
+constexpr size_t kNaW = kNaBits + kNaAlign(sizeof(uint32_t) * DS_MAX_HYP * kNaWords);
+constexpr size_t kNaMidx = kNaW + kNaAlign(sizeof(float) * DS_MAX_HYP * DS_NOALLOC_MAX_MATCHES);
+constexpr size_t kNaHyp = kNaMidx + kNaAlign(sizeof(int) * DS_NOALLOC_MAX_MATCHES);
+constexpr size_t kNaCnt = kNaHyp + kNaAlign(sizeof(int) * DS_MAX_HYP);
+constexpr size_t kNaTotal = kNaCnt + 256;
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_ransac_scratch[kNaTotal];
+
+// Copies the caller's indices into the scratch, replacing any out-of-range template pixel or
+// reference id by 0 (so no kernel reads out of bounds) and raising the flag.
+__global__ void k_na_indices(const int* __restrict__ midx_in, int M, const int* __restrict__ hyp_in,
+                             int n_hyp, int npx, const float* __restrict__ depth0,
+                             int* __restrict__ midx, int* __restrict__ hyp, int* flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < M) {
+    int j = midx_in[i];
+    if (j < 0 || j >= npx || !(depth0[j] > 0.f)) {
+      j = 0;
+      atomicOr(flag, 1);
+    }
+    midx[i] = j;
+  }
+  if (i < n_hyp) {
+    int k = hyp_in[i];
+    if (k < 0 || k >= M) {
+      k = 0;
+      atomicOr(flag, 1);
+    }
+    hyp[i] = k;
+  }
+}
+
 }  // namespace ds
+
+namespace {
+bool device_memory(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+}  // namespace
+
+extern "C" int ds_ransac_noalloc(const float* depth0, int32_t W, int32_t H, ds_intrinsics K,
+                                 const int32_t* match_tmpl_idx, const float* match_xyz, int32_t M,
+                                 const int32_t* hyp_list, int32_t n_hyp, int32_t n_reweight,
+                                 double H_mm, double keep_frac, uint32_t* mask_bits, float* w_M,
+                                 uint32_t* kept_bits, double* score_nh, void* cuda_stream) {
+  using namespace ds;
+  if (W < 8 || H < 8 || W > 4096 || H > 4096 || M < 1 || M > DS_NOALLOC_MAX_MATCHES ||
+      n_hyp < 1 || n_hyp > DS_MAX_HYP || n_hyp > M || n_reweight < 1 || n_reweight > 1000 ||
+      !(H_mm > 0) || !(keep_frac >= 0 && keep_frac <= 1) || !(K.fx > 0) || !(K.fy > 0))
+    return DS_ERR_ARG;
+  const void* ptrs[] = {depth0, match_tmpl_idx, match_xyz, hyp_list, mask_bits, w_M, kept_bits,
+                        score_nh};
+  for (const void* p : ptrs)
+    if (!p || !device_memory(p)) return DS_ERR_ARG;
+  // the scratch's device address, looked up once per device with that device current
+  static std::mutex mu;
+  static void* base_of[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DS_ERR_CUDA;
+  unsigned char* base;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!base_of[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_ransac_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return DS_ERR_CUDA;
+      }
+      base_of[dev] = p;
+      cudaFuncSetAttribute(k_ransac_hyp, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    }
+    base = (unsigned char*)base_of[dev];
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  uint32_t* hbits = (uint32_t*)(base + kNaBits);
+  float* hw = (float*)(base + kNaW);
+  int* midx = (int*)(base + kNaMidx);
+  int* hyp = (int*)(base + kNaHyp);
+  int* counts = (int*)(base + kNaCnt);
+  int* flag = counts + 2;
+  // the array keeps the previous call's contents: clear the words that accumulate
+  cudaMemsetAsync(counts, 0, 4 * sizeof(int), s);
+  const int npx = W * H;
+  const int nt = M > n_hyp ? M : n_hyp;
+  k_na_indices<<<(nt + 255) / 256, 256, 0, s>>>(match_tmpl_idx, M, hyp_list, n_hyp, npx, depth0,
+                                                 midx, hyp, flag);
+  const int sm = ransac_smem_bytes(M);  // <= 220 KB for M <= DS_NOALLOC_MAX_MATCHES
+  k_ransac_hyp<<<n_hyp, kRansacThreads, sm, s>>>(depth0, W, K.fx, K.fy, K.cx, K.cy, midx,
+                                                 match_xyz, M, hyp, n_reweight, H_mm, 1, nullptr,
+                                                 hbits, hw, score_nh);
+  k_ransac_combine<<<(M + 255) / 256, 256, 0, s>>>(hbits, hw, score_nh, n_hyp, M, keep_frac,
+                                                     mask_bits, w_M, kept_bits, counts);
+  if (cudaGetLastError() != cudaSuccess) return DS_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return DS_ERR_CUDA;
+  int bad = 0;
+  if (cudaMemcpy(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return DS_ERR_CUDA;
+  return bad ? DS_ERR_ARG : DS_OK;
+}
+

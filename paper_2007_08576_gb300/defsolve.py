@@ -28,7 +28,8 @@ EXPORTS = [
     "ds_batch_destroy", "ds_batch_set_tracing", "ds_batch_phase_times", "ds_get_deformation", "ds_get_deformation64",
     "ds_set_deformation", "ds_get_inlier_mask", "ds_get_ransac", "ds_get_cost",
     "ds_get_blend_table", "ds_get_frame_points", "ds_linearize", "ds_set_tracing",
-    "ds_get_phase_times", "ds_get_counters", "ds_destroy", "ds_status_str", "ds_version",
+    "ds_get_phase_times", "ds_get_counters", "ds_ransac_noalloc", "ds_destroy", "ds_status_str",
+    "ds_version",
 ]
 
 
@@ -103,6 +104,8 @@ def lib(path: str | None = None):
         "ds_set_tracing": (i32, [vp, i32]),
         "ds_get_phase_times": (i32, [vp, vp]),
         "ds_get_counters": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
+        "ds_ransac_noalloc": (i32, [vp, i32, i32, DsIntrinsics, vp, vp, i32, vp, i32, i32, f64,
+                                    f64, vp, vp, vp, vp, vp]),
         "ds_destroy": (i32, [vp]),
         "ds_status_str": (ctypes.c_char_p, [i32]),
         "ds_version": (ctypes.c_char_p, []),
@@ -288,6 +291,26 @@ def ds_get_counters(h=None) -> int:
     k = ctypes.c_int64()
     _check("ds_get_counters", lib().ds_get_counters(h, ctypes.byref(k)))
     return k.value
+
+
+def _dev_ptr(t, itemsize):
+    """Device pointer of a contiguous torch CUDA tensor with the given element size."""
+    if not (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous() and t.element_size() == itemsize):
+        raise TypeError("expected a contiguous CUDA tensor with %d-byte elements" % itemsize)
+    return t.data_ptr()
+
+
+def ds_ransac_noalloc(depth0, W, H, K, match_idx, match_xyz, M, hyp, n_hyp, n_reweight, H_mm,
+                      keep_frac, mask_bits, w_M, kept_bits, score_nh, stream=None):
+    """RANSAC preselection into caller-provided device tensors, with no allocation in the
+    library (see include/defsolve.h). Bit outputs may be int32 or uint32 tensors."""
+    Kc = DsIntrinsics(*[float(k) for k in K])
+    rc = lib().ds_ransac_noalloc(_dev_ptr(depth0, 4), int(W), int(H), Kc, _dev_ptr(match_idx, 4),
+                                 _dev_ptr(match_xyz, 4), int(M), _dev_ptr(hyp, 4), int(n_hyp),
+                                 int(n_reweight), float(H_mm), float(keep_frac),
+                                 _dev_ptr(mask_bits, 4), _dev_ptr(w_M, 4), _dev_ptr(kept_bits, 4),
+                                 _dev_ptr(score_nh, 8), stream)
+    _check("ds_ransac_noalloc", rc)
 
 
 def ds_destroy(h):
