@@ -91,24 +91,42 @@ struct Vec2<double> {
 };
 
 // Loads tile (ti, tj) of A transposed into shared memory: S[m * LDT + r] = A[ti*TB + r][tj*TB + m]
-// (zero outside the matrix). Two-element vector loads along rows (n is even, so rows stay
-// 8-byte aligned for float and 16-byte aligned for double).
+// (zero outside the matrix). Lane <-> row: each thread reads a contiguous run of one row with
+// 16-byte vector loads and writes it down a column of S, so a warp's shared stores hit 32
+// consecutive banks. Rows are 16-byte aligned when n is a multiple of 4 (FP32) / 2 (FP64);
+// otherwise the scalar path is taken.
 template <typename T, int TB>
 __device__ __forceinline__ void load_tile_t(const T* A, int n, int ti, int tj, T* S) {
-  using V2 = typename Vec2<T>::type;
   constexpr int LDT = TileCfg<T, TB>::LDT;
+  constexpr int VE = 16 / sizeof(T);           // elements per 16-byte vector
+  constexpr int RUN = TB * TB / 256;           // elements per thread (16 FP32 / 4 FP64)
+  constexpr int SPLIT = TB / RUN;              // threads per row
   const int r0 = ti * TB, c0 = tj * TB;
-  for (int e = threadIdx.x; e < TB * TB / 2; e += blockDim.x) {
-    const int r = e / (TB / 2), m = 2 * (e % (TB / 2));
-    V2 v;
-    if (r0 + r < n && c0 + m + 1 < n) {
-      v = __ldcg(reinterpret_cast<const V2*>(A + (size_t)(r0 + r) * n + c0 + m));
-    } else {
-      v.x = (r0 + r < n && c0 + m < n) ? ldcg(A + (size_t)(r0 + r) * n + c0 + m) : (T)0;
-      v.y = (T)0;
+  const int r = threadIdx.x % TB;
+  const int m0 = (threadIdx.x / TB) * RUN;
+  (void)SPLIT;
+  const bool full = (r0 + TB <= n) && (c0 + TB <= n) && ((n * sizeof(T)) % 16 == 0);
+  if (full) {
+    const T* src = A + (size_t)(r0 + r) * n + c0 + m0;
+#pragma unroll
+    for (int v = 0; v < RUN / VE; ++v) {
+      T buf[VE];
+      if constexpr (sizeof(T) == 4) {
+        float4 x = __ldcg(reinterpret_cast<const float4*>(src) + v);
+        buf[0] = x.x; buf[1] = x.y; buf[2] = x.z; buf[3] = x.w;
+      } else {
+        double2 x = __ldcg(reinterpret_cast<const double2*>(src) + v);
+        buf[0] = x.x; buf[1] = x.y;
+      }
+#pragma unroll
+      for (int e = 0; e < VE; ++e) S[(m0 + v * VE + e) * LDT + r] = buf[e];
     }
-    S[m * LDT + r] = v.x;
-    S[(m + 1) * LDT + r] = v.y;
+  } else {
+#pragma unroll
+    for (int e = 0; e < RUN; ++e) {
+      const int m = m0 + e;
+      S[m * LDT + r] = (r0 + r < n && c0 + m < n) ? ldcg(A + (size_t)(r0 + r) * n + c0 + m) : (T)0;
+    }
   }
 }
 
@@ -144,20 +162,42 @@ __device__ __forceinline__ void tile_abt_t(const T* Pt, const T* Qt,
 }
 
 // Stores (or subtracts from) this thread's RT x RT block of tile (ti, tj); lower_only keeps
-// r >= c (diagonal tiles).
+// r >= c (diagonal tiles). Interior blocks of an aligned matrix move as one 16-byte vector per row.
 template <typename T, int TB, bool SUB>
 __device__ __forceinline__ void store_block(T* A, int n, int ti, int tj,
                                             const T (&v)[TileCfg<T, TB>::RT][TileCfg<T, TB>::RT],
                                             bool lower_only) {
   constexpr int RT = TileCfg<T, TB>::RT;
   const int tr = (threadIdx.x / 16) * RT, tc = (threadIdx.x % 16) * RT;
+  const int rb = ti * TB + tr, cb = tj * TB + tc;
+  const bool vec = !lower_only && rb + RT <= n && cb + RT <= n && ((n * sizeof(T)) % 16 == 0);
+  if (vec) {
+#pragma unroll
+    for (int a = 0; a < RT; ++a) {
+      T* p = A + (size_t)(rb + a) * n + cb;
+      if constexpr (RT == 4) {
+        float4 o = SUB ? __ldcg(reinterpret_cast<const float4*>(p)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        o.x = SUB ? o.x - v[a][0] : v[a][0];
+        o.y = SUB ? o.y - v[a][1] : v[a][1];
+        o.z = SUB ? o.z - v[a][2] : v[a][2];
+        o.w = SUB ? o.w - v[a][3] : v[a][3];
+        __stcg(reinterpret_cast<float4*>(p), o);
+      } else {
+        double2 o = SUB ? __ldcg(reinterpret_cast<const double2*>(p)) : make_double2(0.0, 0.0);
+        o.x = SUB ? o.x - v[a][0] : v[a][0];
+        o.y = SUB ? o.y - v[a][1] : v[a][1];
+        __stcg(reinterpret_cast<double2*>(p), o);
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int a = 0; a < RT; ++a) {
-    const int r = ti * TB + tr + a;
+    const int r = rb + a;
     if (r >= n) continue;
 #pragma unroll
     for (int b = 0; b < RT; ++b) {
-      const int c = tj * TB + tc + b;
+      const int c = cb + b;
       if (c < n && (!lower_only || c <= r)) {
         T* p = A + (size_t)r * n + c;
         __stcg(p, SUB ? ldcg(p) - v[a][b] : v[a][b]);
@@ -371,13 +411,10 @@ __device__ void task_crit(T* A, T* Dinv, int n, int nt, int k, double* status, T
 // TRSM: L_ik = A_ik (L_kk^-1)^T.
 template <typename T, int TB>
 __device__ void task_trsm(T* A, const T* Dinv, int n, int i, int k, T* Pt, T* Qt) {
-  constexpr int RT = TileCfg<T, TB>::RT, LDT = TileCfg<T, TB>::LDT;
+  constexpr int RT = TileCfg<T, TB>::RT;
   load_tile_t<T, TB>(A, n, i, k, Pt);
   const T* D = Dinv + (size_t)k * TB * TB;
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    const int cc = e / TB, m = e % TB;
-    Qt[m * LDT + cc] = ldcg(D + e);
-  }
+  load_tile_t<T, TB>(D, TB, 0, 0, Qt);   // Qt[m][c] = Dinv[c][m]
   __syncthreads();
   T acc[RT][RT];
   tile_abt_t<T, TB>(Pt, Qt, acc);
