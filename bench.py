@@ -21,6 +21,7 @@ Multi-GPU runs are independent replicas (one set of streams per rank, no collect
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -39,6 +40,23 @@ METRIC = "frames/s and p50/p99 frame latency vs plain GPU solve, at ≤1e-3 mm e
 PREC = {"fp64": 0, "fp32": 1, "fp32_refine": 2}
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate per GPU (nominal)
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_chol_dag launch on this
+# workload (32 problems, FP32 factor), from the full ncu capture summarised in
+# profiles/k_chol_dag_f32_seq_320x240_n256_batch32.md. It describes the kernel source it was taken
+# on (first 16 hex digits of the sha256 of csrc/chol.cu) and is reported as null for any other.
+CHOL_TRAFFIC = {"chol_sha256": "4895a44eb5261eee", "precision": 2, "streams": 32,
+                "bytes": 817284864 + 844839680}
+
+
+def _chol_traffic(prec, streams):
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2007_08576_gb300",
+                       "csrc", "chol.cu")
+    with open(src, "rb") as f:
+        digest = hashlib.sha256(f.read()).hexdigest()[:16]
+    c = CHOL_TRAFFIC
+    if digest != c["chol_sha256"] or prec != c["precision"] or streams != c["streams"]:
+        return None
+    return c["bytes"]
 
 
 def _dist():
@@ -326,6 +344,7 @@ def run_gpu(args):
     else:
         peak, peak_src = FP32_SIMT_TFLOPS, "152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz"
     dgemm = measure_dgemm_tflops(torch, dev) if prec == 0 else None
+    traffic = _chol_traffic(prec, S)
 
     result = None
     if rank == 0:
@@ -354,7 +373,9 @@ def run_gpu(args):
             "gpu_launches": int(launches),
             "roofline": {"bound": "alu", "kernel": "k_chol_dag (persistent tile Cholesky, all problems)",
                          "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
-                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "traffic_unit": "DRAM bytes per launch (ncu)",
+                         "algorithmic_bytes": int(2 * S * n * n * (8 if prec == 0 else 4)),
                          "peak_source": peak_src,
                          "algorithmic": "n^3/3 flop per factorisation, 10 per frame",
                          "dgemm_measured_tflops": round(dgemm, 4) if dgemm else None},
