@@ -126,6 +126,7 @@ struct ds_ctx {
   void* d_v3 = nullptr;
   int* d_lcnt = nullptr;      // factorisation task counters
   int* d_lflags = nullptr;    // solve row flags
+  void* d_Lp = nullptr;       // packed transposed factor tiles
   int4* d_tasks = nullptr;
   int ntasks = 0;
   int nt = 0;
@@ -198,6 +199,7 @@ void free_cp(ds_ctx* h) {
   dfree(h->d_A32); dfree(h->d_A64); dfree(h->d_Af32); dfree(h->d_Dinv); dfree(h->d_blk);
   dfree(h->d_gdata); dfree(h->d_b); dfree(h->d_x); dfree(h->d_r); dfree(h->d_v1);
   dfree(h->d_v2); dfree(h->d_v3); dfree(h->d_lcnt); dfree(h->d_lflags); dfree(h->d_tasks);
+  dfree(h->d_Lp);
   dfree(h->d_desc);
   h->N = h->n = 0;
   h->have_frame = false;
@@ -278,22 +280,13 @@ __global__ void k_sanitize(int* __restrict__ midx, int M, int first_valid) {
   if (i < M && midx[i] < 0) midx[i] = first_valid;
 }
 
-// Tile tasks of one problem's factorisation in a topological order with one step of look-ahead:
-// CRIT(k) (last update of (k,k), POTRF(k), TRSM(k+1,k)), TRSM(i>k+1, k), the rest of step k-1's
-// trailing update, then step k's update of column k+1 (which the next critical task needs).
-// Encoding: {0, type | k << 4, i, j}.
+// Tile tasks of one problem's left-looking factorisation, column by column: DIAG(j), then
+// OFF(j+1, j), ..., OFF(nt-1, j). Every task depends only on tasks earlier in this order.
+// Encoding: {0, type, i, j} with type 0 = DIAG, 1 = OFF.
 void make_chol_tasks(int nt, std::vector<int4>& out) {
-  auto C = [&](int k) { out.push_back(make_int4(0, 0 | (k << 4), k, k)); };
-  auto T = [&](int i, int k) { out.push_back(make_int4(0, 1 | (k << 4), i, k)); };
-  auto G = [&](int i, int j, int k) { out.push_back(make_int4(0, 2 | (k << 4), i, j)); };
-  for (int k = 0; k < nt; ++k) {
-    C(k);
-    for (int i = k + 2; i < nt; ++i) T(i, k);
-    if (k >= 1)
-      for (int j = k + 1; j < nt; ++j)
-        for (int i = j; i < nt; ++i) G(i, j, k - 1);
-    if (k + 1 < nt)
-      for (int i = k + 2; i < nt; ++i) G(i, k + 1, k);
+  for (int j = 0; j < nt; ++j) {
+    out.push_back(make_int4(0, 0, j, j));
+    for (int i = j + 1; i < nt; ++i) out.push_back(make_int4(0, 1, i, j));
   }
 }
 
@@ -796,7 +789,9 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
       (rc = dalloc((char**)&h->d_v3, tsz * n)) ||
       (rc = dalloc((char**)&h->d_Dinv, tsz * (size_t)nt * TB * TB)) ||
       (rc = dalloc(&h->d_lcnt, (size_t)nt + 2 * (size_t)nt * nt)) ||
-      (rc = dalloc(&h->d_lflags, 2 * (size_t)nt))) {
+      (rc = dalloc(&h->d_lflags, 2 * (size_t)nt)) ||
+      (rc = dalloc((char**)&h->d_Lp, tsz * (prec == DS_PREC_FP64 ? chol_packed_elems<double>(nt)
+                                                                 : chol_packed_elems<float>(nt))))) {
     free_cp(h);
     return rc;
   }
@@ -871,6 +866,7 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
     lp.A = prec == DS_PREC_FP64 ? (void*)h->d_A64
                                 : (prec == DS_PREC_FP32_REFINE ? (void*)h->d_Af32 : (void*)h->d_A32);
     lp.Dinv = h->d_Dinv;
+    lp.Lp = h->d_Lp;
     lp.n = n;
     lp.nt = nt;
     lp.cnt = h->d_lcnt;

@@ -350,110 +350,149 @@ __device__ __forceinline__ void load_diag_block(const T* A, int n, int k,
     }
 }
 
-// The critical task of step k: the last update of tile (k,k) (from column k-1), its Cholesky
-// and inverse, and the solve of tile (k+1, k) that the next critical task needs. Shared layout:
-// Pt/Qt (transposed operand tiles, LDT) and the factor / inverse tiles Ls / Xs (LDS = TB + 1).
-template <typename T, int TB>
-__device__ void task_crit(T* A, T* Dinv, int n, int nt, int k, double* status, T* Pt, T* Qt,
-                          T* Ls, T* Xs, T* tmp, int* pdone, const int* upd_next, int* err,
-                          unsigned long long budget_ns, int* s_ok) {
-  constexpr int RT = TileCfg<T, TB>::RT, LDT = TileCfg<T, TB>::LDT, LDS = TB + 1;
-  const int tr = (threadIdx.x / 16) * RT, tc = (threadIdx.x % 16) * RT;
-  const int r0 = k * TB;
-  T acc[RT][RT];
-  if (k >= 1) {
-    load_tile_t<T, TB>(A, n, k, k - 1, Pt);
-    __syncthreads();
-    tile_abt_t<T, TB>(Pt, Pt, acc);
-  }
-#pragma unroll
-  for (int p = 0; p < RT; ++p)
-#pragma unroll
-    for (int q = 0; q < RT; ++q) {
-      const int r = tr + p, cc = tc + q;
-      T v;
-      if (r0 + r < n && r0 + cc < n)
-        v = cc <= r ? ldcg(A + (size_t)(r0 + r) * n + r0 + cc) - (k >= 1 ? acc[p][q] : (T)0) : (T)0;
-      else
-        v = (r == cc) ? (T)1 : (T)0;
-      Ls[r * LDS + cc] = v;
-      Xs[r * LDS + cc] = (r == cc) ? (T)1 : (T)0;
+// ----------------------------------------------------------------------------- factorisation
+
+// 1-D bulk copies global -> shared on the TMA engine, completing on an mbarrier (transaction
+// bytes). Used only for the packed L tiles, which are 16-byte aligned and a multiple of 16 bytes.
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes,
+                                          unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Bounded wait for phase `parity` of a bulk-copy barrier; false (and *err raised) on timeout.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int* err,
+                                          unsigned long long budget_ns) {
+  if (mbar_test(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (!mbar_test(bar, parity)) {
+    if (globaltimer() - t0 > budget_ns) {
+      atomicExch(err, 1);
+      return false;
     }
-  __syncthreads();
-  potrf_blocked<T, TB>(Ls, Xs, tmp, r0, status);
-  // write L_kk (lower), L_kk^-1, and keep the inverse transposed for the solve: Qt[m][c] = X[c][m]
-  T* D = Dinv + (size_t)k * TB * TB;
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    const int r = e / TB, cc = e % TB;
-    const T xv = cc <= r ? Xs[r * LDS + cc] : (T)0;
-    __stcg(D + e, xv);
-    Qt[cc * LDT + r] = xv;
-    if (cc <= r && r0 + r < n) __stcg(A + (size_t)(r0 + r) * n + r0 + cc, Ls[r * LDS + cc]);
   }
-  // publish L_kk and its inverse now: the other TRSM tasks of column k can start while this
-  // task waits for tile (k+1, k) and solves it
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicExch(pdone, 1);
-    if (k + 1 < nt) *s_ok = wait_ge(upd_next, k, err, budget_ns);
-    __threadfence();
-  }
-  __syncthreads();
-  if (k + 1 < nt && *s_ok) {
-    load_tile_t<T, TB>(A, n, k + 1, k, Pt);
-    __syncthreads();
-    tile_abt_t<T, TB>(Pt, Qt, acc);
-    store_block<T, TB, false>(A, n, k + 1, k, acc, false);
+  return true;
+}
+// Orders this thread's earlier generic-proxy global writes before later async-proxy (bulk copy)
+// reads of the same data by any thread that synchronises with it.
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// acc[a][b] += sum_m P^T[m][tr + a] Q^T[m][tc + b] (transposed operand tiles, row stride LDT).
+template <typename T, int TB>
+__device__ __forceinline__ void tile_abt_acc(const T* Pt, const T* Qt,
+                                             T (&acc)[TileCfg<T, TB>::RT][TileCfg<T, TB>::RT]) {
+  constexpr int RT = TileCfg<T, TB>::RT, LDT = TileCfg<T, TB>::LDT;
+  const int tr = (threadIdx.x / 16) * RT, tc = (threadIdx.x % 16) * RT;
+#pragma unroll 4
+  for (int m = 0; m < TB; ++m) {
+    T x[RT], y[RT];
+    if constexpr (RT == 4) {
+      float4 xv = *reinterpret_cast<const float4*>(Pt + m * LDT + tr);
+      float4 yv = *reinterpret_cast<const float4*>(Qt + m * LDT + tc);
+      x[0] = xv.x; x[1] = xv.y; x[2] = xv.z; x[3] = xv.w;
+      y[0] = yv.x; y[1] = yv.y; y[2] = yv.z; y[3] = yv.w;
+    } else {
+      double2 xv = *reinterpret_cast<const double2*>(Pt + m * LDT + tr);
+      double2 yv = *reinterpret_cast<const double2*>(Qt + m * LDT + tc);
+      x[0] = xv.x; x[1] = xv.y;
+      y[0] = yv.x; y[1] = yv.y;
+    }
+#pragma unroll
+    for (int a = 0; a < RT; ++a)
+#pragma unroll
+      for (int b = 0; b < RT; ++b) acc[a][b] += x[a] * y[b];
   }
 }
 
-// TRSM: L_ik = A_ik (L_kk^-1)^T.
+// Packed tile slot of (i, k), k <= i: slot i (i + 1) / 2 + k of TB x LDT elements. Off-diagonal
+// slots hold L_ik transposed (slot[m * LDT + r] = L_ik[r][m]); diagonal slots hold
+// (L_kk^-1)^T in the same form (slot[m * LDT + c] = (L_kk^-1)[c][m]).
+__host__ __device__ __forceinline__ size_t tile_slot(int i, int k) {
+  return (size_t)i * (i + 1) / 2 + k;
+}
+
+// This thread's RT x RT block of tile (ti, tj) of A (zero outside the matrix).
 template <typename T, int TB>
-__device__ void task_trsm(T* A, const T* Dinv, int n, int i, int k, T* Pt, T* Qt) {
+__device__ __forceinline__ void load_block(const T* A, int n, int ti, int tj,
+                                           T (&v)[TileCfg<T, TB>::RT][TileCfg<T, TB>::RT]) {
   constexpr int RT = TileCfg<T, TB>::RT;
-  load_tile_t<T, TB>(A, n, i, k, Pt);
-  const T* D = Dinv + (size_t)k * TB * TB;
-  load_tile_t<T, TB>(D, TB, 0, 0, Qt);   // Qt[m][c] = Dinv[c][m]
-  __syncthreads();
-  T acc[RT][RT];
-  tile_abt_t<T, TB>(Pt, Qt, acc);
-  store_block<T, TB, false>(A, n, i, k, acc, false);
+  const int rb = ti * TB + (threadIdx.x / 16) * RT, cb = tj * TB + (threadIdx.x % 16) * RT;
+  const bool vec = rb + RT <= n && cb + RT <= n && ((n * sizeof(T)) % 16 == 0);
+#pragma unroll
+  for (int a = 0; a < RT; ++a) {
+    const T* p = A + (size_t)(rb + a) * n + cb;
+    if (vec) {
+      if constexpr (RT == 4) {
+        const float4 o = __ldcg(reinterpret_cast<const float4*>(p));
+        v[a][0] = o.x; v[a][1] = o.y; v[a][2] = o.z; v[a][3] = o.w;
+      } else {
+        const double2 o = __ldcg(reinterpret_cast<const double2*>(p));
+        v[a][0] = o.x; v[a][1] = o.y;
+      }
+    } else {
+#pragma unroll
+      for (int b = 0; b < RT; ++b)
+        v[a][b] = (rb + a < n && cb + b < n) ? ldcg(p + b) : (T)0;
+    }
+  }
 }
 
-// GEMM: A_ij -= L_ik L_jk^T.
+// Counters of a problem: [0, nt) diagonal tile done (L_kk, its inverse), [nt, nt + nt^2) tile
+// (i, k) done (i * nt + k). Task types: 0 DIAG(j), 1 OFF(i, j), i > j.
 template <typename T, int TB>
-__device__ void task_gemm(T* A, int n, int i, int j, int k, T* Pt, T* Qt) {
-  constexpr int RT = TileCfg<T, TB>::RT;
-  load_tile_t<T, TB>(A, n, i, k, Pt);
-  if (j != i) load_tile_t<T, TB>(A, n, j, k, Qt);
-  __syncthreads();
-  T acc[RT][RT];
-  tile_abt_t<T, TB>(Pt, j != i ? Qt : Pt, acc);
-  store_block<T, TB, true>(A, n, i, j, acc, i == j);
-}
-
-// counters of a problem: [0, nt) POTRF done, [nt, nt + nt^2) TRSM done (i*nt + k),
-// [nt + nt^2, nt + 2 nt^2) updates applied to tile (i, j). Task types: 0 critical task
-// (last update of (k,k), POTRF(k), TRSM(k+1,k)), 1 TRSM(i,k), 2 GEMM(i,j,k).
-template <typename T, int TB>
-__global__ __launch_bounds__(256) void k_chol_dag(const ProbDesc* const* __restrict__ descs,
+__global__ __launch_bounds__(256, 3) void k_chol_dag(const ProbDesc* const* __restrict__ descs,
                                                   int np, int nticket, int* __restrict__ head,
                                                   int* __restrict__ err,
                                                   unsigned long long budget_ns) {
-  constexpr int LDT = TileCfg<T, TB>::LDT;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T* Pt = reinterpret_cast<T*>(smraw);
-  T* Qt = Pt + TB * LDT;
-  T* Ls = Qt + TB * LDT;
-  T* Xs = Ls + TB * (TB + 1);
-  T* tmp = Xs + TB * (TB + 1);
-  __shared__ int s_t, s_ok;
+  constexpr int RT = TileCfg<T, TB>::RT, LDT = TileCfg<T, TB>::LDT, LDS = TB + 1;
+  constexpr int TILE = TB * LDT;
+  constexpr unsigned TBYTES = TILE * sizeof(T);
+  extern __shared__ __align__(128) unsigned char smraw[];
+  T* buf = reinterpret_cast<T*>(smraw);  // 4 tiles: stage 0 (P, Q), stage 1 (P, Q)
+  __shared__ unsigned long long bar[2];
+  __shared__ int s_t, s_ok, s_iss, s_dok;
+  const int tid = threadIdx.x;
+  const int tr = (tid / 16) * RT, tc = (tid % 16) * RT;
+  if (tid == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+  }
+  __syncthreads();
+  unsigned ph[2] = {0u, 0u};
   for (;;) {
-    if (threadIdx.x == 0) s_t = atomicAdd(head, 1);
+    if (tid == 0) s_t = atomicAdd(head, 1);
     __syncthreads();
     const int t = s_t;
-    if (t >= nticket) return;
+    if (t >= nticket) break;
     // ticket -> (problem, local task): problems interleaved round-robin
     const LinProblem& P = descs[t % np]->lp;
     const int local = t / np;
@@ -463,58 +502,174 @@ __global__ __launch_bounds__(256) void k_chol_dag(const ProbDesc* const* __restr
     }
     const int4 tk = P.tasks[local];
 #if defined(DS_TASK_TRACE)
-    if (threadIdx.x == 0) ds_trace_mark(t, 0);
+    if (tid == 0) ds_trace_mark(t, 0);
 #endif
-    const int type = tk.y & 15, k = tk.y >> 4, i = tk.z, j = tk.w;
-    const int nt = P.nt;
+    const bool diag = (tk.y & 15) == 0;
+    const int i = tk.z, j = tk.w, nt = P.nt, n = P.n;
     int* pdone = P.cnt;
     int* tdone = P.cnt + nt;
-    int* upd = P.cnt + nt + nt * nt;
     T* A = (T*)P.A;
-    T* Dinv = (T*)P.Dinv;
-    if (threadIdx.x == 0) {
-      bool ok = true;
-      if (type == 0) {
-        if (k >= 1)
-          ok = wait_ge(&upd[k * nt + k], k - 1, err, budget_ns) &&
-               wait_ge(&tdone[k * nt + k - 1], 1, err, budget_ns);
-      } else if (type == 1) {
-        ok = wait_ge(&pdone[k], 1, err, budget_ns) && wait_ge(&upd[i * nt + k], k, err, budget_ns);
-      } else {
-        ok = wait_ge(&tdone[i * nt + k], 1, err, budget_ns) &&
-             wait_ge(&tdone[j * nt + k], 1, err, budget_ns) &&
-             wait_ge(&upd[i * nt + j], k, err, budget_ns);
+    T* Lp = (T*)P.Lp;
+    const T* Li = Lp + tile_slot(i, 0) * TILE;   // row panel i (slots (i, 0..i))
+    const T* Lj = Lp + tile_slot(j, 0) * TILE;
+    auto ready = [&](int k) {
+      const volatile int* f = tdone;
+      return f[i * nt + k] >= 1 && (diag || f[j * nt + k] >= 1);
+    };
+    auto wait_deps = [&](int k) {
+      return wait_ge(&tdone[i * nt + k], 1, err, budget_ns) &&
+             (diag || wait_ge(&tdone[j * nt + k], 1, err, budget_ns));
+    };
+    auto issue = [&](int k, int s) {
+      __threadfence();
+      fence_proxy_async_global();
+      T* dst = buf + 2 * s * TILE;
+      mbar_expect(&bar[s], diag ? TBYTES : 2 * TBYTES);
+      bulk_load(dst, Li + (size_t)k * TILE, TBYTES, &bar[s]);
+      if (!diag) bulk_load(dst + TILE, Lj + (size_t)k * TILE, TBYTES, &bar[s]);
+    };
+
+    // ---- C = A_ij - sum_{k < j} L_ik L_jk^T, streamed through two stages of packed tiles
+    T acc[RT][RT];
+#pragma unroll
+    for (int a = 0; a < RT; ++a)
+#pragma unroll
+      for (int b = 0; b < RT; ++b) acc[a][b] = (T)0;
+    const int K = j;
+    if (tid == 0) {
+      s_ok = *(volatile int*)err == 0;
+      if (K > 0 && s_ok) {
+        s_ok = wait_deps(0);
+        if (s_ok) issue(0, 0);
       }
-      __threadfence();
-      s_ok = ok;
     }
     __syncthreads();
+    bool ok = s_ok;
+    for (int k = 0; k < K && ok; ++k) {
+      const int s = k & 1;
+      if (tid == 0) {
+        s_iss = 0;
+        if (k + 1 < K && ready(k + 1)) {
+          issue(k + 1, s ^ 1);
+          s_iss = 1;
+        }
+      }
+      const bool got = mbar_wait(&bar[s], ph[s], err, budget_ns);
+      ph[s] ^= 1u;
+      if (__syncthreads_or(!got)) {
+        // a copy did not complete in time: let any copy in flight land, then leave
+        if (tid == 0) s_ok = 0;
+        mbar_wait(&bar[s ^ 1], ph[s ^ 1], err, budget_ns);
+        return;
+      }
+      const T* Pt = buf + 2 * s * TILE;
+      tile_abt_acc<T, TB>(Pt, diag ? Pt : Pt + TILE, acc);
+      if (tid == 0 && k + 1 < K && !s_iss) {
+        s_ok = wait_deps(k + 1);
+        if (s_ok) issue(k + 1, s ^ 1);
+      }
+      __syncthreads();
+      ok = s_ok;
+    }
 #if defined(DS_TASK_TRACE)
-    if (threadIdx.x == 0) ds_trace_mark(t, 1);
+    if (tid == 0) ds_trace_mark(t, 1);
 #endif
-    if (s_ok) {
-      if (type == 0)
-        task_crit<T, TB>(A, Dinv, P.n, nt, k, P.status, Pt, Qt, Ls, Xs, tmp, &pdone[k],
-                         k + 1 < nt ? &upd[(k + 1) * nt + k] : nullptr, err, budget_ns, &s_ok);
-      else if (type == 1)
-        task_trsm<T, TB>(A, Dinv, P.n, i, k, Pt, Qt);
-      else
-        task_gemm<T, TB>(A, P.n, i, j, k, Pt, Qt);
+
+    if (ok) {
+      T* Ls = buf;                 // the stage buffers are free again
+      T* Xs = Ls + TB * LDS;
+      T* tmp = Xs + TB * LDS;
+      if (diag) {
+        // ---- DIAG(j): L_jj = chol(C), X = L_jj^-1; identity padding past n
+        const int r0 = j * TB;
+        T v[RT][RT];
+        load_block<T, TB>(A, n, j, j, v);
+#pragma unroll
+        for (int a = 0; a < RT; ++a)
+#pragma unroll
+          for (int b = 0; b < RT; ++b) {
+            const int r = tr + a, c = tc + b;
+            T x;
+            if (r0 + r < n && r0 + c < n)
+              x = c <= r ? v[a][b] - acc[a][b] : (T)0;
+            else
+              x = (r == c) ? (T)1 : (T)0;
+            Ls[r * LDS + c] = x;
+            Xs[r * LDS + c] = (r == c) ? (T)1 : (T)0;
+          }
+        __syncthreads();
+        potrf_blocked<T, TB>(Ls, Xs, tmp, r0, P.status);
+        // L_jj -> A (lower), X -> Dinv (row-major, for the solves) and X^T -> packed slot
+        T* D = (T*)P.Dinv + (size_t)j * TB * TB;
+        T* S = Lp + tile_slot(j, j) * TILE;
+        for (int e = tid; e < TB * TB; e += blockDim.x) {
+          const int r = e / TB, c = e % TB;
+          __stcg(D + e, c <= r ? Xs[r * LDS + c] : (T)0);
+          __stcg(S + r * LDT + c, c >= r ? Xs[c * LDS + r] : (T)0);
+          if (c <= r && r0 + r < n) __stcg(A + (size_t)(r0 + r) * n + r0 + c, Ls[r * LDS + c]);
+        }
+      } else {
+        // ---- OFF(i, j): L_ij = C (L_jj^-1)^T
+        T v[RT][RT];
+        load_block<T, TB>(A, n, i, j, v);
+        T* Ct = buf;                // C^T
+        T* Dt = buf + TILE;         // (L_jj^-1)^T, packed
+        if (tid == 0) {
+          s_dok = wait_ge(&pdone[j], 1, err, budget_ns);
+          if (s_dok) {
+            __threadfence();
+            fence_proxy_async_global();
+            mbar_expect(&bar[0], TBYTES);
+            bulk_load(Dt, Lp + tile_slot(j, j) * TILE, TBYTES, &bar[0]);
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < RT; ++a)
+#pragma unroll
+          for (int b = 0; b < RT; ++b) Ct[(tc + b) * LDT + tr + a] = v[a][b] - acc[a][b];
+        __syncthreads();
+        if (s_dok) {
+          const bool got = mbar_wait(&bar[0], ph[0], err, budget_ns);
+          ph[0] ^= 1u;
+          if (__syncthreads_or(!got)) return;
+#pragma unroll
+          for (int a = 0; a < RT; ++a)
+#pragma unroll
+            for (int b = 0; b < RT; ++b) acc[a][b] = (T)0;
+          tile_abt_acc<T, TB>(Ct, Dt, acc);
+          store_block<T, TB, false>(A, n, i, j, acc, false);
+          // L_ij^T -> packed slot, staged in shared memory for coalesced stores
+          T* St = buf + 2 * TILE;
+#pragma unroll
+          for (int a = 0; a < RT; ++a)
+#pragma unroll
+            for (int b = 0; b < RT; ++b) St[(tc + b) * LDT + tr + a] = acc[a][b];
+          __syncthreads();
+          T* S = Lp + tile_slot(i, j) * TILE;
+          constexpr int VE = 16 / sizeof(T);
+          for (int e = tid; e < TILE / VE; e += blockDim.x) {
+            if constexpr (VE == 4)
+              __stcg(reinterpret_cast<float4*>(S) + e, reinterpret_cast<const float4*>(St)[e]);
+            else
+              __stcg(reinterpret_cast<double2*>(S) + e, reinterpret_cast<const double2*>(St)[e]);
+          }
+        }
+      }
     }
+    // generic shared writes above happen before the next task's bulk copies into the same bytes
+    fence_proxy_async_shared();
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       __threadfence();
+      fence_proxy_async_global();
 #if defined(DS_TASK_TRACE)
       ds_trace_mark(t, 2);
 #endif
-      if (type == 0) {
-        atomicExch(&pdone[k], 1);  // already published mid-task unless the task was skipped
-        if (k + 1 < nt) atomicExch(&tdone[(k + 1) * nt + k], 1);
-      } else if (type == 1) {
-        atomicExch(&tdone[i * nt + k], 1);
-      } else {
-        atomicExch(&upd[i * nt + j], k + 1);
-      }
+      // published even when skipped after an error, so that no task waits on it
+      if (diag)
+        atomicExch(&pdone[j], 1);
+      else
+        atomicExch(&tdone[i * nt + j], 1);
     }
   }
 }
@@ -712,6 +867,14 @@ int chol_tile() {
 template int chol_tile<float>();
 template int chol_tile<double>();
 
+template <typename T>
+size_t chol_packed_elems(int nt) {
+  constexpr int TB = sizeof(T) == 8 ? 32 : 64;
+  return tile_slot(nt, 0) * (size_t)TB * TileCfg<T, TB>::LDT;
+}
+template size_t chol_packed_elems<float>(int);
+template size_t chol_packed_elems<double>(int);
+
 static int g_sms = 0;
 static int num_sms() {
   if (!g_sms) {
@@ -726,8 +889,7 @@ static int num_sms() {
 template <typename T>
 void launch_chol_dag(const BatchTabs& B, cudaStream_t s) {
   constexpr int TB = sizeof(T) == 8 ? 32 : 64;
-  const size_t sm = 2 * sizeof(T) * TB * TileCfg<T, TB>::LDT + 2 * sizeof(T) * TB * (TB + 1) +
-                    8 * sizeof(T) * TB;
+  const size_t sm = 4 * sizeof(T) * TB * TileCfg<T, TB>::LDT;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_chol_dag<T, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

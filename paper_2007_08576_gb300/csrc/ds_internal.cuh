@@ -57,6 +57,7 @@ __host__ __device__ constexpr int kSlotPairJ(int k) {
 struct LinProblem {
   void* A;
   void* Dinv;
+  void* Lp;  // packed transposed tiles of L (and of the diagonal inverses), nt (nt + 1) / 2 slots
   int n, nt;
   int* cnt;
   int* flags;
@@ -158,6 +159,8 @@ void launch_iter_end(const BatchTabs& B, int it, bool step, cudaStream_t s);
 // chol.cu
 template <typename T>
 int chol_tile();
+template <typename T>
+size_t chol_packed_elems(int nt);  // elements of the packed L tiles of an nt x nt tile matrix
 template <typename T>
 void launch_chol_dag(const BatchTabs& B, cudaStream_t s);
 template <typename T>
