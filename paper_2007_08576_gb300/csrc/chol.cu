@@ -229,65 +229,70 @@ __device__ __forceinline__ T shfl(T v, int src) {
 
 // Cholesky of a diagonal tile in shared memory (L[r * LDS + c], lower, identity padding past the
 // matrix) together with its inverse X (lower part written in full). The tile is processed in
-// blocks of PB = 8 columns:
-//   (1) warp 0 factors the 8 x 8 diagonal block and inverts it with shuffles (lane i owns row
-//       i; no block-wide barrier inside);
+// blocks of PB = 8 columns (4 in FP64):
+//   (1) warp 0 factors the PB x PB diagonal block and inverts it in registers (each lane factors
+//       the block redundantly, lane c then solves column c of the inverse);
 //   (2) the rows below take L_rb = A_rb D^T (D = the block's inverse), one thread per row;
 //   (3) the block's rows of X left of the block: X_bc = -D sum_q L_bq X_qc;
-//   (4) the trailing lower triangle gets the rank-8 update with the new panel.
-// Three barriers per 8 columns; 256 threads (8 warps).
+//   (4) the trailing lower triangle gets the rank-PB update with the new panel.
+// Three barriers per block; 256 threads (8 warps).
 template <typename T, int TB>
 __device__ void potrf_blocked(T* L, T* X, T* tmp, int row0, double* status) {
-  constexpr int LDS = TB + 1, PB = 8, NBK = TB / PB;
+  // 8-column blocks in FP32; 4 in FP64, where the register-resident block factor would spill
+  constexpr int LDS = TB + 1, PB = sizeof(T) == 8 ? 4 : 8, NBK = TB / PB;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int kb = 0; kb < NBK; ++kb) {
     const int c0 = kb * PB;
     if (warp == 0) {
-      const int i = lane & (PB - 1);
-      T a[PB], xr[PB];
+      // every lane factors the whole 8 x 8 block in registers (no communication): left-looking
+      // column by column, l[r][j] = (a[r][j] - sum_{q<j} l[r][q] l[j][q]) / l[j][j]
+      T l[PB][PB], dinv[PB];
 #pragma unroll
-      for (int c = 0; c < PB; ++c) {
-        a[c] = (c <= i) ? L[(c0 + i) * LDS + c0 + c] : (T)0;
-        xr[c] = (c == i) ? (T)1 : (T)0;
-      }
+      for (int r = 0; r < PB; ++r)
+#pragma unroll
+        for (int c = 0; c <= r; ++c) l[r][c] = L[(c0 + r) * LDS + c0 + c];
 #pragma unroll
       for (int j = 0; j < PB; ++j) {
-        T p = shfl(a[j], j);
+        T p = l[j][j];
+#pragma unroll
+        for (int q = 0; q < j; ++q) p -= l[j][q] * l[j][q];
         if (!(p > (T)0)) {
           if (status && lane == 0)
             atomicCAS((unsigned long long*)status, 0ull,
                       __double_as_longlong((double)(row0 + c0 + j + 1)));
           p = (T)1;
         }
-        const T inv = rsqrt_newton<T>(p), d = p * inv;
-        const T lij = (i > j) ? a[j] * inv : ((i == j) ? d : (T)0);
-        a[j] = lij;
-        T xj[PB];
+        const T inv = rsqrt_newton<T>(p);
+        dinv[j] = inv;
+        l[j][j] = p * inv;
 #pragma unroll
-        for (int c = 0; c < PB; ++c) xj[c] = (c <= j) ? shfl(xr[c], j) * inv : (T)0;
-        if (i == j) {
+        for (int r = j + 1; r < PB; ++r) {
+          T v = l[r][j];
 #pragma unroll
-          for (int c = 0; c < PB; ++c)
-            if (c <= j) xr[c] = xj[c];
+          for (int q = 0; q < j; ++q) v -= l[r][q] * l[j][q];
+          l[r][j] = v * inv;
         }
+      }
+      // lane c < 8 solves column c of the inverse: x_c = 1 / l_cc,
+      // x_r = -(sum_{c <= q < r} l[r][q] x_q) / l_rr
+      const int c = lane;
+      T x[PB];
 #pragma unroll
-        for (int c = j + 1; c < PB; ++c) {
-          const T lcj = shfl(a[j], c);
-          if (i > j && c <= i) a[c] -= lij * lcj;
-        }
-        if (i > j) {
+      for (int r = 0; r < PB; ++r) {
+        T v = (T)0;
 #pragma unroll
-          for (int c = 0; c < PB; ++c)
-            if (c <= j) xr[c] -= lij * xj[c];
-        }
+        for (int q = 0; q < r; ++q)
+          if (q >= c) v -= l[r][q] * x[q];
+        x[r] = r == c ? dinv[r] : (r > c ? v * dinv[r] : (T)0);
       }
       if (lane < PB) {
 #pragma unroll
-        for (int c = 0; c < PB; ++c)
-          if (c <= i) {
-            L[(c0 + i) * LDS + c0 + c] = a[c];
-            X[(c0 + i) * LDS + c0 + c] = xr[c];
-          }
+        for (int r = 0; r < PB; ++r) {
+          if (r >= c) X[(c0 + r) * LDS + c0 + c] = x[r];
+#pragma unroll
+          for (int q = 0; q <= r; ++q)
+            if (r == lane) L[(c0 + r) * LDS + c0 + q] = l[r][q];
+        }
       }
     }
     __syncthreads();
@@ -305,13 +310,15 @@ __device__ void potrf_blocked(T* L, T* X, T* tmp, int row0, double* status) {
       }
     }
     // (3a) tmp[m][c] = sum_{q = c}^{c0 - 1} L[c0 + m][q] X[q][c]   (warp m, lanes over c)
-    for (int c = lane; c < c0; c += 32) {
-      T s = (T)0;
-      for (int q = c; q < c0; ++q) s += L[(c0 + warp) * LDS + q] * X[q * LDS + c];
-      tmp[warp * TB + c] = s;
-    }
+    if (warp < PB)
+      for (int c = lane; c < c0; c += 32) {
+        T s = (T)0;
+#pragma unroll 4
+        for (int q = c; q < c0; ++q) s += L[(c0 + warp) * LDS + q] * X[q * LDS + c];
+        tmp[warp * TB + c] = s;
+      }
     __syncthreads();
-    // (4) rank-8 update of the trailing lower triangle
+    // (4) rank-PB update of the trailing lower triangle
     for (int r = c0 + PB + warp; r < TB; r += 8)
       for (int c = c0 + PB + lane; c <= r; c += 32) {
         T s = (T)0;
@@ -320,34 +327,204 @@ __device__ void potrf_blocked(T* L, T* X, T* tmp, int row0, double* status) {
         L[r * LDS + c] -= s;
       }
     // (3b) X[c0 + i][c] = -sum_m D[i][m] tmp[m][c]   (warp i, lanes over c)
-    for (int c = lane; c < c0; c += 32) {
-      T s = (T)0;
+    if (warp < PB)
+      for (int c = lane; c < c0; c += 32) {
+        T s = (T)0;
 #pragma unroll
-      for (int m = 0; m < PB; ++m)
-        if (m <= warp) s += X[(c0 + warp) * LDS + c0 + m] * tmp[m * TB + c];
-      X[(c0 + warp) * LDS + c] = -s;
-    }
+        for (int m = 0; m < PB; ++m)
+          if (m <= warp) s += X[(c0 + warp) * LDS + c0 + m] * tmp[m * TB + c];
+        X[(c0 + warp) * LDS + c] = -s;
+      }
     __syncthreads();
   }
 }
 
-// Loads this thread's RT x RT block of tile (k, k) (lower part; identity padding past n).
-template <typename T, int TB>
-__device__ __forceinline__ void load_diag_block(const T* A, int n, int k,
-                                                T (&a)[TileCfg<T, TB>::RT][TileCfg<T, TB>::RT]) {
-  constexpr int RT = TileCfg<T, TB>::RT;
-  const int tr = (threadIdx.x / 16) * RT, tc = (threadIdx.x % 16) * RT;
-  const int r0 = k * TB;
+// One doubling level of a lower-triangular inverse held in shared memory (row stride TB + 1,
+// zeros above the diagonal): for every pair of H x H diagonal blocks starting at s0 = 2 H g,
+// Tm = L21 X11 and X21 = -X22 Tm, with L21 = L[s0 + H.., s0..], X11 / X22 the diagonal blocks.
+// Each thread forms K consecutive outputs of a row (K = 1..4) with the shared row operand reused.
+template <typename T, int TB, int H>
+__device__ __forceinline__ void inverse_level(const T* L, T* X, T* Tm) {
+  constexpr int LDS = TB + 1, TOTAL = TB * H / 2;
+  constexpr int K = TOTAL >= 1024 ? 4 : (TOTAL >= 512 ? 2 : 1);
+  constexpr int NT = TOTAL / K;   // working threads
+  const int tid = threadIdx.x;
+  if (tid < NT) {
+    const int e = tid * K, g = e / (H * H), r = (e % (H * H)) / H, c = e % H, s0 = 2 * H * g;
+    T v[K];
 #pragma unroll
-  for (int p = 0; p < RT; ++p)
+    for (int k = 0; k < K; ++k) v[k] = (T)0;
 #pragma unroll
-    for (int q = 0; q < RT; ++q) {
-      const int r = tr + p, cc = tc + q;
-      if (r0 + r < n && r0 + cc < n)
-        a[p][q] = cc <= r ? ldcg(A + (size_t)(r0 + r) * n + r0 + cc) : (T)0;
-      else
-        a[p][q] = (r == cc) ? (T)1 : (T)0;
+    for (int m = 0; m < H; ++m) {
+      const T l = L[(s0 + H + r) * LDS + s0 + m];
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[k] += l * X[(s0 + m) * LDS + s0 + c + k];
     }
+#pragma unroll
+    for (int k = 0; k < K; ++k) Tm[e + k] = v[k];
+  }
+  __syncthreads();
+  if (tid < NT) {
+    const int e = tid * K, g = e / (H * H), r = (e % (H * H)) / H, c = e % H, s0 = 2 * H * g;
+    T v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = (T)0;
+#pragma unroll
+    for (int m = 0; m < H; ++m) {
+      const T xv = X[(s0 + H + r) * LDS + s0 + H + m];
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[k] += xv * Tm[g * H * H + m * H + c + k];
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) X[(s0 + H + r) * LDS + s0 + c + k] = -v[k];
+  }
+  __syncthreads();
+}
+
+// Register-blocked Cholesky of a diagonal tile with its inverse. Thread (ty, tx) = (tid / 16,
+// tid % 16) holds a[p][q] = C[ty RT + p][tx RT + q] (lower part used; identity padding past the
+// matrix). Columns are taken in blocks of PB = 2 RT; the PB x PB diagonal block kb is held by four
+// threads of warp kb, so
+//   (1) warp kb gathers the block in shared memory, every lane factors it in registers and lane c
+//       solves column c of its inverse D (no block-wide barrier);
+//   (2) the two threads holding each RT-row slice of the panel below exchange their halves with a
+//       shuffle and form L_rb = A_rb D^T, published transposed for the update;
+//   (4) every thread right of the panel subtracts the rank-PB product from its registers.
+// Two barriers per block. The inverse's off-diagonal blocks then follow by recursive doubling,
+// X21 = -X22 (L21 X11), for h = PB, 2 PB, 4 PB (two barriers per level). Output: L (lower part)
+// and X = L^-1 in shared memory with row stride TB + 1; X must be zero on entry. Scratch: Pt
+// (PB x (TB + 16 / sizeof(T))), Dsm (PB x PB), Tm (TB x TB / 4).
+template <typename T, int TB>
+__device__ void potrf_regs(T (&a)[TileCfg<T, TB>::RT][TileCfg<T, TB>::RT], T* L, T* X, T* Pt,
+                           T* Dsm, T* Tm, int row0, double* status) {
+  constexpr int RT = TileCfg<T, TB>::RT, PB = 2 * RT, NBK = TB / PB, LDS = TB + 1;
+  constexpr int LDP = TileCfg<T, TB>::LDT;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ty = tid / 16, tx = tid % 16, tr = ty * RT, tc = tx * RT;
+  for (int kb = 0; kb < NBK; ++kb) {
+    const int c0 = kb * PB;
+    if (warp == kb) {
+      if ((tx >> 1) == kb) {
+#pragma unroll
+        for (int p = 0; p < RT; ++p)
+#pragma unroll
+          for (int q = 0; q < RT; ++q)
+            if (tc + q <= tr + p) L[(tr + p) * LDS + tc + q] = a[p][q];
+      }
+      __syncwarp();
+      T l[PB][PB], dinv[PB];
+#pragma unroll
+      for (int r = 0; r < PB; ++r)
+#pragma unroll
+        for (int c = 0; c <= r; ++c) l[r][c] = L[(c0 + r) * LDS + c0 + c];
+#pragma unroll
+      for (int j = 0; j < PB; ++j) {
+        T piv = l[j][j];
+#pragma unroll
+        for (int q = 0; q < j; ++q) piv -= l[j][q] * l[j][q];
+        if (!(piv > (T)0)) {
+          if (status && lane == 0)
+            atomicCAS((unsigned long long*)status, 0ull,
+                      __double_as_longlong((double)(row0 + c0 + j + 1)));
+          piv = (T)1;
+        }
+        const T inv = rsqrt_newton<T>(piv);
+        dinv[j] = inv;
+        l[j][j] = piv * inv;
+#pragma unroll
+        for (int r = j + 1; r < PB; ++r) {
+          T v = l[r][j];
+#pragma unroll
+          for (int q = 0; q < j; ++q) v -= l[r][q] * l[j][q];
+          l[r][j] = v * inv;
+        }
+      }
+      // lane c < PB: column c of the inverse, x_c = 1 / l_cc, x_r = -(sum_{c<=q<r} l_rq x_q) / l_rr
+      const int c = lane;
+      T x[PB];
+#pragma unroll
+      for (int r = 0; r < PB; ++r) {
+        T v = (T)0;
+#pragma unroll
+        for (int q = 0; q < r; ++q) v -= (q >= c ? l[r][q] : (T)0) * x[q];
+        x[r] = r == c ? dinv[r] : (r > c ? v * dinv[r] : (T)0);
+      }
+      __syncwarp();
+      // lane q writes column q of L's block (values picked by select, no divergent branches)
+#pragma unroll
+      for (int r = 0; r < PB; ++r) {
+        T v = l[r][0];
+#pragma unroll
+        for (int q = 1; q <= r; ++q) v = lane == q ? l[r][q] : v;
+        if (lane <= r) L[(c0 + r) * LDS + c0 + lane] = v;
+      }
+      if (lane < PB) {
+#pragma unroll
+        for (int r = 0; r < PB; ++r) {
+          X[(c0 + r) * LDS + c0 + c] = x[r];
+          Dsm[r * PB + c] = x[r];
+        }
+      }
+    }
+    __syncthreads();
+    // (2) panel below the block: threads tx = 2 kb, 2 kb + 1 (adjacent lanes), rows past the block
+    if ((tx >> 1) == kb && tr >= c0 + PB) {
+      const unsigned pair = 3u << (lane & 30);
+      const int half = tx & 1;
+      T row[RT][PB];
+#pragma unroll
+      for (int p = 0; p < RT; ++p)
+#pragma unroll
+        for (int q = 0; q < RT; ++q) {
+          const T other = __shfl_xor_sync(pair, a[p][q], 1);
+          row[p][q] = half ? other : a[p][q];
+          row[p][RT + q] = half ? a[p][q] : other;
+        }
+#pragma unroll
+      for (int q = 0; q < RT; ++q) {
+        const int qg = half * RT + q;
+        T d[PB];
+#pragma unroll
+        for (int m = 0; m < PB; ++m) d[m] = m <= qg ? Dsm[qg * PB + m] : (T)0;
+#pragma unroll
+        for (int p = 0; p < RT; ++p) {
+          T v = (T)0;
+#pragma unroll
+          for (int m = 0; m < PB; ++m) v += row[p][m] * d[m];
+          L[(tr + p) * LDS + c0 + qg] = v;
+          Pt[qg * LDP + tr + p] = v;
+        }
+      }
+    }
+    __syncthreads();
+    // (4) rank-PB update of the register blocks right of the panel (lower part)
+    if (tc >= c0 + PB && tc <= tr + RT - 1) {
+#pragma unroll
+      for (int m = 0; m < PB; ++m) {
+        T xv[RT], yv[RT];
+        if constexpr (RT == 4) {
+          const float4 u = *reinterpret_cast<const float4*>(Pt + m * LDP + tr);
+          const float4 w = *reinterpret_cast<const float4*>(Pt + m * LDP + tc);
+          xv[0] = u.x; xv[1] = u.y; xv[2] = u.z; xv[3] = u.w;
+          yv[0] = w.x; yv[1] = w.y; yv[2] = w.z; yv[3] = w.w;
+        } else {
+          const double2 u = *reinterpret_cast<const double2*>(Pt + m * LDP + tr);
+          const double2 w = *reinterpret_cast<const double2*>(Pt + m * LDP + tc);
+          xv[0] = u.x; xv[1] = u.y;
+          yv[0] = w.x; yv[1] = w.y;
+        }
+#pragma unroll
+        for (int p = 0; p < RT; ++p)
+#pragma unroll
+          for (int q = 0; q < RT; ++q) a[p][q] -= xv[p] * yv[q];
+      }
+    }
+  }
+  // off-diagonal blocks of the inverse by recursive doubling (X zero above the diagonal)
+  inverse_level<T, TB, PB>(L, X, Tm);
+  inverse_level<T, TB, 2 * PB>(L, X, Tm);
+  inverse_level<T, TB, 4 * PB>(L, X, Tm);
+  static_assert(8 * PB == TB, "three doubling levels");
 }
 
 // ----------------------------------------------------------------------------- factorisation
@@ -468,8 +645,11 @@ __device__ __forceinline__ void load_block(const T* A, int n, int ti, int tj,
 
 // Counters of a problem: [0, nt) diagonal tile done (L_kk, its inverse), [nt, nt + nt^2) tile
 // (i, k) done (i * nt + k). Task types: 0 DIAG(j), 1 OFF(i, j), i > j.
+#ifndef DS_CHOL_CTAS_PER_SM
+#define DS_CHOL_CTAS_PER_SM 3  // register budget: 3 CTAs of 256 threads per SM
+#endif
 template <typename T, int TB>
-__global__ __launch_bounds__(256, 3) void k_chol_dag(const ProbDesc* const* __restrict__ descs,
+__global__ __launch_bounds__(256, DS_CHOL_CTAS_PER_SM) void k_chol_dag(const ProbDesc* const* __restrict__ descs,
                                                   int np, int nticket, int* __restrict__ head,
                                                   int* __restrict__ err,
                                                   unsigned long long budget_ns) {
@@ -578,9 +758,11 @@ __global__ __launch_bounds__(256, 3) void k_chol_dag(const ProbDesc* const* __re
     if (ok) {
       T* Ls = buf;                 // the stage buffers are free again
       T* Xs = Ls + TB * LDS;
-      T* tmp = Xs + TB * LDS;
       if (diag) {
         // ---- DIAG(j): L_jj = chol(C), X = L_jj^-1; identity padding past n
+        T* Pt = Xs + TB * LDS;
+        T* Dsm = Pt + 2 * RT * LDT;
+        T* Tm = Dsm + 4 * RT * RT;
         const int r0 = j * TB;
         T v[RT][RT];
         load_block<T, TB>(A, n, j, j, v);
@@ -589,16 +771,14 @@ __global__ __launch_bounds__(256, 3) void k_chol_dag(const ProbDesc* const* __re
 #pragma unroll
           for (int b = 0; b < RT; ++b) {
             const int r = tr + a, c = tc + b;
-            T x;
-            if (r0 + r < n && r0 + c < n)
-              x = c <= r ? v[a][b] - acc[a][b] : (T)0;
-            else
-              x = (r == c) ? (T)1 : (T)0;
-            Ls[r * LDS + c] = x;
-            Xs[r * LDS + c] = (r == c) ? (T)1 : (T)0;
+            v[a][b] = (r0 + r < n && r0 + c < n) ? v[a][b] - acc[a][b] : (r == c ? (T)1 : (T)0);
           }
+        for (int e = tid; e < TB * LDS; e += blockDim.x) Xs[e] = (T)0;
         __syncthreads();
-        potrf_blocked<T, TB>(Ls, Xs, tmp, r0, P.status);
+        potrf_regs<T, TB>(v, Ls, Xs, Pt, Dsm, Tm, r0, P.status);
+#if defined(DS_TASK_TRACE)
+        if (tid == 0) ds_trace_mark(t, 3);
+#endif
         // L_jj -> A (lower), X -> Dinv (row-major, for the solves) and X^T -> packed slot
         T* D = (T*)P.Dinv + (size_t)j * TB * TB;
         T* S = Lp + tile_slot(j, j) * TILE;

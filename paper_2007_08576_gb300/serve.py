@@ -69,7 +69,9 @@ def stream_bytes(W: int, H: int, N: int, M: int, precision: int) -> int:
     b += n * (8 * 3 + 8 * 3 + 4)                        # vectors
     tb = 32 if precision == 0 else 64
     nt = (n + tb - 1) // tb
-    b += 4 * (nt + 2 * nt * nt) + 8 * nt * tb * tb
+    tsz = 8 if precision == 0 else 4
+    b += 4 * (nt + 2 * nt * nt) + tsz * nt * tb * tb
+    b += tsz * nt * (nt + 1) // 2 * tb * (tb + 16 // tsz)   # packed factor tiles
     b += nt * (nt + 1) // 2 * 16 * 2                    # task list
     b += M * (4 + 12 + 4 + 4) + M * 64 * (7 * 8 + 4)    # matches and RANSAC scratch
     return int(b)
