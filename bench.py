@@ -353,8 +353,8 @@ def run_gpu(args):
             "metric": METRIC, "value": round(value, 3), "unit": "frames/s", "n_gpus": world,
             "steps": K, "warmup": W, "ms_per_step": round(float(total_s * 1e3 / K), 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f32 residuals/J^T J, f64 Cholesky+refine",
-                      "fp32": "f32", "fp32_refine": "f32 J^T J + Cholesky, f64 refine residuals"}[args.precision],
+            "dtype": {"fp64": "f32 residuals/J^T J, f64 Cholesky, double-f32 refine residuals",
+                      "fp32": "f32", "fp32_refine": "f32 J^T J + Cholesky, double-f32 (48-bit) refine residuals"}[args.precision],
             "data": "synthetic (seeded heightfield + deformation + camera motion, ray-cast depth)",
             "config": {"workload": WORKLOAD, "template": "320x240", "control_points": N,
                        "matches": M, "gn_iters": ITERS, "precision": args.precision,

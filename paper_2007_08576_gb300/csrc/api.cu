@@ -121,6 +121,7 @@ struct ds_ctx {
   double* d_b = nullptr;
   double* d_x = nullptr;
   double* d_r = nullptr;
+  float2* d_xf = nullptr;
   void* d_v1 = nullptr;
   void* d_v2 = nullptr;
   void* d_v3 = nullptr;
@@ -197,7 +198,7 @@ void free_cp(ds_ctx* h) {
   dfree(h->d_pn); dfree(h->d_tp); dfree(h->d_tw); dfree(h->d_rank); dfree(h->d_seg);
   dfree(h->d_segbp); dfree(h->d_rowptr); dfree(h->d_rowcol); dfree(h->d_rowbp);
   dfree(h->d_A32); dfree(h->d_A64); dfree(h->d_Af32); dfree(h->d_Dinv); dfree(h->d_blk);
-  dfree(h->d_gdata); dfree(h->d_b); dfree(h->d_x); dfree(h->d_r); dfree(h->d_v1);
+  dfree(h->d_gdata); dfree(h->d_b); dfree(h->d_x); dfree(h->d_r); dfree(h->d_xf); dfree(h->d_v1);
   dfree(h->d_v2); dfree(h->d_v3); dfree(h->d_lcnt); dfree(h->d_lflags); dfree(h->d_tasks);
   dfree(h->d_Lp);
   dfree(h->d_desc);
@@ -290,6 +291,16 @@ void make_chol_tasks(int nt, std::vector<int4>& out) {
   }
 }
 
+// Claim order of the factorisation tickets of a batch: problems interleaved round-robin, each
+// problem's tasks in their own (topological) order, so every task waits only on earlier tickets.
+void make_chol_tickets(const std::vector<int>& ntasks, std::vector<int2>& out) {
+  int mx = 0;
+  for (int v : ntasks) mx = std::max(mx, v);
+  for (int l = 0; l < mx; ++l)
+    for (int p = 0; p < (int)ntasks.size(); ++p)
+      if (l < ntasks[p]) out.push_back(make_int2(p, l));
+}
+
 // Events recorded while the stream is captured become event-record nodes of the graph only with
 // cudaEventRecordExternal (a plain record is a capture-internal dependency marker).
 void trace(ds_batch_s* b, int it, int k) {
@@ -334,7 +345,8 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   b->refine_steps = steps;
   b->stream = stream;
   b->own_stream = own;
-  std::vector<int2> icp, rows, nodes, vec, res;
+  std::vector<int2> icp, rows, nodes, vec, res, chol;
+  std::vector<int> ntasks(n);
   int max_tasks = 0, max_nt = 0;
   std::vector<const ProbDesc*> descs(n);
   for (int p = 0; p < n; ++p) {
@@ -345,10 +357,13 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
     for (int c = 0; c * 128 < h->N; ++c) nodes.push_back(make_int2(p, c));
     for (int c = 0; c * 256 < h->n; ++c) vec.push_back(make_int2(p, c));
     for (int c = 0; c * 8 < h->n; ++c) res.push_back(make_int2(p, c));
+    ntasks[p] = h->ntasks;
     max_tasks = std::max(max_tasks, h->ntasks);
     max_nt = std::max(max_nt, h->nt);
   }
-  const size_t ntab = icp.size() + rows.size() + nodes.size() + vec.size() + res.size();
+  make_chol_tickets(ntasks, chol);
+  const size_t ntab =
+      icp.size() + rows.size() + nodes.size() + vec.size() + res.size() + chol.size();
   int rc;
   if ((rc = dalloc(&b->d_descs, n)) || (rc = dalloc(&b->d_tab, ntab)) ||
       (rc = dalloc(&b->d_words, 8))) {
@@ -357,7 +372,8 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   }
   std::vector<int2> all;
   all.reserve(ntab);
-  for (auto* v : {&icp, &rows, &nodes, &vec, &res}) all.insert(all.end(), v->begin(), v->end());
+  for (auto* v : {&icp, &rows, &nodes, &vec, &res, &chol})
+    all.insert(all.end(), v->begin(), v->end());
   cudaMemcpy(b->d_descs, descs.data(), sizeof(void*) * n, cudaMemcpyHostToDevice);
   cudaMemcpy(b->d_tab, all.data(), sizeof(int2) * ntab, cudaMemcpyHostToDevice);
   cudaMemset(b->d_words, 0, sizeof(int) * 8);
@@ -370,6 +386,7 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   T.nodes = b->d_tab + off; T.n_nodes = (int)nodes.size(); off += nodes.size();
   T.vec = b->d_tab + off; T.n_vec = (int)vec.size(); off += vec.size();
   T.res = b->d_tab + off; T.n_res = (int)res.size(); off += res.size();
+  T.chol = b->d_tab + off; T.n_chol = (int)chol.size(); off += chol.size();
   T.orb_ctas = 16;
   T.max_tasks = max_tasks;
   T.max_nt = max_nt;
@@ -785,6 +802,7 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
       (rc = dalloc(&h->d_rowbp, h->nbp)) || (rc = dalloc(&h->d_A32, nn)) ||
       (rc = dalloc(&h->d_blk, 36 * (size_t)h->nbp)) || (rc = dalloc(&h->d_gdata, n)) ||
       (rc = dalloc(&h->d_b, n)) || (rc = dalloc(&h->d_x, n)) || (rc = dalloc(&h->d_r, n)) ||
+      (rc = dalloc(&h->d_xf, n)) ||
       (rc = dalloc((char**)&h->d_v1, tsz * n)) || (rc = dalloc((char**)&h->d_v2, tsz * n)) ||
       (rc = dalloc((char**)&h->d_v3, tsz * n)) ||
       (rc = dalloc((char**)&h->d_Dinv, tsz * (size_t)nt * TB * TB)) ||
@@ -862,6 +880,7 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
     D.b = h->d_b;
     D.x = h->d_x;
     D.r = h->d_r;
+    D.xf = h->d_xf;
     LinProblem& lp = D.lp;
     lp.A = prec == DS_PREC_FP64 ? (void*)h->d_A64
                                 : (prec == DS_PREC_FP32_REFINE ? (void*)h->d_Af32 : (void*)h->d_A32);

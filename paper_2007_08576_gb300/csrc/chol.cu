@@ -649,10 +649,9 @@ __device__ __forceinline__ void load_block(const T* A, int n, int ti, int tj,
 #define DS_CHOL_CTAS_PER_SM 3  // register budget: 3 CTAs of 256 threads per SM
 #endif
 template <typename T, int TB>
-__global__ __launch_bounds__(256, DS_CHOL_CTAS_PER_SM) void k_chol_dag(const ProbDesc* const* __restrict__ descs,
-                                                  int np, int nticket, int* __restrict__ head,
-                                                  int* __restrict__ err,
-                                                  unsigned long long budget_ns) {
+__global__ __launch_bounds__(256, DS_CHOL_CTAS_PER_SM) void k_chol_dag(
+    const ProbDesc* const* __restrict__ descs, const int2* __restrict__ tickets, int nticket,
+    int* __restrict__ head, int* __restrict__ err, unsigned long long budget_ns) {
   constexpr int RT = TileCfg<T, TB>::RT, LDT = TileCfg<T, TB>::LDT, LDS = TB + 1;
   constexpr int TILE = TB * LDT;
   constexpr unsigned TBYTES = TILE * sizeof(T);
@@ -673,14 +672,10 @@ __global__ __launch_bounds__(256, DS_CHOL_CTAS_PER_SM) void k_chol_dag(const Pro
     __syncthreads();
     const int t = s_t;
     if (t >= nticket) break;
-    // ticket -> (problem, local task): problems interleaved round-robin
-    const LinProblem& P = descs[t % np]->lp;
-    const int local = t / np;
-    if (local >= P.ntasks) {
-      __syncthreads();
-      continue;
-    }
-    const int4 tk = P.tasks[local];
+    // ticket -> (problem, task); each problem's tasks appear in their own order
+    const int2 pt = tickets[t];
+    const LinProblem& P = descs[pt.x]->lp;
+    const int4 tk = P.tasks[pt.y];
 #if defined(DS_TASK_TRACE)
     if (tid == 0) ds_trace_mark(t, 0);
 #endif
@@ -1080,9 +1075,8 @@ void launch_chol_dag(const BatchTabs& B, cudaStream_t s) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_dag<T, TB>, 256, sm);
     per_sm = std::max(1, std::min(per_sm, 4));
   }
-  const int nticket = B.P * B.max_tasks;
-  const int grid = std::min(nticket, per_sm * num_sms());
-  k_chol_dag<T, TB><<<grid, 256, sm, s>>>(B.d, B.P, nticket, B.words + 0, B.words + 5,
+  const int grid = std::min(B.n_chol, per_sm * num_sms());
+  k_chol_dag<T, TB><<<grid, 256, sm, s>>>(B.d, B.chol, B.n_chol, B.words + 0, B.words + 5,
                                           2000000000ull);
   ++g_launches;
 }
@@ -1126,7 +1120,10 @@ __global__ void k_vec_out(const ProbDesc* const* __restrict__ descs, const int2*
   const int i = w.y * 256 + threadIdx.x;
   if (i < D.n) {
     const double v = (double)((const T*)D.lp.x)[i];
-    D.x[i] = assign ? v : D.x[i] + v;
+    const double xi = assign ? v : D.x[i] + v;
+    D.x[i] = xi;
+    const float hi = __double2float_rn(xi);
+    D.xf[i] = make_float2(hi, __double2float_rn(xi - (double)hi));
   }
 }
 template <typename T>
@@ -1135,8 +1132,23 @@ void launch_vec_out(const BatchTabs& B, bool assign, cudaStream_t s) {
   ++g_launches;
 }
 
-// r = b - A x with A the full symmetric FP32 matrix, accumulated in FP64; one warp per row,
-// (problem, 8-row chunk) per CTA.
+// r = b - A x with A the full symmetric FP32 matrix and x = hi + lo (two floats, written with x):
+// each product a x_hi is split exactly with an FMA (a x_hi = p + e), a x_lo is added to the error
+// term, and the sum is kept as an unevaluated pair of floats (two-sum), i.e. about 48 significant
+// bits, the precision of FP64 accumulation for these sums, at FP32 instruction rates (the FP64
+// pipe of this GPU is 1/64 of FP32). One warp per row, (problem, 8-row chunk) per CTA.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void df_add_term(float a, float2 x, float& sh, float& sl) {
+  const float p = __fmul_rn(a, x.x);
+  const float t = __fmaf_rn(a, x.y, __fmaf_rn(a, x.x, -p));  // (a x_hi - p) + a x_lo
+  float e;
+  two_sum(sh, p, sh, e);
+  sl = __fadd_rn(sl, __fadd_rn(e, t));
+}
 __global__ __launch_bounds__(256) void k_residual64(const ProbDesc* const* __restrict__ descs,
                                                     const int2* __restrict__ tab) {
   const int2 w = tab[blockIdx.x];
@@ -1145,11 +1157,27 @@ __global__ __launch_bounds__(256) void k_residual64(const ProbDesc* const* __res
   const int row = w.y * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (row >= n) return;
   const float* a = D.Aref + (size_t)row * n;
-  const double* x = D.x;
-  double s = 0.0;
-  for (int j = lane; j < n; j += 32) s += (double)a[j] * x[j];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) D.r[row] = D.b[row] - s;
+  const float2* __restrict__ x = D.xf;
+  float sh = 0.f, sl = 0.f;
+  if ((n & 3) == 0) {
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    for (int q = lane; q < (n >> 2); q += 32) {
+      const float4 v = __ldcs(a4 + q);
+      df_add_term(v.x, x[4 * q], sh, sl);
+      df_add_term(v.y, x[4 * q + 1], sh, sl);
+      df_add_term(v.z, x[4 * q + 2], sh, sl);
+      df_add_term(v.w, x[4 * q + 3], sh, sl);
+    }
+  } else {
+    for (int j = lane; j < n; j += 32) df_add_term(a[j], x[j], sh, sl);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, sh, o), ol = __shfl_xor_sync(0xffffffffu, sl, o);
+    float e;
+    two_sum(sh, oh, sh, e);
+    sl = __fadd_rn(sl, __fadd_rn(ol, e));
+  }
+  if (lane == 0) D.r[row] = D.b[row] - ((double)sh + (double)sl);
 }
 
 void launch_residual64(const BatchTabs& B, cudaStream_t s) {

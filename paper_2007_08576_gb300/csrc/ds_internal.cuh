@@ -105,6 +105,7 @@ struct ProbDesc {
   double* b;
   double* x;
   double* r;
+  float2* xf;              // x as an unevaluated sum of two floats (hi, lo), for the residual
   LinProblem lp;
 };
 
@@ -143,6 +144,8 @@ struct BatchTabs {
   const int2* res;           // (problem, 8-row chunk of the refinement residual)
   int n_res;
   int orb_ctas;              // CTAs per problem of the ORB pass (grid-stride over M)
+  const int2* chol;          // (problem, task) per factorisation ticket, in claim order
+  int n_chol;
   int max_tasks;             // max factorisation tasks over the problems
   int max_nt;                // max tile rows over the problems
   int* words;                // [0] factorisation head, [1..4] solve heads, [5] timeout word
