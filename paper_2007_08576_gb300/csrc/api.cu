@@ -88,6 +88,7 @@ struct ds_ctx {
   int* d_rank = nullptr;
   int4* d_seg = nullptr;
   int* d_segbp = nullptr;
+  int* d_segstart = nullptr;
   int* d_rowptr = nullptr;
   int* d_rowcol = nullptr;
   int* d_rowbp = nullptr;
@@ -196,7 +197,7 @@ void free_cp(ds_ctx* h) {
   }
   dfree(h->d_g64); dfree(h->d_gc); dfree(h->d_q64); dfree(h->d_t64); dfree(h->d_node);
   dfree(h->d_pn); dfree(h->d_tp); dfree(h->d_tw); dfree(h->d_rank); dfree(h->d_seg);
-  dfree(h->d_segbp); dfree(h->d_rowptr); dfree(h->d_rowcol); dfree(h->d_rowbp);
+  dfree(h->d_segbp); dfree(h->d_segstart); dfree(h->d_rowptr); dfree(h->d_rowcol); dfree(h->d_rowbp);
   dfree(h->d_A32); dfree(h->d_A64); dfree(h->d_Af32); dfree(h->d_Dinv); dfree(h->d_blk);
   dfree(h->d_gdata); dfree(h->d_b); dfree(h->d_x); dfree(h->d_r); dfree(h->d_xf); dfree(h->d_v1);
   dfree(h->d_v2); dfree(h->d_v3); dfree(h->d_lcnt); dfree(h->d_lflags); dfree(h->d_tasks);
@@ -352,7 +353,7 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   for (int p = 0; p < n; ++p) {
     ds_ctx* h = hs[p];
     descs[p] = h->d_desc;
-    for (int t = 0; t * kTile < h->P; ++t) icp.push_back(make_int2(p, t));
+    for (int t = 0; t * kSegPerCta * kSegPerWarp < h->S; ++t) icp.push_back(make_int2(p, t));
     for (int i = 0; i < h->N; ++i) rows.push_back(make_int2(p, i));
     for (int c = 0; c * 128 < h->N; ++c) nodes.push_back(make_int2(p, c));
     for (int c = 0; c * 256 < h->n; ++c) vec.push_back(make_int2(p, c));
@@ -724,7 +725,7 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
   std::vector<float4> tp(P), tw(P);
   std::vector<int> rank(npx, -1);
   std::vector<int4> segn;
-  std::vector<int> segbp;
+  std::vector<int> segbp, segstart;
   std::unordered_map<uint64_t, int> bpmap;
   std::vector<std::pair<int, int>> bplist;
   auto bp_of = [&](int a, int b) {
@@ -743,6 +744,7 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
       int s[4] = {q.x, q.y, q.z, q.w};
       std::sort(s, s + 4);
       segn.push_back(make_int4(s[0], s[1], s[2], s[3]));
+      segstart.push_back(r);
       for (int k = 0; k < 10; ++k) {
         int i = kSlotPairI(k), jj = kSlotPairJ(k);
         segbp.push_back(bp_of(s[i], s[jj]));
@@ -773,18 +775,30 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
     rank[pixel] = r;
   }
   h->S = (int)segn.size();
+  segstart.push_back(P);
   h->nbp = (int)bplist.size();
-  // CSR of the block pairs by row
-  std::vector<int> rowptr(N + 1, 0), rowcol(h->nbp), rowbp(h->nbp);
-  for (auto& pr : bplist) rowptr[pr.first + 1]++;
+  // CSR of the data blocks by node row, both triangles: pair (a, b), a >= b, is listed in row a
+  // (column b, block id) and, when a > b, in row b (column a, block id | kBlkTransposed)
+  std::vector<int> rowptr(N + 1, 0);
+  for (auto& pr : bplist) {
+    rowptr[pr.first + 1]++;
+    if (pr.first != pr.second) rowptr[pr.second + 1]++;
+  }
   for (int i = 0; i < N; ++i) rowptr[i + 1] += rowptr[i];
+  const int nent = rowptr[N];
+  std::vector<int> rowcol(std::max(nent, 1)), rowbp(std::max(nent, 1));
   {
     std::vector<int> fill(rowptr.begin(), rowptr.end() - 1);
     for (int id = 0; id < h->nbp; ++id) {
-      int a = bplist[id].first;
-      rowcol[fill[a]] = bplist[id].second;
+      const int a = bplist[id].first, bb = bplist[id].second;
+      rowcol[fill[a]] = bb;
       rowbp[fill[a]] = id;
       fill[a]++;
+      if (a != bb) {
+        rowcol[fill[bb]] = a;
+        rowbp[fill[bb]] = id | kBlkTransposed;
+        fill[bb]++;
+      }
     }
   }
   const int n = h->n;
@@ -798,8 +812,9 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
       (rc = dalloc(&h->d_node, N)) || (rc = dalloc(&h->d_pn, N)) || (rc = dalloc(&h->d_tp, P)) ||
       (rc = dalloc(&h->d_tw, P)) || (rc = dalloc(&h->d_rank, npx)) ||
       (rc = dalloc(&h->d_seg, h->S)) || (rc = dalloc(&h->d_segbp, 10 * h->S)) ||
-      (rc = dalloc(&h->d_rowptr, N + 1)) || (rc = dalloc(&h->d_rowcol, h->nbp)) ||
-      (rc = dalloc(&h->d_rowbp, h->nbp)) || (rc = dalloc(&h->d_A32, nn)) ||
+      (rc = dalloc(&h->d_segstart, h->S + 1)) ||
+      (rc = dalloc(&h->d_rowptr, N + 1)) || (rc = dalloc(&h->d_rowcol, rowcol.size())) ||
+      (rc = dalloc(&h->d_rowbp, rowbp.size())) || (rc = dalloc(&h->d_A32, nn)) ||
       (rc = dalloc(&h->d_blk, 36 * (size_t)h->nbp)) || (rc = dalloc(&h->d_gdata, n)) ||
       (rc = dalloc(&h->d_b, n)) || (rc = dalloc(&h->d_x, n)) || (rc = dalloc(&h->d_r, n)) ||
       (rc = dalloc(&h->d_xf, n)) ||
@@ -860,6 +875,8 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
     D.tw = h->d_tw;
     D.seg = h->d_seg;
     D.segbp = h->d_segbp;
+    D.segstart = h->d_segstart;
+    D.S = h->S;
     D.rank = h->d_rank;
     D.tpts = h->d_tpts;
     D.tnrm = h->d_tnrm;
@@ -911,9 +928,10 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
   cudaMemcpy(h->d_rank, rank.data(), sizeof(int) * npx, cudaMemcpyHostToDevice);
   cudaMemcpy(h->d_seg, segn.data(), sizeof(int4) * h->S, cudaMemcpyHostToDevice);
   cudaMemcpy(h->d_segbp, segbp.data(), sizeof(int) * 10 * h->S, cudaMemcpyHostToDevice);
+  cudaMemcpy(h->d_segstart, segstart.data(), sizeof(int) * (h->S + 1), cudaMemcpyHostToDevice);
   cudaMemcpy(h->d_rowptr, rowptr.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice);
-  cudaMemcpy(h->d_rowcol, rowcol.data(), sizeof(int) * h->nbp, cudaMemcpyHostToDevice);
-  cudaMemcpy(h->d_rowbp, rowbp.data(), sizeof(int) * h->nbp, cudaMemcpyHostToDevice);
+  cudaMemcpy(h->d_rowcol, rowcol.data(), sizeof(int) * rowcol.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(h->d_rowbp, rowbp.data(), sizeof(int) * rowbp.size(), cudaMemcpyHostToDevice);
   cudaMemset(h->d_A32, 0, sizeof(float) * nn);
   if (h->d_A64) cudaMemset(h->d_A64, 0, sizeof(double) * nn);
   if (h->d_Af32) cudaMemset(h->d_Af32, 0, sizeof(float) * nn);

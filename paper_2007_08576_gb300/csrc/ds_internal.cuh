@@ -72,7 +72,7 @@ struct LinProblem {
 // Everything the per-iteration kernels need about one problem (one handle). Lives in device
 // memory; kernels read sizes that change per frame (M) from it, so captured graphs stay valid.
 struct ProbDesc {
-  int W, H, P, N, n, M, nbp;
+  int W, H, P, N, n, M, nbp, S;
   float fx, fy, cx, cy;
   float tukey_c, H_mm, w_orb, w_angle, w_rot, inv2sig2;
   double w_arap0, lam, eps;
@@ -81,6 +81,7 @@ struct ProbDesc {
   const float4* tw;        // blend weights per sorted point (slot order)
   const int4* seg;         // node quadruple of each segment (ascending ids)
   const int* segbp;        // 10 block-pair ids per segment
+  const int* segstart;     // first sorted point of each segment (S + 1 entries)
   const int* rank;         // template pixel -> sorted position, -1 if no point
   const float4* tpts;      // live points (x, y, z, valid)
   const float4* tnrm;      // live normals
@@ -88,7 +89,7 @@ struct ProbDesc {
   const float* mxyz;
   const uint32_t* mask;
   const float* what;
-  const int* rowptr;       // CSR of the block pairs by row
+  const int* rowptr;       // CSR of the data blocks by node row (both triangles)
   const int* rowcol;
   const int* rowbp;
   const double* g64;       // node positions (FP64)
@@ -109,7 +110,10 @@ struct ProbDesc {
   LinProblem lp;
 };
 
-constexpr int kTile = 256;        // points per CTA of the ICP pass
+constexpr int kBlkTransposed = 1 << 30;  // CSR flag: the row uses the block transposed
+constexpr int kTile = 256;        // threads per CTA of the ICP pass
+constexpr int kSegPerCta = kTile / 32;  // warps (concurrent segments) per CTA of the ICP pass
+constexpr int kSegPerWarp = 4;          // segments each ICP warp takes in turn
 constexpr int kOuts = 10 * 36 + 24;  // per-segment outputs: 10 blocks of 6x6, 24 gradient entries
 
 // ----------------------------------------------------------------------------- launchers
@@ -133,7 +137,7 @@ void launch_ransac(const float* depth0, int W, ds_intrinsics K, const int* midx,
 struct BatchTabs {
   const ProbDesc* const* d;  // descriptor pointer per problem
   int P;                     // problems
-  const int2* icp;           // (problem, 256-point tile)
+  const int2* icp;           // (problem, group of kSegPerCta x kSegPerWarp segments)
   int n_icp;
   const int2* rows;          // (problem, node) of the dense ARAP pass
   int n_rows;

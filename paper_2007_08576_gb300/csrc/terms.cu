@@ -193,12 +193,13 @@ struct Blend {
   float sgn[4];  // sign alignment per slot
 };
 
-__device__ __forceinline__ void blend_point(const NodeGPU* __restrict__ node, const int* nid,
-                                            const float* alpha, int near, V p, Blend& B,
-                                            NodeGPU* nd) {
-#pragma unroll
-  for (int k = 0; k < 4; ++k) nd[k] = node[nid[k]];
-  Q qn = q4(nd[near].q);
+// Blends the 4 node transforms in nd[] (registers or shared memory) at template point p.
+__device__ __forceinline__ void blend_nodes(const NodeGPU* nd, const float* alpha, int near, V p,
+                                            Blend& B) {
+  // the nearest node's rotation, picked by selects (a runtime index into a register array would
+  // place it in local memory)
+  const float4 qn4 = near == 0 ? nd[0].q : near == 1 ? nd[1].q : near == 2 ? nd[2].q : nd[3].q;
+  Q qn = q4(qn4);
   Q br = {0, 0, 0, 0}, bd = {0, 0, 0, 0};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -227,6 +228,14 @@ __device__ __forceinline__ void blend_point(const NodeGPU* __restrict__ node, co
   B.bd = bd;
   B.inv_s = 1.f / s;
   B.x = mul(y, B.inv_s);
+}
+
+__device__ __forceinline__ void blend_point(const NodeGPU* __restrict__ node, const int* nid,
+                                            const float* alpha, int near, V p, Blend& B,
+                                            NodeGPU* nd) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) nd[k] = node[nid[k]];
+  blend_nodes(nd, alpha, near, p, B);
 }
 
 // h = d(n . x') / db for a direction n (8 entries: b_r then b_d).
@@ -269,19 +278,25 @@ __device__ __forceinline__ void slot_jac(const float* h, const NodeGPU& nd, floa
 
 // ----------------------------------------------------------------------------- ICP
 
-// One thread per template point (points sorted by their node quadruple, so that a segment of
-// consecutive points shares the same 4 nodes). Each CTA reduces the sqrt-weighted Jacobians of
-// its tile per segment in shared memory and adds the segment's 10 blocks and gradient into
-// the block table with one atomic per entry.
-__global__ __launch_bounds__(kTile) void k_icp(const ProbDesc* const* __restrict__ descs,
-                                               const int2* __restrict__ tab) {
+// One warp per segment (a run of sorted template points sharing the same 4 nodes); a CTA's
+// warp w takes segments base + w + 8 k, k < kSegPerWarp. The segment's 4 node transforms are
+// staged in the warp's shared memory. The lanes take 32 of the segment's points at a time: each
+// forms its point's association, Tukey weight and sqrt-weighted Jacobian row (24 entries, plus
+// the weighted residual) and stages it in the warp's shared rows; then every lane accumulates 12
+// fixed entries of the segment's 384 outputs over those points. Lanes 0..29 own two rows of one
+// 6 x 6 slot-pair block (block l / 3, rows 2 (l % 3) and 2 (l % 3) + 1), lanes 30 and 31 own
+// twelve gradient entries each. At the end of the segment each lane adds its 12 entries with
+// one atomic each; cost, weight and count go out with one atomic triple per warp. Warps never
+// wait for one another.
+__global__ __launch_bounds__(kTile, 2) void k_icp(const ProbDesc* const* __restrict__ descs,
+                                                  const int2* __restrict__ tab) {
   const int2 wk = tab[blockIdx.x];
   const ProbDesc& D = *descs[wk.x];
   const float4* __restrict__ tp = D.tp;
   const float4* __restrict__ tw = D.tw;
   const int4* __restrict__ segnodes = D.seg;
   const int* __restrict__ segbp = D.segbp;
-  const int P = D.P;
+  const int* __restrict__ segstart = D.segstart;
   const NodeGPU* __restrict__ node = D.node;
   const float4* __restrict__ tgt_pt = D.tpts;
   const float4* __restrict__ tgt_nrm = D.tnrm;
@@ -290,129 +305,127 @@ __global__ __launch_bounds__(kTile) void k_icp(const ProbDesc* const* __restrict
   float* __restrict__ blk = D.blk;
   float* __restrict__ gdata = D.gdata;
   double* __restrict__ acc = D.acc;
-  __shared__ float sJ[kTile][25];
-  __shared__ int sSeg[kTile];
-  __shared__ int sStart[kTile + 1];
-  __shared__ int sWarpCnt[kTile / 32 + 1];
-  __shared__ float sRed[3][kTile / 32];
-  const int tid = threadIdx.x;
-  const int base = wk.y * kTile;
-  const int len = min(kTile, P - base);
-  const int pidx = base + tid;
-  float Jt[24];
+  __shared__ float sJ[kSegPerCta][32][25];
+  __shared__ NodeGPU sNode[kSegPerCta][4];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool grad = lane >= 30;
+  const int q = grad ? 0 : lane / 3;
+  const int ra = 6 * kSlotPairI(q) + 2 * (lane % 3);   // this lane's two Jacobian rows
+  const int cb = 6 * kSlotPairJ(q);                    // and the partner slot's columns
+  const int g0 = (lane - 30) * 12;                     // gradient entries of lanes 30, 31
+  float(*rows)[25] = sJ[warp];
+  NodeGPU* nd = sNode[warp];
+  float cost = 0.f, wsum = 0.f, nval = 0.f;
+  for (int k = 0; k < kSegPerWarp; ++k) {
+    const int sg = wk.y * kSegPerCta * kSegPerWarp + k * kSegPerCta + warp;
+    if (sg >= D.S) break;
+    const int lo = segstart[sg], hi = segstart[sg + 1];
+    const int4 nn = segnodes[sg];
+    __syncwarp();
+    if (lane < 16) {
+      const int sl = lane >> 2, f = lane & 3;
+      const int id = sl == 0 ? nn.x : sl == 1 ? nn.y : sl == 2 ? nn.z : nn.w;
+      reinterpret_cast<float4*>(&nd[sl])[f] = reinterpret_cast<const float4*>(&node[id])[f];
+    }
+    __syncwarp();
+    float a[12];
 #pragma unroll
-  for (int i = 0; i < 24; ++i) Jt[i] = 0.f;
-  float rt = 0.f, rho = 0.f, wv = 0.f, nv = 0.f;
-  int seg = -1;
-  if (tid < len) {
-    float4 a = tp[pidx];
-    int bits = __float_as_int(a.w);
-    seg = bits >> 2;
-    int near = bits & 3;
-    int4 nn = segnodes[seg];
-    float4 al = tw[pidx];
-    int nid[4] = {nn.x, nn.y, nn.z, nn.w};
-    float alp[4] = {al.x, al.y, al.z, al.w};
-    V p = {a.x, a.y, a.z};
-    Blend B;
-    NodeGPU nd[4];
-    blend_point(node, nid, alp, near, p, B, nd);
-    V x = B.x;
-    if (x.z > 0.f) {
-      float u = fx * x.x / x.z + cx;
-      float v = fy * x.y / x.z + cy;
-      float pu = floorf(u + 0.5f), pv = floorf(v + 0.5f);
-      if (pu >= 0.f && pu < (float)W && pv >= 0.f && pv < (float)H) {
-        int pix = (int)pv * W + (int)pu;
-        float4 q = tgt_pt[pix];
-        if (q.w > 0.f) {
-          float4 n4 = tgt_nrm[pix];
-          V n = {n4.x, n4.y, n4.z};
-          float r = dot(n, sub(x, {q.x, q.y, q.z}));
-          nv = 1.f;
-          float cc6 = c * c * (1.f / 6.f);
-          if (fabsf(r) < c) {
-            float uu = r / c;
-            float sig = 1.f - uu * uu;
-            wv = sig * sig;
-            rho = cc6 * (1.f - sig * sig * sig);
-            float h[8];
-            dir_grad(n, p, B, h);
+    for (int e = 0; e < 12; ++e) a[e] = 0.f;
+    for (int c0 = lo; c0 < hi; c0 += 32) {
+      const int pidx = c0 + lane;
+      float Jt[24];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) slot_jac(h, nd[k], alp[k] * B.sgn[k] * sig, &Jt[6 * k]);
-            rt = sig * r;
-          } else {
-            rho = cc6;
+      for (int i = 0; i < 24; ++i) Jt[i] = 0.f;
+      float rt = 0.f;
+      if (pidx < hi) {
+        const float4 pa = tp[pidx];
+        const int near = __float_as_int(pa.w) & 3;
+        const float4 al = tw[pidx];
+        const float alp[4] = {al.x, al.y, al.z, al.w};
+        const V p = {pa.x, pa.y, pa.z};
+        Blend B;
+        blend_nodes(nd, alp, near, p, B);
+        const V x = B.x;
+        if (x.z > 0.f) {
+          const float u = fx * x.x / x.z + cx;
+          const float v = fy * x.y / x.z + cy;
+          const float pu = floorf(u + 0.5f), pv = floorf(v + 0.5f);
+          if (pu >= 0.f && pu < (float)W && pv >= 0.f && pv < (float)H) {
+            const int pix = (int)pv * W + (int)pu;
+            const float4 tq = tgt_pt[pix];
+            if (tq.w > 0.f) {
+              const float4 n4 = tgt_nrm[pix];
+              const V n = {n4.x, n4.y, n4.z};
+              const float r = dot(n, sub(x, {tq.x, tq.y, tq.z}));
+              nval += 1.f;
+              const float cc6 = c * c * (1.f / 6.f);
+              if (fabsf(r) < c) {
+                const float uu = r / c;
+                const float sig = 1.f - uu * uu;
+                wsum += sig * sig;
+                cost += cc6 * (1.f - sig * sig * sig);
+                float h[8];
+                dir_grad(n, p, B, h);
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+                  slot_jac(h, nd[s], alp[s] * B.sgn[s] * sig, &Jt[6 * s]);
+                rt = sig * r;
+              } else {
+                cost += cc6;
+              }
+            }
           }
         }
       }
-    }
-  }
 #pragma unroll
-  for (int i = 0; i < 24; ++i) sJ[tid][i] = Jt[i];
-  sJ[tid][24] = rt;
-  sSeg[tid] = seg;
-  // cost / weight / count reduction
-  {
-    float v0 = rho, v1 = wv, v2 = nv;
-    for (int o = 16; o > 0; o >>= 1) {
-      v0 += __shfl_xor_sync(0xffffffffu, v0, o);
-      v1 += __shfl_xor_sync(0xffffffffu, v1, o);
-      v2 += __shfl_xor_sync(0xffffffffu, v2, o);
-    }
-    if ((tid & 31) == 0) {
-      sRed[0][tid >> 5] = v0;
-      sRed[1][tid >> 5] = v1;
-      sRed[2][tid >> 5] = v2;
-    }
-  }
-  __syncthreads();
-  // segment starts within the tile (segments are contiguous because points are sorted)
-  bool start = tid < len && (tid == 0 || sSeg[tid] != sSeg[tid - 1]);
-  unsigned bal = __ballot_sync(0xffffffffu, start);
-  if ((tid & 31) == 0) sWarpCnt[tid >> 5] = __popc(bal);
-  if (tid == 0) {
-    double a0 = 0, a1 = 0, a2 = 0;
-    for (int w = 0; w < kTile / 32; ++w) {
-      a0 += sRed[0][w];
-      a1 += sRed[1][w];
-      a2 += sRed[2][w];
-    }
-    atomicAdd(&acc[ACC_COST_ICP], a0);
-    atomicAdd(&acc[ACC_WSUM_ICP], a1);
-    atomicAdd(&acc[ACC_NVALID], a2);
-  }
-  __syncthreads();
-  if (start) {
-    int off = 0;
-    for (int w = 0; w < (tid >> 5); ++w) off += sWarpCnt[w];
-    off += __popc(bal & ((1u << (tid & 31)) - 1u));
-    sStart[off] = tid;
-  }
-  int nseg = 0;
-  for (int w = 0; w < kTile / 32; ++w) nseg += sWarpCnt[w];
-  if (tid == 0) sStart[nseg] = len;
-  __syncthreads();
-  for (int si = 0; si < nseg; ++si) {
-    const int lo = sStart[si], hi = sStart[si + 1];
-    const int sg = sSeg[lo];
-    for (int o = tid; o < kOuts; o += kTile) {
-      float s = 0.f;
-      if (o < 360) {
-        int k = o / 36, e = o % 36;
-        int ai = 6 * kSlotPairI(k) + e / 6, bj = 6 * kSlotPairJ(k) + e % 6;
-        for (int pp = lo; pp < hi; ++pp) s += sJ[pp][ai] * sJ[pp][bj];
-        if (s != 0.f) atomicAdd(&blk[(size_t)segbp[sg * 10 + k] * 36 + e], s);
+      for (int i = 0; i < 24; ++i) rows[lane][i] = Jt[i];
+      rows[lane][24] = rt;
+      __syncwarp();
+      const int np = min(32, hi - c0);
+      if (!grad) {
+#pragma unroll 2
+        for (int t = 0; t < np; ++t) {
+          const float x0 = rows[t][ra], x1 = rows[t][ra + 1];
+#pragma unroll
+          for (int cc = 0; cc < 6; ++cc) {
+            const float y = rows[t][cb + cc];
+            a[cc] += x0 * y;
+            a[6 + cc] += x1 * y;
+          }
+        }
       } else {
-        int a = o - 360;
-        for (int pp = lo; pp < hi; ++pp) s += sJ[pp][a] * sJ[pp][24];
-        if (s != 0.f) {
-          int4 nn = segnodes[sg];
-          int nd = (a / 6 == 0) ? nn.x : (a / 6 == 1) ? nn.y : (a / 6 == 2) ? nn.z : nn.w;
-          atomicAdd(&gdata[6 * nd + a % 6], s);
+#pragma unroll 2
+        for (int t = 0; t < np; ++t) {
+          const float rr = rows[t][24];
+#pragma unroll
+          for (int e = 0; e < 12; ++e) a[e] += rows[t][g0 + e] * rr;
         }
       }
+      __syncwarp();
     }
+    if (!grad) {
+      float* dst = blk + (size_t)segbp[sg * 10 + q] * 36 + 12 * (lane % 3);
+#pragma unroll
+      for (int e = 0; e < 12; ++e)
+        if (a[e] != 0.f) atomicAdd(dst + e, a[e]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 12; ++e) {
+        const int kk = g0 + e, sl = kk / 6;
+        const int ndi = sl == 0 ? nn.x : sl == 1 ? nn.y : sl == 2 ? nn.z : nn.w;
+        if (a[e] != 0.f) atomicAdd(&gdata[6 * ndi + kk % 6], a[e]);
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    cost += __shfl_xor_sync(0xffffffffu, cost, o);
+    wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+    nval += __shfl_xor_sync(0xffffffffu, nval, o);
+  }
+  if (lane == 0 && nval != 0.f) {
+    atomicAdd(&acc[ACC_COST_ICP], (double)cost);
+    atomicAdd(&acc[ACC_WSUM_ICP], (double)wsum);
+    atomicAdd(&acc[ACC_NVALID], (double)nval);
   }
 }
 
@@ -480,18 +493,22 @@ __global__ __launch_bounds__(128) void k_orb(const ProbDesc* const* __restrict__
           for (int s = 0; s < 4; ++s) slot_jac(h, nd[s], alp[s] * B.sgn[s] * sig, &J[row][6 * s]);
         }
         float rr[3] = {sig * r.x, sig * r.y, sig * r.z};
+        // fully unrolled so that J stays in registers
+#pragma unroll
         for (int kk = 0; kk < 10; ++kk) {
-          int bp = segbp[seg * 10 + kk];
-          int ib = 6 * kSlotPairI(kk), jb = 6 * kSlotPairJ(kk);
+          float* dst = blk + (size_t)segbp[seg * 10 + kk] * 36;
+          const int ib = 6 * kSlotPairI(kk), jb = 6 * kSlotPairJ(kk);
+#pragma unroll
           for (int e = 0; e < 36; ++e) {
-            int ai = ib + e / 6, bj = jb + e % 6;
-            float v = J[0][ai] * J[0][bj] + J[1][ai] * J[1][bj] + J[2][ai] * J[2][bj];
-            if (v != 0.f) atomicAdd(&blk[(size_t)bp * 36 + e], v);
+            const int ai = ib + e / 6, bj = jb + e % 6;
+            const float v = J[0][ai] * J[0][bj] + J[1][ai] * J[1][bj] + J[2][ai] * J[2][bj];
+            if (v != 0.f) atomicAdd(dst + e, v);
           }
         }
+#pragma unroll
         for (int a2 = 0; a2 < 24; ++a2) {
-          float v = J[0][a2] * rr[0] + J[1][a2] * rr[1] + J[2][a2] * rr[2];
-          int ndid = nid[a2 / 6];
+          const float v = J[0][a2] * rr[0] + J[1][a2] * rr[1] + J[2][a2] * rr[2];
+          const int ndid = a2 < 6 ? nn.x : a2 < 12 ? nn.y : a2 < 18 ? nn.z : nn.w;
           if (v != 0.f) atomicAdd(&gdata[6 * ndid + a2 % 6], v);
         }
       }
@@ -518,6 +535,25 @@ void launch_orb(const BatchTabs& B, cudaStream_t s) {
 template <typename T>
 __device__ __forceinline__ void store_out(T* p, float v) {
   *p = (T)v;
+}
+
+constexpr int kArapMaxN = 2048;   // control points per problem (the API's limit)
+constexpr int kArapChunk = 256;   // partner nodes per panel chunk (= threads per CTA)
+
+// Copies len floats of a shared-memory row to global memory: 16-byte stores (FP32, row start
+// 16-byte aligned) with a scalar tail; FP64 destinations are converted element by element.
+template <typename T>
+__device__ __forceinline__ void row_out(T* dst, const float* src, int len, bool aligned) {
+  if constexpr (sizeof(T) == 4) {
+    if (aligned) {
+      const int n4 = len >> 2;
+      for (int k = threadIdx.x; k < n4; k += blockDim.x)
+        reinterpret_cast<float4*>(dst)[k] = reinterpret_cast<const float4*>(src)[k];
+      for (int k = 4 * n4 + threadIdx.x; k < len; k += blockDim.x) dst[k] = src[k];
+      return;
+    }
+  }
+  for (int k = threadIdx.x; k < len; k += blockDim.x) store_out(dst + k, src[k]);
 }
 
 // One CTA per block row i1. For every partner i2 != i1 the CTA evaluates both ordered pairs
@@ -550,7 +586,8 @@ __global__ __launch_bounds__(256) void k_arap_assemble(const ProbDesc* const* __
   T* __restrict__ Afac = lin_only ? (T*)D.Aref : (T*)D.lp.A;
   float* __restrict__ Aref = (!lin_only && D.write_ref) ? D.Aref : nullptr;
   double* __restrict__ b = D.b;
-  extern __shared__ int smap[];
+  extern __shared__ __align__(16) int smap[];          // node -> data block code of this row
+  float* panel = reinterpret_cast<float*>(smap + kArapMaxN);  // 6 rows x kArapChunk nodes
   __shared__ float sRed[28][8];
   const int i1 = wk.y;
   const int n = 6 * N;
@@ -573,67 +610,80 @@ __global__ __launch_bounds__(256) void k_arap_assemble(const ProbDesc* const* __
   // diag accumulators: theta-theta (sym 6: xx xy xz yy yz zz), theta-t (9), t-t (sym 6)
   float Dtt[6] = {0, 0, 0, 0, 0, 0}, Dtx[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   float Dxx[6] = {0, 0, 0, 0, 0, 0}, G[6] = {0, 0, 0, 0, 0, 0}, cost = 0.f;
-  for (int i2 = threadIdx.x; i2 < N; i2 += blockDim.x) {
-    if (i2 == i1) continue;
-    const PairNode o = pn[i2];
-    const Q q2 = q4(o.q);
-    const V g2 = v3(o.g), p2 = v3(o.p);
-    V dg = sub(g2, g1);
-    float L0 = sqrtf(dot(dg, dg));
-    V e = sub(p2, p1);
-    float l = sqrtf(dot(e, e));
-    float il = 1.f / l;
-    V v = mul(e, il);
-    V a = {dot(R1a, dg), dot(R1b, dg), dot(R1c, dg)};
-    V u = mul(a, rsqrtf(dot(a, a)));
-    V mdg = {-dg.x, -dg.y, -dg.z};
-    V a2 = {dot(v3(o.R0), mdg), dot(v3(o.R1), mdg), dot(v3(o.R2), mdg)};
-    V u2 = mul(a2, rsqrtf(dot(a2, a2)));
-    Q r = qmul(q2, qconj(q1));
-    float qq = qdot(q1, q2);
-    float s = qq >= 0.f ? 1.f : -1.f;
-    float w = wA * __expf(-dot(dg, dg) * inv2sig2);
-    float Wl = w, Wa = w * w_angle, Wr = w * w_rot;
-    float rl = l - L0;
-    V ang = sub(u, v);
-    Q rot = {q1.w - s * q2.w, q1.x - s * q2.x, q1.y - s * q2.y, q1.z - s * q2.z};
-    cost += 0.5f * (Wl * rl * rl + Wa * dot(ang, ang) + Wr * qdot(rot, rot));
-    // C = W_a [u]x P / l with P = I - v v^T:  [u]x - (u x v) v^T
-    V uxv = cross(u, v);
-    float ca = Wa * il;
-    float C[9] = {ca * (0.f - uxv.x * v.x), ca * (-u.z - uxv.x * v.y), ca * (u.y - uxv.x * v.z),
-                  ca * (u.z - uxv.y * v.x), ca * (0.f - uxv.y * v.y), ca * (-u.x - uxv.y * v.z),
-                  ca * (-u.y - uxv.z * v.x), ca * (u.x - uxv.z * v.y), ca * (0.f - uxv.z * v.z)};
-    // Tm = W_l v v^T + W_a (I - v v^T) / l^2
-    float tb = Wa * il * il;
-    float tv = Wl - tb;
-    float Tm[6] = {tb + tv * v.x * v.x, tv * v.x * v.y, tv * v.x * v.z,
-                   tb + tv * v.y * v.y, tv * v.y * v.z, tb + tv * v.z * v.z};
-    // diag
-    float hr = 0.5f * Wr;
-    Dtt[0] += Wa * (1.f - u.x * u.x) + hr;
-    Dtt[1] += -Wa * u.x * u.y;
-    Dtt[2] += -Wa * u.x * u.z;
-    Dtt[3] += Wa * (1.f - u.y * u.y) + hr;
-    Dtt[4] += -Wa * u.y * u.z;
-    Dtt[5] += Wa * (1.f - u.z * u.z) + hr;
+  // The CTA builds its 6 matrix rows chunk by chunk (kArapChunk partner nodes, one per thread)
+  // in shared memory and streams them out with coalesced 16-byte stores: the full rows into the
+  // refinement matrix, the part left of the diagonal block into the factor. A(i1, i2) for
+  // i2 > i1 is the transpose of A(i2, i1); the pair formula below, taken with i1 as the row,
+  // gives it directly.
+  constexpr int PW = 6 * kArapChunk;  // panel row width (floats)
+  for (int ch = 0; ch * kArapChunk < N; ++ch) {
+    const int i2 = ch * kArapChunk + threadIdx.x;
+    const int ncol = 6 * min(kArapChunk, N - ch * kArapChunk);
+    float* pc = panel + 6 * threadIdx.x;
+    if (i2 < N && i2 == i1) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Dtx[i] += C[i];
+      for (int rr = 0; rr < 6; ++rr)
 #pragma unroll
-    for (int i = 0; i < 6; ++i) Dxx[i] += 2.f * Tm[i];
-    // gradient
-    V rv = {r.x, r.y, r.z};
-    G[0] += -Wa * uxv.x - s * Wr * rv.x;
-    G[1] += -Wa * uxv.y - s * Wr * rv.y;
-    G[2] += -Wa * uxv.z - s * Wr * rv.z;
-    V Pu = sub(u, mul(v, dot(v, u)));
-    V Pu2 = sub(u2, mul(v, dot(v, u2)));
-    V gt = add(mul(v, -2.f * Wl * rl), mul(sub(Pu, Pu2), Wa * il));
-    G[3] += gt.x;
-    G[4] += gt.y;
-    G[5] += gt.z;
-    if (i2 < i1) {
-      // off-diagonal block (rows: i1's theta,t; cols: i2's theta,t)
+        for (int cc = 0; cc < 6; ++cc) pc[rr * PW + cc] = 0.f;  // written after the reduction
+    } else if (i2 < N) {
+      const PairNode o = pn[i2];
+      const Q q2 = q4(o.q);
+      const V g2 = v3(o.g), p2 = v3(o.p);
+      V dg = sub(g2, g1);
+      float L0 = sqrtf(dot(dg, dg));
+      V e = sub(p2, p1);
+      float l = sqrtf(dot(e, e));
+      float il = 1.f / l;
+      V v = mul(e, il);
+      V a = {dot(R1a, dg), dot(R1b, dg), dot(R1c, dg)};
+      V u = mul(a, rsqrtf(dot(a, a)));
+      V mdg = {-dg.x, -dg.y, -dg.z};
+      V a2 = {dot(v3(o.R0), mdg), dot(v3(o.R1), mdg), dot(v3(o.R2), mdg)};
+      V u2 = mul(a2, rsqrtf(dot(a2, a2)));
+      Q r = qmul(q2, qconj(q1));
+      float qq = qdot(q1, q2);
+      float s = qq >= 0.f ? 1.f : -1.f;
+      float w = wA * __expf(-dot(dg, dg) * inv2sig2);
+      float Wl = w, Wa = w * w_angle, Wr = w * w_rot;
+      float rl = l - L0;
+      V ang = sub(u, v);
+      Q rot = {q1.w - s * q2.w, q1.x - s * q2.x, q1.y - s * q2.y, q1.z - s * q2.z};
+      cost += 0.5f * (Wl * rl * rl + Wa * dot(ang, ang) + Wr * qdot(rot, rot));
+      // C = W_a [u]x P / l with P = I - v v^T:  [u]x - (u x v) v^T
+      V uxv = cross(u, v);
+      float ca = Wa * il;
+      float C[9] = {ca * (0.f - uxv.x * v.x), ca * (-u.z - uxv.x * v.y), ca * (u.y - uxv.x * v.z),
+                    ca * (u.z - uxv.y * v.x), ca * (0.f - uxv.y * v.y), ca * (-u.x - uxv.y * v.z),
+                    ca * (-u.y - uxv.z * v.x), ca * (u.x - uxv.z * v.y), ca * (0.f - uxv.z * v.z)};
+      // Tm = W_l v v^T + W_a (I - v v^T) / l^2
+      float tb = Wa * il * il;
+      float tv = Wl - tb;
+      float Tm[6] = {tb + tv * v.x * v.x, tv * v.x * v.y, tv * v.x * v.z,
+                     tb + tv * v.y * v.y, tv * v.y * v.z, tb + tv * v.z * v.z};
+      // diag
+      float hr = 0.5f * Wr;
+      Dtt[0] += Wa * (1.f - u.x * u.x) + hr;
+      Dtt[1] += -Wa * u.x * u.y;
+      Dtt[2] += -Wa * u.x * u.z;
+      Dtt[3] += Wa * (1.f - u.y * u.y) + hr;
+      Dtt[4] += -Wa * u.y * u.z;
+      Dtt[5] += Wa * (1.f - u.z * u.z) + hr;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) Dtx[i] += C[i];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) Dxx[i] += 2.f * Tm[i];
+      // gradient
+      V rv = {r.x, r.y, r.z};
+      G[0] += -Wa * uxv.x - s * Wr * rv.x;
+      G[1] += -Wa * uxv.y - s * Wr * rv.y;
+      G[2] += -Wa * uxv.z - s * Wr * rv.z;
+      V Pu = sub(u, mul(v, dot(v, u)));
+      V Pu2 = sub(u2, mul(v, dot(v, u2)));
+      V gt = add(mul(v, -2.f * Wl * rl), mul(sub(Pu, Pu2), Wa * il));
+      G[3] += gt.x;
+      G[4] += gt.y;
+      G[5] += gt.z;
+      // off-diagonal block A(i1, i2) (rows: i1's theta,t; cols: i2's theta,t)
       float O[36];
       float hs = -0.5f * s * Wr;
       // theta-theta: hs (r_w I - [r_v]x)
@@ -672,33 +722,35 @@ __global__ __launch_bounds__(256) void k_arap_assemble(const ProbDesc* const* __
       O[5 * 6 + 3] = -2.f * Tm[2];
       O[5 * 6 + 4] = -2.f * Tm[4];
       O[5 * 6 + 5] = -2.f * Tm[5];
-      int bp = smap[i2];
-      if (bp >= 0) {
-        const float* db = blk + (size_t)bp * 36;
+      const int code = smap[i2];
+      if (code >= 0) {
+        const float* db = blk + (size_t)(code & ~kBlkTransposed) * 36;
+        if (code & kBlkTransposed) {
 #pragma unroll
-        for (int i = 0; i < 36; ++i) O[i] += db[i];
-      }
+          for (int rr = 0; rr < 6; ++rr)
 #pragma unroll
-      for (int rr = 0; rr < 6; ++rr) {
-        T* row = Afac + (size_t)(6 * i1 + rr) * n + 6 * i2;
+            for (int cc = 0; cc < 6; ++cc) O[rr * 6 + cc] += db[cc * 6 + rr];
+        } else {
 #pragma unroll
-        for (int cc = 0; cc < 6; ++cc) store_out(row + cc, O[rr * 6 + cc]);
-      }
-      if (Aref) {
-#pragma unroll
-        for (int rr = 0; rr < 6; ++rr) {
-          float* row = Aref + (size_t)(6 * i1 + rr) * n + 6 * i2;
-#pragma unroll
-          for (int cc = 0; cc < 6; ++cc) row[cc] = O[rr * 6 + cc];
-        }
-#pragma unroll
-        for (int cc = 0; cc < 6; ++cc) {
-          float* row = Aref + (size_t)(6 * i2 + cc) * n + 6 * i1;
-#pragma unroll
-          for (int rr = 0; rr < 6; ++rr) row[rr] = O[rr * 6 + cc];
+          for (int i = 0; i < 36; ++i) O[i] += db[i];
         }
       }
+#pragma unroll
+      for (int rr = 0; rr < 6; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) pc[rr * PW + cc] = O[rr * 6 + cc];
     }
+    __syncthreads();
+    const int c0 = ch * PW;
+    const int nlo = max(0, min(ncol, 6 * i1 - c0));  // factor columns left of the diagonal block
+#pragma unroll 1
+    for (int rr = 0; rr < 6; ++rr) {
+      const float* src = panel + rr * PW;
+      const size_t rowoff = (size_t)(6 * i1 + rr) * n + c0;
+      if (Aref) row_out<float>(Aref + rowoff, src, ncol, (n & 3) == 0);
+      row_out<T>(Afac + rowoff, src, nlo, (n & 3) == 0);
+    }
+    __syncthreads();
   }
   // block reduction of the 28 per-thread sums
   float vals[28];
@@ -762,9 +814,15 @@ __global__ __launch_bounds__(256) void k_arap_assemble(const ProbDesc* const* __
 
 template <typename T>
 void launch_arap_assemble(const BatchTabs& B, bool first, bool lin_only, cudaStream_t s) {
-  // dynamic shared memory: the node -> data block map of the row (N <= 2048 by the API)
-  const int sm = sizeof(int) * 2048;
-  k_arap_assemble<T><<<B.n_rows, 256, sm, s>>>(B.d, B.rows, first ? 1 : 0, lin_only ? 1 : 0);
+  // dynamic shared memory: the node -> data block map of the row and the 6-row panel
+  const int sm = sizeof(int) * kArapMaxN + sizeof(float) * 6 * 6 * kArapChunk;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_arap_assemble<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    attr = true;
+  }
+  k_arap_assemble<T><<<B.n_rows, kArapChunk, sm, s>>>(B.d, B.rows, first ? 1 : 0,
+                                                       lin_only ? 1 : 0);
   ++g_launches;
 }
 
