@@ -54,6 +54,10 @@ struct ds_batch_s {
   int last_iters = 0;
   cudaEvent_t ev_done = nullptr;
   std::vector<cudaEvent_t> ev_in;
+  // side stream of the linearisation: the ORB pass runs beside the ICP pass (both only add
+  // into the block table and the gradient)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool error = false;
 };
 
@@ -317,7 +321,11 @@ void destroy_batch(ds_batch_s* b) {
   if (b->ev_made)
     for (int i = 0; i < DS_MAX_ITERS; ++i)
       for (int k = 0; k < 5; ++k) cudaEventDestroy(b->ev[i][k]);
+  if (b->side) cudaStreamSynchronize(b->side);
   if (b->ev_done) cudaEventDestroy(b->ev_done);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
+  if (b->side) cudaStreamDestroy(b->side);
   for (auto e : b->ev_in) cudaEventDestroy(e);
   dfree(b->d_descs);
   dfree(b->d_tab);
@@ -392,7 +400,10 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   T.max_tasks = max_tasks;
   T.max_nt = max_nt;
   T.words = b->d_words;
-  if (cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming) != cudaSuccess) {
+  if (cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess) {
     destroy_batch(b);
     return DS_ERR_CUDA;
   }
@@ -423,6 +434,18 @@ void enqueue_factor_solve(ds_batch_s* b) {
   }
 }
 
+// ICP on the batch stream, ORB beside it on the side stream (fork / join through events, which
+// stream capture turns into graph edges).
+void linearize_data_terms(ds_batch_s* b, cudaStream_t s) {
+  const BatchTabs& B = b->tabs;
+  cudaEventRecord(b->ev_fork, s);
+  cudaStreamWaitEvent(b->side, b->ev_fork, 0);
+  launch_orb(B, b->side);
+  cudaEventRecord(b->ev_join, b->side);
+  launch_icp(B, s);
+  cudaStreamWaitEvent(s, b->ev_join, 0);
+}
+
 void enqueue_solve(ds_batch_s* b, int iters) {
   cudaStream_t s = b->stream;
   const BatchTabs& B = b->tabs;
@@ -431,8 +454,7 @@ void enqueue_solve(ds_batch_s* b, int iters) {
     b->cur_it = it;
     trace(b, it, 0);
     launch_iter_begin(B, s);
-    launch_icp(B, s);
-    launch_orb(B, s);
+    linearize_data_terms(b, s);
     if (b->fp64)
       launch_arap_assemble<double>(B, it == 0, false, s);
     else
@@ -1285,8 +1307,7 @@ int ds_linearize(ds_handle h, double w_arap_in, double* A_nn, double* b_n, doubl
   if (!first)
     cudaMemcpyAsync(h->d_acc + ACC_W_ARAP, &w_arap_in, sizeof(double), cudaMemcpyHostToDevice, s);
   launch_iter_begin(B, s);
-  launch_icp(B, s);
-  launch_orb(B, s);
+  linearize_data_terms(h->self, s);
   launch_arap_assemble<float>(B, first, true, s);
   rc = sync_status(h);
   if (rc) return rc;
