@@ -48,6 +48,15 @@ CHOL_TRAFFIC = {"chol_sha256": "5eb09e6b651e9cb2", "precision": 2, "streams": 32
                 "bytes": 673264640 + 348546560}
 
 
+def _measured_bf16():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1900.0   # earlier GB300 measurement, used when the file is absent
+
+
 def _chol_traffic(prec, streams):
     src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2007_08576_gb300",
                        "csrc", "chol.cu")
@@ -197,7 +206,7 @@ def run_gpu(args):
     dframes = [dev_frames(sc) for sc in scenes]
 
     # ---------------------------------------------------------------- batched mixed precision
-    prm = d.default_params(precision=prec)
+    prm = d.default_params(precision=prec, factor_tc=1 if args.factor_tc else 0)
     handles, hstreams = [], []
     for j in range(S):
         sc = scenes[j % n_scenes]
@@ -307,7 +316,7 @@ def run_gpu(args):
     if rank == 0 and args.served_frames > 0:
         rng = np.random.default_rng(7)
         rates = rng.uniform(15.0, 60.0, S)
-        srv = Server(GpuEngine(d.default_params(precision=prec)), budget_bytes=int(0.6 * torch.cuda.mem_get_info()[0]))
+        srv = Server(GpuEngine(d.default_params(precision=prec, factor_tc=1 if args.factor_tc else 0)), budget_bytes=int(0.6 * torch.cuda.mem_get_info()[0]))
         for j in range(S):
             sc = scenes[j % n_scenes]
             srv.open_stream(j, StreamSpec(sc.template_depth, sc.K, sc.nodes, max_matches=M))
@@ -339,12 +348,19 @@ def run_gpu(args):
     flops_per_step = S * ITERS * n ** 3 / 3.0
     factor_ms = phase[1] / K
     achieved = flops_per_step / (factor_ms * 1e-3) / 1e12
+    bound = "alu"
     if prec == 0:
         peak, peak_src = FP64_NOMINAL_TFLOPS, "nominal GB300 FP64 rate"
+    elif args.factor_tc:
+        # tensor-pipe work: three TF32 products per FP32 product; peak = measured bf16 burst x the
+        # nominal dense TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s)
+        bound = "tensor"
+        achieved *= 3.0
+        peak, peak_src = _measured_bf16() * 1.1 / 2.25, "measured bf16 burst x nominal tf32/bf16"
     else:
         peak, peak_src = FP32_SIMT_TFLOPS, "152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz"
     dgemm = measure_dgemm_tflops(torch, dev) if prec == 0 else None
-    traffic = _chol_traffic(prec, S)
+    traffic = None if args.factor_tc else _chol_traffic(prec, S)
 
     result = None
     if rank == 0:
@@ -358,6 +374,7 @@ def run_gpu(args):
             "data": "synthetic (seeded heightfield + deformation + camera motion, ray-cast depth)",
             "config": {"workload": WORKLOAD, "template": "320x240", "control_points": N,
                        "matches": M, "gn_iters": ITERS, "precision": args.precision,
+                       "factor": "tensor cores (tcgen05, 3xTF32)" if args.factor_tc else "FP32 SIMT tile kernel",
                        "streams_per_batch": S, "distinct_scenes": n_scenes, "frames_per_scene": F,
                        "step": f"one frame of each of {S} streams, one batched solve",
                        "l2": "flushed (256 MB write) before each step", "parallelism": f"replicas x{world}"},
@@ -371,13 +388,18 @@ def run_gpu(args):
             "e2e": {"value": round(world * S * K / e2e_tot, 3), "unit": "frames/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
-            "roofline": {"bound": "alu", "kernel": "k_chol_dag (persistent tile Cholesky, all problems)",
+            "roofline": {"bound": bound,
+                         "kernel": ("k_chol_tc (persistent tile Cholesky on tcgen05, all problems)"
+                                    if args.factor_tc and prec != 0 else
+                                    "k_chol_dag (persistent tile Cholesky, all problems)"),
                          "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "traffic_unit": "DRAM bytes per launch (ncu)",
                          "algorithmic_bytes": int(2 * S * n * n * (8 if prec == 0 else 4)),
                          "peak_source": peak_src,
-                         "algorithmic": "n^3/3 flop per factorisation, 10 per frame",
+                         "algorithmic": ("3 x n^3/3 TF32 flop per factorisation, 10 per frame"
+                                         if bound == "tensor" else
+                                         "n^3/3 flop per factorisation, 10 per frame"),
                          "dgemm_measured_tflops": round(dgemm, 4) if dgemm else None},
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
@@ -456,6 +478,8 @@ def main():
     ap.add_argument("--frames", type=int, default=4, help="frames per scene (cycled)")
     ap.add_argument("--served-frames", type=int, default=2000, dest="served_frames")
     ap.add_argument("--no-cpu", action="store_true", dest="no_cpu")
+    ap.add_argument("--factor-tc", action="store_true", dest="factor_tc",
+                    help="FP32 factorisation on the tensor cores (tcgen05, 3xTF32)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3

@@ -87,6 +87,10 @@ typedef struct {
   int32_t precision;        /* ds_precision                                                      */
   int32_t refine_steps;     /* refinement steps in DS_PREC_FP64 / DS_PREC_FP32_REFINE (0..4)     */
   int32_t use_graph;        /* 1: replay the GN loop as a CUDA graph (default), 0: plain launches */
+  int32_t factor_tc;        /* FP32 precisions: 0 = factorisation on the FP32 SIMT pipes (default),
+                             * 1 = on the tensor cores (tcgen05 kind::tf32, each product as three
+                             * TF32 terms hi*hi + hi*lo + lo*hi, FP32-level accuracy). Ignored in
+                             * DS_PREC_FP64. Handles of one batch must agree.                     */
 } ds_params;
 
 /* Per-solve statistics (filled by ds_solve when its `out` is not NULL). */

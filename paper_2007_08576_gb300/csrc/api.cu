@@ -342,10 +342,12 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   const bool fp64 = hs[0]->prec_fp64;
   const int prec = hs[0]->prm.precision;
   const int steps = prec == DS_PREC_FP32 ? 0 : hs[0]->prm.refine_steps;
+  const int ftc = fp64 ? 0 : hs[0]->prm.factor_tc;
   for (int i = 1; i < n; ++i) {
     const int ps = hs[i]->prm.precision == DS_PREC_FP32 ? 0 : hs[i]->prm.refine_steps;
+    const int ft = hs[i]->prec_fp64 ? 0 : hs[i]->prm.factor_tc;
     if (hs[i]->prec_fp64 != fp64 || (hs[i]->prm.precision == DS_PREC_FP32) != (prec == DS_PREC_FP32) ||
-        ps != steps)
+        ps != steps || ft != ftc)
       return DS_ERR_ARG;
   }
   ds_batch_s* b = new ds_batch_s();
@@ -397,6 +399,7 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   T.res = b->d_tab + off; T.n_res = (int)res.size(); off += res.size();
   T.chol = b->d_tab + off; T.n_chol = (int)chol.size(); off += chol.size();
   T.orb_ctas = 16;
+  T.factor_tc = ftc;
   T.max_tasks = max_tasks;
   T.max_nt = max_nt;
   T.words = b->d_words;
@@ -548,7 +551,7 @@ bool valid_params(const ds_params& p) {
          p.eps_damp >= 0 && p.keep_frac >= 0 && p.keep_frac <= 1 && p.sigma_blend_scale > 0 &&
          p.sigma_arap_scale > 0 && p.precision >= 0 && p.precision <= 2 && p.refine_steps >= 0 &&
          p.refine_steps <= 3 && p.w_orb >= 0 && p.w_angle >= 0 && p.w_rot >= 0 &&
-         p.w_arap0 >= 0;
+         p.w_arap0 >= 0 && (p.factor_tc == 0 || p.factor_tc == 1);
 }
 
 bool is_host_ptr(const void* p);
@@ -576,6 +579,7 @@ void ds_default_params(ds_params* p) {
   p->precision = DS_PREC_FP64;
   p->refine_steps = 2;
   p->use_graph = 1;
+  p->factor_tc = 0;
 }
 
 const char* ds_status_str(int status) {

@@ -1042,10 +1042,412 @@ int chol_tile() {
 template int chol_tile<float>();
 template int chol_tile<double>();
 
+// ----------------------------------------------------------------------------- tensor-core factor
+
+// FP32 factorisation on the 5th-generation tensor cores. The same left-looking tile tasks as
+// k_chol_dag, with every 64 x 64 x 64 product done by tcgen05.mma (kind::tf32, M = N = 64,
+// accumulator in tensor memory) in three terms, A_hi B_hi + A_hi B_lo + A_lo B_hi, where
+// x = x_hi + x_lo with x_hi the round-to-nearest TF32 value of x: products accurate to about
+// 2^-21 relative, i.e. at FP32 level for the refinement that follows.
+//
+// Packed slots: 8192 floats per tile, TF32 hi part then lo part, each in the canonical K-major
+// layout without swizzle (core matrices of 8 rows x 16 bytes; element (r, m) at float offset
+// ((r / 8) * 16 + m / 4) * 32 + (r % 8) * 4 + m % 4; K-direction core stride 128 B, row-group
+// stride 2048 B). Off-diagonal slot (i, k) holds L_ik (rows r, K index m); diagonal slot (j, j)
+// holds X = L_jj^-1 (rows c, K index m), the B operand of C X^T.
+//
+// Thread 0 runs each task's K loop alone: it waits for the producers, streams the two operand
+// slots of step k into one of two shared-memory stages with bulk copies, issues the 24 MMAs and
+// commits them to the stage's mbarrier, which frees the stage for step k + 2. All 256 threads
+// then read the accumulator (warp w: rows 16 (w % 4) + lane for lanes < 16, columns
+// 32 (w / 4) .. + 31) for the diagonal Cholesky (SIMT, potrf_regs) or for C = A_ij - acc, whose
+// product with X^T is one more 3-term MMA.
+#ifndef DS_TC_PROF
+#define DS_TC_PROF(slot, t0)
+#endif
+
+namespace tc {
+
+constexpr int kSlot = 8192;             // floats per packed slot (hi + lo)
+constexpr unsigned kSlotBytes = 32768;
+constexpr unsigned kStageBytes = 2 * kSlotBytes;
+constexpr unsigned kSmem = 2 * kStageBytes;
+// kind::tf32, D = F32 (bit 4), A = B = TF32 (bits 7, 10), K-major A and B, N = 64, M = 64
+constexpr unsigned kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) | ((64u >> 4) << 24);
+
+__device__ __forceinline__ int kmaj(int r, int m) {
+  return ((r >> 3) * 16 + (m >> 2)) * 32 + (r & 7) * 4 + (m & 3);
+}
+__device__ __forceinline__ uint64_t sdesc(unsigned saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) |
+         ((uint64_t)(2048 >> 4) << 32) | ((uint64_t)1 << 46);
+}
+__device__ __forceinline__ float tf32_rna(float x) {
+  unsigned u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+  return __uint_as_float(u);
+}
+__device__ __forceinline__ void mma(unsigned tmem, uint64_t a, uint64_t b, unsigned acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+// D (+)= A B^T over K = 64 for two packed slots in shared memory, three TF32 terms
+__device__ __forceinline__ void mma_3x(unsigned tmem, const float* a, const float* b,
+                                       bool accumulate) {
+  const unsigned sa = smem_u32(a), sb = smem_u32(b);
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const unsigned ah = t == 2 ? sa + 16384u : sa, bh = t == 1 ? sb + 16384u : sb;
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk)
+      mma(tmem, sdesc(ah + 256u * kk), sdesc(bh + 256u * kk),
+          (accumulate || t > 0 || kk > 0) ? 1u : 0u);
+  }
+}
+__device__ __forceinline__ void commit(unsigned long long* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// this thread's 32 accumulator values (lanes >= 16 receive values of unused lanes)
+__device__ __forceinline__ void tmem_read32(unsigned tmem, float (&v)[32]) {
+  const int warp = threadIdx.x >> 5;
+  const unsigned ta = tmem + ((unsigned)(32 * (warp & 3)) << 16) + 32u * (warp >> 2);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    unsigned r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(ta + 16u * h));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[16 * h + i] = __uint_as_float(r[i]);
+  }
+}
+// writes 4 consecutive values (row r, columns m .. m + 3, m % 4 == 0) of a tile into a packed
+// slot as hi and lo parts
+__device__ __forceinline__ void put4(float* slot, int r, int m, float a, float b, float c,
+                                     float d) {
+  const float ha = tf32_rna(a), hb = tf32_rna(b), hc = tf32_rna(c), hd = tf32_rna(d);
+  const int o = kmaj(r, m);
+  *reinterpret_cast<float4*>(slot + o) = make_float4(ha, hb, hc, hd);
+  *reinterpret_cast<float4*>(slot + 4096 + o) = make_float4(
+      tf32_rna(a - ha), tf32_rna(b - hb), tf32_rna(c - hc), tf32_rna(d - hd));
+}
+__device__ __forceinline__ void put4_global(float* slot, int r, int m, float a, float b, float c,
+                                            float d) {
+  const float ha = tf32_rna(a), hb = tf32_rna(b), hc = tf32_rna(c), hd = tf32_rna(d);
+  const int o = kmaj(r, m);
+  __stcg(reinterpret_cast<float4*>(slot + o), make_float4(ha, hb, hc, hd));
+  __stcg(reinterpret_cast<float4*>(slot + 4096 + o),
+         make_float4(tf32_rna(a - ha), tf32_rna(b - hb), tf32_rna(c - hc), tf32_rna(d - hd)));
+}
+
+}  // namespace tc
+
+__global__ __launch_bounds__(256, 1) void k_chol_tc(const ProbDesc* const* __restrict__ descs,
+                                                    const int2* __restrict__ tickets,
+                                                    int nticket, int* __restrict__ head,
+                                                    int* __restrict__ err,
+                                                    unsigned long long budget_ns) {
+  constexpr int TB = 64, LDS = TB + 1, RT = 4;
+  constexpr int LDT = TileCfg<float, TB>::LDT;
+  extern __shared__ __align__(1024) unsigned char smtc[];
+  float* buf = reinterpret_cast<float*>(smtc);  // stage s: A slot at s * 16384, B slot + 8192
+  __shared__ __align__(8) unsigned long long bcopy[2], bmma[2], bfin;
+  __shared__ unsigned s_tmem;
+  __shared__ int s_t, s_ok;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tr = (tid / 16) * RT, tc_ = (tid % 16) * RT;
+  // accumulator coordinates of this thread (valid for lane < 16)
+  const int arow = 16 * (warp & 3) + lane, acol = 32 * (warp >> 2);
+  if (tid == 0) {
+    mbar_init(&bcopy[0]);
+    mbar_init(&bcopy[1]);
+    mbar_init(&bmma[0]);
+    mbar_init(&bmma[1]);
+    mbar_init(&bfin);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(
+                     smem_u32(&s_tmem))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const unsigned tmem = s_tmem;
+  unsigned cph[2] = {0u, 0u};   // thread 0: parity of the next copy wait per stage
+  int mc[2] = {0, 0}, mw[2] = {0, 0};  // thread 0: commits issued / waited per stage
+  unsigned fph = 0u;            // all threads: parity of the next task-level MMA wait
+  for (;;) {
+    if (tid == 0) s_t = atomicAdd(head, 1);
+    __syncthreads();
+    const int t = s_t;
+    if (t >= nticket) break;
+    const int2 pt = tickets[t];
+    const LinProblem& P = descs[pt.x]->lp;
+    const int4 tk = P.tasks[pt.y];
+#if defined(DS_TASK_TRACE)
+    if (tid == 0) ds_trace_mark(t, 0);
+#endif
+    const bool diag = (tk.y & 15) == 0;
+    const int i = tk.z, j = tk.w, nt = P.nt, n = P.n;
+    int* pdone = P.cnt;
+    int* tdone = P.cnt + nt;
+    float* A = (float*)P.A;
+    float* Lp = (float*)P.Lp;
+    const int K = j;
+    // ---- K loop (thread 0): C = A_ij - sum_{k < j} L_ik L_jk^T accumulated in tensor memory
+    if (tid == 0) {
+      const float* Li = Lp + tile_slot(i, 0) * tc::kSlot;
+      const float* Lj = Lp + tile_slot(j, 0) * tc::kSlot;
+      auto wait_deps = [&](int k) {
+        return wait_ge(&tdone[i * nt + k], 1, err, budget_ns) &&
+               (diag || wait_ge(&tdone[j * nt + k], 1, err, budget_ns));
+      };
+      auto issue = [&](int k, int s) {
+        __threadfence();
+        fence_proxy_async_global();
+        float* st = buf + s * 16384;
+        mbar_expect(&bcopy[s], diag ? tc::kSlotBytes : 2 * tc::kSlotBytes);
+        bulk_load(st, Li + (size_t)k * tc::kSlot, tc::kSlotBytes, &bcopy[s]);
+        if (!diag) bulk_load(st + 8192, Lj + (size_t)k * tc::kSlot, tc::kSlotBytes, &bcopy[s]);
+      };
+      auto wait_mma = [&](int s) {
+        const bool ok = mbar_wait(&bmma[s], (unsigned)(mw[s] & 1), err, budget_ns);
+        ++mw[s];
+        return ok;
+      };
+      bool ok = *(volatile int*)err == 0;
+      int issued = 0;   // copies issued in this task; each is waited exactly once below
+      if (K > 0 && ok) {
+        ok = wait_deps(0);
+        if (ok) {
+          issue(0, 0);
+          issued = 1;
+        }
+      }
+      for (int k = 0; k < issued; ++k) {
+        const int s = k & 1;
+        [[maybe_unused]] long long c0 = clock64();
+        const bool got = mbar_wait(&bcopy[s], cph[s], err, budget_ns);
+        DS_TC_PROF(0, c0);   // waiting for the operand copies
+        cph[s] ^= 1u;
+        if (!got) {   // timed out (error word raised): no further copies or products
+          ok = false;
+          break;
+        }
+        tc::fence_after();
+        const float* st = buf + s * 16384;
+        c0 = clock64();
+        tc::mma_3x(tmem, st, diag ? st : st + 8192, k > 0);
+        tc::commit(&bmma[s]);
+        DS_TC_PROF(1, c0);   // issuing the products
+        ++mc[s];
+        if (ok && k + 1 < K) {
+          c0 = clock64();
+          if (mw[s ^ 1] < mc[s ^ 1]) ok = wait_mma(s ^ 1);   // step k - 1 released stage s ^ 1
+          DS_TC_PROF(2, c0);   // waiting for the previous step's products
+          c0 = clock64();
+          if (ok) ok = wait_deps(k + 1);
+          DS_TC_PROF(3, c0);   // waiting for producers
+          if (ok) {
+            issue(k + 1, s ^ 1);
+            ++issued;
+          }
+        }
+      }
+      tc::commit(&bfin);   // arrives when every product issued so far has completed
+      for (int s = 0; s < 2; ++s)
+        while (mw[s] < mc[s]) wait_mma(s);
+      s_ok = ok;
+    }
+    __syncthreads();
+    {
+      const bool got = mbar_wait(&bfin, fph, err, budget_ns);
+      fph ^= 1u;
+      if (__syncthreads_or(!got)) {
+        break;
+      }
+    }
+    tc::fence_after();
+#if defined(DS_TASK_TRACE)
+    if (tid == 0) ds_trace_mark(t, 1);
+#endif
+    const bool ok = s_ok;
+    float acc[32];
+    if (ok && K > 0) {
+      tc::tmem_read32(tmem, acc);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 32; ++e) acc[e] = 0.f;
+    }
+    tc::fence_before();
+    __syncthreads();   // accumulator read before the stage buffers / tensor memory are reused
+    if (ok) {
+      float* Ls = buf;
+      float* Xs = Ls + TB * LDS;
+      if (diag) {
+        // ---- DIAG(j): C = A_jj - acc (lower; identity padding), L_jj = chol(C), X = L_jj^-1
+        float* Pt = Xs + TB * LDS;
+        float* Dsm = Pt + 2 * RT * LDT;
+        float* Tm = Dsm + 4 * RT * RT;
+        const int r0 = j * TB;
+        if (lane < 16) {
+          const int r = arow;
+#pragma unroll
+          for (int e = 0; e < 32; ++e) {
+            const int c = acol + e;
+            float x;
+            if (r0 + r < n && r0 + c < n)
+              x = c <= r ? ldcg(A + (size_t)(r0 + r) * n + r0 + c) - acc[e] : 0.f;
+            else
+              x = (r == c) ? 1.f : 0.f;
+            Ls[r * LDS + c] = x;
+          }
+        }
+        for (int e = tid; e < TB * LDS; e += blockDim.x) Xs[e] = 0.f;
+        __syncthreads();
+        float v[RT][RT];
+#pragma unroll
+        for (int a = 0; a < RT; ++a)
+#pragma unroll
+          for (int b = 0; b < RT; ++b) v[a][b] = Ls[(tr + a) * LDS + tc_ + b];
+        __syncthreads();
+        potrf_regs<float, TB>(v, Ls, Xs, Pt, Dsm, Tm, r0, P.status);
+#if defined(DS_TASK_TRACE)
+        if (tid == 0) ds_trace_mark(t, 3);
+#endif
+        float* D = (float*)P.Dinv + (size_t)j * TB * TB;
+        float* S = Lp + tile_slot(j, j) * tc::kSlot;
+        for (int e = tid; e < TB * TB; e += blockDim.x) {
+          const int r = e / TB, c = e % TB;
+          __stcg(D + e, c <= r ? Xs[r * LDS + c] : 0.f);
+          if (c <= r && r0 + r < n) __stcg(A + (size_t)(r0 + r) * n + r0 + c, Ls[r * LDS + c]);
+        }
+        // X in the packed K-major hi / lo form (rows c, K index m), 4 columns per thread step
+        for (int e = tid; e < TB * TB / 4; e += blockDim.x) {
+          const int r = e / (TB / 4), m = 4 * (e % (TB / 4));
+          float x4[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) x4[q] = m + q <= r ? Xs[r * LDS + m + q] : 0.f;
+          tc::put4_global(S, r, m, x4[0], x4[1], x4[2], x4[3]);
+        }
+      } else {
+        // ---- OFF(i, j): C = A_ij - acc, L_ij = C X^T with X = L_jj^-1 from slot (j, j)
+        float* Cs = buf;            // C as a packed operand (hi / lo)
+        float* Xp = buf + 8192;     // X slot
+        if (tid == 0) {
+          s_ok = wait_ge(&pdone[j], 1, err, budget_ns);
+          if (s_ok) {
+            __threadfence();
+            fence_proxy_async_global();
+            mbar_expect(&bcopy[0], tc::kSlotBytes);
+            bulk_load(Xp, Lp + tile_slot(j, j) * tc::kSlot, tc::kSlotBytes, &bcopy[0]);
+          }
+        }
+        if (lane < 16) {
+          const int r = arow, rg = i * TB + r;
+#pragma unroll
+          for (int g = 0; g < 8; ++g) {
+            const int c = acol + 4 * g, cg = j * TB + c;
+            float a4[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              a4[q] = (rg < n && cg + q < n) ? ldcg(A + (size_t)rg * n + cg + q) - acc[4 * g + q]
+                                             : 0.f;
+            tc::put4(Cs, r, c, a4[0], a4[1], a4[2], a4[3]);
+          }
+        }
+        fence_proxy_async_shared();
+        __syncthreads();
+        const bool dok = s_ok;
+        if (dok) {
+          if (tid == 0) {
+            const bool got = mbar_wait(&bcopy[0], cph[0], err, budget_ns);
+            cph[0] ^= 1u;
+            if (got) {
+              tc::fence_after();
+              tc::mma_3x(tmem, Cs, Xp, false);
+            }
+            tc::commit(&bfin);
+          }
+          const bool got = mbar_wait(&bfin, fph, err, budget_ns);
+          fph ^= 1u;
+          if (__syncthreads_or(!got)) {
+            break;
+          }
+          tc::fence_after();
+          float l[32];
+          tc::tmem_read32(tmem, l);
+          tc::fence_before();
+          if (lane < 16) {
+            const int r = arow, rg = i * TB + r;
+            float* S = Lp + tile_slot(i, j) * tc::kSlot;
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+              const int c = acol + 4 * g, cg = j * TB + c;
+              if (rg < n) {
+                if (cg + 3 < n && (n & 3) == 0) {
+                  __stcg(reinterpret_cast<float4*>(A + (size_t)rg * n + cg),
+                         make_float4(l[4 * g], l[4 * g + 1], l[4 * g + 2], l[4 * g + 3]));
+                } else {
+#pragma unroll
+                  for (int q = 0; q < 4; ++q)
+                    if (cg + q < n) __stcg(A + (size_t)rg * n + cg + q, l[4 * g + q]);
+                }
+              }
+              tc::put4_global(S, r, c, l[4 * g], l[4 * g + 1], l[4 * g + 2], l[4 * g + 3]);
+            }
+          }
+        }
+      }
+    }
+    // generic shared writes above happen before the next task's bulk copies into the same bytes
+    fence_proxy_async_shared();
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      fence_proxy_async_global();
+#if defined(DS_TASK_TRACE)
+      ds_trace_mark(t, 2);
+#endif
+      if (diag)
+        atomicExch(&pdone[j], 1);
+      else
+        atomicExch(&tdone[i * nt + j], 1);
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
+  }
+}
+
 template <typename T>
 size_t chol_packed_elems(int nt) {
   constexpr int TB = sizeof(T) == 8 ? 32 : 64;
-  return tile_slot(nt, 0) * (size_t)TB * TileCfg<T, TB>::LDT;
+  // FP32: room for the tensor-core slots (hi + lo, K-major), which are larger than the SIMT
+  // kernel's transposed padded tiles; FP64: transposed padded tiles
+  return sizeof(T) == 4 ? tile_slot(nt, 0) * (size_t)tc::kSlot
+                        : tile_slot(nt, 0) * (size_t)TB * TileCfg<T, TB>::LDT;
 }
 template size_t chol_packed_elems<float>(int);
 template size_t chol_packed_elems<double>(int);
@@ -1063,6 +1465,19 @@ static int num_sms() {
 
 template <typename T>
 void launch_chol_dag(const BatchTabs& B, cudaStream_t s) {
+  if (sizeof(T) == 4 && B.factor_tc) {
+    static int per_sm = 0;
+    if (!per_sm) {
+      cudaFuncSetAttribute(k_chol_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_tc, 256, tc::kSmem);
+      per_sm = std::max(1, std::min(per_sm, 2));
+    }
+    const int grid = std::min(B.n_chol, per_sm * num_sms());
+    k_chol_tc<<<grid, 256, tc::kSmem, s>>>(B.d, B.chol, B.n_chol, B.words + 0, B.words + 5,
+                                            2000000000ull);
+    ++g_launches;
+    return;
+  }
   constexpr int TB = sizeof(T) == 8 ? 32 : 64;
   const size_t sm = 4 * sizeof(T) * TB * TileCfg<T, TB>::LDT;
   static bool attr = false;

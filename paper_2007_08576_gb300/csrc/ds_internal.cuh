@@ -150,6 +150,7 @@ struct BatchTabs {
   int orb_ctas;              // CTAs per problem of the ORB pass (grid-stride over M)
   const int2* chol;          // (problem, task) per factorisation ticket, in claim order
   int n_chol;
+  int factor_tc;             // FP32 factorisation on the tensor cores (1) or the SIMT pipes (0)
   int max_tasks;             // max factorisation tasks over the problems
   int max_nt;                // max tile rows over the problems
   int* words;                // [0] factorisation head, [1..4] solve heads, [5] timeout word
@@ -167,7 +168,7 @@ void launch_iter_end(const BatchTabs& B, int it, bool step, cudaStream_t s);
 template <typename T>
 int chol_tile();
 template <typename T>
-size_t chol_packed_elems(int nt);  // elements of the packed L tiles of an nt x nt tile matrix
+size_t chol_packed_elems(int nt);  // elements of the packed L tiles (either FP32 kernel's layout)
 template <typename T>
 void launch_chol_dag(const BatchTabs& B, cudaStream_t s);
 template <typename T>

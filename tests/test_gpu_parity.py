@@ -368,3 +368,62 @@ def test_batch_rejects_mixed_precision(d, tiny):
     assert e.value.status == d.DS_ERR_ARG
     a.close()
     b.close()
+
+
+# ----------------------------------------------------------------------------- tensor-core factor
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_tensor_core_factor_matches_oracle_tiny_and_ragged(d, tiny, mid, prec):
+    """FP32 factorisation on tcgen05 (three TF32 terms per product): the same parity bar."""
+    for sc in (tiny, mid):
+        fr = sc.frames[0]
+        p = d.default_params(precision=prec, factor_tc=1)
+        s, st, q, t = gpu_frame(d, sc, fr, p)
+        tpl, res = _oracle(sc, fr, oracle_params(p))
+        err = np.abs(tpl.g + t - res.pos).max()
+        assert err <= POS_TOL_MM, err
+        rel = np.abs(np.array(st.cost[:10]) - np.array(res.costs)) / np.array(res.costs)
+        assert rel.max() <= COST_RTOL, rel
+        s.close()
+
+
+def test_tensor_core_factor_full_size_frame(d):
+    sc = scene(CONFIGS["seq_320x240_n256"], 1000)
+    fr = sc.frames[0]
+    p = d.default_params(precision=2, factor_tc=1)
+    s, st, q, t = gpu_frame(d, sc, fr, p)
+    tpl, res = _oracle(sc, fr, oracle_params(p))
+    err = np.abs(tpl.g + t - res.pos).max()
+    assert err <= POS_TOL_MM, err
+    rel = np.abs(np.array(st.cost[:10]) - np.array(res.costs)) / np.array(res.costs)
+    assert rel.max() <= COST_RTOL, rel
+    s.close()
+
+
+def test_tensor_core_factor_batch_equals_simt_and_agreement_rule(d, tiny, mid):
+    """An uneven batch factored on the tensor cores gives the SIMT batch's result within the
+    parity tolerance; handles that disagree on the factor kernel cannot share a batch."""
+    outs = {}
+    for ftc in (0, 1):
+        p = d.default_params(precision=2, factor_tc=ftc)
+        solvers = []
+        for sc in (mid, tiny, mid):
+            s = d.Solver(sc.template_depth, sc.K, sc.nodes, p)
+            fr = sc.frames[0]
+            s.submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+            solvers.append(s)
+        d.ds_solve_batch([s.h for s in solvers], 10)
+        outs[ftc] = [s.deformation64()[1] for s in solvers]
+        for s in solvers:
+            s.close()
+    for a, b in zip(outs[0], outs[1]):
+        assert np.abs(a - b).max() <= POS_TOL_MM
+    a = d.Solver(tiny.template_depth, tiny.K, tiny.nodes, d.default_params(precision=2))
+    b = d.Solver(tiny.template_depth, tiny.K, tiny.nodes,
+                 d.default_params(precision=2, factor_tc=1))
+    with pytest.raises(d.DsError) as e:
+        d.ds_batch_create([a.h, b.h])
+    assert e.value.status == d.DS_ERR_ARG
+    a.close()
+    b.close()
