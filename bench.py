@@ -57,6 +57,15 @@ def _measured_bf16():
         return 1900.0   # earlier GB300 measurement, used when the file is absent
 
 
+def _measured_hbm():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0   # earlier GB300 measurement, used when the file is absent
+
+
 def _chol_traffic(prec, streams):
     src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2007_08576_gb300",
                        "csrc", "chol.cu")
@@ -206,7 +215,8 @@ def run_gpu(args):
     dframes = [dev_frames(sc) for sc in scenes]
 
     # ---------------------------------------------------------------- batched mixed precision
-    prm = d.default_params(precision=prec, factor_tc=1 if args.factor_tc else 0)
+    solver_id = 1 if args.solver == "block_jacobi" else 0
+    prm = d.default_params(precision=prec, factor_tc=1 if args.factor_tc else 0, solver=solver_id)
     handles, hstreams = [], []
     for j in range(S):
         sc = scenes[j % n_scenes]
@@ -233,7 +243,7 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize()
     k0 = d.ds_get_counters(None)
-    step_ms, phase = [], np.zeros(4)
+    step_ms, phase, host_ms = [], np.zeros(4), []
     with ClockSampler(local) as clk:
         for i in range(K):
             with torch.cuda.stream(stream):
@@ -241,7 +251,9 @@ def run_gpu(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
+            th = time.perf_counter()
             step(W + i, e0)
+            host_ms.append((time.perf_counter() - th) * 1e3)
             e1.record(stream)
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
@@ -316,7 +328,8 @@ def run_gpu(args):
     if rank == 0 and args.served_frames > 0:
         rng = np.random.default_rng(7)
         rates = rng.uniform(15.0, 60.0, S)
-        srv = Server(GpuEngine(d.default_params(precision=prec, factor_tc=1 if args.factor_tc else 0)), budget_bytes=int(0.6 * torch.cuda.mem_get_info()[0]))
+        srv = Server(GpuEngine(d.default_params(precision=prec, factor_tc=1 if args.factor_tc else 0,
+                                                solver=solver_id)), budget_bytes=int(0.6 * torch.cuda.mem_get_info()[0]))
         for j in range(S):
             sc = scenes[j % n_scenes]
             srv.open_stream(j, StreamSpec(sc.template_depth, sc.K, sc.nodes, max_matches=M))
@@ -349,7 +362,17 @@ def run_gpu(args):
     factor_ms = phase[1] / K
     achieved = flops_per_step / (factor_ms * 1e-3) / 1e12
     bound = "alu"
-    if prec == 0:
+    unit = "TFLOP/s"
+    if solver_id == 1:
+        # no factorisation: the linearisation dominates; its algorithmic bytes are the ICP pass's
+        # 64 B per template point (32 B template point + weights, 32 B gathered live point +
+        # normal) per iteration
+        pts = sum(int((sc.template_depth > 0).sum()) for sc in scenes) * S / len(scenes)
+        bytes_per_step = 64.0 * pts * ITERS
+        achieved = bytes_per_step / (phase[0] / K * 1e-3) / 1e9
+        bound, unit = "hbm", "GB/s"
+        peak, peak_src = _measured_hbm(), "MEASURED_PEAKS.json hbm_gbs"
+    elif prec == 0:
         peak, peak_src = FP64_NOMINAL_TFLOPS, "nominal GB300 FP64 rate"
     elif args.factor_tc:
         # tensor-pipe work: three TF32 products per FP32 product; peak = measured bf16 burst x the
@@ -360,7 +383,7 @@ def run_gpu(args):
     else:
         peak, peak_src = FP32_SIMT_TFLOPS, "152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz"
     dgemm = measure_dgemm_tflops(torch, dev) if prec == 0 else None
-    traffic = None if args.factor_tc else _chol_traffic(prec, S)
+    traffic = None if (args.factor_tc or solver_id == 1) else _chol_traffic(prec, S)
 
     result = None
     if rank == 0:
@@ -374,6 +397,7 @@ def run_gpu(args):
             "data": "synthetic (seeded heightfield + deformation + camera motion, ray-cast depth)",
             "config": {"workload": WORKLOAD, "template": "320x240", "control_points": N,
                        "matches": M, "gn_iters": ITERS, "precision": args.precision,
+                       "solver": args.solver,
                        "factor": "tensor cores (tcgen05, 3xTF32)" if args.factor_tc else "FP32 SIMT tile kernel",
                        "streams_per_batch": S, "distinct_scenes": n_scenes, "frames_per_scene": F,
                        "step": f"one frame of each of {S} streams, one batched solve",
@@ -383,21 +407,26 @@ def run_gpu(args):
                                         "latency_ms": _stats_ms(plain_ms)},
             "speedup_vs_plain": round(value / (world * plain_fps), 2),
             "served": served,
+            "host_enqueue_ms_per_step": round(float(np.median(host_ms)), 3),
             "phase_ms_per_step": {"linearize": round(phase[0] / K, 4), "factor": round(phase[1] / K, 4),
                                   "solve_refine": round(phase[2] / K, 4), "update": round(phase[3] / K, 4)},
             "e2e": {"value": round(world * S * K / e2e_tot, 3), "unit": "frames/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
             "roofline": {"bound": bound,
-                         "kernel": ("k_chol_tc (persistent tile Cholesky on tcgen05, all problems)"
+                         "kernel": ("linearisation (k_icp + k_orb + k_arap_assemble diagonal blocks)"
+                                    if solver_id == 1 else
+                                    "k_chol_tc (persistent tile Cholesky on tcgen05, all problems)"
                                     if args.factor_tc and prec != 0 else
                                     "k_chol_dag (persistent tile Cholesky, all problems)"),
-                         "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
+                         "achieved": round(achieved, 4), "peak": peak, "unit": unit,
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "traffic_unit": "DRAM bytes per launch (ncu)",
                          "algorithmic_bytes": int(2 * S * n * n * (8 if prec == 0 else 4)),
                          "peak_source": peak_src,
-                         "algorithmic": ("3 x n^3/3 TF32 flop per factorisation, 10 per frame"
+                         "algorithmic": ("64 B per template point per iteration (ICP)"
+                                         if solver_id == 1 else
+                                         "3 x n^3/3 TF32 flop per factorisation, 10 per frame"
                                          if bound == "tensor" else
                                          "n^3/3 flop per factorisation, 10 per frame"),
                          "dgemm_measured_tflops": round(dgemm, 4) if dgemm else None},
@@ -478,6 +507,8 @@ def main():
     ap.add_argument("--frames", type=int, default=4, help="frames per scene (cycled)")
     ap.add_argument("--served-frames", type=int, default=2000, dest="served_frames")
     ap.add_argument("--no-cpu", action="store_true", dest="no_cpu")
+    ap.add_argument("--solver", default="dense", choices=["dense", "block_jacobi"],
+                    help="dense 6N x 6N Cholesky, or per-node 6 x 6 solves (Section 2)")
     ap.add_argument("--factor-tc", action="store_true", dest="factor_tc",
                     help="FP32 factorisation on the tensor cores (tcgen05, 3xTF32)")
     args = ap.parse_args()

@@ -91,6 +91,11 @@ typedef struct {
                              * 1 = on the tensor cores (tcgen05 kind::tf32, each product as three
                              * TF32 terms hi*hi + hi*lo + lo*hi, FP32-level accuracy). Ignored in
                              * DS_PREC_FP64. Handles of one batch must agree.                     */
+  int32_t solver;           /* 0 = one Cholesky of the dense 6N x 6N damped system (default);
+                             * 1 = block-Jacobi: each control point's 6 unknowns from its own 6 x 6
+                             * damped diagonal block (FP64 Cholesky per node), the reading of
+                             * Section 2's "update each W_i independently"; no factorisation of
+                             * the coupled system and no refinement. Handles of one batch agree.  */
 } ds_params;
 
 /* Per-solve statistics (filled by ds_solve when its `out` is not NULL). */

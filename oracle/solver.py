@@ -7,7 +7,8 @@ decomposition; w_ORB = 10 and w_ARAP is rescaled by the summed ICP and ORB weigh
 Readings used here (the CUDA path implements the same ones):
 * the normal equations couple all 6N unknowns (one dense system) and are damped with a fixed
   lambda: A + lambda (diag(A) + eps), lambda = 1e-4, eps = 1e-9, with no accept/reject test, so
-  both sides run the same number of iterations;
+  both sides run the same number of iterations; the paper's "each W_i independently" is the
+  alternative block-Jacobi step (each control point's 6 x 6 diagonal block alone);
 * w_ARAP = w_arap0 * (sum of ICP Tukey weights + w_ORB * sum of ORB weights) / N, evaluated once
   per frame at the warm-start state and then held for the frame;
 * each template point is blended by its 4 nearest control points (3D distance at time 0, ties
@@ -40,6 +41,7 @@ class Params:
     keep_frac: float = 0.5
     n_hyp: int = 30              # Section 2.1
     n_reweight: int = 10         # Section 2.1
+    solver: str = "dense"        # "dense" Cholesky of the 6N system, or "block_jacobi" (per node)
 
 
 @dataclasses.dataclass
@@ -195,6 +197,18 @@ def cholesky_solve(A, b):
     return scipy.linalg.solve_triangular(L.T, y, lower=False)
 
 
+def block_jacobi_solve(A, b):
+    """Section 2 solves the LM step by updating each W_i independently: every control point's
+    6 unknowns from its own 6 x 6 diagonal block of the (damped) normal matrix, the coupling
+    blocks between control points left out. x_i = A_ii^-1 b_i, each by a Cholesky
+    factorisation."""
+    n = A.shape[0]
+    x = np.empty(n)
+    for i in range(0, n, 6):
+        x[i:i + 6] = cholesky_solve(A[i:i + 6, i:i + 6], b[i:i + 6])
+    return x
+
+
 @dataclasses.dataclass
 class FrameResult:
     q: np.ndarray
@@ -228,7 +242,11 @@ def solve_frame(tpl: Template, depth, match_idx, match_xyz, hyp, prm: Params = P
     for _ in range(iters):
         lin, w_arap = linearize(tpl, tgt, q, t, orb, w_arap, prm)
         costs.append(lin.cost)
-        delta = cholesky_solve(damp(lin.A, prm), lin.b)
+        Ad = damp(lin.A, prm)
+        if prm.solver == "block_jacobi":
+            delta = block_jacobi_solve(Ad, lin.b)
+        else:
+            delta = cholesky_solve(Ad, lin.b)
         q, t = dqb.apply_step(q, t, delta)
         states.append((q.copy(), t.copy()))
         if keep_lins:

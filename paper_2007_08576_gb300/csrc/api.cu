@@ -40,6 +40,7 @@ struct ds_batch_s {
   bool own_stream = false;
   bool fp64 = false;
   int refine_steps = 0;
+  bool block_jacobi = false;   // per-node 6 x 6 solves instead of the dense factorisation
   BatchTabs tabs{};
   const ProbDesc** d_descs = nullptr;
   int2* d_tab = nullptr;   // all work tables, back to back
@@ -343,17 +344,19 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   const int prec = hs[0]->prm.precision;
   const int steps = prec == DS_PREC_FP32 ? 0 : hs[0]->prm.refine_steps;
   const int ftc = fp64 ? 0 : hs[0]->prm.factor_tc;
+  const int solver = hs[0]->prm.solver;
   for (int i = 1; i < n; ++i) {
     const int ps = hs[i]->prm.precision == DS_PREC_FP32 ? 0 : hs[i]->prm.refine_steps;
     const int ft = hs[i]->prec_fp64 ? 0 : hs[i]->prm.factor_tc;
     if (hs[i]->prec_fp64 != fp64 || (hs[i]->prm.precision == DS_PREC_FP32) != (prec == DS_PREC_FP32) ||
-        ps != steps || ft != ftc)
+        ps != steps || ft != ftc || hs[i]->prm.solver != solver)
       return DS_ERR_ARG;
   }
   ds_batch_s* b = new ds_batch_s();
   b->hs.assign(hs, hs + n);
   b->fp64 = fp64;
   b->refine_steps = steps;
+  b->block_jacobi = solver == 1;
   b->stream = stream;
   b->own_stream = own;
   std::vector<int2> icp, rows, nodes, vec, res, chol;
@@ -458,6 +461,22 @@ void enqueue_solve(ds_batch_s* b, int iters) {
     trace(b, it, 0);
     launch_iter_begin(B, s);
     linearize_data_terms(b, s);
+    if (b->block_jacobi) {
+      // diagonal blocks and gradient only, then one FP64 6 x 6 Cholesky solve per control point
+      if (b->fp64)
+        launch_arap_assemble<double>(B, it == 0, false, s, true);
+      else
+        launch_arap_assemble<float>(B, it == 0, false, s, true);
+      trace(b, it, 1);
+      if (b->fp64)
+        launch_block_jacobi<double>(B, s);
+      else
+        launch_block_jacobi<float>(B, s);
+      trace(b, it, 2);
+      trace(b, it, 4);
+      launch_iter_end(B, it, true, s);
+      continue;
+    }
     if (b->fp64)
       launch_arap_assemble<double>(B, it == 0, false, s);
     else
@@ -551,7 +570,8 @@ bool valid_params(const ds_params& p) {
          p.eps_damp >= 0 && p.keep_frac >= 0 && p.keep_frac <= 1 && p.sigma_blend_scale > 0 &&
          p.sigma_arap_scale > 0 && p.precision >= 0 && p.precision <= 2 && p.refine_steps >= 0 &&
          p.refine_steps <= 3 && p.w_orb >= 0 && p.w_angle >= 0 && p.w_rot >= 0 &&
-         p.w_arap0 >= 0 && (p.factor_tc == 0 || p.factor_tc == 1);
+         p.w_arap0 >= 0 && (p.factor_tc == 0 || p.factor_tc == 1) &&
+         (p.solver == 0 || p.solver == 1);
 }
 
 bool is_host_ptr(const void* p);
@@ -580,6 +600,7 @@ void ds_default_params(ds_params* p) {
   p->refine_steps = 2;
   p->use_graph = 1;
   p->factor_tc = 0;
+  p->solver = 0;
 }
 
 const char* ds_status_str(int status) {

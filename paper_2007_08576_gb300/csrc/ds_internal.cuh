@@ -161,7 +161,10 @@ void launch_iter_begin(const BatchTabs& B, cudaStream_t s);
 void launch_icp(const BatchTabs& B, cudaStream_t s);
 void launch_orb(const BatchTabs& B, cudaStream_t s);
 template <typename T>
-void launch_arap_assemble(const BatchTabs& B, bool first, bool lin_only, cudaStream_t s);
+void launch_arap_assemble(const BatchTabs& B, bool first, bool lin_only, cudaStream_t s,
+                          bool diag_only = false);
+template <typename T>
+void launch_block_jacobi(const BatchTabs& B, cudaStream_t s);
 void launch_iter_end(const BatchTabs& B, int it, bool step, cudaStream_t s);
 
 // chol.cu

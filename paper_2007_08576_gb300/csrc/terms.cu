@@ -556,6 +556,90 @@ __device__ __forceinline__ void row_out(T* dst, const float* src, int len, bool 
   for (int k = threadIdx.x; k < len; k += blockDim.x) store_out(dst + k, src[k]);
 }
 
+// The terms of one ordered pair (i1 = the CTA's row node with state q1, g1, p1, R1 rows; i2 = o)
+// shared by the diagonal block, the gradient and the off-diagonal block A(i1, i2); adds the
+// pair's diagonal-block, gradient and cost contributions to the caller's accumulators.
+struct ArapPair {
+  Q r;           // q_i2 (x) q_i1*
+  V v, u2;       // unit(p_i2 - p_i1), unit(R_i2 (g_i1 - g_i2))
+  float s, Wr, ca;
+  float C[9];    // W_a [u]x P / l
+  float Tm[6];   // W_l v v^T + W_a P / l^2 (symmetric, xx xy xz yy yz zz)
+};
+__device__ __forceinline__ ArapPair arap_pair(const PairNode& o, Q q1, V g1, V p1, V R1a, V R1b,
+                                              V R1c, float wA, float inv2sig2, float w_angle,
+                                              float w_rot, float (&Dtt)[6], float (&Dtx)[9],
+                                              float (&Dxx)[6], float (&G)[6], float& cost) {
+  ArapPair pr;
+  const Q q2 = q4(o.q);
+  const V g2 = v3(o.g), p2 = v3(o.p);
+  V dg = sub(g2, g1);
+  float L0 = sqrtf(dot(dg, dg));
+  V e = sub(p2, p1);
+  float l = sqrtf(dot(e, e));
+  float il = 1.f / l;
+  V v = mul(e, il);
+  V a = {dot(R1a, dg), dot(R1b, dg), dot(R1c, dg)};
+  V u = mul(a, rsqrtf(dot(a, a)));
+  V mdg = {-dg.x, -dg.y, -dg.z};
+  V a2 = {dot(v3(o.R0), mdg), dot(v3(o.R1), mdg), dot(v3(o.R2), mdg)};
+  V u2 = mul(a2, rsqrtf(dot(a2, a2)));
+  Q r = qmul(q2, qconj(q1));
+  float qq = qdot(q1, q2);
+  float s = qq >= 0.f ? 1.f : -1.f;
+  float w = wA * __expf(-dot(dg, dg) * inv2sig2);
+  float Wl = w, Wa = w * w_angle, Wr = w * w_rot;
+  float rl = l - L0;
+  V ang = sub(u, v);
+  Q rot = {q1.w - s * q2.w, q1.x - s * q2.x, q1.y - s * q2.y, q1.z - s * q2.z};
+  cost += 0.5f * (Wl * rl * rl + Wa * dot(ang, ang) + Wr * qdot(rot, rot));
+  // C = W_a [u]x P / l with P = I - v v^T:  [u]x - (u x v) v^T
+  V uxv = cross(u, v);
+  float ca = Wa * il;
+  const float C[9] = {ca * (0.f - uxv.x * v.x), ca * (-u.z - uxv.x * v.y), ca * (u.y - uxv.x * v.z),
+                      ca * (u.z - uxv.y * v.x), ca * (0.f - uxv.y * v.y), ca * (-u.x - uxv.y * v.z),
+                      ca * (-u.y - uxv.z * v.x), ca * (u.x - uxv.z * v.y), ca * (0.f - uxv.z * v.z)};
+  // Tm = W_l v v^T + W_a (I - v v^T) / l^2
+  float tb = Wa * il * il;
+  float tv = Wl - tb;
+  const float Tm[6] = {tb + tv * v.x * v.x, tv * v.x * v.y, tv * v.x * v.z,
+                       tb + tv * v.y * v.y, tv * v.y * v.z, tb + tv * v.z * v.z};
+  // diag
+  float hr = 0.5f * Wr;
+  Dtt[0] += Wa * (1.f - u.x * u.x) + hr;
+  Dtt[1] += -Wa * u.x * u.y;
+  Dtt[2] += -Wa * u.x * u.z;
+  Dtt[3] += Wa * (1.f - u.y * u.y) + hr;
+  Dtt[4] += -Wa * u.y * u.z;
+  Dtt[5] += Wa * (1.f - u.z * u.z) + hr;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) Dtx[i] += C[i];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) Dxx[i] += 2.f * Tm[i];
+  // gradient
+  V rv = {r.x, r.y, r.z};
+  G[0] += -Wa * uxv.x - s * Wr * rv.x;
+  G[1] += -Wa * uxv.y - s * Wr * rv.y;
+  G[2] += -Wa * uxv.z - s * Wr * rv.z;
+  V Pu = sub(u, mul(v, dot(v, u)));
+  V Pu2 = sub(u2, mul(v, dot(v, u2)));
+  V gt = add(mul(v, -2.f * Wl * rl), mul(sub(Pu, Pu2), Wa * il));
+  G[3] += gt.x;
+  G[4] += gt.y;
+  G[5] += gt.z;
+  pr.r = r;
+  pr.v = v;
+  pr.u2 = u2;
+  pr.s = s;
+  pr.Wr = Wr;
+  pr.ca = ca;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) pr.C[i] = C[i];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) pr.Tm[i] = Tm[i];
+  return pr;
+}
+
 // One CTA per block row i1. For every partner i2 != i1 the CTA evaluates both ordered pairs
 // (i1, i2) and (i2, i1) in closed form; with u = unit(R_a (g_b - g_a)), v = unit(p_b - p_a),
 // l = |p_b - p_a|, P = I - v v^T, r = q_b (x) q_a*, s = sign(q_a . q_b) and per-pair weights
@@ -568,7 +652,8 @@ __device__ __forceinline__ void row_out(T* dst, const float* src, int len, bool 
 template <typename T>
 __global__ __launch_bounds__(256) void k_arap_assemble(const ProbDesc* const* __restrict__ descs,
                                                        const int2* __restrict__ tab,
-                                                       int first_iter, int lin_only) {
+                                                       int first_iter, int lin_only,
+                                                       int diag_only) {
   const int2 wk = tab[blockIdx.x];
   const ProbDesc& D = *descs[wk.x];
   const PairNode* __restrict__ pn = D.pn;
@@ -620,69 +705,26 @@ __global__ __launch_bounds__(256) void k_arap_assemble(const ProbDesc* const* __
     const int i2 = ch * kArapChunk + threadIdx.x;
     const int ncol = 6 * min(kArapChunk, N - ch * kArapChunk);
     float* pc = panel + 6 * threadIdx.x;
+    if (diag_only) {
+      // block-Jacobi solves need only the diagonal block and the gradient of this row
+      if (i2 < N && i2 != i1)
+        arap_pair(pn[i2], q1, g1, p1, R1a, R1b, R1c, wA, inv2sig2, w_angle, w_rot, Dtt, Dtx, Dxx,
+                  G, cost);
+      continue;
+    }
     if (i2 < N && i2 == i1) {
 #pragma unroll
       for (int rr = 0; rr < 6; ++rr)
 #pragma unroll
         for (int cc = 0; cc < 6; ++cc) pc[rr * PW + cc] = 0.f;  // written after the reduction
     } else if (i2 < N) {
-      const PairNode o = pn[i2];
-      const Q q2 = q4(o.q);
-      const V g2 = v3(o.g), p2 = v3(o.p);
-      V dg = sub(g2, g1);
-      float L0 = sqrtf(dot(dg, dg));
-      V e = sub(p2, p1);
-      float l = sqrtf(dot(e, e));
-      float il = 1.f / l;
-      V v = mul(e, il);
-      V a = {dot(R1a, dg), dot(R1b, dg), dot(R1c, dg)};
-      V u = mul(a, rsqrtf(dot(a, a)));
-      V mdg = {-dg.x, -dg.y, -dg.z};
-      V a2 = {dot(v3(o.R0), mdg), dot(v3(o.R1), mdg), dot(v3(o.R2), mdg)};
-      V u2 = mul(a2, rsqrtf(dot(a2, a2)));
-      Q r = qmul(q2, qconj(q1));
-      float qq = qdot(q1, q2);
-      float s = qq >= 0.f ? 1.f : -1.f;
-      float w = wA * __expf(-dot(dg, dg) * inv2sig2);
-      float Wl = w, Wa = w * w_angle, Wr = w * w_rot;
-      float rl = l - L0;
-      V ang = sub(u, v);
-      Q rot = {q1.w - s * q2.w, q1.x - s * q2.x, q1.y - s * q2.y, q1.z - s * q2.z};
-      cost += 0.5f * (Wl * rl * rl + Wa * dot(ang, ang) + Wr * qdot(rot, rot));
-      // C = W_a [u]x P / l with P = I - v v^T:  [u]x - (u x v) v^T
-      V uxv = cross(u, v);
-      float ca = Wa * il;
-      float C[9] = {ca * (0.f - uxv.x * v.x), ca * (-u.z - uxv.x * v.y), ca * (u.y - uxv.x * v.z),
-                    ca * (u.z - uxv.y * v.x), ca * (0.f - uxv.y * v.y), ca * (-u.x - uxv.y * v.z),
-                    ca * (-u.y - uxv.z * v.x), ca * (u.x - uxv.z * v.y), ca * (0.f - uxv.z * v.z)};
-      // Tm = W_l v v^T + W_a (I - v v^T) / l^2
-      float tb = Wa * il * il;
-      float tv = Wl - tb;
-      float Tm[6] = {tb + tv * v.x * v.x, tv * v.x * v.y, tv * v.x * v.z,
-                     tb + tv * v.y * v.y, tv * v.y * v.z, tb + tv * v.z * v.z};
-      // diag
-      float hr = 0.5f * Wr;
-      Dtt[0] += Wa * (1.f - u.x * u.x) + hr;
-      Dtt[1] += -Wa * u.x * u.y;
-      Dtt[2] += -Wa * u.x * u.z;
-      Dtt[3] += Wa * (1.f - u.y * u.y) + hr;
-      Dtt[4] += -Wa * u.y * u.z;
-      Dtt[5] += Wa * (1.f - u.z * u.z) + hr;
-#pragma unroll
-      for (int i = 0; i < 9; ++i) Dtx[i] += C[i];
-#pragma unroll
-      for (int i = 0; i < 6; ++i) Dxx[i] += 2.f * Tm[i];
-      // gradient
-      V rv = {r.x, r.y, r.z};
-      G[0] += -Wa * uxv.x - s * Wr * rv.x;
-      G[1] += -Wa * uxv.y - s * Wr * rv.y;
-      G[2] += -Wa * uxv.z - s * Wr * rv.z;
-      V Pu = sub(u, mul(v, dot(v, u)));
-      V Pu2 = sub(u2, mul(v, dot(v, u2)));
-      V gt = add(mul(v, -2.f * Wl * rl), mul(sub(Pu, Pu2), Wa * il));
-      G[3] += gt.x;
-      G[4] += gt.y;
-      G[5] += gt.z;
+      const ArapPair pr = arap_pair(pn[i2], q1, g1, p1, R1a, R1b, R1c, wA, inv2sig2, w_angle,
+                                    w_rot, Dtt, Dtx, Dxx, G, cost);
+      const Q r = pr.r;
+      const V u2 = pr.u2, v = pr.v;
+      const float s = pr.s, Wr = pr.Wr, ca = pr.ca;
+      const float* C = pr.C;
+      const float* Tm = pr.Tm;
       // off-diagonal block A(i1, i2) (rows: i1's theta,t; cols: i2's theta,t)
       float O[36];
       float hs = -0.5f * s * Wr;
@@ -813,7 +855,8 @@ __global__ __launch_bounds__(256) void k_arap_assemble(const ProbDesc* const* __
 }
 
 template <typename T>
-void launch_arap_assemble(const BatchTabs& B, bool first, bool lin_only, cudaStream_t s) {
+void launch_arap_assemble(const BatchTabs& B, bool first, bool lin_only, cudaStream_t s,
+                          bool diag_only) {
   // dynamic shared memory: the node -> data block map of the row and the 6-row panel
   const int sm = sizeof(int) * kArapMaxN + sizeof(float) * 6 * 6 * kArapChunk;
   static bool attr = false;
@@ -822,11 +865,73 @@ void launch_arap_assemble(const BatchTabs& B, bool first, bool lin_only, cudaStr
     attr = true;
   }
   k_arap_assemble<T><<<B.n_rows, kArapChunk, sm, s>>>(B.d, B.rows, first ? 1 : 0,
-                                                       lin_only ? 1 : 0);
+                                                       lin_only ? 1 : 0, diag_only ? 1 : 0);
   ++g_launches;
 }
 
-template void launch_arap_assemble<float>(const BatchTabs&, bool, bool, cudaStream_t);
-template void launch_arap_assemble<double>(const BatchTabs&, bool, bool, cudaStream_t);
+template void launch_arap_assemble<float>(const BatchTabs&, bool, bool, cudaStream_t, bool);
+template void launch_arap_assemble<double>(const BatchTabs&, bool, bool, cudaStream_t, bool);
+
+// Block-Jacobi step: x_i = A_ii^-1 b_i for every control point i, A_ii the damped 6 x 6 diagonal
+// block written by the assembly; FP64 Cholesky of each block, one thread per node.
+template <typename T>
+__global__ void k_block_jacobi(const ProbDesc* const* __restrict__ descs,
+                               const int2* __restrict__ tab) {
+  const int2 w = tab[blockIdx.x];
+  const ProbDesc& D = *descs[w.x];
+  const int i = w.y * 128 + threadIdx.x;
+  if (i >= D.N) return;
+  const int n = D.n;
+  const T* A = (const T*)D.lp.A;
+  double L[6][6], y[6];
+#pragma unroll
+  for (int r = 0; r < 6; ++r)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) L[r][c] = c <= r ? (double)A[(size_t)(6 * i + r) * n + 6 * i + c] : 0.0;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    double p = L[j][j];
+#pragma unroll
+    for (int q = 0; q < j; ++q) p -= L[j][q] * L[j][q];
+    if (!(p > 0.0)) {
+      atomicCAS((unsigned long long*)(D.acc + ACC_STATUS), 0ull,
+                __double_as_longlong((double)(6 * i + j + 1)));
+      p = 1.0;
+    }
+    const double d = sqrt(p);
+    L[j][j] = d;
+#pragma unroll
+    for (int r = j + 1; r < 6; ++r) {
+      double v = L[r][j];
+#pragma unroll
+      for (int q = 0; q < j; ++q) v -= L[r][q] * L[j][q];
+      L[r][j] = v / d;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 6; ++r) {
+    double v = D.b[6 * i + r];
+#pragma unroll
+    for (int q = 0; q < r; ++q) v -= L[r][q] * y[q];
+    y[r] = v / L[r][r];
+  }
+#pragma unroll
+  for (int r = 5; r >= 0; --r) {
+    double v = y[r];
+#pragma unroll
+    for (int q = r + 1; q < 6; ++q) v -= L[q][r] * y[q];
+    y[r] = v / L[r][r];
+  }
+#pragma unroll
+  for (int r = 0; r < 6; ++r) D.x[6 * i + r] = y[r];
+}
+
+template <typename T>
+void launch_block_jacobi(const BatchTabs& B, cudaStream_t s) {
+  k_block_jacobi<T><<<B.n_nodes, 128, 0, s>>>(B.d, B.nodes);
+  ++g_launches;
+}
+template void launch_block_jacobi<float>(const BatchTabs&, cudaStream_t);
+template void launch_block_jacobi<double>(const BatchTabs&, cudaStream_t);
 
 }  // namespace ds

@@ -28,7 +28,8 @@ def oracle_params(p):
     return solver.Params(w_orb=p.w_orb, w_angle=p.w_angle, w_rot=p.w_rot, w_arap0=p.w_arap0,
                          H=p.H_mm, tukey_c=p.tukey_c_mm, sigma_blend_scale=p.sigma_blend_scale,
                          sigma_arap_scale=p.sigma_arap_scale, lam=p.lambda_, eps=p.eps_damp,
-                         keep_frac=p.keep_frac, n_hyp=p.n_hyp, n_reweight=p.n_reweight)
+                         keep_frac=p.keep_frac, n_hyp=p.n_hyp, n_reweight=p.n_reweight,
+                         solver="block_jacobi" if getattr(p, "solver", 0) == 1 else "dense")
 
 
 def gpu_frame(d, sc, frame, params, iters=10, solver_obj=None):

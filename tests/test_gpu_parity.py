@@ -427,3 +427,40 @@ def test_tensor_core_factor_batch_equals_simt_and_agreement_rule(d, tiny, mid):
     assert e.value.status == d.DS_ERR_ARG
     a.close()
     b.close()
+
+
+# ----------------------------------------------------------------------------- block-Jacobi solver
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_block_jacobi_matches_oracle(d, tiny, mid, prec):
+    """Per-node 6 x 6 solves (Section 2's independent W_i updates): same parity bar."""
+    for sc in (tiny, mid):
+        fr = sc.frames[0]
+        p = d.default_params(precision=prec, solver=1)
+        s, st, q, t = gpu_frame(d, sc, fr, p)
+        tpl, res = _oracle(sc, fr, oracle_params(p))
+        err = np.abs(tpl.g + t - res.pos).max()
+        assert err <= POS_TOL_MM, err
+        rel = np.abs(np.array(st.cost[:10]) - np.array(res.costs)) / np.array(res.costs)
+        assert rel.max() <= COST_RTOL, rel
+        s.close()
+
+
+def test_block_jacobi_full_size_frame_and_batch_rule(d, tiny):
+    sc = scene(CONFIGS["seq_320x240_n256"], 1000)
+    fr = sc.frames[0]
+    p = d.default_params(precision=2, solver=1)
+    s, st, q, t = gpu_frame(d, sc, fr, p)
+    tpl, res = _oracle(sc, fr, oracle_params(p))
+    assert np.abs(tpl.g + t - res.pos).max() <= POS_TOL_MM
+    rel = np.abs(np.array(st.cost[:10]) - np.array(res.costs)) / np.array(res.costs)
+    assert rel.max() <= COST_RTOL, rel
+    s.close()
+    a = d.Solver(tiny.template_depth, tiny.K, tiny.nodes, d.default_params(precision=2))
+    b = d.Solver(tiny.template_depth, tiny.K, tiny.nodes, d.default_params(precision=2, solver=1))
+    with pytest.raises(d.DsError) as e:
+        d.ds_batch_create([a.h, b.h])
+    assert e.value.status == d.DS_ERR_ARG
+    a.close()
+    b.close()

@@ -472,3 +472,48 @@ def test_gauss_newton_cost_non_increasing(tiny):
     c = np.array(res.costs)
     assert (np.diff(c) <= 1e-9 * c[:-1]).all(), c
     assert c[-1] < 0.2 * c[0]
+
+
+# ----------------------------------------------------------------------------- block-Jacobi step
+
+
+def test_block_jacobi_step_equals_block_diagonal_gaussian_elimination(tiny):
+    """The per-node step is the solution of the damped system with every coupling block between
+    control points removed (checked against plain Gaussian elimination on that matrix)."""
+    sc, tpl = tiny
+    f = sc.frames[0]
+    res = solver.solve_frame(tpl, f.depth, f.match_idx, f.match_xyz, f.hyp, iters=1, keep_lins=True)
+    A = solver.damp(res.lins[0].A, solver.Params())
+    b = res.lins[0].b
+    n = A.shape[0]
+    node = np.arange(n) // 6
+    Ab = np.where(node[:, None] == node[None, :], A, 0.0)
+    x = solver.block_jacobi_solve(A, b)
+    xg = _gauss_partial_pivot(Ab, b)
+    assert np.abs(x - xg).max() <= 1e-9 * np.abs(xg).max()
+    # and it differs from the coupled step (the off-diagonal blocks are not zero here)
+    assert np.abs(x - solver.cholesky_solve(A, b)).max() > 1e-3 * np.abs(xg).max()
+
+
+def test_block_jacobi_keeps_an_exact_rigid_motion():
+    """At the exact rigid motion of a plane every residual and gradient vanishes, so the
+    block-Jacobi iteration stays there."""
+    cfg = Config("rigid_plane", 80, 60, 32, 200, 0, 0.0, 0.0, 0.0, 0.0, 0.0, 3.0, 2.0, 1,
+                 planar=True)
+    sc = make_scene(cfg, 31, f64=True)
+    f = sc.frames[0]
+    tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes)
+    exact = solver.solve_frame(tpl, f.depth, f.match_idx, f.match_xyz, f.hyp, iters=10)
+    prm = solver.Params(solver="block_jacobi")
+    res = solver.solve_frame(tpl, f.depth, f.match_idx, f.match_xyz, f.hyp, prm=prm, iters=3,
+                             q0=exact.q, t0=exact.t)
+    assert np.abs(res.pos - f.node_truth).max() < 1e-9
+
+
+def test_block_jacobi_cost_non_increasing(tiny):
+    sc, tpl = tiny
+    f = sc.frames[0]
+    prm = solver.Params(solver="block_jacobi")
+    res = solver.solve_frame(tpl, f.depth, f.match_idx, f.match_xyz, f.hyp, prm=prm, iters=10)
+    c = np.array(res.costs)
+    assert (np.diff(c) <= 1e-9 * c[:-1]).all(), c
