@@ -170,6 +170,10 @@ int ds_batch_destroy(ds_batch b);
  * the last ds_batch_solve's iterations; the phases cover all problems of the batch). */
 int ds_batch_set_tracing(ds_batch b, int32_t on);
 int ds_batch_phase_times(ds_batch b, double* ms4);
+/* Graph replay of a batch: 1 (default when every handle's use_graph is set) captures the
+ * Gauss-Newton loop into a CUDA graph on the first ds_batch_solve and replays it; 0 launches the
+ * kernels directly (no capture cost, for batch compositions used once). DS_ERR_ARG on NULL. */
+int ds_batch_set_graph(ds_batch b, int32_t on);
 
 /* Convenience: a temporary batch over n handles, solved and synchronised. */
 int ds_solve_batch(ds_handle* hs, int32_t n, int32_t iters);

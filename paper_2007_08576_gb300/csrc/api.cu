@@ -41,6 +41,7 @@ struct ds_batch_s {
   bool fp64 = false;
   int refine_steps = 0;
   bool block_jacobi = false;   // per-node 6 x 6 solves instead of the dense factorisation
+  bool no_graph = false;       // ds_batch_set_graph(b, 0): direct launches
   BatchTabs tabs{};
   const ProbDesc** d_descs = nullptr;
   int2* d_tab = nullptr;   // all work tables, back to back
@@ -1152,9 +1153,15 @@ int ds_batch_solve(ds_batch b, int32_t iters) {
   if (b->error) return DS_ERR_CUDA;
   for (ds_ctx* h : b->hs)
     if (!h->have_frame || h->N == 0) return DS_ERR_STATE;
-  bool graph = true;
+  bool graph = !b->no_graph;
   for (ds_ctx* h : b->hs) graph = graph && h->prm.use_graph;
   return run_batch(b, iters, graph);
+}
+
+int ds_batch_set_graph(ds_batch b, int32_t on) {
+  if (!b) return DS_ERR_ARG;
+  b->no_graph = on == 0;
+  return DS_OK;
 }
 
 int ds_batch_status(ds_batch b) {

@@ -25,7 +25,7 @@ DS_MAX_HYP = 64
 EXPORTS = [
     "ds_default_params", "ds_create_template", "ds_set_control_points", "ds_submit_frame",
     "ds_solve", "ds_solve_batch", "ds_batch_create", "ds_batch_solve", "ds_batch_status",
-    "ds_batch_destroy", "ds_batch_set_tracing", "ds_batch_phase_times", "ds_get_deformation", "ds_get_deformation64",
+    "ds_batch_destroy", "ds_batch_set_tracing", "ds_batch_phase_times", "ds_batch_set_graph", "ds_get_deformation", "ds_get_deformation64",
     "ds_set_deformation", "ds_get_inlier_mask", "ds_get_ransac", "ds_get_cost",
     "ds_get_blend_table", "ds_get_frame_points", "ds_linearize", "ds_set_tracing",
     "ds_get_phase_times", "ds_get_counters", "ds_ransac_noalloc", "ds_destroy", "ds_status_str",
@@ -92,6 +92,7 @@ def lib(path: str | None = None):
         "ds_batch_status": (i32, [vp]),
         "ds_batch_destroy": (i32, [vp]),
         "ds_batch_set_tracing": (i32, [vp, i32]),
+        "ds_batch_set_graph": (i32, [vp, i32]),
         "ds_batch_phase_times": (i32, [vp, vp]),
         "ds_get_deformation": (i32, [vp, vp, vp, vp]),
         "ds_get_deformation64": (i32, [vp, vp, vp]),
@@ -212,6 +213,10 @@ def ds_batch_status(b):
 
 def ds_batch_set_tracing(b, on=True):
     _check("ds_batch_set_tracing", lib().ds_batch_set_tracing(b, 1 if on else 0))
+
+
+def ds_batch_set_graph(b, on=True):
+    _check("ds_batch_set_graph", lib().ds_batch_set_graph(b, 1 if on else 0))
 
 
 def ds_batch_phase_times(b):

@@ -9,7 +9,8 @@ arrive asynchronously; every scheduler round (``poll``)
   2. admits waiting streams while the device-memory budget allows,
   3. launches one batch over every admitted stream that has a queued frame and is not already in
      flight (the streams' frames are submitted, then one batched Gauss-Newton solve covers all of
-     them).
+     them), unless max_inflight batches are already on the GPU: then the ready frames wait and
+     join the next batch.
 
 Several batches are in flight at once on their own CUDA streams (their stream sets are
 disjoint), so frames arriving while others are on the GPU are admitted into the next batch and
@@ -87,7 +88,8 @@ class GpuEngine:
         self.d = defsolve
         self.torch = torch
         self.params = params if params is not None else defsolve.default_params(precision=2)
-        self.params.use_graph = 1 if use_graph else 0
+        self.params.use_graph = 1
+        self.use_graph = bool(use_graph)
         self.cache = collections.OrderedDict()
         self.cache_cap = cache
 
@@ -112,9 +114,12 @@ class GpuEngine:
         key = tuple(sorted(id(s) for s in solvers))
         if key in self.cache:
             b, stream, ev = self.cache.pop(key)
+            # a composition seen again: capture its loop into a graph (replayed from now on)
+            self.d.ds_batch_set_graph(b, self.use_graph)
         else:
             stream = self.torch.cuda.Stream()
             b = self.d.ds_batch_create([s.h for s in solvers], stream.cuda_stream)
+            self.d.ds_batch_set_graph(b, False)   # first use: direct launches, no capture cost
             ev = None
             while len(self.cache) >= self.cache_cap:
                 _, (ob, _, _) = self.cache.popitem(last=False)
@@ -135,11 +140,14 @@ class GpuEngine:
 
 class Server:
     def __init__(self, engine, budget_bytes: int, iters: int = 10, max_batch: int = 64,
-                 clock=time.perf_counter):
+                 max_inflight: int = 2, clock=time.perf_counter):
         self.engine = engine
         self.budget = int(budget_bytes)
         self.iters = iters
         self.max_batch = max_batch
+        # batches on the GPU at once: frames that arrive meanwhile wait and join the next batch,
+        # so batches grow with the load instead of splitting into many small concurrent ones
+        self.max_inflight = max_inflight
         self.clock = clock
         self.used = 0
         self.streams = {}                 # sid -> dict(spec, solver, queue, busy, bytes)
@@ -226,7 +234,7 @@ class Server:
         ready = [sid for sid, st in self.streams.items()
                  if st["solver"] is not None and not st["busy"] and st["queue"]]
         ready = ready[: self.max_batch]
-        if ready:
+        if ready and len(self.in_flight) < self.max_inflight:
             solvers, items = [], []
             for sid in ready:
                 st = self.streams[sid]

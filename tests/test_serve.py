@@ -149,3 +149,22 @@ def test_served_results_equal_alone():
     assert st["frames"] == 9
     for i in range(3):
         srv.close_stream(i)
+
+
+def test_inflight_cap_coalesces_waiting_frames():
+    """With at most one batch on the GPU, frames that arrive meanwhile wait and then go out
+    together as one larger batch."""
+    eng = FakeEngine(delay=2)
+    srv = Server(eng, budget_bytes=1 << 40, max_inflight=1)
+    for s in "abcd":
+        srv.open_stream(s, _spec())
+    srv.submit("a", _frame())
+    srv.poll()                                   # batch 1: a
+    assert len(eng.launches) == 1 and len(srv.in_flight) == 1
+    for s in "bcd":
+        srv.submit(s, _frame())
+    srv.poll()                                   # capped: b, c, d wait
+    assert len(eng.launches) == 1
+    srv.drain()
+    assert len(eng.launches) == 2 and len(eng.launches[1]["ids"]) == 3
+    assert srv.stats()["frames"] == 4
