@@ -464,3 +464,68 @@ def test_block_jacobi_full_size_frame_and_batch_rule(d, tiny):
     assert e.value.status == d.DS_ERR_ARG
     a.close()
     b.close()
+
+
+# ----------------------------------------------------------------------------- largest sizes
+
+
+@pytest.mark.gpu
+def test_full_size_640x480_n1024_two_iterations(d):
+    """The largest workload (640x480 template, 1024 control points: 6144 unknowns, a dense
+    6144 x 6144 system; 4000 matches, 50 % outliers): RANSAC mask bit-exact, control points and
+    costs at the parity bar after two Gauss-Newton iterations (the FP64 oracle needs ~16 s and
+    ~7 GB per iteration at this size)."""
+    sc = scene(CONFIGS["seq_640x480_n1024"], 2000)
+    fr = sc.frames[0]
+    p = d.default_params()
+    s, st, q, t = gpu_frame(d, sc, fr, p, iters=2)
+    tpl, res = _oracle(sc, fr, oracle_params(p), iters=2)
+    mask = s.mask()
+    listed, _ = ransac_listed(res.ransac, p.H_mm)
+    assert np.array_equal(mask[~listed], res.ransac["mask"][~listed])
+    err = np.abs(tpl.g + t - res.pos).max()
+    assert err <= POS_TOL_MM, err
+    rel = np.abs(np.array(st.cost[:2]) - np.array(res.costs)) / np.array(res.costs)
+    assert rel.max() <= COST_RTOL, rel
+    s.close()
+
+
+@pytest.mark.gpu
+def test_mixed_size_batch():
+    """Batched uneven solves as in the batched workload: templates drawn from 160x120, 320x240
+    and 640x480, control points uniform in [64, 1024], outlier rates uniform in [20 %, 60 %];
+    one batch equals every problem solved alone, and the smallest problem equals the oracle."""
+    from gpu_common import lib
+    from synth.scene import Config
+    d = lib()
+    rng = np.random.default_rng(64)
+    sizes = [(160, 120), (320, 240), (640, 480)]
+    cfgs = []
+    for k in range(5):
+        W, H = sizes[k % 3]
+        N = int(rng.integers(64, 1025))
+        out = float(rng.uniform(0.2, 0.6))
+        M = int(min(4000, W * H // 20))
+        cfgs.append(Config(f"mix{k}_{W}x{H}_n{N}", W, H, N, M, 20, out, 0.5, 0.1, 10.0, 1.0,
+                           0.2, 0.5, 1))
+    scenes = [scene(c, 6400 + k) for k, c in enumerate(cfgs)]
+    p = d.default_params(precision=2)
+    alone = []
+    for sc in scenes:
+        s, st, q, t = gpu_frame(d, sc, sc.frames[0], p)
+        alone.append(t)
+        s.close()
+    solvers = []
+    for sc in scenes:
+        s = d.Solver(sc.template_depth, sc.K, sc.nodes, p)
+        fr = sc.frames[0]
+        s.submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+        solvers.append(s)
+    d.ds_solve_batch([s.h for s in solvers], 10)
+    for s, t in zip(solvers, alone):
+        assert np.abs(s.deformation64()[1] - t).max() <= 1e-4
+        s.close()
+    k = int(np.argmin([c.W * c.H * c.N for c in cfgs]))
+    sc = scenes[k]
+    tpl, res = _oracle(sc, sc.frames[0], oracle_params(p))
+    assert np.abs(tpl.g + alone[k] - res.pos).max() <= POS_TOL_MM
