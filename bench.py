@@ -48,6 +48,27 @@ CHOL_TRAFFIC = {"chol_sha256": "5eb09e6b651e9cb2", "precision": 2, "streams": 32
                 "bytes": 673264640 + 348546560}
 
 
+def max_over_ranks(x, world, dev):
+    """The slowest rank's time: replicas run independent streams, the job ends with the last."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, total_s):
+    """Whole-job rate: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / total_s
+
+
+def replica_seeds(rank, n_scenes):
+    """Scene seeds of a rank: every replica solves its own streams."""
+    return [1000 + 100 * rank + k for k in range(n_scenes)]
+
+
 def _measured_bf16():
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
     try:
@@ -199,7 +220,7 @@ def run_gpu(args):
     n_scenes = min(args.scenes, S)
     F = args.frames
     from synth import CONFIGS, make_scene
-    scenes = [make_scene(CONFIGS[WORKLOAD], 1000 + 100 * rank + k, n_frames=F) for k in range(n_scenes)]
+    scenes = [make_scene(CONFIGS[WORKLOAD], sd, n_frames=F) for sd in replica_seeds(rank, n_scenes)]
     N = len(scenes[0].nodes)
     M = len(scenes[0].frames[0].match_idx)
     n = 6 * N
@@ -261,12 +282,8 @@ def run_gpu(args):
     d.ds_batch_status(batch)
     torch.cuda.synchronize()
     launches = d.ds_get_counters(None) - k0
-    total_s = sum(step_ms) * 1e-3
-    if world > 1:
-        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * S * K / total_s
+    total_s = max_over_ranks(sum(step_ms) * 1e-3, world, dev)
+    value = job_throughput(world, S * K, total_s)
 
     # end to end through the C ABI: pinned host frames in, deformations out, every step
     pin = [[[torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
@@ -288,11 +305,7 @@ def run_gpu(args):
             d.ds_get_deformation(h, *outs[j])
         if i >= W:
             e2e_s.append(time.perf_counter() - t0)
-    e2e_tot = sum(e2e_s)
-    if world > 1:
-        t = torch.tensor([e2e_tot], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_tot = float(t.item())
+    e2e_tot = max_over_ranks(sum(e2e_s), world, dev)
     f0 = scenes[0].frames[0]
     h2d = S * (f0.depth.nbytes + f0.match_idx.nbytes + np.ascontiguousarray(f0.match_xyz).nbytes +
                f0.hyp.nbytes)
@@ -416,7 +429,7 @@ def run_gpu(args):
             "host_enqueue_ms_per_step": round(float(np.median(host_ms)), 3),
             "phase_ms_per_step": {"linearize": round(phase[0] / K, 4), "factor": round(phase[1] / K, 4),
                                   "solve_refine": round(phase[2] / K, 4), "update": round(phase[3] / K, 4)},
-            "e2e": {"value": round(world * S * K / e2e_tot, 3), "unit": "frames/s",
+            "e2e": {"value": round(job_throughput(world, S * K, e2e_tot), 3), "unit": "frames/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
             "roofline": {"bound": bound,
