@@ -58,8 +58,8 @@ struct ds_batch_s {
   std::vector<cudaEvent_t> ev_in;
   // side stream of the linearisation: the ORB pass runs beside the ICP pass (both only add
   // into the block table and the gradient)
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t side = nullptr, side2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
   bool error = false;
 };
 
@@ -124,6 +124,7 @@ struct ds_ctx {
   float* d_Af32 = nullptr;    // FP32 factor copy (DS_PREC_FP32_REFINE)
   void* d_Dinv = nullptr;
   float* d_blk = nullptr;
+  float* d_adiag = nullptr;   // per node ARAP-only diagonal block + gradient (deferred assembly)
   float* d_gdata = nullptr;
   double* d_b = nullptr;
   double* d_x = nullptr;
@@ -204,7 +205,7 @@ void free_cp(ds_ctx* h) {
   dfree(h->d_g64); dfree(h->d_gc); dfree(h->d_q64); dfree(h->d_t64); dfree(h->d_node);
   dfree(h->d_pn); dfree(h->d_tp); dfree(h->d_tw); dfree(h->d_rank); dfree(h->d_seg);
   dfree(h->d_segbp); dfree(h->d_segstart); dfree(h->d_rowptr); dfree(h->d_rowcol); dfree(h->d_rowbp);
-  dfree(h->d_A32); dfree(h->d_A64); dfree(h->d_Af32); dfree(h->d_Dinv); dfree(h->d_blk);
+  dfree(h->d_A32); dfree(h->d_A64); dfree(h->d_Af32); dfree(h->d_Dinv); dfree(h->d_blk); dfree(h->d_adiag);
   dfree(h->d_gdata); dfree(h->d_b); dfree(h->d_x); dfree(h->d_r); dfree(h->d_xf); dfree(h->d_v1);
   dfree(h->d_v2); dfree(h->d_v3); dfree(h->d_lcnt); dfree(h->d_lflags); dfree(h->d_tasks);
   dfree(h->d_Lp);
@@ -324,10 +325,13 @@ void destroy_batch(ds_batch_s* b) {
     for (int i = 0; i < DS_MAX_ITERS; ++i)
       for (int k = 0; k < 5; ++k) cudaEventDestroy(b->ev[i][k]);
   if (b->side) cudaStreamSynchronize(b->side);
+  if (b->side2) cudaStreamSynchronize(b->side2);
   if (b->ev_done) cudaEventDestroy(b->ev_done);
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   if (b->ev_join) cudaEventDestroy(b->ev_join);
+  if (b->ev_join2) cudaEventDestroy(b->ev_join2);
   if (b->side) cudaStreamDestroy(b->side);
+  if (b->side2) cudaStreamDestroy(b->side2);
   for (auto e : b->ev_in) cudaEventDestroy(e);
   dfree(b->d_descs);
   dfree(b->d_tab);
@@ -410,7 +414,9 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   if (cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaEventCreateWithFlags(&b->ev_join2, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->side2, cudaStreamNonBlocking) != cudaSuccess) {
     destroy_batch(b);
     return DS_ERR_CUDA;
   }
@@ -478,10 +484,25 @@ void enqueue_solve(ds_batch_s* b, int iters) {
       launch_iter_end(B, it, true, s);
       continue;
     }
-    if (b->fp64)
-      launch_arap_assemble<double>(B, it == 0, false, s);
-    else
-      launch_arap_assemble<float>(B, it == 0, false, s);
+    if (it > 0) {
+      // w_ARAP is fixed after the frame's first linearisation, so the pair assembly runs beside
+      // the data terms (second side stream); the data blocks, damping and b follow the join
+      cudaStreamWaitEvent(b->side2, b->ev_fork, 0);
+      if (b->fp64)
+        launch_arap_deferred<double>(B, b->side2);
+      else
+        launch_arap_deferred<float>(B, b->side2);
+      cudaEventRecord(b->ev_join2, b->side2);
+      cudaStreamWaitEvent(s, b->ev_join2, 0);
+      if (b->fp64)
+        launch_arap_finalize<double>(B, s);
+      else
+        launch_arap_finalize<float>(B, s);
+    } else if (b->fp64) {
+      launch_arap_assemble<double>(B, true, false, s);
+    } else {
+      launch_arap_assemble<float>(B, true, false, s);
+    }
     trace(b, it, 1);
     if (b->fp64)
       enqueue_factor_solve<double>(b);
@@ -864,6 +885,7 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
       (rc = dalloc(&h->d_rowptr, N + 1)) || (rc = dalloc(&h->d_rowcol, rowcol.size())) ||
       (rc = dalloc(&h->d_rowbp, rowbp.size())) || (rc = dalloc(&h->d_A32, nn)) ||
       (rc = dalloc(&h->d_blk, 36 * (size_t)h->nbp)) || (rc = dalloc(&h->d_gdata, n)) ||
+      (rc = dalloc(&h->d_adiag, 48 * (size_t)N)) ||
       (rc = dalloc(&h->d_b, n)) || (rc = dalloc(&h->d_x, n)) || (rc = dalloc(&h->d_r, n)) ||
       (rc = dalloc(&h->d_xf, n)) ||
       (rc = dalloc((char**)&h->d_v1, tsz * n)) || (rc = dalloc((char**)&h->d_v2, tsz * n)) ||
@@ -936,6 +958,7 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
     D.node = h->d_node;
     D.pn = h->d_pn;
     D.blk = h->d_blk;
+    D.adiag = h->d_adiag;
     D.gdata = h->d_gdata;
     D.acc = h->d_acc;
     D.hist = h->d_hist;

@@ -97,6 +97,7 @@ struct ProbDesc {
   NodeGPU* node;
   PairNode* pn;
   float* blk;              // block-sparse data-term blocks (36 floats per pair)
+  float* adiag;            // per node: ARAP-only diagonal block (36) and gradient (6), 48 floats
   float* gdata;            // data-term gradient
   double* acc;             // ACC_* scalars
   double* hist;            // DS_MAX_ITERS x 6
@@ -165,6 +166,12 @@ void launch_arap_assemble(const BatchTabs& B, bool first, bool lin_only, cudaStr
                           bool diag_only = false);
 template <typename T>
 void launch_block_jacobi(const BatchTabs& B, cudaStream_t s);
+// ARAP pairs without the data terms (beside the ICP / ORB passes), then the data blocks, the
+// diagonal blocks with damping and the right-hand side
+template <typename T>
+void launch_arap_deferred(const BatchTabs& B, cudaStream_t s);
+template <typename T>
+void launch_arap_finalize(const BatchTabs& B, cudaStream_t s);
 void launch_iter_end(const BatchTabs& B, int it, bool step, cudaStream_t s);
 
 // chol.cu

@@ -653,7 +653,7 @@ template <typename T>
 __global__ __launch_bounds__(256) void k_arap_assemble(const ProbDesc* const* __restrict__ descs,
                                                        const int2* __restrict__ tab,
                                                        int first_iter, int lin_only,
-                                                       int diag_only) {
+                                                       int diag_only, int deferred) {
   const int2 wk = tab[blockIdx.x];
   const ProbDesc& D = *descs[wk.x];
   const PairNode* __restrict__ pn = D.pn;
@@ -671,6 +671,7 @@ __global__ __launch_bounds__(256) void k_arap_assemble(const ProbDesc* const* __
   T* __restrict__ Afac = lin_only ? (T*)D.Aref : (T*)D.lp.A;
   float* __restrict__ Aref = (!lin_only && D.write_ref) ? D.Aref : nullptr;
   double* __restrict__ b = D.b;
+  float* __restrict__ D_adiag = D.adiag;
   extern __shared__ __align__(16) int smap[];          // node -> data block code of this row
   float* panel = reinterpret_cast<float*>(smap + kArapMaxN);  // 6 rows x kArapChunk nodes
   __shared__ float sRed[28][8];
@@ -764,7 +765,7 @@ __global__ __launch_bounds__(256) void k_arap_assemble(const ProbDesc* const* __
       O[5 * 6 + 3] = -2.f * Tm[2];
       O[5 * 6 + 4] = -2.f * Tm[4];
       O[5 * 6 + 5] = -2.f * Tm[5];
-      const int code = smap[i2];
+      const int code = deferred ? -1 : smap[i2];   // deferred: data blocks added later
       if (code >= 0) {
         const float* db = blk + (size_t)(code & ~kBlkTransposed) * 36;
         if (code & kBlkTransposed) {
@@ -838,6 +839,13 @@ __global__ __launch_bounds__(256) void k_arap_assemble(const ProbDesc* const* __
     D[21] = t[15]; D[22] = t[16]; D[23] = t[17];
     D[27] = t[16]; D[28] = t[18]; D[29] = t[19];
     D[33] = t[17]; D[34] = t[19]; D[35] = t[20];
+    if (deferred) {   // ARAP-only diagonal block and gradient, for k_arap_finalize
+      float* ad = D_adiag + 48 * (size_t)i1;
+      for (int i = 0; i < 36; ++i) ad[i] = D[i];
+      for (int j = 0; j < 6; ++j) ad[36 + j] = t[21 + j];
+      atomicAdd(&acc[ACC_COST_ARAP], (double)t[27]);
+      return;
+    }
     int bp = smap[i1];
     if (bp >= 0) {
       const float* db = blk + (size_t)bp * 36;
@@ -865,12 +873,77 @@ void launch_arap_assemble(const BatchTabs& B, bool first, bool lin_only, cudaStr
     attr = true;
   }
   k_arap_assemble<T><<<B.n_rows, kArapChunk, sm, s>>>(B.d, B.rows, first ? 1 : 0,
-                                                       lin_only ? 1 : 0, diag_only ? 1 : 0);
+                                                       lin_only ? 1 : 0, diag_only ? 1 : 0, 0);
   ++g_launches;
 }
 
 template void launch_arap_assemble<float>(const BatchTabs&, bool, bool, cudaStream_t, bool);
 template void launch_arap_assemble<double>(const BatchTabs&, bool, bool, cudaStream_t, bool);
+
+template <typename T>
+void launch_arap_deferred(const BatchTabs& B, cudaStream_t s) {
+  const int sm = sizeof(int) * kArapMaxN + sizeof(float) * 6 * 6 * kArapChunk;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_arap_assemble<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    attr = true;
+  }
+  k_arap_assemble<T><<<B.n_rows, kArapChunk, sm, s>>>(B.d, B.rows, 0, 0, 0, 1);
+  ++g_launches;
+}
+
+// After the deferred ARAP pass and the data terms: adds every data block of node row i (both
+// triangles of the refinement matrix, the lower one of the factor copy), forms the diagonal
+// block = ARAP + data, damps it and writes b_i = -(ARAP + data gradient). One CTA of 64 threads
+// per node row; the row's block entries are spread over the threads (36 values each).
+template <typename T>
+__global__ __launch_bounds__(64) void k_arap_finalize(const ProbDesc* const* __restrict__ descs,
+                                                      const int2* __restrict__ tab) {
+  const int2 w = tab[blockIdx.x];
+  const ProbDesc& D = *descs[w.x];
+  const int i = w.y, n = D.n;
+  T* Afac = (T*)D.lp.A;
+  float* Aref = D.write_ref ? D.Aref : nullptr;
+  const float* ad = D.adiag + 48 * (size_t)i;
+  __shared__ float Db[36];
+  if (threadIdx.x < 36) Db[threadIdx.x] = ad[threadIdx.x];
+  __syncthreads();
+  const int e0 = D.rowptr[i], ne = D.rowptr[i + 1] - e0;
+  for (int q = threadIdx.x; q < 36 * ne; q += blockDim.x) {
+    const int e = e0 + q / 36, k = q % 36, r = k / 6, cc = k % 6;
+    const int c = D.rowcol[e], code = D.rowbp[e];
+    const float* db = D.blk + (size_t)(code & ~kBlkTransposed) * 36;
+    const float v = (code & kBlkTransposed) ? db[cc * 6 + r] : db[k];
+    if (c == i) {
+      Db[k] += v;   // the diagonal pair appears once in its row: one thread per entry
+      continue;
+    }
+    const size_t off = (size_t)(6 * i + r) * n + 6 * c + cc;
+    if (Aref) Aref[off] += v;
+    if (c < i) Afac[off] += (T)v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 36) {
+    const int r = threadIdx.x / 6, cc = threadIdx.x % 6;
+    float v = Db[threadIdx.x];
+    if (r == cc) v += (float)(D.lam * ((double)v + D.eps));
+    const size_t off = (size_t)(6 * i + r) * n + 6 * i + cc;
+    Afac[off] = (T)v;
+    if (Aref) Aref[off] = v;
+  }
+  if (threadIdx.x < 6)
+    D.b[6 * i + threadIdx.x] = -((double)ad[36 + threadIdx.x] + (double)D.gdata[6 * i + threadIdx.x]);
+}
+
+template <typename T>
+void launch_arap_finalize(const BatchTabs& B, cudaStream_t s) {
+  k_arap_finalize<T><<<B.n_rows, 64, 0, s>>>(B.d, B.rows);
+  ++g_launches;
+}
+template void launch_arap_deferred<float>(const BatchTabs&, cudaStream_t);
+template void launch_arap_deferred<double>(const BatchTabs&, cudaStream_t);
+template void launch_arap_finalize<float>(const BatchTabs&, cudaStream_t);
+template void launch_arap_finalize<double>(const BatchTabs&, cudaStream_t);
 
 // Block-Jacobi step: x_i = A_ii^-1 b_i for every control point i, A_ii the damped 6 x 6 diagonal
 // block written by the assembly; FP64 Cholesky of each block, one thread per node.
