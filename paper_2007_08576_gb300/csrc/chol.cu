@@ -1,66 +1,33 @@
-// Cholesky factorisation and triangular solves of the damped normal equations (Section 2:
-// "we perform Cholesky decomposition to update W_i"), for T = double (FP64 factor, TB = 32) or
-// T = float (FP32 factor, TB = 64), plus the FP64 residual of the refinement steps.
+// Cholesky factorisation of the damped normal equations (Section 2: "we perform Cholesky
+// decomposition to update W_i"), for T = double (FP64 factor, TB = 32) or T = float (FP32
+// factor, TB = 64; on the SIMT pipes, or on the tensor cores in k_chol_tc).
 //
 // Layout: A is n x n row-major; only the lower triangle is read or written. The matrix is cut
 // into TB x TB tiles (the last row/column of tiles is ragged).
 //
-// Factorisation: one persistent launch runs the tile tasks of a right-looking blocked Cholesky
-//   CRIT(k)       the critical chain of step k in one task: A_kk -= L_k,k-1 L_k,k-1^T,
-//                 L_kk = chol(A_kk) with its inverse L_kk^-1 (kept for the solves), and
-//                 L_k+1,k = A_k+1,k L_kk^-T
-//   TRSM(i,k)     L_ik = A_ik L_kk^-T (as a product with the stored inverse), i > k + 1
-//   GEMM(i,j,k)   A_ij -= L_ik L_jk^T          (k < j <= i, except the last update of (k+1,k+1))
-// in a fixed topological order (with one step of look-ahead: the column that feeds the next
-// critical task is issued before the rest of the trailing update). CTAs claim tasks in that order from
-// an atomic ticket counter; a task waits on per-tile counters written by earlier tickets. Every
-// ticket a CTA waits on was claimed earlier by a running CTA, so the waits always end; they are
-// bounded anyway (globaltimer deadline) and a timeout sets an error word, after which all CTAs
-// drain the queue without computing. Tiles written inside the launch are read through L2
-// (ld.global.cg) because L1 is not coherent across SMs.
-//
-// Triangular solves: one launch, one ticket per tile row and direction (forward tickets first,
-// then backward in reverse row order): y_i = L_ii^-1 (b_i - sum_{j<i} L_ij y_j), then
-// x_i = L_ii^-T (y_i - sum_{j>i} L_ji^T x_j), each term consumed as soon as its producer
-// publishes it.
+// One persistent launch per Gauss-Newton iteration runs the tile tasks of a left-looking blocked
+// Cholesky for every problem of a batch, one task per output tile, in column order:
+//   DIAG(j)     C = A_jj - sum_{k<j} L_jk L_jk^T;  L_jj = chol(C) with its inverse L_jj^-1
+//   OFF(i, j)   C = A_ij - sum_{k<j} L_ik L_jk^T;  L_ij = C (L_jj^-1)^T          (i > j)
+// The finished tiles are also kept in packed slots (transposed and padded for the SIMT kernel,
+// TF32 hi / lo parts in the K-major core-matrix layout for the tensor-core kernel) that the
+// later tasks stream into shared memory with bulk copies. CTAs claim tasks from an atomic ticket
+// counter through a per-batch claim-order table; a task waits on per-tile counters written by
+// earlier tickets. Every ticket a CTA waits on was claimed earlier by a running CTA, so the waits
+// always end; they are bounded anyway (globaltimer deadline) and a timeout sets an error word,
+// after which all CTAs drain the queue without computing. Tiles written inside the launch are
+// read through L2 (ld.global.cg, bulk copies) because L1 is not coherent across SMs.
 //
 // A pivot <= 0 (or NaN) is recorded in the problem's status word as 1 + its row and replaced by
 // 1 so that the rest stays finite; the host reports DS_ERR_NOT_SPD.
 #include <math.h>
 
+#include "dev_util.cuh"
 #include "ds_internal.cuh"
 
 namespace ds {
 
-__device__ __forceinline__ unsigned long long globaltimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
 
-// Bounded wait until *p >= v. Returns false (and raises *err) on timeout or if *err is set.
-__device__ __forceinline__ bool wait_ge(const int* p, int v, int* err,
-                                        unsigned long long budget_ns) {
-  const volatile int* vp = p;
-  const volatile int* ve = err;
-  if (*vp >= v) return true;
-  unsigned long long t0 = globaltimer();
-  int it = 0;
-  while (*vp < v) {
-    if (*ve) return false;
-    if ((++it & 31) == 0 && globaltimer() - t0 > budget_ns) {
-      atomicExch(err, 1);
-      return false;
-    }
-    __nanosleep(64);
-  }
-  return true;
-}
-
-template <typename T>
-__device__ __forceinline__ T ldcg(const T* p) {
-  return __ldcg(p);
-}
 
 template <typename T>
 __device__ __forceinline__ T tsqrt(T x);
@@ -853,192 +820,6 @@ __global__ __launch_bounds__(256, DS_CHOL_CTAS_PER_SM) void k_chol_dag(
   }
 }
 
-// ----------------------------------------------------------------------------- solves
-
-// Register-prefetched tile GEMVs of the triangular solves (256 threads).
-// Row form (forward): thread (warp w, lane l) holds M[r][c] for r = w + 8 s, c = l + 32 t.
-// Column form (backward): thread (r = tid % TB, slice sl = tid / TB) holds M[c][r] for
-// c = sl + SL q, SL = 256 / TB. Both hold TB * TB / 256 values per thread.
-template <typename T, int TB>
-struct SolveTile {
-  static constexpr int NV = TB * TB / 256;
-  static constexpr int RS = TB / 8;    // rows per warp (row form)
-  static constexpr int CS = TB / 32;   // columns per lane (row form)
-  static constexpr int SL = 256 / TB;  // slices (column form)
-};
-
-template <typename T, int TB>
-__device__ __forceinline__ void prefetch_rows(const T* M, size_t ld, int nr, int nc,
-                                              T (&v)[SolveTile<T, TB>::NV]) {
-  constexpr int RS = SolveTile<T, TB>::RS, CS = SolveTile<T, TB>::CS;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int s = 0; s < RS; ++s)
-#pragma unroll
-    for (int t = 0; t < CS; ++t) {
-      const int r = warp + 8 * s, c = lane + 32 * t;
-      v[s * CS + t] = (r < nr && c < nc) ? ldcg(M + (size_t)r * ld + c) : (T)0;
-    }
-}
-
-template <typename T, int TB>
-__device__ __forceinline__ void prefetch_cols(const T* M, size_t ld, int nr, int nc,
-                                              T (&v)[SolveTile<T, TB>::NV]) {
-  constexpr int SL = SolveTile<T, TB>::SL, NV = SolveTile<T, TB>::NV;
-  const int r = threadIdx.x % TB, sl = threadIdx.x / TB;
-#pragma unroll
-  for (int q = 0; q < NV; ++q) {
-    const int c = sl + SL * q;
-    v[q] = (r < nr && c < nc) ? ldcg(M + (size_t)c * ld + r) : (T)0;
-  }
-}
-
-// acc[r] (-)= sum_c M[r][c] vin[c] from prefetched row-form values.
-template <typename T, int TB>
-__device__ __forceinline__ void gemv_rows_pf(const T (&v)[SolveTile<T, TB>::NV], const T* vin,
-                                             T* acc, bool sub) {
-  constexpr int RS = SolveTile<T, TB>::RS, CS = SolveTile<T, TB>::CS;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int s = 0; s < RS; ++s) {
-    T sum = (T)0;
-#pragma unroll
-    for (int t = 0; t < CS; ++t) sum += v[s * CS + t] * vin[lane + 32 * t];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0) acc[warp + 8 * s] = sub ? acc[warp + 8 * s] - sum : sum;
-  }
-}
-
-// acc[r] (-)= sum_c M[c][r] vin[c] from prefetched column-form values (reduction through part).
-template <typename T, int TB>
-__device__ __forceinline__ void gemv_cols_pf(const T (&v)[SolveTile<T, TB>::NV], const T* vin,
-                                             T* acc, bool sub, T (*part)[17]) {
-  constexpr int SL = SolveTile<T, TB>::SL, NV = SolveTile<T, TB>::NV;
-  const int r = threadIdx.x % TB, sl = threadIdx.x / TB;
-  T sum = (T)0;
-#pragma unroll
-  for (int q = 0; q < NV; ++q) sum += v[q] * vin[sl + SL * q];
-  part[r][sl] = sum;
-  __syncthreads();
-  if (threadIdx.x < TB) {
-    T a = (T)0;
-#pragma unroll
-    for (int q = 0; q < SL; ++q) a += part[threadIdx.x][q];
-    acc[threadIdx.x] = sub ? acc[threadIdx.x] - a : a;
-  }
-}
-
-// Tickets per problem: [0, nt) forward rows 0..nt-1, [nt, 2nt) backward rows nt-1..0.
-// flags: [0, nt) forward row done, [nt, 2nt) backward row done. Every tile a ticket needs is
-// loaded into registers before the wait on its producer (the tiles do not depend on it), so a
-// dependency costs one flag hand-off and one 64-value vector load.
-template <typename T, int TB>
-__global__ __launch_bounds__(256) void k_trsv_dag(const ProbDesc* const* __restrict__ descs,
-                                                  int np, int nticket, int solve_id,
-                                                  int* __restrict__ head, int* __restrict__ err,
-                                                  unsigned long long budget_ns) {
-  constexpr int NV = SolveTile<T, TB>::NV;
-  __shared__ T acc[TB];
-  __shared__ T vin[TB];
-  __shared__ T part[TB][17];
-  __shared__ int s_t, s_ok;
-  for (;;) {
-    if (threadIdx.x == 0) s_t = atomicAdd(head, 1);
-    __syncthreads();
-    const int t = s_t;
-    if (t >= nticket) return;
-    const LinProblem& P = descs[t % np]->lp;
-    const int2 tk = make_int2(t % np, t / np);
-    if (tk.y >= 2 * P.nt) {
-      __syncthreads();
-      continue;
-    }
-    const int nt = P.nt, n = P.n;
-    const bool fwd = tk.y < nt;
-    const int i = fwd ? tk.y : 2 * nt - 1 - tk.y;
-    const int r0 = i * TB;
-    const int nr = min(TB, n - r0);
-    const T* L = (const T*)P.A;
-    const T* D = (const T*)P.Dinv + (size_t)i * TB * TB;
-    int* flag = P.flags;
-    T* y = (T*)P.y;
-    T* x = (T*)P.x;
-    const T* rhs = (const T*)P.rhs;
-    const T* src = fwd ? y : x;
-    T dv[NV];  // the diagonal block's inverse, prefetched
-    if (fwd)
-      prefetch_rows<T, TB>(D, TB, TB, TB, dv);
-    else
-      prefetch_cols<T, TB>(D, TB, TB, TB, dv);
-    bool ok = true;
-    if (threadIdx.x == 0) {
-      ok = fwd ? true : wait_ge(&flag[i], solve_id, err, budget_ns);
-      __threadfence();
-      s_ok = ok;
-    }
-    __syncthreads();
-    ok = s_ok;
-    if (threadIdx.x < TB)
-      acc[threadIdx.x] = (threadIdx.x < nr && ok) ? ldcg((fwd ? rhs : y) + r0 + threadIdx.x) : (T)0;
-    const int cnt = fwd ? i : nt - 1 - i;
-    T lv[NV];
-    if (cnt > 0) {
-      const int jt = fwd ? 0 : nt - 1;
-      const int c0 = jt * TB, nc = min(TB, n - c0);
-      if (fwd)
-        prefetch_rows<T, TB>(L + (size_t)r0 * n + c0, n, nr, nc, lv);
-      else
-        prefetch_cols<T, TB>(L + (size_t)c0 * n + r0, n, nr, nc, lv);
-    }
-    for (int q = 0; q < cnt && ok; ++q) {
-      const int jt = fwd ? q : nt - 1 - q;
-      if (threadIdx.x == 0) {
-        s_ok = wait_ge(&flag[fwd ? jt : nt + jt], solve_id, err, budget_ns);
-        __threadfence();
-      }
-      __syncthreads();
-      ok = s_ok;
-      if (!ok) break;
-      const int c0 = jt * TB;
-      const int nc = min(TB, n - c0);
-      if (threadIdx.x < TB) vin[threadIdx.x] = threadIdx.x < nc ? ldcg(src + c0 + threadIdx.x) : (T)0;
-      __syncthreads();
-      T cur[NV];
-#pragma unroll
-      for (int e = 0; e < NV; ++e) cur[e] = lv[e];
-      if (q + 1 < cnt) {  // next tile while this one is used
-        const int jn = fwd ? q + 1 : nt - 2 - q;
-        const int cn = jn * TB, ncn = min(TB, n - cn);
-        if (fwd)
-          prefetch_rows<T, TB>(L + (size_t)r0 * n + cn, n, nr, ncn, lv);
-        else
-          prefetch_cols<T, TB>(L + (size_t)cn * n + r0, n, nr, ncn, lv);
-      }
-      if (fwd)
-        gemv_rows_pf<T, TB>(cur, vin, acc, true);
-      else
-        gemv_cols_pf<T, TB>(cur, vin, acc, true, part);
-      __syncthreads();
-    }
-    if (ok) {
-      if (threadIdx.x < TB) vin[threadIdx.x] = acc[threadIdx.x];
-      __syncthreads();
-      if (fwd)
-        gemv_rows_pf<T, TB>(dv, vin, acc, false);
-      else
-        gemv_cols_pf<T, TB>(dv, vin, acc, false, part);
-      __syncthreads();
-      if (threadIdx.x < nr) __stcg((fwd ? y : x) + r0 + threadIdx.x, acc[threadIdx.x]);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      atomicExch(&flag[fwd ? i : nt + i], solve_id);
-    }
-  }
-}
-
 template <typename T>
 int chol_tile() {
   return sizeof(T) == 8 ? 32 : 64;
@@ -1456,16 +1237,7 @@ size_t chol_packed_elems(int nt) {
 template size_t chol_packed_elems<float>(int);
 template size_t chol_packed_elems<double>(int);
 
-static int g_sms = 0;
-static int num_sms() {
-  if (!g_sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_sms <= 0) g_sms = 1;
-  }
-  return g_sms;
-}
+
 
 template <typename T>
 void launch_chol_dag(const BatchTabs& B, cudaStream_t s) {
@@ -1500,130 +1272,7 @@ void launch_chol_dag(const BatchTabs& B, cudaStream_t s) {
   ++g_launches;
 }
 
-template <typename T>
-void launch_trsv_dag(const BatchTabs& B, int solve_id, cudaStream_t s) {
-  constexpr int TB = sizeof(T) == 8 ? 32 : 64;
-  static int per_sm = 0;
-  if (!per_sm) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trsv_dag<T, TB>, 256, 0);
-    per_sm = std::max(1, std::min(per_sm, 4));
-  }
-  const int nticket = B.P * 2 * B.max_nt;
-  const int grid = std::min(nticket, per_sm * num_sms());
-  k_trsv_dag<T, TB><<<grid, 256, 0, s>>>(B.d, B.P, nticket, solve_id, B.words + solve_id,
-                                          B.words + 5, 2000000000ull);
-  ++g_launches;
-}
-
-// rhs (T) = b or r (FP64), per (problem, 256-element chunk)
-template <typename T>
-__global__ void k_vec_in(const ProbDesc* const* __restrict__ descs, const int2* __restrict__ tab,
-                         int from_r) {
-  const int2 w = tab[blockIdx.x];
-  const ProbDesc& D = *descs[w.x];
-  const int i = w.y * 256 + threadIdx.x;
-  if (i < D.n) ((T*)D.lp.rhs)[i] = (T)(from_r ? D.r[i] : D.b[i]);
-}
-template <typename T>
-void launch_vec_in(const BatchTabs& B, bool from_r, cudaStream_t s) {
-  k_vec_in<T><<<B.n_vec, 256, 0, s>>>(B.d, B.vec, from_r ? 1 : 0);
-  ++g_launches;
-}
-
-// x (FP64) = or += solution (T)
-template <typename T>
-__global__ void k_vec_out(const ProbDesc* const* __restrict__ descs, const int2* __restrict__ tab,
-                          int assign) {
-  const int2 w = tab[blockIdx.x];
-  const ProbDesc& D = *descs[w.x];
-  const int i = w.y * 256 + threadIdx.x;
-  if (i < D.n) {
-    const double v = (double)((const T*)D.lp.x)[i];
-    const double xi = assign ? v : D.x[i] + v;
-    D.x[i] = xi;
-    const float hi = __double2float_rn(xi);
-    D.xf[i] = make_float2(hi, __double2float_rn(xi - (double)hi));
-  }
-}
-template <typename T>
-void launch_vec_out(const BatchTabs& B, bool assign, cudaStream_t s) {
-  k_vec_out<T><<<B.n_vec, 256, 0, s>>>(B.d, B.vec, assign ? 1 : 0);
-  ++g_launches;
-}
-
-// r = b - A x with A the full symmetric FP32 matrix and x = hi + lo (two floats, written with x):
-// each product a x_hi is split exactly with an FMA (a x_hi = p + e), a x_lo is added to the error
-// term, and the sum is kept as an unevaluated pair of floats (two-sum), i.e. about 48 significant
-// bits, the precision of FP64 accumulation for these sums, at FP32 instruction rates (the FP64
-// pipe of this GPU is 1/64 of FP32). One warp per row, (problem, 8-row chunk) per CTA.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-__device__ __forceinline__ void df_add_term(float a, float2 x, float& sh, float& sl) {
-  const float p = __fmul_rn(a, x.x);
-  const float t = __fmaf_rn(a, x.y, __fmaf_rn(a, x.x, -p));  // (a x_hi - p) + a x_lo
-  float e;
-  two_sum(sh, p, sh, e);
-  sl = __fadd_rn(sl, __fadd_rn(e, t));
-}
-__global__ __launch_bounds__(256) void k_residual64(const ProbDesc* const* __restrict__ descs,
-                                                    const int2* __restrict__ tab) {
-  const int2 w = tab[blockIdx.x];
-  const ProbDesc& D = *descs[w.x];
-  const int n = D.n;
-  const int row = w.y * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (row >= n) return;
-  const float* a = D.Aref + (size_t)row * n;
-  const float2* __restrict__ x = D.xf;
-  float sh = 0.f, sl = 0.f;
-  if ((n & 3) == 0) {
-    const float4* a4 = reinterpret_cast<const float4*>(a);
-    for (int q = lane; q < (n >> 2); q += 32) {
-      const float4 v = __ldcs(a4 + q);
-      df_add_term(v.x, x[4 * q], sh, sl);
-      df_add_term(v.y, x[4 * q + 1], sh, sl);
-      df_add_term(v.z, x[4 * q + 2], sh, sl);
-      df_add_term(v.w, x[4 * q + 3], sh, sl);
-    }
-  } else {
-    for (int j = lane; j < n; j += 32) df_add_term(a[j], x[j], sh, sl);
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    const float oh = __shfl_xor_sync(0xffffffffu, sh, o), ol = __shfl_xor_sync(0xffffffffu, sl, o);
-    float e;
-    two_sum(sh, oh, sh, e);
-    sl = __fadd_rn(sl, __fadd_rn(ol, e));
-  }
-  if (lane == 0) D.r[row] = D.b[row] - ((double)sh + (double)sl);
-}
-
-void launch_residual64(const BatchTabs& B, cudaStream_t s) {
-  k_residual64<<<B.n_res, 256, 0, s>>>(B.d, B.res);
-  ++g_launches;
-}
-
-// Full symmetric FP64 copy of a lower-stored FP32 matrix (inspection only).
-__global__ void k_sym_unpack(const float* __restrict__ A, int n, double* __restrict__ out) {
-  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (size_t)n * n) return;
-  int i = (int)(e / n), j = (int)(e % n);
-  out[e] = (double)(i >= j ? A[(size_t)i * n + j] : A[(size_t)j * n + i]);
-}
-void launch_sym_unpack(const float* A, int n, double* out, cudaStream_t s) {
-  size_t tot = (size_t)n * n;
-  k_sym_unpack<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(A, n, out);
-  ++g_launches;
-}
-
 template void launch_chol_dag<float>(const BatchTabs&, cudaStream_t);
 template void launch_chol_dag<double>(const BatchTabs&, cudaStream_t);
-template void launch_trsv_dag<float>(const BatchTabs&, int, cudaStream_t);
-template void launch_trsv_dag<double>(const BatchTabs&, int, cudaStream_t);
-template void launch_vec_in<float>(const BatchTabs&, bool, cudaStream_t);
-template void launch_vec_in<double>(const BatchTabs&, bool, cudaStream_t);
-template void launch_vec_out<float>(const BatchTabs&, bool, cudaStream_t);
-template void launch_vec_out<double>(const BatchTabs&, bool, cudaStream_t);
 
 }  // namespace ds

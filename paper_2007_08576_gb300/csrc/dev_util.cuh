@@ -1,0 +1,49 @@
+// Device helpers shared by the factorisation and the solve kernels: the global timer, bounded
+// waits on counters written by other CTAs, L2-only loads, the SM count.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace ds {
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait until *p >= v. Returns false (and raises *err) on timeout or if *err is set.
+__device__ __forceinline__ bool wait_ge(const int* p, int v, int* err,
+                                        unsigned long long budget_ns) {
+  const volatile int* vp = p;
+  const volatile int* ve = err;
+  if (*vp >= v) return true;
+  unsigned long long t0 = globaltimer();
+  int it = 0;
+  while (*vp < v) {
+    if (*ve) return false;
+    if ((++it & 31) == 0 && globaltimer() - t0 > budget_ns) {
+      atomicExch(err, 1);
+      return false;
+    }
+    __nanosleep(64);
+  }
+  return true;
+}
+
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) {
+  return __ldcg(p);
+}
+
+inline int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+}  // namespace ds
