@@ -46,88 +46,6 @@ struct TileCfg {
   static constexpr int LDT = TB + 16 / sizeof(T);  // transposed shared tile row stride (16 B pad)
 };
 
-template <typename T>
-struct Vec2 {};
-template <>
-struct Vec2<float> {
-  using type = float2;
-};
-template <>
-struct Vec2<double> {
-  using type = double2;
-};
-
-// Loads tile (ti, tj) of A transposed into shared memory: S[m * LDT + r] = A[ti*TB + r][tj*TB + m]
-// (zero outside the matrix). Lane <-> row: each thread reads a contiguous run of one row with
-// 16-byte vector loads and writes it down a column of S, so a warp's shared stores hit 32
-// consecutive banks. Rows are 16-byte aligned when n is a multiple of 4 (FP32) / 2 (FP64);
-// otherwise the scalar path is taken.
-template <typename T, int TB>
-__device__ __forceinline__ void load_tile_t(const T* A, int n, int ti, int tj, T* S) {
-  constexpr int LDT = TileCfg<T, TB>::LDT;
-  constexpr int VE = 16 / sizeof(T);           // elements per 16-byte vector
-  constexpr int RUN = TB * TB / 256;           // elements per thread (16 FP32 / 4 FP64)
-  constexpr int SPLIT = TB / RUN;              // threads per row
-  const int r0 = ti * TB, c0 = tj * TB;
-  const int r = threadIdx.x % TB;
-  const int m0 = (threadIdx.x / TB) * RUN;
-  (void)SPLIT;
-  const bool full = (r0 + TB <= n) && (c0 + TB <= n) && ((n * sizeof(T)) % 16 == 0);
-  if (full) {
-    const T* src = A + (size_t)(r0 + r) * n + c0 + m0;
-#pragma unroll
-    for (int v = 0; v < RUN / VE; ++v) {
-      T buf[VE];
-      if constexpr (sizeof(T) == 4) {
-        float4 x = __ldcg(reinterpret_cast<const float4*>(src) + v);
-        buf[0] = x.x; buf[1] = x.y; buf[2] = x.z; buf[3] = x.w;
-      } else {
-        double2 x = __ldcg(reinterpret_cast<const double2*>(src) + v);
-        buf[0] = x.x; buf[1] = x.y;
-      }
-#pragma unroll
-      for (int e = 0; e < VE; ++e) S[(m0 + v * VE + e) * LDT + r] = buf[e];
-    }
-  } else {
-#pragma unroll
-    for (int e = 0; e < RUN; ++e) {
-      const int m = m0 + e;
-      S[m * LDT + r] = (r0 + r < n && c0 + m < n) ? ldcg(A + (size_t)(r0 + r) * n + c0 + m) : (T)0;
-    }
-  }
-}
-
-// acc[a][b] = sum_m P^T[m][tr + a] Q^T[m][tc + b] over m < TB (transposed shared operands).
-template <typename T, int TB>
-__device__ __forceinline__ void tile_abt_t(const T* Pt, const T* Qt,
-                                           T (&acc)[TileCfg<T, TB>::RT][TileCfg<T, TB>::RT]) {
-  constexpr int RT = TileCfg<T, TB>::RT, LDT = TileCfg<T, TB>::LDT;
-  const int tr = (threadIdx.x / 16) * RT, tc = (threadIdx.x % 16) * RT;
-#pragma unroll
-  for (int a = 0; a < RT; ++a)
-#pragma unroll
-    for (int b = 0; b < RT; ++b) acc[a][b] = (T)0;
-#pragma unroll 4
-  for (int m = 0; m < TB; ++m) {
-    T x[RT], y[RT];
-    if constexpr (RT == 4) {
-      float4 xv = *reinterpret_cast<const float4*>(Pt + m * LDT + tr);
-      float4 yv = *reinterpret_cast<const float4*>(Qt + m * LDT + tc);
-      x[0] = xv.x; x[1] = xv.y; x[2] = xv.z; x[3] = xv.w;
-      y[0] = yv.x; y[1] = yv.y; y[2] = yv.z; y[3] = yv.w;
-    } else {
-      double2 xv = *reinterpret_cast<const double2*>(Pt + m * LDT + tr);
-      double2 yv = *reinterpret_cast<const double2*>(Qt + m * LDT + tc);
-      x[0] = xv.x; x[1] = xv.y;
-      y[0] = yv.x; y[1] = yv.y;
-    }
-#pragma unroll
-    for (int a = 0; a < RT; ++a)
-#pragma unroll
-      for (int b = 0; b < RT; ++b) acc[a][b] += x[a] * y[b];
-  }
-}
-
 // Stores (or subtracts from) this thread's RT x RT block of tile (ti, tj); lower_only keeps
 // r >= c (diagonal tiles). Interior blocks of an aligned matrix move as one 16-byte vector per row.
 template <typename T, int TB, bool SUB>
@@ -189,122 +107,6 @@ __device__ __forceinline__ double rsqrt_newton<double>(double p) {
   return y * (1.5 - 0.5 * p * y * y);
 }
 
-template <typename T>
-__device__ __forceinline__ T shfl(T v, int src) {
-  return __shfl_sync(0xffffffffu, v, src);
-}
-
-// Cholesky of a diagonal tile in shared memory (L[r * LDS + c], lower, identity padding past the
-// matrix) together with its inverse X (lower part written in full). The tile is processed in
-// blocks of PB = 8 columns (4 in FP64):
-//   (1) warp 0 factors the PB x PB diagonal block and inverts it in registers (each lane factors
-//       the block redundantly, lane c then solves column c of the inverse);
-//   (2) the rows below take L_rb = A_rb D^T (D = the block's inverse), one thread per row;
-//   (3) the block's rows of X left of the block: X_bc = -D sum_q L_bq X_qc;
-//   (4) the trailing lower triangle gets the rank-PB update with the new panel.
-// Three barriers per block; 256 threads (8 warps).
-template <typename T, int TB>
-__device__ void potrf_blocked(T* L, T* X, T* tmp, int row0, double* status) {
-  // 8-column blocks in FP32; 4 in FP64, where the register-resident block factor would spill
-  constexpr int LDS = TB + 1, PB = sizeof(T) == 8 ? 4 : 8, NBK = TB / PB;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int kb = 0; kb < NBK; ++kb) {
-    const int c0 = kb * PB;
-    if (warp == 0) {
-      // every lane factors the whole 8 x 8 block in registers (no communication): left-looking
-      // column by column, l[r][j] = (a[r][j] - sum_{q<j} l[r][q] l[j][q]) / l[j][j]
-      T l[PB][PB], dinv[PB];
-#pragma unroll
-      for (int r = 0; r < PB; ++r)
-#pragma unroll
-        for (int c = 0; c <= r; ++c) l[r][c] = L[(c0 + r) * LDS + c0 + c];
-#pragma unroll
-      for (int j = 0; j < PB; ++j) {
-        T p = l[j][j];
-#pragma unroll
-        for (int q = 0; q < j; ++q) p -= l[j][q] * l[j][q];
-        if (!(p > (T)0)) {
-          if (status && lane == 0)
-            atomicCAS((unsigned long long*)status, 0ull,
-                      __double_as_longlong((double)(row0 + c0 + j + 1)));
-          p = (T)1;
-        }
-        const T inv = rsqrt_newton<T>(p);
-        dinv[j] = inv;
-        l[j][j] = p * inv;
-#pragma unroll
-        for (int r = j + 1; r < PB; ++r) {
-          T v = l[r][j];
-#pragma unroll
-          for (int q = 0; q < j; ++q) v -= l[r][q] * l[j][q];
-          l[r][j] = v * inv;
-        }
-      }
-      // lane c < 8 solves column c of the inverse: x_c = 1 / l_cc,
-      // x_r = -(sum_{c <= q < r} l[r][q] x_q) / l_rr
-      const int c = lane;
-      T x[PB];
-#pragma unroll
-      for (int r = 0; r < PB; ++r) {
-        T v = (T)0;
-#pragma unroll
-        for (int q = 0; q < r; ++q)
-          if (q >= c) v -= l[r][q] * x[q];
-        x[r] = r == c ? dinv[r] : (r > c ? v * dinv[r] : (T)0);
-      }
-      if (lane < PB) {
-#pragma unroll
-        for (int r = 0; r < PB; ++r) {
-          if (r >= c) X[(c0 + r) * LDS + c0 + c] = x[r];
-#pragma unroll
-          for (int q = 0; q <= r; ++q)
-            if (r == lane) L[(c0 + r) * LDS + c0 + q] = l[r][q];
-        }
-      }
-    }
-    __syncthreads();
-    // (2) rows below the block
-    for (int r = c0 + PB + tid; r < TB; r += blockDim.x) {
-      T row[PB];
-#pragma unroll
-      for (int m = 0; m < PB; ++m) row[m] = L[r * LDS + c0 + m];
-#pragma unroll
-      for (int c = 0; c < PB; ++c) {
-        T s = (T)0;
-#pragma unroll
-        for (int m = 0; m <= c; ++m) s += row[m] * X[(c0 + c) * LDS + c0 + m];
-        L[r * LDS + c0 + c] = s;
-      }
-    }
-    // (3a) tmp[m][c] = sum_{q = c}^{c0 - 1} L[c0 + m][q] X[q][c]   (warp m, lanes over c)
-    if (warp < PB)
-      for (int c = lane; c < c0; c += 32) {
-        T s = (T)0;
-#pragma unroll 4
-        for (int q = c; q < c0; ++q) s += L[(c0 + warp) * LDS + q] * X[q * LDS + c];
-        tmp[warp * TB + c] = s;
-      }
-    __syncthreads();
-    // (4) rank-PB update of the trailing lower triangle
-    for (int r = c0 + PB + warp; r < TB; r += 8)
-      for (int c = c0 + PB + lane; c <= r; c += 32) {
-        T s = (T)0;
-#pragma unroll
-        for (int q = 0; q < PB; ++q) s += L[r * LDS + c0 + q] * L[c * LDS + c0 + q];
-        L[r * LDS + c] -= s;
-      }
-    // (3b) X[c0 + i][c] = -sum_m D[i][m] tmp[m][c]   (warp i, lanes over c)
-    if (warp < PB)
-      for (int c = lane; c < c0; c += 32) {
-        T s = (T)0;
-#pragma unroll
-        for (int m = 0; m < PB; ++m)
-          if (m <= warp) s += X[(c0 + warp) * LDS + c0 + m] * tmp[m * TB + c];
-        X[(c0 + warp) * LDS + c] = -s;
-      }
-    __syncthreads();
-  }
-}
 
 // One doubling level of a lower-triangular inverse held in shared memory (row stride TB + 1,
 // zeros above the diagonal): for every pair of H x H diagonal blocks starting at s0 = 2 H g,
