@@ -44,8 +44,8 @@ FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x ma
 # workload (32 problems, FP32 factor), from the full ncu capture summarised in
 # profiles/k_chol_dag_f32_seq_320x240_n256_batch32.md. It describes the kernel source it was taken
 # on (first 16 hex digits of the sha256 of csrc/chol.cu) and is reported as null for any other.
-CHOL_TRAFFIC = {"chol_sha256": "cdd102d859b0606d", "precision": 2, "streams": 32,
-                "bytes": 687928320 + 356298752}
+CHOL_TRAFFIC = {"chol_sha256": "47794e8459102c6a", "precision": 2, "streams": 32,
+                "bytes": 683611392 + 356222464}
 
 
 def max_over_ranks(x, world, dev):
