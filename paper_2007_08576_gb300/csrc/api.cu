@@ -130,7 +130,6 @@ struct ds_ctx {
   double* d_x = nullptr;
   double* d_r = nullptr;
   float2* d_xf = nullptr;
-  void* d_v1 = nullptr;
   void* d_v2 = nullptr;
   void* d_v3 = nullptr;
   int* d_lcnt = nullptr;      // factorisation task counters
@@ -206,7 +205,7 @@ void free_cp(ds_ctx* h) {
   dfree(h->d_pn); dfree(h->d_tp); dfree(h->d_tw); dfree(h->d_rank); dfree(h->d_seg);
   dfree(h->d_segbp); dfree(h->d_segstart); dfree(h->d_rowptr); dfree(h->d_rowcol); dfree(h->d_rowbp);
   dfree(h->d_A32); dfree(h->d_A64); dfree(h->d_Af32); dfree(h->d_Dinv); dfree(h->d_blk); dfree(h->d_adiag);
-  dfree(h->d_gdata); dfree(h->d_b); dfree(h->d_x); dfree(h->d_r); dfree(h->d_xf); dfree(h->d_v1);
+  dfree(h->d_gdata); dfree(h->d_b); dfree(h->d_x); dfree(h->d_r); dfree(h->d_xf);
   dfree(h->d_v2); dfree(h->d_v3); dfree(h->d_lcnt); dfree(h->d_lflags); dfree(h->d_tasks);
   dfree(h->d_Lp);
   dfree(h->d_desc);
@@ -436,14 +435,10 @@ void enqueue_factor_solve(ds_batch_s* b) {
   const BatchTabs& B = b->tabs;
   launch_chol_dag<T>(B, s);
   trace(b, b->cur_it, 2);
-  launch_vec_in<T>(B, false, s);
-  launch_trsv_dag<T>(B, 1, s);
-  launch_vec_out<T>(B, true, s);
+  launch_trsv_dag<T>(B, 1, false, true, s);
   for (int k = 0; k < b->refine_steps; ++k) {
     launch_residual64(B, s);
-    launch_vec_in<T>(B, true, s);
-    launch_trsv_dag<T>(B, 2 + k, s);
-    launch_vec_out<T>(B, false, s);
+    launch_trsv_dag<T>(B, 2 + k, true, false, s);
   }
 }
 
@@ -888,7 +883,7 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
       (rc = dalloc(&h->d_adiag, 48 * (size_t)N)) ||
       (rc = dalloc(&h->d_b, n)) || (rc = dalloc(&h->d_x, n)) || (rc = dalloc(&h->d_r, n)) ||
       (rc = dalloc(&h->d_xf, n)) ||
-      (rc = dalloc((char**)&h->d_v1, tsz * n)) || (rc = dalloc((char**)&h->d_v2, tsz * n)) ||
+      (rc = dalloc((char**)&h->d_v2, tsz * n)) ||
       (rc = dalloc((char**)&h->d_v3, tsz * n)) ||
       (rc = dalloc((char**)&h->d_Dinv, tsz * (size_t)nt * TB * TB)) ||
       (rc = dalloc(&h->d_lcnt, (size_t)nt + 2 * (size_t)nt * nt)) ||
@@ -981,7 +976,6 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
     lp.tasks = h->d_tasks;
     lp.ntasks = h->ntasks;
     lp.status = h->d_acc + ACC_STATUS;
-    lp.rhs = h->d_v1;
     lp.y = h->d_v3;
     lp.x = h->d_v2;
     if ((rc = dalloc(&h->d_desc, 1))) {

@@ -52,8 +52,8 @@ __host__ __device__ constexpr int kSlotPairJ(int k) {
 // batch). A: n x n lower, factored in place; Dinv: inverses of the nt diagonal tiles (TB x TB);
 // cnt: task counters of the factorisation (nt + 2 nt^2 ints); flags: 2 nt ints of the solves
 // (a row is done for solve s when its flag equals s); tasks: the problem's factorisation tasks
-// in topological order; status: FP64 word receiving 1 + row of a non-positive pivot; rhs / y /
-// x: vectors of the solve (T).
+// in topological order; status: FP64 word receiving 1 + row of a non-positive pivot; y / x:
+// the forward and backward solutions of the solve (T).
 struct LinProblem {
   void* A;
   void* Dinv;
@@ -64,7 +64,6 @@ struct LinProblem {
   const int4* tasks;
   int ntasks;
   double* status;
-  void* rhs;
   void* y;
   void* x;
 };
@@ -182,12 +181,8 @@ size_t chol_packed_elems(int nt);  // elements of the packed L tiles (either FP3
 template <typename T>
 void launch_chol_dag(const BatchTabs& B, cudaStream_t s);
 template <typename T>
-void launch_trsv_dag(const BatchTabs& B, int solve_id, cudaStream_t s);
-// vector steps of the solve: rhs = (T) b (k = 0) or (T) r (k > 0); x (=|+=) solution
-template <typename T>
-void launch_vec_in(const BatchTabs& B, bool from_r, cudaStream_t s);
-template <typename T>
-void launch_vec_out(const BatchTabs& B, bool assign, cudaStream_t s);
+void launch_trsv_dag(const BatchTabs& B, int solve_id, bool from_r, bool assign, cudaStream_t s);
+// refinement residual r = b - A x against the FP32 system (double-float accumulation)
 void launch_residual64(const BatchTabs& B, cudaStream_t s);
 void launch_sym_unpack(const float* A, int n, double* out, cudaStream_t s);
 

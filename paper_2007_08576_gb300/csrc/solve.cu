@@ -93,10 +93,14 @@ __device__ __forceinline__ void gemv_cols_pf(const T (&v)[SolveTile<T, TB>::NV],
 // flags: [0, nt) forward row done, [nt, 2nt) backward row done. Every tile a ticket needs is
 // loaded into registers before the wait on its producer (the tiles do not depend on it), so a
 // dependency costs one flag hand-off and one 64-value vector load.
+// The forward tickets read the right-hand side from b (first solve) or from the refinement
+// residual r (from_r) in FP64; the backward tickets also write the solution into the FP64 x
+// (assigned, or added to it for a refinement step) and its two-float split for the residual.
 template <typename T, int TB>
 __global__ __launch_bounds__(256) void k_trsv_dag(const ProbDesc* const* __restrict__ descs,
-                                                  int np, int nticket, int solve_id,
-                                                  int* __restrict__ head, int* __restrict__ err,
+                                                  int np, int nticket, int solve_id, int from_r,
+                                                  int assign, int* __restrict__ head,
+                                                  int* __restrict__ err,
                                                   unsigned long long budget_ns) {
   constexpr int NV = SolveTile<T, TB>::NV;
   __shared__ T acc[TB];
@@ -108,7 +112,8 @@ __global__ __launch_bounds__(256) void k_trsv_dag(const ProbDesc* const* __restr
     __syncthreads();
     const int t = s_t;
     if (t >= nticket) return;
-    const LinProblem& P = descs[t % np]->lp;
+    const ProbDesc& PD = *descs[t % np];
+    const LinProblem& P = PD.lp;
     const int2 tk = make_int2(t % np, t / np);
     if (tk.y >= 2 * P.nt) {
       __syncthreads();
@@ -124,7 +129,7 @@ __global__ __launch_bounds__(256) void k_trsv_dag(const ProbDesc* const* __restr
     int* flag = P.flags;
     T* y = (T*)P.y;
     T* x = (T*)P.x;
-    const T* rhs = (const T*)P.rhs;
+    const double* rhs = from_r ? PD.r : PD.b;
     const T* src = fwd ? y : x;
     T dv[NV];  // the diagonal block's inverse, prefetched
     if (fwd)
@@ -140,7 +145,9 @@ __global__ __launch_bounds__(256) void k_trsv_dag(const ProbDesc* const* __restr
     __syncthreads();
     ok = s_ok;
     if (threadIdx.x < TB)
-      acc[threadIdx.x] = (threadIdx.x < nr && ok) ? ldcg((fwd ? rhs : y) + r0 + threadIdx.x) : (T)0;
+      acc[threadIdx.x] = (threadIdx.x < nr && ok)
+                             ? (fwd ? (T)ldcg(rhs + r0 + threadIdx.x) : ldcg(y + r0 + threadIdx.x))
+                             : (T)0;
     const int cnt = fwd ? i : nt - 1 - i;
     T lv[NV];
     if (cnt > 0) {
@@ -189,7 +196,17 @@ __global__ __launch_bounds__(256) void k_trsv_dag(const ProbDesc* const* __restr
       else
         gemv_cols_pf<T, TB>(dv, vin, acc, false, part);
       __syncthreads();
-      if (threadIdx.x < nr) __stcg((fwd ? y : x) + r0 + threadIdx.x, acc[threadIdx.x]);
+      if (threadIdx.x < nr) {
+        const T v = acc[threadIdx.x];
+        __stcg((fwd ? y : x) + r0 + threadIdx.x, v);
+        if (!fwd) {
+          const int e = r0 + threadIdx.x;
+          const double xi = assign ? (double)v : PD.x[e] + (double)v;
+          PD.x[e] = xi;
+          const float hi = __double2float_rn(xi);
+          PD.xf[e] = make_float2(hi, __double2float_rn(xi - (double)hi));
+        }
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -201,7 +218,7 @@ __global__ __launch_bounds__(256) void k_trsv_dag(const ProbDesc* const* __restr
 
 
 template <typename T>
-void launch_trsv_dag(const BatchTabs& B, int solve_id, cudaStream_t s) {
+void launch_trsv_dag(const BatchTabs& B, int solve_id, bool from_r, bool assign, cudaStream_t s) {
   constexpr int TB = sizeof(T) == 8 ? 32 : 64;
   static int per_sm = 0;
   if (!per_sm) {
@@ -210,44 +227,9 @@ void launch_trsv_dag(const BatchTabs& B, int solve_id, cudaStream_t s) {
   }
   const int nticket = B.P * 2 * B.max_nt;
   const int grid = std::min(nticket, per_sm * num_sms());
-  k_trsv_dag<T, TB><<<grid, 256, 0, s>>>(B.d, B.P, nticket, solve_id, B.words + solve_id,
-                                          B.words + 5, 2000000000ull);
-  ++g_launches;
-}
-
-// rhs (T) = b or r (FP64), per (problem, 256-element chunk)
-template <typename T>
-__global__ void k_vec_in(const ProbDesc* const* __restrict__ descs, const int2* __restrict__ tab,
-                         int from_r) {
-  const int2 w = tab[blockIdx.x];
-  const ProbDesc& D = *descs[w.x];
-  const int i = w.y * 256 + threadIdx.x;
-  if (i < D.n) ((T*)D.lp.rhs)[i] = (T)(from_r ? D.r[i] : D.b[i]);
-}
-template <typename T>
-void launch_vec_in(const BatchTabs& B, bool from_r, cudaStream_t s) {
-  k_vec_in<T><<<B.n_vec, 256, 0, s>>>(B.d, B.vec, from_r ? 1 : 0);
-  ++g_launches;
-}
-
-// x (FP64) = or += solution (T)
-template <typename T>
-__global__ void k_vec_out(const ProbDesc* const* __restrict__ descs, const int2* __restrict__ tab,
-                          int assign) {
-  const int2 w = tab[blockIdx.x];
-  const ProbDesc& D = *descs[w.x];
-  const int i = w.y * 256 + threadIdx.x;
-  if (i < D.n) {
-    const double v = (double)((const T*)D.lp.x)[i];
-    const double xi = assign ? v : D.x[i] + v;
-    D.x[i] = xi;
-    const float hi = __double2float_rn(xi);
-    D.xf[i] = make_float2(hi, __double2float_rn(xi - (double)hi));
-  }
-}
-template <typename T>
-void launch_vec_out(const BatchTabs& B, bool assign, cudaStream_t s) {
-  k_vec_out<T><<<B.n_vec, 256, 0, s>>>(B.d, B.vec, assign ? 1 : 0);
+  k_trsv_dag<T, TB><<<grid, 256, 0, s>>>(B.d, B.P, nticket, solve_id, from_r ? 1 : 0,
+                                          assign ? 1 : 0, B.words + solve_id, B.words + 5,
+                                          2000000000ull);
   ++g_launches;
 }
 
@@ -317,11 +299,7 @@ void launch_sym_unpack(const float* A, int n, double* out, cudaStream_t s) {
   ++g_launches;
 }
 
-template void launch_trsv_dag<float>(const BatchTabs&, int, cudaStream_t);
-template void launch_trsv_dag<double>(const BatchTabs&, int, cudaStream_t);
-template void launch_vec_in<float>(const BatchTabs&, bool, cudaStream_t);
-template void launch_vec_in<double>(const BatchTabs&, bool, cudaStream_t);
-template void launch_vec_out<float>(const BatchTabs&, bool, cudaStream_t);
-template void launch_vec_out<double>(const BatchTabs&, bool, cudaStream_t);
+template void launch_trsv_dag<float>(const BatchTabs&, int, bool, bool, cudaStream_t);
+template void launch_trsv_dag<double>(const BatchTabs&, int, bool, bool, cudaStream_t);
 
 }  // namespace ds
