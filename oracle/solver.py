@@ -15,7 +15,11 @@ Readings used here (the CUDA path implements the same ones):
   to the lower node id) with weights exp(-d^2 / (2 sigma_b^2)) normalised to 1, sigma_b =
   sigma_blend_scale x the mean nearest-neighbour spacing of the control points;
 * the ORB match points of the template side (o1 of Eq. 2) are the template's back-projected
-  points at the matched pixels.
+  points at the matched pixels (ransac_o1 = "template"), or, in the warm-start variant
+  (ransac_o1 = "warm"), those template points warped by the frame's warm-start state, so that the
+  rigid model of the 1-point RANSAC only has to explain the motion since the previous frame;
+* the ICP association rounds the projection to the nearest pixel (assoc = "nearest") or blends
+  the 4 surrounding pixels bilinearly (assoc = "bilinear", terms.associate_bilinear).
 """
 import dataclasses
 
@@ -42,6 +46,8 @@ class Params:
     n_hyp: int = 30              # Section 2.1
     n_reweight: int = 10         # Section 2.1
     solver: str = "dense"        # "dense" Cholesky of the 6N system, or "block_jacobi" (per node)
+    assoc: str = "nearest"       # ICP association: "nearest" pixel or "bilinear" blend
+    ransac_o1: str = "template"  # RANSAC o1: "template" points or "warm" (warped by the warm start)
 
 
 @dataclasses.dataclass
@@ -152,19 +158,34 @@ def data_terms(tpl: Template, tgt: Target, q, t, orb, prm: Params):
     """ICP and ORB rows at state (q, t).  orb = (match_idx, o2, mask, what) or None."""
     x, Jx = dqb.warp_points(q, t, tpl.g, tpl.p, tpl.nid, tpl.alpha, tpl.nid[:, 0])
     icp, c_icp, ws_icp, pix, valid = terms.icp_rows(x, Jx, tpl.nid, tgt.X, tgt.n, tgt.ok, tpl.K,
-                                                    tpl.W, tpl.H, prm.tukey_c)
+                                                    tpl.W, tpl.H, prm.tukey_c, prm.assoc)
     rows = [icp]
     c_orb, ws_orb = 0.0, 0.0
     if orb is not None and len(orb[0]) > 0:
         midx, o2, mask, what = orb
-        # template rank of each matched pixel
-        rank = np.full(tpl.W * tpl.H, -1, dtype=np.int64)
-        rank[tpl.pidx] = np.arange(tpl.pidx.shape[0])
-        jr = rank[np.asarray(midx, dtype=np.int64)]
+        jr = template_rank(tpl, midx)
         xk, Jk = x[jr], Jx[jr]
         orb_r, c_orb, ws_orb = terms.orb_rows(xk, Jk, tpl.nid[jr], o2, mask, what, prm.H, prm.w_orb)
         rows.append(orb_r)
     return rows, c_icp, c_orb, ws_icp, ws_orb, pix, valid
+
+
+def template_rank(tpl: Template, pix):
+    """Position of each template pixel in the list of valid template points."""
+    rank = np.full(tpl.W * tpl.H, -1, dtype=np.int64)
+    rank[tpl.pidx] = np.arange(tpl.pidx.shape[0])
+    return rank[np.asarray(pix, dtype=np.int64)]
+
+
+def ransac_o1(tpl: Template, midx, q, t, prm: Params):
+    """o1 of Eq. 2 for the matched template pixels: the template points, or (warm-start
+    variant) the same points warped by the state (q, t) the frame starts from."""
+    if prm.ransac_o1 == "warm":
+        jr = template_rank(tpl, midx)
+        x, _ = dqb.warp_points(q, t, tpl.g, tpl.p[jr], tpl.nid[jr], tpl.alpha[jr], tpl.nid[jr, 0],
+                               with_jac=False)
+        return x
+    return tpl.X0[np.asarray(midx, dtype=np.int64)]
 
 
 def linearize(tpl: Template, tgt: Target, q, t, orb, w_arap, prm: Params):
@@ -229,7 +250,7 @@ def solve_frame(tpl: Template, depth, match_idx, match_xyz, hyp, prm: Params = P
     t = np.zeros((N, 3)) if t0 is None else np.asarray(t0, np.float64).copy()
     tgt = prepare_target(depth, tpl.K)
     midx = np.asarray(match_idx, dtype=np.int64)
-    o1 = tpl.X0[midx]
+    o1 = ransac_o1(tpl, midx, q, t, prm) if len(midx) > 0 else np.zeros((0, 3))
     o2 = np.asarray(match_xyz, dtype=np.float64).reshape(-1, 3)
     if len(midx) > 0:
         rs = ransac.ransac_1p(o1, o2, np.asarray(hyp), prm.H, prm.n_reweight, prm.keep_frac)

@@ -53,14 +53,62 @@ def associate(x, K, W, H, tgt_ok):
     return pix, valid, u, v
 
 
-def icp_rows(x, Jx, nid, tgtX, tgtN, tgt_ok, K, W, H, c):
+def associate_bilinear(x, K, W, H, tgtX, tgtN, tgt_ok):
+    """Continuous variant of the projective association (Section 2 "rasterization"; an
+    interpolated lookup replaces the pixel rounding): with (u, v) the projection of the warped
+    point, u0 = floor(u), a = u - u0 (v0, b likewise), the 4 pixels (u0 + i, v0 + j),
+    i, j in {0, 1}, carry the bilinear weights (1 - a)(1 - b), a (1 - b), (1 - a) b, a b.  Pixels
+    outside the image or not usable are dropped and the weights of the others renormalised:
+    q = sum_c w_c X_c / sum_c w_c over usable corners, n = the same blend of normals, normalised.
+    Valid iff z > 0, the usable weight sum is >= 1/2 and the normal blend is nonzero.  (Along
+    one axis next to an unusable pixel the point stays valid exactly while the nearest-pixel
+    rule would pick the usable pixel; the result is continuous in (u, v) inside the valid set,
+    including at integer coordinates, where the template points fall at the identity state.)
+
+    Returns (q (P, 3), n (P, 3), valid (P,) bool, corner pixels (P, 4), weights (P, 4)); the
+    weights are the renormalised ones (0 for dropped corners)."""
+    fx, fy, cx, cy = K
+    z = x[:, 2]
+    zs = np.where(z > 0, z, 1.0)
+    u = fx * x[:, 0] / zs + cx
+    v = fy * x[:, 1] / zs + cy
+    u0 = np.floor(u)
+    v0 = np.floor(v)
+    a = u - u0
+    b = v - v0
+    cu = np.stack([u0, u0 + 1, u0, u0 + 1], 1)
+    cv = np.stack([v0, v0, v0 + 1, v0 + 1], 1)
+    inimg = (z[:, None] > 0) & (cu >= 0) & (cu <= W - 1) & (cv >= 0) & (cv <= H - 1)
+    pix = np.where(inimg, cv * W + cu, 0).astype(np.int64)
+    usable = inimg & tgt_ok.reshape(-1)[pix]
+    wts = np.stack([(1 - a) * (1 - b), a * (1 - b), (1 - a) * b, a * b], 1) * usable
+    ws = wts.sum(1)
+    X = tgtX.reshape(-1, 3)[pix]                       # (P, 4, 3)
+    Nn = tgtN.reshape(-1, 3)[pix]
+    wn = wts / np.where(ws > 0, ws, 1.0)[:, None]
+    q = (wn[:, :, None] * X).sum(1)
+    nb = (wn[:, :, None] * Nn).sum(1)
+    ln = np.linalg.norm(nb, axis=1)
+    valid = (z > 0) & (ws >= 0.5) & (ln > 0)
+    n = nb / np.where(ln > 0, ln, 1.0)[:, None]
+    return q, n, valid, pix, wn
+
+
+def icp_rows(x, Jx, nid, tgtX, tgtN, tgt_ok, K, W, H, c, assoc="nearest"):
     """Point-to-plane ICP with Tukey weights: r_j = n_q . (x'_j - q) at the associated target
     pixel q (Section 2, ICP paragraph).  x: (P, 3) warped template points, Jx: (P, 3, 4, 6).
+    assoc = "nearest" (pixel rounding) or "bilinear" (associate_bilinear); in both the target
+    point and normal are held fixed in the Jacobian, J = n^T dx'/d(dtheta, dt).
 
-    Returns (Rows over the valid associations, cost, sum of Tukey weights, pixel, valid)."""
-    pix, valid, _, _ = associate(x, K, W, H, tgt_ok)
-    q = tgtX.reshape(-1, 3)[pix]
-    n = tgtN.reshape(-1, 3)[pix]
+    Returns (Rows over the valid associations, cost, sum of Tukey weights, pixel, valid); the
+    pixel of a bilinear association is its (u0, v0) corner."""
+    if assoc == "bilinear":
+        q, n, valid, pix4, _ = associate_bilinear(x, K, W, H, tgtX, tgtN, tgt_ok)
+        pix = pix4[:, 0]
+    else:
+        pix, valid, _, _ = associate(x, K, W, H, tgt_ok)
+        q = tgtX.reshape(-1, 3)[pix]
+        n = tgtN.reshape(-1, 3)[pix]
     r = (n * (x - q)).sum(1)
     w = tukey_weight(r, c)
     rho = tukey_rho(r, c)

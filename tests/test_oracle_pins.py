@@ -517,3 +517,226 @@ def test_block_jacobi_cost_non_increasing(tiny):
     res = solver.solve_frame(tpl, f.depth, f.match_idx, f.match_xyz, f.hyp, prm=prm, iters=10)
     c = np.array(res.costs)
     assert (np.diff(c) <= 1e-9 * c[:-1]).all(), c
+
+
+# ----------------------------------------------------------------------------- bilinear association
+
+
+def _random_target(rng, W, H):
+    X = rng.normal(size=(H, W, 3)) + np.array([0.0, 0.0, 50.0])
+    n = rng.normal(size=(H, W, 3))
+    n /= np.linalg.norm(n, axis=-1, keepdims=True)
+    return X, n
+
+
+def test_bilinear_association_equals_tent_sum_brute_force():
+    """The blend is the tent-kernel sum over the image's usable pixels, weight of pixel (i, j)
+    max(0, 1 - |u - i|) max(0, 1 - |v - j|), normalised by the sum of those weights; valid iff
+    that sum is >= 1/2."""
+    rng = np.random.default_rng(21)
+    W, H = 9, 7
+    K = (9.0, 9.0, 4.0, 3.0)
+    X, n = _random_target(rng, W, H)
+    ok = rng.uniform(size=(H, W)) > 0.15
+    x = np.concatenate([rng.uniform(-6, 6, (300, 1)), rng.uniform(-5, 5, (300, 1)),
+                        rng.uniform(8, 20, (300, 1))], 1)
+    q, nn, valid, _, _ = terms.associate_bilinear(x, K, W, H, X, n, ok)
+    fx, fy, cx, cy = K
+    nvalid = 0
+    for k in range(x.shape[0]):
+        u = fx * x[k, 0] / x[k, 2] + cx
+        v = fy * x[k, 1] / x[k, 2] + cy
+        ws = 0.0
+        qs = np.zeros(3)
+        ns = np.zeros(3)
+        for j in range(H):
+            for i in range(W):
+                w = max(0.0, 1 - abs(u - i)) * max(0.0, 1 - abs(v - j))
+                if ok[j, i]:
+                    ws += w
+                    qs += w * X[j, i]
+                    ns += w * n[j, i]
+        assert valid[k] == (ws >= 0.5 and np.linalg.norm(ns) > 0), (k, u, v, ws)
+        if not valid[k]:
+            continue
+        nvalid += 1
+        assert np.abs(q[k] - qs / ws).max() < 1e-12
+        assert np.abs(nn[k] - ns / np.linalg.norm(ns)).max() < 1e-12
+    assert 50 < nvalid < 300
+
+
+def test_bilinear_association_validity():
+    rng = np.random.default_rng(22)
+    W, H = 9, 7
+    K = (9.0, 9.0, 4.0, 3.0)
+    X, n = _random_target(rng, W, H)
+    ok = np.ones((H, W), dtype=bool)
+    ok[3, 5] = False
+    # projections (u, v) chosen directly: z = 10, x = (u - cx) z / fx
+    uv = np.array([[5.0, 3.0], [5.4, 3.0], [5.6, 3.0], [4.4, 3.0], [5.5, 3.5], [5.75, 3.75],
+                   [8.0, 3.0], [8.4, 3.0], [8.6, 3.0], [-0.1, 2.0], [-0.6, 2.0], [2.0, 6.0],
+                   [0.0, 0.0]])
+    x = np.stack([(uv[:, 0] - 4.0) * 10 / 9.0, (uv[:, 1] - 3.0) * 10 / 9.0, np.full(len(uv), 10.0)], 1)
+    _, _, valid, _, w = terms.associate_bilinear(x, K, W, H, X, n, ok)
+    # usable weight: 0, 0.4, 0.6, 0.6, 0.75, 0.9375; right edge: 1, 0.6, 0.4; left edge: 0.9,
+    # 0.4; bottom row 1; corner 1
+    assert list(valid) == [False, False, True, True, True, True, True, True, False, True, False,
+                           True, True]
+    assert np.abs(w[valid].sum(1) - 1).max() < 1e-15
+    # behind the camera
+    _, _, v2, _, _ = terms.associate_bilinear(np.array([[0.0, 0.0, -5.0]]), K, W, H, X, n, ok)
+    assert not v2[0]
+
+
+def test_bilinear_association_on_a_plane_is_the_exact_distance():
+    """On a planar target every blend of pixel points lies on the plane and every normal is the
+    plane's, so r = n0 . x - c0 exactly (closed form), for any point projecting inside."""
+    H, W = 12, 16
+    K = (16.0, 16.0, 7.5, 5.5)
+    n0 = np.array([0.2, -0.3, -1.0])
+    n0 /= np.linalg.norm(n0)
+    c0 = -100.0
+    u, v = np.meshgrid(np.arange(W), np.arange(H))
+    d = np.stack([(u - 7.5) / 16.0, (v - 5.5) / 16.0, np.ones_like(u, dtype=float)], -1)
+    X, valid = frame.backproject(c0 / (d @ n0), K)
+    nrm, ok = frame.target_normals(X, valid)
+    rng = np.random.default_rng(23)
+    uu = rng.uniform(0.5, W - 1.5, 300)
+    vv = rng.uniform(0.5, H - 1.5, 300)
+    z = rng.uniform(80, 120, 300)
+    x = np.stack([(uu - 7.5) * z / 16.0, (vv - 5.5) * z / 16.0, z], 1)
+    q, nn, vb, _, _ = terms.associate_bilinear(x, K, W, H, X, nrm, ok)
+    inner = (uu >= 1) & (uu < W - 2) & (vv >= 1) & (vv < H - 2)   # all 4 corners off the border
+    assert vb[inner].all() and vb.sum() > inner.sum()
+    r = (nn * (x - q)).sum(1)
+    assert np.abs(r[vb] - (x[vb] @ n0 - c0)).max() < 1e-9
+
+
+def test_bilinear_association_is_continuous_where_rounding_jumps():
+    """Along a line of points crossing many pixel boundaries the largest change of the bilinear
+    residual between neighbouring samples shrinks with the sampling step (a continuous function);
+    the nearest-pixel residual keeps jumps of fixed size at the half-pixel crossings."""
+    sc = make_scene(CONFIGS["frame_80x60_n32"], 1000, f64=True)
+    tgt = solver.prepare_target(sc.frames[0].depth, sc.K)
+    Hh, Ww = tgt.ok.shape
+    fx, fy, cx, cy = sc.K
+    z = tgt.X[30, 40, 2] + 4.0     # off the surface, so that the normal matters
+
+    def jumps(ns):
+        us = np.linspace(30.2, 49.8, ns)
+        x = np.stack([(us - cx) * z / fx, np.full_like(us, (30.3 - cy) * z / fy),
+                      np.full_like(us, z)], 1)
+        q, n, vb, _, _ = terms.associate_bilinear(x, sc.K, Ww, Hh, tgt.X, tgt.n, tgt.ok)
+        assert vb.all()
+        rb = (n * (x - q)).sum(1)
+        pix, vn, _, _ = terms.associate(x, sc.K, Ww, Hh, tgt.ok)
+        assert vn.all()
+        rn = (tgt.n.reshape(-1, 3)[pix] * (x - tgt.X.reshape(-1, 3)[pix])).sum(1)
+        return np.abs(np.diff(rb)).max(), np.abs(np.diff(rn)).max()
+
+    b1, n1 = jumps(2001)
+    b2, n2 = jumps(20001)
+    assert b2 < 0.2 * b1, (b1, b2)
+    assert n2 > 0.5 * n1, (n1, n2)
+    assert n2 > 10 * b2
+
+
+def test_bilinear_at_pixel_centres_equals_nearest():
+    sc = make_scene(CONFIGS["frame_80x60_n32"], 1000, f64=True)
+    tgt = solver.prepare_target(sc.frames[0].depth, sc.K)
+    Hh, Ww = tgt.ok.shape
+    fx, fy, cx, cy = sc.K
+    rng = np.random.default_rng(24)
+    pts = []
+    for _ in range(200):
+        i, j = rng.integers(2, Ww - 3), rng.integers(2, Hh - 3)
+        z = rng.uniform(80, 120)
+        pts.append([(i - cx) * z / fx, (j - cy) * z / fy, z])
+    x = np.array(pts)
+    qb, nb, vb, _, _ = terms.associate_bilinear(x, sc.K, Ww, Hh, tgt.X, tgt.n, tgt.ok)
+    pix, vn, _, _ = terms.associate(x, sc.K, Ww, Hh, tgt.ok)
+    assert np.array_equal(vb, vn)      # at a pixel centre the two validity rules agree
+    both = vb & vn
+    assert both.sum() > 100
+    assert np.abs(qb[both] - tgt.X.reshape(-1, 3)[pix[both]]).max() < 1e-9
+    assert np.abs(nb[both] - tgt.n.reshape(-1, 3)[pix[both]]).max() < 1e-9
+
+
+def test_bilinear_exact_recovery_of_a_rigid_motion_on_a_plane():
+    cfg = Config("rigid_plane", 80, 60, 32, 200, 0, 0.0, 0.0, 0.0, 0.0, 0.0, 3.0, 2.0, 1,
+                 planar=True)
+    sc = make_scene(cfg, 31, f64=True)
+    f = sc.frames[0]
+    prm = solver.Params(assoc="bilinear")
+    tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes, prm)
+    res = solver.solve_frame(tpl, f.depth, f.match_idx, f.match_xyz, f.hyp, prm, iters=10)
+    assert np.abs(res.pos - f.node_truth).max() < 1e-9
+    assert np.abs(rotmat(res.q) - f.motion.Rc).max() < 1e-9
+
+
+# ----------------------------------------------------------------------------- warm-start RANSAC o1
+
+
+def test_warm_o1_at_the_identity_is_the_template():
+    sc, tpl = make_scene(CONFIGS["frame_80x60_n32"], 1000, f64=True), None
+    tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes)
+    f = sc.frames[0]
+    N = tpl.g.shape[0]
+    q = np.tile([1.0, 0, 0, 0], (N, 1))
+    t = np.zeros((N, 3))
+    o1w = solver.ransac_o1(tpl, f.match_idx, q, t, solver.Params(ransac_o1="warm"))
+    o1t = solver.ransac_o1(tpl, f.match_idx, q, t, solver.Params())
+    assert np.array_equal(o1t, tpl.X0[f.match_idx])
+    assert np.abs(o1w - o1t).max() < 1e-12
+
+
+def test_warm_o1_common_rigid_state_leaves_ransac_unchanged():
+    """Every node on one rigid map x -> R x + T: the warped o1 is that map of the template
+    points, and the rectified distances of Eq. 2-4 do not change (the fitted rotation absorbs R,
+    the rectification removes T)."""
+    sc = make_scene(CONFIGS["frame_80x60_n32"], 1000, f64=True)
+    tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes)
+    f = sc.frames[0]
+    rng = np.random.default_rng(25)
+    N = tpl.g.shape[0]
+    qr = qexp_half(rng.normal(size=3) * 0.2)
+    R = rotmat(qr)
+    T = rng.normal(size=3) * 5.0
+    q = np.tile(qr, (N, 1))
+    t = T + tpl.g @ R.T - tpl.g
+    prm = solver.Params(ransac_o1="warm")
+    o1w = solver.ransac_o1(tpl, f.match_idx, q, t, prm)
+    p = tpl.X0[f.match_idx]
+    assert np.abs(o1w - (p @ R.T + T)).max() < 1e-9
+    a = ransac.ransac_1p(p, f.match_xyz, f.hyp, 2.0, 10, 0.5)
+    b = ransac.ransac_1p(o1w, f.match_xyz, f.hyp, 2.0, 10, 0.5)
+    assert np.abs(a["d"] - b["d"]).max() < 1e-8
+    assert np.array_equal(a["kept"], b["kept"])
+    near = np.zeros(len(f.match_idx), dtype=bool)
+    for h in np.flatnonzero(a["kept"]):
+        near |= np.abs(a["d"][h] - 2.0) <= 1e-6
+    assert np.array_equal(a["mask"][~near], b["mask"][~near])
+
+
+def test_warm_o1_recovers_planted_inliers_under_a_nonrigid_state():
+    """Live matches made by a known non-rigid state (inliers exact, outliers >= 20 mm off): with
+    o1 warped by that state the rigid model is exact for every inlier, so the preselection is
+    the planted set; from the template points it is not."""
+    sc = make_scene(CONFIGS["frame_80x60_n32"], 1000, f64=True)
+    tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes)
+    rng = np.random.default_rng(26)
+    N = tpl.g.shape[0]
+    q, t = random_state(rng, N, rot=0.3, trans=3.0)
+    M = 150
+    midx = rng.choice(tpl.pidx, size=M, replace=False)
+    prm = solver.Params(ransac_o1="warm")
+    truth = solver.ransac_o1(tpl, midx, q, t, prm)
+    inl = rng.uniform(size=M) >= 0.3
+    off = rng.normal(size=(M, 3))
+    off *= rng.uniform(20, 40, (M, 1)) / np.linalg.norm(off, axis=1, keepdims=True)
+    o2 = np.where(inl[:, None], truth, truth + off)
+    hyp = rng.choice(M, size=30, replace=False)
+    rs = ransac.ransac_1p(truth, o2, hyp, 2.0, 10, 0.5)
+    assert np.array_equal(rs["mask"], inl)
+    rt = ransac.ransac_1p(tpl.X0[midx], o2, hyp, 2.0, 10, 0.5)
+    assert not np.array_equal(rt["mask"], inl)
