@@ -164,13 +164,27 @@ def gen_frames(n_frames: int, seed: int):
     return make_scene(CONFIGS[WORKLOAD], seed, n_frames=n_frames)
 
 
-def cpu_baseline(sc):
+def oracle_params(args):
+    """The oracle's parameters for the method variant the GPU arm runs."""
+    from oracle import solver
+    return solver.Params(solver=args.solver, assoc=args.assoc, ransac_o1=args.ransac_o1)
+
+
+def variant_params(d, args, prec):
+    """The CUDA path's ds_params for the same variant."""
+    return d.default_params(precision=prec, factor_tc=1 if args.factor_tc else 0,
+                            solver=1 if args.solver == "block_jacobi" else 0,
+                            assoc=1 if args.assoc == "bilinear" else 0,
+                            ransac_o1=1 if args.ransac_o1 == "warm" else 0)
+
+
+def cpu_baseline(sc, prm):
     """The FP64 oracle on the host cores: one whole frame (prep, RANSAC, 10 iterations)."""
     from oracle import solver
-    tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes)
+    tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes, prm)
     f = sc.frames[0]
     t0 = time.perf_counter()
-    solver.solve_frame(tpl, f.depth, f.match_idx, f.match_xyz, f.hyp, iters=ITERS)
+    solver.solve_frame(tpl, f.depth, f.match_idx, f.match_xyz, f.hyp, prm, iters=ITERS)
     dt = time.perf_counter() - t0
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return {"value": 1.0 / dt, "unit": "frames/s", "cores": cores, "kind": "oracle",
@@ -237,7 +251,7 @@ def run_gpu(args):
 
     # ---------------------------------------------------------------- batched mixed precision
     solver_id = 1 if args.solver == "block_jacobi" else 0
-    prm = d.default_params(precision=prec, factor_tc=1 if args.factor_tc else 0, solver=solver_id)
+    prm = variant_params(d, args, prec)
     handles, hstreams = [], []
     for j in range(S):
         sc = scenes[j % n_scenes]
@@ -340,8 +354,7 @@ def run_gpu(args):
     def serve_run(rate_scale, n_frames, seed):
         rng = np.random.default_rng(seed)
         rates = rng.uniform(15.0, 60.0, S) * rate_scale
-        srv = Server(GpuEngine(d.default_params(precision=prec, factor_tc=1 if args.factor_tc else 0,
-                                                solver=solver_id)),
+        srv = Server(GpuEngine(variant_params(d, args, prec)),
                      budget_bytes=int(0.6 * torch.cuda.mem_get_info()[0]))
         for j in range(S):
             sc = scenes[j % n_scenes]
@@ -405,7 +418,7 @@ def run_gpu(args):
 
     result = None
     if rank == 0:
-        cpu = cpu_baseline(scenes[0]) if world == 1 and not args.no_cpu else None
+        cpu = cpu_baseline(scenes[0], oracle_params(args)) if world == 1 and not args.no_cpu else None
         result = {
             "metric": METRIC, "value": round(value, 3), "unit": "frames/s", "n_gpus": world,
             "steps": K, "warmup": W, "ms_per_step": round(float(total_s * 1e3 / K), 4),
@@ -415,7 +428,8 @@ def run_gpu(args):
             "data": "synthetic (seeded heightfield + deformation + camera motion, ray-cast depth)",
             "config": {"workload": WORKLOAD, "template": "320x240", "control_points": N,
                        "matches": M, "gn_iters": ITERS, "precision": args.precision,
-                       "solver": args.solver,
+                       "solver": args.solver, "icp_association": args.assoc,
+                       "ransac_o1": args.ransac_o1,
                        "factor": "tensor cores (tcgen05, 3xTF32)" if args.factor_tc else "FP32 SIMT tile kernel",
                        "streams_per_batch": S, "distinct_scenes": n_scenes, "frames_per_scene": F,
                        "step": f"one frame of each of {S} streams, one batched solve",
@@ -468,24 +482,26 @@ def run_reference(args):
     from oracle import ransac, solver
     sc = gen_frames(1, 1000)
     f = sc.frames[0]
-    prm = solver.Params()
+    prm = oracle_params(args)
     tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes, prm)
-    t0 = time.perf_counter()
-    tgt = solver.prepare_target(f.depth, tpl.K)
-    rs = ransac.ransac_1p(tpl.X0[f.match_idx], f.match_xyz, f.hyp, prm.H, prm.n_reweight,
-                          prm.keep_frac)
-    t_pre = time.perf_counter() - t0
-    orb = (f.match_idx, f.match_xyz.astype(np.float64), rs["mask"], rs["what"])
     N = len(sc.nodes)
     q = np.tile([1.0, 0, 0, 0], (N, 1))
     t = np.zeros((N, 3))
+    t0 = time.perf_counter()
+    tgt = solver.prepare_target(f.depth, tpl.K)
+    rs = ransac.ransac_1p(solver.ransac_o1(tpl, f.match_idx, q, t, prm), f.match_xyz, f.hyp,
+                          prm.H, prm.n_reweight, prm.keep_frac)
+    t_pre = time.perf_counter() - t0
+    orb = (f.match_idx, f.match_xyz.astype(np.float64), rs["mask"], rs["what"])
     w_arap = None
     from oracle import dqb
 
     def it():
         nonlocal q, t, w_arap
         lin, w_arap = solver.linearize(tpl, tgt, q, t, orb, w_arap, prm)
-        delta = solver.cholesky_solve(solver.damp(lin.A, prm), lin.b)
+        Ad = solver.damp(lin.A, prm)
+        delta = (solver.block_jacobi_solve(Ad, lin.b) if prm.solver == "block_jacobi"
+                 else solver.cholesky_solve(Ad, lin.b))
         q, t = dqb.apply_step(q, t, delta)
 
     for _ in range(args.warmup):
@@ -530,6 +546,10 @@ def main():
                     help="dense 6N x 6N Cholesky, or per-node 6 x 6 solves (Section 2)")
     ap.add_argument("--factor-tc", action="store_true", dest="factor_tc",
                     help="FP32 factorisation on the tensor cores (tcgen05, 3xTF32)")
+    ap.add_argument("--assoc", default="nearest", choices=["nearest", "bilinear"],
+                    help="ICP association: nearest pixel or bilinear blend of 4 pixels")
+    ap.add_argument("--ransac-o1", default="template", choices=["template", "warm"],
+                    dest="ransac_o1", help="RANSAC o1: template points or warm-start warped points")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3

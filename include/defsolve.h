@@ -96,6 +96,19 @@ typedef struct {
                              * damped diagonal block (FP64 Cholesky per node), the reading of
                              * Section 2's "update each W_i independently"; no factorisation of
                              * the coupled system and no refinement. Handles of one batch agree.  */
+  int32_t assoc;            /* ICP association (Section 2, projective "rasterization"):
+                             * 0 = nearest pixel, floor(u + 1/2) (default);
+                             * 1 = bilinear: target point and normal blended from the usable
+                             * pixels among the 4 around the projection (weights (1-a)(1-b),
+                             * a(1-b), (1-a)b, ab with a, b the fractional parts, renormalised over
+                             * the usable ones), normal renormalised; valid iff the usable weight
+                             * is >= 1/2. The Jacobian holds the blended point and normal fixed, as
+                             * with the nearest pixel.                                            */
+  int32_t ransac_o1;        /* o1 of Eq. 2 (the template side of each match) in the RANSAC:
+                             * 0 = the template point at the matched pixel (default);
+                             * 1 = warm start: that point warped by the handle's current warps
+                             * (the state the frame's solve starts from), in FP64, so the rigid
+                             * model only has to explain the motion since the previous frame.     */
 } ds_params;
 
 /* Per-solve statistics (filled by ds_solve when its `out` is not NULL). */

@@ -116,6 +116,7 @@ struct ds_ctx {
   double* d_rs_score = nullptr;
   uint32_t* d_rs_mask = nullptr;
   float* d_rs_what = nullptr;
+  double* d_rs_o1 = nullptr;      // warm-start o1 points (M x 3 FP64)
   uint32_t* d_rs_kept = nullptr;
   int* d_rs_counts = nullptr;
   // linear system
@@ -588,7 +589,8 @@ bool valid_params(const ds_params& p) {
          p.sigma_arap_scale > 0 && p.precision >= 0 && p.precision <= 2 && p.refine_steps >= 0 &&
          p.refine_steps <= 3 && p.w_orb >= 0 && p.w_angle >= 0 && p.w_rot >= 0 &&
          p.w_arap0 >= 0 && (p.factor_tc == 0 || p.factor_tc == 1) &&
-         (p.solver == 0 || p.solver == 1);
+         (p.solver == 0 || p.solver == 1) && (p.assoc == 0 || p.assoc == 1) &&
+         (p.ransac_o1 == 0 || p.ransac_o1 == 1);
 }
 
 bool is_host_ptr(const void* p);
@@ -618,6 +620,8 @@ void ds_default_params(ds_params* p) {
   p->use_graph = 1;
   p->factor_tc = 0;
   p->solver = 0;
+  p->assoc = 0;
+  p->ransac_o1 = 0;
 }
 
 const char* ds_status_str(int status) {
@@ -936,6 +940,7 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
     D.lam = h->prm.lambda;
     D.eps = h->prm.eps_damp;
     D.write_ref = (prec != DS_PREC_FP32 && h->prm.refine_steps > 0) ? 1 : 0;
+    D.assoc = h->prm.assoc;
     D.tp = h->d_tp;
     D.tw = h->d_tw;
     D.seg = h->d_seg;
@@ -1047,14 +1052,15 @@ int ds_submit_frame(ds_handle h, const float* depth_hw, const int32_t* match_tmp
   if (M > h->M_cap) {
     cudaStreamSynchronize(s);
     dfree(h->d_midx); dfree(h->d_mxyz); dfree(h->d_rs_scratch); dfree(h->d_rs_hbits);
-    dfree(h->d_rs_hw); dfree(h->d_rs_mask); dfree(h->d_rs_what);
+    dfree(h->d_rs_hw); dfree(h->d_rs_mask); dfree(h->d_rs_what); dfree(h->d_rs_o1);
     int cap = std::max(M, 64);
     int words = (cap + 31) / 32;
     if ((rc = dalloc(&h->d_midx, cap)) || (rc = dalloc(&h->d_mxyz, 3 * (size_t)cap)) ||
         (rc = dalloc(&h->d_rs_scratch, (size_t)7 * cap * DS_MAX_HYP)) ||
         (rc = dalloc(&h->d_rs_hbits, (size_t)words * DS_MAX_HYP)) ||
         (rc = dalloc(&h->d_rs_hw, (size_t)cap * DS_MAX_HYP)) ||
-        (rc = dalloc(&h->d_rs_mask, words)) || (rc = dalloc(&h->d_rs_what, cap))) {
+        (rc = dalloc(&h->d_rs_mask, words)) || (rc = dalloc(&h->d_rs_what, cap)) ||
+        (rc = dalloc(&h->d_rs_o1, 3 * (size_t)cap))) {
       h->M_cap = 0;
       return rc;
     }
@@ -1087,8 +1093,13 @@ int ds_submit_frame(ds_handle h, const float* depth_hw, const int32_t* match_tmp
   launch_check_finite(h->d_mxyz, 3 * M, h->d_flag, s);
   launch_frame_prep(h->d_depth, h->W, h->H, h->K, h->d_tpts, h->d_tnrm, s);
   if (M > 0) {
+    const bool warm = h->prm.ransac_o1 == 1;
+    if (warm)
+      launch_warm_o1(h->d_midx, M, h->d_rank, h->d_tp, h->d_seg, h->d_X64, h->d_g64, h->d_q64,
+                     h->d_t64, h->sigma_b, h->d_rs_o1, s);
     launch_ransac(h->d_depth0, h->W, h->K, h->d_midx, h->d_mxyz, M, h->d_hyp, n_hyp,
-                  h->prm.n_reweight, h->prm.H_mm, h->prm.keep_frac, h->d_rs_scratch,
+                  h->prm.n_reweight, h->prm.H_mm, h->prm.keep_frac,
+                  warm ? h->d_rs_o1 : nullptr, h->d_rs_scratch,
                   h->d_rs_hbits, h->d_rs_hw, h->d_rs_score, h->d_rs_mask, h->d_rs_what,
                   h->d_rs_kept, h->d_rs_counts, s);
   }
@@ -1465,6 +1476,7 @@ int ds_destroy(ds_handle h) {
   dfree(h->d_tnrm); dfree(h->d_midx); dfree(h->d_mxyz); dfree(h->d_hyp);
   dfree(h->d_rs_scratch); dfree(h->d_rs_hbits); dfree(h->d_rs_hw); dfree(h->d_rs_score);
   dfree(h->d_rs_mask); dfree(h->d_rs_what); dfree(h->d_rs_kept); dfree(h->d_rs_counts);
+  dfree(h->d_rs_o1);
   dfree(h->d_acc); dfree(h->d_hist); dfree(h->d_flag);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;

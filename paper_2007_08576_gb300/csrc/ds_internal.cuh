@@ -76,6 +76,7 @@ struct ProbDesc {
   float tukey_c, H_mm, w_orb, w_angle, w_rot, inv2sig2;
   double w_arap0, lam, eps;
   int write_ref;           // the refinement needs the FP32 system (full symmetric) besides the factor
+  int assoc;               // ICP association: 0 nearest pixel, 1 bilinear blend of 4 pixels
   const float4* tp;        // sorted template points (x, y, z, bits(seg << 2 | nearest slot))
   const float4* tw;        // blend weights per sorted point (slot order)
   const int4* seg;         // node quadruple of each segment (ascending ids)
@@ -128,10 +129,17 @@ void launch_check_finite(const float* v, int n, int* flag, cudaStream_t s);
 
 // ransac.cu
 int ransac_smem_bytes(int M);
+// o1w: NULL (o1 = template points back-projected from depth0) or M x 3 FP64 o1 points
 void launch_ransac(const float* depth0, int W, ds_intrinsics K, const int* midx,
                    const float* mxyz, int M, const int* hyp, int n_hyp, int n_reweight, double H,
-                   double keep_frac, double* scratch, uint32_t* hbits, float* hw, double* score,
-                   uint32_t* mask, float* what, uint32_t* kept, int* counts, cudaStream_t s);
+                   double keep_frac, const double* o1w, double* scratch, uint32_t* hbits,
+                   float* hw, double* score, uint32_t* mask, float* what, uint32_t* kept,
+                   int* counts, cudaStream_t s);
+// warm-start o1: the matched template points warped by the current FP64 state (blend weights
+// recomputed in FP64 from the template point, the 4 nodes of its segment and sigma_b)
+void launch_warm_o1(const int* midx, int M, const int* rank, const float4* tp, const int4* seg,
+                    const double* X64, const double* g64, const double* q64, const double* t64,
+                    double sigma_b, double* o1, cudaStream_t s);
 
 // Work tables of a batch (device arrays of (problem, index) pairs) and its shared words.
 struct BatchTabs {

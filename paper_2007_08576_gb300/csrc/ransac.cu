@@ -181,7 +181,8 @@ __device__ __forceinline__ void block_sum(double* v, double* red /* NV * 32 */) 
 __global__ __launch_bounds__(kRansacThreads) void k_ransac_hyp(
     const float* __restrict__ depth0, int W, double fx, double fy, double cx, double cy,
     const int* __restrict__ midx, const float* __restrict__ mxyz, int M,
-    const int* __restrict__ hyp, int n_reweight, double H, int use_smem,
+    const int* __restrict__ hyp, int n_reweight, double H, const double* __restrict__ o1w,
+    int use_smem,
     double* __restrict__ scratch, uint32_t* __restrict__ hbits, float* __restrict__ hw,
     double* __restrict__ score) {
   extern __shared__ double sm[];
@@ -198,13 +199,23 @@ __global__ __launch_bounds__(kRansacThreads) void k_ransac_hyp(
   double* S2z = S + 5 * M;
   double* w = S + 6 * M;
   double r1[3], r2[3];
-  tmpl_point64(depth0, W, fx, fy, cx, cy, midx[k0], r1);
+  // o1 of match k: the template point at its pixel, or the given (warm-start) point
+  auto o1_of = [&](int k, double* o) {
+    if (o1w) {
+      o[0] = o1w[3 * k];
+      o[1] = o1w[3 * k + 1];
+      o[2] = o1w[3 * k + 2];
+    } else {
+      tmpl_point64(depth0, W, fx, fy, cx, cy, midx[k], o);
+    }
+  };
+  o1_of(k0, r1);
   r2[0] = (double)mxyz[3 * k0 + 0];
   r2[1] = (double)mxyz[3 * k0 + 1];
   r2[2] = (double)mxyz[3 * k0 + 2];
   for (int k = threadIdx.x; k < M; k += blockDim.x) {
     double o1[3];
-    tmpl_point64(depth0, W, fx, fy, cx, cy, midx[k], o1);
+    o1_of(k, o1);
     S1x[k] = o1[0] - r1[0];
     S1y[k] = o1[1] - r1[1];
     S1z[k] = o1[2] - r1[2];
@@ -348,8 +359,9 @@ int ransac_smem_bytes(int M) { return 7 * (int)sizeof(double) * M; }
 
 void launch_ransac(const float* depth0, int W, ds_intrinsics K, const int* midx,
                    const float* mxyz, int M, const int* hyp, int n_hyp, int n_reweight, double H,
-                   double keep_frac, double* scratch, uint32_t* hbits, float* hw, double* score,
-                   uint32_t* mask, float* what, uint32_t* kept, int* counts, cudaStream_t s) {
+                   double keep_frac, const double* o1w, double* scratch, uint32_t* hbits,
+                   float* hw, double* score, uint32_t* mask, float* what, uint32_t* kept,
+                   int* counts, cudaStream_t s) {
   if (M <= 0 || n_hyp <= 0) return;
   int sm = ransac_smem_bytes(M);
   int use_smem = sm <= 220 * 1024;
@@ -363,12 +375,96 @@ void launch_ransac(const float* depth0, int W, ds_intrinsics K, const int* midx,
     sm = 0;
   }
   k_ransac_hyp<<<n_hyp, kRansacThreads, sm, s>>>(depth0, W, K.fx, K.fy, K.cx, K.cy, midx, mxyz,
-                                                 M, hyp, n_reweight, H, use_smem, scratch, hbits,
-                                                 hw, score);
+                                                 M, hyp, n_reweight, H, o1w, use_smem, scratch,
+                                                 hbits, hw, score);
   ++g_launches;
   cudaMemsetAsync(counts, 0, sizeof(int), s);  // counts[0] is accumulated by every CTA
   k_ransac_combine<<<(M + 255) / 256, 256, 0, s>>>(hbits, hw, score, n_hyp, M, keep_frac, mask,
                                                      what, kept, counts);
+  ++g_launches;
+}
+
+// ----------------------------------------------------------------------------- warm-start o1
+
+// o1 of match k = its template point p warped by the current state (the reading of Section 2.1
+// where the rigid preselection starts from the previous frame's deformation instead of the
+// template), in FP64 throughout so that the RANSAC decisions stay those of an FP64 pipeline:
+// the point's 4 nodes (its segment), blend weights exp(-|p - g|^2 / (2 sigma_b^2)) normalised
+// to 1, node dual quaternions (q, 1/2 (0, T) (x) q) with T = g + t - R g, each sign-aligned to
+// the nearest node's quaternion, blended and applied: x' = (b_r p b_r* + 2 b_d b_r*) / |b_r|^2.
+// One thread per match.
+__global__ void k_warm_o1(const int* __restrict__ midx, int M, const int* __restrict__ rank,
+                          const float4* __restrict__ tp, const int4* __restrict__ seg,
+                          const double* __restrict__ X64, const double* __restrict__ g64,
+                          const double* __restrict__ q64, const double* __restrict__ t64,
+                          double inv2s2, double* __restrict__ o1) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= M) return;
+  const int j = midx[k];
+  const int sp = rank[j];
+  const int bits = __float_as_int(tp[sp].w);
+  const int4 nn = seg[bits >> 2];
+  const int near = bits & 3;
+  const int ids[4] = {nn.x, nn.y, nn.z, nn.w};
+  const double px = X64[3 * j], py = X64[3 * j + 1], pz = X64[3 * j + 2];
+  const int in = ids[near];
+  const double nw = q64[4 * in], nx = q64[4 * in + 1], ny = q64[4 * in + 2], nz = q64[4 * in + 3];
+  double a[4], asum = 0.0;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int i = ids[s];
+    const double dx = px - g64[3 * i], dy = py - g64[3 * i + 1], dz = pz - g64[3 * i + 2];
+    a[s] = exp(-(dx * dx + dy * dy + dz * dz) * inv2s2);
+    asum += a[s];
+  }
+  double bw = 0, bx = 0, by = 0, bz = 0, cw = 0, cx = 0, cy = 0, cz = 0;  // b_r, b_d
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int i = ids[s];
+    const double qw = q64[4 * i], qx = q64[4 * i + 1], qy = q64[4 * i + 2], qz = q64[4 * i + 3];
+    const double gx = g64[3 * i], gy = g64[3 * i + 1], gz = g64[3 * i + 2];
+    // R g
+    const double Rgx = (1 - 2 * (qy * qy + qz * qz)) * gx + 2 * (qx * qy - qw * qz) * gy +
+                       2 * (qx * qz + qw * qy) * gz;
+    const double Rgy = 2 * (qx * qy + qw * qz) * gx + (1 - 2 * (qx * qx + qz * qz)) * gy +
+                       2 * (qy * qz - qw * qx) * gz;
+    const double Rgz = 2 * (qx * qz - qw * qy) * gx + 2 * (qy * qz + qw * qx) * gy +
+                       (1 - 2 * (qx * qx + qy * qy)) * gz;
+    const double Tx = gx + t64[3 * i] - Rgx, Ty = gy + t64[3 * i + 1] - Rgy,
+                 Tz = gz + t64[3 * i + 2] - Rgz;
+    // d = 1/2 (0, T) (x) q
+    const double dw = 0.5 * (-Tx * qx - Ty * qy - Tz * qz);
+    const double dx = 0.5 * (Tx * qw + Ty * qz - Tz * qy);
+    const double dy = 0.5 * (-Tx * qz + Ty * qw + Tz * qx);
+    const double dz = 0.5 * (Tx * qy - Ty * qx + Tz * qw);
+    const double sg = (qw * nw + qx * nx + qy * ny + qz * nz) >= 0.0 ? 1.0 : -1.0;
+    const double w = sg * (a[s] / asum);
+    bw += w * qw; bx += w * qx; by += w * qy; bz += w * qz;
+    cw += w * dw; cx += w * dx; cy += w * dy; cz += w * dz;
+  }
+  // y = vec(b_r (x) (0, p) (x) b_r*) + 2 vec(b_d (x) b_r*)
+  const double bvp = bx * px + by * py + bz * pz;
+  const double bvv = bx * bx + by * by + bz * bz;
+  const double s2 = bw * bw + bvv;
+  const double k0 = bw * bw - bvv;
+  double yx = k0 * px + 2 * bvp * bx + 2 * bw * (by * pz - bz * py);
+  double yy = k0 * py + 2 * bvp * by + 2 * bw * (bz * px - bx * pz);
+  double yz = k0 * pz + 2 * bvp * bz + 2 * bw * (bx * py - by * px);
+  // vec(b_d (x) b_r*) = bw c_v - cw b_v - c_v x b_v
+  yx += 2 * (bw * cx - cw * bx - (cy * bz - cz * by));
+  yy += 2 * (bw * cy - cw * by - (cz * bx - cx * bz));
+  yz += 2 * (bw * cz - cw * bz - (cx * by - cy * bx));
+  o1[3 * k] = yx / s2;
+  o1[3 * k + 1] = yy / s2;
+  o1[3 * k + 2] = yz / s2;
+}
+
+void launch_warm_o1(const int* midx, int M, const int* rank, const float4* tp, const int4* seg,
+                    const double* X64, const double* g64, const double* q64, const double* t64,
+                    double sigma_b, double* o1, cudaStream_t s) {
+  if (M <= 0) return;
+  k_warm_o1<<<(M + 127) / 128, 128, 0, s>>>(midx, M, rank, tp, seg, X64, g64, q64, t64,
+                                             1.0 / (2.0 * sigma_b * sigma_b), o1);
   ++g_launches;
 }
 
@@ -477,8 +573,8 @@ extern "C" int ds_ransac_noalloc(const float* depth0, int32_t W, int32_t H, ds_i
                                                  midx, hyp, flag);
   const int sm = ransac_smem_bytes(M);  // <= 220 KB for M <= DS_NOALLOC_MAX_MATCHES
   k_ransac_hyp<<<n_hyp, kRansacThreads, sm, s>>>(depth0, W, K.fx, K.fy, K.cx, K.cy, midx,
-                                                 match_xyz, M, hyp, n_reweight, H_mm, 1, nullptr,
-                                                 hbits, hw, score_nh);
+                                                 match_xyz, M, hyp, n_reweight, H_mm, nullptr, 1,
+                                                 nullptr, hbits, hw, score_nh);
   k_ransac_combine<<<(M + 255) / 256, 256, 0, s>>>(hbits, hw, score_nh, n_hyp, M, keep_frac,
                                                      mask_bits, w_M, kept_bits, counts);
   if (cudaGetLastError() != cudaSuccess) return DS_ERR_CUDA;

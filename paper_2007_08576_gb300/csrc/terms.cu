@@ -14,7 +14,9 @@
 // with f = h_r (x) q_k*, e = h_d (x) q_k*.
 //
 // ICP (Section 2): r = n_q . (x' - q) at the pixel the warped point projects to (nearest
-// pixel centre), Tukey IRLS weight (1 - (r/c)^2)^2; only the normal-direction distance counts.
+// pixel centre, or the bilinear blend of the usable pixels among the 4 around the projection,
+// weights renormalised, valid iff their weight is >= 1/2, normal renormalised), Tukey IRLS
+// weight (1 - (r/c)^2)^2; only the normal-direction distance counts.
 // ORB (Section 2.1): r = x'(j_k) - o2_k, weight w_ORB * omega_k, omega_k = RANSAC weight of a
 // preselected match, else clamp(1 - |r| / (5H), 0, 1).
 // ARAP (Section 2.2, Eq. 5-6): all ordered pairs of control points, closed-form J^T W J blocks.
@@ -302,6 +304,7 @@ __global__ __launch_bounds__(kTile, 2) void k_icp(const ProbDesc* const* __restr
   const float4* __restrict__ tgt_nrm = D.tnrm;
   const int W = D.W, H = D.H;
   const float fx = D.fx, fy = D.fy, cx = D.cx, cy = D.cy, c = D.tukey_c;
+  const bool bilinear = D.assoc == 1;
   float* __restrict__ blk = D.blk;
   float* __restrict__ gdata = D.gdata;
   double* __restrict__ acc = D.acc;
@@ -346,34 +349,71 @@ __global__ __launch_bounds__(kTile, 2) void k_icp(const ProbDesc* const* __restr
         Blend B;
         blend_nodes(nd, alp, near, p, B);
         const V x = B.x;
+        bool assoc_ok = false;
+        V tqv = {0.f, 0.f, 0.f}, n = {0.f, 0.f, 0.f};
         if (x.z > 0.f) {
           const float u = fx * x.x / x.z + cx;
           const float v = fy * x.y / x.z + cy;
-          const float pu = floorf(u + 0.5f), pv = floorf(v + 0.5f);
-          if (pu >= 0.f && pu < (float)W && pv >= 0.f && pv < (float)H) {
-            const int pix = (int)pv * W + (int)pu;
-            const float4 tq = tgt_pt[pix];
-            if (tq.w > 0.f) {
-              const float4 n4 = tgt_nrm[pix];
-              const V n = {n4.x, n4.y, n4.z};
-              const float r = dot(n, sub(x, {tq.x, tq.y, tq.z}));
-              nval += 1.f;
-              const float cc6 = c * c * (1.f / 6.f);
-              if (fabsf(r) < c) {
-                const float uu = r / c;
-                const float sig = 1.f - uu * uu;
-                wsum += sig * sig;
-                cost += cc6 * (1.f - sig * sig * sig);
-                float h[8];
-                dir_grad(n, p, B, h);
-#pragma unroll
-                for (int s = 0; s < 4; ++s)
-                  slot_jac(h, nd[s], alp[s] * B.sgn[s] * sig, &Jt[6 * s]);
-                rt = sig * r;
-              } else {
-                cost += cc6;
+          if (!bilinear) {
+            const float pu = floorf(u + 0.5f), pv = floorf(v + 0.5f);
+            if (pu >= 0.f && pu < (float)W && pv >= 0.f && pv < (float)H) {
+              const int pix = (int)pv * W + (int)pu;
+              const float4 tq = tgt_pt[pix];
+              if (tq.w > 0.f) {
+                const float4 n4 = tgt_nrm[pix];
+                tqv = {tq.x, tq.y, tq.z};
+                n = {n4.x, n4.y, n4.z};
+                assoc_ok = true;
               }
             }
+          } else {
+            // the 4 pixels around (u, v), bilinear weights from the fractional parts; corners
+            // outside the image or not usable are dropped and the rest renormalised, valid iff
+            // the usable weight is >= 1/2
+            const float u0 = floorf(u), v0 = floorf(v);
+            const float a = u - u0, b = v - v0;
+            const float wc[4] = {(1.f - a) * (1.f - b), a * (1.f - b), (1.f - a) * b, a * b};
+            float ws = 0.f;
+            V qs = {0.f, 0.f, 0.f}, ns = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int c4 = 0; c4 < 4; ++c4) {
+              const float cu = u0 + (float)(c4 & 1), cv = v0 + (float)(c4 >> 1);
+              if (cu >= 0.f && cu <= (float)(W - 1) && cv >= 0.f && cv <= (float)(H - 1)) {
+                const int pc = (int)cv * W + (int)cu;
+                const float4 Xc = tgt_pt[pc];
+                if (Xc.w > 0.f) {
+                  const float4 Nc = tgt_nrm[pc];
+                  ws += wc[c4];
+                  qs = add(qs, mul({Xc.x, Xc.y, Xc.z}, wc[c4]));
+                  ns = add(ns, mul({Nc.x, Nc.y, Nc.z}, wc[c4]));
+                }
+              }
+            }
+            const float l2 = dot(ns, ns);
+            if (ws >= 0.5f && l2 > 0.f) {
+              tqv = mul(qs, 1.f / ws);
+              n = mul(ns, rsqrtf(l2));
+              assoc_ok = true;
+            }
+          }
+        }
+        if (assoc_ok) {
+          const float r = dot(n, sub(x, tqv));
+          nval += 1.f;
+          const float cc6 = c * c * (1.f / 6.f);
+          if (fabsf(r) < c) {
+            const float uu = r / c;
+            const float sig = 1.f - uu * uu;
+            wsum += sig * sig;
+            cost += cc6 * (1.f - sig * sig * sig);
+            float h[8];
+            dir_grad(n, p, B, h);
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+              slot_jac(h, nd[s], alp[s] * B.sgn[s] * sig, &Jt[6 * s]);
+            rt = sig * r;
+          } else {
+            cost += cc6;
           }
         }
       }

@@ -29,7 +29,9 @@ def oracle_params(p):
                          H=p.H_mm, tukey_c=p.tukey_c_mm, sigma_blend_scale=p.sigma_blend_scale,
                          sigma_arap_scale=p.sigma_arap_scale, lam=p.lambda_, eps=p.eps_damp,
                          keep_frac=p.keep_frac, n_hyp=p.n_hyp, n_reweight=p.n_reweight,
-                         solver="block_jacobi" if getattr(p, "solver", 0) == 1 else "dense")
+                         solver="block_jacobi" if getattr(p, "solver", 0) == 1 else "dense",
+                         assoc="bilinear" if getattr(p, "assoc", 0) == 1 else "nearest",
+                         ransac_o1="warm" if getattr(p, "ransac_o1", 0) == 1 else "template")
 
 
 def gpu_frame(d, sc, frame, params, iters=10, solver_obj=None):

@@ -86,7 +86,17 @@ def test_ransac_mask_bit_exact(d, which, tiny, mid):
     p = d.default_params()
     s = d.Solver(sc.template_depth, sc.K, sc.nodes, p)
     s.submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
-    M = len(fr.match_idx)
+    from oracle import ransac
+    X0, _ = oframe.backproject(sc.template_depth, sc.K)
+    rs = ransac.ransac_1p(X0.reshape(-1, 3)[fr.match_idx], fr.match_xyz, fr.hyp, p.H_mm,
+                          p.n_reweight, p.keep_frac)
+    _check_ransac(d, s, p, rs, len(fr.match_idx))
+    s.close()
+
+
+def _check_ransac(d, s, p, rs, M):
+    """The handle's last RANSAC against the oracle's: kept references and masks bit-exact outside
+    the listed band, scores and weights to rounding."""
     bits = np.zeros((M + 31) // 32, np.uint32)
     d.ds_get_inlier_mask(s.h, bits)
     w = np.zeros(M, np.float32)
@@ -95,17 +105,12 @@ def test_ransac_mask_bit_exact(d, which, tiny, mid):
     d.ds_get_ransac(s.h, w, kept, score)
     gmask = unpack_bits(bits, M)
     gkept = unpack_bits(kept, p.n_hyp)
-    from oracle import ransac
-    X0, _ = oframe.backproject(sc.template_depth, sc.K)
-    rs = ransac.ransac_1p(X0.reshape(-1, 3)[fr.match_idx], fr.match_xyz, fr.hyp, p.H_mm,
-                          p.n_reweight, p.keep_frac)
     listed, amb = ransac_listed(rs, p.H_mm)
     assert np.array_equal(gkept[~amb], rs["kept"][~amb])
     assert np.array_equal(gmask[~listed], rs["mask"][~listed]), np.flatnonzero(gmask != rs["mask"])
     assert np.abs(score - rs["score"]).max() <= 1e-9 * np.abs(rs["score"]).max()
     assert np.abs(w[~listed] - rs["what"][~listed]).max() < 1e-6
     assert listed.sum() <= max(1, M // 100)
-    s.close()
 
 
 # ----------------------------------------------------------------------------- linearisation
@@ -529,3 +534,134 @@ def test_mixed_size_batch():
     sc = scenes[k]
     tpl, res = _oracle(sc, sc.frames[0], oracle_params(p))
     assert np.abs(tpl.g + alone[k] - res.pos).max() <= POS_TOL_MM
+
+
+# ----------------------------------------------------------------------------- association and RANSAC variants
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_bilinear_association_matches_oracle(d, tiny, mid, prec):
+    """ICP with the target point and normal blended from the 4 pixels around the projection."""
+    for sc in (tiny, mid):
+        fr = sc.frames[0]
+        p = d.default_params(precision=prec, assoc=1)
+        s, st, q, t = gpu_frame(d, sc, fr, p)
+        tpl, res = _oracle(sc, fr, oracle_params(p))
+        err = np.abs(tpl.g + t - res.pos).max()
+        assert err <= POS_TOL_MM, err
+        rel = np.abs(np.array(st.cost[:10]) - np.array(res.costs)) / np.array(res.costs)
+        assert rel.max() <= COST_RTOL, rel
+        assert abs(st.w_arap - res.w_arap) <= 1e-6 * res.w_arap
+        s.close()
+
+
+def test_bilinear_normal_equations_match_oracle(d, mid):
+    sc = mid
+    fr = sc.frames[0]
+    p = d.default_params(assoc=1)
+    prm = oracle_params(p)
+    s = d.Solver(sc.template_depth, sc.K, sc.nodes, p)
+    s.submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+    n = 6 * len(sc.nodes)
+    A = np.zeros((n, n))
+    b = np.zeros(n)
+    c3 = np.zeros(3)
+    w_arap = d.ds_linearize(s.h, 0.0, A, b, c3)
+    tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes, prm)
+    tgt = solver.prepare_target(fr.depth, tpl.K)
+    from oracle import ransac
+    rs = ransac.ransac_1p(tpl.X0[fr.match_idx], fr.match_xyz, fr.hyp, prm.H, prm.n_reweight,
+                          prm.keep_frac)
+    orb = (fr.match_idx, fr.match_xyz.astype(np.float64), rs["mask"], rs["what"])
+    N = len(sc.nodes)
+    lin, wo = solver.linearize(tpl, tgt, np.tile([1.0, 0, 0, 0], (N, 1)), np.zeros((N, 3)), orb,
+                               None, prm)
+    assert abs(w_arap - wo) <= 1e-5 * wo
+    scale = np.abs(lin.A).max()
+    assert np.abs(A - lin.A).max() <= 2e-5 * scale, np.abs(A - lin.A).max() / scale
+    assert np.abs(b - lin.b).max() <= 2e-5 * np.abs(lin.b).max()
+    s.close()
+
+
+def test_bilinear_association_full_size_frame(d):
+    sc = scene(CONFIGS["seq_320x240_n256"], 1000)
+    fr = sc.frames[0]
+    p = d.default_params(precision=2, assoc=1)
+    s, st, q, t = gpu_frame(d, sc, fr, p)
+    tpl, res = _oracle(sc, fr, oracle_params(p))
+    assert np.abs(tpl.g + t - res.pos).max() <= POS_TOL_MM
+    rel = np.abs(np.array(st.cost[:10]) - np.array(res.costs)) / np.array(res.costs)
+    assert rel.max() <= COST_RTOL, rel
+    s.close()
+
+
+@pytest.mark.parametrize("which", ["tiny", "full"])
+def test_warm_start_ransac_bit_exact(d, which, tiny):
+    """RANSAC o1 = the template points warped by the handle's current state (FP64 on both
+    sides): the state is set through the ABI, read back in FP64 and given to the oracle."""
+    sc = tiny if which == "tiny" else scene(CONFIGS["seq_320x240_n256"], 1000)
+    fr = sc.frames[0]
+    p = d.default_params(ransac_o1=1)
+    prm = oracle_params(p)
+    s = d.Solver(sc.template_depth, sc.K, sc.nodes, p)
+    rng = np.random.default_rng(5)
+    N = len(sc.nodes)
+    from oracle.quat import qexp_half
+    ax = rng.normal(size=(N, 3))
+    q = qexp_half(ax / np.linalg.norm(ax, axis=1, keepdims=True) * rng.uniform(0, 0.1, (N, 1)))
+    t = rng.normal(scale=1.5, size=(N, 3))
+    d.ds_set_deformation(s.h, q.astype(np.float32), t.astype(np.float32))
+    q64, t64 = s.deformation64()
+    s.submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+    from oracle import ransac
+    tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes, prm)
+    o1 = solver.ransac_o1(tpl, fr.match_idx, q64, t64, prm)
+    assert np.abs(o1 - tpl.X0[fr.match_idx]).max() > 1.0     # the warm start moved the points
+    rs = ransac.ransac_1p(o1, fr.match_xyz, fr.hyp, p.H_mm, p.n_reweight, p.keep_frac)
+    _check_ransac(d, s, p, rs, len(fr.match_idx))
+    s.close()
+
+
+def test_warm_started_sequence_with_both_variants(d):
+    """Three consecutive frames with bilinear association and warm-start RANSAC; each frame of
+    the oracle starts from the state the CUDA path starts from (read back in FP64)."""
+    from synth.scene import Config
+    cfg = Config("seq_120x90_n40", 120, 90, 40, 300, 8, 0.4, 0.5, 0.1, 8.0, 1.0, 0.3, 0.5, 3)
+    sc = scene(cfg, 77, n_frames=3)
+    p = d.default_params(precision=2, assoc=1, ransac_o1=1)
+    prm = oracle_params(p)
+    s = d.Solver(sc.template_depth, sc.K, sc.nodes, p)
+    tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes, prm)
+    for fr in sc.frames:
+        q0, t0 = s.deformation64()
+        s.submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+        st = s.solve(10, stats=True)
+        res = solver.solve_frame(tpl, fr.depth, fr.match_idx, fr.match_xyz, fr.hyp, prm, 10,
+                                 q0=q0, t0=t0)
+        _check_ransac(d, s, p, res.ransac, len(fr.match_idx))
+        _, t = s.deformation64()
+        assert np.abs(tpl.g + t - res.pos).max() <= POS_TOL_MM
+        rel = np.abs(np.array(st.cost[:10]) - np.array(res.costs)) / np.array(res.costs)
+        assert rel.max() <= COST_RTOL, rel
+    s.close()
+
+
+def test_batch_mixes_association_variants(d, tiny, mid):
+    """Handles of one batch may use different associations; each result equals its own solve."""
+    ps = [d.default_params(precision=2, assoc=a) for a in (1, 0, 1)]
+    scs = (tiny, mid, mid)
+    solvers = []
+    for sc, p in zip(scs, ps):
+        s = d.Solver(sc.template_depth, sc.K, sc.nodes, p)
+        fr = sc.frames[0]
+        s.submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+        solvers.append(s)
+    d.ds_solve_batch([s.h for s in solvers], 10)
+    outs = [s.deformation64()[1] for s in solvers]
+    for sc, p, o in zip(scs, ps, outs):
+        s2, st, q, t = gpu_frame(d, sc, sc.frames[0], p)
+        assert np.abs(o - t).max() <= 1e-4
+        s2.close()
+    assert np.abs(outs[1] - outs[2]).max() > 1e-6      # the two associations differ
+    for s in solvers:
+        s.close()
