@@ -148,10 +148,12 @@ def raycast_template(hf: Heightfield, W: int, H: int, iters: int = 40):
     return depth, X0
 
 
-def render_target(hf: Heightfield, mo: Motion, W: int, H: int, iters: int = 12):
+def render_target(hf: Heightfield, mo: Motion, W: int, H: int, iters: int = 12,
+                  return_xy: bool = False):
     """Depth map of the deformed, moved surface: per target pixel, 2D Newton over the surface
     parameters (x, y) until the projected point hits the pixel centre.  Pixels whose iteration
-    does not settle to 1e-7 px, or whose point is behind the camera, get depth 0."""
+    does not settle to 1e-7 px, or whose point is behind the camera, get depth 0.  With
+    return_xy, also the surface parameters (x, y) seen at each pixel."""
     fx, fy, cx, cy = intrinsics_for(W, H)
     up, vp = np.meshgrid(np.arange(W, dtype=np.float64), np.arange(H, dtype=np.float64))
     x = (up - cx) / fx * 100.0
@@ -180,6 +182,8 @@ def render_target(hf: Heightfield, mo: Motion, W: int, H: int, iters: int = 12):
     pu = fx * Y[..., 0] / Y[..., 2] + cx
     pv = fy * Y[..., 1] / Y[..., 2] + cy
     ok = (np.abs(pu - up) < 1e-7) & (np.abs(pv - vp) < 1e-7) & (Y[..., 2] > 1.0)
+    if return_xy:
+        return np.where(ok, Y[..., 2], 0.0), x, y
     return np.where(ok, Y[..., 2], 0.0)
 
 
