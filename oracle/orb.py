@@ -178,10 +178,19 @@ def detect(img, depth, pattern, prm: OrbParams = OrbParams()):
                 n_total=n_total)
 
 
-def hamming(D1, D2):
-    """(n1, n2) Hamming distances between two sets of 256-bit descriptors."""
-    x = np.bitwise_xor(np.asarray(D1, np.uint32)[:, None, :], np.asarray(D2, np.uint32)[None, :, :])
-    return np.unpackbits(x.view(np.uint8), axis=-1).sum(-1).astype(np.int64)
+_POP8 = np.array([bin(i).count("1") for i in range(256)], dtype=np.uint16)
+
+
+def hamming(D1, D2, rows=128):
+    """(n1, n2) Hamming distances between two sets of 256-bit descriptors (popcount of the XOR;
+    evaluated `rows` descriptors of D1 at a time to bound memory)."""
+    D1 = np.ascontiguousarray(D1, np.uint32)
+    D2 = np.ascontiguousarray(D2, np.uint32)
+    out = np.empty((len(D1), len(D2)), dtype=np.int64)
+    for a in range(0, len(D1), rows):
+        x = np.bitwise_xor(D1[a:a + rows, None, :], D2[None, :, :])
+        out[a:a + rows] = _POP8[x.view(np.uint8)].sum(-1)
+    return out
 
 
 def match(Dt, Dl, max_dist):

@@ -15,7 +15,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdefsolve.so")
 
-SOURCES = ["api.cu", "frame.cu", "ransac.cu", "terms.cu", "chol.cu", "solve.cu"]
+SOURCES = ["api.cu", "frame.cu", "ransac.cu", "terms.cu", "chol.cu", "solve.cu", "orb.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]
@@ -30,7 +30,7 @@ def _nvcc() -> str:
 
 def _deps() -> list[str]:
     out = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh"))]
-    out.append(os.path.join(INCLUDE, "defsolve.h"))
+    out += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     return out
 
 

@@ -1,4 +1,4 @@
-"""Python binding of libdefsolve (the C ABI in include/defsolve.h).
+"""Python binding of libdefsolve (the C ABI in include/defsolve.h and include/defsolve_orb.h).
 
 Argument marshalling only: every step of the solve runs in the library's CUDA kernels. Arrays
 may be numpy arrays (host memory) or torch CUDA tensors (device memory); both are passed to the
@@ -21,7 +21,7 @@ DS_PREC_FP64, DS_PREC_FP32, DS_PREC_FP32_REFINE = 0, 1, 2
 DS_MAX_ITERS = 64
 DS_MAX_HYP = 64
 
-# every exported symbol of include/defsolve.h
+# every exported symbol of include/defsolve.h and include/defsolve_orb.h
 EXPORTS = [
     "ds_default_params", "ds_create_template", "ds_set_control_points", "ds_submit_frame",
     "ds_solve", "ds_solve_batch", "ds_batch_create", "ds_batch_solve", "ds_batch_status",
@@ -30,6 +30,9 @@ EXPORTS = [
     "ds_get_blend_table", "ds_get_frame_points", "ds_linearize", "ds_set_tracing",
     "ds_get_phase_times", "ds_get_counters", "ds_ransac_noalloc", "ds_destroy", "ds_status_str",
     "ds_version",
+    "ds_orb_default_params", "ds_orb_create", "ds_orb_detect", "ds_orb_num_keypoints",
+    "ds_orb_get_keypoints", "ds_orb_match", "ds_orb_num_matches", "ds_orb_get_matches",
+    "ds_orb_match_device", "ds_orb_destroy",
 ]
 
 
@@ -50,6 +53,11 @@ class DsParams(ctypes.Structure):
                 ("use_graph", ctypes.c_int32), ("factor_tc", ctypes.c_int32),
                 ("solver", ctypes.c_int32), ("assoc", ctypes.c_int32),
                 ("ransac_o1", ctypes.c_int32)]
+
+
+class DsOrbParams(ctypes.Structure):
+    _fields_ = [("fast_t", ctypes.c_int32), ("border", ctypes.c_int32),
+                ("max_dist", ctypes.c_int32), ("max_kp", ctypes.c_int32)]
 
 
 class DsSolveStats(ctypes.Structure):
@@ -112,6 +120,17 @@ def lib(path: str | None = None):
         "ds_destroy": (i32, [vp]),
         "ds_status_str": (ctypes.c_char_p, [i32]),
         "ds_version": (ctypes.c_char_p, []),
+        "ds_orb_default_params": (None, [ctypes.POINTER(DsOrbParams)]),
+        "ds_orb_create": (i32, [i32, i32, DsIntrinsics, ctypes.POINTER(DsOrbParams), vp, vp,
+                                ctypes.POINTER(vp)]),
+        "ds_orb_detect": (i32, [vp, vp, vp]),
+        "ds_orb_num_keypoints": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "ds_orb_get_keypoints": (i32, [vp, vp, vp, vp, vp]),
+        "ds_orb_match": (i32, [vp, vp]),
+        "ds_orb_num_matches": (i32, [vp, ctypes.POINTER(i32)]),
+        "ds_orb_get_matches": (i32, [vp, vp, vp, vp, vp, vp]),
+        "ds_orb_match_device": (i32, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]),
+        "ds_orb_destroy": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -141,6 +160,7 @@ def _ptr(x, dtype):
     if hasattr(x, "data_ptr"):
         import torch
         tmap = {np.float32: torch.float32, np.float64: torch.float64, np.int32: torch.int32,
+                np.uint8: torch.uint8,
                 np.uint32: torch.uint32 if hasattr(torch, "uint32") else torch.int32}
         if x.dtype != tmap[np.dtype(dtype).type] or not x.is_contiguous():
             raise TypeError(f"expected a contiguous tensor of {np.dtype(dtype)}")
@@ -377,6 +397,111 @@ class Solver:
         if self.h is not None:
             ds_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------------------- ORB features
+
+
+def orb_default_params(**kw) -> DsOrbParams:
+    p = DsOrbParams()
+    lib().ds_orb_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def ds_orb_create(W, H, K, pattern, params: DsOrbParams | None = None, stream=None):
+    o = ctypes.c_void_p()
+    Kc = DsIntrinsics(*[float(k) for k in K])
+    rc = lib().ds_orb_create(int(W), int(H), Kc, ctypes.byref(params) if params is not None else None,
+                             _ptr(pattern, np.float64), stream, ctypes.byref(o))
+    _check("ds_orb_create", rc)
+    return o
+
+
+def ds_orb_detect(o, image_hw, depth_hw=None):
+    _check("ds_orb_detect", lib().ds_orb_detect(o, _ptr(image_hw, np.uint8), _ptr(depth_hw, np.float32)))
+
+
+def ds_orb_num_keypoints(o):
+    n, tot = ctypes.c_int32(), ctypes.c_int32()
+    _check("ds_orb_num_keypoints", lib().ds_orb_num_keypoints(o, ctypes.byref(n), ctypes.byref(tot)))
+    return n.value, tot.value
+
+
+def ds_orb_get_keypoints(o, pix=None, score=None, bin_=None, desc=None):
+    _check("ds_orb_get_keypoints", lib().ds_orb_get_keypoints(
+        o, _ptr(pix, np.int32), _ptr(score, np.int32), _ptr(bin_, np.int32), _ptr(desc, np.uint32)))
+
+
+def ds_orb_match(tmpl, live):
+    _check("ds_orb_match", lib().ds_orb_match(tmpl, live))
+
+
+def ds_orb_num_matches(live) -> int:
+    m = ctypes.c_int32()
+    _check("ds_orb_num_matches", lib().ds_orb_num_matches(live, ctypes.byref(m)))
+    return m.value
+
+
+def ds_orb_get_matches(live, tmpl_kp=None, live_kp=None, dist=None, tmpl_pixel=None, xyz=None):
+    _check("ds_orb_get_matches", lib().ds_orb_get_matches(
+        live, _ptr(tmpl_kp, np.int32), _ptr(live_kp, np.int32), _ptr(dist, np.int32),
+        _ptr(tmpl_pixel, np.int32), _ptr(xyz, np.float32)))
+
+
+def ds_orb_match_device(live):
+    """Device addresses (ints) of the match arrays: template pixel per match, M x 3 points."""
+    a, b = ctypes.c_void_p(), ctypes.c_void_p()
+    _check("ds_orb_match_device", lib().ds_orb_match_device(live, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def ds_orb_destroy(o):
+    _check("ds_orb_destroy", lib().ds_orb_destroy(o))
+
+
+class Orb:
+    """One feature context (template or live side) over W x H images."""
+
+    def __init__(self, W, H, K, pattern, params: DsOrbParams | None = None, stream=None):
+        self.W, self.H = int(W), int(H)
+        self.o = ds_orb_create(W, H, K, np.ascontiguousarray(pattern, np.float64), params, stream)
+
+    def detect(self, image, depth=None):
+        img = np.ascontiguousarray(image, np.uint8) if isinstance(image, np.ndarray) else image
+        dep = (np.ascontiguousarray(depth, np.float32) if isinstance(depth, np.ndarray)
+               else depth)
+        ds_orb_detect(self.o, img, dep)
+
+    def keypoints(self):
+        n, tot = ds_orb_num_keypoints(self.o)
+        pix = np.zeros(n, np.int32)
+        score = np.zeros(n, np.int32)
+        b = np.zeros(n, np.int32)
+        desc = np.zeros((n, 8), np.uint32)
+        ds_orb_get_keypoints(self.o, pix, score, b, desc)
+        return dict(pix=pix, score=score, bin=b, desc=desc, n_total=tot)
+
+    def match_from(self, tmpl: "Orb"):
+        """Matches tmpl's keypoints to this (live) object's; returns the host copies."""
+        ds_orb_match(tmpl.o, self.o)
+        M = ds_orb_num_matches(self.o)
+        out = dict(t=np.zeros(M, np.int32), l=np.zeros(M, np.int32), dist=np.zeros(M, np.int32),
+                   tmpl_pix=np.zeros(M, np.int32), xyz=np.zeros((M, 3), np.float32))
+        ds_orb_get_matches(self.o, out["t"], out["l"], out["dist"], out["tmpl_pix"], out["xyz"])
+        return out
+
+    def close(self):
+        if self.o:
+            ds_orb_destroy(self.o)
+            self.o = None
 
     def __del__(self):
         try:

@@ -1,5 +1,5 @@
 """The C-ABI library builds for sm_103a, loads without a GPU and exports every entry point that
-include/defsolve.h declares (no compute calls here)."""
+include/*.h declares (no compute calls here)."""
 import ctypes
 import os
 import re
@@ -10,7 +10,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_symbols():
-    src = open(os.path.join(ROOT, "include", "defsolve.h")).read()
+    inc = os.path.join(ROOT, "include")
+    src = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc))
+                  if f.endswith(".h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(ds_[a-z0-9_]+)\s*\(", src)))
 
