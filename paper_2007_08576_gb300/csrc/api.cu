@@ -33,6 +33,7 @@ thread_local int64_t g_launches = 0;
 }
 
 static std::atomic<int64_t> g_total_kernels{0};
+void ds::count_kernels(int64_t n) { g_total_kernels += n; }
 
 struct ds_batch_s {
   std::vector<ds_ctx*> hs;

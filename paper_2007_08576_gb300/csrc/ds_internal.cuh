@@ -197,5 +197,8 @@ void launch_sym_unpack(const float* A, int n, double* out, cudaStream_t s);
 // Kernels enqueued by this host thread (stream launches, including those recorded into a graph
 // under capture); the API layer reads differences of it.
 extern thread_local int64_t g_launches;
+// Adds kernels launched outside a handle (feature contexts) to the library-wide count that
+// ds_get_counters(NULL) reports.
+void count_kernels(int64_t n);
 
 }  // namespace ds

@@ -448,6 +448,7 @@ int ds_orb_create(int32_t W, int32_t H, ds_intrinsics K, const ds_orb_params* p,
   cudaMemcpyAsync(d_pat, o->h_pat, sizeof(o->h_pat), cudaMemcpyHostToDevice, o->stream);
   ds::k_pattern_table<<<(ds::kNbins * ds::kTests + 255) / 256, 256, 0, o->stream>>>(d_pat, o->d_tab);
   ++ds::g_launches;
+  ds::count_kernels(1);
   const cudaError_t e = cudaStreamSynchronize(o->stream);
   ds::orb_free(d_pat);
   if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) {
@@ -482,6 +483,7 @@ int ds_orb_detect(ds_orb o, const uint8_t* image_hw, const float* depth_hw) {
   ds::k_describe<<<(o->max_kp + 7) / 8, 256, 0, s>>>(o->d_img, o->d_box, W, o->d_kp_pix, o->d_nkp,
                                                      o->d_tab, o->d_kp_bin, o->d_desc);
   ds::g_launches += 4;
+  ds::count_kernels(4);
   o->detected = true;
   o->have_depth = depth_hw != nullptr;
   cudaEventRecord(o->ev, s);
@@ -541,6 +543,7 @@ int ds_orb_match(ds_orb tmpl, ds_orb live) {
                                      live->K.cy, live->d_m, live->d_m + K8, live->d_m + 2 * K8,
                                      live->d_m + 3 * K8, live->d_m_xyz, live->d_nkp + 2);
   ds::g_launches += 3;
+  ds::count_kernels(3);
   cudaEventRecord(live->ev, s);
   return orb_check(live);
 }
