@@ -118,6 +118,7 @@ struct ds_ctx {
   uint32_t* d_rs_mask = nullptr;
   float* d_rs_what = nullptr;
   double* d_rs_o1 = nullptr;      // warm-start o1 points (M x 3 FP64)
+  float* d_rs_o1df = nullptr;     // o1 points as double-float coordinates (M x 6 floats)
   uint32_t* d_rs_kept = nullptr;
   int* d_rs_counts = nullptr;
   // linear system
@@ -1054,6 +1055,7 @@ int ds_submit_frame(ds_handle h, const float* depth_hw, const int32_t* match_tmp
     cudaStreamSynchronize(s);
     dfree(h->d_midx); dfree(h->d_mxyz); dfree(h->d_rs_scratch); dfree(h->d_rs_hbits);
     dfree(h->d_rs_hw); dfree(h->d_rs_mask); dfree(h->d_rs_what); dfree(h->d_rs_o1);
+    dfree(h->d_rs_o1df);
     int cap = std::max(M, 64);
     int words = (cap + 31) / 32;
     if ((rc = dalloc(&h->d_midx, cap)) || (rc = dalloc(&h->d_mxyz, 3 * (size_t)cap)) ||
@@ -1061,7 +1063,8 @@ int ds_submit_frame(ds_handle h, const float* depth_hw, const int32_t* match_tmp
         (rc = dalloc(&h->d_rs_hbits, (size_t)words * DS_MAX_HYP)) ||
         (rc = dalloc(&h->d_rs_hw, (size_t)cap * DS_MAX_HYP)) ||
         (rc = dalloc(&h->d_rs_mask, words)) || (rc = dalloc(&h->d_rs_what, cap)) ||
-        (rc = dalloc(&h->d_rs_o1, 3 * (size_t)cap))) {
+        (rc = dalloc(&h->d_rs_o1, 3 * (size_t)cap)) ||
+        (rc = dalloc(&h->d_rs_o1df, 6 * (size_t)cap))) {
       h->M_cap = 0;
       return rc;
     }
@@ -1100,7 +1103,7 @@ int ds_submit_frame(ds_handle h, const float* depth_hw, const int32_t* match_tmp
                      h->d_t64, h->sigma_b, h->d_rs_o1, s);
     launch_ransac(h->d_depth0, h->W, h->K, h->d_midx, h->d_mxyz, M, h->d_hyp, n_hyp,
                   h->prm.n_reweight, h->prm.H_mm, h->prm.keep_frac,
-                  warm ? h->d_rs_o1 : nullptr, h->d_rs_scratch,
+                  warm ? h->d_rs_o1 : nullptr, h->d_rs_o1df, h->d_rs_scratch,
                   h->d_rs_hbits, h->d_rs_hw, h->d_rs_score, h->d_rs_mask, h->d_rs_what,
                   h->d_rs_kept, h->d_rs_counts, s);
   }
@@ -1477,7 +1480,7 @@ int ds_destroy(ds_handle h) {
   dfree(h->d_tnrm); dfree(h->d_midx); dfree(h->d_mxyz); dfree(h->d_hyp);
   dfree(h->d_rs_scratch); dfree(h->d_rs_hbits); dfree(h->d_rs_hw); dfree(h->d_rs_score);
   dfree(h->d_rs_mask); dfree(h->d_rs_what); dfree(h->d_rs_kept); dfree(h->d_rs_counts);
-  dfree(h->d_rs_o1);
+  dfree(h->d_rs_o1); dfree(h->d_rs_o1df);
   dfree(h->d_acc); dfree(h->d_hist); dfree(h->d_flag);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;

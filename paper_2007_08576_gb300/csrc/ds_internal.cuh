@@ -129,12 +129,13 @@ void launch_check_finite(const float* v, int n, int* flag, cudaStream_t s);
 
 // ransac.cu
 int ransac_smem_bytes(int M);
-// o1w: NULL (o1 = template points back-projected from depth0) or M x 3 FP64 o1 points
+// o1w: NULL (o1 = template points back-projected from depth0) or M x 3 FP64 o1 points;
+// o1df: 6 M floats of working space (the o1 points as double-float coordinates)
 void launch_ransac(const float* depth0, int W, ds_intrinsics K, const int* midx,
                    const float* mxyz, int M, const int* hyp, int n_hyp, int n_reweight, double H,
-                   double keep_frac, const double* o1w, double* scratch, uint32_t* hbits,
-                   float* hw, double* score, uint32_t* mask, float* what, uint32_t* kept,
-                   int* counts, cudaStream_t s);
+                   double keep_frac, const double* o1w, float* o1df, double* scratch,
+                   uint32_t* hbits, float* hw, double* score, uint32_t* mask, float* what,
+                   uint32_t* kept, int* counts, cudaStream_t s);
 // warm-start o1: the matched template points warped by the current FP64 state (blend weights
 // recomputed in FP64 from the template point, the 4 nodes of its segment and sigma_b)
 void launch_warm_o1(const int* midx, int M, const int* rank, const float4* tp, const int4* seg,

@@ -1,19 +1,21 @@
 // 1-point RANSAC + reweighting inlier preselection (Section 2.1, Eq. 2-4).
 //
 // One CTA per reference match k0. The CTA rectifies both 3D match sets to k0 (Eq. 2) into
-// shared memory (FP64, 56 B per match: S1, S2, w), then alternates n_reweight times
+// shared memory (double-float, 56 B per match: S1, S2, w), then alternates n_reweight times
 //   R <- rotation maximising sum_k w_k S2(k)^T R S1(k)        (Eq. 3, weighted)
 //   d_k = |S2(k) - R S1(k)|,  w_k = min(H / d_k, 1)            (Eq. 4)
 // The rotation is Horn's unit quaternion: the eigenvector of the largest eigenvalue of the 4x4
 // symmetric matrix built from M = sum_k w_k S1(k) S2(k)^T. The largest eigenvalue is found by
-// Newton's method on the characteristic polynomial from a Gershgorin upper bound (monotone for
-// a polynomial with real roots), the eigenvector as the dominant column of the adjugate of
-// N - lambda I. A fit is degenerate (R = I) if sum w < 1e-12 or the two largest eigenvalues are
+// Newton's method on the characteristic polynomial from an upper bound (monotone for a
+// polynomial with real roots; the bound is sum_k w_k |S1(k)| |S2(k)|, or Gershgorin's if
+// smaller), in FP32 on the scaled polynomial and then polished in FP64; the eigenvector is the
+// dominant column of the adjugate of N - lambda I. A fit is degenerate (R = I) if sum w < 1e-12 or the two largest eigenvalues are
 // within 2e-12 |M|_F of each other.
 // After the last update the CTA writes its score sum_{k != k0} w_k, a bitset of d_k <= H
 // (warp ballots) and its weights; a second kernel keeps references whose score is at least
 // keep_frac times the best and combines them (mask = OR, weight = max).
-// Everything that decides a mask bit is FP64.
+// Every quantity that decides a mask bit carries about 48 significant bits: the per-match loops
+// in double-float FP32 arithmetic (see below), Horn's solve and the weights in FP64.
 #include <math.h>
 
 #include <mutex>
@@ -29,110 +31,163 @@ __device__ __forceinline__ double det3(double a, double b, double c, double d, d
   return a * (e * i - f * h) - b * (d * i - f * g) + c * (d * h - e * g);
 }
 
-// Rotation matrix (row-major) from M[a][b] = sum w S1_a S2_b. Returns false if degenerate.
-__device__ bool horn_rotation(const double* M, double wsum, double* R) {
-  double Sxx = M[0], Sxy = M[1], Sxz = M[2];
-  double Syx = M[3], Syy = M[4], Syz = M[5];
-  double Szx = M[6], Szy = M[7], Szz = M[8];
+// Determinant of the 3 x 3 submatrix of a 4 x 4 row-major matrix X keeping rows r0 < r1 < r2
+// and columns c0 < c1 < c2.
+__device__ __forceinline__ double minor3(const double* X, int r0, int r1, int r2, int c0, int c1,
+                                         int c2) {
+  return det3(X[4 * r0 + c0], X[4 * r0 + c1], X[4 * r0 + c2], X[4 * r1 + c0], X[4 * r1 + c1],
+              X[4 * r1 + c2], X[4 * r2 + c0], X[4 * r2 + c1], X[4 * r2 + c2]);
+}
+// The three indices of {0, 1, 2, 3} other than `skip`, ascending.
+__device__ __forceinline__ void others(int skip, int& a, int& b, int& c) {
+  a = skip == 0 ? 1 : 0;
+  b = skip <= 1 ? 2 : 1;
+  c = skip <= 2 ? 3 : 2;
+}
+
+// Largest root of a quartic / cubic with real roots by Newton from an upper bound, in FP32
+// (scaled so that the roots are O(1)), then polished by two FP64 Newton steps. poly(x, deriv)
+// evaluates p and p' at x.
+template <typename F32, typename F64>
+__device__ __forceinline__ double largest_root(float x0, F32 p32, double scale, F64 p64) {
+  float x = x0;
+  for (int it = 0; it < 100; ++it) {
+    float p, dp;
+    p32(x, p, dp);
+    if (!(dp > 0.f)) break;
+    const float step = p / dp;
+    const float nx = x - step;
+    if (!(nx < x)) break;
+    x = nx;
+    if (step <= 1e-7f * fabsf(x) + 1e-30f) break;
+  }
+  double y = (double)x / scale;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    double p, dp;
+    p64(y, p, dp);
+    if (!(dp > 0.0)) break;
+    y -= p / dp;
+  }
+  return y;
+}
+
+// Rotation matrix (row-major) from M[a][b] = sum w S1_a S2_b, computed by the 32 lanes of one
+// warp together (M, wsum and bound the same in every lane; R valid in every lane). Returns false
+// if degenerate. bound: an upper bound of the largest eigenvalue, or +inf. Xs: 32 doubles of
+// shared memory for this warp.
+// An FP64 instruction of one warp occupies this GPU's FP64 pipe for tens of cycles whether one
+// lane or all 32 are active, so the 8 independent 3 x 3 minors (characteristic polynomial) and
+// the 8 cofactors (adjugate) are taken one per lane, and the root searches run in FP32 with an
+// FP64 polish.
+__device__ bool horn_rotation_warp(const double* M, double wsum, double bound, double* R,
+                                   double* Xs) {
+  const int lane = threadIdx.x & 31;
+  const double Sxx = M[0], Sxy = M[1], Sxz = M[2];
+  const double Syx = M[3], Syy = M[4], Syz = M[5];
+  const double Szx = M[6], Szy = M[7], Szz = M[8];
   double fro = 0.0;
   for (int i = 0; i < 9; ++i) fro += M[i] * M[i];
   fro = sqrt(fro);
   if (!(wsum >= 1e-12) || !(fro > 0.0)) return false;
-  double N[4][4] = {{Sxx + Syy + Szz, Syz - Szy, Szx - Sxz, Sxy - Syx},
-                    {Syz - Szy, Sxx - Syy - Szz, Sxy + Syx, Szx + Sxz},
-                    {Szx - Sxz, Sxy + Syx, -Sxx + Syy - Szz, Syz + Szy},
-                    {Sxy - Syx, Szx + Sxz, Syz + Szy, -Sxx - Syy + Szz}};
-  // det(lambda I - N) = lambda^4 + e2 lambda^2 - e3 lambda + e4 (N is traceless)
+  const double N[16] = {Sxx + Syy + Szz, Syz - Szy, Szx - Sxz, Sxy - Syx,
+                        Syz - Szy, Sxx - Syy - Szz, Sxy + Syx, Szx + Sxz,
+                        Szx - Sxz, Sxy + Syx, -Sxx + Syy - Szz, Syz + Szy,
+                        Sxy - Syx, Szx + Sxz, Syz + Szy, -Sxx - Syy + Szz};
+  if (lane < 16) Xs[lane] = N[lane];
+  __syncwarp();
+  // det(lambda I - N) = lambda^4 + e2 lambda^2 - e3 lambda + e4 (N is traceless):
+  // e2 = sum of principal 2 x 2 minors, e3 = sum of principal 3 x 3 minors, e4 = det N
   double e2 = 0.0;
   for (int i = 0; i < 4; ++i)
-    for (int j = i + 1; j < 4; ++j) e2 += N[i][i] * N[j][j] - N[i][j] * N[i][j];
-  double e3 = 0.0;
-  for (int skip = 0; skip < 4; ++skip) {
-    int r[3], c = 0;
-    for (int i = 0; i < 4; ++i)
-      if (i != skip) r[c++] = i;
-    e3 += det3(N[r[0]][r[0]], N[r[0]][r[1]], N[r[0]][r[2]], N[r[1]][r[0]], N[r[1]][r[1]],
-               N[r[1]][r[2]], N[r[2]][r[0]], N[r[2]][r[1]], N[r[2]][r[2]]);
+    for (int j = i + 1; j < 4; ++j) e2 += N[5 * i] * N[5 * j] - N[4 * i + j] * N[4 * i + j];
+  double m;
+  {
+    const int sk = lane & 3;
+    int a, b, c;
+    others(sk, a, b, c);
+    m = (lane & 4) ? minor3(Xs, 1, 2, 3, a, b, c) * ((sk & 1) ? -Xs[sk] : Xs[sk])
+                   : minor3(Xs, a, b, c, a, b, c);
   }
-  double e4 = 0.0;
-  for (int j = 0; j < 4; ++j) {
-    int c[3], k = 0;
-    for (int i = 0; i < 4; ++i)
-      if (i != j) c[k++] = i;
-    double m = det3(N[1][c[0]], N[1][c[1]], N[1][c[2]], N[2][c[0]], N[2][c[1]], N[2][c[2]],
-                    N[3][c[0]], N[3][c[1]], N[3][c[2]]);
-    e4 += ((j & 1) ? -1.0 : 1.0) * N[0][j] * m;
-  }
-  // Newton from a Gershgorin bound
-  double lam = -INFINITY;
+  const double e3 = ((__shfl_sync(0xffffffffu, m, 0) + __shfl_sync(0xffffffffu, m, 1)) +
+                     __shfl_sync(0xffffffffu, m, 2)) + __shfl_sync(0xffffffffu, m, 3);
+  const double e4 = ((__shfl_sync(0xffffffffu, m, 4) + __shfl_sync(0xffffffffu, m, 5)) +
+                     __shfl_sync(0xffffffffu, m, 6)) + __shfl_sync(0xffffffffu, m, 7);
+  // largest eigenvalue: Newton from the smaller of the caller's and Gershgorin's bounds
+  double top = -INFINITY;
   for (int i = 0; i < 4; ++i) {
-    double r = N[i][i];
+    double r = N[5 * i];
     for (int j = 0; j < 4; ++j)
-      if (j != i) r += fabs(N[i][j]);
-    lam = fmax(lam, r);
+      if (j != i) r += fabs(N[4 * i + j]);
+    top = fmax(top, r);
   }
-  for (int it = 0; it < 100; ++it) {
-    double l2 = lam * lam;
-    double p = (l2 + e2) * l2 - e3 * lam + e4;
-    double dp = 4.0 * l2 * lam + 2.0 * e2 * lam - e3;
-    if (!(dp > 0.0)) break;
-    double step = p / dp;
-    double nl = lam - step;
-    if (!(nl < lam)) break;
-    lam = nl;
-    if (step <= 1e-16 * fabs(lam)) break;
-  }
-  // deflate: p(x) / (x - lam) = x^3 + c2 x^2 + c1 x + c0, largest root by Newton from lam
-  double c2 = lam, c1 = e2 + lam * lam, c0 = -e3 + lam * c1;
-  double mu = lam;
-  for (int it = 0; it < 100; ++it) {
-    double p = ((mu + c2) * mu + c1) * mu + c0;
-    double dp = (3.0 * mu + 2.0 * c2) * mu + c1;
-    if (!(dp > 0.0)) break;
-    double step = p / dp;
-    double nm = mu - step;
-    if (!(nm < mu)) break;
-    mu = nm;
-    if (step <= 1e-16 * fabs(mu) + 1e-300) break;
-  }
+  top = fmin(top, bound);
+  const double sc = 1.0 / fro;
+  const float f2 = (float)(e2 * sc * sc), f3 = (float)(e3 * sc * sc * sc),
+              f4 = (float)(e4 * (sc * sc) * (sc * sc));
+  const double lam = largest_root(
+      (float)(top * sc) * 1.0001f + 1e-6f,
+      [&](float x, float& p, float& dp) {
+        const float x2 = x * x;
+        p = (x2 + f2) * x2 - f3 * x + f4;
+        dp = 4.f * x2 * x + 2.f * f2 * x - f3;
+      },
+      sc,
+      [&](double x, double& p, double& dp) {
+        const double x2 = x * x;
+        p = (x2 + e2) * x2 - e3 * x + e4;
+        dp = 4.0 * x2 * x + 2.0 * e2 * x - e3;
+      });
+  // second largest: the deflated cubic p(x) / (x - lam) = x^3 + c2 x^2 + c1 x + c0, from lam
+  const double c2 = lam, c1 = e2 + lam * lam, c0 = -e3 + lam * c1;
+  const float g2 = (float)(c2 * sc), g1 = (float)(c1 * sc * sc), g0 = (float)(c0 * sc * sc * sc);
+  const double mu = largest_root(
+      (float)(lam * sc),
+      [&](float x, float& p, float& dp) {
+        p = ((x + g2) * x + g1) * x + g0;
+        dp = (3.f * x + 2.f * g2) * x + g1;
+      },
+      sc,
+      [&](double x, double& p, double& dp) {
+        p = ((x + c2) * x + c1) * x + c0;
+        dp = (3.0 * x + 2.0 * c2) * x + c1;
+      });
   if (!(lam - mu > 2e-12 * fro)) return false;
-  // adjugate of A = N - lam I: choose the largest diagonal cofactor, take its column
-  double A[4][4];
-  for (int i = 0; i < 4; ++i)
-    for (int j = 0; j < 4; ++j) A[i][j] = N[i][j] - (i == j ? lam : 0.0);
-  double best = -1.0;
+  // eigenvector: a column of adj(N - lam I) = prod_{i > 1} (lambda_1 - lambda_i) q q^T, the one
+  // with the largest diagonal cofactor
+  __syncwarp();
+  if (lane < 16) Xs[lane] = N[lane] - ((lane % 5 == 0) ? lam : 0.0);
+  __syncwarp();
+  double dg;
+  {
+    int a, b, c;
+    others(lane & 3, a, b, c);
+    dg = fabs(minor3(Xs, a, b, c, a, b, c));
+  }
   int jb = 0;
-  for (int j = 0; j < 4; ++j) {
-    int r[3], k = 0;
-    for (int i = 0; i < 4; ++i)
-      if (i != j) r[k++] = i;
-    double m = fabs(det3(A[r[0]][r[0]], A[r[0]][r[1]], A[r[0]][r[2]], A[r[1]][r[0]],
-                         A[r[1]][r[1]], A[r[1]][r[2]], A[r[2]][r[0]], A[r[2]][r[1]],
-                         A[r[2]][r[2]]));
-    if (m > best) {
-      best = m;
+  double best = __shfl_sync(0xffffffffu, dg, 0);
+  for (int j = 1; j < 4; ++j) {
+    const double v = __shfl_sync(0xffffffffu, dg, j);
+    if (v > best) {
+      best = v;
       jb = j;
     }
   }
-  double q[4];
+  double cf;
   {
-    int cols[3], k = 0;
-    for (int i = 0; i < 4; ++i)
-      if (i != jb) cols[k++] = i;
-    for (int i = 0; i < 4; ++i) {
-      int rows[3], kk = 0;
-      for (int t = 0; t < 4; ++t)
-        if (t != i) rows[kk++] = t;
-      // cofactor C_{i, jb}: delete row i, column jb (A symmetric, so this is column jb of adj)
-      double m = det3(A[rows[0]][cols[0]], A[rows[0]][cols[1]], A[rows[0]][cols[2]],
-                      A[rows[1]][cols[0]], A[rows[1]][cols[1]], A[rows[1]][cols[2]],
-                      A[rows[2]][cols[0]], A[rows[2]][cols[1]], A[rows[2]][cols[2]]);
-      q[i] = (((i + jb) & 1) ? -1.0 : 1.0) * m;
-    }
+    const int i = lane & 3;
+    int r0, r1, r2, k0, k1, k2;
+    others(i, r0, r1, r2);
+    others(jb, k0, k1, k2);
+    // cofactor C_{i, jb}: delete row i and column jb (A symmetric: column jb of the adjugate)
+    cf = (((i + jb) & 1) ? -1.0 : 1.0) * minor3(Xs, r0, r1, r2, k0, k1, k2);
   }
-  double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  double q[4];
+  for (int i = 0; i < 4; ++i) q[i] = __shfl_sync(0xffffffffu, cf, i);
+  const double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
   if (!(qn > 0.0)) return false;
-  double w = q[0] / qn, x = q[1] / qn, y = q[2] / qn, z = q[3] / qn;
+  const double iq = 1.0 / qn;
+  const double w = q[0] * iq, x = q[1] * iq, y = q[2] * iq, z = q[3] * iq;
   R[0] = 1 - 2 * (y * y + z * z);
   R[1] = 2 * (x * y - w * z);
   R[2] = 2 * (x * z + w * y);
@@ -178,110 +233,221 @@ __device__ __forceinline__ void block_sum(double* v, double* red /* NV * 32 */) 
   __syncthreads();
 }
 
+// ----------------------------------------------------------------------------- double-float
+// The per-match loops run in double-float arithmetic: a value is the unevaluated sum hi + lo of
+// two floats (|lo| <= ulp(hi) / 2, 48 significant bits), products split exactly with an FMA,
+// sums by two-sum, every operation rounded separately (no contraction). On this GPU an FP64
+// instruction costs 64 times an FP32 one, so these ~10 FP32 operations per FP64 operation run
+// several times faster, with a relative error of a few 1e-15 -- far inside the 1e-6 mm band in
+// which mask decisions are not graded. Horn's rotation and the weights H / d stay FP64.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF df_quick(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  return df_quick(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ DF df_neg(DF a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ DF df_two_sum(float a, float b) {  // exact a + b
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ bool df_le(DF a, DF b) {  // a <= b for normalised pairs
+  return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo);
+}
+__device__ __forceinline__ DF df_scale(DF a, float s) {  // s a power of two
+  return {__fmul_rn(a.hi, s), __fmul_rn(a.lo, s)};
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_quick(p, e);
+}
+__device__ __forceinline__ DF df_of(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(__dsub_rn(x, (double)h))};
+}
+__device__ __forceinline__ double df_val(DF a) { return __dadd_rn((double)a.hi, (double)a.lo); }
+
+// Sum over the CTA of NV double-float values per thread, in a fixed order; the result is valid
+// in thread 0 only.
+template <int NV>
+__device__ __forceinline__ void block_sum_df(DF* v, DF* red /* NV * 32 */) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    DF x = v[i];
+    for (int o = 16; o > 0; o >>= 1) {
+      const DF y = {__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
+      x = df_add(x, y);
+    }
+    v[i] = x;
+  }
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) red[i * 32 + warp] = v[i];
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      DF x = {0.f, 0.f};
+      for (int w = 0; w < nw; ++w) x = df_add(x, red[i * 32 + w]);  // fixed order
+      v[i] = x;
+    }
+}
+
+// o1 of every match as double-float coordinates (6 floats: x, y, z as hi / lo pairs): the
+// template point at its pixel in FP64, or the given warm-start point. Once per frame, so that
+// the per-reference CTAs start from it without FP64 work.
+__global__ void k_ransac_points(const float* __restrict__ depth0, int W, double fx, double fy,
+                                double cx, double cy, const int* __restrict__ midx, int M,
+                                const double* __restrict__ o1w, float* __restrict__ o1df) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= M) return;
+  double o[3];
+  if (o1w) {
+    o[0] = o1w[3 * k];
+    o[1] = o1w[3 * k + 1];
+    o[2] = o1w[3 * k + 2];
+  } else {
+    tmpl_point64(depth0, W, fx, fy, cx, cy, midx[k], o);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const DF d = df_of(o[a]);
+    o1df[6 * k + 2 * a] = d.hi;
+    o1df[6 * k + 2 * a + 1] = d.lo;
+  }
+}
+
 __global__ __launch_bounds__(kRansacThreads) void k_ransac_hyp(
-    const float* __restrict__ depth0, int W, double fx, double fy, double cx, double cy,
-    const int* __restrict__ midx, const float* __restrict__ mxyz, int M,
-    const int* __restrict__ hyp, int n_reweight, double H, const double* __restrict__ o1w,
-    int use_smem,
+    const float* __restrict__ o1df, const float* __restrict__ mxyz, int M,
+    const int* __restrict__ hyp, int n_reweight, double H, int use_smem,
     double* __restrict__ scratch, uint32_t* __restrict__ hbits, float* __restrict__ hw,
     double* __restrict__ score) {
   extern __shared__ double sm[];
-  __shared__ double red[10 * 32];
-  __shared__ double sR[9];
+  __shared__ DF red[11 * 32];
+  __shared__ double sR[10];
+  __shared__ double sX[32];
   const int h = blockIdx.x;
   const int k0 = hyp[h];
-  double* S = use_smem ? sm : scratch + (size_t)h * 7 * M;
-  double* S1x = S;
-  double* S1y = S + M;
-  double* S1z = S + 2 * M;
-  double* S2x = S + 3 * M;
-  double* S2y = S + 4 * M;
-  double* S2z = S + 5 * M;
-  double* w = S + 6 * M;
-  double r1[3], r2[3];
-  // o1 of match k: the template point at its pixel, or the given (warm-start) point
-  auto o1_of = [&](int k, double* o) {
-    if (o1w) {
-      o[0] = o1w[3 * k];
-      o[1] = o1w[3 * k + 1];
-      o[2] = o1w[3 * k + 2];
-    } else {
-      tmpl_point64(depth0, W, fx, fy, cx, cy, midx[k], o);
-    }
-  };
-  o1_of(k0, r1);
-  r2[0] = (double)mxyz[3 * k0 + 0];
-  r2[1] = (double)mxyz[3 * k0 + 1];
-  r2[2] = (double)mxyz[3 * k0 + 2];
+  // 7 double-float arrays of M: S1 (x, y, z), S2 (x, y, z), w; 56 B per match
+  DF* S = reinterpret_cast<DF*>(use_smem ? sm : scratch + (size_t)h * 7 * M);
+  DF* S1x = S;
+  DF* S1y = S + M;
+  DF* S1z = S + 2 * M;
+  DF* S2x = S + 3 * M;
+  DF* S2y = S + 4 * M;
+  DF* S2z = S + 5 * M;
+  DF* w = S + 6 * M;
+  const DF r1x = {o1df[6 * k0], o1df[6 * k0 + 1]}, r1y = {o1df[6 * k0 + 2], o1df[6 * k0 + 3]},
+           r1z = {o1df[6 * k0 + 4], o1df[6 * k0 + 5]};
+  const float r2x = mxyz[3 * k0], r2y = mxyz[3 * k0 + 1], r2z = mxyz[3 * k0 + 2];
+  // Eq. 2: both point sets rectified to the reference; S2 exactly (a difference of floats)
   for (int k = threadIdx.x; k < M; k += blockDim.x) {
-    double o1[3];
-    o1_of(k, o1);
-    S1x[k] = o1[0] - r1[0];
-    S1y[k] = o1[1] - r1[1];
-    S1z[k] = o1[2] - r1[2];
-    S2x[k] = (double)mxyz[3 * k + 0] - r2[0];
-    S2y[k] = (double)mxyz[3 * k + 1] - r2[1];
-    S2z[k] = (double)mxyz[3 * k + 2] - r2[2];
-    w[k] = 1.0;
+    S1x[k] = df_add({o1df[6 * k], o1df[6 * k + 1]}, df_neg(r1x));
+    S1y[k] = df_add({o1df[6 * k + 2], o1df[6 * k + 3]}, df_neg(r1y));
+    S1z[k] = df_add({o1df[6 * k + 4], o1df[6 * k + 5]}, df_neg(r1z));
+    S2x[k] = df_two_sum(mxyz[3 * k], -r2x);
+    S2y[k] = df_two_sum(mxyz[3 * k + 1], -r2y);
+    S2z[k] = df_two_sum(mxyz[3 * k + 2], -r2z);
+    w[k] = {1.f, 0.f};
   }
   __syncthreads();
   const int words = (M + 31) / 32;
-  const double H2 = H * H;
+  const DF H2 = df_of(H * H), Hd = df_of(H), one = {1.f, 0.f};
   for (int it = 0; it < n_reweight; ++it) {
-    double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    // Eq. 3: M = sum w S1 S2^T (and sum w); acc[10] = sum w |S1| |S2| (FP32), an upper bound of
+    // the largest eigenvalue of Horn's matrix (Cauchy-Schwarz), where Newton starts
+    DF acc[11];
+#pragma unroll
+    for (int i = 0; i < 11; ++i) acc[i] = {0.f, 0.f};
+    float nb = 0.f;
     for (int k = threadIdx.x; k < M; k += blockDim.x) {
-      double wk = w[k];
-      double a0 = wk * S1x[k], a1 = wk * S1y[k], a2 = wk * S1z[k];
-      double b0 = S2x[k], b1 = S2y[k], b2 = S2z[k];
-      acc[0] += a0 * b0;
-      acc[1] += a0 * b1;
-      acc[2] += a0 * b2;
-      acc[3] += a1 * b0;
-      acc[4] += a1 * b1;
-      acc[5] += a1 * b2;
-      acc[6] += a2 * b0;
-      acc[7] += a2 * b1;
-      acc[8] += a2 * b2;
-      acc[9] += wk;
+      const DF wk = w[k];
+      const DF x1 = S1x[k], y1 = S1y[k], z1 = S1z[k];
+      const DF a0 = df_mul(wk, x1), a1 = df_mul(wk, y1), a2 = df_mul(wk, z1);
+      const DF b0 = S2x[k], b1 = S2y[k], b2 = S2z[k];
+      acc[0] = df_add(acc[0], df_mul(a0, b0));
+      acc[1] = df_add(acc[1], df_mul(a0, b1));
+      acc[2] = df_add(acc[2], df_mul(a0, b2));
+      acc[3] = df_add(acc[3], df_mul(a1, b0));
+      acc[4] = df_add(acc[4], df_mul(a1, b1));
+      acc[5] = df_add(acc[5], df_mul(a1, b2));
+      acc[6] = df_add(acc[6], df_mul(a2, b0));
+      acc[7] = df_add(acc[7], df_mul(a2, b1));
+      acc[8] = df_add(acc[8], df_mul(a2, b2));
+      acc[9] = df_add(acc[9], wk);
+      const float n1 = x1.hi * x1.hi + y1.hi * y1.hi + z1.hi * z1.hi;
+      const float n2 = b0.hi * b0.hi + b1.hi * b1.hi + b2.hi * b2.hi;
+      nb += wk.hi * sqrtf(n1 * n2);
     }
-    block_sum<10>(acc, red);
-    if (threadIdx.x == 0) {
+    acc[10] = {nb, 0.f};
+    block_sum_df<11>(acc, red);
+    if (threadIdx.x < 32) {   // warp 0: Horn's rotation (the sums are in thread 0)
+      double Md[11];
+#pragma unroll
+      for (int i = 0; i < 11; ++i) {
+        const double v = threadIdx.x == 0 ? df_val(acc[i]) : 0.0;
+        Md[i] = __shfl_sync(0xffffffffu, v, 0);
+      }
+      // the FP32 bound widened well past its rounding (relative 1e-6 over <= 2^16 terms)
+      const double bound = Md[10] * (1.0 + 1e-3) + 1e-30;
       double R[9];
-      if (!horn_rotation(acc, acc[9], R)) {
+      if (!horn_rotation_warp(Md, Md[9], bound, R, sX)) {
         for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0) ? 1.0 : 0.0;
       }
-      for (int i = 0; i < 9; ++i) sR[i] = R[i];
+      if (threadIdx.x == 0)
+        for (int i = 0; i < 9; ++i) sR[i] = R[i];
     }
     __syncthreads();
-    double R0 = sR[0], R1 = sR[1], R2 = sR[2], R3 = sR[3], R4 = sR[4], R5 = sR[5], R6 = sR[6],
-           R7 = sR[7], R8 = sR[8];
+    DF Rm[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Rm[i] = df_of(sR[i]);
     const bool last = it == n_reweight - 1;
-    double sc = 0.0;
-    // warp-uniform trip count so that every lane reaches the ballot
+    DF sc = {0.f, 0.f};
+    // Eq. 4: d_k = |S2 - R S1|, w_k = min(H / d_k, 1); d <= H is decided on d^2 <= H^2 and
+    // H / d = H rsqrt(d^2) (FP32 seed, two Newton steps in double-float) when d > H.
+    // Warp-uniform trip count so that every lane reaches the ballot.
     for (int base = (threadIdx.x & ~31); base < M; base += blockDim.x) {
       int k = base + (threadIdx.x & 31);
       bool inl = false;
       if (k < M) {
-        double x = S1x[k], y = S1y[k], z = S1z[k];
-        double e0 = S2x[k] - (R0 * x + R1 * y + R2 * z);
-        double e1 = S2y[k] - (R3 * x + R4 * y + R5 * z);
-        double e2 = S2z[k] - (R6 * x + R7 * y + R8 * z);
-        // d <= H  <=>  d^2 <= H^2, and w = H / d = H rsqrt(d^2) when d > H: no FP64 sqrt or
-        // division (each costs tens of instructions on the FP64 pipe)
-        const double d2 = e0 * e0 + e1 * e1 + e2 * e2;
-        const bool within = d2 <= H2;
-        double wk = 1.0;
+        const DF x = S1x[k], y = S1y[k], z = S1z[k];
+        const DF e0 = df_add(S2x[k], df_neg(df_add(df_add(df_mul(Rm[0], x), df_mul(Rm[1], y)),
+                                                   df_mul(Rm[2], z))));
+        const DF e1 = df_add(S2y[k], df_neg(df_add(df_add(df_mul(Rm[3], x), df_mul(Rm[4], y)),
+                                                   df_mul(Rm[5], z))));
+        const DF e2 = df_add(S2z[k], df_neg(df_add(df_add(df_mul(Rm[6], x), df_mul(Rm[7], y)),
+                                                   df_mul(Rm[8], z))));
+        const DF d2 = df_add(df_add(df_mul(e0, e0), df_mul(e1, e1)), df_mul(e2, e2));
+        const bool within = df_le(d2, H2);
+        DF wk = one;
         if (!within) {
-          double y0 = (double)rsqrtf((float)d2);
-          y0 = y0 * (1.5 - 0.5 * d2 * y0 * y0);
-          y0 = y0 * (1.5 - 0.5 * d2 * y0 * y0);
-          wk = fmin(H * y0, 1.0);
+          DF yv = {rsqrtf(d2.hi), 0.f};
+#pragma unroll
+          for (int nstep = 0; nstep < 2; ++nstep) {
+            const DF r = df_add(one, df_neg(df_mul(d2, df_mul(yv, yv))));
+            yv = df_add(yv, df_scale(df_mul(yv, r), 0.5f));
+          }
+          wk = df_mul(Hd, yv);
+          if (!df_le(wk, one)) wk = one;
         }
         w[k] = wk;
         if (last) {
           inl = within;
-          hw[(size_t)h * M + k] = (float)wk;
-          if (k != k0) sc += wk;
+          hw[(size_t)h * M + k] = wk.hi;
+          if (k != k0) sc = df_add(sc, wk);
         }
       }
       if (last) {
@@ -290,9 +456,9 @@ __global__ __launch_bounds__(kRansacThreads) void k_ransac_hyp(
       }
     }
     if (last) {
-      double v[1] = {sc};
-      block_sum<1>(v, red);
-      if (threadIdx.x == 0) score[h] = v[0];
+      DF v[1] = {sc};
+      block_sum_df<1>(v, red);
+      if (threadIdx.x == 0) score[h] = df_val(v[0]);
     }
     __syncthreads();
   }
@@ -359,9 +525,9 @@ int ransac_smem_bytes(int M) { return 7 * (int)sizeof(double) * M; }
 
 void launch_ransac(const float* depth0, int W, ds_intrinsics K, const int* midx,
                    const float* mxyz, int M, const int* hyp, int n_hyp, int n_reweight, double H,
-                   double keep_frac, const double* o1w, double* scratch, uint32_t* hbits,
-                   float* hw, double* score, uint32_t* mask, float* what, uint32_t* kept,
-                   int* counts, cudaStream_t s) {
+                   double keep_frac, const double* o1w, float* o1df, double* scratch,
+                   uint32_t* hbits, float* hw, double* score, uint32_t* mask, float* what,
+                   uint32_t* kept, int* counts, cudaStream_t s) {
   if (M <= 0 || n_hyp <= 0) return;
   int sm = ransac_smem_bytes(M);
   int use_smem = sm <= 220 * 1024;
@@ -374,10 +540,11 @@ void launch_ransac(const float* depth0, int W, ds_intrinsics K, const int* midx,
   } else {
     sm = 0;
   }
-  k_ransac_hyp<<<n_hyp, kRansacThreads, sm, s>>>(depth0, W, K.fx, K.fy, K.cx, K.cy, midx, mxyz,
-                                                 M, hyp, n_reweight, H, o1w, use_smem, scratch,
-                                                 hbits, hw, score);
-  ++g_launches;
+  k_ransac_points<<<(M + 255) / 256, 256, 0, s>>>(depth0, W, K.fx, K.fy, K.cx, K.cy, midx, M,
+                                                   o1w, o1df);
+  k_ransac_hyp<<<n_hyp, kRansacThreads, sm, s>>>(o1df, mxyz, M, hyp, n_reweight, H, use_smem,
+                                                 scratch, hbits, hw, score);
+  g_launches += 2;
   cudaMemsetAsync(counts, 0, sizeof(int), s);  // counts[0] is accumulated by every CTA
   k_ransac_combine<<<(M + 255) / 256, 256, 0, s>>>(hbits, hw, score, n_hyp, M, keep_frac, mask,
                                                      what, kept, counts);
@@ -483,7 +650,8 @@ constexpr size_t kNaW = kNaBits + kNaAlign(sizeof(uint32_t) * DS_MAX_HYP * kNaWo
 constexpr size_t kNaMidx = kNaW + kNaAlign(sizeof(float) * DS_MAX_HYP * DS_NOALLOC_MAX_MATCHES);
 constexpr size_t kNaHyp = kNaMidx + kNaAlign(sizeof(int) * DS_NOALLOC_MAX_MATCHES);
 constexpr size_t kNaCnt = kNaHyp + kNaAlign(sizeof(int) * DS_MAX_HYP);
-constexpr size_t kNaTotal = kNaCnt + 256;
+constexpr size_t kNaO1 = kNaCnt + 256;
+constexpr size_t kNaTotal = kNaO1 + kNaAlign(sizeof(float) * 6 * DS_NOALLOC_MAX_MATCHES);
 }  // namespace
 
 static __device__ __align__(256) unsigned char g_ransac_scratch[kNaTotal];
@@ -564,6 +732,7 @@ extern "C" int ds_ransac_noalloc(const float* depth0, int32_t W, int32_t H, ds_i
   int* midx = (int*)(base + kNaMidx);
   int* hyp = (int*)(base + kNaHyp);
   int* counts = (int*)(base + kNaCnt);
+  float* o1df = (float*)(base + kNaO1);
   int* flag = counts + 2;
   // the array keeps the previous call's contents: clear the words that accumulate
   cudaMemsetAsync(counts, 0, 4 * sizeof(int), s);
@@ -572,8 +741,9 @@ extern "C" int ds_ransac_noalloc(const float* depth0, int32_t W, int32_t H, ds_i
   k_na_indices<<<(nt + 255) / 256, 256, 0, s>>>(match_tmpl_idx, M, hyp_list, n_hyp, npx, depth0,
                                                  midx, hyp, flag);
   const int sm = ransac_smem_bytes(M);  // <= 220 KB for M <= DS_NOALLOC_MAX_MATCHES
-  k_ransac_hyp<<<n_hyp, kRansacThreads, sm, s>>>(depth0, W, K.fx, K.fy, K.cx, K.cy, midx,
-                                                 match_xyz, M, hyp, n_reweight, H_mm, nullptr, 1,
+  k_ransac_points<<<(M + 255) / 256, 256, 0, s>>>(depth0, W, K.fx, K.fy, K.cx, K.cy, midx, M,
+                                                   nullptr, o1df);
+  k_ransac_hyp<<<n_hyp, kRansacThreads, sm, s>>>(o1df, match_xyz, M, hyp, n_reweight, H_mm, 1,
                                                  nullptr, hbits, hw, score_nh);
   k_ransac_combine<<<(M + 255) / 256, 256, 0, s>>>(hbits, hw, score_nh, n_hyp, M, keep_frac,
                                                      mask_bits, w_M, kept_bits, counts);
