@@ -45,29 +45,54 @@ __device__ __forceinline__ void others(int skip, int& a, int& b, int& c) {
   c = skip <= 2 ? 3 : 2;
 }
 
-// Largest root of a quartic / cubic with real roots by Newton from an upper bound, in FP32
-// (scaled so that the roots are O(1)), then polished by two FP64 Newton steps. poly(x, deriv)
-// evaluates p and p' at x.
+// Largest root of a quartic / cubic with real roots, O(1) after the caller's scaling: Newton
+// from an upper bound x0 in FP32 (monotone from above), then FP64 Newton, monotone from above
+// again, from the FP32 root raised by a bound of its error (a few FP32 roundings of the
+// polynomial's terms, mag, divided by p'): ~2 FP64 steps for a well separated root, more when
+// p' is small (a nearly repeated root). The FP64 step divides by p' through an FP32 reciprocal
+// refined once (relative error ~1e-14, which only scales the step). p32(x, p, dp, mag) and
+// p64(x, p, dp) evaluate p, p' (and the sum of the terms' magnitudes) at x.
+// 1 / sqrt(v) to FP32 accuracy for any positive finite double (exponent split off first).
+__device__ __forceinline__ double rsqrt_seed(double v) {
+  int e;
+  double m = frexp(v, &e);
+  if (e & 1) {
+    m *= 2.0;
+    e -= 1;
+  }
+  return (double)rsqrtf((float)m) * ldexp(1.0, -e / 2);
+}
 template <typename F32, typename F64>
-__device__ __forceinline__ double largest_root(float x0, F32 p32, double scale, F64 p64) {
-  float x = x0;
+__device__ __forceinline__ double largest_root(double x0, F32 p32, F64 p64, double decided = -1.0) {
+  float x = __double2float_ru(x0), dpf = 0.f, mag = 0.f;   // rounded up: still an upper bound
   for (int it = 0; it < 100; ++it) {
-    float p, dp;
-    p32(x, p, dp);
-    if (!(dp > 0.f)) break;
-    const float step = p / dp;
+    float p;
+    p32(x, p, dpf, mag);
+    if (!(dpf > 0.f)) break;
+    const float step = p / dpf;
     const float nx = x - step;
     if (!(nx < x)) break;
     x = nx;
     if (step <= 1e-7f * fabsf(x) + 1e-30f) break;
   }
-  double y = (double)x / scale;
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
+  double y = (dpf > 0.f) ? (double)x + (1e-6 * (double)mag / (double)dpf + 1e-7 * fabs((double)x))
+                         : x0;
+  y = fmin(y, x0);
+  // the caller only needs to know whether the root lies below `decided`: an upper bound below
+  // it settles that without the FP64 steps
+  if (y < decided) return y;
+  for (int it = 0; it < 100; ++it) {
     double p, dp;
     p64(y, p, dp);
     if (!(dp > 0.0)) break;
-    y -= p / dp;
+    double r = (double)__frcp_rn((float)dp);
+    r = r * (2.0 - dp * r);
+    const double step = p * r;
+    const double ny = y - step;
+    if (!(ny < y)) break;
+    y = ny;
+    // quadratic convergence: after a step this small the error is ~1e-18 relative
+    if (step <= 1e-9 * fabs(y) + 1e-300) break;
   }
   return y;
 }
@@ -86,10 +111,15 @@ __device__ bool horn_rotation_warp(const double* M, double wsum, double bound, d
   const double Sxx = M[0], Sxy = M[1], Sxz = M[2];
   const double Syx = M[3], Syy = M[4], Syz = M[5];
   const double Szx = M[6], Szy = M[7], Szz = M[8];
-  double fro = 0.0;
-  for (int i = 0; i < 9; ++i) fro += M[i] * M[i];
-  fro = sqrt(fro);
-  if (!(wsum >= 1e-12) || !(fro > 0.0)) return false;
+  double f2sum = 0.0;
+  for (int i = 0; i < 9; ++i) f2sum += M[i] * M[i];
+  if (!(wsum >= 1e-12) || !(f2sum > 0.0) || !(f2sum < INFINITY)) return false;
+  // |M|_F to FP32 accuracy (it only sets the degeneracy threshold) and a power of two sc within
+  // a factor 2 of 1 / |M|_F that scales the roots to O(1) exactly
+  const double fro = f2sum * rsqrt_seed(f2sum);
+  int ex;
+  frexp(f2sum, &ex);
+  const double sc = ldexp(1.0, -(ex / 2)), inv_sc = ldexp(1.0, ex / 2);
   const double N[16] = {Sxx + Syy + Szz, Syz - Szy, Szx - Sxz, Sxy - Syx,
                         Syz - Szy, Sxx - Syy - Szz, Sxy + Syx, Szx + Sxz,
                         Szx - Sxz, Sxy + Syx, -Sxx + Syy - Szz, Syz + Szy,
@@ -98,60 +128,72 @@ __device__ bool horn_rotation_warp(const double* M, double wsum, double bound, d
   __syncwarp();
   // det(lambda I - N) = lambda^4 + e2 lambda^2 - e3 lambda + e4 (N is traceless):
   // e2 = sum of principal 2 x 2 minors, e3 = sum of principal 3 x 3 minors, e4 = det N
-  double e2 = 0.0;
-  for (int i = 0; i < 4; ++i)
-    for (int j = i + 1; j < 4; ++j) e2 += N[5 * i] * N[5 * j] - N[4 * i + j] * N[4 * i + j];
-  double m;
+  // lanes 0-3: principal 3 x 3 minors (e3); lanes 4-7: row-0 cofactors times N_0j (e4);
+  // lanes 8-13: principal 2 x 2 minors (e2)
+  double m, m2;
   {
     const int sk = lane & 3;
     int a, b, c;
     others(sk, a, b, c);
-    m = (lane & 4) ? minor3(Xs, 1, 2, 3, a, b, c) * ((sk & 1) ? -Xs[sk] : Xs[sk])
-                   : minor3(Xs, a, b, c, a, b, c);
+    const bool row0 = (lane & 4) != 0;
+    const double f = row0 ? ((sk & 1) ? -Xs[sk] : Xs[sk]) : 1.0;
+    m = minor3(Xs, row0 ? 1 : a, row0 ? 2 : b, row0 ? 3 : c, a, b, c) * f;
+    const int pr = lane >= 8 && lane < 14 ? lane - 8 : 0;     // pair (i, j), i < j
+    const int i = pr < 3 ? 0 : pr < 5 ? 1 : 2;
+    const int j = pr < 3 ? pr + 1 : pr < 5 ? pr - 1 : 3;
+    m2 = Xs[5 * i] * Xs[5 * j] - Xs[4 * i + j] * Xs[4 * i + j];
   }
+  double e2 = 0.0;
+  for (int l = 8; l < 14; ++l) e2 += __shfl_sync(0xffffffffu, m2, l);
   const double e3 = ((__shfl_sync(0xffffffffu, m, 0) + __shfl_sync(0xffffffffu, m, 1)) +
                      __shfl_sync(0xffffffffu, m, 2)) + __shfl_sync(0xffffffffu, m, 3);
   const double e4 = ((__shfl_sync(0xffffffffu, m, 4) + __shfl_sync(0xffffffffu, m, 5)) +
                      __shfl_sync(0xffffffffu, m, 6)) + __shfl_sync(0xffffffffu, m, 7);
-  // largest eigenvalue: Newton from the smaller of the caller's and Gershgorin's bounds
-  double top = -INFINITY;
-  for (int i = 0; i < 4; ++i) {
-    double r = N[5 * i];
-    for (int j = 0; j < 4; ++j)
-      if (j != i) r += fabs(N[4 * i + j]);
-    top = fmax(top, r);
+  // largest eigenvalue: Newton from the caller's bound, or Gershgorin's without one
+  double top = bound;
+  if (!(top < INFINITY)) {
+    top = -INFINITY;
+    for (int i = 0; i < 4; ++i) {
+      double r = N[5 * i];
+      for (int j = 0; j < 4; ++j)
+        if (j != i) r += fabs(N[4 * i + j]);
+      top = fmax(top, r);
+    }
   }
-  top = fmin(top, bound);
-  const double sc = 1.0 / fro;
-  const float f2 = (float)(e2 * sc * sc), f3 = (float)(e3 * sc * sc * sc),
-              f4 = (float)(e4 * (sc * sc) * (sc * sc));
-  const double lam = largest_root(
-      (float)(top * sc) * 1.0001f + 1e-6f,
-      [&](float x, float& p, float& dp) {
+  // scaled quartic x^4 + E2 x^2 - E3 x + E4 (x = lambda sc, exact power-of-two scalings)
+  const double E2 = e2 * (sc * sc), E3 = e3 * (sc * sc * sc), E4 = e4 * ((sc * sc) * (sc * sc));
+  const float f2 = (float)E2, f3 = (float)E3, f4 = (float)E4;
+  const double ls = largest_root(
+      top * sc,
+      [&](float x, float& p, float& dp, float& mag) {
         const float x2 = x * x;
         p = (x2 + f2) * x2 - f3 * x + f4;
         dp = 4.f * x2 * x + 2.f * f2 * x - f3;
+        mag = x2 * x2 + fabsf(f2) * x2 + fabsf(f3 * x) + fabsf(f4);
       },
-      sc,
       [&](double x, double& p, double& dp) {
         const double x2 = x * x;
-        p = (x2 + e2) * x2 - e3 * x + e4;
-        dp = 4.0 * x2 * x + 2.0 * e2 * x - e3;
+        p = (x2 + E2) * x2 - E3 * x + E4;
+        dp = 4.0 * x2 * x + 2.0 * E2 * x - E3;
       });
-  // second largest: the deflated cubic p(x) / (x - lam) = x^3 + c2 x^2 + c1 x + c0, from lam
-  const double c2 = lam, c1 = e2 + lam * lam, c0 = -e3 + lam * c1;
-  const float g2 = (float)(c2 * sc), g1 = (float)(c1 * sc * sc), g0 = (float)(c0 * sc * sc * sc);
-  const double mu = largest_root(
-      (float)(lam * sc),
-      [&](float x, float& p, float& dp) {
+  // second largest: the deflated cubic p(x) / (x - ls) = x^3 + C2 x^2 + C1 x + C0, from ls
+  const double C2 = ls, C1 = E2 + ls * ls, C0 = -E3 + ls * C1;
+  const float g2 = (float)C2, g1 = (float)C1, g0 = (float)C0;
+  const double ms = largest_root(
+      ls,
+      [&](float x, float& p, float& dp, float& mag) {
         p = ((x + g2) * x + g1) * x + g0;
         dp = (3.f * x + 2.f * g2) * x + g1;
+        mag = fabsf(x * x * x) + fabsf(g2 * x * x) + fabsf(g1 * x) + fabsf(g0);
       },
-      sc,
       [&](double x, double& p, double& dp) {
-        p = ((x + c2) * x + c1) * x + c0;
-        dp = (3.0 * x + 2.0 * c2) * x + c1;
-      });
+        p = ((x + C2) * x + C1) * x + C0;
+        dp = (3.0 * x + 2.0 * C2) * x + C1;
+      },
+      ls - 4e-12 * fro * sc);
+  // degenerate iff the two largest eigenvalues are within 2e-12 |M|_F (an upper bound of the
+  // second one below ls - 4e-12 |M|_F sc already decides it, with a factor 2 to spare)
+  const double lam = ls * inv_sc, mu = ms * inv_sc;
   if (!(lam - mu > 2e-12 * fro)) return false;
   // eigenvector: a column of adj(N - lam I) = prod_{i > 1} (lambda_1 - lambda_i) q q^T, the one
   // with the largest diagonal cofactor
@@ -184,9 +226,11 @@ __device__ bool horn_rotation_warp(const double* M, double wsum, double bound, d
   }
   double q[4];
   for (int i = 0; i < 4; ++i) q[i] = __shfl_sync(0xffffffffu, cf, i);
-  const double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-  if (!(qn > 0.0)) return false;
-  const double iq = 1.0 / qn;
+  const double qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+  if (!(qq > 0.0) || !(qq < INFINITY)) return false;
+  // 1 / |q|: FP32-accurate seed, one FP64 Newton step (relative error ~1e-14)
+  double iq = rsqrt_seed(qq);
+  iq = iq * (1.5 - 0.5 * qq * iq * iq);
   const double w = q[0] * iq, x = q[1] * iq, y = q[2] * iq, z = q[3] * iq;
   R[0] = 1 - 2 * (y * y + z * z);
   R[1] = 2 * (x * y - w * z);
@@ -278,8 +322,8 @@ __device__ __forceinline__ DF df_of(double x) {
 }
 __device__ __forceinline__ double df_val(DF a) { return __dadd_rn((double)a.hi, (double)a.lo); }
 
-// Sum over the CTA of NV double-float values per thread, in a fixed order; the result is valid
-// in thread 0 only.
+// Sum over the CTA of NV double-float values per thread, in a fixed order (NV <= 32); the result
+// is valid in warp 0 only.
 template <int NV>
 __device__ __forceinline__ void block_sum_df(DF* v, DF* red /* NV * 32 */) {
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -297,13 +341,14 @@ __device__ __forceinline__ void block_sum_df(DF* v, DF* red /* NV * 32 */) {
 #pragma unroll
     for (int i = 0; i < NV; ++i) red[i * 32 + warp] = v[i];
   __syncthreads();
-  if (threadIdx.x == 0)
+  if (warp == 0) {   // lane i sums value i over the warps (fixed order), then every lane gathers
+    DF x = {0.f, 0.f};
+    if (lane < NV)
+      for (int w = 0; w < nw; ++w) x = df_add(x, red[lane * 32 + w]);
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      DF x = {0.f, 0.f};
-      for (int w = 0; w < nw; ++w) x = df_add(x, red[i * 32 + w]);  // fixed order
-      v[i] = x;
-    }
+    for (int i = 0; i < NV; ++i)
+      v[i] = {__shfl_sync(0xffffffffu, x.hi, i), __shfl_sync(0xffffffffu, x.lo, i)};
+  }
 }
 
 // o1 of every match as double-float coordinates (6 floats: x, y, z as hi / lo pairs): the
