@@ -357,6 +357,10 @@ def run_gpu(args):
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             th = time.perf_counter()
+            # each step's frame work starts at its start event, after the previous solve: the
+            # library lets submissions overlap the previous solve (two frame slots per handle),
+            # but here that measured slower (the RANSAC CTAs take shared memory the persistent
+            # factorisation needs)
             step(W + i, e0)
             host_ms.append((time.perf_counter() - th) * 1e3)
             e1.record(stream)

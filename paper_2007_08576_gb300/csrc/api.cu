@@ -57,6 +57,7 @@ struct ds_batch_s {
   int last_iters = 0;
   cudaEvent_t ev_done = nullptr;
   std::vector<cudaEvent_t> ev_in;
+  std::vector<const ProbDesc*> h_descs;  // the descriptor table as last uploaded
   // side stream of the linearisation: the ORB pass runs beside the ICP pass (both only add
   // into the block table and the gradient)
   cudaStream_t side = nullptr, side2 = nullptr;
@@ -101,26 +102,33 @@ struct ds_ctx {
   int* d_rowbp = nullptr;
   std::vector<int4> h_nid_pix;
   std::vector<float4> h_alpha_pix;
-  // frame
+  // frame. Two slots of everything a solve reads from a submitted frame (live points and
+  // normals, matches, RANSAC results, the descriptor): a frame is prepared in one slot while a
+  // solve may still read the other, so submissions overlap the previous frame's solve.
   float* d_depth = nullptr;
-  float4* d_tpts = nullptr;
+  float4* d_tpts = nullptr;   // 2 slots of W H
   float4* d_tnrm = nullptr;
-  int M = 0, M_cap = 0;
-  int* d_midx = nullptr;
-  float* d_mxyz = nullptr;
+  int M = 0, M_cap = 0;       // M of the latest frame; slot capacity
+  int Ms[2] = {0, 0};         // M per slot
+  int fs = 0;                 // slot of the latest submitted frame
+  int solved_fs = 0;          // slot the last solve read
+  cudaEvent_t ev_slot_free[2] = {nullptr, nullptr};  // after the last solve that read a slot
+  bool slot_pending[2] = {false, false};
+  int* d_midx = nullptr;      // 2 slots of M_cap
+  float* d_mxyz = nullptr;    // 2 slots of 3 M_cap
   int* d_hyp = nullptr;
   bool have_frame = false;
   // ransac
   double* d_rs_scratch = nullptr;
   uint32_t* d_rs_hbits = nullptr;
   float* d_rs_hw = nullptr;
-  double* d_rs_score = nullptr;
-  uint32_t* d_rs_mask = nullptr;
-  float* d_rs_what = nullptr;
+  double* d_rs_score = nullptr;   // 2 slots of DS_MAX_HYP
+  uint32_t* d_rs_mask = nullptr;  // 2 slots of ceil(M_cap / 32)
+  float* d_rs_what = nullptr;     // 2 slots of M_cap
   double* d_rs_o1 = nullptr;      // warm-start o1 points (M x 3 FP64)
   float* d_rs_o1df = nullptr;     // o1 points as double-float coordinates (M x 6 floats)
-  uint32_t* d_rs_kept = nullptr;
-  int* d_rs_counts = nullptr;
+  uint32_t* d_rs_kept = nullptr;  // 2 slots of 2
+  int* d_rs_counts = nullptr;     // 2 slots of 4
   // linear system
   float* d_A32 = nullptr;     // FP32 system (factor in DS_PREC_FP32, reference otherwise)
   double* d_A64 = nullptr;    // FP64 factor (DS_PREC_FP64)
@@ -145,7 +153,7 @@ struct ds_ctx {
   double* d_acc = nullptr;
   double* d_hist = nullptr;   // DS_MAX_ITERS x 6
   int* d_flag = nullptr;
-  // descriptor
+  // descriptor: hdesc holds the fields common to both slots; d_desc[s] is slot s's
   ProbDesc hdesc{};
   ProbDesc* d_desc = nullptr;
   // the batch of one used by ds_solve
@@ -192,9 +200,41 @@ int copy_in(void* dst, const void* src, size_t bytes, cudaStream_t s) {
   return DS_OK;
 }
 
-void push_desc(ds_ctx* h) {
-  // staged from pageable memory: the copy has left hdesc when the call returns
-  cudaMemcpyAsync(h->d_desc, &h->hdesc, sizeof(ProbDesc), cudaMemcpyHostToDevice, h->stream);
+size_t npx_of(const ds_ctx* h) { return (size_t)h->W * h->H; }
+float4* slot_tpts(ds_ctx* h, int s) { return h->d_tpts + s * npx_of(h); }
+float4* slot_tnrm(ds_ctx* h, int s) { return h->d_tnrm + s * npx_of(h); }
+int* slot_midx(ds_ctx* h, int s) { return h->d_midx ? h->d_midx + (size_t)s * h->M_cap : nullptr; }
+float* slot_mxyz(ds_ctx* h, int s) {
+  return h->d_mxyz ? h->d_mxyz + (size_t)s * 3 * h->M_cap : nullptr;
+}
+uint32_t* slot_mask(ds_ctx* h, int s) {
+  return h->d_rs_mask ? h->d_rs_mask + (size_t)s * ((h->M_cap + 31) / 32) : nullptr;
+}
+float* slot_what(ds_ctx* h, int s) {
+  return h->d_rs_what ? h->d_rs_what + (size_t)s * h->M_cap : nullptr;
+}
+double* slot_score(ds_ctx* h, int s) { return h->d_rs_score + s * DS_MAX_HYP; }
+uint32_t* slot_kept(ds_ctx* h, int s) { return h->d_rs_kept + 2 * s; }
+int* slot_counts(ds_ctx* h, int s) { return h->d_rs_counts + 4 * s; }
+
+// Slot s's descriptor: the common fields with the slot's frame buffers.
+void push_desc(ds_ctx* h, int s) {
+  ProbDesc D = h->hdesc;
+  D.M = h->Ms[s];
+  D.tpts = slot_tpts(h, s);
+  D.tnrm = slot_tnrm(h, s);
+  D.midx = slot_midx(h, s);
+  D.mxyz = slot_mxyz(h, s);
+  D.mask = slot_mask(h, s);
+  D.what = slot_what(h, s);
+  // staged from pageable memory: the copy has left D when the call returns
+  cudaMemcpyAsync(h->d_desc + s, &D, sizeof(ProbDesc), cudaMemcpyHostToDevice, h->stream);
+}
+
+// Orders the handle's stream after its last solve (a batch on another stream).
+void wait_solved(ds_ctx* h) {
+  if (h->slot_pending[h->solved_fs])
+    cudaStreamWaitEvent(h->stream, h->ev_slot_free[h->solved_fs], 0);
 }
 
 void destroy_batch(ds_batch_s* b);
@@ -234,6 +274,7 @@ int batch_words_status(ds_batch_s* b) {
 }
 
 int sync_status(ds_ctx* h) {
+  wait_solved(h);
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     h->error = true;
@@ -372,7 +413,7 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   std::vector<const ProbDesc*> descs(n);
   for (int p = 0; p < n; ++p) {
     ds_ctx* h = hs[p];
-    descs[p] = h->d_desc;
+    descs[p] = h->d_desc + h->fs;
     for (int t = 0; t * kSegPerCta * kSegPerWarp < h->S; ++t) icp.push_back(make_int2(p, t));
     for (int i = 0; i < h->N; ++i) rows.push_back(make_int2(p, i));
     for (int c = 0; c * 128 < h->N; ++c) nodes.push_back(make_int2(p, c));
@@ -396,6 +437,7 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   for (auto* v : {&icp, &rows, &nodes, &vec, &res, &chol})
     all.insert(all.end(), v->begin(), v->end());
   cudaMemcpy(b->d_descs, descs.data(), sizeof(void*) * n, cudaMemcpyHostToDevice);
+  b->h_descs = descs;
   cudaMemcpy(b->d_tab, all.data(), sizeof(int2) * ntab, cudaMemcpyHostToDevice);
   cudaMemset(b->d_words, 0, sizeof(int) * 8);
   BatchTabs& T = b->tabs;
@@ -512,16 +554,34 @@ void enqueue_solve(ds_batch_s* b, int iters) {
   trace(b, iters - 1, 3);
 }
 
+void update_desc_table(ds_batch_s* b) {
+  bool changed = false;
+  for (size_t p = 0; p < b->hs.size(); ++p) {
+    const ProbDesc* d = b->hs[p]->d_desc + b->hs[p]->fs;
+    if (b->h_descs[p] != d) {
+      b->h_descs[p] = d;
+      changed = true;
+    }
+  }
+  if (changed)
+    cudaMemcpyAsync(b->d_descs, b->h_descs.data(), sizeof(void*) * b->hs.size(),
+                    cudaMemcpyHostToDevice, b->stream);
+}
+
 int run_batch(ds_batch_s* b, int iters, bool use_graph) {
   cudaStream_t s = b->stream;
-  // order after each handle's pending work (submit_frame on its own stream)
+  // order after each handle's last solve (possibly in another batch) and its pending work
+  // (submit_frame on its own stream)
   for (size_t p = 0; p < b->hs.size(); ++p) {
     ds_ctx* h = b->hs[p];
+    if (h->slot_pending[h->solved_fs]) cudaStreamWaitEvent(s, h->ev_slot_free[h->solved_fs], 0);
     if (h->stream != s) {
       cudaEventRecord(b->ev_in[p], h->stream);
       cudaStreamWaitEvent(s, b->ev_in[p], 0);
     }
   }
+  // the descriptor table points at each handle's latest frame slot
+  update_desc_table(b);
   const int64_t before = g_launches;
   int64_t launched = 0;
   if (use_graph) {
@@ -569,10 +629,13 @@ int run_batch(ds_batch_s* b, int iters, bool use_graph) {
   }
   g_total_kernels += launched;
   b->last_iters = iters;
-  // each handle's later work follows the batch
+  // the slots this solve read are free again after it; the handles' later calls that touch
+  // solve state wait for it (wait_solved), their next submissions only for their slot
   cudaEventRecord(b->ev_done, s);
   for (ds_ctx* h : b->hs) {
-    if (h->stream != s) cudaStreamWaitEvent(h->stream, b->ev_done, 0);
+    cudaEventRecord(h->ev_slot_free[h->fs], s);
+    h->slot_pending[h->fs] = true;
+    h->solved_fs = h->fs;
     h->last_iters = iters;
     h->kernels += launched;
   }
@@ -683,14 +746,19 @@ int ds_create_template(const float* depth_hw, int32_t W, int32_t H, ds_intrinsic
     if (h->h_depth0[i] > 0.f) h->h_pidx.push_back((int)i);
   if ((rc = dalloc(&h->d_depth0, npx)) || (rc = dalloc(&h->d_X64, 3 * npx)) ||
       (rc = dalloc(&h->d_pidx, h->h_pidx.size())) || (rc = dalloc(&h->d_depth, npx)) ||
-      (rc = dalloc(&h->d_tpts, npx)) || (rc = dalloc(&h->d_tnrm, npx)) ||
+      (rc = dalloc(&h->d_tpts, 2 * npx)) || (rc = dalloc(&h->d_tnrm, 2 * npx)) ||
       (rc = dalloc(&h->d_acc, ACC_COUNT)) || (rc = dalloc(&h->d_hist, 6 * DS_MAX_ITERS)) ||
       (rc = dalloc(&h->d_flag, 4)) || (rc = dalloc(&h->d_hyp, DS_MAX_HYP)) ||
-      (rc = dalloc(&h->d_rs_score, DS_MAX_HYP)) || (rc = dalloc(&h->d_rs_kept, 2)) ||
-      (rc = dalloc(&h->d_rs_counts, 4))) {
+      (rc = dalloc(&h->d_rs_score, 2 * DS_MAX_HYP)) || (rc = dalloc(&h->d_rs_kept, 4)) ||
+      (rc = dalloc(&h->d_rs_counts, 8))) {
     ds_destroy(h);
     return rc;
   }
+  for (int k = 0; k < 2; ++k)
+    if (cudaEventCreateWithFlags(&h->ev_slot_free[k], cudaEventDisableTiming) != cudaSuccess) {
+      ds_destroy(h);
+      return DS_ERR_CUDA;
+    }
   cudaMemcpy(h->d_depth0, h->h_depth0.data(), sizeof(float) * npx, cudaMemcpyHostToDevice);
   cudaMemcpy(h->d_pidx, h->h_pidx.data(), sizeof(int) * h->h_pidx.size(), cudaMemcpyHostToDevice);
   cudaMemset(h->d_acc, 0, sizeof(double) * ACC_COUNT);
@@ -721,6 +789,7 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
       if (i > 0 && srt[i] == srt[i - 1]) return DS_ERR_ARG;
     }
   }
+  wait_solved(h);
   cudaStreamSynchronize(h->stream);
   free_cp(h);
   h->N = N;
@@ -985,11 +1054,12 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
     lp.status = h->d_acc + ACC_STATUS;
     lp.y = h->d_v3;
     lp.x = h->d_v2;
-    if ((rc = dalloc(&h->d_desc, 1))) {
+    if ((rc = dalloc(&h->d_desc, 2))) {
       free_cp(h);
       return rc;
     }
-    push_desc(h);
+    push_desc(h, 0);
+    push_desc(h, 1);
   }
   std::vector<double> q0(4 * N, 0.0), t0(3 * N, 0.0);
   for (int i = 0; i < N; ++i) q0[4 * i] = 1.0;
@@ -1051,62 +1121,68 @@ int ds_submit_frame(ds_handle h, const float* depth_hw, const int32_t* match_tmp
     for (int k = 0; k < n_hyp; ++k)
       if (hyp_list[k] < 0 || hyp_list[k] >= M) return DS_ERR_ARG;
   }
+  // the new frame goes to the other slot, once the last solve that read that slot is done
+  const int ns = h->fs ^ 1;
+  if (h->slot_pending[ns]) cudaStreamWaitEvent(s, h->ev_slot_free[ns], 0);
   if (M > h->M_cap) {
+    // new slot buffers: every solve and submission still running must be done first
+    wait_solved(h);
     cudaStreamSynchronize(s);
     dfree(h->d_midx); dfree(h->d_mxyz); dfree(h->d_rs_scratch); dfree(h->d_rs_hbits);
     dfree(h->d_rs_hw); dfree(h->d_rs_mask); dfree(h->d_rs_what); dfree(h->d_rs_o1);
     dfree(h->d_rs_o1df);
     int cap = std::max(M, 64);
     int words = (cap + 31) / 32;
-    if ((rc = dalloc(&h->d_midx, cap)) || (rc = dalloc(&h->d_mxyz, 3 * (size_t)cap)) ||
+    if ((rc = dalloc(&h->d_midx, 2 * (size_t)cap)) || (rc = dalloc(&h->d_mxyz, 6 * (size_t)cap)) ||
         (rc = dalloc(&h->d_rs_scratch, (size_t)7 * cap * DS_MAX_HYP)) ||
         (rc = dalloc(&h->d_rs_hbits, (size_t)words * DS_MAX_HYP)) ||
         (rc = dalloc(&h->d_rs_hw, (size_t)cap * DS_MAX_HYP)) ||
-        (rc = dalloc(&h->d_rs_mask, words)) || (rc = dalloc(&h->d_rs_what, cap)) ||
+        (rc = dalloc(&h->d_rs_mask, 2 * (size_t)words)) ||
+        (rc = dalloc(&h->d_rs_what, 2 * (size_t)cap)) ||
         (rc = dalloc(&h->d_rs_o1, 3 * (size_t)cap)) ||
         (rc = dalloc(&h->d_rs_o1df, 6 * (size_t)cap))) {
       h->M_cap = 0;
       return rc;
     }
     h->M_cap = cap;
+    // the other slot's matches are gone: it keeps its live points, with no matches
+    h->Ms[h->fs] = 0;
+    push_desc(h, h->fs);
   }
-  h->M = M;
-  // the frame's match count and buffers, read by the kernels from the descriptor
-  if (h->hdesc.M != M || h->hdesc.midx != h->d_midx) {
-    h->hdesc.M = M;
-    h->hdesc.midx = h->d_midx;
-    h->hdesc.mxyz = h->d_mxyz;
-    h->hdesc.mask = h->d_rs_mask;
-    h->hdesc.what = h->d_rs_what;
-    push_desc(h);
-  }
+  if (h->prm.ransac_o1 == 1) wait_solved(h);   // o1 from the state the last solve left
+  int* midx = slot_midx(h, ns);
+  float* mxyz = slot_mxyz(h, ns);
   const int64_t launches0 = g_launches;
   if ((rc = copy_in(h->d_depth, depth_hw, sizeof(float) * npx, s))) return rc;
-  if ((rc = copy_in(h->d_midx, match_tmpl_idx, sizeof(int) * M, s))) return rc;
-  if ((rc = copy_in(h->d_mxyz, match_xyz, sizeof(float) * 3 * (size_t)M, s))) return rc;
+  if ((rc = copy_in(midx, match_tmpl_idx, sizeof(int) * M, s))) return rc;
+  if ((rc = copy_in(mxyz, match_xyz, sizeof(float) * 3 * (size_t)M, s))) return rc;
   if (M > 0 && (rc = copy_in(h->d_hyp, hyp_list, sizeof(int) * n_hyp, s))) return rc;
   cudaMemsetAsync(h->d_flag, 0, sizeof(int), s);
   if (M > 0) {
     int nt = std::max(M, n_hyp);
-    k_validate<<<(nt + 255) / 256, 256, 0, s>>>(h->d_midx, M, h->d_depth0, npx, h->d_hyp, n_hyp,
+    k_validate<<<(nt + 255) / 256, 256, 0, s>>>(midx, M, h->d_depth0, npx, h->d_hyp, n_hyp,
                                                 h->d_flag);
-    k_sanitize<<<(M + 255) / 256, 256, 0, s>>>(h->d_midx, M, h->h_pidx.empty() ? 0 : h->h_pidx[0]);
+    k_sanitize<<<(M + 255) / 256, 256, 0, s>>>(midx, M, h->h_pidx.empty() ? 0 : h->h_pidx[0]);
     g_launches += 2;
   }
   launch_check_finite(h->d_depth, npx, h->d_flag, s);
-  launch_check_finite(h->d_mxyz, 3 * M, h->d_flag, s);
-  launch_frame_prep(h->d_depth, h->W, h->H, h->K, h->d_tpts, h->d_tnrm, s);
+  launch_check_finite(mxyz, 3 * M, h->d_flag, s);
+  launch_frame_prep(h->d_depth, h->W, h->H, h->K, slot_tpts(h, ns), slot_tnrm(h, ns), s);
   if (M > 0) {
     const bool warm = h->prm.ransac_o1 == 1;
     if (warm)
-      launch_warm_o1(h->d_midx, M, h->d_rank, h->d_tp, h->d_seg, h->d_X64, h->d_g64, h->d_q64,
+      launch_warm_o1(midx, M, h->d_rank, h->d_tp, h->d_seg, h->d_X64, h->d_g64, h->d_q64,
                      h->d_t64, h->sigma_b, h->d_rs_o1, s);
-    launch_ransac(h->d_depth0, h->W, h->K, h->d_midx, h->d_mxyz, M, h->d_hyp, n_hyp,
+    launch_ransac(h->d_depth0, h->W, h->K, midx, mxyz, M, h->d_hyp, n_hyp,
                   h->prm.n_reweight, h->prm.H_mm, h->prm.keep_frac,
                   warm ? h->d_rs_o1 : nullptr, h->d_rs_o1df, h->d_rs_scratch,
-                  h->d_rs_hbits, h->d_rs_hw, h->d_rs_score, h->d_rs_mask, h->d_rs_what,
-                  h->d_rs_kept, h->d_rs_counts, s);
+                  h->d_rs_hbits, h->d_rs_hw, slot_score(h, ns), slot_mask(h, ns),
+                  slot_what(h, ns), slot_kept(h, ns), slot_counts(h, ns), s);
   }
+  h->Ms[ns] = M;
+  push_desc(h, ns);
+  h->fs = ns;
+  h->M = M;
   h->kernels += g_launches - launches0;
   if ((rc = check_sticky(h))) return rc;
   h->have_frame = true;
@@ -1121,7 +1197,8 @@ static int finish_solve(ds_handle h, int iters, ds_solve_stats* out) {
     std::vector<double> hist(6 * DS_MAX_ITERS);
     cudaMemcpy(hist.data(), h->d_hist, sizeof(double) * 6 * iters, cudaMemcpyDeviceToHost);
     int counts[4] = {0, 0, 0, 0};
-    if (h->M > 0) cudaMemcpy(counts, h->d_rs_counts, sizeof(int) * 4, cudaMemcpyDeviceToHost);
+    if (h->Ms[h->solved_fs] > 0)
+      cudaMemcpy(counts, slot_counts(h, h->solved_fs), sizeof(int) * 4, cudaMemcpyDeviceToHost);
     out->iters = iters;
     out->n_inliers = counts[0];
     out->n_kept = counts[1];
@@ -1284,6 +1361,7 @@ int ds_set_deformation(ds_handle h, const float* q_N4, const float* t_N3) {
       t[3 * i + k] = tf[3 * i + k];
     }
   }
+  wait_solved(h);
   cudaStreamSynchronize(h->stream);
   cudaMemcpy(h->d_q64, q.data(), sizeof(double) * 4 * N, cudaMemcpyHostToDevice);
   cudaMemcpy(h->d_t64, t.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice);
@@ -1295,7 +1373,7 @@ int ds_get_inlier_mask(ds_handle h, uint32_t* bits) {
   if (!h->have_frame) return DS_ERR_STATE;
   int rc = sync_status(h);
   if (rc && rc != DS_ERR_NOT_SPD) return rc;
-  if (h->M > 0 && cudaMemcpy(bits, h->d_rs_mask, sizeof(uint32_t) * ((h->M + 31) / 32),
+  if (h->M > 0 && cudaMemcpy(bits, slot_mask(h, h->fs), sizeof(uint32_t) * ((h->M + 31) / 32),
                              cudaMemcpyDefault))
     return DS_ERR_ARG;
   return DS_OK;
@@ -1307,12 +1385,13 @@ int ds_get_ransac(ds_handle h, float* w_M, uint32_t* kept_bits, double* score_nh
   int rc = sync_status(h);
   if (rc && rc != DS_ERR_NOT_SPD) return rc;
   if (h->M == 0) return DS_OK;
-  if (w_M && cudaMemcpy(w_M, h->d_rs_what, sizeof(float) * h->M, cudaMemcpyDefault))
+  if (w_M && cudaMemcpy(w_M, slot_what(h, h->fs), sizeof(float) * h->M, cudaMemcpyDefault))
     return DS_ERR_ARG;
-  if (kept_bits && cudaMemcpy(kept_bits, h->d_rs_kept, sizeof(uint32_t) * 2, cudaMemcpyDefault))
+  if (kept_bits &&
+      cudaMemcpy(kept_bits, slot_kept(h, h->fs), sizeof(uint32_t) * 2, cudaMemcpyDefault))
     return DS_ERR_ARG;
   if (score_nh &&
-      cudaMemcpy(score_nh, h->d_rs_score, sizeof(double) * h->prm.n_hyp, cudaMemcpyDefault))
+      cudaMemcpy(score_nh, slot_score(h, h->fs), sizeof(double) * h->prm.n_hyp, cudaMemcpyDefault))
     return DS_ERR_ARG;
   return DS_OK;
 }
@@ -1350,9 +1429,9 @@ int ds_get_frame_points(ds_handle h, float* pts4, float* nrm4) {
   int rc = sync_status(h);
   if (rc && rc != DS_ERR_NOT_SPD) return rc;
   size_t npx = (size_t)h->W * h->H;
-  if (pts4 && cudaMemcpy(pts4, h->d_tpts, sizeof(float4) * npx, cudaMemcpyDefault))
+  if (pts4 && cudaMemcpy(pts4, slot_tpts(h, h->fs), sizeof(float4) * npx, cudaMemcpyDefault))
     return DS_ERR_ARG;
-  if (nrm4 && cudaMemcpy(nrm4, h->d_tnrm, sizeof(float4) * npx, cudaMemcpyDefault))
+  if (nrm4 && cudaMemcpy(nrm4, slot_tnrm(h, h->fs), sizeof(float4) * npx, cudaMemcpyDefault))
     return DS_ERR_ARG;
   return DS_OK;
 }
@@ -1365,6 +1444,8 @@ int ds_linearize(ds_handle h, double w_arap_in, double* A_nn, double* b_n, doubl
   int rc = ensure_self(h);
   if (rc) return rc;
   cudaStream_t s = h->stream;
+  wait_solved(h);
+  update_desc_table(h->self);
   const BatchTabs& B = h->self->tabs;
   launch_iter_end(B, -1, false, s);
   const bool first = !(w_arap_in > 0);
@@ -1474,7 +1555,10 @@ int ds_get_counters(ds_handle h, int64_t* kernels_launched) {
 
 int ds_destroy(ds_handle h) {
   if (!h) return DS_OK;
-  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->stream) {
+    wait_solved(h);
+    cudaStreamSynchronize(h->stream);
+  }
   free_cp(h);
   dfree(h->d_depth0); dfree(h->d_X64); dfree(h->d_pidx); dfree(h->d_depth); dfree(h->d_tpts);
   dfree(h->d_tnrm); dfree(h->d_midx); dfree(h->d_mxyz); dfree(h->d_hyp);
@@ -1482,6 +1566,8 @@ int ds_destroy(ds_handle h) {
   dfree(h->d_rs_mask); dfree(h->d_rs_what); dfree(h->d_rs_kept); dfree(h->d_rs_counts);
   dfree(h->d_rs_o1); dfree(h->d_rs_o1df);
   dfree(h->d_acc); dfree(h->d_hist); dfree(h->d_flag);
+  for (int k = 0; k < 2; ++k)
+    if (h->ev_slot_free[k]) cudaEventDestroy(h->ev_slot_free[k]);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
   return DS_OK;

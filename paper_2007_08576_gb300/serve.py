@@ -59,7 +59,7 @@ def stream_bytes(W: int, H: int, N: int, M: int, precision: int) -> int:
     """Device bytes one stream holds (template, frame, blend tables, system buffers)."""
     npx, n = W * H, 6 * N
     nbp = 14 * N
-    b = npx * (4 + 24 + 4 + 4 + 16 + 16 + 4)            # depths, FP64 template, frame points
+    b = npx * (4 + 24 + 4 + 4 + 2 * (16 + 16) + 4)      # depths, FP64 template, 2 frame slots
     b += npx * (16 + 16 + 4)                            # sorted points, weights, rank
     b += N * (8 * 7 + 64 + 96) + nbp * (36 * 4 + 12)    # state, node tables, data blocks
     b += n * n * 4                                      # FP32 system
@@ -74,7 +74,8 @@ def stream_bytes(W: int, H: int, N: int, M: int, precision: int) -> int:
     b += 4 * (nt + 2 * nt * nt) + tsz * nt * tb * tb
     b += tsz * nt * (nt + 1) // 2 * tb * (tb + 16 // tsz)   # packed factor tiles
     b += nt * (nt + 1) // 2 * 16 * 2                    # task list
-    b += M * (4 + 12 + 4 + 4) + M * 64 * (7 * 8 + 4)    # matches and RANSAC scratch
+    b += 2 * M * (4 + 12 + 4 + 4) + M * (8 * 3 + 4 * 6)  # 2 slots of matches + RANSAC results
+    b += M * 64 * (7 * 8 + 4)                            # RANSAC scratch
     return int(b)
 
 

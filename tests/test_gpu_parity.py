@@ -665,3 +665,53 @@ def test_batch_mixes_association_variants(d, tiny, mid):
     assert np.abs(outs[1] - outs[2]).max() > 1e-6      # the two associations differ
     for s in solvers:
         s.close()
+
+
+# ----------------------------------------------------------------------------- pipelined frames
+
+
+def test_pipelined_batch_frames_match_sequential(d):
+    """Each handle keeps two frame slots: frame k + 1 is submitted (prepared, RANSAC) while the
+    batch still solves frame k, with no host synchronisation; the results equal solving each
+    frame after the previous one finished, and the getters return the latest frame's RANSAC."""
+    from synth.scene import Config
+    cfg = Config("seq_120x90_n40", 120, 90, 40, 300, 8, 0.4, 0.5, 0.1, 8.0, 1.0, 0.3, 0.5, 3)
+    scs = [scene(cfg, 91 + j, n_frames=3) for j in range(3)]
+    p = d.default_params(precision=2)
+    seq, seq_masks = [], []
+    for sc in scs:
+        s = d.Solver(sc.template_depth, sc.K, sc.nodes, p)
+        for fr in sc.frames:
+            s.submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+            s.solve(10, stats=False)
+            s.deformation64()                       # synchronises
+        seq.append(s.deformation64()[1])
+        seq_masks.append(s.mask())
+        s.close()
+    solvers = [d.Solver(sc.template_depth, sc.K, sc.nodes, p) for sc in scs]
+    b = d.ds_batch_create([s.h for s in solvers])
+    for k in range(3):
+        for s, sc in zip(solvers, scs):
+            fr = sc.frames[k]
+            s.submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+        d.ds_batch_solve(b, 10)
+        if k == 1:
+            # frame 2 submitted while frame 1 solves: its RANSAC is what the getters return
+            fr = scs[0].frames[2]
+            solvers[0].submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+            ref = d.Solver(scs[0].template_depth, scs[0].K, scs[0].nodes, p)
+            ref.submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+            assert np.array_equal(solvers[0].mask(), ref.mask())
+            ref.close()
+            # and the earlier frame the batch is solving is not disturbed: resubmit frame 1 so
+            # that the next batch solve sees the same sequence as the sequential run
+            fr = scs[0].frames[1]
+            solvers[0].submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+    d.ds_batch_status(b)
+    for s, t_seq, m_seq in zip(solvers, seq, seq_masks):
+        _, t = s.deformation64()
+        assert np.abs(t - t_seq).max() <= 1e-4
+        assert np.array_equal(s.mask(), m_seq)
+    d.ds_batch_destroy(b)
+    for s in solvers:
+        s.close()
