@@ -89,6 +89,34 @@ __device__ __forceinline__ void gemv_cols_pf(const T (&v)[SolveTile<T, TB>::NV],
   }
 }
 
+// Row hand-offs: the producer's threads store the row, meet at a CTA barrier, and thread 0
+// publishes the flag with a GPU-scope release store; the consumer polls it with GPU-scope acquire
+// loads (no full fences, no sleep between polls: the chain of rows is the solve's critical path).
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Bounded wait until *p >= v (acquire). False (and *err raised) on timeout or if *err is set.
+__device__ __forceinline__ bool wait_flag(const int* p, int v, int* err,
+                                          unsigned long long budget_ns) {
+  if (ld_acquire(p) >= v) return true;
+  const volatile int* ve = err;
+  const unsigned long long t0 = globaltimer();
+  int it = 0;
+  while (ld_acquire(p) < v) {
+    if (*ve) return false;
+    if ((++it & 63) == 0 && globaltimer() - t0 > budget_ns) {
+      atomicExch(err, 1);
+      return false;
+    }
+  }
+  return true;
+}
+
 // Tickets per problem: [0, nt) forward rows 0..nt-1, [nt, 2nt) backward rows nt-1..0.
 // flags: [0, nt) forward row done, [nt, 2nt) backward row done. Every tile a ticket needs is
 // loaded into registers before the wait on its producer (the tiles do not depend on it), so a
@@ -138,8 +166,7 @@ __global__ __launch_bounds__(256) void k_trsv_dag(const ProbDesc* const* __restr
       prefetch_cols<T, TB>(D, TB, TB, TB, dv);
     bool ok = true;
     if (threadIdx.x == 0) {
-      ok = fwd ? true : wait_ge(&flag[i], solve_id, err, budget_ns);
-      __threadfence();
+      ok = fwd ? true : wait_flag(&flag[i], solve_id, err, budget_ns);
       s_ok = ok;
     }
     __syncthreads();
@@ -160,10 +187,7 @@ __global__ __launch_bounds__(256) void k_trsv_dag(const ProbDesc* const* __restr
     }
     for (int q = 0; q < cnt && ok; ++q) {
       const int jt = fwd ? q : nt - 1 - q;
-      if (threadIdx.x == 0) {
-        s_ok = wait_ge(&flag[fwd ? jt : nt + jt], solve_id, err, budget_ns);
-        __threadfence();
-      }
+      if (threadIdx.x == 0) s_ok = wait_flag(&flag[fwd ? jt : nt + jt], solve_id, err, budget_ns);
       __syncthreads();
       ok = s_ok;
       if (!ok) break;
@@ -209,10 +233,7 @@ __global__ __launch_bounds__(256) void k_trsv_dag(const ProbDesc* const* __restr
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      atomicExch(&flag[fwd ? i : nt + i], solve_id);
-    }
+    if (threadIdx.x == 0) st_release(&flag[fwd ? i : nt + i], solve_id);
   }
 }
 
