@@ -41,11 +41,12 @@ PREC = {"fp64": 0, "fp32": 1, "fp32_refine": 2}
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate per GPU (nominal)
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_chol_dag launch on this
-# workload (32 problems, FP32 factor), from the full ncu capture summarised in
+# workload (32 problems, FP32 factor), from the ncu capture summarised in
 # profiles/k_chol_dag_f32_seq_320x240_n256_batch32.md. It describes the kernel source it was taken
-# on (first 16 hex digits of the sha256 of csrc/chol.cu) and is reported as null for any other.
-CHOL_TRAFFIC = {"chol_sha256": "47794e8459102c6a", "precision": 2, "streams": 32,
-                "bytes": 683611392 + 356222464}
+# on (first 16 hex digits of the sha256 of csrc/chol.cu + csrc/dev_util.cuh) and is reported as
+# null for any other.
+CHOL_TRAFFIC = {"chol_sha256": "8c5b33a357e51b2c", "precision": 2, "streams": 32,
+                "bytes": 663056896 + 355572480}
 
 
 def max_over_ranks(x, world, dev):
@@ -87,11 +88,20 @@ def _measured_hbm():
         return 6800.0   # earlier GB300 measurement, used when the file is absent
 
 
+def _chol_source_digest():
+    """First 16 hex digits of the sha256 of the factorisation kernel's sources (chol.cu and the
+    device helpers it includes)."""
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2007_08576_gb300",
+                        "csrc")
+    h = hashlib.sha256()
+    for name in ("chol.cu", "dev_util.cuh"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def _chol_traffic(prec, streams):
-    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2007_08576_gb300",
-                       "csrc", "chol.cu")
-    with open(src, "rb") as f:
-        digest = hashlib.sha256(f.read()).hexdigest()[:16]
+    digest = _chol_source_digest()
     c = CHOL_TRAFFIC
     if digest != c["chol_sha256"] or prec != c["precision"] or streams != c["streams"]:
         return None

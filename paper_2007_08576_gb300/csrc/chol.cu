@@ -460,16 +460,16 @@ __global__ __launch_bounds__(256, DS_CHOL_CTAS_PER_SM) void k_chol_dag(
     T* Lp = (T*)P.Lp;
     const T* Li = Lp + tile_slot(i, 0) * TILE;   // row panel i (slots (i, 0..i))
     const T* Lj = Lp + tile_slot(j, 0) * TILE;
+    // dependencies are read with acquire loads (the producers publish with release stores), so
+    // a copy needs only the proxy fence before it
     auto ready = [&](int k) {
-      const volatile int* f = tdone;
-      return f[i * nt + k] >= 1 && (diag || f[j * nt + k] >= 1);
+      return ld_acquire(&tdone[i * nt + k]) >= 1 && (diag || ld_acquire(&tdone[j * nt + k]) >= 1);
     };
     auto wait_deps = [&](int k) {
-      return wait_ge(&tdone[i * nt + k], 1, err, budget_ns) &&
-             (diag || wait_ge(&tdone[j * nt + k], 1, err, budget_ns));
+      return wait_flag(&tdone[i * nt + k], 1, err, budget_ns) &&
+             (diag || wait_flag(&tdone[j * nt + k], 1, err, budget_ns));
     };
     auto issue = [&](int k, int s) {
-      __threadfence();
       fence_proxy_async_global();
       T* dst = buf + 2 * s * TILE;
       mbar_expect(&bar[s], diag ? TBYTES : 2 * TBYTES);
@@ -563,9 +563,8 @@ __global__ __launch_bounds__(256, DS_CHOL_CTAS_PER_SM) void k_chol_dag(
         T* Ct = buf;                // C^T
         T* Dt = buf + TILE;         // (L_jj^-1)^T, packed
         if (tid == 0) {
-          s_dok = wait_ge(&pdone[j], 1, err, budget_ns);
+          s_dok = wait_flag(&pdone[j], 1, err, budget_ns);
           if (s_dok) {
-            __threadfence();
             fence_proxy_async_global();
             mbar_expect(&bar[0], TBYTES);
             bulk_load(Dt, Lp + tile_slot(j, j) * TILE, TBYTES, &bar[0]);
@@ -608,16 +607,15 @@ __global__ __launch_bounds__(256, DS_CHOL_CTAS_PER_SM) void k_chol_dag(
     fence_proxy_async_shared();
     __syncthreads();
     if (tid == 0) {
-      __threadfence();
       fence_proxy_async_global();
 #if defined(DS_TASK_TRACE)
       ds_trace_mark(t, 2);
 #endif
       // published even when skipped after an error, so that no task waits on it
       if (diag)
-        atomicExch(&pdone[j], 1);
+        st_release(&pdone[j], 1);
       else
-        atomicExch(&tdone[i * nt + j], 1);
+        st_release(&tdone[i * nt + j], 1);
     }
   }
 }

@@ -1,5 +1,6 @@
 // Device helpers shared by the factorisation and the solve kernels: the global timer, bounded
-// waits on counters written by other CTAs, L2-only loads, the SM count.
+// waits on counters written by other CTAs (polling with sleeps, or with acquire loads),
+// release stores, L2-only loads, the SM count.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -26,6 +27,33 @@ __device__ __forceinline__ bool wait_ge(const int* p, int v, int* err,
       return false;
     }
     __nanosleep(64);
+  }
+  return true;
+}
+
+// GPU-scope acquire load / release store of a flag word.
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Bounded wait until *p >= v with acquire loads and no sleep between polls (for waits on a
+// critical path). False (and *err raised) on timeout or if *err is set.
+__device__ __forceinline__ bool wait_flag(const int* p, int v, int* err,
+                                          unsigned long long budget_ns) {
+  if (ld_acquire(p) >= v) return true;
+  const volatile int* ve = err;
+  const unsigned long long t0 = globaltimer();
+  int it = 0;
+  while (ld_acquire(p) < v) {
+    if (*ve) return false;
+    if ((++it & 63) == 0 && globaltimer() - t0 > budget_ns) {
+      atomicExch(err, 1);
+      return false;
+    }
   }
   return true;
 }

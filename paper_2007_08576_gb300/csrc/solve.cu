@@ -90,32 +90,9 @@ __device__ __forceinline__ void gemv_cols_pf(const T (&v)[SolveTile<T, TB>::NV],
 }
 
 // Row hand-offs: the producer's threads store the row, meet at a CTA barrier, and thread 0
-// publishes the flag with a GPU-scope release store; the consumer polls it with GPU-scope acquire
-// loads (no full fences, no sleep between polls: the chain of rows is the solve's critical path).
-__device__ __forceinline__ int ld_acquire(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(int* p, int v) {
-  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-// Bounded wait until *p >= v (acquire). False (and *err raised) on timeout or if *err is set.
-__device__ __forceinline__ bool wait_flag(const int* p, int v, int* err,
-                                          unsigned long long budget_ns) {
-  if (ld_acquire(p) >= v) return true;
-  const volatile int* ve = err;
-  const unsigned long long t0 = globaltimer();
-  int it = 0;
-  while (ld_acquire(p) < v) {
-    if (*ve) return false;
-    if ((++it & 63) == 0 && globaltimer() - t0 > budget_ns) {
-      atomicExch(err, 1);
-      return false;
-    }
-  }
-  return true;
-}
+// publishes the flag with a GPU-scope release store (st_release); the consumer polls it with
+// GPU-scope acquire loads (wait_flag): no full fences, no sleep between polls, since the chain of
+// rows is the solve's critical path.
 
 // Tickets per problem: [0, nt) forward rows 0..nt-1, [nt, 2nt) backward rows nt-1..0.
 // flags: [0, nt) forward row done, [nt, 2nt) backward row done. Every tile a ticket needs is
