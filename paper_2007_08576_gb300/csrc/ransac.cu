@@ -254,29 +254,6 @@ __device__ __forceinline__ void tmpl_point64(const float* depth0, int W, double 
   o[2] = z;
 }
 
-template <int NV>
-__device__ __forceinline__ void block_sum(double* v, double* red /* NV * 32 */) {
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    double x = v[i];
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    v[i] = x;
-  }
-  __syncthreads();
-  if (lane == 0)
-#pragma unroll
-    for (int i = 0; i < NV; ++i) red[i * 32 + warp] = v[i];
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    double x = 0.0;
-    for (int w = 0; w < nw; ++w) x += red[i * 32 + w];  // fixed order
-    v[i] = x;
-  }
-  __syncthreads();
-}
-
 // ----------------------------------------------------------------------------- double-float
 // The per-match loops run in double-float arithmetic: a value is the unevaluated sum hi + lo of
 // two floats (|lo| <= ulp(hi) / 2, 48 significant bits), products split exactly with an FMA,
