@@ -152,6 +152,10 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N);
  * is replaced by 0 before any kernel reads it, and the next synchronising call (ds_solve with
  * stats, any ds_get_*) returns DS_ERR_ARG. Non-finite depth or match coordinates are reported
  * the same way as DS_ERR_BAD_INPUT.
+ * A handle keeps two frame slots: a frame goes to the slot the last solve did not read, so it
+ * may be submitted while that solve (e.g. a batch on another stream) still runs; it waits only
+ * for the solve that last read its slot (and, with ransac_o1 = 1, for the last solve, whose
+ * state it warps). A solve uses the latest submitted frame.
  * Errors: DS_ERR_ARG, DS_ERR_BAD_INPUT, DS_ERR_STATE (no control points), DS_ERR_CUDA. */
 int ds_submit_frame(ds_handle h, const float* depth_hw, const int32_t* match_tmpl_idx,
                     const float* match_xyz, int32_t M, const int32_t* hyp_list);
@@ -167,9 +171,11 @@ int ds_solve(ds_handle h, int32_t iters, ds_solve_stats* out);
  * every kernel launch of an iteration covers the work lists of all problems (ICP tiles, ORB
  * matches, ARAP rows, factorisation tile tasks, solve tiles), and the iterations are captured
  * once as a CUDA graph per iteration count. Handles keep their own stream for submit_frame and
- * ds_get_*; the batch orders its work after the handles' pending work and the handles' later
- * work after the batch. A handle may belong to several batches; a batch must not run while one
- * of its handles is being solved elsewhere. cuda_stream: stream of the batch or NULL (owned).
+ * ds_get_*; the batch orders its work after the handles' pending work and their earlier solves;
+ * a handle's later calls that read or change its solve state (ds_get_*, ds_set_deformation,
+ * ds_linearize, ds_set_control_points, ds_destroy) wait for its last solve, and its later
+ * submissions only for the solve that read the frame slot they reuse. A handle may belong to
+ * several batches. cuda_stream: stream of the batch or NULL (owned).
  * Errors: DS_ERR_ARG (empty, mixed precision, a handle without control points), DS_ERR_OOM. */
 typedef struct ds_batch_s* ds_batch;
 int ds_batch_create(const ds_handle* hs, int32_t n, void* cuda_stream, ds_batch* out);
