@@ -7,8 +7,9 @@
 //                9-run test on the doubled 16-bit mask) and the 5 x 5 box sum of the pixel;
 //   k_keep_count 256 pixels per CTA in row-major order: keypoint test (response > 0, no
 //                neighbour larger, inside the border, positive depth), CTA count;
-//   k_compact    the same test again, each CTA's offset = sum of the earlier CTAs' counts,
-//                in-CTA order by ballots: keypoints land in ascending pixel order with no sort;
+//   k_block_offsets  one CTA: exclusive prefix sums of the CTA counts and the totals;
+//   k_compact    the same test again, each CTA's keypoints at its offset, in-CTA order by
+//                ballots: keypoints land in ascending pixel order with no sort;
 //   k_describe   one warp per keypoint: intensity-centroid moments over the radius-15 disc,
 //                the orientation bin in FP64, 256 tests as 8 ballots of 32 lanes.
 // Matching (ds_orb_match): k_nearest twice (template -> live, live -> template), one warp per
@@ -104,38 +105,69 @@ __global__ __launch_bounds__(256) void k_keep_count(const int* __restrict__ scor
   if (threadIdx.x == 0) cnt[blockIdx.x] = c;
 }
 
+// Exclusive prefix sums of the CTA counts (one CTA of 1024 threads, 1024 counts per round) and
+// the keypoint totals.
+__global__ __launch_bounds__(1024) void k_block_offsets(const int* __restrict__ cnt, int nblk,
+                                                        int max_kp, int* __restrict__ off,
+                                                        int* __restrict__ nkp) {
+  __shared__ int s_warp[32];
+  __shared__ int s_base;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_base = 0;
+  __syncthreads();
+  for (int b0 = 0; b0 < nblk; b0 += 1024) {
+    const int b = b0 + tid;
+    const int v = b < nblk ? cnt[b] : 0;
+    int x = v;   // inclusive scan within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {   // inclusive scan of the warp totals
+      int w = s_warp[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      s_warp[lane] = w;
+    }
+    __syncthreads();
+    if (b < nblk) off[b] = s_base + (warp > 0 ? s_warp[warp - 1] : 0) + x - v;
+    __syncthreads();
+    if (tid == 0) s_base += s_warp[31];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    nkp[0] = min(s_base, max_kp);
+    nkp[1] = s_base;
+  }
+}
+
+// Keypoints of each CTA's 256 pixels at its offset, in pixel order (ballots within the CTA).
 __global__ __launch_bounds__(256) void k_compact(const int* __restrict__ score,
                                                  const float* __restrict__ depth, int W, int H,
-                                                 int border, const int* __restrict__ cnt,
-                                                 int nblk, int max_kp, int* __restrict__ kp_pix,
-                                                 int* __restrict__ kp_score, int* __restrict__ nkp) {
-  __shared__ int s_red[8], s_warp[8];
+                                                 int border, const int* __restrict__ off,
+                                                 int max_kp, int* __restrict__ kp_pix,
+                                                 int* __restrict__ kp_score) {
+  __shared__ int s_warp[8];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int pre = 0;
-  for (int b = tid; b < blockIdx.x; b += 256) pre += cnt[b];
-  for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(0xffffffffu, pre, o);
-  if (lane == 0) s_red[warp] = pre;
   const int i = blockIdx.x * 256 + tid;
   const bool kp = is_keypoint(score, depth, W, H, border, i);
   const unsigned bal = __ballot_sync(0xffffffffu, kp);
   if (lane == 0) s_warp[warp] = __popc(bal);
   __syncthreads();
-  int base = 0, woff = 0, total_blk = 0;
+  int woff = 0;
 #pragma unroll
-  for (int w = 0; w < 8; ++w) {
-    base += s_red[w];
+  for (int w = 0; w < 8; ++w)
     if (w < warp) woff += s_warp[w];
-    total_blk += s_warp[w];
-  }
-  const int idx = base + woff + __popc(bal & ((1u << lane) - 1u));
+  const int idx = off[blockIdx.x] + woff + __popc(bal & ((1u << lane) - 1u));
   if (kp && idx < max_kp) {
     kp_pix[idx] = i;
     kp_score[idx] = score[i];
-  }
-  if (blockIdx.x == nblk - 1 && tid == 0) {
-    const int total = base + total_blk;
-    nkp[0] = min(total, max_kp);
-    nkp[1] = total;
   }
 }
 
@@ -329,6 +361,7 @@ struct ds_orb_s {
   int* d_score = nullptr;
   int* d_box = nullptr;
   int* d_cnt = nullptr;
+  int* d_off = nullptr;        // exclusive prefix sums of d_cnt
   int nblk = 0;
   char4* d_tab = nullptr;
   int* d_kp_pix = nullptr;
@@ -353,7 +386,7 @@ int orb_check(ds_orb o) {
 void orb_release(ds_orb o) {
   using ds::orb_free;
   orb_free(o->d_img); orb_free(o->d_depth); orb_free(o->d_score); orb_free(o->d_box);
-  orb_free(o->d_cnt); orb_free(o->d_tab); orb_free(o->d_kp_pix); orb_free(o->d_kp_score);
+  orb_free(o->d_cnt); orb_free(o->d_off); orb_free(o->d_tab); orb_free(o->d_kp_pix); orb_free(o->d_kp_score);
   orb_free(o->d_kp_bin); orb_free(o->d_desc); orb_free(o->d_nkp); orb_free(o->d_best_l);
   orb_free(o->d_best_t); orb_free(o->d_m); orb_free(o->d_m_xyz);
   if (o->ev) cudaEventDestroy(o->ev);
@@ -426,7 +459,7 @@ int ds_orb_create(int32_t W, int32_t H, ds_intrinsics K, const ds_orb_params* p,
   double* d_pat = nullptr;
   if ((rc = orb_alloc(&o->d_img, npx)) || (rc = orb_alloc(&o->d_depth, npx)) ||
       (rc = orb_alloc(&o->d_score, npx)) || (rc = orb_alloc(&o->d_box, npx)) ||
-      (rc = orb_alloc(&o->d_cnt, (size_t)o->nblk)) ||
+      (rc = orb_alloc(&o->d_cnt, (size_t)o->nblk)) || (rc = orb_alloc(&o->d_off, (size_t)o->nblk)) ||
       (rc = orb_alloc(&o->d_tab, (size_t)ds::kNbins * ds::kTests)) ||
       (rc = orb_alloc(&o->d_kp_pix, (size_t)K8)) || (rc = orb_alloc(&o->d_kp_score, (size_t)K8)) ||
       (rc = orb_alloc(&o->d_kp_bin, (size_t)K8)) || (rc = orb_alloc(&o->d_desc, (size_t)K8 * 8)) ||
@@ -478,12 +511,13 @@ int ds_orb_detect(ds_orb o, const uint8_t* image_hw, const float* depth_hw) {
   ds::k_fast_box<<<grd, blk, 0, s>>>(o->d_img, W, H, o->prm.fast_t, o->d_score, o->d_box);
   const float* dep = depth_hw ? o->d_depth : nullptr;
   ds::k_keep_count<<<o->nblk, 256, 0, s>>>(o->d_score, dep, W, H, o->prm.border, o->d_cnt);
-  ds::k_compact<<<o->nblk, 256, 0, s>>>(o->d_score, dep, W, H, o->prm.border, o->d_cnt, o->nblk,
-                                        o->max_kp, o->d_kp_pix, o->d_kp_score, o->d_nkp);
+  ds::k_block_offsets<<<1, 1024, 0, s>>>(o->d_cnt, o->nblk, o->max_kp, o->d_off, o->d_nkp);
+  ds::k_compact<<<o->nblk, 256, 0, s>>>(o->d_score, dep, W, H, o->prm.border, o->d_off,
+                                        o->max_kp, o->d_kp_pix, o->d_kp_score);
   ds::k_describe<<<(o->max_kp + 7) / 8, 256, 0, s>>>(o->d_img, o->d_box, W, o->d_kp_pix, o->d_nkp,
                                                      o->d_tab, o->d_kp_bin, o->d_desc);
-  ds::g_launches += 4;
-  ds::count_kernels(4);
+  ds::g_launches += 5;
+  ds::count_kernels(5);
   o->detected = true;
   o->have_depth = depth_hw != nullptr;
   cudaEventRecord(o->ev, s);
