@@ -407,7 +407,7 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   b->block_jacobi = solver == 1;
   b->stream = stream;
   b->own_stream = own;
-  std::vector<int2> icp, rows, nodes, vec, res, chol;
+  std::vector<int2> icp, rows, nodes, res, chol;
   std::vector<int> ntasks(n);
   int max_tasks = 0, max_nt = 0;
   std::vector<const ProbDesc*> descs(n);
@@ -417,7 +417,6 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
     for (int t = 0; t * kSegPerCta * kSegPerWarp < h->S; ++t) icp.push_back(make_int2(p, t));
     for (int i = 0; i < h->N; ++i) rows.push_back(make_int2(p, i));
     for (int c = 0; c * 128 < h->N; ++c) nodes.push_back(make_int2(p, c));
-    for (int c = 0; c * 256 < h->n; ++c) vec.push_back(make_int2(p, c));
     for (int c = 0; c * 8 < h->n; ++c) res.push_back(make_int2(p, c));
     ntasks[p] = h->ntasks;
     max_tasks = std::max(max_tasks, h->ntasks);
@@ -425,7 +424,7 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   }
   make_chol_tickets(ntasks, chol);
   const size_t ntab =
-      icp.size() + rows.size() + nodes.size() + vec.size() + res.size() + chol.size();
+      icp.size() + rows.size() + nodes.size() + res.size() + chol.size();
   int rc;
   if ((rc = dalloc(&b->d_descs, n)) || (rc = dalloc(&b->d_tab, ntab)) ||
       (rc = dalloc(&b->d_words, 8))) {
@@ -434,7 +433,7 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   }
   std::vector<int2> all;
   all.reserve(ntab);
-  for (auto* v : {&icp, &rows, &nodes, &vec, &res, &chol})
+  for (auto* v : {&icp, &rows, &nodes, &res, &chol})
     all.insert(all.end(), v->begin(), v->end());
   cudaMemcpy(b->d_descs, descs.data(), sizeof(void*) * n, cudaMemcpyHostToDevice);
   b->h_descs = descs;
@@ -447,7 +446,6 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   T.icp = b->d_tab + off; T.n_icp = (int)icp.size(); off += icp.size();
   T.rows = b->d_tab + off; T.n_rows = (int)rows.size(); off += rows.size();
   T.nodes = b->d_tab + off; T.n_nodes = (int)nodes.size(); off += nodes.size();
-  T.vec = b->d_tab + off; T.n_vec = (int)vec.size(); off += vec.size();
   T.res = b->d_tab + off; T.n_res = (int)res.size(); off += res.size();
   T.chol = b->d_tab + off; T.n_chol = (int)chol.size(); off += chol.size();
   T.orb_ctas = 16;

@@ -152,8 +152,6 @@ struct BatchTabs {
   int n_rows;
   const int2* nodes;         // (problem, 128-node chunk)
   int n_nodes;
-  const int2* vec;           // (problem, 256-element chunk of the 6N vectors)
-  int n_vec;
   const int2* res;           // (problem, 8-row chunk of the refinement residual)
   int n_res;
   int orb_ctas;              // CTAs per problem of the ORB pass (grid-stride over M)
