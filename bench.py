@@ -41,10 +41,10 @@ PREC = {"fp64": 0, "fp32": 1, "fp32_refine": 2}
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate per GPU (nominal)
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_chol_dag launch on this
-# workload (32 problems, FP32 factor), from the ncu capture summarised in
-# profiles/k_chol_dag_f32_seq_320x240_n256_batch32.md. It describes the kernel source it was taken
-# on (first 16 hex digits of the sha256 of csrc/chol.cu + csrc/dev_util.cuh) and is reported as
-# null for any other.
+# workload (32 problems, FP32 factor), from an ncu capture of one launch of the warm-up steps
+# (`ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_chol_dag -s 2 -c 1 ...`).
+# It describes the kernel source it was taken on (first 16 hex digits of the sha256 of
+# csrc/chol.cu + csrc/dev_util.cuh) and is reported as null for any other.
 CHOL_TRAFFIC = {"chol_sha256": "8c5b33a357e51b2c", "precision": 2, "streams": 32,
                 "bytes": 663056896 + 355572480}
 
