@@ -740,3 +740,19 @@ def test_warm_o1_recovers_planted_inliers_under_a_nonrigid_state():
     assert np.array_equal(rs["mask"], inl)
     rt = ransac.ransac_1p(tpl.X0[midx], o2, hyp, 2.0, 10, 0.5)
     assert not np.array_equal(rt["mask"], inl)
+
+
+def test_warm_o1_is_invariant_to_quaternion_signs():
+    """q and -q are the same rotation: flipping the sign of any nodes' quaternions leaves the
+    warped o1 points unchanged (the blend aligns signs to the nearest node)."""
+    sc = make_scene(CONFIGS["frame_80x60_n32"], 1000, f64=True)
+    tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes)
+    f = sc.frames[0]
+    rng = np.random.default_rng(27)
+    N = tpl.g.shape[0]
+    q, t = random_state(rng, N, rot=0.3, trans=3.0)
+    prm = solver.Params(ransac_o1="warm")
+    a = solver.ransac_o1(tpl, f.match_idx, q, t, prm)
+    flip = rng.uniform(size=N) < 0.5
+    b = solver.ransac_o1(tpl, f.match_idx, np.where(flip[:, None], -q, q), t, prm)
+    assert flip.any() and np.abs(a - b).max() < 1e-9

@@ -225,3 +225,17 @@ def test_matches_of_a_deformed_frame_land_on_the_true_points():
     assert len(err) > 400
     assert (err < 2.0).mean() > 0.8
     assert np.all(np.asarray(sc.template_depth).reshape(-1)[m["tmpl_pix"]] > 0)
+
+
+def test_detection_is_invariant_to_an_intensity_offset():
+    """FAST compares differences, the centroid's moments of a constant vanish over the symmetric
+    disc and both box sums of a test gain the same amount: adding a constant to an image (with
+    no clipping) changes no keypoint, response, bin or descriptor bit."""
+    img = _textured_crop().astype(np.int64)
+    img = np.clip(img, 0, 200).astype(np.uint8)
+    pat = orb_pattern(7)
+    a = orb.detect(img, None, pat)
+    b = orb.detect((img.astype(np.int64) + 37).astype(np.uint8), None, pat)
+    assert len(a["pix"]) > 30
+    assert np.array_equal(a["pix"], b["pix"]) and np.array_equal(a["score"], b["score"])
+    assert np.array_equal(a["bin"], b["bin"]) and np.array_equal(a["desc"], b["desc"])
