@@ -715,3 +715,30 @@ def test_pipelined_batch_frames_match_sequential(d):
     d.ds_batch_destroy(b)
     for s in solvers:
         s.close()
+
+
+def test_ransac_degenerate_fit_is_the_identity(d, tiny):
+    """Every match on the same template pixel: S1 = 0 for every reference, M = sum w S2 S1^T = 0,
+    and both sides take R = I (Horn's matrix vanishes; the oracle's SVD has no singular value
+    above zero), so d_k = |S2(k)| decides each mask bit."""
+    sc = tiny
+    fr = sc.frames[0]
+    rng = np.random.default_rng(12)
+    j = int(sc.nodes[3])
+    M = 60
+    midx = np.full(M, j, np.int32)
+    X0, _ = oframe.backproject(sc.template_depth, sc.K)
+    o1 = X0.reshape(-1, 3)[midx]
+    off = rng.normal(size=(M, 3))
+    off *= rng.uniform(0.0, 6.0, (M, 1)) / np.linalg.norm(off, axis=1, keepdims=True)
+    xyz = (o1 + off).astype(np.float32)
+    hyp = rng.choice(M, size=30, replace=False).astype(np.int32)
+    p = d.default_params()
+    s = d.Solver(sc.template_depth, sc.K, sc.nodes, p)
+    s.submit(fr.depth, midx, xyz, hyp)
+    from oracle import ransac
+    rs = ransac.ransac_1p(o1, xyz, hyp, p.H_mm, p.n_reweight, p.keep_frac)
+    assert np.array_equal(ransac.kabsch(o1 - o1[0], xyz - xyz[0], np.ones(M)), np.eye(3))
+    assert rs["mask"].any() and not rs["mask"].all()
+    _check_ransac(d, s, p, rs, M)
+    s.close()
