@@ -78,8 +78,10 @@ int ds_orb_num_keypoints(ds_orb o, int32_t* n_kept, int32_t* n_total);
 int ds_orb_get_keypoints(ds_orb o, int32_t* pix, int32_t* score, int32_t* bin, uint32_t* desc_8);
 
 /* Matches the keypoints of `tmpl` (detected once on the template image) to those of `live`
- * (detected with its depth), on live's stream after tmpl's pending work. The results stay in
- * `live`. Both contexts must have the same pattern; tmpl and live may be the same object.
+ * (detected with its depth), on live's stream after tmpl's pending work; tmpl's stream then waits
+ * for the match, so a later ds_orb_detect on tmpl cannot overwrite what it reads. The results
+ * stay in `live`. Both contexts must have the same pattern; tmpl and live may be the same
+ * object.
  * Errors: DS_ERR_ARG (NULL, different image sizes), DS_ERR_STATE (nothing detected, or no live
  * depth), DS_ERR_CUDA. */
 int ds_orb_match(ds_orb tmpl, ds_orb live);

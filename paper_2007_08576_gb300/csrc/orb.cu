@@ -579,6 +579,8 @@ int ds_orb_match(ds_orb tmpl, ds_orb live) {
   ds::g_launches += 3;
   ds::count_kernels(3);
   cudaEventRecord(live->ev, s);
+  // later work on the template's stream (a new detection) waits until the match has read it
+  if (tmpl != live) cudaStreamWaitEvent(tmpl->stream, live->ev, 0);
   return orb_check(live);
 }
 
