@@ -1139,7 +1139,12 @@ int ds_submit_frame(ds_handle h, const float* depth_hw, const int32_t* match_tmp
         (rc = dalloc(&h->d_rs_what, 2 * (size_t)cap)) ||
         (rc = dalloc(&h->d_rs_o1, 3 * (size_t)cap)) ||
         (rc = dalloc(&h->d_rs_o1df, 6 * (size_t)cap))) {
+      // no slot may keep pointers into the freed buffers: both hold no frame now
       h->M_cap = 0;
+      h->Ms[0] = h->Ms[1] = 0;
+      push_desc(h, 0);
+      push_desc(h, 1);
+      h->have_frame = false;
       return rc;
     }
     h->M_cap = cap;
