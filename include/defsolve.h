@@ -52,9 +52,11 @@ typedef enum {
  * mode; the state is kept in FP64. */
 typedef enum {
   DS_PREC_FP64 = 0,        /* FP64 Cholesky + FP64 triangular solves + refinement steps whose
-                              residual b - A x is accumulated in FP64 against the FP32 matrix */
+                              residual b - A x against the FP32 matrix is accumulated in
+                              double-float FP32 arithmetic (FMA-exact products, two-sum
+                              accumulation: ~48 significant bits) and subtracted from b in FP64 */
   DS_PREC_FP32 = 1,        /* plain: FP32 Cholesky and solves, no refinement                   */
-  DS_PREC_FP32_REFINE = 2  /* FP32 Cholesky, FP64 residual refinement steps                   */
+  DS_PREC_FP32_REFINE = 2  /* FP32 Cholesky and solves + the same refinement steps            */
 } ds_precision;
 
 #define DS_MAX_ITERS 64
@@ -85,7 +87,7 @@ typedef struct {
   int32_t n_reweight;       /* reweighting iterations per reference                              */
   int32_t n_nearest;        /* control points blended per template point; must be 4             */
   int32_t precision;        /* ds_precision                                                      */
-  int32_t refine_steps;     /* refinement steps in DS_PREC_FP64 / DS_PREC_FP32_REFINE (0..4)     */
+  int32_t refine_steps;     /* refinement steps in DS_PREC_FP64 / DS_PREC_FP32_REFINE (0..3)     */
   int32_t use_graph;        /* 1: replay the GN loop as a CUDA graph (default), 0: plain launches */
   int32_t factor_tc;        /* FP32 precisions: 0 = factorisation on the FP32 SIMT pipes (default),
                              * 1 = on the tensor cores (tcgen05 kind::tf32, each product as three
@@ -175,12 +177,17 @@ int ds_solve(ds_handle h, int32_t iters, ds_solve_stats* out);
  * a handle's later calls that read or change its solve state (ds_get_*, ds_set_deformation,
  * ds_linearize, ds_set_control_points, ds_destroy) wait for its last solve, and its later
  * submissions only for the solve that read the frame slot they reuse. A handle may belong to
- * several batches. cuda_stream: stream of the batch or NULL (owned).
- * Errors: DS_ERR_ARG (empty, mixed precision, a handle without control points), DS_ERR_OOM. */
+ * several batches, once in each. A batch's work tables are built from its handles' control
+ * points: once a handle gets new control points (ds_set_control_points) or is destroyed, every
+ * batch listing it refuses to solve (DS_ERR_STATE) and is only good for ds_batch_destroy;
+ * batches and handles may be destroyed in either order. cuda_stream: stream of the batch or NULL
+ * (owned). Errors: DS_ERR_ARG (empty, mixed precision, a handle without control points, a handle
+ * listed twice), DS_ERR_OOM. */
 typedef struct ds_batch_s* ds_batch;
 int ds_batch_create(const ds_handle* hs, int32_t n, void* cuda_stream, ds_batch* out);
 /* Runs `iters` iterations (1..DS_MAX_ITERS) on every handle of the batch; each handle must have
- * a submitted frame. Asynchronous; results are read per handle (ds_get_*), and
+ * a submitted frame (else DS_ERR_STATE, also for a stale batch). Asynchronous; results are read
+ * per handle (ds_get_*), and
  * ds_batch_status synchronises the batch and reports DS_ERR_TIMEOUT / DS_ERR_NOT_SPD. */
 int ds_batch_solve(ds_batch b, int32_t iters);
 int ds_batch_status(ds_batch b);

@@ -63,6 +63,9 @@ struct ds_batch_s {
   cudaStream_t side = nullptr, side2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
   bool error = false;
+  // a handle's control points changed, or it was destroyed (its entry in hs is then NULL): the
+  // work tables and descriptor pointers are the old ones, so the batch no longer runs
+  bool stale = false;
 };
 
 struct ds_ctx {
@@ -158,6 +161,7 @@ struct ds_ctx {
   ProbDesc* d_desc = nullptr;
   // the batch of one used by ds_solve
   ds_batch_s* self = nullptr;
+  std::vector<ds_batch_s*> batches;   // every batch that lists this handle (self included)
   bool tracing = false;
   int64_t kernels = 0;
   int last_iters = 0;
@@ -239,11 +243,22 @@ void wait_solved(ds_ctx* h) {
 
 void destroy_batch(ds_batch_s* b);
 
+// The handle's batches stop running: its control points change or (leaving) it goes away, and
+// then no batch keeps a pointer to it.
+void invalidate_batches(ds_ctx* h, bool leaving) {
+  for (ds_batch_s* b : h->batches) {
+    b->stale = true;
+    if (leaving) std::replace(b->hs.begin(), b->hs.end(), h, (ds_ctx*)nullptr);
+  }
+  if (leaving) h->batches.clear();
+}
+
 void free_cp(ds_ctx* h) {
   if (h->self) {
     destroy_batch(h->self);
     h->self = nullptr;
   }
+  invalidate_batches(h, false);
   dfree(h->d_g64); dfree(h->d_gc); dfree(h->d_q64); dfree(h->d_t64); dfree(h->d_node);
   dfree(h->d_pn); dfree(h->d_tp); dfree(h->d_tw); dfree(h->d_rank); dfree(h->d_seg);
   dfree(h->d_segbp); dfree(h->d_segstart); dfree(h->d_rowptr); dfree(h->d_rowcol); dfree(h->d_rowbp);
@@ -362,6 +377,8 @@ void trace(ds_batch_s* b, int it, int k) {
 
 void destroy_batch(ds_batch_s* b) {
   if (!b) return;
+  for (ds_ctx* h : b->hs)
+    if (h) h->batches.erase(std::remove(h->batches.begin(), h->batches.end(), b), h->batches.end());
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   if (b->ev_made)
@@ -386,8 +403,11 @@ void destroy_batch(ds_batch_s* b) {
 int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch_s** out) {
   *out = nullptr;
   if (n < 1) return DS_ERR_ARG;
-  for (int i = 0; i < n; ++i)
+  for (int i = 0; i < n; ++i) {
     if (!hs[i] || hs[i]->N == 0 || hs[i]->error) return DS_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return DS_ERR_ARG;   // one problem per handle
+  }
   const bool fp64 = hs[0]->prec_fp64;
   const int prec = hs[0]->prm.precision;
   const int steps = prec == DS_PREC_FP32 ? 0 : hs[0]->prm.refine_steps;
@@ -468,6 +488,7 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
       destroy_batch(b);
       return DS_ERR_CUDA;
     }
+  for (ds_ctx* h : b->hs) h->batches.push_back(b);
   *out = b;
   return DS_OK;
 }
@@ -1263,6 +1284,7 @@ int ds_batch_create(const ds_handle* hs, int32_t n, void* cuda_stream, ds_batch*
 int ds_batch_solve(ds_batch b, int32_t iters) {
   if (!b || iters < 1 || iters > DS_MAX_ITERS) return DS_ERR_ARG;
   if (b->error) return DS_ERR_CUDA;
+  if (b->stale) return DS_ERR_STATE;
   for (ds_ctx* h : b->hs)
     if (!h->have_frame || h->N == 0) return DS_ERR_STATE;
   bool graph = !b->no_graph;
@@ -1281,6 +1303,7 @@ int ds_batch_status(ds_batch b) {
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return DS_ERR_CUDA;
   int rc = batch_words_status(b);
   if (rc) return rc;
+  if (b->stale) return DS_OK;   // nothing ran since the change; the handles report their own
   for (ds_ctx* h : b->hs) {
     double st = 0;
     cudaMemcpy(&st, h->d_acc + ACC_STATUS, sizeof(double), cudaMemcpyDeviceToHost);
@@ -1562,6 +1585,7 @@ int ds_destroy(ds_handle h) {
     wait_solved(h);
     cudaStreamSynchronize(h->stream);
   }
+  invalidate_batches(h, true);
   free_cp(h);
   dfree(h->d_depth0); dfree(h->d_X64); dfree(h->d_pidx); dfree(h->d_depth); dfree(h->d_tpts);
   dfree(h->d_tnrm); dfree(h->d_midx); dfree(h->d_mxyz); dfree(h->d_hyp);

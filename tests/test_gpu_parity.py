@@ -375,6 +375,41 @@ def test_batch_rejects_mixed_precision(d, tiny):
     b.close()
 
 
+def test_batch_membership(d, tiny):
+    """A handle appears once per batch; new control points or a destroyed handle stop every
+    batch that lists it (DS_ERR_STATE) instead of running on stale tables; batches and handles
+    may be destroyed in either order."""
+    sc, fr = tiny, tiny.frames[0]
+    p = d.default_params(precision=2)
+    a = d.Solver(sc.template_depth, sc.K, sc.nodes, p)
+    c = d.Solver(sc.template_depth, sc.K, sc.nodes, p)
+    for s in (a, c):
+        s.submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+    with pytest.raises(d.DsError) as e:
+        d.ds_batch_create([a.h, c.h, a.h])
+    assert e.value.status == d.DS_ERR_ARG
+    b1 = d.ds_batch_create([a.h, c.h])
+    b2 = d.ds_batch_create([c.h])
+    d.ds_batch_solve(b1, 2)
+    d.ds_batch_status(b1)
+    d.ds_set_control_points(a.h, sc.nodes)        # same nodes, new tables: b1 is stale
+    with pytest.raises(d.DsError) as e:
+        d.ds_batch_solve(b1, 2)
+    assert e.value.status == d.DS_ERR_STATE
+    d.ds_batch_solve(b2, 2)                       # b2 does not list a
+    d.ds_batch_status(b2)
+    a.submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+    a.solve(2, stats=False)                       # a alone still works (its own batch)
+    a.deformation64()
+    c.close()                                     # destroyed before its batches
+    for b in (b1, b2):
+        with pytest.raises(d.DsError) as e:
+            d.ds_batch_solve(b, 2)
+        assert e.value.status == d.DS_ERR_STATE
+        d.ds_batch_destroy(b)
+    a.close()
+
+
 # ----------------------------------------------------------------------------- tensor-core factor
 
 
