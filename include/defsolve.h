@@ -272,6 +272,19 @@ int ds_ransac_noalloc(const float* depth0, int32_t W, int32_t H, ds_intrinsics K
                       double keep_frac, uint32_t* mask_bits, float* w_M, uint32_t* kept_bits,
                       double* score_nh, void* cuda_stream);
 
+/* Failure-detection self-test of the bounded device-side waits behind every hand-off between
+ * CTAs (the factorisation's tile counters and the triangular solves' row flags). One thread
+ * waits for a device flag that nothing sets, by acquire polling (kind 0: the waits of the SIMT
+ * factorisation and of the solves) or by polling with sleeps (kind 1: the tensor-core
+ * factorisation), with a budget of budget_ns (1e3..1e8 ns). With peer_error = 1 the error word
+ * is raised before the wait, as when another CTA has already given up, and the wait must end at
+ * once. No GPU fault is involved and the context stays usable. Synchronous (a stream of its
+ * own). Returns DS_ERR_TIMEOUT when the wait gave up (the designed outcome), DS_OK if it saw
+ * the flag, DS_ERR_ARG (kind, budget or peer_error out of range), DS_ERR_OOM, DS_ERR_CUDA.
+ * *waited_ms (may be NULL) receives the device time the wait took. */
+int ds_selftest_bounded_wait(int32_t kind, int64_t budget_ns, int32_t peer_error,
+                             double* waited_ms);
+
 /* Releases everything the handle owns. NULL is accepted. */
 int ds_destroy(ds_handle h);
 

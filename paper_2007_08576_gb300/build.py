@@ -15,7 +15,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdefsolve.so")
 
-SOURCES = ["api.cu", "frame.cu", "ransac.cu", "terms.cu", "chol.cu", "solve.cu", "orb.cu"]
+SOURCES = ["api.cu", "frame.cu", "ransac.cu", "terms.cu", "chol.cu", "solve.cu", "orb.cu",
+           "selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -28,8 +28,8 @@ EXPORTS = [
     "ds_batch_destroy", "ds_batch_set_tracing", "ds_batch_phase_times", "ds_batch_set_graph", "ds_get_deformation", "ds_get_deformation64",
     "ds_set_deformation", "ds_get_inlier_mask", "ds_get_ransac", "ds_get_cost",
     "ds_get_blend_table", "ds_get_frame_points", "ds_linearize", "ds_set_tracing",
-    "ds_get_phase_times", "ds_get_counters", "ds_ransac_noalloc", "ds_destroy", "ds_status_str",
-    "ds_version",
+    "ds_get_phase_times", "ds_get_counters", "ds_ransac_noalloc", "ds_selftest_bounded_wait",
+    "ds_destroy", "ds_status_str", "ds_version",
     "ds_orb_default_params", "ds_orb_create", "ds_orb_detect", "ds_orb_num_keypoints",
     "ds_orb_get_keypoints", "ds_orb_match", "ds_orb_num_matches", "ds_orb_get_matches",
     "ds_orb_match_device", "ds_orb_destroy",
@@ -117,6 +117,7 @@ def lib(path: str | None = None):
         "ds_get_counters": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
         "ds_ransac_noalloc": (i32, [vp, i32, i32, DsIntrinsics, vp, vp, i32, vp, i32, i32, f64,
                                     f64, vp, vp, vp, vp, vp]),
+        "ds_selftest_bounded_wait": (i32, [i32, ctypes.c_int64, i32, ctypes.POINTER(f64)]),
         "ds_destroy": (i32, [vp]),
         "ds_status_str": (ctypes.c_char_p, [i32]),
         "ds_version": (ctypes.c_char_p, []),
@@ -338,6 +339,16 @@ def ds_ransac_noalloc(depth0, W, H, K, match_idx, match_xyz, M, hyp, n_hyp, n_re
                                  _dev_ptr(mask_bits, 4), _dev_ptr(w_M, 4), _dev_ptr(kept_bits, 4),
                                  _dev_ptr(score_nh, 8), stream)
     _check("ds_ransac_noalloc", rc)
+
+
+def ds_selftest_bounded_wait(kind, budget_ns, peer_error=0):
+    """(status, device milliseconds) of one bounded wait on a flag that nothing sets (see
+    include/defsolve.h): DS_ERR_TIMEOUT is the designed outcome; other errors raise."""
+    ms = ctypes.c_double(0.0)
+    rc = lib().ds_selftest_bounded_wait(int(kind), int(budget_ns), int(peer_error), ctypes.byref(ms))
+    if rc not in (DS_OK, DS_ERR_TIMEOUT):
+        raise DsError("ds_selftest_bounded_wait", rc)
+    return rc, ms.value
 
 
 def ds_destroy(h):

@@ -61,3 +61,9 @@ def test_argument_errors_need_no_gpu(built):
     h = ctypes.c_void_p()
     K = d.DsIntrinsics(80.0, 80.0, 39.5, 29.5)
     assert L.ds_create_template(None, 80, 60, K, None, None, ctypes.byref(h)) == d.DS_ERR_ARG
+    # the bounded-wait self-test checks its arguments before touching the device
+    ms = ctypes.c_double()
+    assert L.ds_selftest_bounded_wait(2, 1000000, 0, ctypes.byref(ms)) == d.DS_ERR_ARG
+    assert L.ds_selftest_bounded_wait(0, 10, 0, ctypes.byref(ms)) == d.DS_ERR_ARG
+    assert L.ds_selftest_bounded_wait(0, 10**9, 0, ctypes.byref(ms)) == d.DS_ERR_ARG
+    assert L.ds_selftest_bounded_wait(1, 1000000, 3, ctypes.byref(ms)) == d.DS_ERR_ARG

@@ -410,6 +410,26 @@ def test_batch_membership(d, tiny):
     a.close()
 
 
+def test_bounded_waits_give_up_and_the_context_stays_usable(d, tiny):
+    """Failure detection without a GPU fault: a wait on a flag that nothing sets gives up after
+    its budget with DS_ERR_TIMEOUT (both wait helpers of the hand-offs between CTAs); with the
+    error word already raised by a peer it ends at once; afterwards a frame still solves to the
+    oracle."""
+    for kind in (0, 1):
+        st, ms = d.ds_selftest_bounded_wait(kind, 2_000_000)
+        assert st == d.DS_ERR_TIMEOUT
+        assert 2.0 <= ms < 1000.0
+        st, ms = d.ds_selftest_bounded_wait(kind, 50_000_000, peer_error=1)
+        assert st == d.DS_ERR_TIMEOUT
+        assert ms < 5.0
+    sc, fr = tiny, tiny.frames[0]
+    p = d.default_params(precision=2)
+    s, st, q, t = gpu_frame(d, sc, fr, p)
+    tpl, res = _oracle(sc, fr, oracle_params(p))
+    assert np.abs(tpl.g + t - res.pos).max() <= POS_TOL_MM
+    s.close()
+
+
 # ----------------------------------------------------------------------------- tensor-core factor
 
 
