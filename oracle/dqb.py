@@ -20,7 +20,8 @@ from .quat import CONJ, pure, qconj, qexp_half, qL, qmul, qR, rotmat, skew
 
 
 def node_dq(q, t, g):
-    """Dual quaternions (N, 8) of the node transforms."""
+    """Dual quaternions (N, 8) of the node transforms.
+    Section 2: each control point's warp W_i as a dual quaternion."""
     R = rotmat(q)
     T = g + t - np.einsum("nij,nj->ni", R, g)
     d = 0.5 * qmul(pure(T), q)
@@ -33,7 +34,8 @@ def node_dq_jac(q, t, g):
     Real part:  d q / d dtheta = 1/2 qR(q)[:, 1:4]     (from (0, dtheta/2) (x) q)
     Dual part:  d = 1/2 (0, T) (x) q, with dT/d dtheta = [R g]x and dT/d dt = I, so by the
                 product rule d d / d dtheta = 1/2 qL((0,T)) (d q / d dtheta)
-                + 1/2 qR(q)[:, 1:4] [R g]x  and  d d / d dt = 1/2 qR(q)[:, 1:4]."""
+                + 1/2 qR(q)[:, 1:4] [R g]x  and  d d / d dt = 1/2 qR(q)[:, 1:4].
+    Derivative of Section 2's node dual quaternion for the Gauss-Newton step."""
     N = q.shape[0]
     R = rotmat(q)
     Rg = np.einsum("nij,nj->ni", R, g)
@@ -51,7 +53,8 @@ def blend(dq, nid, alpha, near):
     """b_j = sum_k alpha_jk s_jk dq[nid_jk] with s_jk = sign(q_nid_jk . q_near_j) (+1 on 0).
 
     dq: (N, 8); nid, alpha: (P, 4); near: (P,) node id of each point's nearest node.
-    Returns b (P, 8) and the signs s (P, 4)."""
+    Returns b (P, 8) and the signs s (P, 4).
+    Section 2: a template point follows the interpolation of its neighbouring control points."""
     qk = dq[nid, 0:4]                           # (P, 4, 4)
     qn = dq[near, 0:4]                          # (P, 4)
     s = np.where(np.einsum("pki,pi->pk", qk, qn) >= 0, 1.0, -1.0)
@@ -60,7 +63,8 @@ def blend(dq, nid, alpha, near):
 
 
 def apply_dq(b, p):
-    """x' = (vec(b_r (x) (0,p) (x) b_r*) + 2 vec(b_d (x) b_r*)) / |b_r|^2.  b (P,8), p (P,3)."""
+    """x' = (vec(b_r (x) (0,p) (x) b_r*) + 2 vec(b_d (x) b_r*)) / |b_r|^2.  b (P,8), p (P,3).
+    Section 2: the blended dual quaternion applied to a template point."""
     br, bd = b[:, 0:4], b[:, 4:8]
     y = qmul(qmul(br, pure(p)), qconj(br))[:, 1:4] + 2.0 * qmul(bd, qconj(br))[:, 1:4]
     s = (br * br).sum(1)
@@ -70,7 +74,8 @@ def apply_dq(b, p):
 def apply_dq_jac(b, p):
     """d x' / d b: (P, 3, 8), from x' = y / s with s = |b_r|^2 and
        dy/db_r = Pv [qR((0,p) (x) b_r*) + qL(b_r (x) (0,p)) CONJ + 2 qL(b_d) CONJ],
-       dy/db_d = 2 Pv qR(b_r*),  ds/db_r = 2 b_r."""
+       dy/db_d = 2 Pv qR(b_r*),  ds/db_r = 2 b_r.
+    Derivative of Section 2's warp of a point for the Gauss-Newton step."""
     br, bd = b[:, 0:4], b[:, 4:8]
     pp = pure(p)
     brc = qconj(br)
@@ -85,7 +90,8 @@ def apply_dq_jac(b, p):
 
 
 def warp_points(q, t, g, p, nid, alpha, near, with_jac=True):
-    """Warped points x' (P, 3) and, if asked, d x' / d(dtheta, dt) of the 4 nodes: (P, 3, 4, 6)."""
+    """Warped points x' (P, 3) and, if asked, d x' / d(dtheta, dt) of the 4 nodes: (P, 3, 4, 6).
+    Section 2: the deformed template."""
     dq = node_dq(q, t, g)
     b, s = blend(dq, nid, alpha, near)
     x = apply_dq(b, p)
@@ -99,7 +105,8 @@ def warp_points(q, t, g, p, nid, alpha, near, with_jac=True):
 
 def apply_step(q, t, delta):
     """Node update of the Gauss-Newton step delta (N*6,): q <- normalize(exp(dtheta/2) (x) q),
-    flipped to q_w >= 0; t <- t + dt."""
+    flipped to q_w >= 0; t <- t + dt.
+    Section 2: the Levenberg-Marquardt update of every W_i, taken as a damped Gauss-Newton step."""
     d = np.asarray(delta, dtype=np.float64).reshape(-1, 6)
     qn = qmul(qexp_half(d[:, 0:3]), q)
     qn = qn / np.linalg.norm(qn, axis=1, keepdims=True)

@@ -11,7 +11,8 @@ def backproject(depth, K):
     """X(u, v) = ((u - cx) z / fx, (v - cy) z / fy, z); valid where z > 0 and finite.
 
     depth: (H, W) array (any float dtype, widened to float64).  K = (fx, fy, cx, cy).
-    Returns X (H, W, 3) float64 and valid (H, W) bool."""
+    Returns X (H, W, 3) float64 and valid (H, W) bool.
+    Section 2: the point maps of the template and of the live depth."""
     fx, fy, cx, cy = (float(k) for k in K)
     z = np.asarray(depth, dtype=np.float64)
     H, W = z.shape
@@ -29,7 +30,8 @@ def target_normals(X, valid):
     flipped so that n_z <= 0 (toward the camera).  A pixel is usable when it and its four
     neighbours are valid, it is not on the image border and |c| > 0.
 
-    Returns n (H, W, 3) and usable (H, W) bool."""
+    Returns n (H, W, 3) and usable (H, W) bool.
+    Section 2, ICP paragraph: the normals of the point-to-plane distance."""
     H, W, _ = X.shape
     n = np.zeros_like(X)
     ok = np.zeros((H, W), dtype=bool)

@@ -49,7 +49,8 @@ class OrbParams:
 
 
 def fast_circle():
-    """The 16 offsets (dx, dy) of the radius-3 digital circle in increasing angle."""
+    """The 16 offsets (dx, dy) of the radius-3 digital circle in increasing angle.
+    Section 2.1: FAST corners."""
     pts = [(dx, dy) for dy in range(-3, 4) for dx in range(-3, 4)
            if round(math.hypot(dx, dy)) == 3]
     pts.sort(key=lambda p: math.atan2(p[1], p[0]))
@@ -58,7 +59,8 @@ def fast_circle():
 
 def fast_scores(img, t):
     """FAST-9 response of every pixel (int64 (H, W)); 0 for non-corners and for pixels whose
-    circle leaves the image."""
+    circle leaves the image.
+    Section 2.1: FAST corners and their responses."""
     I = np.asarray(img, dtype=np.int64)
     H, W = I.shape
     out = np.zeros((H, W), dtype=np.int64)
@@ -83,7 +85,8 @@ def fast_scores(img, t):
 
 
 def suppress(score, border, depth=None):
-    """Keep mask of the uniform detection (see the module notes)."""
+    """Keep mask of the uniform detection (see the module notes).
+    Section 2.1: a corner is dropped when a neighbour has a larger response."""
     H, W = score.shape
     keep = score > 0
     inner = np.zeros_like(keep)
@@ -101,12 +104,14 @@ def suppress(score, border, depth=None):
 
 
 def disc_offsets(radius=15):
+    """The patch of ORB's intensity-centroid orientation (Section 2.1 uses ORB features)."""
     return [(dx, dy) for dy in range(-radius, radius + 1) for dx in range(-radius, radius + 1)
             if dx * dx + dy * dy <= radius * radius]
 
 
 def orientation(img, pix, nbins=32):
-    """(theta, bin) of each keypoint pixel."""
+    """(theta, bin) of each keypoint pixel.
+    Section 2.1 (ORB features): intensity-centroid orientation."""
     I = np.asarray(img, dtype=np.int64)
     H, W = I.shape
     u = np.asarray(pix) % W
@@ -124,7 +129,8 @@ def orientation(img, pix, nbins=32):
 
 
 def rotated_pattern(pattern, nbins=32):
-    """Integer test offsets (nbins, 256, 4): the pattern rotated by 2 pi k / nbins, rounded."""
+    """Integer test offsets (nbins, 256, 4): the pattern rotated by 2 pi k / nbins, rounded.
+    Section 2.1 (ORB features): the steered test pattern."""
     pattern = np.asarray(pattern, dtype=np.float64)
     out = np.zeros((nbins, pattern.shape[0], 4), dtype=np.int64)
     for k in range(nbins):
@@ -138,7 +144,8 @@ def rotated_pattern(pattern, nbins=32):
 
 
 def box5(img):
-    """5 x 5 box sums (int64 (H, W)), 0 within 2 pixels of the edge."""
+    """5 x 5 box sums (int64 (H, W)), 0 within 2 pixels of the edge.
+    Section 2.1 (ORB features): the smoothed intensities the binary tests compare."""
     I = np.asarray(img, dtype=np.int64)
     H, W = I.shape
     out = np.zeros((H, W), dtype=np.int64)
@@ -151,7 +158,8 @@ def box5(img):
 
 
 def descriptors(img, pix, bins, pattern, nbins=32):
-    """(K, 8) uint32 steered binary descriptors."""
+    """(K, 8) uint32 steered binary descriptors.
+    Section 2.1 (ORB features): steered binary descriptors."""
     W = img.shape[1]
     S = box5(img)
     tab = rotated_pattern(pattern, nbins)[np.asarray(bins)]       # (K, 256, 4)
@@ -167,7 +175,8 @@ def descriptors(img, pix, bins, pattern, nbins=32):
 
 
 def detect(img, depth, pattern, prm: OrbParams = OrbParams()):
-    """Keypoints of one image: dict with pix (ascending), score, theta, bin, desc."""
+    """Keypoints of one image: dict with pix (ascending), score, theta, bin, desc.
+    Section 2.1: uniform ORB detection and description of one image."""
     sc = fast_scores(img, prm.fast_t)
     keep = suppress(sc, prm.border, depth)
     pix = np.flatnonzero(keep)[:prm.max_kp]
@@ -183,7 +192,8 @@ _POP8 = np.array([bin(i).count("1") for i in range(256)], dtype=np.uint16)
 
 def hamming(D1, D2, rows=128):
     """(n1, n2) Hamming distances between two sets of 256-bit descriptors (popcount of the XOR;
-    evaluated `rows` descriptors of D1 at a time to bound memory)."""
+    evaluated `rows` descriptors of D1 at a time to bound memory).
+    Section 2.1: the distance the template and live features are matched by."""
     D1 = np.ascontiguousarray(D1, np.uint32)
     D2 = np.ascontiguousarray(D2, np.uint32)
     out = np.empty((len(D1), len(D2)), dtype=np.int64)
@@ -194,7 +204,8 @@ def hamming(D1, D2, rows=128):
 
 
 def match(Dt, Dl, max_dist):
-    """Mutual nearest neighbours within max_dist: (t index, l index, distance), ascending t."""
+    """Mutual nearest neighbours within max_dist: (t index, l index, distance), ascending t.
+    Section 2.1: template features matched to a live frame."""
     if len(Dt) == 0 or len(Dl) == 0:
         e = np.zeros(0, dtype=np.int64)
         return e, e.copy(), e.copy()
@@ -208,7 +219,8 @@ def match(Dt, Dl, max_dist):
 
 
 def match_points(tmpl, live, live_depth, K, max_dist):
-    """The matches as the solve's inputs: template pixel per match and the live 3D point."""
+    """The matches as the solve's inputs: template pixel per match and the live 3D point.
+    Eq. 2: the matched 3D points o1 (template) and o2 (live)."""
     ti, li, dist = match(tmpl["desc"], live["desc"], max_dist)
     fx, fy, cx, cy = (float(k) for k in K)
     W = np.asarray(live_depth).shape[1]

@@ -6,7 +6,8 @@ import numpy as np
 
 
 def qmul(a, b):
-    """Hamilton product, broadcasting over leading axes."""
+    """Hamilton product, broadcasting over leading axes.
+    Quaternion algebra of Section 2's dual-quaternion warp."""
     a0, a1, a2, a3 = np.moveaxis(np.asarray(a, dtype=np.float64), -1, 0)
     b0, b1, b2, b3 = np.moveaxis(np.asarray(b, dtype=np.float64), -1, 0)
     return np.stack([a0 * b0 - a1 * b1 - a2 * b2 - a3 * b3,
@@ -16,6 +17,7 @@ def qmul(a, b):
 
 
 def qconj(q):
+    """Quaternion conjugate (algebra of Section 2's dual-quaternion warp)."""
     q = np.asarray(q, dtype=np.float64)
     return q * np.array([1.0, -1.0, -1.0, -1.0])
 
@@ -24,7 +26,8 @@ CONJ = np.diag([1.0, -1.0, -1.0, -1.0])
 
 
 def qL(a):
-    """Left-product matrix: a (x) b = qL(a) @ b.  Shape (..., 4, 4)."""
+    """Left-product matrix: a (x) b = qL(a) @ b.  Shape (..., 4, 4).
+    Quaternion algebra of Section 2's dual-quaternion warp."""
     a0, a1, a2, a3 = np.moveaxis(np.asarray(a, dtype=np.float64), -1, 0)
     return np.stack([np.stack([a0, -a1, -a2, -a3], -1),
                      np.stack([a1, a0, -a3, a2], -1),
@@ -33,7 +36,8 @@ def qL(a):
 
 
 def qR(b):
-    """Right-product matrix: a (x) b = qR(b) @ a.  Shape (..., 4, 4)."""
+    """Right-product matrix: a (x) b = qR(b) @ a.  Shape (..., 4, 4).
+    Quaternion algebra of Section 2's dual-quaternion warp."""
     b0, b1, b2, b3 = np.moveaxis(np.asarray(b, dtype=np.float64), -1, 0)
     return np.stack([np.stack([b0, -b1, -b2, -b3], -1),
                      np.stack([b1, b0, b3, -b2], -1),
@@ -42,13 +46,15 @@ def qR(b):
 
 
 def pure(v):
-    """Embed 3-vectors as pure quaternions (0, v)."""
+    """Embed 3-vectors as pure quaternions (0, v).
+    Quaternion algebra of Section 2's dual-quaternion warp."""
     v = np.asarray(v, dtype=np.float64)
     return np.concatenate([np.zeros(v.shape[:-1] + (1,)), v], axis=-1)
 
 
 def rotmat(q):
-    """Rotation matrix of a unit quaternion: R v = vec(q (x) (0, v) (x) q*)."""
+    """Rotation matrix of a unit quaternion: R v = vec(q (x) (0, v) (x) q*).
+    Quaternion algebra of Section 2's dual-quaternion warp."""
     q = np.asarray(q, dtype=np.float64)
     w, x, y, z = np.moveaxis(q, -1, 0)
     return np.stack([np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], -1),
@@ -58,7 +64,8 @@ def rotmat(q):
 
 
 def qexp_half(theta):
-    """Unit quaternion of the rotation vector theta: (cos(|theta|/2), sin(|theta|/2) theta/|theta|)."""
+    """Unit quaternion of the rotation vector theta: (cos(|theta|/2), sin(|theta|/2) theta/|theta|).
+    The rotation increment of Section 2's Gauss-Newton step."""
     theta = np.asarray(theta, dtype=np.float64)
     a = np.linalg.norm(theta, axis=-1)
     safe = np.where(a > 0, a, 1.0)
@@ -67,7 +74,8 @@ def qexp_half(theta):
 
 
 def skew(v):
-    """[v]x with [v]x u = v x u.  Shape (..., 3, 3)."""
+    """[v]x with [v]x u = v x u.  Shape (..., 3, 3).
+    Cross-product matrix (algebra of Section 2's warp Jacobians)."""
     v = np.asarray(v, dtype=np.float64)
     z = np.zeros(v.shape[:-1])
     x, y, w = np.moveaxis(v, -1, 0)

@@ -21,7 +21,8 @@ import numpy as np
 
 
 def kabsch(S1, S2, w):
-    """Weighted rotation R maximising sum_k w_k S2(k)^T R S1(k).  S1, S2: (M, 3); w: (M,)."""
+    """Weighted rotation R maximising sum_k w_k S2(k)^T R S1(k).  S1, S2: (M, 3); w: (M,).
+    Eq. 3: the rotation of the 1-point RANSAC fit."""
     C = (S2 * w[:, None]).T @ S1
     if w.sum() < 1e-12:
         return np.eye(3)
@@ -75,7 +76,8 @@ def ransac_1p(o1, o2, hyp, H, n_reweight=10, keep_frac=0.5):
       what  (M,)        weight of each match (max over kept references)
       kept  (NH,) bool  kept references
       score (NH,)       sum_{k != k0} w_k per reference
-      d, w  (NH, M)     final distances and weights per reference."""
+      d, w  (NH, M)     final distances and weights per reference.
+    Section 2.1, Eq. 2-4: 1-point RANSAC with reweighting and the preselection it gives."""
     o1 = np.asarray(o1, dtype=np.float64)
     o2 = np.asarray(o2, dtype=np.float64)
     NH = len(hyp)

@@ -70,7 +70,8 @@ class Template:
 
 def nearest_nodes(p, g, k=4, chunk=8192):
     """k nearest nodes of every point by squared distance (dx^2 + dy^2) + dz^2, ties to the lower
-    node id.  Returns (ids (P, k), squared distances (P, k))."""
+    node id.  Returns (ids (P, k), squared distances (P, k)).
+    Section 2: a template point's neighbouring control points."""
     P = p.shape[0]
     ids = np.zeros((P, k), dtype=np.int64)
     d2k = np.zeros((P, k))
@@ -87,7 +88,8 @@ def nearest_nodes(p, g, k=4, chunk=8192):
 
 
 def setup_template(depth, K, nodes, prm: Params = Params()):
-    """Back-project the template, place the control points and build the blend tables."""
+    """Back-project the template, place the control points and build the blend tables.
+    Section 2: template, control points and blending."""
     H, W = depth.shape
     X0, valid0 = frame.backproject(depth, K)
     X0 = X0.reshape(-1, 3)
@@ -118,13 +120,15 @@ class Target:
 
 
 def prepare_target(depth, K):
+    """Section 2: the live point map and normals the ICP term associates with."""
     X, valid = frame.backproject(depth, K)
     n, ok = frame.target_normals(X, valid)
     return Target(X, n, ok)
 
 
 def assemble(rows_list, n):
-    """A = sum W J^T J (dense n x n), b = -sum W J^T r."""
+    """A = sum W J^T J (dense n x n), b = -sum W J^T r.
+    Section 2: the normal equations of Eq. 1 for the Cholesky solve."""
     A = np.zeros((n, n))
     b = np.zeros(n)
     for rw in rows_list:
@@ -171,7 +175,8 @@ def data_terms(tpl: Template, tgt: Target, q, t, orb, prm: Params):
 
 
 def template_rank(tpl: Template, pix):
-    """Position of each template pixel in the list of valid template points."""
+    """Position of each template pixel in the list of valid template points.
+    Section 2.1: the template point o1 of a match (Eq. 2)."""
     rank = np.full(tpl.W * tpl.H, -1, dtype=np.int64)
     rank[tpl.pidx] = np.arange(tpl.pidx.shape[0])
     return rank[np.asarray(pix, dtype=np.int64)]
@@ -190,7 +195,8 @@ def ransac_o1(tpl: Template, midx, q, t, prm: Params):
 
 def linearize(tpl: Template, tgt: Target, q, t, orb, w_arap, prm: Params):
     """Normal equations (undamped) and cost at state (q, t).  If w_arap is None it is set from
-    the data-term weights at this state (the per-frame rule) and returned in the result."""
+    the data-term weights at this state (the per-frame rule) and returned in the result.
+    Eq. 1: f_ICP + w_ORB f_ORB + w_ARAP f_ARAP and its normal equations."""
     rows, c_icp, c_orb, ws_icp, ws_orb, pix, valid = data_terms(tpl, tgt, q, t, orb, prm)
     N = tpl.g.shape[0]
     if w_arap is None:
@@ -204,7 +210,8 @@ def linearize(tpl: Template, tgt: Target, q, t, orb, w_arap, prm: Params):
 
 
 def damp(A, prm: Params):
-    """A + lambda (diag(A) + eps) on the diagonal."""
+    """A + lambda (diag(A) + eps) on the diagonal.
+    Section 2 (Levenberg-Marquardt): the damping of the normal equations."""
     Ad = A.copy()
     idx = np.arange(A.shape[0])
     Ad[idx, idx] += prm.lam * (np.diag(A) + prm.eps)
@@ -244,7 +251,8 @@ class FrameResult:
 
 def solve_frame(tpl: Template, depth, match_idx, match_xyz, hyp, prm: Params = Params(), iters=10,
                 q0=None, t0=None, keep_lins=False):
-    """One frame: target prep, 1-point RANSAC, then `iters` damped Gauss-Newton iterations."""
+    """One frame: target prep, 1-point RANSAC, then `iters` damped Gauss-Newton iterations.
+    Sections 2 and 2.1: one frame's whole deformation solve."""
     N = tpl.g.shape[0]
     q = np.tile([1.0, 0.0, 0.0, 0.0], (N, 1)) if q0 is None else np.asarray(q0, np.float64).copy()
     t = np.zeros((N, 3)) if t0 is None else np.asarray(t0, np.float64).copy()

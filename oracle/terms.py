@@ -25,13 +25,15 @@ class Rows:
 
 
 def tukey_weight(r, c):
-    """IRLS weight of Tukey's biweight: (1 - (r/c)^2)^2 for |r| < c, else 0."""
+    """IRLS weight of Tukey's biweight: (1 - (r/c)^2)^2 for |r| < c, else 0.
+    Section 2, ICP paragraph: Tukey's penalty on the point-to-plane residual."""
     u = r / c
     return np.where(np.abs(r) < c, (1.0 - u * u) ** 2, 0.0)
 
 
 def tukey_rho(r, c):
-    """Tukey's penalty c^2/6 (1 - (1 - (r/c)^2)^3), capped at c^2/6 for |r| >= c."""
+    """Tukey's penalty c^2/6 (1 - (1 - (r/c)^2)^3), capped at c^2/6 for |r| >= c.
+    Section 2, ICP paragraph: Tukey's penalty on the point-to-plane residual."""
     u = r / c
     return np.where(np.abs(r) < c, c * c / 6.0 * (1.0 - (1.0 - u * u) ** 3), c * c / 6.0)
 
