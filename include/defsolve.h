@@ -42,7 +42,8 @@ typedef enum {
   DS_ERR_ARG = 1,       /* a null pointer, a size out of range, an index outside the image  */
   DS_ERR_OOM = 2,       /* a device allocation failed                                       */
   DS_ERR_BAD_INPUT = 3, /* non-finite depth or match coordinates                             */
-  DS_ERR_NOT_SPD = 4,   /* a Cholesky pivot <= 0 even after the damping retries              */
+  DS_ERR_NOT_SPD = 4,   /* a Cholesky pivot <= 0 (or NaN); it was replaced by 1 so that the
+                           iteration stays finite, and the frame's result is not reliable     */
   DS_ERR_STATE = 5,     /* call order violated (e.g. solve before submit_frame)              */
   DS_ERR_TIMEOUT = 6,   /* a bounded device-side wait gave up                                */
   DS_ERR_CUDA = 7       /* any other CUDA runtime error                                      */
