@@ -131,7 +131,7 @@ typedef struct {
 void ds_default_params(ds_params* p);
 
 /* Creates a handle from a template depth map (Section 2: the template is generated from the
- * first frame). depth_hw: H x W FP32 depths in mm, <= 0 or non-finite = no surface.
+ * first frame). depth_hw: H x W FP32 depths in mm, <= 0 = no surface (NaN / inf are rejected).
  * W, H in [8, 4096]. p may be NULL (defaults). cuda_stream: the cudaStream_t to run on, or
  * NULL for a stream owned by the handle. On success *out receives the handle.
  * Errors: DS_ERR_ARG, DS_ERR_BAD_INPUT (NaN/inf depth), DS_ERR_OOM, DS_ERR_CUDA. */
@@ -151,8 +151,9 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N);
  * (Section 2.1). Runs the frame preparation (live points and normals) and the RANSAC
  * preselection on the handle's stream. M in [0, 65536]; with M == 0 hyp_list may be NULL.
  * Host-memory indices are checked before the call returns. Device-memory indices are checked
- * on the device without a host synchronisation: an out-of-range template pixel or reference id
- * is replaced by 0 before any kernel reads it, and the next synchronising call (ds_solve with
+ * on the device without a host synchronisation: an out-of-range template pixel (or one without
+ * a template point) is replaced by the first valid template pixel and an out-of-range reference
+ * id by 0 before any kernel reads them, and the next synchronising call (ds_solve with
  * stats, any ds_get_*) returns DS_ERR_ARG. Non-finite depth or match coordinates are reported
  * the same way as DS_ERR_BAD_INPUT.
  * A handle keeps two frame slots: a frame goes to the slot the last solve did not read, so it
