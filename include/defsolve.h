@@ -167,7 +167,9 @@ int ds_submit_frame(ds_handle h, const float* depth_hw, const int32_t* match_tmp
 /* Runs `iters` damped Gauss-Newton iterations (1..DS_MAX_ITERS) of Eq. 1 on the submitted
  * frame, starting from the current warps (warm start). Asynchronous unless `out` is not NULL,
  * in which case the stream is synchronised and *out filled.
- * Errors: DS_ERR_ARG, DS_ERR_STATE (no frame), DS_ERR_NOT_SPD, DS_ERR_CUDA. */
+ * Errors: DS_ERR_ARG (also a bad device-side index of the frame), DS_ERR_STATE (no frame),
+ * DS_ERR_BAD_INPUT (non-finite frame data), DS_ERR_NOT_SPD, DS_ERR_TIMEOUT, DS_ERR_CUDA; the
+ * errors found on the device are returned by the synchronising calls. */
 int ds_solve(ds_handle h, int32_t iters, ds_solve_stats* out);
 
 /* Batched solves of uneven problems. A batch groups n handles (same precision and refinement
