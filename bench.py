@@ -5,7 +5,8 @@ Workload: concurrent streams of the 320x240 / 256-control-point / 2000-match seq
 frame preparation, 1-point RANSAC preselection and 10 damped Gauss-Newton iterations (ICP + ORB +
 dense ARAP, assembly, Cholesky, solves, update), warm-started from the stream's previous frame.
 A step is one frame of every one of S streams (default 32), solved as one batch in mixed
-precision (FP32 J^T J and factorisation, FP64 refinement residuals).
+precision (FP32 J^T J and factorisation; two refinement steps whose residuals are accumulated
+in double-float FP32 arithmetic, ~48 bits).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32_refine|fp32|fp64]
   python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
