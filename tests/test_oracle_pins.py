@@ -756,3 +756,28 @@ def test_warm_o1_is_invariant_to_quaternion_signs():
     flip = rng.uniform(size=N) < 0.5
     b = solver.ransac_o1(tpl, f.match_idx, np.where(flip[:, None], -q, q), t, prm)
     assert flip.any() and np.abs(a - b).max() < 1e-9
+
+
+def test_dynamic_arap_weight_counts_the_data_weights(tiny):
+    """Section 2 (after Eq. 1): w_ARAP scales with the summed ICP and ORB weights per control
+    point.  Live depth = template depth at the identity: every ICP association has residual 0
+    (Tukey weight 1) on exactly the usable target pixels, and matches to the template's own
+    points are all preselected with weight 1, so w_ARAP = w_arap0 (usable pixels + w_ORB M) / N."""
+    sc, tpl = tiny
+    prm = solver.Params()
+    N = tpl.g.shape[0]
+    rng = np.random.default_rng(5)
+    midx = rng.choice(tpl.pidx, size=40, replace=False)
+    o2 = tpl.X0[midx]
+    rs = ransac.ransac_1p(o2, o2, np.arange(30), prm.H, prm.n_reweight, prm.keep_frac)
+    assert rs["mask"].all()
+    tgt = solver.prepare_target(sc.template_depth, sc.K)
+    usable = int(np.asarray(tgt.ok).reshape(-1)[tpl.pidx].sum())
+    q = np.tile([1.0, 0.0, 0.0, 0.0], (N, 1))
+    lin, w = solver.linearize(tpl, tgt, q, np.zeros((N, 3)), (midx, o2, rs["mask"], rs["what"]),
+                              None, prm)
+    assert lin.n_icp == usable and lin.wsum_icp == pytest.approx(usable, rel=1e-12)
+    assert lin.wsum_orb == pytest.approx(40.0, rel=1e-12)
+    assert w == pytest.approx(prm.w_arap0 * (usable + prm.w_orb * 40) / N, rel=1e-12)
+    # the ICP and ORB costs vanish with the residuals; the ARAP term is zero at the identity
+    assert lin.cost_icp < 1e-20 and lin.cost_orb < 1e-20 and lin.cost_arap < 1e-20
