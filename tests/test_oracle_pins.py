@@ -781,3 +781,26 @@ def test_dynamic_arap_weight_counts_the_data_weights(tiny):
     assert w == pytest.approx(prm.w_arap0 * (usable + prm.w_orb * 40) / N, rel=1e-12)
     # the ICP and ORB costs vanish with the residuals; the ARAP term is zero at the identity
     assert lin.cost_icp < 1e-20 and lin.cost_orb < 1e-20 and lin.cost_arap < 1e-20
+
+
+def test_arap_cost_closed_form_two_nodes():
+    """Eq. 5-6 on two control points 10 mm apart (pair weight w, both ordered pairs), against
+    costs written out by hand: node 1 turned by theta about an axis across the pair (length kept;
+    pair (1, 2) sees the angle theta, both pairs the quaternion difference of a theta / 2 turn),
+    then node 2 moved sideways by d (no rotation; both pairs see the length change and the angle
+    atan(d / 10))."""
+    g = np.array([[0.0, 0.0, 100.0], [10.0, 0.0, 100.0]])
+    w, w_arap, w_angle, w_rot = 0.7, 1.3, 20.0, 100.0
+    wpair = np.array([[0.0, w], [w, 0.0]])
+    th = 0.3
+    q = np.array([[math.cos(th / 2), 0.0, 0.0, math.sin(th / 2)], [1.0, 0.0, 0.0, 0.0]])
+    _, c = terms.arap_rows(q, np.zeros((2, 3)), g, wpair, w_arap, w_angle, w_rot)
+    want = 0.5 * w_arap * w * (w_angle * (2 - 2 * math.cos(th))
+                               + w_rot * 2 * (2 - 2 * math.cos(th / 2)))
+    assert c == pytest.approx(want, rel=1e-12)
+    dd = 4.0
+    ell = math.hypot(10.0, dd)
+    t = np.array([[0.0, 0.0, 0.0], [0.0, dd, 0.0]])
+    _, c = terms.arap_rows(np.tile([1.0, 0, 0, 0], (2, 1)), t, g, wpair, w_arap, w_angle, w_rot)
+    want = 0.5 * w_arap * w * (2 * (ell - 10.0) ** 2 + w_angle * 2 * (2 - 2 * 10.0 / ell))
+    assert c == pytest.approx(want, rel=1e-12)
