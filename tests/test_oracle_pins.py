@@ -804,3 +804,27 @@ def test_arap_cost_closed_form_two_nodes():
     _, c = terms.arap_rows(np.tile([1.0, 0, 0, 0], (2, 1)), t, g, wpair, w_arap, w_angle, w_rot)
     want = 0.5 * w_arap * w * (2 * (ell - 10.0) ** 2 + w_angle * 2 * (2 - 2 * 10.0 / ell))
     assert c == pytest.approx(want, rel=1e-12)
+
+
+def test_point_to_plane_ignores_tangential_offsets():
+    """Section 2, ICP paragraph: only the distance along the live surface's normal counts.  On a
+    fronto-parallel plane at 100 mm (normal (0, 0, -1), towards the camera), points moved off
+    the plane by delta along the normal and anywhere within it have residual exactly delta,
+    whichever pixel they land on, and the cost is the Tukey penalty of those deltas."""
+    W, H = 80, 60
+    K = (80.0, 80.0, 39.5, 29.5)
+    tgt = solver.prepare_target(np.full((H, W), 100.0), K)
+    rng = np.random.default_rng(11)
+    P = 300
+    u = rng.uniform(6, W - 7, P)
+    v = rng.uniform(6, H - 7, P)
+    delta = rng.uniform(-3.0, 3.0, P)
+    x = np.stack([(u - K[2]) * 100.0 / K[0], (v - K[3]) * 100.0 / K[1], np.full(P, 100.0)], 1)
+    x[:, 2] -= delta                       # + delta along n = (0, 0, -1)
+    rows, cost, wsum, pix, valid = terms.icp_rows(x, np.zeros((P, 3, 4, 6)),
+                                                  np.zeros((P, 4), dtype=np.int64), tgt.X,
+                                                  tgt.n, tgt.ok, K, W, H, 10.0)
+    assert valid.all()
+    assert np.abs(rows.r - delta).max() < 1e-12
+    assert cost == pytest.approx(terms.tukey_rho(delta, 10.0).sum(), rel=1e-12)
+    assert wsum == pytest.approx(terms.tukey_weight(delta, 10.0).sum(), rel=1e-12)
