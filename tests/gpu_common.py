@@ -6,7 +6,7 @@ from oracle import solver
 from synth import make_scene
 from synth.scene import Config
 
-# Tolerances (the benchmark spec's): control points within 1e-3 mm, cost within 1e-5 relative,
+# Parity tolerances: control points within 1e-3 mm, cost within 1e-5 relative,
 # RANSAC masks bit-exact outside the 1e-6 mm band around H.
 POS_TOL_MM = 1e-3
 COST_RTOL = 1e-5
