@@ -46,7 +46,7 @@ FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x ma
 # (`ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_chol_dag -s 2 -c 1 ...`).
 # It describes the kernel source it was taken on (first 16 hex digits of the sha256 of
 # csrc/chol.cu + csrc/dev_util.cuh) and is reported as null for any other.
-CHOL_TRAFFIC = {"chol_sha256": "8c5b33a357e51b2c", "precision": 2, "streams": 32,
+CHOL_TRAFFIC = {"chol_sha256": "a3f5333f6fac6ff8", "precision": 2, "streams": 32,
                 "bytes": 663056896 + 355572480}
 
 

@@ -97,7 +97,7 @@ typedef struct {
   int32_t solver;           /* 0 = one Cholesky of the dense 6N x 6N damped system (default);
                              * 1 = block-Jacobi: each control point's 6 unknowns from its own 6 x 6
                              * damped diagonal block (FP64 Cholesky per node), the reading of
-                             * Section 2's "update each W_i independently"; no factorisation of
+                             * Section 2's separate update of every W_i; no factorisation of
                              * the coupled system and no refinement. Handles of one batch agree.  */
   int32_t assoc;            /* ICP association (Section 2, projective "rasterization"):
                              * 0 = nearest pixel, floor(u + 1/2) (default);

@@ -3,7 +3,7 @@
  * Section 2.1 (first paragraph) of Zhou & Jagadeesan, "Real-time Surface Deformation Recovery
  * from Stereo Videos": FAST corners are detected on the GPU and a corner is suppressed when a
  * neighbouring pixel has a larger corner response, which spreads the features over low-texture
- * areas; the ORB features of the initial template are matched to every live frame, giving the
+ * areas; every live frame is then matched against the template's features, which gives the
  * two 3D point sets o1 (template) and o2 (live) of Eq. 2. The matches feed ds_submit_frame
  * (defsolve.h) directly.
  *

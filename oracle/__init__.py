@@ -14,7 +14,7 @@ It is a plain, slow, step-by-step restatement of the method in float64 numpy:
 * ransac.py  1-point RANSAC with reweighting, Eq. 2-4 and Section 2.1 (30 references,
              10 reweighting iterations)
 * dqb.py     dual-quaternion warp of template points by their neighbouring control points
-             (Section 2, "interpolation of neighboring control points") and its Jacobian
+             (Section 2: a point follows a blend of nearby control points) and its Jacobian
 * terms.py   the three cost terms of Eq. 1: ICP (Tukey, point-to-plane, projective
              association), ORB matches (Section 2.1 weights) and dense ARAP (Eq. 5-6)
 * solver.py  template set-up, normal-equation assembly, damped Gauss-Newton with a Cholesky

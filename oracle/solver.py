@@ -7,8 +7,9 @@ decomposition; w_ORB = 10 and w_ARAP is rescaled by the summed ICP and ORB weigh
 Readings used here (the CUDA path implements the same ones):
 * the normal equations couple all 6N unknowns (one dense system) and are damped with a fixed
   lambda: A + lambda (diag(A) + eps), lambda = 1e-4, eps = 1e-9, with no accept/reject test, so
-  both sides run the same number of iterations; the paper's "each W_i independently" is the
-  alternative block-Jacobi step (each control point's 6 x 6 diagonal block alone);
+  both sides run the same number of iterations; the per-control-point update Section 2
+  describes is the alternative block-Jacobi step (each control point's 6 x 6 diagonal block
+  alone);
 * w_ARAP = w_arap0 * (sum of ICP Tukey weights + w_ORB * sum of ORB weights) / N, evaluated once
   per frame at the warm-start state and then held for the frame;
 * each template point is blended by its 4 nearest control points (3D distance at time 0, ties
@@ -226,7 +227,7 @@ def cholesky_solve(A, b):
 
 
 def block_jacobi_solve(A, b):
-    """Section 2 solves the LM step by updating each W_i independently: every control point's
+    """Section 2 takes the LM step one control point at a time: every control point's
     6 unknowns from its own 6 x 6 diagonal block of the (damped) normal matrix, the coupling
     blocks between control points left out. x_i = A_ii^-1 b_i, each by a Cholesky
     factorisation."""

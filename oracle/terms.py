@@ -170,7 +170,7 @@ def arap_rows(q, t, g, wpair, w_arap, w_angle, w_rot, chunk=64):
       r_rot = q_i1 - s q_i2, s = sign(q_i1 . q_i2)                            (4 rows)
 
     |r_ang|^2 = 2 - 2 cos(angle), a smooth stand-in for the angle of Eq. 6; r_rot compares the
-    first four dual-quaternion components (the rotation quaternions) up to the q ~ -q sign.
+    rotation quaternions (the dual quaternions' real parts) up to the q ~ -q sign.
     Row weights: w_ARAP w_i1i2 x (1, w_angle, w_rot).  Columns: (dtheta, dt) of i1 then i2."""
     N = g.shape[0]
     R = rotmat(q)

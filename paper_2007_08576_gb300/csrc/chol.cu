@@ -1,6 +1,6 @@
-// Cholesky factorisation of the damped normal equations (Section 2: "we perform Cholesky
-// decomposition to update W_i"), for T = double (FP64 factor, TB = 32) or T = float (FP32
-// factor, TB = 64; on the SIMT pipes, or on the tensor cores in k_chol_tc).
+// Cholesky factorisation of the damped normal equations (Section 2 solves the step for the
+// warps W_i through a Cholesky factorisation), for T = double (FP64 factor, TB = 32) or T = float
+// (FP32 factor, TB = 64; on the SIMT pipes, or on the tensor cores in k_chol_tc).
 //
 // Layout: A is n x n row-major; only the lower triangle is read or written. The matrix is cut
 // into TB x TB tiles (the last row/column of tiles is ragged).
