@@ -67,3 +67,20 @@ def test_argument_errors_need_no_gpu(built):
     assert L.ds_selftest_bounded_wait(0, 10, 0, ctypes.byref(ms)) == d.DS_ERR_ARG
     assert L.ds_selftest_bounded_wait(0, 10**9, 0, ctypes.byref(ms)) == d.DS_ERR_ARG
     assert L.ds_selftest_bounded_wait(1, 1000000, 3, ctypes.byref(ms)) == d.DS_ERR_ARG
+
+
+def test_binding_fails_loudly_without_the_library():
+    """No CPU fallback: with the shared library absent the binding raises instead of computing."""
+    import subprocess
+    import sys
+    code = ("from paper_2007_08576_gb300 import defsolve as d\n"
+            "d.LIB_PATH = '/nonexistent/libdefsolve.so'\n"
+            "try:\n"
+            "    d.Solver\n"
+            "    d.lib()\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', e)\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert "raised:" in r.stdout and "not built" in r.stdout
