@@ -828,3 +828,16 @@ def test_point_to_plane_ignores_tangential_offsets():
     assert np.abs(rows.r - delta).max() < 1e-12
     assert cost == pytest.approx(terms.tukey_rho(delta, 10.0).sum(), rel=1e-12)
     assert wsum == pytest.approx(terms.tukey_weight(delta, 10.0).sum(), rel=1e-12)
+
+
+def test_no_data_keeps_the_identity(tiny):
+    """Degenerate frame: a live depth map with no surface and no matches.  Only the ARAP term
+    remains; it is zero with zero gradient at the identity (a common rigid state), so every
+    damped Gauss-Newton step is exactly zero and the cost stays 0."""
+    sc, tpl = tiny
+    res = solver.solve_frame(tpl, np.zeros_like(sc.template_depth), np.zeros(0, np.int32),
+                             np.zeros((0, 3)), np.zeros(0, np.int32), iters=3)
+    N = tpl.g.shape[0]
+    assert np.array_equal(res.q, np.tile([1.0, 0.0, 0.0, 0.0], (N, 1)))
+    assert np.array_equal(res.t, np.zeros((N, 3)))
+    assert res.costs == [0.0, 0.0, 0.0]
