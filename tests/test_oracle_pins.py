@@ -841,3 +841,27 @@ def test_no_data_keeps_the_identity(tiny):
     assert np.array_equal(res.q, np.tile([1.0, 0.0, 0.0, 0.0], (N, 1)))
     assert np.array_equal(res.t, np.zeros((N, 3)))
     assert res.costs == [0.0, 0.0, 0.0]
+
+
+def test_association_validity_with_holes_and_points_behind_the_camera():
+    """Section 2's projective association is valid only in front of the camera, inside the
+    image and on a usable target pixel: brute force over every pixel with a random hole mask."""
+    rng = np.random.default_rng(21)
+    W, H = 9, 7
+    K = (9.0, 9.0, 4.0, 3.0)
+    x = np.concatenate([rng.uniform(-6, 6, (400, 2)), rng.uniform(-4, 12, (400, 1))], 1)
+    x[:5, 2] = 0.0                                # on the camera plane: never valid
+    tgt_ok = rng.random((H, W)) < 0.7
+    pix, valid, _, _ = terms.associate(x, K, W, H, tgt_ok)
+    for i in range(x.shape[0]):
+        want = False
+        if x[i, 2] > 0:
+            u = K[0] * x[i, 0] / x[i, 2] + K[2]
+            v = K[1] * x[i, 1] / x[i, 2] + K[3]
+            for pv in range(H):
+                for pu in range(W):
+                    if -0.5 <= u - pu < 0.5 and -0.5 <= v - pv < 0.5:
+                        want = bool(tgt_ok[pv, pu])
+                        assert not want or pix[i] == pv * W + pu
+        assert valid[i] == want, i
+    assert valid.any() and not valid.all()
