@@ -9,8 +9,8 @@
 // Newton's method on the characteristic polynomial from an upper bound (monotone for a
 // polynomial with real roots; the bound is sum_k w_k |S1(k)| |S2(k)|, or Gershgorin's if
 // smaller), in FP32 on the scaled polynomial and then polished in FP64; the eigenvector is the
-// dominant column of the adjugate of N - lambda I. A fit is degenerate (R = I) if sum w < 1e-12 or the two largest eigenvalues are
-// within 2e-12 |M|_F of each other.
+// dominant column of the adjugate of N - lambda I. A fit is degenerate (R = I) if sum w < 1e-12
+// or the two largest eigenvalues are within 2e-12 |M|_F of each other.
 // After the last update the CTA writes its score sum_{k != k0} w_k, a bitset of d_k <= H
 // (warp ballots) and its weights; a second kernel keeps references whose score is at least
 // keep_frac times the best and combines them (mask = OR, weight = max).
@@ -45,13 +45,6 @@ __device__ __forceinline__ void others(int skip, int& a, int& b, int& c) {
   c = skip <= 2 ? 3 : 2;
 }
 
-// Largest root of a quartic / cubic with real roots, O(1) after the caller's scaling: Newton
-// from an upper bound x0 in FP32 (monotone from above), then FP64 Newton, monotone from above
-// again, from the FP32 root raised by a bound of its error (a few FP32 roundings of the
-// polynomial's terms, mag, divided by p'): ~2 FP64 steps for a well separated root, more when
-// p' is small (a nearly repeated root). The FP64 step divides by p' through an FP32 reciprocal
-// refined once (relative error ~1e-14, which only scales the step). p32(x, p, dp, mag) and
-// p64(x, p, dp) evaluate p, p' (and the sum of the terms' magnitudes) at x.
 // 1 / sqrt(v) to FP32 accuracy for any positive finite double (exponent split off first).
 __device__ __forceinline__ double rsqrt_seed(double v) {
   int e;
@@ -62,6 +55,13 @@ __device__ __forceinline__ double rsqrt_seed(double v) {
   }
   return (double)rsqrtf((float)m) * ldexp(1.0, -e / 2);
 }
+// Largest root of a quartic / cubic with real roots, O(1) after the caller's scaling: Newton
+// from an upper bound x0 in FP32 (monotone from above), then FP64 Newton, monotone from above
+// again, from the FP32 root raised by a bound of its error (a few FP32 roundings of the
+// polynomial's terms, mag, divided by p'): ~2 FP64 steps for a well separated root, more when
+// p' is small (a nearly repeated root). The FP64 step divides by p' through an FP32 reciprocal
+// refined once (relative error ~1e-14, which only scales the step). p32(x, p, dp, mag) and
+// p64(x, p, dp) evaluate p, p' (and the sum of the terms' magnitudes) at x.
 template <typename F32, typename F64>
 __device__ __forceinline__ double largest_root(double x0, F32 p32, F64 p64, double decided = -1.0) {
   float x = __double2float_ru(x0), dpf = 0.f, mag = 0.f;   // rounded up: still an upper bound
