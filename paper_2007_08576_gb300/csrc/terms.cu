@@ -23,8 +23,9 @@
 //
 // Accumulation: the ICP and ORB passes add their 6x6 blocks into a block-sparse table (one
 // entry per node pair that shares a template point) and their gradients into a vector; the
-// ARAP pass writes every lower block of A exactly once, adding the data blocks, the damping
-// lambda (diag + eps) and b = -(J^T W r).
+// ARAP pass builds each control point's 6 rows of A once (every pair block, the data blocks,
+// the damping lambda (diag + eps)) and b = -(J^T W r), writing the full rows into the refinement
+// matrix and the part up to the diagonal into the matrix the factorisation overwrites.
 #include <math.h>
 
 #include "ds_internal.cuh"
