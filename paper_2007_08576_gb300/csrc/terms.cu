@@ -25,7 +25,8 @@
 // entry per node pair that shares a template point) and their gradients into a vector; the
 // ARAP pass builds each control point's 6 rows of A once (every pair block, the data blocks,
 // the damping lambda (diag + eps)) and b = -(J^T W r), writing the full rows into the refinement
-// matrix and the part up to the diagonal into the matrix the factorisation overwrites.
+// matrix and the part left of the diagonal block, then the damped diagonal block, into the
+// matrix the factorisation overwrites.
 #include <math.h>
 
 #include "ds_internal.cuh"
