@@ -4,8 +4,8 @@
  * C ABI of the library libdefsolve.so. The operation is the deformation recovery of
  * Zhou & Jagadeesan, "Real-time Surface Deformation Recovery from Stereo Videos":
  *   - a depth template is deformed by sparse control points, each carrying a rigid warp W_i
- *     (Section 2: dual-quaternion warp, template points follow the interpolation of their
- *     neighbouring control points);
+ *     (Section 2: dual-quaternion warp; a template point moves with a blend of the control
+ *     points near it);
  *   - the warps minimise f_ICP + w_ORB f_ORB + w_ARAP f_ARAP (Eq. 1): point-to-plane ICP with
  *     Tukey weights from projective association (Section 2), feature matches weighted by
  *     1-point RANSAC + reweighting (Section 2.1, Eq. 2-4) and dense all-pairs ARAP

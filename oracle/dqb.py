@@ -1,8 +1,7 @@
 """Dual-quaternion warp of template points by their neighbouring control points (oracle).
 
 Section 2: every control point i carries a dual quaternion W_i (a 6-DoF rigid transform) and a
-template point is deformed by the interpolation of its neighbouring control points, as in
-DynamicFusion.  Readings used here:
+template point moves with a blend of the control points near it, as in DynamicFusion.  Readings used here:
 
 * node state: unit quaternion q_i and translation t_i with the node-centred transform
   W_i(x) = R_i (x - g_i) + g_i + t_i, g_i the node's template position; as a dual quaternion
@@ -54,7 +53,7 @@ def blend(dq, nid, alpha, near):
 
     dq: (N, 8); nid, alpha: (P, 4); near: (P,) node id of each point's nearest node.
     Returns b (P, 8) and the signs s (P, 4).
-    Section 2: a template point follows the interpolation of its neighbouring control points."""
+    Section 2: a template point moves with a blend of the control points near it."""
     qk = dq[nid, 0:4]                           # (P, 4, 4)
     qn = dq[near, 0:4]                          # (P, 4)
     s = np.where(np.einsum("pki,pi->pk", qk, qn) >= 0, 1.0, -1.0)

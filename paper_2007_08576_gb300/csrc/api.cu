@@ -9,10 +9,11 @@
 //     (the block-sparse pattern of the ICP and ORB contributions to A) and lists the tile tasks
 //     of the factorisation;
 //   * a device descriptor (ProbDesc) gathers every pointer and size the kernels need.
-// Per frame: copy-in, device-side index validation, live points and normals, RANSAC.
+// Per frame: copy-in, device-side index validation, live points and normals, RANSAC, into the
+// frame slot (of two per handle) that the last solve did not read.
 // Per Gauss-Newton iteration (for every problem of a batch at once): counters reset, ICP, ORB,
-// dense ARAP + assembly + damping, persistent Cholesky, persistent solves (+ FP64 refinement),
-// state update. A single-handle solve is a batch of one. The iterations of a solve are captured
+// dense ARAP + assembly + damping, persistent Cholesky, persistent solves (+ refinement steps
+// with double-float residuals), state update. A single-handle solve is a batch of one. The iterations of a solve are captured
 // once as a CUDA graph per batch and iteration count and replayed.
 #include <math.h>
 #include <string.h>

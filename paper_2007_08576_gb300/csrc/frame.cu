@@ -5,8 +5,8 @@
 //   the nearest-control-point decisions of the blend table are taken on exactly the values
 //   a plain FP64 evaluation of the same formula produces.
 // * Blend table: the 4 nearest control points of every template point by 3D distance at
-//   time 0 (Section 2: template points follow the interpolation of their neighbouring control
-//   points), ties to the lower node id, Gaussian weights normalised to one.
+//   time 0 (Section 2: a template point moves with a blend of the control points near it),
+//   ties to the lower node id, Gaussian weights normalised to one.
 // * Live frame: FP32 points and central-difference normals (Section 2: only the distance
 //   along the normal direction is used by ICP), oriented toward the camera.
 #include <math.h>
