@@ -61,7 +61,8 @@ def stream_bytes(W: int, H: int, N: int, M: int, precision: int) -> int:
     nbp = 14 * N
     b = npx * (4 + 24 + 4 + 4 + 2 * (16 + 16) + 4)      # depths, FP64 template, 2 frame slots
     b += npx * (16 + 16 + 4)                            # sorted points, weights, rank
-    b += N * (8 * 7 + 64 + 96) + nbp * (36 * 4 + 12)    # state, node tables, data blocks
+    # state, node tables, ARAP diagonal blocks, data blocks
+    b += N * (8 * 7 + 64 + 96 + 48 * 4) + nbp * (36 * 4 + 12)
     b += n * n * 4                                      # FP32 system
     if precision == 0:
         b += n * n * 8                                  # FP64 factor
@@ -72,10 +73,13 @@ def stream_bytes(W: int, H: int, N: int, M: int, precision: int) -> int:
     nt = (n + tb - 1) // tb
     tsz = 8 if precision == 0 else 4
     b += 4 * (nt + 2 * nt * nt) + tsz * nt * tb * tb
-    b += tsz * nt * (nt + 1) // 2 * tb * (tb + 16 // tsz)   # packed factor tiles
+    # packed factor tiles: FP64 transposed padded tiles; FP32 slots sized for the tensor-core
+    # kernel's hi / lo operand layout (8192 floats), which also hold the SIMT kernel's tiles
+    slot = tb * (tb + 16 // tsz) if precision == 0 else 8192
+    b += tsz * nt * (nt + 1) // 2 * slot
     b += nt * (nt + 1) // 2 * 16 * 2                    # task list
     b += 2 * M * (4 + 12 + 4 + 4) + M * (8 * 3 + 4 * 6)  # 2 slots of matches + RANSAC results
-    b += M * 64 * (7 * 8 + 4)                            # RANSAC scratch
+    b += M * 64 * (7 * 8 + 4) + M * 8                   # RANSAC scratch, weights, bitsets
     return int(b)
 
 
