@@ -865,3 +865,33 @@ def test_association_validity_with_holes_and_points_behind_the_camera():
                         assert not want or pix[i] == pv * W + pu
         assert valid[i] == want, i
     assert valid.any() and not valid.all()
+
+
+def test_quaternion_algebra_textbook_identities():
+    """The quaternion helpers behind Section 2's warp against textbook facts: the product is
+    norm-multiplicative and matches its left / right matrices, rotation matrices compose like
+    the product and are proper rotations, and exp(theta / 2) is Rodrigues' rotation by |theta|
+    about theta / |theta|."""
+    from oracle.quat import qL, qmul, qR, rotmat, skew
+    rng = np.random.default_rng(17)
+    a, b = rng.normal(size=(50, 4)), rng.normal(size=(50, 4))
+    ab = qmul(a, b)
+    assert np.allclose(np.linalg.norm(ab, axis=1),
+                       np.linalg.norm(a, axis=1) * np.linalg.norm(b, axis=1), rtol=1e-13)
+    assert np.allclose(np.einsum("pij,pj->pi", qL(a), b), ab, atol=1e-13)
+    assert np.allclose(np.einsum("pij,pj->pi", qR(b), a), ab, atol=1e-13)
+    ua = a / np.linalg.norm(a, axis=1, keepdims=True)
+    ub = b / np.linalg.norm(b, axis=1, keepdims=True)
+    Ra, Rb, Rab = rotmat(ua), rotmat(ub), rotmat(qmul(ua, ub))
+    assert np.allclose(Rab, Ra @ Rb, atol=1e-13)
+    assert np.allclose(Ra @ np.swapaxes(Ra, 1, 2), np.eye(3), atol=1e-13)
+    assert np.allclose(np.linalg.det(Ra), 1.0, atol=1e-13)
+    th = rng.normal(size=(50, 3))
+    ang = np.linalg.norm(th, axis=1)
+    k = th / ang[:, None]
+    Kx = skew(k)
+    rod = (np.eye(3) + np.sin(ang)[:, None, None] * Kx
+           + (1 - np.cos(ang))[:, None, None] * (Kx @ Kx))
+    assert np.allclose(rotmat(qexp_half(th)), rod, atol=1e-13)
+    v = rng.normal(size=(50, 3))
+    assert np.allclose(np.einsum("pij,pj->pi", skew(k), v), np.cross(k, v), atol=1e-14)
