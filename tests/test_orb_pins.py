@@ -239,3 +239,26 @@ def test_detection_is_invariant_to_an_intensity_offset():
     assert len(a["pix"]) > 30
     assert np.array_equal(a["pix"], b["pix"]) and np.array_equal(a["score"], b["score"])
     assert np.array_equal(a["bin"], b["bin"]) and np.array_equal(a["desc"], b["desc"])
+
+
+def test_box_sums_and_hamming_distances_brute_force():
+    """The descriptor's 5 x 5 box sums and the matcher's Hamming distance against their plain
+    definitions: explicit 25-pixel sums (0 where the box leaves the image) and bit counts of the
+    XOR of every word pair."""
+    rng = np.random.default_rng(33)
+    img = rng.integers(0, 256, (11, 13), dtype=np.uint8)
+    S = orb.box5(img)
+    H, W = img.shape
+    for v in range(H):
+        for u in range(W):
+            if 2 <= v < H - 2 and 2 <= u < W - 2:
+                want = sum(int(img[v + dy, u + dx]) for dy in range(-2, 3) for dx in range(-2, 3))
+            else:
+                want = 0
+            assert S[v, u] == want, (v, u)
+    D1 = rng.integers(0, 2**32, (7, 8), dtype=np.uint64).astype(np.uint32)
+    D2 = rng.integers(0, 2**32, (5, 8), dtype=np.uint64).astype(np.uint32)
+    Hd = orb.hamming(D1, D2, rows=3)
+    for i in range(7):
+        for j in range(5):
+            assert Hd[i, j] == sum(bin(int(a) ^ int(b)).count("1") for a, b in zip(D1[i], D2[j]))
