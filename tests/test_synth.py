@@ -54,3 +54,23 @@ def test_occlusion_fraction_and_reproducibility():
     assert not np.array_equal(a.frames[0].match_idx, c.frames[0].match_idx)
     empty = (a.frames[0].depth == 0).mean()
     assert cfg.occlusion * 0.8 <= empty <= cfg.occlusion * 1.5 + 0.05
+
+
+def test_live_pixels_see_the_moved_surface_and_its_texture():
+    """Each live pixel with depth sees the moved surface point whose lateral coordinates it
+    reports: that point projects back onto the pixel, its depth is the pixel's, and the pixel's
+    grey level is the texture there."""
+    from synth import make_textured_scene
+    from synth.texture import to_u8
+    ts = make_textured_scene(CONFIGS["frame_80x60_n32"], 1000, n_frames=1, f64=True)
+    sc, fr = ts.scene, ts.scene.frames[0]
+    fx, fy, cx, cy = sc.K
+    dep = np.asarray(fr.depth)
+    ok = dep > 0
+    xy = ts.live_xy[0]
+    Y, _, _ = fr.motion.surface(sc.hf, xy[..., 0][ok], xy[..., 1][ok])
+    v, u = np.nonzero(ok)
+    assert np.abs(fx * Y[:, 0] / Y[:, 2] + cx - u).max() < 1e-6
+    assert np.abs(fy * Y[:, 1] / Y[:, 2] + cy - v).max() < 1e-6
+    assert np.abs(Y[:, 2] - dep[ok]).max() < 1e-6
+    assert np.array_equal(ts.images[0], to_u8(ts.texture.eval(xy[..., 0], xy[..., 1]), ok))
