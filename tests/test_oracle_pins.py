@@ -922,3 +922,85 @@ def test_ransac_preselects_the_rigid_majority_over_a_shifted_minority():
         assert np.array_equal(rs["d"][h] <= 2.0, np.arange(len(o1)) < nA)
     assert np.array_equal(rs["mask"], np.arange(len(o1)) < nA)
     assert np.all(rs["what"][:nA] == 1.0) and np.all(rs["what"][nA:] < 1.0)
+
+
+# ----------------------------------------------------------------------------- set-up weights
+
+
+def _plane_template(nodes_uv, W=12, H=12):
+    """A fronto-parallel plane at z = 100 mm seen with f = 100 and the principal point at pixel
+    (0, 0), so the template point of pixel (u, v) is exactly (u, v, 100) mm."""
+    depth = np.full((H, W), 100.0)
+    K = (100.0, 100.0, 0.0, 0.0)
+    nodes = np.array([v * W + u for u, v in nodes_uv], dtype=np.int64)
+    return solver.setup_template(depth, K, nodes), W
+
+
+def test_blend_weights_closed_form_on_an_uneven_row_of_nodes():
+    """Section 2 blending under the Gaussian-over-4-nearest reading.  Four control points on a
+    row at x = 0, 1, 3, 7 mm: their nearest-neighbour spacings are 1, 1, 2 and 4 mm, so
+    sigma_b = their mean = 2 mm (the minimum, 1, the maximum, 4, the median, 1.5, and the mean
+    over all pairs, 3.5, all differ).  Every template point's 4 weights are then
+    exp(-d^2 / 8) over the 4 nodes, normalised to sum 1, ordered nearest first with ties to the
+    lower node id; the values below are those exponentials written out for three points."""
+    tpl, W = _plane_template([(0, 0), (1, 0), (3, 0), (7, 0)])
+    assert tpl.sigma_b == pytest.approx(2.0, rel=1e-15)
+
+    def weights_of(u, v):
+        j = int(np.flatnonzero(tpl.pidx == v * W + u)[0])
+        return tpl.nid[j], tpl.alpha[j]
+
+    e = math.exp
+    cases = {
+        # (pixel) -> (node ids nearest first, squared distances over 2 sigma_b^2 = 8)
+        (0, 0): ([0, 1, 2, 3], [0.0, 1 / 8, 9 / 8, 49 / 8]),
+        (5, 0): ([2, 3, 1, 0], [4 / 8, 4 / 8, 16 / 8, 25 / 8]),    # tie 2 / 3 -> lower id first
+        (3, 2): ([2, 1, 0, 3], [4 / 8, 8 / 8, 13 / 8, 20 / 8]),
+    }
+    for (u, v), (ids, ex) in cases.items():
+        nid, alpha = weights_of(u, v)
+        a = np.array([e(-x) for x in ex])
+        assert list(nid) == ids, (u, v)
+        assert np.abs(alpha - a / a.sum()).max() < 1e-15, (u, v)
+        assert alpha.sum() == pytest.approx(1.0, abs=1e-15)
+
+
+def test_blend_weights_on_a_square_lattice():
+    """Control points on a square lattice of 4 mm: sigma_b = 4 mm exactly.  A point at the
+    centre of a lattice cell is equidistant from its 4 corners and gets 1/4 from each; a point
+    on a lattice corner node gets 1 : e^-1/2 : e^-1/2 : e^-1 from itself, its two lattice
+    neighbours and the diagonal one, i.e. the outer product of (1, e^-1/2) / (1 + e^-1/2)."""
+    tpl, W = _plane_template([(u, v) for v in (2, 6, 10) for u in (2, 6, 10)])
+    assert tpl.sigma_b == pytest.approx(4.0, rel=1e-15)
+    j = int(np.flatnonzero(tpl.pidx == 4 * W + 4)[0])      # centre of the cell (2..6) x (2..6)
+    assert sorted(tpl.nid[j]) == [0, 1, 3, 4]
+    assert np.abs(tpl.alpha[j] - 0.25).max() < 1e-15
+    j = int(np.flatnonzero(tpl.pidx == 2 * W + 2)[0])      # on the corner node 0
+    r = math.exp(-0.5)
+    want = np.array([1.0, r, r, r * r]) / (1.0 + r) ** 2
+    assert list(tpl.nid[j]) == [0, 1, 3, 4]
+    assert np.abs(tpl.alpha[j] - want).max() < 1e-15
+
+
+def test_arap_pair_weights_closed_form():
+    """Section 2.2 pair weights under the reading w = exp(-|g_i1 - g_i2|^2 / (2 sigma_A^2)),
+    sigma_A = 0.25 x the diagonal of the control points' 3D bounding box, zero on the diagonal.
+    Nodes (0, 0, 0), (2, 3, 6), (2, 0, 0): box 2 x 3 x 6, diagonal 7, sigma_A = 1.75,
+    2 sigma_A^2 = 6.125; the squared distances are 49, 4 and 45."""
+    g = np.array([[0.0, 0.0, 0.0], [2.0, 3.0, 6.0], [2.0, 0.0, 0.0]])
+    w, sig = terms.arap_pair_weights(g, 0.25)
+    assert sig == pytest.approx(1.75, rel=1e-15)
+    want = np.zeros((3, 3))
+    want[0, 1] = want[1, 0] = math.exp(-49 / 6.125)
+    want[0, 2] = want[2, 0] = math.exp(-4 / 6.125)
+    want[1, 2] = want[2, 1] = math.exp(-45 / 6.125)
+    assert np.abs(w - want).max() < 1e-16
+    # the template set-up uses the same rule on its control points: on the plane, nodes at
+    # (0, 0), (3, 0), (0, 4) mm and one inside the box at (1, 1) span a 3 x 4 box, diagonal 5,
+    # sigma_A = 1.25; squared distances 9, 16, 25 between the corners, 2, 5, 10 to (1, 1)
+    tpl, _ = _plane_template([(0, 0), (3, 0), (0, 4), (1, 1)])
+    assert tpl.sigma_A == pytest.approx(1.25, rel=1e-15)
+    s2 = 2 * 1.25 ** 2
+    d2 = np.array([[0, 9, 16, 2], [9, 0, 25, 5], [16, 25, 0, 10], [2, 5, 10, 0]], dtype=float)
+    want = np.exp(-d2 / s2) * (1 - np.eye(4))
+    assert np.abs(tpl.wpair - want).max() < 1e-16
