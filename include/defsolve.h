@@ -253,17 +253,27 @@ int ds_set_tracing(ds_handle h, int32_t on);
 int ds_get_phase_times(ds_handle h, double* ms4);
 int ds_get_counters(ds_handle h, int64_t* kernels_launched);
 
+/* Device bytes the handle holds now: every buffer it has allocated and not yet released (the
+ * template, the control-point tables and normal-equation buffers sized at
+ * ds_set_control_points, the two frame slots' match and RANSAC buffers sized by the largest M
+ * submitted so far). Batches and captured graphs are not included. For admission control by
+ * device memory (the serving loop of the paper's real-time setting runs many streams on one
+ * GPU). No synchronisation. Errors: DS_ERR_ARG (NULL). */
+int ds_get_device_bytes(ds_handle h, int64_t* bytes);
+
 /* 1-point RANSAC preselection without any allocation, for callers that cannot allocate device
  * memory (for example a host process that runs inside a pre-sized memory pool, or a real-time
  * loop where an allocation can block on a device-wide synchronisation). The paper has no
- * counterpart; it computes exactly what ds_submit_frame's preselection computes (Section 2.1),
- * into caller-provided device buffers.
+ * counterpart: it is the same preselection that ds_submit_frame runs, written into
+ * caller-provided device buffers.
  * All pointers are device memory owned by the caller: depth0 (H x W template depth), the M match
  * pixels and live points, the n_hyp reference ids; outputs mask_bits[ceil(M/32)], w_M[M],
  * kept_bits[2], score_nh[n_hyp]. Limits: 1 <= M <= DS_NOALLOC_MAX_MATCHES, n_hyp <= DS_MAX_HYP.
  * The working memory is one fixed array compiled into the library (about 1.1 MB, held on every
  * device that loads the library until the process exits). The first call on a device looks up
- * that array's device address; make that first call before any stream capture. All calls share
+ * that array's device address and sets the kernel's shared-memory limit there (a failure of
+ * either is returned as DS_ERR_CUDA and retried by the next call); make that first call before
+ * any stream capture. All calls share
  * the array: calls that overlap on the GPU (other streams, other threads) race and must not be
  * issued. The call runs on cuda_stream (NULL: the legacy default stream) and synchronises it
  * before returning. Errors: DS_ERR_ARG (sizes beyond the limits, a null or host pointer, an

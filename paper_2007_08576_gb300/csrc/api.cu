@@ -167,6 +167,9 @@ struct ds_ctx {
   int64_t kernels = 0;
   int last_iters = 0;
   bool error = false;
+  // device bytes this handle holds (every buffer it allocated and has not freed), by pointer
+  std::unordered_map<const void*, size_t> alloc_bytes;
+  size_t device_bytes = 0;
 };
 
 namespace {
@@ -197,6 +200,29 @@ template <typename T>
 void dfree(T*& p) {
   if (p) cudaFree((void*)p);
   p = nullptr;
+}
+
+// Allocation and release of a handle's buffers, counted in the handle's device bytes.
+template <typename T>
+int halloc(ds_ctx* h, T** p, size_t count) {
+  const int rc = dalloc(p, count);
+  if (rc == DS_OK) {
+    const size_t b = sizeof(T) * (count ? count : 1);
+    h->alloc_bytes[(const void*)*p] = b;
+    h->device_bytes += b;
+  }
+  return rc;
+}
+template <typename T>
+void hfree(ds_ctx* h, T*& p) {
+  if (p) {
+    auto it = h->alloc_bytes.find((const void*)p);
+    if (it != h->alloc_bytes.end()) {
+      h->device_bytes -= it->second;
+      h->alloc_bytes.erase(it);
+    }
+  }
+  dfree(p);
 }
 
 int copy_in(void* dst, const void* src, size_t bytes, cudaStream_t s) {
@@ -260,14 +286,14 @@ void free_cp(ds_ctx* h) {
     h->self = nullptr;
   }
   invalidate_batches(h, false);
-  dfree(h->d_g64); dfree(h->d_gc); dfree(h->d_q64); dfree(h->d_t64); dfree(h->d_node);
-  dfree(h->d_pn); dfree(h->d_tp); dfree(h->d_tw); dfree(h->d_rank); dfree(h->d_seg);
-  dfree(h->d_segbp); dfree(h->d_segstart); dfree(h->d_rowptr); dfree(h->d_rowcol); dfree(h->d_rowbp);
-  dfree(h->d_A32); dfree(h->d_A64); dfree(h->d_Af32); dfree(h->d_Dinv); dfree(h->d_blk); dfree(h->d_adiag);
-  dfree(h->d_gdata); dfree(h->d_b); dfree(h->d_x); dfree(h->d_r); dfree(h->d_xf);
-  dfree(h->d_v2); dfree(h->d_v3); dfree(h->d_lcnt); dfree(h->d_lflags); dfree(h->d_tasks);
-  dfree(h->d_Lp);
-  dfree(h->d_desc);
+  hfree(h, h->d_g64); hfree(h, h->d_gc); hfree(h, h->d_q64); hfree(h, h->d_t64); hfree(h, h->d_node);
+  hfree(h, h->d_pn); hfree(h, h->d_tp); hfree(h, h->d_tw); hfree(h, h->d_rank); hfree(h, h->d_seg);
+  hfree(h, h->d_segbp); hfree(h, h->d_segstart); hfree(h, h->d_rowptr); hfree(h, h->d_rowcol); hfree(h, h->d_rowbp);
+  hfree(h, h->d_A32); hfree(h, h->d_A64); hfree(h, h->d_Af32); hfree(h, h->d_Dinv); hfree(h, h->d_blk); hfree(h, h->d_adiag);
+  hfree(h, h->d_gdata); hfree(h, h->d_b); hfree(h, h->d_x); hfree(h, h->d_r); hfree(h, h->d_xf);
+  hfree(h, h->d_v2); hfree(h, h->d_v3); hfree(h, h->d_lcnt); hfree(h, h->d_lflags); hfree(h, h->d_tasks);
+  hfree(h, h->d_Lp);
+  hfree(h, h->d_desc);
   h->N = h->n = 0;
   h->have_frame = false;
 }
@@ -764,13 +790,13 @@ int ds_create_template(const float* depth_hw, int32_t W, int32_t H, ds_intrinsic
     }
   for (size_t i = 0; i < npx; ++i)
     if (h->h_depth0[i] > 0.f) h->h_pidx.push_back((int)i);
-  if ((rc = dalloc(&h->d_depth0, npx)) || (rc = dalloc(&h->d_X64, 3 * npx)) ||
-      (rc = dalloc(&h->d_pidx, h->h_pidx.size())) || (rc = dalloc(&h->d_depth, npx)) ||
-      (rc = dalloc(&h->d_tpts, 2 * npx)) || (rc = dalloc(&h->d_tnrm, 2 * npx)) ||
-      (rc = dalloc(&h->d_acc, ACC_COUNT)) || (rc = dalloc(&h->d_hist, 6 * DS_MAX_ITERS)) ||
-      (rc = dalloc(&h->d_flag, 4)) || (rc = dalloc(&h->d_hyp, DS_MAX_HYP)) ||
-      (rc = dalloc(&h->d_rs_score, 2 * DS_MAX_HYP)) || (rc = dalloc(&h->d_rs_kept, 4)) ||
-      (rc = dalloc(&h->d_rs_counts, 8))) {
+  if ((rc = halloc(h, &h->d_depth0, npx)) || (rc = halloc(h, &h->d_X64, 3 * npx)) ||
+      (rc = halloc(h, &h->d_pidx, h->h_pidx.size())) || (rc = halloc(h, &h->d_depth, npx)) ||
+      (rc = halloc(h, &h->d_tpts, 2 * npx)) || (rc = halloc(h, &h->d_tnrm, 2 * npx)) ||
+      (rc = halloc(h, &h->d_acc, ACC_COUNT)) || (rc = halloc(h, &h->d_hist, 6 * DS_MAX_ITERS)) ||
+      (rc = halloc(h, &h->d_flag, 4)) || (rc = halloc(h, &h->d_hyp, DS_MAX_HYP)) ||
+      (rc = halloc(h, &h->d_rs_score, 2 * DS_MAX_HYP)) || (rc = halloc(h, &h->d_rs_kept, 4)) ||
+      (rc = halloc(h, &h->d_rs_counts, 8))) {
     ds_destroy(h);
     return rc;
   }
@@ -847,7 +873,7 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
   h->P = P;
   int4* d_nid = nullptr;
   float4* d_alpha = nullptr;
-  if ((rc = dalloc(&h->d_g64, 3 * N)) || (rc = dalloc(&h->d_gc, 3)) ||
+  if ((rc = halloc(h, &h->d_g64, 3 * N)) || (rc = halloc(h, &h->d_gc, 3)) ||
       (rc = dalloc(&d_nid, P)) || (rc = dalloc(&d_alpha, P))) {
     dfree(d_nid);
     dfree(d_alpha);
@@ -967,32 +993,32 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
   const int nt = (n + TB - 1) / TB;
   h->nt = nt;
   const size_t tsz = prec == DS_PREC_FP64 ? sizeof(double) : sizeof(float);
-  if ((rc = dalloc(&h->d_q64, 4 * N)) || (rc = dalloc(&h->d_t64, 3 * N)) ||
-      (rc = dalloc(&h->d_node, N)) || (rc = dalloc(&h->d_pn, N)) || (rc = dalloc(&h->d_tp, P)) ||
-      (rc = dalloc(&h->d_tw, P)) || (rc = dalloc(&h->d_rank, npx)) ||
-      (rc = dalloc(&h->d_seg, h->S)) || (rc = dalloc(&h->d_segbp, 10 * h->S)) ||
-      (rc = dalloc(&h->d_segstart, h->S + 1)) ||
-      (rc = dalloc(&h->d_rowptr, N + 1)) || (rc = dalloc(&h->d_rowcol, rowcol.size())) ||
-      (rc = dalloc(&h->d_rowbp, rowbp.size())) || (rc = dalloc(&h->d_A32, nn)) ||
-      (rc = dalloc(&h->d_blk, 36 * (size_t)h->nbp)) || (rc = dalloc(&h->d_gdata, n)) ||
-      (rc = dalloc(&h->d_adiag, 48 * (size_t)N)) ||
-      (rc = dalloc(&h->d_b, n)) || (rc = dalloc(&h->d_x, n)) || (rc = dalloc(&h->d_r, n)) ||
-      (rc = dalloc(&h->d_xf, n)) ||
-      (rc = dalloc((char**)&h->d_v2, tsz * n)) ||
-      (rc = dalloc((char**)&h->d_v3, tsz * n)) ||
-      (rc = dalloc((char**)&h->d_Dinv, tsz * (size_t)nt * TB * TB)) ||
-      (rc = dalloc(&h->d_lcnt, (size_t)nt + 2 * (size_t)nt * nt)) ||
-      (rc = dalloc(&h->d_lflags, 2 * (size_t)nt)) ||
-      (rc = dalloc((char**)&h->d_Lp, tsz * (prec == DS_PREC_FP64 ? chol_packed_elems<double>(nt)
+  if ((rc = halloc(h, &h->d_q64, 4 * N)) || (rc = halloc(h, &h->d_t64, 3 * N)) ||
+      (rc = halloc(h, &h->d_node, N)) || (rc = halloc(h, &h->d_pn, N)) || (rc = halloc(h, &h->d_tp, P)) ||
+      (rc = halloc(h, &h->d_tw, P)) || (rc = halloc(h, &h->d_rank, npx)) ||
+      (rc = halloc(h, &h->d_seg, h->S)) || (rc = halloc(h, &h->d_segbp, 10 * h->S)) ||
+      (rc = halloc(h, &h->d_segstart, h->S + 1)) ||
+      (rc = halloc(h, &h->d_rowptr, N + 1)) || (rc = halloc(h, &h->d_rowcol, rowcol.size())) ||
+      (rc = halloc(h, &h->d_rowbp, rowbp.size())) || (rc = halloc(h, &h->d_A32, nn)) ||
+      (rc = halloc(h, &h->d_blk, 36 * (size_t)h->nbp)) || (rc = halloc(h, &h->d_gdata, n)) ||
+      (rc = halloc(h, &h->d_adiag, 48 * (size_t)N)) ||
+      (rc = halloc(h, &h->d_b, n)) || (rc = halloc(h, &h->d_x, n)) || (rc = halloc(h, &h->d_r, n)) ||
+      (rc = halloc(h, &h->d_xf, n)) ||
+      (rc = halloc(h, (char**)&h->d_v2, tsz * n)) ||
+      (rc = halloc(h, (char**)&h->d_v3, tsz * n)) ||
+      (rc = halloc(h, (char**)&h->d_Dinv, tsz * (size_t)nt * TB * TB)) ||
+      (rc = halloc(h, &h->d_lcnt, (size_t)nt + 2 * (size_t)nt * nt)) ||
+      (rc = halloc(h, &h->d_lflags, 2 * (size_t)nt)) ||
+      (rc = halloc(h, (char**)&h->d_Lp, tsz * (prec == DS_PREC_FP64 ? chol_packed_elems<double>(nt)
                                                                  : chol_packed_elems<float>(nt))))) {
     free_cp(h);
     return rc;
   }
-  if (prec == DS_PREC_FP64 && (rc = dalloc(&h->d_A64, nn))) {
+  if (prec == DS_PREC_FP64 && (rc = halloc(h, &h->d_A64, nn))) {
     free_cp(h);
     return rc;
   }
-  if (prec == DS_PREC_FP32_REFINE && (rc = dalloc(&h->d_Af32, nn))) {
+  if (prec == DS_PREC_FP32_REFINE && (rc = halloc(h, &h->d_Af32, nn))) {
     free_cp(h);
     return rc;
   }
@@ -1000,7 +1026,7 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
     std::vector<int4> tasks;
     make_chol_tasks(nt, tasks);
     h->ntasks = (int)tasks.size();
-    if ((rc = dalloc(&h->d_tasks, tasks.size()))) {
+    if ((rc = halloc(h, &h->d_tasks, tasks.size()))) {
       free_cp(h);
       return rc;
     }
@@ -1074,7 +1100,7 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
     lp.status = h->d_acc + ACC_STATUS;
     lp.y = h->d_v3;
     lp.x = h->d_v2;
-    if ((rc = dalloc(&h->d_desc, 2))) {
+    if ((rc = halloc(h, &h->d_desc, 2))) {
       free_cp(h);
       return rc;
     }
@@ -1148,19 +1174,19 @@ int ds_submit_frame(ds_handle h, const float* depth_hw, const int32_t* match_tmp
     // new slot buffers: every solve and submission still running must be done first
     wait_solved(h);
     cudaStreamSynchronize(s);
-    dfree(h->d_midx); dfree(h->d_mxyz); dfree(h->d_rs_scratch); dfree(h->d_rs_hbits);
-    dfree(h->d_rs_hw); dfree(h->d_rs_mask); dfree(h->d_rs_what); dfree(h->d_rs_o1);
-    dfree(h->d_rs_o1df);
+    hfree(h, h->d_midx); hfree(h, h->d_mxyz); hfree(h, h->d_rs_scratch); hfree(h, h->d_rs_hbits);
+    hfree(h, h->d_rs_hw); hfree(h, h->d_rs_mask); hfree(h, h->d_rs_what); hfree(h, h->d_rs_o1);
+    hfree(h, h->d_rs_o1df);
     int cap = std::max(M, 64);
     int words = (cap + 31) / 32;
-    if ((rc = dalloc(&h->d_midx, 2 * (size_t)cap)) || (rc = dalloc(&h->d_mxyz, 6 * (size_t)cap)) ||
-        (rc = dalloc(&h->d_rs_scratch, (size_t)7 * cap * DS_MAX_HYP)) ||
-        (rc = dalloc(&h->d_rs_hbits, (size_t)words * DS_MAX_HYP)) ||
-        (rc = dalloc(&h->d_rs_hw, (size_t)cap * DS_MAX_HYP)) ||
-        (rc = dalloc(&h->d_rs_mask, 2 * (size_t)words)) ||
-        (rc = dalloc(&h->d_rs_what, 2 * (size_t)cap)) ||
-        (rc = dalloc(&h->d_rs_o1, 3 * (size_t)cap)) ||
-        (rc = dalloc(&h->d_rs_o1df, 6 * (size_t)cap))) {
+    if ((rc = halloc(h, &h->d_midx, 2 * (size_t)cap)) || (rc = halloc(h, &h->d_mxyz, 6 * (size_t)cap)) ||
+        (rc = halloc(h, &h->d_rs_scratch, (size_t)7 * cap * DS_MAX_HYP)) ||
+        (rc = halloc(h, &h->d_rs_hbits, (size_t)words * DS_MAX_HYP)) ||
+        (rc = halloc(h, &h->d_rs_hw, (size_t)cap * DS_MAX_HYP)) ||
+        (rc = halloc(h, &h->d_rs_mask, 2 * (size_t)words)) ||
+        (rc = halloc(h, &h->d_rs_what, 2 * (size_t)cap)) ||
+        (rc = halloc(h, &h->d_rs_o1, 3 * (size_t)cap)) ||
+        (rc = halloc(h, &h->d_rs_o1df, 6 * (size_t)cap))) {
       // no slot may keep pointers into the freed buffers: both hold no frame now
       h->M_cap = 0;
       h->Ms[0] = h->Ms[1] = 0;
@@ -1574,6 +1600,12 @@ int ds_batch_phase_times(ds_batch b, double* ms4) {
   return batch_phase_times(b, ms4);
 }
 
+int ds_get_device_bytes(ds_handle h, int64_t* bytes) {
+  if (!h || !bytes) return DS_ERR_ARG;
+  *bytes = (int64_t)h->device_bytes;
+  return DS_OK;
+}
+
 int ds_get_counters(ds_handle h, int64_t* kernels_launched) {
   if (!kernels_launched) return DS_ERR_ARG;
   *kernels_launched = h ? h->kernels : g_total_kernels.load();
@@ -1588,12 +1620,12 @@ int ds_destroy(ds_handle h) {
   }
   invalidate_batches(h, true);
   free_cp(h);
-  dfree(h->d_depth0); dfree(h->d_X64); dfree(h->d_pidx); dfree(h->d_depth); dfree(h->d_tpts);
-  dfree(h->d_tnrm); dfree(h->d_midx); dfree(h->d_mxyz); dfree(h->d_hyp);
-  dfree(h->d_rs_scratch); dfree(h->d_rs_hbits); dfree(h->d_rs_hw); dfree(h->d_rs_score);
-  dfree(h->d_rs_mask); dfree(h->d_rs_what); dfree(h->d_rs_kept); dfree(h->d_rs_counts);
-  dfree(h->d_rs_o1); dfree(h->d_rs_o1df);
-  dfree(h->d_acc); dfree(h->d_hist); dfree(h->d_flag);
+  hfree(h, h->d_depth0); hfree(h, h->d_X64); hfree(h, h->d_pidx); hfree(h, h->d_depth); hfree(h, h->d_tpts);
+  hfree(h, h->d_tnrm); hfree(h, h->d_midx); hfree(h, h->d_mxyz); hfree(h, h->d_hyp);
+  hfree(h, h->d_rs_scratch); hfree(h, h->d_rs_hbits); hfree(h, h->d_rs_hw); hfree(h, h->d_rs_score);
+  hfree(h, h->d_rs_mask); hfree(h, h->d_rs_what); hfree(h, h->d_rs_kept); hfree(h, h->d_rs_counts);
+  hfree(h, h->d_rs_o1); hfree(h, h->d_rs_o1df);
+  hfree(h, h->d_acc); hfree(h, h->d_hist); hfree(h, h->d_flag);
   for (int k = 0; k < 2; ++k)
     if (h->ev_slot_free[k]) cudaEventDestroy(h->ev_slot_free[k]);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);

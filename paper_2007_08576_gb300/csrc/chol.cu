@@ -1042,12 +1042,9 @@ template size_t chol_packed_elems<double>(int);
 template <typename T>
 void launch_chol_dag(const BatchTabs& B, cudaStream_t s) {
   if (sizeof(T) == 4 && B.factor_tc) {
-    static int per_sm = 0;
-    if (!per_sm) {
-      cudaFuncSetAttribute(k_chol_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmem);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_tc, 256, tc::kSmem);
-      per_sm = std::max(1, std::min(per_sm, 2));
-    }
+    static PerDevice attr_tc, occ_tc;
+    set_smem_once(attr_tc, k_chol_tc, (int)tc::kSmem);
+    const int per_sm = ctas_per_sm_once(occ_tc, k_chol_tc, 256, tc::kSmem, 2);
     const int grid = std::min(B.n_chol, per_sm * num_sms());
     k_chol_tc<<<grid, 256, tc::kSmem, s>>>(B.d, B.chol, B.n_chol, B.words + 0, B.words + 5,
                                             2000000000ull);
@@ -1056,16 +1053,9 @@ void launch_chol_dag(const BatchTabs& B, cudaStream_t s) {
   }
   constexpr int TB = sizeof(T) == 8 ? 32 : 64;
   const size_t sm = 4 * sizeof(T) * TB * TileCfg<T, TB>::LDT;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_chol_dag<T, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr = true;
-  }
-  static int per_sm = 0;
-  if (!per_sm) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_dag<T, TB>, 256, sm);
-    per_sm = std::max(1, std::min(per_sm, 4));
-  }
+  static PerDevice attr, occ;
+  set_smem_once(attr, k_chol_dag<T, TB>, (int)sm);
+  const int per_sm = ctas_per_sm_once(occ, k_chol_dag<T, TB>, 256, sm, 4);
   const int grid = std::min(B.n_chol, per_sm * num_sms());
   k_chol_dag<T, TB><<<grid, 256, sm, s>>>(B.d, B.chol, B.n_chol, B.words + 0, B.words + 5,
                                           2000000000ull);

@@ -1,6 +1,6 @@
 // Device helpers shared by the factorisation and the solve kernels: the global timer, bounded
 // waits on counters written by other CTAs (polling with sleeps, or with acquire loads),
-// release stores, L2-only loads, the SM count.
+// release stores, L2-only loads.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -61,17 +61,6 @@ __device__ __forceinline__ bool wait_flag(const int* p, int v, int* err,
 template <typename T>
 __device__ __forceinline__ T ldcg(const T* p) {
   return __ldcg(p);
-}
-
-inline int num_sms() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
-  return sms;
 }
 
 }  // namespace ds

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "defsolve.h"
+#include "per_device.h"
 
 namespace ds {
 
@@ -116,6 +117,63 @@ constexpr int kTile = 256;        // threads per CTA of the ICP pass
 constexpr int kSegPerCta = kTile / 32;  // warps (concurrent segments) per CTA of the ICP pass
 constexpr int kSegPerWarp = 4;          // segments each ICP warp takes in turn
 constexpr int kOuts = 10 * 36 + 24;  // per-segment outputs: 10 blocks of 6x6, 24 gradient entries
+
+// ----------------------------------------------------------------------------- launch set-up
+
+// A launch setting computed once per device (a shared-memory attribute set, an occupancy, the SM
+// count): kernel attributes are per device, so the value is cached per device (PerDeviceValue,
+// per_device.h) for the device current in the calling thread.
+class PerDevice {
+ public:
+  template <typename F>
+  int get(F&& compute) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    const int v = cache_.get(dev, compute);
+    if (v <= 0) cudaGetLastError();
+    return v;
+  }
+
+ private:
+  PerDeviceValue cache_;
+};
+
+// Sets a kernel's dynamic shared-memory limit once per device; false if the attribute call fails.
+template <typename K>
+bool set_smem_once(PerDevice& pd, K kernel, int bytes) {
+  return pd.get([&] {
+           return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       bytes) == cudaSuccess ? 1 : 0;
+         }) > 0;
+}
+
+// Resident CTAs per SM of a kernel (clamped to [1, cap]), once per device.
+template <typename K>
+int ctas_per_sm_once(PerDevice& pd, K kernel, int threads, size_t smem, int cap) {
+  const int v = pd.get([&] {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess)
+      return 0;
+    return n < 1 ? 1 : (n > cap ? cap : n);
+  });
+  return v > 0 ? v : 1;
+}
+
+// SMs of the current device (once per device).
+inline int num_sms() {
+  static PerDevice pd;
+  const int v = pd.get([] {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return 0;
+    return sms;
+  });
+  return v > 0 ? v : 1;
+}
 
 // ----------------------------------------------------------------------------- launchers
 // frame.cu

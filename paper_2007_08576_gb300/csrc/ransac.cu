@@ -554,11 +554,9 @@ void launch_ransac(const float* depth0, int W, ds_intrinsics K, const int* midx,
   int sm = ransac_smem_bytes(M);
   int use_smem = sm <= 220 * 1024;
   if (use_smem) {
-    static bool attr_done = false;
-    if (!attr_done) {
-      cudaFuncSetAttribute(k_ransac_hyp, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-      attr_done = true;
-    }
+    static PerDevice attr;
+    // a failed attribute set leaves the launch to fail, which the caller's error check reports
+    set_smem_once(attr, k_ransac_hyp, 220 * 1024);
   } else {
     sm = 0;
   }
@@ -743,8 +741,14 @@ extern "C" int ds_ransac_noalloc(const float* depth0, int32_t W, int32_t H, ds_i
         cudaGetLastError();
         return DS_ERR_CUDA;
       }
+      // the kernel's shared-memory limit is a per-device setting too; the device is only marked
+      // set up once both calls succeeded, so a failure is retried by the next call
+      if (cudaFuncSetAttribute(k_ransac_hyp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               220 * 1024) != cudaSuccess) {
+        cudaGetLastError();
+        return DS_ERR_CUDA;
+      }
       base_of[dev] = p;
-      cudaFuncSetAttribute(k_ransac_hyp, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     }
     base = (unsigned char*)base_of[dev];
   }

@@ -218,11 +218,8 @@ __global__ __launch_bounds__(256) void k_trsv_dag(const ProbDesc* const* __restr
 template <typename T>
 void launch_trsv_dag(const BatchTabs& B, int solve_id, bool from_r, bool assign, cudaStream_t s) {
   constexpr int TB = sizeof(T) == 8 ? 32 : 64;
-  static int per_sm = 0;
-  if (!per_sm) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trsv_dag<T, TB>, 256, 0);
-    per_sm = std::max(1, std::min(per_sm, 4));
-  }
+  static PerDevice occ;
+  const int per_sm = ctas_per_sm_once(occ, k_trsv_dag<T, TB>, 256, 0, 4);
   const int nticket = B.P * 2 * B.max_nt;
   const int grid = std::min(nticket, per_sm * num_sms());
   k_trsv_dag<T, TB><<<grid, 256, 0, s>>>(B.d, B.P, nticket, solve_id, from_r ? 1 : 0,

@@ -909,11 +909,8 @@ void launch_arap_assemble(const BatchTabs& B, bool first, bool lin_only, cudaStr
                           bool diag_only) {
   // dynamic shared memory: the node -> data block map of the row and the 6-row panel
   const int sm = sizeof(int) * kArapMaxN + sizeof(float) * 6 * 6 * kArapChunk;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_arap_assemble<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    attr = true;
-  }
+  static PerDevice attr;
+  set_smem_once(attr, k_arap_assemble<T>, sm);
   k_arap_assemble<T><<<B.n_rows, kArapChunk, sm, s>>>(B.d, B.rows, first ? 1 : 0,
                                                        lin_only ? 1 : 0, diag_only ? 1 : 0, 0);
   ++g_launches;
@@ -925,11 +922,8 @@ template void launch_arap_assemble<double>(const BatchTabs&, bool, bool, cudaStr
 template <typename T>
 void launch_arap_deferred(const BatchTabs& B, cudaStream_t s) {
   const int sm = sizeof(int) * kArapMaxN + sizeof(float) * 6 * 6 * kArapChunk;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_arap_assemble<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    attr = true;
-  }
+  static PerDevice attr;
+  set_smem_once(attr, k_arap_assemble<T>, sm);
   k_arap_assemble<T><<<B.n_rows, kArapChunk, sm, s>>>(B.d, B.rows, 0, 0, 0, 1);
   ++g_launches;
 }

@@ -28,7 +28,8 @@ EXPORTS = [
     "ds_batch_destroy", "ds_batch_set_tracing", "ds_batch_phase_times", "ds_batch_set_graph", "ds_get_deformation", "ds_get_deformation64",
     "ds_set_deformation", "ds_get_inlier_mask", "ds_get_ransac", "ds_get_cost",
     "ds_get_blend_table", "ds_get_frame_points", "ds_linearize", "ds_set_tracing",
-    "ds_get_phase_times", "ds_get_counters", "ds_ransac_noalloc", "ds_selftest_bounded_wait",
+    "ds_get_phase_times", "ds_get_counters", "ds_get_device_bytes", "ds_ransac_noalloc",
+    "ds_selftest_bounded_wait",
     "ds_destroy", "ds_status_str", "ds_version",
     "ds_orb_default_params", "ds_orb_create", "ds_orb_detect", "ds_orb_num_keypoints",
     "ds_orb_get_keypoints", "ds_orb_match", "ds_orb_num_matches", "ds_orb_get_matches",
@@ -115,6 +116,7 @@ def lib(path: str | None = None):
         "ds_set_tracing": (i32, [vp, i32]),
         "ds_get_phase_times": (i32, [vp, vp]),
         "ds_get_counters": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
+        "ds_get_device_bytes": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
         "ds_ransac_noalloc": (i32, [vp, i32, i32, DsIntrinsics, vp, vp, i32, vp, i32, i32, f64,
                                     f64, vp, vp, vp, vp, vp]),
         "ds_selftest_bounded_wait": (i32, [i32, ctypes.c_int64, i32, ctypes.POINTER(f64)]),
@@ -319,6 +321,12 @@ def ds_get_counters(h=None) -> int:
     k = ctypes.c_int64()
     _check("ds_get_counters", lib().ds_get_counters(h, ctypes.byref(k)))
     return k.value
+
+
+def ds_get_device_bytes(h) -> int:
+    b = ctypes.c_int64()
+    _check("ds_get_device_bytes", lib().ds_get_device_bytes(h, ctypes.byref(b)))
+    return b.value
 
 
 def _dev_ptr(t, itemsize):

@@ -142,6 +142,10 @@ class GpuEngine:
         q, t, p = s.deformation()
         return q, t, p
 
+    def device_bytes(self, s) -> int:
+        """Bytes the library reports the stream's handle holds now."""
+        return self.d.ds_get_device_bytes(s.h)
+
 
 class Server:
     def __init__(self, engine, budget_bytes: int, iters: int = 10, max_batch: int = 64,
@@ -189,7 +193,7 @@ class Server:
             fut.cancel()
         if st["solver"] is not None:
             self.engine.destroy(st["solver"])
-            self.used -= st["bytes"]
+            self.used -= st.get("counted", 0)
         else:
             self.waiting.remove(sid)
         del self.streams[sid]
@@ -203,15 +207,30 @@ class Server:
                 break
             self.waiting.popleft()
             st["solver"] = self.engine.create(st["spec"])
-            self.used += st["bytes"]
+            self._account(st)
+
+    def _account(self, st):
+        """Counts a stream at the larger of its estimate and what the engine reports it holds
+        (the library's own allocation count), so growth the estimate missed is not lost."""
+        actual = int(getattr(self.engine, "device_bytes", lambda s: 0)(st["solver"]))
+        new = max(st["bytes"], actual)
+        self.used += new - st.get("counted", 0)
+        st["counted"] = new
+        st["bytes"] = new
 
     # -- frames
     def submit(self, sid, frame: FrameIn, t_arrival=None) -> Future:
+        """Queues a frame. A frame with more matches than the stream's max_matches is refused
+        (ValueError): its buffers would outgrow the device bytes the stream was admitted with."""
+        st = self.streams[sid]
+        if frame.match_idx is not None and len(frame.match_idx) > st["spec"].max_matches:
+            raise ValueError(f"stream {sid}: {len(frame.match_idx)} matches exceed its "
+                             f"max_matches = {st['spec'].max_matches}")
         fut = Future()
         t = self.clock() if t_arrival is None else t_arrival
         if self.t_first is None:
             self.t_first = t
-        self.streams[sid]["queue"].append((fut, t, frame))
+        st["queue"].append((fut, t, frame))
         return fut
 
     def poll(self) -> int:
@@ -245,6 +264,7 @@ class Server:
                 st = self.streams[sid]
                 fut, t_arr, frame = st["queue"].popleft()
                 self.engine.submit(st["solver"], frame)
+                self._account(st)
                 st["busy"] = True
                 solvers.append(st["solver"])
                 items.append((fut, t_arr))

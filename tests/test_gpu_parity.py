@@ -183,20 +183,6 @@ def test_solve_matches_oracle_mid_ragged(d, mid):
     s.close()
 
 
-def test_solve_matches_oracle_full_size_frame(d):
-    """The benchmark's workload size: 320x240 template, 256 nodes, 2000 matches."""
-    sc = scene(CONFIGS["seq_320x240_n256"], 1000)
-    fr = sc.frames[0]
-    p = d.default_params()
-    s, st, q, t = gpu_frame(d, sc, fr, p)
-    tpl, res = _oracle(sc, fr, oracle_params(p))
-    err = np.abs(tpl.g + t - res.pos).max()
-    assert err <= POS_TOL_MM, err
-    rel = np.abs(np.array(st.cost[:10]) - np.array(res.costs)) / np.array(res.costs)
-    assert rel.max() <= COST_RTOL, rel
-    s.close()
-
-
 def test_warm_started_sequence(d):
     """Three consecutive frames, each warm-started from the previous result on both sides."""
     from synth.scene import Config
@@ -527,27 +513,6 @@ def test_block_jacobi_full_size_frame_and_batch_rule(d, tiny):
 
 
 # ----------------------------------------------------------------------------- largest sizes
-
-
-@pytest.mark.gpu
-def test_full_size_640x480_n1024_two_iterations(d):
-    """The largest workload (640x480 template, 1024 control points: 6144 unknowns, a dense
-    6144 x 6144 system; 4000 matches, 50 % outliers): RANSAC mask bit-exact, control points and
-    costs at the parity bar after two Gauss-Newton iterations (the FP64 oracle needs ~16 s and
-    ~7 GB per iteration at this size)."""
-    sc = scene(CONFIGS["seq_640x480_n1024"], 2000)
-    fr = sc.frames[0]
-    p = d.default_params()
-    s, st, q, t = gpu_frame(d, sc, fr, p, iters=2)
-    tpl, res = _oracle(sc, fr, oracle_params(p), iters=2)
-    mask = s.mask()
-    listed, _ = ransac_listed(res.ransac, p.H_mm)
-    assert np.array_equal(mask[~listed], res.ransac["mask"][~listed])
-    err = np.abs(tpl.g + t - res.pos).max()
-    assert err <= POS_TOL_MM, err
-    rel = np.abs(np.array(st.cost[:2]) - np.array(res.costs)) / np.array(res.costs)
-    assert rel.max() <= COST_RTOL, rel
-    s.close()
 
 
 @pytest.mark.gpu

@@ -149,6 +149,50 @@ def test_served_results_equal_alone():
     assert st["frames"] == 9
     for i in range(3):
         srv.close_stream(i)
+    # the served results also equal the FP64 oracle's warm-started sequence of each stream
+    from gpu_common import POS_TOL_MM, oracle_params
+    from oracle import solver
+    prm = oracle_params(p)
+    for s, sc in enumerate(scenes):
+        tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes, prm)
+        q0 = t0 = None
+        for k, f in enumerate(sc.frames):
+            res = solver.solve_frame(tpl, f.depth, f.match_idx, f.match_xyz, f.hyp, prm, 10,
+                                     q0=q0, t0=t0)
+            q0, t0 = res.q, res.t
+            assert np.abs(futs[s][k].result().pos - res.pos).max() <= POS_TOL_MM, (s, k)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,ftc", [(0, 0), (1, 0), (2, 0), (2, 1)])
+def test_admission_estimate_covers_the_librarys_allocations(prec, ftc):
+    """The admitter's per-stream estimate (stream_bytes) against the bytes the library reports
+    the handle holds (ds_get_device_bytes, its own allocation count) after a full-size frame
+    (320x240 template, 256 control points, 2000 matches) is submitted and solved: never below
+    it, and within 10 % above it. The device's free memory (cudaMemGetInfo) drops by at least
+    the library's count."""
+    torch = pytest.importorskip("torch")
+    from gpu_common import lib
+    from synth import CONFIGS, make_scene
+    d = lib()
+    sc = make_scene(CONFIGS["seq_320x240_n256"], 1000, n_frames=1)
+    f = sc.frames[0]
+    M = len(f.match_idx)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    s = d.Solver(sc.template_depth, sc.K, sc.nodes, d.default_params(precision=prec,
+                                                                      factor_tc=ftc))
+    s.submit(f.depth, f.match_idx, f.match_xyz, f.hyp)
+    s.solve(10, stats=True)
+    actual = d.ds_get_device_bytes(s.h)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    est = stream_bytes(sc.W, sc.H, len(sc.nodes), M, prec)
+    s.close()
+    assert actual > 0
+    assert est >= actual, (est, actual)
+    assert est <= 1.10 * actual, (est, actual)
+    assert free0 - free1 >= actual, (free0 - free1, actual)
 
 
 def test_inflight_cap_coalesces_waiting_frames():
@@ -168,3 +212,39 @@ def test_inflight_cap_coalesces_waiting_frames():
     srv.drain()
     assert len(eng.launches) == 2 and len(eng.launches[1]["ids"]) == 3
     assert srv.stats()["frames"] == 4
+
+
+def test_frames_beyond_max_matches_are_refused():
+    srv = Server(FakeEngine(), budget_bytes=1 << 40)
+    srv.open_stream("a", _spec())                    # max_matches = 200
+    ok = FrameIn(None, np.zeros(200, np.int32), np.zeros((200, 3), np.float32), None)
+    srv.submit("a", ok)
+    big = FrameIn(None, np.zeros(201, np.int32), np.zeros((201, 3), np.float32), None)
+    with pytest.raises(ValueError):
+        srv.submit("a", big)
+    srv.drain()
+    assert srv.stats()["frames"] == 1
+
+
+def test_accounting_follows_the_engines_reported_bytes():
+    """A stream is counted at the larger of its estimate and the bytes the engine reports it
+    holds (the library's own allocation count), after admission and after every submission;
+    closing it returns exactly what was counted."""
+    class Reporting(FakeEngine):
+        extra = 0
+
+        def device_bytes(self, s):
+            return stream_bytes(80, 60, 32, 200, 2) + self.extra
+
+    eng = Reporting()
+    one = stream_bytes(80, 60, 32, 200, 2)
+    srv = Server(eng, budget_bytes=10 * one)
+    srv.open_stream("a", _spec())
+    assert srv.used == one
+    eng.extra = 1000                                  # the library holds more than estimated
+    srv.submit("a", _frame())
+    srv.poll()
+    assert srv.used == one + 1000
+    srv.drain()
+    srv.close_stream("a")
+    assert srv.used == 0

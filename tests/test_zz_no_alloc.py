@@ -66,3 +66,68 @@ def test_noalloc_ransac_rejects_oversize():
                             z(157, dt=torch.int32), z(M), z(2, dt=torch.int32),
                             z(30, dt=torch.float64))
     assert e.value.status == d.DS_ERR_ARG
+
+
+def _noalloc(d, torch, dev, sc, midx_np, hyp_np, fr, p):
+    M = len(midx_np)
+    t = lambda a, dt=None: torch.from_numpy(np.ascontiguousarray(a, dt)).to(dev)
+    bits = torch.zeros((M + 31) // 32, dtype=torch.int32, device=dev)
+    w = torch.zeros(M, dtype=torch.float32, device=dev)
+    kept = torch.zeros(2, dtype=torch.int32, device=dev)
+    score = torch.zeros(p.n_hyp, dtype=torch.float64, device=dev)
+    d.ds_ransac_noalloc(t(sc.template_depth, np.float32), sc.W, sc.H, sc.K, t(midx_np),
+                        t(fr.match_xyz, np.float32), M, t(hyp_np), p.n_hyp, p.n_reweight, p.H_mm,
+                        p.keep_frac, bits, w, kept, score)
+    return (bits.cpu().numpy().view(np.uint32), w.cpu().numpy(), kept.cpu().numpy().view(np.uint32),
+            score.cpu().numpy())
+
+
+def test_noalloc_ransac_at_its_limits_matches_handle_path():
+    """M = DS_NOALLOC_MAX_MATCHES = 4000 matches and 64 references (DS_MAX_HYP): the largest
+    case, whose per-match staging takes 224,000 B of the kernel's dynamic shared memory."""
+    torch = pytest.importorskip("torch")
+    from synth.scene import Config
+    d = lib()
+    p = d.default_params(n_hyp=64)
+    dev = torch.device("cuda", 0)
+    cfg = Config("na_200x150_m4000", 200, 150, 40, 4000, 8, 0.45, 0.5, 0.05, 6.0, 0.0, 2.0, 1.5,
+                 1, n_hyp=64)
+    sc = make_scene(cfg, 777)
+    fr = sc.frames[0]
+    M = len(fr.match_idx)
+    assert M == 4000 and len(fr.hyp) == 64
+    ref_bits, ref_w, ref_kept, ref_score = _handle_path(d, sc, fr, p)
+    for _ in range(2):
+        bits, w, kept, score = _noalloc(d, torch, dev, sc, fr.match_idx, fr.hyp, fr, p)
+        assert np.array_equal(unpack_bits(bits, M), unpack_bits(ref_bits, M))
+        assert np.array_equal(kept, ref_kept)
+        assert np.abs(w - ref_w).max() <= 1e-6
+        assert np.abs(score - ref_score).max() <= 1e-9 * np.abs(ref_score).max()
+
+
+def test_noalloc_ransac_reports_bad_indices_and_recovers():
+    """An out-of-range match pixel and an out-of-range reference id are replaced on the device
+    (no read outside the caller's buffers) and reported as DS_ERR_ARG after the run; the next
+    call with good indices is clean and equals the handle path."""
+    torch = pytest.importorskip("torch")
+    d = lib()
+    p = d.default_params()
+    dev = torch.device("cuda", 0)
+    sc = make_scene(MID, 4242)
+    fr = sc.frames[0]
+    M = len(fr.match_idx)
+    bad_idx = fr.match_idx.copy()
+    bad_idx[5] = sc.W * sc.H + 17          # past the image
+    bad_hyp = fr.hyp.copy()
+    bad_hyp[3] = M + 2                     # past the matches
+    with pytest.raises(d.DsError) as e:
+        _noalloc(d, torch, dev, sc, bad_idx, fr.hyp, fr, p)
+    assert e.value.status == d.DS_ERR_ARG
+    with pytest.raises(d.DsError) as e:
+        _noalloc(d, torch, dev, sc, fr.match_idx, bad_hyp, fr, p)
+    assert e.value.status == d.DS_ERR_ARG
+    ref_bits, ref_w, ref_kept, ref_score = _handle_path(d, sc, fr, p)
+    bits, w, kept, score = _noalloc(d, torch, dev, sc, fr.match_idx, fr.hyp, fr, p)
+    assert np.array_equal(unpack_bits(bits, M), unpack_bits(ref_bits, M))
+    assert np.array_equal(kept, ref_kept)
+    assert np.abs(w - ref_w).max() <= 1e-6
