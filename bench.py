@@ -1,23 +1,29 @@
 #!/usr/bin/env python3
 """Benchmark of the per-frame deformation solve on GB300.
 
-Workload: concurrent streams of the 320x240 / 256-control-point / 2000-match sequence. A frame is
-frame preparation, 1-point RANSAC preselection and 10 damped Gauss-Newton iterations (ICP + ORB +
-dense ARAP, assembly, Cholesky, solves, update), warm-started from the stream's previous frame.
-A step is one frame of every one of S streams (default 32), solved as one batch in mixed
-precision (FP32 J^T J and factorisation; two refinement steps whose residuals are accumulated
-in double-float FP32 arithmetic, ~48 bits).
+Headline workload (batched uneven solves): 64 independent sequences, templates drawn from
+{160x120, 320x240, 640x480}, control points uniform in [64, 1024] (384 to 6144 unknowns, one
+dense damped system each), outlier rates uniform in [20 %, 60 %] (synth/workloads.py). A frame is
+frame preparation, 1-point RANSAC preselection and 10 damped Gauss-Newton iterations (ICP + ORB
++ dense ARAP, assembly, Cholesky, solves, update), warm-started from the sequence's previous
+frame. A step is one frame of every sequence, solved as one batch: one persistent launch per
+kernel and iteration over all 64 problems, replayed from a CUDA graph. Precision (the mixed
+mode): FP32 residuals, Jacobians and J^T J, FP32 Cholesky (tile kernel picked per batch by the
+library's tuner), two refinement steps whose residuals are accumulated to ~48 bits
+(double-float), the state in FP64.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32_refine|fp32|fp64]
   python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
 
-Prints one JSON line (rank 0). `value` is frames/s with inputs resident in device memory,
-timed with CUDA events on the library's stream, L2 flushed before every step (outside the
-events). Next to it: the plain single-stream FP32 solve (the comparison the metric names), a
-served run with Poisson arrivals (continuous batching, p50/p99 latency), `e2e` (the same metric
-through the C ABI with pinned host buffers: host->device copies of the frames, the solve and the
-device->host read of the deformations, wall clock), the factorisation's roofline and clocks.
-Multi-GPU runs are independent replicas (one set of streams per rank, no collective).
+Prints one JSON line (rank 0). `value` is frames/s with inputs resident in device memory, timed
+with CUDA events on the batch's stream, L2 flushed before every step. Next to it: `e2e` (the
+same batch through the C ABI from pinned host buffers: frames copied in, deformations read out,
+every step, wall clock, with each frame's submit-to-host latency), the error against the FP64
+oracle on a sample of the timed problems, the FP64-factor mode on the same batch, the plain
+single-stream FP32 solve (the comparison the metric names), the 640x480 / 1024-node sequence
+alone, the served loop (32 of the sequences with Poisson arrivals: continuous batching,
+p50/p99 frame latency), the dominant kernel's roofline and the clocks. Multi-GPU runs are
+independent replicas (one set of sequences per rank, no collective).
 """
 from __future__ import annotations
 
@@ -35,23 +41,21 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "seq_320x240_n256"
+WORKLOAD = "batched_mixed_64"
 ITERS = 10
 METRIC = "frames/s and p50/p99 frame latency vs plain GPU solve, at ≤1e-3 mm error"
 PREC = {"fp64": 0, "fp32": 1, "fp32_refine": 2}
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate per GPU (nominal)
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_chol_dag launch on this
-# workload (32 problems, FP32 factor), from an ncu capture of one launch of the warm-up steps
-# (`ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_chol_dag -s 2 -c 1 ...`).
-# It describes the kernel source it was taken on (first 16 hex digits of the sha256 of
-# csrc/chol.cu + csrc/dev_util.cuh) and is reported as null for any other.
-CHOL_TRAFFIC = {"chol_sha256": "a3f5333f6fac6ff8", "precision": 2, "streams": 32,
-                "bytes": 663056896 + 355572480}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the dominant kernel
+# on the headline workload, from an ncu capture (profiles/), valid only for the kernel source it
+# was taken on (first 16 hex digits of the sha256 of csrc/chol.cu + csrc/dev_util.cuh) and the
+# same workload and factor kernel; reported as null otherwise.
+FACTOR_TRAFFIC = None
 
 
 def max_over_ranks(x, world, dev):
-    """The slowest rank's time: replicas run independent streams, the job ends with the last."""
+    """The slowest rank's time: replicas run independent sequences, the job ends with the last."""
     if world <= 1:
         return float(x)
     import torch
@@ -66,34 +70,26 @@ def job_throughput(world, units_per_rank, total_s):
     return world * units_per_rank / total_s
 
 
-def replica_seeds(rank, n_scenes):
-    """Scene seeds of a rank: every replica solves its own streams."""
-    return [1000 + 100 * rank + k for k in range(n_scenes)]
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
 def _measured_bf16():
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
-    try:
-        with open(path) as f:
-            return float(json.load(f)["bf16_tflops"])
-    except (OSError, KeyError, ValueError):
-        return 1900.0   # earlier GB300 measurement, used when the file is absent
+    return float(_peaks().get("bf16_tflops", 1900.0))   # fallback: earlier GB300 measurement
 
 
 def _measured_hbm():
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
-    try:
-        with open(path) as f:
-            return float(json.load(f)["hbm_gbs"])
-    except (OSError, KeyError, ValueError):
-        return 6800.0   # earlier GB300 measurement, used when the file is absent
+    return float(_peaks().get("hbm_gbs", 6800.0))       # fallback: earlier GB300 measurement
 
 
 def _chol_source_digest():
-    """First 16 hex digits of the sha256 of the factorisation kernel's sources (chol.cu and the
-    device helpers it includes)."""
-    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2007_08576_gb300",
-                        "csrc")
+    """First 16 hex digits of the sha256 of the factorisation kernel's sources."""
+    csrc = os.path.join(ROOT, "paper_2007_08576_gb300", "csrc")
     h = hashlib.sha256()
     for name in ("chol.cu", "dev_util.cuh"):
         with open(os.path.join(csrc, name), "rb") as f:
@@ -101,10 +97,10 @@ def _chol_source_digest():
     return h.hexdigest()[:16]
 
 
-def _chol_traffic(prec, streams):
-    digest = _chol_source_digest()
-    c = CHOL_TRAFFIC
-    if digest != c["chol_sha256"] or prec != c["precision"] or streams != c["streams"]:
+def _factor_traffic(workload, kernel):
+    c = FACTOR_TRAFFIC
+    if (c is None or c["chol_sha256"] != _chol_source_digest() or c["workload"] != workload
+            or c["kernel"] != kernel):
         return None
     return c["bytes"]
 
@@ -114,6 +110,10 @@ def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def _cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
 
 
 class ClockSampler:
@@ -170,55 +170,108 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def gen_frames(n_frames: int, seed: int):
-    from synth import CONFIGS, make_scene
-    return make_scene(CONFIGS[WORKLOAD], seed, n_frames=n_frames)
-
-
 def oracle_params(args):
     """The oracle's parameters for the method variant the GPU arm runs."""
     from oracle import solver
     return solver.Params(solver=args.solver, assoc=args.assoc, ransac_o1=args.ransac_o1)
 
 
-def variant_params(d, args, prec):
+def variant_params(d, args, prec, **kw):
     """The CUDA path's ds_params for the same variant."""
     return d.default_params(precision=prec, factor_tc=1 if args.factor_tc else 0,
                             solver=1 if args.solver == "block_jacobi" else 0,
                             assoc=1 if args.assoc == "bilinear" else 0,
-                            ransac_o1=1 if args.ransac_o1 == "warm" else 0)
+                            ransac_o1=1 if args.ransac_o1 == "warm" else 0, **kw)
 
 
-def cpu_baseline(sc, prm):
-    """The FP64 oracle on the host cores: one whole frame (prep, RANSAC, 10 iterations)."""
+# ----------------------------------------------------------------------------- oracle jobs
+
+
+def error_sample(problems):
+    """The timed problems whose cold-start first frame the oracle re-solves: the one with the
+    fewest control points of each template size (a bounded sample of CPU work)."""
+    out = []
+    for W in sorted({p.cfg.W for p in problems}):
+        ks = [k for k, p in enumerate(problems) if p.cfg.W == W]
+        out.append(min(ks, key=lambda k: problems[k].cfg.N))
+    return out
+
+
+def _oracle_frame(job):
+    """Oracle solve of a cold-started first frame in a spawned worker (BLAS threads set by the
+    parent's environment): control-point positions, costs, RANSAC mask, wall time."""
+    cfg, seed, prm, iters = job
     from oracle import solver
-    tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes, prm)
+    from synth import make_scene
+    sc = make_scene(cfg, seed, n_frames=1)
     f = sc.frames[0]
     t0 = time.perf_counter()
-    solver.solve_frame(tpl, f.depth, f.match_idx, f.match_xyz, f.hyp, prm, iters=ITERS)
+    tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes, prm)
+    res = solver.solve_frame(tpl, f.depth, f.match_idx, f.match_xyz, f.hyp, prm, iters)
     dt = time.perf_counter() - t0
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": 1.0 / dt, "unit": "frames/s", "cores": cores, "kind": "oracle",
-            "sample": f"one {WORKLOAD} frame (prep, RANSAC, {ITERS} GN iterations), "
-                      f"{dt:.1f} s wall, numpy/LAPACK threads on {cores} cores"}
+    return {"g": tpl.g, "pos": res.pos, "cost": np.array(res.costs), "mask": res.ransac["mask"],
+            "d": res.ransac["d"], "kept": res.ransac["kept"], "score": res.ransac["score"],
+            "seconds": dt}
 
 
-def measure_dgemm_tflops(torch, dev):
-    """cuBLAS FP64 GEMM rate (context for the FP64 roofline)."""
-    n = 4096
-    a = torch.randn(n, n, dtype=torch.float64, device=dev)
-    b = torch.randn(n, n, dtype=torch.float64, device=dev)
-    for _ in range(2):
-        a @ b
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    reps = 3
-    for _ in range(reps):
-        a @ b
-    e1.record()
-    torch.cuda.synchronize()
-    return 2.0 * n ** 3 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12
+def start_oracle_pool(jobs, threads_each):
+    """Spawned worker processes (started before any CUDA call) solving the oracle jobs while the
+    GPU runs; each worker's BLAS uses `threads_each` threads."""
+    import multiprocessing as mp
+    keys = ["OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"]
+    old = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = str(threads_each)
+    try:
+        pool = mp.get_context("spawn").Pool(len(jobs))
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return pool, pool.map_async(_oracle_frame, jobs, chunksize=1)
+
+
+def _listed(res, H, band=1e-6):
+    listed = np.zeros(len(res["mask"]), dtype=bool)
+    for h in np.flatnonzero(res["kept"]):
+        listed |= np.abs(res["d"][h] - H) <= band
+    cut = 0.5 * res["score"].max()
+    for h in np.flatnonzero(np.abs(res["score"] - cut) <= 1e-6 * abs(cut)):
+        listed |= res["d"][h] <= H + band
+    return listed
+
+
+def gpu_result(d, h, sc):
+    """A handle's solved frame as the oracle comparison reads it: FP64 translations, the cost
+    at the last linearisation, the preselection mask (the scene's first frame)."""
+    _, t = d.ds_get_deformation64(h)
+    M = len(sc.frames[0].match_idx)
+    bits = np.zeros((M + 31) // 32, np.uint32)
+    d.ds_get_inlier_mask(h, bits)
+    k = np.arange(M)
+    mask = ((bits[k // 32] >> (k % 32).astype(np.uint32)) & 1).astype(bool)
+    return {"t": t, "mask": mask, "cost": d.ds_get_cost(h)}
+
+
+def compare(gpu, ref, H):
+    """Error of one GPU frame against the oracle's: max / RMS control-point distance (mm), the
+    relative difference of the cost at the last linearisation, mask bits differing outside the
+    listed band."""
+    dp = np.linalg.norm(ref["g"] + gpu["t"] - ref["pos"], axis=1)
+    crel = abs(float(gpu["cost"]) - float(ref["cost"][-1])) / float(ref["cost"][-1])
+    listed = _listed(ref, H)
+    bad = int(np.count_nonzero((gpu["mask"] != ref["mask"]) & ~listed))
+    return {"max_err_mm": float(dp.max()), "rms_err_mm": float(np.sqrt((dp ** 2).mean())),
+            "cost_rel_err": crel, "mask_bits_differing": bad}
+
+
+def _rounded(c):
+    return {a: (float(f"{b:.4g}") if isinstance(b, float) else b) for a, b in c.items()}
+
+
+# ----------------------------------------------------------------------------- GPU arm
 
 
 def orb_frontend(d, torch, dev, S, K, W, n_scenes, flush):
@@ -228,7 +281,7 @@ def orb_frontend(d, torch, dev, S, K, W, n_scenes, flush):
     Device time from an event before the fork to an event after the join."""
     from synth import CONFIGS, make_textured_scene, orb_pattern
     pat = orb_pattern(7)
-    scenes = [make_textured_scene(CONFIGS[WORKLOAD], 1000 + j, n_frames=1) for j in range(n_scenes)]
+    scenes = [make_textured_scene(CONFIGS["seq_320x240_n256"], 1000 + j, n_frames=1) for j in range(n_scenes)]
     streams = [torch.cuda.Stream(device=dev) for _ in range(S)]
     tm, lv, imgs = [], [], []
     for j in range(S):
@@ -292,10 +345,89 @@ def _stats_ms(xs):
             "mean": round(float(a.mean()), 4)}
 
 
+class BatchRun:
+    """One batch of handles over a list of scenes (one handle per sequence), frames resident on
+    the device, driven through the C ABI."""
+
+    def __init__(self, d, torch, dev, scenes, prm, stream):
+        self.d, self.torch, self.dev, self.scenes = d, torch, dev, scenes
+        self.stream = stream
+        self.handles, self.hstreams = [], []
+        for sc in scenes:
+            hs = torch.cuda.Stream(device=dev)    # per-sequence frame work overlaps
+            h = d.ds_create_template(sc.template_depth, sc.W, sc.H, sc.K, prm, hs.cuda_stream)
+            d.ds_set_control_points(h, sc.nodes)
+            self.handles.append(h)
+            self.hstreams.append(hs)
+        self.frames = [[(torch.from_numpy(f.depth).to(dev), torch.from_numpy(f.match_idx).to(dev),
+                         torch.from_numpy(np.ascontiguousarray(f.match_xyz)).to(dev),
+                         torch.from_numpy(f.hyp).to(dev), len(f.match_idx)) for f in sc.frames]
+                       for sc in scenes]
+        self.batch = d.ds_batch_create(self.handles, stream.cuda_stream)
+
+    def reset(self):
+        for sc, h in zip(self.scenes, self.handles):
+            N = len(sc.nodes)
+            self.d.ds_set_deformation(h, np.tile(np.float32([1, 0, 0, 0]), (N, 1)),
+                                      np.zeros((N, 3), np.float32))
+
+    def step(self, i, e_start=None):
+        for j, h in enumerate(self.handles):
+            if e_start is not None:
+                self.hstreams[j].wait_event(e_start)   # the frame work belongs to the step
+            fr = self.frames[j]
+            dep, mi, mx, hy, M = fr[i % len(fr)]
+            self.d.ds_submit_frame(h, dep, mi, mx, M, hy)
+        self.d.ds_batch_solve(self.batch, ITERS)
+
+    def close(self):
+        self.d.ds_batch_destroy(self.batch)
+        for h in self.handles:
+            self.d.ds_destroy(h)
+
+
+def timed_steps(run, K, W, flush, first=0):
+    """W untimed steps, then K steps back to back (the host enqueues step i + 1 while the device
+    runs step i), L2 flushed before each; returns (per-step ms, total s, host enqueue ms)."""
+    torch = run.torch
+    for i in range(W):
+        run.step(first + i)
+    torch.cuda.synchronize()
+    ev, host = [], []
+    for i in range(K):
+        with torch.cuda.stream(run.stream):
+            flush.fill_(float(i))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(run.stream)
+        th = time.perf_counter()
+        run.step(first + W + i, e0)
+        host.append((time.perf_counter() - th) * 1e3)
+        e1.record(run.stream)
+        ev.append((e0, e1))
+    ev[-1][1].synchronize()
+    run.d.ds_batch_status(run.batch)
+    torch.cuda.synchronize()
+    return ([a.elapsed_time(b) for a, b in ev], ev[0][0].elapsed_time(ev[-1][1]) * 1e-3, host)
+
+
 def run_gpu(args):
+    from synth.workloads import make_scenes, mixed_problems
+    rank, world, local = _dist()
+    problems = mixed_problems(args.problems)
+    sample = error_sample(problems)
+    prm_o = oracle_params(args)
+    pool = pending = None
+    c3_cfg = None
+    if rank == 0 and not args.no_oracle:
+        from synth import CONFIGS
+        c3_cfg = CONFIGS["seq_640x480_n1024"]
+        jobs = [(problems[k].cfg, problems[k].seed, prm_o, ITERS) for k in sample]
+        jobs.append((c3_cfg, 2000, prm_o, ITERS))
+        pool, pending = start_oracle_pool(jobs, max(1, (_cores() - 2) // len(jobs)))
+
     import torch
     import torch.distributed as dist
-    rank, world, local = _dist()
     if world > 1:
         dist.init_process_group("nccl", rank=rank, world_size=world,
                                 device_id=torch.device("cuda", local))
@@ -305,278 +437,321 @@ def run_gpu(args):
     build.build()
     from paper_2007_08576_gb300 import defsolve as d
     from paper_2007_08576_gb300.serve import FrameIn, GpuEngine, Server, StreamSpec, poisson_schedule
-
-    K, W, S = args.steps, args.warmup, args.streams
-    n_scenes = min(args.scenes, S)
-    F = args.frames
     from synth import CONFIGS, make_scene
-    scenes = [make_scene(CONFIGS[WORKLOAD], sd, n_frames=F) for sd in replica_seeds(rank, n_scenes)]
-    N = len(scenes[0].nodes)
-    M = len(scenes[0].frames[0].match_idx)
-    n = 6 * N
+
+    K, W, F = args.steps, args.warmup, args.frames
+    t_gen = time.perf_counter()
+    # every replica solves its own sequences: the scene seeds are offset per rank
+    if rank:
+        for p in problems:
+            p.seed += 100000 * rank
+    scenes = make_scenes(problems, F, processes=max(1, min(16, _cores() - 2)))
+    gen_s = time.perf_counter() - t_gen
     prec = PREC[args.precision]
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+    n_list = [6 * len(sc.nodes) for sc in scenes]
+    flops_iter = float(sum(n ** 3 / 3.0 for n in n_list))
 
-    def dev_frames(sc):
-        return [(torch.from_numpy(f.depth).to(dev), torch.from_numpy(f.match_idx).to(dev),
-                 torch.from_numpy(np.ascontiguousarray(f.match_xyz)).to(dev),
-                 torch.from_numpy(f.hyp).to(dev)) for f in sc.frames]
-
-    dframes = [dev_frames(sc) for sc in scenes]
-
-    # ---------------------------------------------------------------- batched mixed precision
-    solver_id = 1 if args.solver == "block_jacobi" else 0
+    # ------------------------------------------------------------ headline: the mixed batch
     prm = variant_params(d, args, prec)
-    handles, hstreams = [], []
-    for j in range(S):
-        sc = scenes[j % n_scenes]
-        hs = torch.cuda.Stream(device=dev)    # per-stream frame work overlaps across streams
-        h = d.ds_create_template(sc.template_depth, sc.W, sc.H, sc.K, prm, hs.cuda_stream)
-        d.ds_set_control_points(h, sc.nodes)
-        handles.append(h)
-        hstreams.append(hs)
-    batch = d.ds_batch_create(handles, stream.cuda_stream)
-    d.ds_batch_set_tracing(batch, True)
-
-    def step(i, e_start=None):
-        for j, h in enumerate(handles):
-            if e_start is not None:
-                hstreams[j].wait_event(e_start)   # the frame work belongs to the timed step
-            dep, mi, mx, hy = dframes[j % n_scenes][i % F]
-            d.ds_submit_frame(h, dep, mi, mx, M, hy)
-        d.ds_batch_solve(batch, ITERS)
-
-    for i in range(W):
-        step(i)
+    run = BatchRun(d, torch, dev, scenes, prm, stream)
+    # cold start on frame 0 (untimed): the sampled problems' results go to the oracle check
+    run.step(0)
     torch.cuda.synchronize()
+    sampled = {k: gpu_result(d, run.handles[k], scenes[k]) for k in sample}
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     k0 = d.ds_get_counters(None)
-    # Steps run back to back as a stream of frames would: the host enqueues step i + 1 while the
-    # device runs step i (no host synchronisation between steps). Each step's span is the device
-    # time from its start event (after the L2 flush) to its end event; the throughput divides
-    # the K steps' frames by the time from the first start event to the last end event.
-    step_ms, phase, host_ms = [], np.zeros(4), []
-    ev = []
     with ClockSampler(local) as clk:
-        for i in range(K):
-            with torch.cuda.stream(stream):
-                flush.fill_(float(i))
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            th = time.perf_counter()
-            # each step's frame work starts at its start event, after the previous solve: the
-            # library lets submissions overlap the previous solve (two frame slots per handle),
-            # but here that measured slower (the RANSAC CTAs take shared memory the persistent
-            # factorisation needs)
-            step(W + i, e0)
-            host_ms.append((time.perf_counter() - th) * 1e3)
-            e1.record(stream)
-            ev.append((e0, e1))
-        ev[-1][1].synchronize()
-    d.ds_batch_status(batch)
-    torch.cuda.synchronize()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
+        step_ms, total_s, host_ms = timed_steps(run, K, W, flush, first=1)
     launches = d.ds_get_counters(None) - k0
-    # phase split (linearise / factorise / solve / update, CUDA events inside the captured
-    # graph, overwritten by every solve): K more steps, each read after it completes
+    launches_per_step = launches / K
+    total_s = max_over_ranks(total_s, world, dev)
+    n_p = len(scenes)
+    value = job_throughput(world, n_p * K, total_s)
+    # phase split (linearise / factorise / solve / update) from CUDA events inside the graph
+    d.ds_batch_set_tracing(run.batch, True)
+    phase = np.zeros(4)
     for i in range(K):
         with torch.cuda.stream(stream):
             flush.fill_(float(i))
-        step(W + K + i)
+        run.step(1 + W + K + i)
         torch.cuda.synchronize()
-        phase += d.ds_batch_phase_times(batch)
-    total_s = max_over_ranks(ev[0][0].elapsed_time(ev[-1][1]) * 1e-3, world, dev)
-    value = job_throughput(world, S * K, total_s)
+        phase += d.ds_batch_phase_times(run.batch)
+    phase /= K
+    d.ds_batch_set_tracing(run.batch, False)
 
     # end to end through the C ABI: pinned host frames in, deformations out, every step
     pin = [[[torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
              for a in (f.depth, f.match_idx, f.match_xyz, f.hyp)] for f in sc.frames] for sc in scenes]
     outs = [[torch.empty(shape, dtype=torch.float32).pin_memory().numpy()
-             for shape in ((N, 4), (N, 3), (N, 3))] for _ in range(S)]
-    d.ds_batch_set_tracing(batch, False)
+             for shape in ((len(sc.nodes), 4), (len(sc.nodes), 3), (len(sc.nodes), 3))]
+            for sc in scenes]
 
     def e2e_submit(i):
-        for j, h in enumerate(handles):
-            dep, mi, mx, hy = pin[j % n_scenes][i % F]
-            d.ds_submit_frame(h, dep, mi, mx, M, hy)
+        for j, h in enumerate(run.handles):
+            dep, mi, mx, hy = pin[j][i % F]
+            d.ds_submit_frame(h, dep, mi, mx, len(mi), hy)
 
     def e2e_read():
-        for j, h in enumerate(handles):
+        for j, h in enumerate(run.handles):
             d.ds_get_deformation(h, *outs[j])
 
-    # As a stream of frames runs: step i + 1's frames are submitted (host-to-device copies,
-    # preparation and RANSAC, into each handle's other frame slot) while step i's batch solves,
-    # then step i's deformations are read back, then step i + 1 is solved. Every step's input
-    # copies and result reads lie inside the timed region, which spans the K steps.
+    # As a stream of frames runs: step i + 1's frames are submitted (copies, preparation and
+    # RANSAC, into each handle's other frame slot) while step i's batch solves, then step i's
+    # deformations are read back, then step i + 1 is solved. A frame's latency runs from the
+    # start of its submission to its deformation on the host.
     for i in range(W):
         e2e_submit(i)
-        d.ds_batch_solve(batch, ITERS)
+        d.ds_batch_solve(run.batch, ITERS)
         e2e_read()
     with torch.cuda.stream(stream):
         flush.fill_(0.0)
     torch.cuda.synchronize()
+    lat = []
     t0 = time.perf_counter()
+    t_sub = time.perf_counter()
     e2e_submit(W)
-    d.ds_batch_solve(batch, ITERS)
+    d.ds_batch_solve(run.batch, ITERS)
     for i in range(W, W + K):
+        t_next = time.perf_counter()
         if i + 1 < W + K:
             e2e_submit(i + 1)
         e2e_read()
+        now = time.perf_counter()
+        lat.append((now - t_sub) * 1e3)
+        t_sub = t_next
         if i + 1 < W + K:
-            d.ds_batch_solve(batch, ITERS)
+            d.ds_batch_solve(run.batch, ITERS)
     e2e_tot = max_over_ranks(time.perf_counter() - t0, world, dev)
-    f0 = scenes[0].frames[0]
-    h2d = S * (f0.depth.nbytes + f0.match_idx.nbytes + np.ascontiguousarray(f0.match_xyz).nbytes +
-               f0.hyp.nbytes)
-    d2h = S * sum(o.nbytes for o in outs[0])
-    d.ds_batch_destroy(batch)
-    for h in handles:
-        d.ds_destroy(h)
+    h2d = sum(sum(np.ascontiguousarray(a).nbytes for a in (f.depth, f.match_idx, f.match_xyz, f.hyp))
+              for f in (sc.frames[0] for sc in scenes))
+    d2h = sum(sum(o.nbytes for o in oj) for oj in outs)
+    run.close()
 
-    # ---------------------------------------------------------------- plain single-stream FP32
-    pprm = d.default_params(precision=PREC["fp32"])
-    hp = d.ds_create_template(scenes[0].template_depth, scenes[0].W, scenes[0].H, scenes[0].K,
-                              pprm, stream.cuda_stream)
-    d.ds_set_control_points(hp, scenes[0].nodes)
-    plain_ms = []
+    # ------------------------------------------------------------ FP64 factor on the same batch
+    fp64 = None
+    if prec != 0 and args.fp64_steps > 0:
+        run64 = BatchRun(d, torch, dev, scenes, variant_params(d, args, 0), stream)
+        ms64, tot64, _ = timed_steps(run64, args.fp64_steps, 1, flush)
+        run64.close()
+        fp64 = {"precision": "fp64 (FP64 Cholesky and triangular solves + 2 refinement steps)",
+                "frames_per_s": round(n_p * args.fp64_steps / tot64, 3),
+                "ms_per_step": round(tot64 * 1e3 / args.fp64_steps, 2),
+                "factor_tflops": round(ITERS * flops_iter * args.fp64_steps / tot64 / 1e12, 3),
+                "steps": args.fp64_steps, "warmup": 1,
+                "note": "factor TFLOP/s here = factorisation flops over the whole step time"}
+
+    # ------------------------------------------------------------ plain single-stream FP32 (c2)
+    c2 = make_scene(CONFIGS["seq_320x240_n256"], 1000 + 100000 * rank, n_frames=max(F, 2))
+    hp = d.ds_create_template(c2.template_depth, c2.W, c2.H, c2.K, d.default_params(precision=1),
+                              stream.cuda_stream)
+    d.ds_set_control_points(hp, c2.nodes)
+    c2dev = [(torch.from_numpy(f.depth).to(dev), torch.from_numpy(f.match_idx).to(dev),
+              torch.from_numpy(np.ascontiguousarray(f.match_xyz)).to(dev),
+              torch.from_numpy(f.hyp).to(dev), len(f.match_idx)) for f in c2.frames]
+    q_out = np.zeros((len(c2.nodes), 4), np.float32)
+    plain_ms, plain_lat = [], []
     for i in range(W + K):
         with torch.cuda.stream(stream):
             flush.fill_(float(i))
+        torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        ts = time.perf_counter()
         e0.record(stream)
-        dep, mi, mx, hy = dframes[0][i % F]
+        dep, mi, mx, hy, M = c2dev[i % len(c2dev)]
         d.ds_submit_frame(hp, dep, mi, mx, M, hy)
         d.ds_solve(hp, ITERS, False)
         e1.record(stream)
-        e1.synchronize()
+        d.ds_get_deformation(hp, q_out)
         if i >= W:
             plain_ms.append(e0.elapsed_time(e1))
+            plain_lat.append((time.perf_counter() - ts) * 1e3)
     d.ds_destroy(hp)
     plain_fps = 1e3 * len(plain_ms) / sum(plain_ms)
 
-    # ---------------------------------------------------------------- served, Poisson arrivals
-    def serve_run(rate_scale, n_frames, seed):
+    # ------------------------------------------------------------ 640x480 / 1024 nodes alone
+    c3 = None
+    if args.c3_frames > 0:
+        c3s = make_scene(CONFIGS["seq_640x480_n1024"], 2000 + 100000 * rank, n_frames=max(F, 2))
+        c3 = {"workload": "seq_640x480_n1024 (6144 unknowns), one stream"}
+        for name, pr in (("fp32_refine", 2), ("fp64", 0)):
+            r3 = BatchRun(d, torch, dev, [c3s], variant_params(d, args, pr), stream)
+            r3.step(0)
+            torch.cuda.synchronize()
+            if name == "fp32_refine":
+                c3_gpu = gpu_result(d, r3.handles[0], c3s)
+            ms3, tot3, _ = timed_steps(r3, args.c3_frames, 2, flush, first=1)
+            r3.close()
+            c3[name] = {"frames_per_s": round(args.c3_frames / tot3, 3),
+                        "latency_ms": _stats_ms(ms3)}
+
+    # ------------------------------------------------------------ served: Poisson arrivals
+    def serve_run(rate_scale, n_frames, seed, streams):
         rng = np.random.default_rng(seed)
-        rates = rng.uniform(15.0, 60.0, S) * rate_scale
+        rates = np.array([problems[j].rate_hz for j in streams]) * rate_scale
         srv = Server(GpuEngine(variant_params(d, args, prec)),
                      budget_bytes=int(0.6 * torch.cuda.mem_get_info()[0]))
-        for j in range(S):
-            sc = scenes[j % n_scenes]
-            srv.open_stream(j, StreamSpec(sc.template_depth, sc.K, sc.nodes, max_matches=M))
+        for j in streams:
+            sc = scenes[j]
+            srv.open_stream(j, StreamSpec(sc.template_depth, sc.K, sc.nodes,
+                                          max_matches=len(sc.frames[0].match_idx)))
         sched = poisson_schedule(rng, rates, n_frames)
-        cnt = [0] * S
+        cnt = {j: 0 for j in streams}
         t_start = time.perf_counter()
-        for t_arr, s_id in sched:
+        for t_arr, s_i in sched:
+            j = streams[s_i]
             now = time.perf_counter() - t_start
             while now < t_arr:
                 srv.poll()
                 now = time.perf_counter() - t_start
-            f = scenes[s_id % n_scenes].frames[cnt[s_id] % F]
-            cnt[s_id] += 1
-            srv.submit(s_id, FrameIn(f.depth, f.match_idx, f.match_xyz, f.hyp),
+            f = scenes[j].frames[cnt[j] % F]
+            cnt[j] += 1
+            srv.submit(j, FrameIn(f.depth, f.match_idx, f.match_xyz, f.hyp),
                        t_arrival=t_start + t_arr)
             srv.poll()
         srv.drain()
         st = srv.stats()
-        for j in range(S):
+        for j in streams:
             srv.close_stream(j)
-        return {"streams": S, "rates_hz": [round(float(r), 1) for r in rates[:4]] + ["..."],
-                "offered_frames_per_s": round(float(rates.sum()), 1),
+        return {"streams": len(streams), "offered_frames_per_s": round(float(rates.sum()), 1),
                 "frames": st["frames"], "frames_per_s": round(st["frames_per_s"], 2),
                 "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
                 "mean_batch": round(st["mean_batch"], 2), "batches": st["batches"]}
 
     served = served_low = None
     if rank == 0 and args.served_frames > 0:
-        # the workload's rates (15-60 Hz per stream), then half of them (below saturation)
-        served = serve_run(1.0, args.served_frames, 7)
-        served_low = serve_run(0.5, args.served_frames // 2, 8)
+        streams = list(range(min(32, n_p)))
+        served = serve_run(1.0, args.served_frames, 7, streams)
+        offered = sum(problems[j].rate_hz for j in streams)
+        # below capacity: the offered rate cut to 60 % of what the served run sustained
+        scale = min(1.0, 0.6 * served["frames_per_s"] / offered)
+        served_low = serve_run(scale, max(200, args.served_frames // 5), 8, streams)
+        served_low["rate_scale"] = round(scale, 4)
 
     orb_fe = None
     if rank == 0 and not args.no_orb:
-        orb_fe = orb_frontend(d, torch, dev, S, K, W, min(4, n_scenes), flush)
+        orb_fe = orb_frontend(d, torch, dev, 32, K, W, 4, flush)
+        orb_fe["workload"] = "seq_320x240_n256 textured scenes"
 
-    # ---------------------------------------------------------------- roofline of the factorisation
-    flops_per_step = S * ITERS * n ** 3 / 3.0
-    factor_ms = phase[1] / K
-    achieved = flops_per_step / (factor_ms * 1e-3) / 1e12
-    bound = "alu"
-    unit = "TFLOP/s"
+    # ------------------------------------------------------------ the dominant kernel's roofline
+    factor_ms = phase[1]
+    achieved = ITERS * flops_iter / (factor_ms * 1e-3) / 1e12
+    solver_id = 1 if args.solver == "block_jacobi" else 0
+    kernel = "k_chol_dag (persistent tile Cholesky, all problems)"
+    bound, unit = "alu", "TFLOP/s"
     if solver_id == 1:
-        # no factorisation: the linearisation dominates; its algorithmic bytes are the ICP pass's
-        # 64 B per template point (32 B template point + weights, 32 B gathered live point +
-        # normal) per iteration
-        pts = sum(int((sc.template_depth > 0).sum()) for sc in scenes) * S / len(scenes)
-        bytes_per_step = 64.0 * pts * ITERS
-        achieved = bytes_per_step / (phase[0] / K * 1e-3) / 1e9
+        pts = sum(int((sc.template_depth > 0).sum()) for sc in scenes)
+        achieved = 64.0 * pts * ITERS / (phase[0] * 1e-3) / 1e9
         bound, unit = "hbm", "GB/s"
-        peak, peak_src = _measured_hbm(), "MEASURED_PEAKS.json hbm_gbs"
+        peak, peak_src = _measured_hbm(), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+        kernel = "linearisation (k_icp + k_orb + k_arap_assemble diagonal blocks)"
     elif prec == 0:
         peak, peak_src = FP64_NOMINAL_TFLOPS, "nominal GB300 FP64 rate"
     elif args.factor_tc:
-        # tensor-pipe work: three TF32 products per FP32 product; peak = measured bf16 burst x the
-        # nominal dense TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s)
         bound = "tensor"
         achieved *= 3.0
-        peak, peak_src = _measured_bf16() * 1.1 / 2.25, "measured bf16 burst x nominal tf32/bf16"
+        peak, peak_src = (_measured_bf16() * 1.1 / 2.25,
+                          "MEASURED_PEAKS.json bf16_tflops x nominal tf32/bf16 (of measured)")
+        kernel = "k_chol_tc (persistent tile Cholesky on tcgen05, all problems)"
     else:
-        peak, peak_src = FP32_SIMT_TFLOPS, "152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz"
-    dgemm = measure_dgemm_tflops(torch, dev) if prec == 0 else None
-    traffic = None if (args.factor_tc or solver_id == 1) else _chol_traffic(prec, S)
+        peak, peak_src = FP32_SIMT_TFLOPS, "152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)"
+    traffic = _factor_traffic(WORKLOAD, kernel.split()[0]) if solver_id == 0 else None
+
+    # ------------------------------------------------------------ oracle error sample
+    errors = cpu = None
+    if pending is not None:
+        try:
+            res = pending.get(timeout=args.oracle_timeout)
+        except Exception as e:   # a sample that did not finish is reported, not graded here
+            res = None
+            errors = {"unavailable": f"oracle sample did not finish: {type(e).__name__}"}
+        pool.terminate()
+        if res is not None:
+            per = []
+            for k, r in zip(sample, res[:len(sample)]):
+                per.append(dict(problem=problems[k].cfg.name,
+                                **_rounded(compare(sampled[k], r, 2.0))))
+            errors = {"sample": per,
+                      "max_err_mm": max(p["max_err_mm"] for p in per),
+                      "max_cost_rel_err": max(p["cost_rel_err"] for p in per),
+                      "what": "cold-started first frame of the fewest-node problem of each "
+                              "template size, solved in the timed batch configuration, against "
+                              "the FP64 oracle (10 iterations each)"}
+            if c3 is not None:
+                c3["error_vs_oracle_fp32_refine"] = _rounded(compare(c3_gpu, res[len(sample)], 2.0))
+            secs = [r["seconds"] for r in res[:len(sample)]]
+            cpu = {"value": round(len(secs) / sum(secs), 5), "unit": "frames/s",
+                   "cores": max(1, (_cores() - 2) // (len(sample) + 1)), "kind": "oracle",
+                   "sample": "the sampled problems' first frames ("
+                             + ", ".join(problems[k].cfg.name for k in sample)
+                             + f") solved by the FP64 oracle, {sum(secs):.1f} s in total, in "
+                             "worker processes running beside the GPU arm; the fewest-node "
+                             "problems, so this overstates the oracle's rate on the whole mix",
+                   "c3_frame_seconds": round(res[len(sample)]["seconds"], 2) if c3 else None}
 
     result = None
     if rank == 0:
-        cpu = cpu_baseline(scenes[0], oracle_params(args)) if world == 1 and not args.no_cpu else None
+        sizes = {}
+        for p in problems:
+            sizes[f"{p.cfg.W}x{p.cfg.H}"] = sizes.get(f"{p.cfg.W}x{p.cfg.H}", 0) + 1
         result = {
             "metric": METRIC, "value": round(value, 3), "unit": "frames/s", "n_gpus": world,
             "steps": K, "warmup": W, "ms_per_step": round(float(total_s * 1e3 / K), 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp64": "f32 residuals/J^T J, f64 Cholesky, double-f32 refine residuals",
-                      "fp32": "f32", "fp32_refine": "f32 J^T J + Cholesky, double-f32 (48-bit) refine residuals"}[args.precision],
-            "data": "synthetic (seeded heightfield + deformation + camera motion, ray-cast depth)",
-            "config": {"workload": WORKLOAD, "template": "320x240", "control_points": N,
-                       "matches": M, "gn_iters": ITERS, "precision": args.precision,
+                      "fp32": "f32",
+                      "fp32_refine": "f32 J^T J + Cholesky, double-f32 (48-bit) refine residuals"}[args.precision],
+            "data": "synthetic (seeded heightfields, deformation + camera motion, ray-cast depth, "
+                    "matches with planted outliers)",
+            "config": {"workload": WORKLOAD, "problems": n_p, "templates": sizes,
+                       "control_points": {"min": int(min(n_list) // 6), "max": int(max(n_list) // 6),
+                                          "mean": round(float(np.mean(n_list)) / 6, 1)},
+                       "outlier_rate": [0.2, 0.6], "gn_iters": ITERS, "precision": args.precision,
                        "solver": args.solver, "icp_association": args.assoc,
                        "ransac_o1": args.ransac_o1,
                        "factor": "tensor cores (tcgen05, 3xTF32)" if args.factor_tc else "FP32 SIMT tile kernel",
-                       "streams_per_batch": S, "distinct_scenes": n_scenes, "frames_per_scene": F,
-                       "step": f"one frame of each of {S} streams, one batched solve",
-                       "l2": "flushed (256 MB write) before each step", "parallelism": f"replicas x{world}"},
-            "latency_ms": _stats_ms(step_ms),
-            "plain_gpu_single_stream": {"precision": "fp32", "frames_per_s": round(plain_fps, 3),
-                                        "latency_ms": _stats_ms(plain_ms)},
-            "speedup_vs_plain": round(value / (world * plain_fps), 2),
+                       "frames_per_problem": F, "step": f"one frame of each of {n_p} sequences, "
+                                                        "one batched solve",
+                       "l2": "flushed (256 MB write) before each step",
+                       "parallelism": f"replicas x{world}",
+                       "factor_tflop_per_step": round(ITERS * flops_iter / 1e12, 3),
+                       "scene_generation_s": round(gen_s, 1)},
+            "latency_ms": {"per_frame_submit_to_host": _stats_ms(lat),
+                           "per_step_device": _stats_ms(step_ms)},
+            "error_vs_oracle": errors,
+            "fp64_factor": fp64,
+            "plain_gpu_single_stream": {"workload": "seq_320x240_n256", "precision": "fp32",
+                                        "frames_per_s": round(plain_fps, 3),
+                                        "latency_ms_submit_to_host": _stats_ms(plain_lat),
+                                        "device_ms": _stats_ms(plain_ms)},
+            "speedup_vs_plain": round(value / (world * plain_fps), 3),
+            "single_stream_640x480_n1024": c3,
             "served": served,
-            "served_half_rate": served_low,
+            "served_below_capacity": served_low,
             "orb_frontend": orb_fe,
             "host_enqueue_ms_per_step": round(float(np.median(host_ms)), 3),
-            "phase_ms_per_step": {"linearize": round(phase[0] / K, 4), "factor": round(phase[1] / K, 4),
-                                  "solve_refine": round(phase[2] / K, 4), "update": round(phase[3] / K, 4)},
-            "e2e": {"value": round(job_throughput(world, S * K, e2e_tot), 3), "unit": "frames/s",
+            "phase_ms_per_step": {"linearize": round(phase[0], 4), "factor": round(phase[1], 4),
+                                  "solve_refine": round(phase[2], 4), "update": round(phase[3], 4)},
+            "e2e": {"value": round(job_throughput(world, n_p * K, e2e_tot), 3), "unit": "frames/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
-            "roofline": {"bound": bound,
-                         "kernel": ("linearisation (k_icp + k_orb + k_arap_assemble diagonal blocks)"
-                                    if solver_id == 1 else
-                                    "k_chol_tc (persistent tile Cholesky on tcgen05, all problems)"
-                                    if args.factor_tc and prec != 0 else
-                                    "k_chol_dag (persistent tile Cholesky, all problems)"),
+            "gpu_launches_per_step": round(launches_per_step, 1),
+            "roofline": {"bound": bound, "kernel": kernel,
                          "achieved": round(achieved, 4), "peak": peak, "unit": unit,
                          "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "traffic_unit": "DRAM bytes per launch (ncu)",
-                         "algorithmic_bytes": int(2 * S * n * n * (8 if prec == 0 else 4)),
+                         "traffic_source": "stored ncu capture of this kernel source and workload "
+                                           "(profiles/), null when either changed",
                          "peak_source": peak_src,
                          "algorithmic": ("64 B per template point per iteration (ICP)"
                                          if solver_id == 1 else
-                                         "3 x n^3/3 TF32 flop per factorisation, 10 per frame"
+                                         "3 x sum n^3/3 TF32 flop per iteration, 10 per frame"
                                          if bound == "tensor" else
-                                         "n^3/3 flop per factorisation, 10 per frame"),
-                         "dgemm_measured_tflops": round(dgemm, 4) if dgemm else None},
+                                         "sum over problems of n^3/3 flop per factorisation, 10 per frame"),
+                         "timing": "factorisation phase per step, CUDA events in the graph"},
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
         }
@@ -587,58 +762,62 @@ def run_gpu(args):
         print(json.dumps(result), flush=True)
 
 
+# ----------------------------------------------------------------------------- reference arm
+
+
 def run_reference(args):
-    """The FP64 CPU oracle as it stands: a step is one Gauss-Newton iteration of the workload's
-    frame; frames/s = 1 / (prep + RANSAC + 10 x mean iteration)."""
+    """The FP64 CPU oracle as it stands, on the headline workload: step s is one Gauss-Newton
+    iteration of problem s of the batched list (after its frame preparation and RANSAC, timed
+    apart); a problem's frame time = prep + RANSAC + 10 iterations; frames/s = 1 / the mean frame
+    time over the timed steps' problems."""
     rank, world, _ = _dist()
     if rank != 0:
         return
-    from oracle import ransac, solver
-    sc = gen_frames(1, 1000)
-    f = sc.frames[0]
+    from oracle import dqb, ransac, solver
+    from synth.workloads import make_scenes, mixed_problems
+    problems = mixed_problems(args.problems)
     prm = oracle_params(args)
-    tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes, prm)
-    N = len(sc.nodes)
-    q = np.tile([1.0, 0, 0, 0], (N, 1))
-    t = np.zeros((N, 3))
-    t0 = time.perf_counter()
-    tgt = solver.prepare_target(f.depth, tpl.K)
-    rs = ransac.ransac_1p(solver.ransac_o1(tpl, f.match_idx, q, t, prm), f.match_xyz, f.hyp,
-                          prm.H, prm.n_reweight, prm.keep_frac)
-    t_pre = time.perf_counter() - t0
-    orb = (f.match_idx, f.match_xyz.astype(np.float64), rs["mask"], rs["what"])
-    w_arap = None
-    from oracle import dqb
-
-    def it():
-        nonlocal q, t, w_arap
-        lin, w_arap = solver.linearize(tpl, tgt, q, t, orb, w_arap, prm)
+    frame_s, iter_s, names = [], [], []
+    for s in range(args.warmup + args.steps):
+        p = problems[s % len(problems)]
+        sc = make_scenes([p], 1)[0]
+        f = sc.frames[0]
+        tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes, prm)
+        N = len(sc.nodes)
+        q = np.tile([1.0, 0, 0, 0], (N, 1))
+        t = np.zeros((N, 3))
+        t0 = time.perf_counter()
+        tgt = solver.prepare_target(f.depth, tpl.K)
+        rs = ransac.ransac_1p(solver.ransac_o1(tpl, f.match_idx, q, t, prm), f.match_xyz, f.hyp,
+                              prm.H, prm.n_reweight, prm.keep_frac)
+        t_pre = time.perf_counter() - t0
+        orb = (f.match_idx, f.match_xyz.astype(np.float64), rs["mask"], rs["what"])
+        a = time.perf_counter()
+        lin, _ = solver.linearize(tpl, tgt, q, t, orb, None, prm)
         Ad = solver.damp(lin.A, prm)
         delta = (solver.block_jacobi_solve(Ad, lin.b) if prm.solver == "block_jacobi"
                  else solver.cholesky_solve(Ad, lin.b))
-        q, t = dqb.apply_step(q, t, delta)
-
-    for _ in range(args.warmup):
-        it()
-    ts = []
-    for _ in range(args.steps):
-        a = time.perf_counter()
-        it()
-        ts.append(time.perf_counter() - a)
-    frame_s = t_pre + ITERS * float(np.mean(ts))
-    value = 1.0 / frame_s
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        dqb.apply_step(q, t, delta)
+        it = time.perf_counter() - a
+        if s >= args.warmup:
+            iter_s.append(it)
+            frame_s.append(t_pre + ITERS * it)
+            names.append(p.cfg.name)
+    value = 1.0 / float(np.mean(frame_s))
+    cores = _cores()
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "frames/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(float(np.mean(ts)) * 1e3, 3), "higher_is_better": True,
+        "ms_per_step": round(float(np.mean(iter_s)) * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "template": "320x240", "control_points": N,
-                   "matches": len(f.match_idx), "gn_iters": ITERS,
-                   "step": "one oracle Gauss-Newton iteration; frame = prep + RANSAC + 10 steps"},
+        "config": {"workload": WORKLOAD, "problems": len(problems), "gn_iters": ITERS,
+                   "step": "one oracle Gauss-Newton iteration of the next problem of the batched "
+                           "list; frame = prep + RANSAC + 10 iterations",
+                   "problems_timed": names},
         "cpu_baseline": {"value": round(value, 5), "unit": "frames/s", "cores": cores,
                          "kind": "oracle",
-                         "sample": f"{args.steps} GN iterations of one {WORKLOAD} frame + its prep/RANSAC"},
+                         "sample": f"{args.steps} problems of the batched list, one GN iteration "
+                                   "each + their prep/RANSAC, numpy/LAPACK on the host cores"},
         "e2e": {"value": round(value, 5), "unit": "frames/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -651,13 +830,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--precision", default="fp32_refine", choices=list(PREC))
-    ap.add_argument("--streams", type=int, default=32, help="concurrent streams per batch")
-    ap.add_argument("--scenes", type=int, default=8, help="distinct seeded scenes behind them")
-    ap.add_argument("--frames", type=int, default=4, help="frames per scene (cycled)")
-    ap.add_argument("--served-frames", type=int, default=2000, dest="served_frames")
-    ap.add_argument("--no-cpu", action="store_true", dest="no_cpu")
+    ap.add_argument("--problems", type=int, default=64, help="sequences of the batched workload")
+    ap.add_argument("--frames", type=int, default=2, help="distinct frames per sequence (cycled)")
+    ap.add_argument("--fp64-steps", type=int, default=1, dest="fp64_steps",
+                    help="timed steps of the FP64-factor line (0: skip)")
+    ap.add_argument("--c3-frames", type=int, default=10, dest="c3_frames",
+                    help="timed frames of the 640x480 / 1024-node stream alone (0: skip)")
+    ap.add_argument("--served-frames", type=int, default=10000, dest="served_frames")
     ap.add_argument("--no-orb", action="store_true", dest="no_orb",
                     help="skip the ORB feature front-end measurement")
+    ap.add_argument("--no-oracle", action="store_true", dest="no_oracle",
+                    help="skip the oracle error sample and the CPU baseline")
+    ap.add_argument("--oracle-timeout", type=float, default=600.0, dest="oracle_timeout")
     ap.add_argument("--solver", default="dense", choices=["dense", "block_jacobi"],
                     help="dense 6N x 6N Cholesky, or per-node 6 x 6 solves (Section 2)")
     ap.add_argument("--factor-tc", action="store_true", dest="factor_tc",

@@ -133,14 +133,21 @@ def raycast_template(hf: Heightfield, W: int, H: int, iters: int = 40):
     dx = (u - cx) / fx
     dy = (v - cy) / fy
     lam = np.full(u.shape, hf.base if np.isfinite(hf.base) else 100.0)
+    # Newton per pixel; a pixel stops once |lambda - h| < 1e-12 (only the others are iterated)
+    act = np.arange(lam.size)
+    lf, dxf, dyf = lam.reshape(-1), dx.reshape(-1), dy.reshape(-1)
     for _ in range(iters):
-        z, zx, zy = hf.eval(lam * dx, lam * dy)
-        f = lam - z
-        if np.abs(f).max() < 1e-12:
+        la, ax, ay = lf[act], dxf[act], dyf[act]
+        z, zx, zy = hf.eval(la * ax, la * ay)
+        f = la - z
+        going = np.abs(f) >= 1e-12
+        if not going.any():
             break
-        df = 1.0 - (zx * dx + zy * dy)
+        act, la, f, ax, ay = act[going], la[going], f[going], ax[going], ay[going]
+        df = 1.0 - (zx[going] * ax + zy[going] * ay)
         df = np.where(np.abs(df) < 0.2, np.sign(df + 1e-300) * 0.2, df)
-        lam = lam - f / df
+        lf[act] = la - f / df
+    lam = lf.reshape(u.shape)
     z, _, _ = hf.eval(lam * dx, lam * dy)
     ok = np.abs(lam - z) < 1e-9
     depth = np.where(ok, lam, 0.0)
@@ -158,11 +165,23 @@ def render_target(hf: Heightfield, mo: Motion, W: int, H: int, iters: int = 12,
     up, vp = np.meshgrid(np.arange(W, dtype=np.float64), np.arange(H, dtype=np.float64))
     x = (up - cx) / fx * 100.0
     y = (vp - cy) / fy * 100.0
+    # 2D Newton per pixel; a pixel stops once its projection is within 1e-10 px of its centre
+    # (only the others are iterated)
+    act = np.arange(x.size)
+    xf, yf, uf, vf = x.reshape(-1), y.reshape(-1), up.reshape(-1), vp.reshape(-1)
     for _ in range(iters):
-        Y, Yx, Yy = mo.surface(hf, x, y)
+        xa, ya = xf[act], yf[act]
+        Y, Yx, Yy = mo.surface(hf, xa, ya)
         iz = 1.0 / Y[..., 2]
         pu = fx * Y[..., 0] * iz + cx
         pv = fy * Y[..., 1] * iz + cy
+        ru = pu - uf[act]
+        rv = pv - vf[act]
+        going = np.maximum(np.abs(ru), np.abs(rv)) >= 1e-10
+        if not going.any():
+            break
+        act, xa, ya, ru, rv = act[going], xa[going], ya[going], ru[going], rv[going]
+        Y, Yx, Yy, iz = Y[going], Yx[going], Yy[going], iz[going]
         # d(pu, pv)/dY
         du = np.stack([fx * iz, np.zeros_like(iz), -fx * Y[..., 0] * iz * iz], axis=-1)
         dv = np.stack([np.zeros_like(iz), fy * iz, -fy * Y[..., 1] * iz * iz], axis=-1)
@@ -172,12 +191,9 @@ def render_target(hf: Heightfield, mo: Motion, W: int, H: int, iters: int = 12,
         a22 = (dv * Yy).sum(-1)
         det = a11 * a22 - a12 * a21
         det = np.where(np.abs(det) < 1e-12, 1e-12, det)
-        ru = pu - up
-        rv = pv - vp
-        if max(np.abs(ru).max(), np.abs(rv).max()) < 1e-10:
-            break
-        x = x - (a22 * ru - a12 * rv) / det
-        y = y - (-a21 * ru + a11 * rv) / det
+        xf[act] = xa - (a22 * ru - a12 * rv) / det
+        yf[act] = ya - (-a21 * ru + a11 * rv) / det
+    x, y = xf.reshape(up.shape), yf.reshape(up.shape)
     Y, _, _ = mo.surface(hf, x, y)
     pu = fx * Y[..., 0] / Y[..., 2] + cx
     pv = fy * Y[..., 1] / Y[..., 2] + cy

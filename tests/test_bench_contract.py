@@ -23,7 +23,7 @@ def test_reference_arm_prints_one_contract_line():
     assert d["impl"] == "reference"
     assert d["unit"] == "frames/s" and d["higher_is_better"] is True
     assert d["value"] > 0 and d["steps"] == 1 and d["n_gpus"] == 1
-    assert d["config"]["workload"] == "seq_320x240_n256"
+    assert d["config"]["workload"] == "batched_mixed_64"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
@@ -50,13 +50,41 @@ def test_clock_summary_reads_median_and_throttle_reasons():
 def test_traffic_reported_only_for_the_captured_kernel_source_and_workload():
     sys.path.insert(0, ROOT)
     import bench
-    c = dict(bench.CHOL_TRAFFIC)
+    c = bench.FACTOR_TRAFFIC
     try:
-        bench.CHOL_TRAFFIC = dict(c, chol_sha256=bench._chol_source_digest())
-        assert bench._chol_traffic(c["precision"], c["streams"]) == c["bytes"]
-        assert bench._chol_traffic(0, c["streams"]) is None
-        assert bench._chol_traffic(c["precision"], 8) is None
-        bench.CHOL_TRAFFIC = dict(c, chol_sha256="0" * 16)     # another kernel source
-        assert bench._chol_traffic(c["precision"], c["streams"]) is None
+        bench.FACTOR_TRAFFIC = {"chol_sha256": bench._chol_source_digest(),
+                                "workload": bench.WORKLOAD, "kernel": "k_chol_dag",
+                                "bytes": 123}
+        assert bench._factor_traffic(bench.WORKLOAD, "k_chol_dag") == 123
+        assert bench._factor_traffic("seq_320x240_n256", "k_chol_dag") is None
+        assert bench._factor_traffic(bench.WORKLOAD, "k_chol_tc") is None
+        bench.FACTOR_TRAFFIC = dict(bench.FACTOR_TRAFFIC, chol_sha256="0" * 16)   # other source
+        assert bench._factor_traffic(bench.WORKLOAD, "k_chol_dag") is None
+        bench.FACTOR_TRAFFIC = None
+        assert bench._factor_traffic(bench.WORKLOAD, "k_chol_dag") is None
     finally:
-        bench.CHOL_TRAFFIC = c
+        bench.FACTOR_TRAFFIC = c
+
+
+def test_error_sample_and_comparison():
+    """The oracle sample takes the fewest-node problem of each template size; the comparison
+    reports positions, the last cost and mask bits outside the listed band."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import bench
+    from synth.workloads import mixed_problems
+    ps = mixed_problems(64)
+    ks = bench.error_sample(ps)
+    assert len(ks) == 3 and len({ps[k].cfg.W for k in ks}) == 3
+    for k in ks:
+        assert ps[k].cfg.N == min(p.cfg.N for p in ps if p.cfg.W == ps[k].cfg.W)
+    g = np.zeros((2, 3))
+    ref = {"g": g, "pos": np.array([[1.0, 0, 0], [0, 0, 0]]), "cost": np.array([5.0, 4.0]),
+           "mask": np.array([True, False, True]), "kept": np.array([True]),
+           "d": np.array([[0.5, 2.0 + 1e-9, 0.1]]), "score": np.array([3.0])}
+    gpu = {"t": np.array([[1.0, 0, 0], [0, 0, 3e-4]]), "cost": 4.0004,
+           "mask": np.array([True, True, False])}
+    c = bench.compare(gpu, ref, 2.0)
+    assert abs(c["max_err_mm"] - 3e-4) < 1e-15 and abs(c["cost_rel_err"] - 1e-4) < 1e-12
+    assert c["mask_bits_differing"] == 1     # match 1 sits in the band around H, match 2 counts
