@@ -45,6 +45,8 @@ WORKLOAD = "batched_mixed_64"
 ITERS = 10
 METRIC = "frames/s and p50/p99 frame latency vs plain GPU solve, at ≤1e-3 mm error"
 PREC = {"fp64": 0, "fp32": 1, "fp32_refine": 2}
+FACTOR = {"simt": 0, "tc64": 1, "tc128": 2, "auto": 3}   # ds_params.factor_tc
+FACTOR_NAMES = ["simt", "tc64", "tc128"]
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate per GPU (nominal)
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the dominant kernel
@@ -178,7 +180,7 @@ def oracle_params(args):
 
 def variant_params(d, args, prec, **kw):
     """The CUDA path's ds_params for the same variant."""
-    return d.default_params(precision=prec, factor_tc=1 if args.factor_tc else 0,
+    return d.default_params(precision=prec, factor_tc=FACTOR[args.factor],
                             solver=1 if args.solver == "block_jacobi" else 0,
                             assoc=1 if args.assoc == "bilinear" else 0,
                             ransac_o1=1 if args.ransac_o1 == "warm" else 0, **kw)
@@ -246,7 +248,9 @@ def _listed(res, H, band=1e-6):
 def gpu_result(d, h, sc):
     """A handle's solved frame as the oracle comparison reads it: FP64 translations, the cost
     at the last linearisation, the preselection mask (the scene's first frame)."""
-    _, t = d.ds_get_deformation64(h)
+    N = len(sc.nodes)
+    t = np.zeros((N, 3), np.float64)
+    d.ds_get_deformation64(h, None, t)
     M = len(sc.frames[0].match_idx)
     bits = np.zeros((M + 31) // 32, np.uint32)
     d.ds_get_inlier_mask(h, bits)
@@ -456,6 +460,20 @@ def run_gpu(args):
     # ------------------------------------------------------------ headline: the mixed batch
     prm = variant_params(d, args, prec)
     run = BatchRun(d, torch, dev, scenes, prm, stream)
+    # the factor kernel: the tuner times the three FP32 kernels on this batch's sizes (auto), or
+    # the one asked for
+    tuner = None
+    factor = args.factor
+    if prec != 0 and args.solver == "dense":
+        if args.factor == "auto":
+            choice, tms = d.ds_batch_tune(run.batch, 3)
+            factor = FACTOR_NAMES[choice]
+            tuner = {"chosen": factor, "ms_per_factorisation": {
+                FACTOR_NAMES[k]: round(float(tms[k]), 3) for k in range(3)},
+                "how": "each kernel on synthetic SPD systems of the batch's 64 sizes, best of 3 "
+                       "launches (CUDA events); cached by batch shape"}
+    else:
+        factor = "fp64" if prec == 0 else "none"
     # cold start on frame 0 (untimed): the sampled problems' results go to the oracle check
     run.step(0)
     torch.cuda.synchronize()
@@ -651,12 +669,14 @@ def run_gpu(args):
         kernel = "linearisation (k_icp + k_orb + k_arap_assemble diagonal blocks)"
     elif prec == 0:
         peak, peak_src = FP64_NOMINAL_TFLOPS, "nominal GB300 FP64 rate"
-    elif args.factor_tc:
+    elif factor in ("tc64", "tc128"):
         bound = "tensor"
         achieved *= 3.0
         peak, peak_src = (_measured_bf16() * 1.1 / 2.25,
                           "MEASURED_PEAKS.json bf16_tflops x nominal tf32/bf16 (of measured)")
-        kernel = "k_chol_tc (persistent tile Cholesky on tcgen05, all problems)"
+        kernel = ("k_chol_tcb (persistent 128 x 128 block Cholesky on tcgen05, all problems)"
+                  if factor == "tc128" else
+                  "k_chol_tc (persistent 64 x 64 tile Cholesky on tcgen05, all problems)")
     else:
         peak, peak_src = FP32_SIMT_TFLOPS, "152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)"
     traffic = _factor_traffic(WORKLOAD, kernel.split()[0]) if solver_id == 0 else None
@@ -713,7 +733,12 @@ def run_gpu(args):
                        "outlier_rate": [0.2, 0.6], "gn_iters": ITERS, "precision": args.precision,
                        "solver": args.solver, "icp_association": args.assoc,
                        "ransac_o1": args.ransac_o1,
-                       "factor": "tensor cores (tcgen05, 3xTF32)" if args.factor_tc else "FP32 SIMT tile kernel",
+                       "factor": {"simt": "FP32 SIMT 64 x 64 tiles",
+                                  "tc64": "tensor cores (tcgen05, 3xTF32), 64 x 64 tiles",
+                                  "tc128": "tensor cores (tcgen05, 3xTF32), 128 x 128 blocks",
+                                  "fp64": "FP64 SIMT 32 x 32 tiles",
+                                  "none": "per-node 6 x 6 solves"}[factor],
+                       "factor_tuner": tuner,
                        "frames_per_problem": F, "step": f"one frame of each of {n_p} sequences, "
                                                         "one batched solve",
                        "l2": "flushed (256 MB write) before each step",
@@ -844,8 +869,10 @@ def main():
     ap.add_argument("--oracle-timeout", type=float, default=600.0, dest="oracle_timeout")
     ap.add_argument("--solver", default="dense", choices=["dense", "block_jacobi"],
                     help="dense 6N x 6N Cholesky, or per-node 6 x 6 solves (Section 2)")
-    ap.add_argument("--factor-tc", action="store_true", dest="factor_tc",
-                    help="FP32 factorisation on the tensor cores (tcgen05, 3xTF32)")
+    ap.add_argument("--factor", default="auto", choices=list(FACTOR),
+                    help="FP32 factorisation kernel: SIMT 64 x 64 tiles, tensor cores (tcgen05, "
+                         "3xTF32) with 64 x 64 tiles or 128 x 128 blocks, or picked by the "
+                         "library's tuner on the batch's sizes (auto)")
     ap.add_argument("--assoc", default="nearest", choices=["nearest", "bilinear"],
                     help="ICP association: nearest pixel or bilinear blend of 4 pixels")
     ap.add_argument("--ransac-o1", default="template", choices=["template", "warm"],

@@ -21,6 +21,8 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
+#include <map>
+#include <mutex>
 #include <numeric>
 #include <unordered_map>
 #include <vector>
@@ -59,6 +61,12 @@ struct ds_batch_s {
   cudaEvent_t ev_done = nullptr;
   std::vector<cudaEvent_t> ev_in;
   std::vector<const ProbDesc*> h_descs;  // the descriptor table as last uploaded
+  // pinned staging of the table's uploads (two, alternating), so that an upload does not make
+  // the host wait for the batch stream; each is reused only after its last copy has run
+  const ProbDesc** h_tab_pin[2] = {nullptr, nullptr};
+  cudaEvent_t ev_tab[2] = {nullptr, nullptr};
+  bool tab_pending[2] = {false, false};
+  int tab_i = 0;
   // side stream of the linearisation: the ORB pass runs beside the ICP pass (both only add
   // into the block table and the gradient)
   cudaStream_t side = nullptr, side2 = nullptr;
@@ -67,6 +75,10 @@ struct ds_batch_s {
   // a handle's control points changed, or it was destroyed (its entry in hs is then NULL): the
   // work tables and descriptor pointers are the old ones, so the batch no longer runs
   bool stale = false;
+  // factor kernel chosen by timing (DS_FACTOR_AUTO handles): tuned once, before the first solve
+  bool auto_factor = false;
+  bool tuned = false;
+  double tune_ms[3] = {-1.0, -1.0, -1.0};
 };
 
 struct ds_ctx {
@@ -152,6 +164,8 @@ struct ds_ctx {
   void* d_Lp = nullptr;       // packed transposed factor tiles
   int4* d_tasks = nullptr;
   int ntasks = 0;
+  int4* d_tasks_b = nullptr;  // 128-block factorisation tasks
+  int ntasks_b = 0;
   int nt = 0;
   bool prec_fp64 = false;
   double* d_acc = nullptr;
@@ -160,6 +174,11 @@ struct ds_ctx {
   // descriptor: hdesc holds the fields common to both slots; d_desc[s] is slot s's
   ProbDesc hdesc{};
   ProbDesc* d_desc = nullptr;
+  // pinned staging of the two slots' descriptor uploads (a copy from pageable memory would make
+  // the host wait for the handle's stream); a slot's staging is reused once its last copy has run
+  ProbDesc* h_desc_pin = nullptr;
+  cudaEvent_t ev_desc[2] = {nullptr, nullptr};
+  bool desc_pending[2] = {false, false};
   // the batch of one used by ds_solve
   ds_batch_s* self = nullptr;
   std::vector<ds_batch_s*> batches;   // every batch that lists this handle (self included)
@@ -248,9 +267,12 @@ double* slot_score(ds_ctx* h, int s) { return h->d_rs_score + s * DS_MAX_HYP; }
 uint32_t* slot_kept(ds_ctx* h, int s) { return h->d_rs_kept + 2 * s; }
 int* slot_counts(ds_ctx* h, int s) { return h->d_rs_counts + 4 * s; }
 
-// Slot s's descriptor: the common fields with the slot's frame buffers.
+// Slot s's descriptor: the common fields with the slot's frame buffers, uploaded on the handle's
+// stream from the slot's pinned staging.
 void push_desc(ds_ctx* h, int s) {
-  ProbDesc D = h->hdesc;
+  if (h->desc_pending[s]) cudaEventSynchronize(h->ev_desc[s]);
+  ProbDesc& D = h->h_desc_pin[s];
+  D = h->hdesc;
   D.M = h->Ms[s];
   D.tpts = slot_tpts(h, s);
   D.tnrm = slot_tnrm(h, s);
@@ -258,8 +280,9 @@ void push_desc(ds_ctx* h, int s) {
   D.mxyz = slot_mxyz(h, s);
   D.mask = slot_mask(h, s);
   D.what = slot_what(h, s);
-  // staged from pageable memory: the copy has left D when the call returns
   cudaMemcpyAsync(h->d_desc + s, &D, sizeof(ProbDesc), cudaMemcpyHostToDevice, h->stream);
+  cudaEventRecord(h->ev_desc[s], h->stream);
+  h->desc_pending[s] = true;
 }
 
 // Orders the handle's stream after its last solve (a batch on another stream).
@@ -292,6 +315,7 @@ void free_cp(ds_ctx* h) {
   hfree(h, h->d_A32); hfree(h, h->d_A64); hfree(h, h->d_Af32); hfree(h, h->d_Dinv); hfree(h, h->d_blk); hfree(h, h->d_adiag);
   hfree(h, h->d_gdata); hfree(h, h->d_b); hfree(h, h->d_x); hfree(h, h->d_r); hfree(h, h->d_xf);
   hfree(h, h->d_v2); hfree(h, h->d_v3); hfree(h, h->d_lcnt); hfree(h, h->d_lflags); hfree(h, h->d_tasks);
+  hfree(h, h->d_tasks_b);
   hfree(h, h->d_Lp);
   hfree(h, h->d_desc);
   h->N = h->n = 0;
@@ -384,6 +408,11 @@ void make_chol_tasks(int nt, std::vector<int4>& out) {
   }
 }
 
+// Block tasks of the 128 x 128 block factorisation, in the same column order (same encoding).
+void make_chol_tasks_b(int nb, std::vector<int4>& out) {
+  make_chol_tasks(nb, out);
+}
+
 // Claim order of the factorisation tickets of a batch: problems interleaved round-robin, each
 // problem's tasks in their own (topological) order, so every task waits only on earlier tickets.
 void make_chol_tickets(const std::vector<int>& ntasks, std::vector<int2>& out) {
@@ -420,6 +449,10 @@ void destroy_batch(ds_batch_s* b) {
   if (b->side) cudaStreamDestroy(b->side);
   if (b->side2) cudaStreamDestroy(b->side2);
   for (auto e : b->ev_in) cudaEventDestroy(e);
+  for (int i = 0; i < 2; ++i) {
+    if (b->ev_tab[i]) cudaEventDestroy(b->ev_tab[i]);
+    if (b->h_tab_pin[i]) cudaFreeHost(b->h_tab_pin[i]);
+  }
   dfree(b->d_descs);
   dfree(b->d_tab);
   dfree(b->d_words);
@@ -438,7 +471,7 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   const bool fp64 = hs[0]->prec_fp64;
   const int prec = hs[0]->prm.precision;
   const int steps = prec == DS_PREC_FP32 ? 0 : hs[0]->prm.refine_steps;
-  const int ftc = fp64 ? 0 : hs[0]->prm.factor_tc;
+  const int ftc = fp64 ? 0 : hs[0]->prm.factor_tc;   // DS_FACTOR_AUTO (3): tuned per batch
   const int solver = hs[0]->prm.solver;
   for (int i = 1; i < n; ++i) {
     const int ps = hs[i]->prm.precision == DS_PREC_FP32 ? 0 : hs[i]->prm.refine_steps;
@@ -454,8 +487,8 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   b->block_jacobi = solver == 1;
   b->stream = stream;
   b->own_stream = own;
-  std::vector<int2> icp, rows, nodes, res, chol;
-  std::vector<int> ntasks(n);
+  std::vector<int2> icp, rows, nodes, res, chol, chol_b;
+  std::vector<int> ntasks(n), ntasks_b(n);
   int max_tasks = 0, max_nt = 0;
   std::vector<const ProbDesc*> descs(n);
   for (int p = 0; p < n; ++p) {
@@ -466,12 +499,14 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
     for (int c = 0; c * 128 < h->N; ++c) nodes.push_back(make_int2(p, c));
     for (int c = 0; c * 8 < h->n; ++c) res.push_back(make_int2(p, c));
     ntasks[p] = h->ntasks;
+    ntasks_b[p] = h->ntasks_b;
     max_tasks = std::max(max_tasks, h->ntasks);
     max_nt = std::max(max_nt, h->nt);
   }
   make_chol_tickets(ntasks, chol);
+  make_chol_tickets(ntasks_b, chol_b);
   const size_t ntab =
-      icp.size() + rows.size() + nodes.size() + res.size() + chol.size();
+      icp.size() + rows.size() + nodes.size() + res.size() + chol.size() + chol_b.size();
   int rc;
   if ((rc = dalloc(&b->d_descs, n)) || (rc = dalloc(&b->d_tab, ntab)) ||
       (rc = dalloc(&b->d_words, 8))) {
@@ -480,7 +515,7 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   }
   std::vector<int2> all;
   all.reserve(ntab);
-  for (auto* v : {&icp, &rows, &nodes, &res, &chol})
+  for (auto* v : {&icp, &rows, &nodes, &res, &chol, &chol_b})
     all.insert(all.end(), v->begin(), v->end());
   cudaMemcpy(b->d_descs, descs.data(), sizeof(void*) * n, cudaMemcpyHostToDevice);
   b->h_descs = descs;
@@ -495,11 +530,20 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   T.nodes = b->d_tab + off; T.n_nodes = (int)nodes.size(); off += nodes.size();
   T.res = b->d_tab + off; T.n_res = (int)res.size(); off += res.size();
   T.chol = b->d_tab + off; T.n_chol = (int)chol.size(); off += chol.size();
+  T.chol_b = b->d_tab + off; T.n_chol_b = (int)chol_b.size(); off += chol_b.size();
   T.orb_ctas = 16;
-  T.factor_tc = ftc;
+  b->auto_factor = ftc == DS_FACTOR_AUTO;
+  T.factor_tc = b->auto_factor ? 0 : ftc;
   T.max_tasks = max_tasks;
   T.max_nt = max_nt;
   T.words = b->d_words;
+  for (int i = 0; i < 2; ++i)
+    if (cudaMallocHost((void**)&b->h_tab_pin[i], sizeof(void*) * n) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_tab[i], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      destroy_batch(b);
+      return DS_ERR_OOM;
+    }
   if (cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess ||
@@ -609,15 +653,20 @@ void update_desc_table(ds_batch_s* b) {
       changed = true;
     }
   }
-  if (changed)
-    cudaMemcpyAsync(b->d_descs, b->h_descs.data(), sizeof(void*) * b->hs.size(),
-                    cudaMemcpyHostToDevice, b->stream);
+  if (!changed) return;
+  const int i = b->tab_i ^= 1;
+  if (b->tab_pending[i]) cudaEventSynchronize(b->ev_tab[i]);
+  std::copy(b->h_descs.begin(), b->h_descs.end(), b->h_tab_pin[i]);
+  cudaMemcpyAsync(b->d_descs, b->h_tab_pin[i], sizeof(void*) * b->hs.size(),
+                  cudaMemcpyHostToDevice, b->stream);
+  cudaEventRecord(b->ev_tab[i], b->stream);
+  b->tab_pending[i] = true;
 }
 
-int run_batch(ds_batch_s* b, int iters, bool use_graph) {
+// Orders the batch stream after each handle's last solve (possibly in another batch) and its
+// pending work (submit_frame on its own stream).
+void order_after_handles(ds_batch_s* b) {
   cudaStream_t s = b->stream;
-  // order after each handle's last solve (possibly in another batch) and its pending work
-  // (submit_frame on its own stream)
   for (size_t p = 0; p < b->hs.size(); ++p) {
     ds_ctx* h = b->hs[p];
     if (h->slot_pending[h->solved_fs]) cudaStreamWaitEvent(s, h->ev_slot_free[h->solved_fs], 0);
@@ -626,6 +675,102 @@ int run_batch(ds_batch_s* b, int iters, bool use_graph) {
       cudaStreamWaitEvent(s, b->ev_in[p], 0);
     }
   }
+}
+
+// Tuned factor-kernel choices by coarse batch shape (ceil log2 of the largest system, rounded
+// log2 of the summed n^3), shared by every batch of the process.
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, int> g_tune_cache;
+
+std::pair<int, int> tune_key(const ds_batch_s* b) {
+  int mx = 1;
+  double f = 0.0;
+  for (const ds_ctx* h : b->hs) {
+    mx = std::max(mx, h->n);
+    f += (double)h->n * h->n * h->n;
+  }
+  return {(int)ceil(log2((double)mx)), (int)lround(log2(f))};
+}
+
+// Times the candidate FP32 factor kernels (SIMT 64 x 64 tiles, tensor cores with 64 x 64 tiles
+// and with 128 x 128 blocks) on synthetic SPD systems of the batch's sizes, written into the
+// factor buffers (the next solve assembles its own systems over them), and keeps the fastest.
+// Each candidate's time is the minimum over `reps` launches (CUDA events on the batch stream).
+int tune_factor(ds_batch_s* b, int reps) {
+  cudaStream_t s = b->stream;
+  BatchTabs& T = b->tabs;
+  order_after_handles(b);
+  update_desc_table(b);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return DS_ERR_CUDA;
+  }
+  int best = 0;
+  double best_ms = INFINITY;
+  int rc = DS_OK;
+  for (int c = 0; c < 3 && rc == DS_OK; ++c) {
+    T.factor_tc = c;
+    float mn = INFINITY;
+    for (int r = 0; r < reps; ++r) {
+      launch_fill_spd(T, s);
+      launch_iter_begin(T, s);
+      cudaEventRecord(e0, s);
+      launch_chol_dag<float>(T, s);
+      cudaEventRecord(e1, s);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        rc = DS_ERR_CUDA;
+        break;
+      }
+      mn = std::min(mn, ms);
+    }
+    g_total_kernels += 3 * reps;
+    b->tune_ms[c] = mn;
+    if (mn < best_ms) {
+      best_ms = mn;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc == DS_OK) rc = batch_words_status(b);
+  // the synthetic systems are SPD; clear the pivot words anyway so that no tuning run reports
+  for (ds_ctx* h : b->hs) cudaMemsetAsync(h->d_acc + ACC_STATUS, 0, sizeof(double), s);
+  if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+    rc = DS_ERR_CUDA;
+  T.factor_tc = best;
+  b->tuned = rc == DS_OK;
+  if (b->gexec) {   // a captured loop holds the previous kernel choice
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    b->g_iters = -1;
+  }
+  if (rc != DS_OK) b->error = true;
+  return rc;
+}
+
+int run_batch(ds_batch_s* b, int iters, bool use_graph) {
+  cudaStream_t s = b->stream;
+  if (b->auto_factor && !b->tuned) {
+    const auto key = tune_key(b);
+    int choice = -1;
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) choice = it->second;
+    }
+    if (choice >= 0) {
+      b->tabs.factor_tc = choice;
+      b->tuned = true;
+    } else {
+      const int rc = tune_factor(b, 2);
+      if (rc) return rc;
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      g_tune_cache[key] = b->tabs.factor_tc;
+    }
+  }
+  order_after_handles(b);
   // the descriptor table points at each handle's latest frame slot
   update_desc_table(b);
   const int64_t before = g_launches;
@@ -699,7 +844,7 @@ bool valid_params(const ds_params& p) {
          p.eps_damp >= 0 && p.keep_frac >= 0 && p.keep_frac <= 1 && p.sigma_blend_scale > 0 &&
          p.sigma_arap_scale > 0 && p.precision >= 0 && p.precision <= 2 && p.refine_steps >= 0 &&
          p.refine_steps <= 3 && p.w_orb >= 0 && p.w_angle >= 0 && p.w_rot >= 0 &&
-         p.w_arap0 >= 0 && (p.factor_tc == 0 || p.factor_tc == 1) &&
+         p.w_arap0 >= 0 && (p.factor_tc >= 0 && p.factor_tc <= DS_FACTOR_AUTO) &&
          (p.solver == 0 || p.solver == 1) && (p.assoc == 0 || p.assoc == 1) &&
          (p.ransac_o1 == 0 || p.ransac_o1 == 1);
 }
@@ -729,7 +874,7 @@ void ds_default_params(ds_params* p) {
   p->precision = DS_PREC_FP64;
   p->refine_steps = 2;
   p->use_graph = 1;
-  p->factor_tc = 0;
+  p->factor_tc = DS_FACTOR_AUTO;
   p->solver = 0;
   p->assoc = 0;
   p->ransac_o1 = 0;
@@ -801,10 +946,17 @@ int ds_create_template(const float* depth_hw, int32_t W, int32_t H, ds_intrinsic
     return rc;
   }
   for (int k = 0; k < 2; ++k)
-    if (cudaEventCreateWithFlags(&h->ev_slot_free[k], cudaEventDisableTiming) != cudaSuccess) {
+    if (cudaEventCreateWithFlags(&h->ev_slot_free[k], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_desc[k], cudaEventDisableTiming) != cudaSuccess) {
       ds_destroy(h);
       return DS_ERR_CUDA;
     }
+  if (cudaMallocHost((void**)&h->h_desc_pin, 2 * sizeof(ProbDesc)) != cudaSuccess) {
+    cudaGetLastError();
+    h->h_desc_pin = nullptr;
+    ds_destroy(h);
+    return DS_ERR_OOM;
+  }
   cudaMemcpy(h->d_depth0, h->h_depth0.data(), sizeof(float) * npx, cudaMemcpyHostToDevice);
   cudaMemcpy(h->d_pidx, h->h_pidx.data(), sizeof(int) * h->h_pidx.size(), cudaMemcpyHostToDevice);
   cudaMemset(h->d_acc, 0, sizeof(double) * ACC_COUNT);
@@ -1031,6 +1183,15 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
       return rc;
     }
     cudaMemcpy(h->d_tasks, tasks.data(), sizeof(int4) * tasks.size(), cudaMemcpyHostToDevice);
+    std::vector<int4> tasks_b;
+    make_chol_tasks_b((n + 127) / 128, tasks_b);
+    h->ntasks_b = (int)tasks_b.size();
+    if ((rc = halloc(h, &h->d_tasks_b, tasks_b.size()))) {
+      free_cp(h);
+      return rc;
+    }
+    cudaMemcpy(h->d_tasks_b, tasks_b.data(), sizeof(int4) * tasks_b.size(),
+               cudaMemcpyHostToDevice);
   }
   h->prec_fp64 = prec == DS_PREC_FP64;
   {
@@ -1097,6 +1258,9 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
     lp.flags = h->d_lflags;
     lp.tasks = h->d_tasks;
     lp.ntasks = h->ntasks;
+    lp.tasks_b = h->d_tasks_b;
+    lp.ntasks_b = h->ntasks_b;
+    lp.nb = (n + 127) / 128;
     lp.status = h->d_acc + ACC_STATUS;
     lp.y = h->d_v3;
     lp.x = h->d_v2;
@@ -1317,6 +1481,35 @@ int ds_batch_solve(ds_batch b, int32_t iters) {
   bool graph = !b->no_graph;
   for (ds_ctx* h : b->hs) graph = graph && h->prm.use_graph;
   return run_batch(b, iters, graph);
+}
+
+int ds_batch_tune(ds_batch b, int32_t reps, int32_t* choice, double* ms3) {
+  if (!b || reps < 1 || reps > 100) return DS_ERR_ARG;
+  if (b->error) return DS_ERR_CUDA;
+  if (b->stale) return DS_ERR_STATE;
+  if (b->fp64 || b->block_jacobi) {
+    if (choice) *choice = -1;   // one kernel only: nothing to choose
+    if (ms3) ms3[0] = ms3[1] = ms3[2] = -1.0;
+    return DS_OK;
+  }
+  const int rc = tune_factor(b, reps);
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[tune_key(b)] = b->tabs.factor_tc;
+  }
+  if (choice) *choice = b->tabs.factor_tc;
+  if (ms3)
+    for (int c = 0; c < 3; ++c) ms3[c] = b->tune_ms[c];
+  return DS_OK;
+}
+
+int ds_batch_factor_kernel(ds_batch b, int32_t* choice, double* ms3) {
+  if (!b || !choice) return DS_ERR_ARG;
+  *choice = (b->fp64 || b->block_jacobi) ? -1 : b->tabs.factor_tc;
+  if (ms3)
+    for (int c = 0; c < 3; ++c) ms3[c] = b->tune_ms[c];
+  return DS_OK;
 }
 
 int ds_batch_set_graph(ds_batch b, int32_t on) {
@@ -1626,8 +1819,11 @@ int ds_destroy(ds_handle h) {
   hfree(h, h->d_rs_mask); hfree(h, h->d_rs_what); hfree(h, h->d_rs_kept); hfree(h, h->d_rs_counts);
   hfree(h, h->d_rs_o1); hfree(h, h->d_rs_o1df);
   hfree(h, h->d_acc); hfree(h, h->d_hist); hfree(h, h->d_flag);
-  for (int k = 0; k < 2; ++k)
+  for (int k = 0; k < 2; ++k) {
     if (h->ev_slot_free[k]) cudaEventDestroy(h->ev_slot_free[k]);
+    if (h->ev_desc[k]) cudaEventDestroy(h->ev_desc[k]);
+  }
+  if (h->h_desc_pin) cudaFreeHost(h->h_desc_pin);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
   return DS_OK;

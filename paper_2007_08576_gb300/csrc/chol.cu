@@ -1026,12 +1026,503 @@ __global__ __launch_bounds__(256, 1) void k_chol_tc(const ProbDesc* const* __res
   }
 }
 
+// ----------------------------------------------------------------------------- 128-block tensor-core factor
+
+// FP32 factorisation on the tensor cores with 128 x 128 blocks: the same left-looking scheme as
+// k_chol_dag, one task per output block, in block-column order:
+//   DIAG(J)     C = A_JJ - sum_{k<J} L_Jk L_Jk^T;  L_JJ = chol(C), X_JJ = L_JJ^-1
+//   OFF(I, J)   C = A_IJ - sum_{k<J} L_Ik L_Jk^T;  L_IJ = C X_JJ^T                (I > J)
+// Every block product is a tcgen05.mma chain with M = N = 128 (kind::tf32, 3 terms per product:
+// a_hi b_hi + a_hi b_lo + a_lo b_hi, x = x_hi + x_lo with x_hi the round-to-nearest TF32 value of
+// x, so each product is accurate to about 2^-21 relative: FP32 level for the refinement steps).
+// The 128 x 128 accumulator lives in tensor memory (128 lanes x 128 columns).
+//
+// Packed block slots (one per finished block (I, J), J <= I): 128 rows x 128 K values as four
+// K-chunks of 32; chunk q holds the TF32 hi part (4096 floats) then the lo part (4096 floats), each
+// in the canonical K-major layout without swizzle: core matrices of 8 rows x 4 floats (128 B),
+// element (r, m) of the chunk at ((r / 8) * 8 + m / 4) * 32 + (r % 8) * 4 + m % 4, i.e. 128 B
+// between core matrices along K and 1024 B between 8-row groups. Slot (I, J), I > J, holds L_IJ
+// (row r, K index = column); slot (J, J) holds X_JJ (row c, K index m), the B operand of C X^T.
+//
+// Thread 0 streams the operand chunks of a product into three 64 KB shared-memory stages with
+// bulk copies (an A chunk and a B chunk of 32 KB each), issues the 12 MMAs of a chunk as soon as
+// its copies land and refills the stage of the previous chunk once that chunk's MMAs have
+// completed (tcgen05.commit on the stage's mbarrier), so the tensor pipe always has the next
+// chunk queued. The diagonal block is factored on the SIMT pipes from the accumulator in 64 x 64
+// halves (potrf_regs), with its 128 x 128 inverse by X10 = -X11 (L10 X00). An off-diagonal
+// block's C = A_IJ - acc is written to its own slot (hi / lo) and streamed back as the A operand
+// of C X_JJ^T, which goes through the same stages. The finished blocks are written to A
+// (row-major, for the triangular solves) and to the packed slots; the diagonal 64 x 64 inverses
+// go to Dinv for the solves.
+namespace tcb {
+
+constexpr int BS = 128;                   // block size
+constexpr int KC = 32;                    // K per chunk
+constexpr int kChunk = BS * KC;           // floats of one part (hi or lo) of a chunk
+constexpr int kSlot = 2 * BS * BS;        // floats per slot (4 chunks of hi + lo)
+constexpr unsigned kPairBytes = 2u * kChunk * 4u;   // 32 KB: hi + lo of one chunk
+constexpr int kStages = 3;
+constexpr unsigned kStageBytes = 2u * kPairBytes;   // A chunk + B chunk
+constexpr unsigned kSmem = kStages * kStageBytes;   // 192 KB
+// kind::tf32, D = F32, A = B = TF32, both K-major, N = 128, M = 128
+constexpr unsigned kIdesc =
+    (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+
+__host__ __device__ __forceinline__ size_t slot(int i, int j) { return (size_t)i * (i + 1) / 2 + j; }
+// offset of element (r, k) of a block (row r, K index k) in its slot (hi part; lo at + kChunk)
+__device__ __forceinline__ int soff(int r, int k) {
+  return (k >> 5) * (2 * kChunk) + (((r >> 3) * 8 + ((k & 31) >> 2)) * 32 + (r & 7) * 4 + (k & 3));
+}
+__device__ __forceinline__ uint64_t sdesc(unsigned saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) |
+         ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46);
+}
+__device__ __forceinline__ void mma(unsigned tmem, uint64_t a, uint64_t b, unsigned acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+// D (+)= A B^T over the 32 K values of one chunk pair (A at sa, B at sb; hi then lo parts)
+__device__ __forceinline__ void mma_chunk(unsigned tmem, unsigned sa, unsigned sb, bool accumulate) {
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const unsigned ah = t == 2 ? sa + kChunk * 4u : sa, bh = t == 1 ? sb + kChunk * 4u : sb;
+#pragma unroll
+    for (int kk = 0; kk < KC / 8; ++kk)
+      mma(tmem, sdesc(ah + 256u * kk), sdesc(bh + 256u * kk),
+          (accumulate || t > 0 || kk > 0) ? 1u : 0u);
+  }
+}
+// 32 consecutive accumulator columns of this thread's lane (row)
+__device__ __forceinline__ void tmem_ld32(unsigned taddr, float (&v)[32]) {
+  unsigned r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+// This thread's 64 accumulator values: row 32 (warp % 4) + lane, columns 64 (warp / 4) + 0..63.
+__device__ __forceinline__ void tmem_row64(unsigned tmem, float (&v)[64]) {
+  const int warp = threadIdx.x >> 5;
+  const unsigned ta = tmem + ((unsigned)(32 * (warp & 3)) << 16) + 64u * (warp >> 2);
+  float h[32];
+  tmem_ld32(ta, h);
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = h[i];
+  tmem_ld32(ta + 32u, h);
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[32 + i] = h[i];
+}
+// four consecutive values (row r, K index k..k+3, k % 4 == 0) of a block into a global slot
+__device__ __forceinline__ void put4(float* slot, int r, int k, float a, float b, float c, float d) {
+  const float ha = tc::tf32_rna(a), hb = tc::tf32_rna(b), hc = tc::tf32_rna(c),
+              hd = tc::tf32_rna(d);
+  const int o = soff(r, k);
+  __stcg(reinterpret_cast<float4*>(slot + o), make_float4(ha, hb, hc, hd));
+  __stcg(reinterpret_cast<float4*>(slot + kChunk + o),
+         make_float4(tc::tf32_rna(a - ha), tc::tf32_rna(b - hb), tc::tf32_rna(c - hc),
+                     tc::tf32_rna(d - hd)));
+}
+
+// Producer / MMA state of thread 0, kept across tasks so the barrier phases stay in step.
+struct Pipe {
+  unsigned cph[kStages];   // parity of the next copy completion per stage
+  int mc[kStages], mw[kStages];   // MMA commits issued / waited per stage
+};
+
+// Thread 0: D = sum_{c < nck} A_c B_c^T, chunk pairs A_c = pa(c), B_c = pb(c) (nullptr: B = A),
+// dep(c) waited before the copies of chunk c. Every issued copy is waited exactly once and every
+// commit is waited before return (so the phases stay in step); bfin is committed after the last
+// MMA. False if a wait gave up (error word raised); the accumulator is then not meaningful.
+template <typename PA, typename PB, typename DEP>
+__device__ bool stream(unsigned tmem, unsigned char* stg, Pipe& pp, unsigned long long* bcopy,
+                       unsigned long long* bmma, unsigned long long* bfin, int nck, PA pa, PB pb,
+                       DEP dep, int* err, unsigned long long budget) {
+  bool ok = true;
+  int issued = 0;
+  auto wait_mma = [&](int s) {
+    const bool g = mbar_wait(&bmma[s], (unsigned)(pp.mw[s] & 1), err, budget);
+    ++pp.mw[s];
+    return g;
+  };
+  auto issue = [&](int c) {
+    const int s = c % kStages;
+    while (pp.mw[s] < pp.mc[s])
+      if (!wait_mma(s)) return false;   // the stage's previous MMAs are done with it
+    if (!dep(c)) return false;
+    fence_proxy_async_global();
+    const float* a = pa(c);
+    const float* b = pb(c);
+    unsigned char* d = stg + s * kStageBytes;
+    mbar_expect(&bcopy[s], b ? 2 * kPairBytes : kPairBytes);
+    bulk_load(d, a, kPairBytes, &bcopy[s]);
+    if (b) bulk_load(d + kPairBytes, b, kPairBytes, &bcopy[s]);
+    return true;
+  };
+  while (ok && issued < nck && issued < kStages) {
+    ok = issue(issued);
+    if (ok) ++issued;
+  }
+  for (int c = 0; c < issued; ++c) {
+    const int s = c % kStages;
+    const bool got = mbar_wait(&bcopy[s], pp.cph[s], err, budget);
+    pp.cph[s] ^= 1u;
+    if (!got) ok = false;
+    if (ok) {
+      tc::fence_after();
+      const unsigned sa = smem_u32(stg + s * kStageBytes);
+      mma_chunk(tmem, sa, pb(c) ? sa + kPairBytes : sa, c > 0);
+      tc::commit(&bmma[s]);
+      ++pp.mc[s];
+      if (c >= 1 && issued < nck) {   // refill the stage chunk c - 1 used
+        ok = issue(issued);
+        if (ok) ++issued;
+      }
+    }
+  }
+  tc::commit(bfin);
+  for (int s = 0; s < kStages; ++s)
+    while (pp.mw[s] < pp.mc[s]) wait_mma(s);
+  return ok;
+}
+
+}  // namespace tcb
+
+__global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __restrict__ descs,
+                                                     const int2* __restrict__ tickets,
+                                                     int nticket, int* __restrict__ head,
+                                                     int* __restrict__ err,
+                                                     unsigned long long budget_ns) {
+  using namespace tcb;
+  constexpr int TB = 64, LDS = TB + 1, RT = 4;
+  constexpr int LDC = BS + 1;
+  extern __shared__ __align__(1024) unsigned char smb[];
+  float* sm = reinterpret_cast<float*>(smb);
+  __shared__ __align__(8) unsigned long long bcopy[kStages], bmma[kStages], bfin;
+  __shared__ unsigned s_tmem;
+  __shared__ int s_t, s_ok, s_str;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tr = (tid / 16) * RT, tcl = (tid % 16) * RT;      // 64 x 64 register blocks
+  const int arow = 32 * (warp & 3) + lane, acol = 64 * (warp >> 2);   // accumulator ownership
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&bcopy[s]);
+      mbar_init(&bmma[s]);
+    }
+    mbar_init(&bfin);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+                     smem_u32(&s_tmem))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const unsigned tmem = s_tmem;
+  Pipe pp;
+  for (int s = 0; s < kStages; ++s) {
+    pp.cph[s] = 0u;
+    pp.mc[s] = pp.mw[s] = 0;
+  }
+  unsigned fph = 0u;   // parity of the next bfin completion (all threads)
+  // A wait that gives up raises the error word; every CTA then leaves its ticket loop (after its
+  // copies and products in flight have completed), and the host reports DS_ERR_TIMEOUT.
+  for (;;) {
+    if (tid == 0) s_t = atomicAdd(head, 1);
+    __syncthreads();
+    const int t = s_t;
+    if (t >= nticket) break;
+    const int2 pt = tickets[t];
+    const LinProblem& P = descs[pt.x]->lp;
+    const int4 tk = P.tasks_b[pt.y];
+    const bool diag = tk.y == 0;
+    const int I = tk.z, J = tk.w, nb = P.nb, n = P.n;
+    int* pdone = P.cnt;
+    int* tdone = P.cnt + nb;
+    float* A = (float*)P.A;
+    float* Lp = (float*)P.Lp;
+    const int nck = 4 * J;
+    // ---- K loop: acc = sum_{k<J} L_Ik L_Jk^T
+    if (tid == 0) {
+      s_ok = *(volatile int*)err == 0;
+      s_str = s_ok && nck > 0;
+      if (s_str) {
+        const float* si = Lp + slot(I, 0) * kSlot;
+        const float* sj = Lp + slot(J, 0) * kSlot;
+        s_ok = stream(
+            tmem, smb, pp, bcopy, bmma, &bfin, nck,
+            [&](int c) { return si + (size_t)(c >> 2) * kSlot + (c & 3) * 2 * kChunk; },
+            [&](int c) -> const float* {
+              return diag ? nullptr : sj + (size_t)(c >> 2) * kSlot + (c & 3) * 2 * kChunk;
+            },
+            [&](int c) {
+              if (c & 3) return true;
+              const int kb = c >> 2;
+              return wait_flag(&tdone[I * nb + kb], 1, err, budget_ns) &&
+                     (diag || wait_flag(&tdone[J * nb + kb], 1, err, budget_ns));
+            },
+            err, budget_ns);
+      }
+    }
+    __syncthreads();
+    bool ok = s_ok;
+    if (s_str) {   // thread 0 streamed the K loop and committed bfin after its last product
+      const bool got = mbar_wait(&bfin, fph, err, budget_ns);
+      fph ^= 1u;
+      ok = !__syncthreads_or(!got || !ok);
+    }
+    if (!ok) break;
+    tc::fence_after();
+    float v[64];
+    if (nck > 0) {
+      tcb::tmem_row64(tmem, v);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 64; ++e) v[e] = 0.f;
+    }
+    tc::fence_before();
+    __syncthreads();   // accumulator read before the stages / tensor memory are reused
+    const int rg = I * BS + arow;   // this thread's matrix row
+    if (diag) {
+      // ---- DIAG(J): C (lower, identity padding) -> L_JJ, X_JJ on the SIMT pipes
+      float* Cs = sm;                       // 128 x 129
+      float* L00 = Cs + BS * LDC;           // 64 x 65 each
+      float* X00 = L00 + TB * LDS;
+      float* L11 = X00 + TB * LDS;
+      float* X11 = L11 + TB * LDS;
+      float* X10 = X11 + TB * LDS;
+      float* Tt = X10 + TB * LDS;
+      float* Pt = Tt + TB * LDS;            // potrf_regs scratch
+      float* Dsm = Pt + 8 * TileCfg<float, TB>::LDT;
+      float* Tm = Dsm + 64;
+      const int r0 = J * BS;
+      // lower part of C inside the matrix; identity on the padding past n; zero above
+#pragma unroll
+      for (int e = 0; e < 64; ++e) {
+        const int c = acol + e;
+        float x;
+        if (rg < n && r0 + c < n)
+          x = c <= arow ? __ldcg(A + (size_t)rg * n + r0 + c) - v[e] : 0.f;
+        else
+          x = c == arow ? 1.f : 0.f;
+        Cs[arow * LDC + c] = x;
+      }
+      for (int e = tid; e < TB * LDS; e += blockDim.x) {
+        X00[e] = 0.f;
+        X11[e] = 0.f;
+      }
+      __syncthreads();
+      float a[RT][RT];
+#pragma unroll
+      for (int p = 0; p < RT; ++p)
+#pragma unroll
+        for (int q = 0; q < RT; ++q) a[p][q] = Cs[(tr + p) * LDC + tcl + q];
+      potrf_regs<float, TB>(a, L00, X00, Pt, Dsm, Tm, r0, P.status);
+      // L10 = C10 X00^T
+      float w[RT][RT];
+#pragma unroll
+      for (int p = 0; p < RT; ++p)
+#pragma unroll
+        for (int q = 0; q < RT; ++q) w[p][q] = 0.f;
+      for (int m = 0; m < TB; ++m) {
+        float x[RT], y[RT];
+#pragma unroll
+        for (int p = 0; p < RT; ++p) x[p] = Cs[(TB + tr + p) * LDC + m];
+#pragma unroll
+        for (int q = 0; q < RT; ++q) y[q] = X00[(tcl + q) * LDS + m];
+#pragma unroll
+        for (int p = 0; p < RT; ++p)
+#pragma unroll
+          for (int q = 0; q < RT; ++q) w[p][q] += x[p] * y[q];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int p = 0; p < RT; ++p)
+#pragma unroll
+        for (int q = 0; q < RT; ++q) Cs[(TB + tr + p) * LDC + tcl + q] = w[p][q];
+      __syncthreads();
+      // C11 - L10 L10^T
+#pragma unroll
+      for (int p = 0; p < RT; ++p)
+#pragma unroll
+        for (int q = 0; q < RT; ++q) a[p][q] = Cs[(TB + tr + p) * LDC + TB + tcl + q];
+      for (int m = 0; m < TB; ++m) {
+        float x[RT], y[RT];
+#pragma unroll
+        for (int p = 0; p < RT; ++p) x[p] = Cs[(TB + tr + p) * LDC + m];
+#pragma unroll
+        for (int q = 0; q < RT; ++q) y[q] = Cs[(TB + tcl + q) * LDC + m];
+#pragma unroll
+        for (int p = 0; p < RT; ++p)
+#pragma unroll
+          for (int q = 0; q < RT; ++q) a[p][q] -= x[p] * y[q];
+      }
+      potrf_regs<float, TB>(a, L11, X11, Pt, Dsm, Tm, r0 + TB, P.status);
+      // T = L10 X00, X10 = -X11 T
+#pragma unroll
+      for (int p = 0; p < RT; ++p)
+#pragma unroll
+        for (int q = 0; q < RT; ++q) w[p][q] = 0.f;
+      for (int m = 0; m < TB; ++m) {
+        float x[RT], y[RT];
+#pragma unroll
+        for (int p = 0; p < RT; ++p) x[p] = Cs[(TB + tr + p) * LDC + m];
+#pragma unroll
+        for (int q = 0; q < RT; ++q) y[q] = X00[m * LDS + tcl + q];
+#pragma unroll
+        for (int p = 0; p < RT; ++p)
+#pragma unroll
+          for (int q = 0; q < RT; ++q) w[p][q] += x[p] * y[q];
+      }
+#pragma unroll
+      for (int p = 0; p < RT; ++p)
+#pragma unroll
+        for (int q = 0; q < RT; ++q) Tt[(tr + p) * LDS + tcl + q] = w[p][q];
+      __syncthreads();
+#pragma unroll
+      for (int p = 0; p < RT; ++p)
+#pragma unroll
+        for (int q = 0; q < RT; ++q) w[p][q] = 0.f;
+      for (int m = 0; m < TB; ++m) {
+        float x[RT], y[RT];
+#pragma unroll
+        for (int p = 0; p < RT; ++p) x[p] = X11[(tr + p) * LDS + m];
+#pragma unroll
+        for (int q = 0; q < RT; ++q) y[q] = Tt[m * LDS + tcl + q];
+#pragma unroll
+        for (int p = 0; p < RT; ++p)
+#pragma unroll
+          for (int q = 0; q < RT; ++q) w[p][q] -= x[p] * y[q];
+      }
+#pragma unroll
+      for (int p = 0; p < RT; ++p)
+#pragma unroll
+        for (int q = 0; q < RT; ++q) X10[(tr + p) * LDS + tcl + q] = w[p][q];
+      __syncthreads();
+      // outputs: L_JJ -> A (lower, in range), X00 / X11 -> Dinv, X_JJ -> slot (J, J)
+      const int nt64 = P.nt;
+      float* D0 = (float*)P.Dinv + (size_t)(2 * J) * TB * TB;
+      for (int e = tid; e < TB * TB; e += blockDim.x) {
+        const int r = e / TB, c = e % TB;
+        __stcg(D0 + e, c <= r ? X00[r * LDS + c] : 0.f);
+        if (2 * J + 1 < nt64) __stcg(D0 + TB * TB + e, c <= r ? X11[r * LDS + c] : 0.f);
+      }
+      for (int e = tid; e < BS * BS; e += blockDim.x) {
+        const int r = e / BS, c = e % BS;
+        if (c > r || r0 + r >= n) continue;
+        const float l = r < TB ? L00[r * LDS + c]
+                               : (c < TB ? Cs[r * LDC + c] : L11[(r - TB) * LDS + c - TB]);
+        __stcg(A + (size_t)(r0 + r) * n + r0 + c, l);
+      }
+      float* S = Lp + slot(J, J) * kSlot;
+      for (int e = tid; e < BS * BS / 4; e += blockDim.x) {
+        const int r = e / (BS / 4), k = 4 * (e % (BS / 4));
+        float x4[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int c = k + q;
+          float x = 0.f;
+          if (c <= r) {
+            if (r < TB) x = X00[r * LDS + c];
+            else if (c < TB) x = X10[(r - TB) * LDS + c];
+            else x = X11[(r - TB) * LDS + c - TB];
+          }
+          x4[q] = x;
+        }
+        tcb::put4(S, r, k, x4[0], x4[1], x4[2], x4[3]);
+      }
+    } else {
+      // ---- OFF(I, J): C = A_IJ - acc into slot (I, J), then L_IJ = C X_JJ^T
+      float* S = Lp + slot(I, J) * kSlot;
+      const int c0 = J * BS;
+#pragma unroll
+      for (int e = 0; e < 64; e += 4) {
+        const int c = acol + e;
+        float x[4] = {0.f, 0.f, 0.f, 0.f};
+        if (rg < n) {
+          const float2 p0 = __ldcg(reinterpret_cast<const float2*>(A + (size_t)rg * n + c0 + c));
+          const float2 p1 =
+              __ldcg(reinterpret_cast<const float2*>(A + (size_t)rg * n + c0 + c + 2));
+          x[0] = p0.x - v[e];
+          x[1] = p0.y - v[e + 1];
+          x[2] = p1.x - v[e + 2];
+          x[3] = p1.y - v[e + 3];
+        }
+        tcb::put4(S, arow, c, x[0], x[1], x[2], x[3]);
+      }
+      fence_proxy_async_global();
+      __syncthreads();
+      if (tid == 0) {
+        const float* sx = Lp + slot(J, J) * kSlot;
+        s_ok = stream(
+            tmem, smb, pp, bcopy, bmma, &bfin, 4,
+            [&](int c) { return (const float*)S + c * 2 * kChunk; },
+            [&](int c) -> const float* { return sx + c * 2 * kChunk; },
+            [&](int c) { return c > 0 || wait_flag(&pdone[J], 1, err, budget_ns); }, err,
+            budget_ns);
+      }
+      __syncthreads();
+      {
+        const bool got = mbar_wait(&bfin, fph, err, budget_ns);
+        fph ^= 1u;
+        if (__syncthreads_or(!got || !s_ok)) break;
+      }
+      tc::fence_after();
+      tcb::tmem_row64(tmem, v);
+      tc::fence_before();
+      __syncthreads();
+      if (rg < n) {
+#pragma unroll
+        for (int e = 0; e < 64; e += 2)
+          __stcg(reinterpret_cast<float2*>(A + (size_t)rg * n + c0 + acol + e),
+                 make_float2(v[e], v[e + 1]));
+      }
+#pragma unroll
+      for (int e = 0; e < 64; e += 4)
+        tcb::put4(S, arow, acol + e, v[e], v[e + 1], v[e + 2], v[e + 3]);
+    }
+    // generic writes (shared: before the next task's copies; global: before other CTAs' copies)
+    fence_proxy_async_shared();
+    fence_proxy_async_global();
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      if (diag)
+        st_release(&pdone[J], 1);
+      else
+        st_release(&tdone[I * nb + J], 1);
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+  }
+}
+
 template <typename T>
 size_t chol_packed_elems(int nt) {
   constexpr int TB = sizeof(T) == 8 ? 32 : 64;
-  // FP32: room for the tensor-core slots (hi + lo, K-major), which are larger than the SIMT
-  // kernel's transposed padded tiles; FP64: transposed padded tiles
-  return sizeof(T) == 4 ? tile_slot(nt, 0) * (size_t)tc::kSlot
+  // FP32: room for the larger of the tensor-core layouts (64-tile and 128-block slots, hi + lo,
+  // K-major), which also holds the SIMT kernel's transposed padded tiles; FP64: transposed
+  // padded tiles
+  const int nb = (nt + 1) / 2;   // 128-row blocks
+  return sizeof(T) == 4 ? std::max(tile_slot(nt, 0) * (size_t)tc::kSlot,
+                                   tcb::slot(nb, 0) * (size_t)tcb::kSlot)
                         : tile_slot(nt, 0) * (size_t)TB * TileCfg<T, TB>::LDT;
 }
 template size_t chol_packed_elems<float>(int);
@@ -1039,8 +1530,38 @@ template size_t chol_packed_elems<double>(int);
 
 
 
+// Synthetic SPD system of every problem's size, for timing the factorisation kernels (FP32
+// precisions): A_ii = n, A_ij = 1 / (2 (1 + |i - j|)^2) below the diagonal (diagonally dominant).
+__global__ void k_fill_spd(const ProbDesc* const* __restrict__ descs) {
+  const LinProblem& P = descs[blockIdx.y]->lp;
+  const int n = P.n;
+  float* A = (float*)P.A;
+  const size_t tot = (size_t)n * n;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    if (j > i) continue;
+    const float d = 1.f + (float)(i - j);
+    A[e] = i == j ? (float)n : 0.5f / (d * d);
+  }
+}
+
+void launch_fill_spd(const BatchTabs& B, cudaStream_t s) {
+  k_fill_spd<<<dim3(64, B.P), 256, 0, s>>>(B.d);
+  ++g_launches;
+}
+
 template <typename T>
 void launch_chol_dag(const BatchTabs& B, cudaStream_t s) {
+  if (sizeof(T) == 4 && B.factor_tc == 2) {
+    static PerDevice attr_b;
+    set_smem_once(attr_b, k_chol_tcb, (int)tcb::kSmem);
+    const int grid = std::min(B.n_chol_b, num_sms());
+    k_chol_tcb<<<grid, 256, tcb::kSmem, s>>>(B.d, B.chol_b, B.n_chol_b, B.words + 0, B.words + 5,
+                                             2000000000ull);
+    ++g_launches;
+    return;
+  }
   if (sizeof(T) == 4 && B.factor_tc) {
     static PerDevice attr_tc, occ_tc;
     set_smem_once(attr_tc, k_chol_tc, (int)tc::kSmem);

@@ -64,6 +64,9 @@ struct LinProblem {
   int* flags;
   const int4* tasks;
   int ntasks;
+  const int4* tasks_b;  // the tasks of the 128 x 128 block factorisation (tensor cores)
+  int ntasks_b;
+  int nb;               // 128-row blocks
   double* status;
   void* y;
   void* x;
@@ -215,7 +218,10 @@ struct BatchTabs {
   int orb_ctas;              // CTAs per problem of the ORB pass (grid-stride over M)
   const int2* chol;          // (problem, task) per factorisation ticket, in claim order
   int n_chol;
-  int factor_tc;             // FP32 factorisation on the tensor cores (1) or the SIMT pipes (0)
+  const int2* chol_b;        // the same for the 128 x 128 block tasks
+  int n_chol_b;
+  int factor_tc;             // FP32 factorisation: 0 SIMT 64-tiles, 1 tensor cores 64-tiles,
+                             // 2 tensor cores 128-blocks
   int max_tasks;             // max factorisation tasks over the problems
   int max_nt;                // max tile rows over the problems
   int* words;                // [0] factorisation head, [1..4] solve heads, [5] timeout word
@@ -242,7 +248,7 @@ void launch_iter_end(const BatchTabs& B, int it, bool step, cudaStream_t s);
 template <typename T>
 int chol_tile();
 template <typename T>
-size_t chol_packed_elems(int nt);  // elements of the packed L tiles (either FP32 kernel's layout)
+size_t chol_packed_elems(int nt);  // elements of the packed L tiles (every FP32 kernel's layout)
 template <typename T>
 void launch_chol_dag(const BatchTabs& B, cudaStream_t s);
 template <typename T>
@@ -250,6 +256,8 @@ void launch_trsv_dag(const BatchTabs& B, int solve_id, bool from_r, bool assign,
 // refinement residual r = b - A x against the FP32 system (double-float accumulation)
 void launch_residual64(const BatchTabs& B, cudaStream_t s);
 void launch_sym_unpack(const float* A, int n, double* out, cudaStream_t s);
+// synthetic SPD systems of the batch's sizes in the FP32 factor buffers (factor kernel timing)
+void launch_fill_spd(const BatchTabs& B, cudaStream_t s);
 
 // Kernels enqueued by this host thread (stream launches, including those recorded into a graph
 // under capture); the API layer reads differences of it.

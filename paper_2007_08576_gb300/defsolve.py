@@ -20,12 +20,14 @@ DS_OK, DS_ERR_ARG, DS_ERR_OOM, DS_ERR_BAD_INPUT, DS_ERR_NOT_SPD, DS_ERR_STATE, D
 DS_PREC_FP64, DS_PREC_FP32, DS_PREC_FP32_REFINE = 0, 1, 2
 DS_MAX_ITERS = 64
 DS_MAX_HYP = 64
+DS_FACTOR_AUTO = 3
 
 # every exported symbol of include/defsolve.h and include/defsolve_orb.h
 EXPORTS = [
     "ds_default_params", "ds_create_template", "ds_set_control_points", "ds_submit_frame",
     "ds_solve", "ds_solve_batch", "ds_batch_create", "ds_batch_solve", "ds_batch_status",
-    "ds_batch_destroy", "ds_batch_set_tracing", "ds_batch_phase_times", "ds_batch_set_graph", "ds_get_deformation", "ds_get_deformation64",
+    "ds_batch_destroy", "ds_batch_set_tracing", "ds_batch_phase_times", "ds_batch_set_graph",
+    "ds_batch_tune", "ds_batch_factor_kernel", "ds_get_deformation", "ds_get_deformation64",
     "ds_set_deformation", "ds_get_inlier_mask", "ds_get_ransac", "ds_get_cost",
     "ds_get_blend_table", "ds_get_frame_points", "ds_linearize", "ds_set_tracing",
     "ds_get_phase_times", "ds_get_counters", "ds_get_device_bytes", "ds_ransac_noalloc",
@@ -103,6 +105,8 @@ def lib(path: str | None = None):
         "ds_batch_destroy": (i32, [vp]),
         "ds_batch_set_tracing": (i32, [vp, i32]),
         "ds_batch_set_graph": (i32, [vp, i32]),
+        "ds_batch_tune": (i32, [vp, i32, ctypes.POINTER(i32), vp]),
+        "ds_batch_factor_kernel": (i32, [vp, ctypes.POINTER(i32), vp]),
         "ds_batch_phase_times": (i32, [vp, vp]),
         "ds_get_deformation": (i32, [vp, vp, vp, vp]),
         "ds_get_deformation64": (i32, [vp, vp, vp]),
@@ -237,6 +241,22 @@ def ds_batch_status(b):
 
 def ds_batch_set_tracing(b, on=True):
     _check("ds_batch_set_tracing", lib().ds_batch_set_tracing(b, 1 if on else 0))
+
+
+def ds_batch_tune(b, reps=3):
+    """(chosen factor kernel, [ms of kernels 0, 1, 2]) after timing them on the batch's sizes."""
+    c = ctypes.c_int32()
+    ms = np.zeros(3, np.float64)
+    _check("ds_batch_tune", lib().ds_batch_tune(b, int(reps), ctypes.byref(c), _ptr(ms, np.float64)))
+    return c.value, ms
+
+
+def ds_batch_factor_kernel(b):
+    c = ctypes.c_int32()
+    ms = np.zeros(3, np.float64)
+    _check("ds_batch_factor_kernel",
+           lib().ds_batch_factor_kernel(b, ctypes.byref(c), _ptr(ms, np.float64)))
+    return c.value, ms
 
 
 def ds_batch_set_graph(b, on=True):

@@ -73,11 +73,15 @@ def stream_bytes(W: int, H: int, N: int, M: int, precision: int) -> int:
     nt = (n + tb - 1) // tb
     tsz = 8 if precision == 0 else 4
     b += 4 * (nt + 2 * nt * nt) + tsz * nt * tb * tb
-    # packed factor tiles: FP64 transposed padded tiles; FP32 slots sized for the tensor-core
-    # kernel's hi / lo operand layout (8192 floats), which also hold the SIMT kernel's tiles
-    slot = tb * (tb + 16 // tsz) if precision == 0 else 8192
-    b += tsz * nt * (nt + 1) // 2 * slot
-    b += nt * (nt + 1) // 2 * 16 * 2                    # task list
+    # packed factor tiles: FP64 transposed padded tiles; FP32: the larger of the tensor-core
+    # layouts (64 x 64 tiles of 8192 floats, 128 x 128 blocks of 32768 floats, hi / lo), which
+    # also holds the SIMT kernel's tiles
+    nb = (n + 127) // 128
+    if precision == 0:
+        b += tsz * nt * (nt + 1) // 2 * tb * (tb + 16 // tsz)
+    else:
+        b += tsz * max(nt * (nt + 1) // 2 * 8192, nb * (nb + 1) // 2 * 32768)
+    b += nt * (nt + 1) // 2 * 16 * 2 + nb * (nb + 1) // 2 * 16   # task lists
     b += 2 * M * (4 + 12 + 4 + 4) + M * (8 * 3 + 4 * 6)  # 2 slots of matches + RANSAC results
     b += M * 64 * (7 * 8 + 4) + M * 8                   # RANSAC scratch, weights, bitsets
     return int(b)
@@ -97,6 +101,9 @@ class GpuEngine:
         self.use_graph = bool(use_graph)
         self.cache = collections.OrderedDict()
         self.cache_cap = cache
+        # per stream: pinned host staging of its frames (a copy from pageable memory would make
+        # the host wait for the stream's earlier work)
+        self.staging = {}
 
     @property
     def precision(self):
@@ -104,16 +111,32 @@ class GpuEngine:
 
     def create(self, spec: StreamSpec):
         s = self.d.Solver(spec.template_depth, spec.K, spec.nodes, self.params)
+        H, W = spec.template_depth.shape
+        M = spec.max_matches
+        pin = lambda shape, dt: self.torch.empty(shape, dtype=dt, pin_memory=True).numpy()
+        t = self.torch
+        self.staging[id(s)] = (pin((H, W), t.float32), pin((M,), t.int32), pin((M, 3), t.float32),
+                               pin((int(self.params.n_hyp),), t.int32))
         return s
 
     def destroy(self, s):
         for key in [k for k in self.cache if id(s) in k]:
             b, _, _ = self.cache.pop(key)
             self.d.ds_batch_destroy(b)
+        self.staging.pop(id(s), None)
         s.close()
 
     def submit(self, s, f: FrameIn):
-        s.submit(f.depth, f.match_idx, f.match_xyz, f.hyp)
+        """Copies the frame into the stream's pinned staging and submits it from there. The
+        staging is free again: the server submits a stream's next frame only after the batch
+        that read its previous one has completed, and that batch ran after the copies."""
+        dep, mi, mx, hy = self.staging[id(s)]
+        M = len(f.match_idx)
+        np.copyto(dep, f.depth)
+        np.copyto(mi[:M], f.match_idx)
+        np.copyto(mx[:M], f.match_xyz)
+        np.copyto(hy[:len(f.hyp)], f.hyp)
+        s.submit(dep, mi[:M], mx[:M], hy[:len(f.hyp)])
 
     def launch(self, solvers, iters):
         key = tuple(sorted(id(s) for s in solvers))

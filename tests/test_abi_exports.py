@@ -67,6 +67,12 @@ def test_argument_errors_need_no_gpu(built):
     assert L.ds_selftest_bounded_wait(0, 10, 0, ctypes.byref(ms)) == d.DS_ERR_ARG
     assert L.ds_selftest_bounded_wait(0, 10**9, 0, ctypes.byref(ms)) == d.DS_ERR_ARG
     assert L.ds_selftest_bounded_wait(1, 1000000, 3, ctypes.byref(ms)) == d.DS_ERR_ARG
+    # the factor tuner and the device-byte count reject a null batch / handle
+    c = ctypes.c_int32()
+    assert L.ds_batch_tune(None, 2, ctypes.byref(c), None) == d.DS_ERR_ARG
+    assert L.ds_batch_factor_kernel(None, ctypes.byref(c), None) == d.DS_ERR_ARG
+    b = ctypes.c_int64()
+    assert L.ds_get_device_bytes(None, ctypes.byref(b)) == d.DS_ERR_ARG
 
 
 def test_binding_fails_loudly_without_the_library():

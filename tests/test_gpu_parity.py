@@ -419,12 +419,14 @@ def test_bounded_waits_give_up_and_the_context_stays_usable(d, tiny):
 # ----------------------------------------------------------------------------- tensor-core factor
 
 
+@pytest.mark.parametrize("ftc", [1, 2], ids=["tiles64", "blocks128"])
 @pytest.mark.parametrize("prec", [1, 2])
-def test_tensor_core_factor_matches_oracle_tiny_and_ragged(d, tiny, mid, prec):
-    """FP32 factorisation on tcgen05 (three TF32 terms per product): the same parity bar."""
+def test_tensor_core_factor_matches_oracle_tiny_and_ragged(d, tiny, mid, prec, ftc):
+    """FP32 factorisation on tcgen05 (three TF32 terms per product): the same parity bar, with
+    64 x 64 tiles and with 128 x 128 blocks."""
     for sc in (tiny, mid):
         fr = sc.frames[0]
-        p = d.default_params(precision=prec, factor_tc=1)
+        p = d.default_params(precision=prec, factor_tc=ftc)
         s, st, q, t = gpu_frame(d, sc, fr, p)
         tpl, res = _oracle(sc, fr, oracle_params(p))
         err = np.abs(tpl.g + t - res.pos).max()
@@ -434,10 +436,11 @@ def test_tensor_core_factor_matches_oracle_tiny_and_ragged(d, tiny, mid, prec):
         s.close()
 
 
-def test_tensor_core_factor_full_size_frame(d):
+@pytest.mark.parametrize("ftc", [1, 2], ids=["tiles64", "blocks128"])
+def test_tensor_core_factor_full_size_frame(d, ftc):
     sc = scene(CONFIGS["seq_320x240_n256"], 1000)
     fr = sc.frames[0]
-    p = d.default_params(precision=2, factor_tc=1)
+    p = d.default_params(precision=2, factor_tc=ftc)
     s, st, q, t = gpu_frame(d, sc, fr, p)
     tpl, res = _oracle(sc, fr, oracle_params(p))
     err = np.abs(tpl.g + t - res.pos).max()
@@ -451,7 +454,7 @@ def test_tensor_core_factor_batch_equals_simt_and_agreement_rule(d, tiny, mid):
     """An uneven batch factored on the tensor cores gives the SIMT batch's result within the
     parity tolerance; handles that disagree on the factor kernel cannot share a batch."""
     outs = {}
-    for ftc in (0, 1):
+    for ftc in (0, 1, 2):
         p = d.default_params(precision=2, factor_tc=ftc)
         solvers = []
         for sc in (mid, tiny, mid):
@@ -463,8 +466,9 @@ def test_tensor_core_factor_batch_equals_simt_and_agreement_rule(d, tiny, mid):
         outs[ftc] = [s.deformation64()[1] for s in solvers]
         for s in solvers:
             s.close()
-    for a, b in zip(outs[0], outs[1]):
-        assert np.abs(a - b).max() <= POS_TOL_MM
+    for ftc in (1, 2):
+        for a, b in zip(outs[0], outs[ftc]):
+            assert np.abs(a - b).max() <= POS_TOL_MM
     a = d.Solver(tiny.template_depth, tiny.K, tiny.nodes, d.default_params(precision=2))
     b = d.Solver(tiny.template_depth, tiny.K, tiny.nodes,
                  d.default_params(precision=2, factor_tc=1))
@@ -761,4 +765,47 @@ def test_ransac_degenerate_fit_is_the_identity(d, tiny):
     assert np.array_equal(ransac.kabsch(o1 - o1[0], xyz - xyz[0], np.ones(M)), np.eye(3))
     assert rs["mask"].any() and not rs["mask"].all()
     _check_ransac(d, s, p, rs, M)
+    s.close()
+
+
+# ----------------------------------------------------------------------------- factor-kernel tuner
+
+
+def test_factor_tuner_picks_the_fastest_and_auto_batches_stay_at_parity(d, tiny, mid):
+    """ds_batch_tune times the three FP32 factor kernels on the batch's sizes and keeps the
+    fastest; a batch of DS_FACTOR_AUTO handles tunes itself (or takes the cached choice) at its
+    first solve, and its results equal the SIMT batch's and the oracle within the parity bar."""
+    from synth.scene import Config
+    cfg3 = Config("seq_120x90_n40", 120, 90, 40, 300, 8, 0.4, 0.5, 0.1, 8.0, 1.0, 0.3, 0.5, 1)
+    scenes = [mid, tiny, scene(cfg3, 99)]
+    outs = {}
+    for ftc in (0, d.DS_FACTOR_AUTO):
+        p = d.default_params(precision=2, factor_tc=ftc)
+        solvers = []
+        for sc in scenes:
+            s = d.Solver(sc.template_depth, sc.K, sc.nodes, p)
+            fr = sc.frames[0]
+            s.submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+            solvers.append(s)
+        b = d.ds_batch_create([s.h for s in solvers])
+        if ftc == d.DS_FACTOR_AUTO:
+            choice, ms = d.ds_batch_tune(b, 2)
+            assert choice in (0, 1, 2) and (ms > 0).all()
+            assert ms[choice] == ms.min()
+            assert d.ds_batch_factor_kernel(b)[0] == choice
+        d.ds_batch_solve(b, 10)
+        d.ds_batch_status(b)
+        outs[ftc] = [s.deformation64()[1] for s in solvers]
+        d.ds_batch_destroy(b)
+        for s in solvers:
+            s.close()
+    for a, c in zip(outs[0], outs[d.DS_FACTOR_AUTO]):
+        assert np.abs(a - c).max() <= POS_TOL_MM
+    sc = scenes[0]
+    tpl, res = _oracle(sc, sc.frames[0], oracle_params(d.default_params(precision=2)))
+    assert np.abs(tpl.g + outs[d.DS_FACTOR_AUTO][0] - res.pos).max() <= POS_TOL_MM
+    # an auto handle solving alone tunes its batch of one at the first solve
+    s, st, q, t = gpu_frame(d, sc, sc.frames[0],
+                            d.default_params(precision=2, factor_tc=d.DS_FACTOR_AUTO))
+    assert np.abs(tpl.g + t - res.pos).max() <= POS_TOL_MM
     s.close()
