@@ -72,6 +72,11 @@ def job_throughput(world, units_per_rank, total_s):
     return world * units_per_rank / total_s
 
 
+def replica_seeds(rank, problems):
+    """Scene seeds of a rank: every replica solves its own sequences (seeds offset per rank)."""
+    return [p.seed + 100000 * rank for p in problems]
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -446,9 +451,8 @@ def run_gpu(args):
     K, W, F = args.steps, args.warmup, args.frames
     t_gen = time.perf_counter()
     # every replica solves its own sequences: the scene seeds are offset per rank
-    if rank:
-        for p in problems:
-            p.seed += 100000 * rank
+    for p, sd in zip(problems, replica_seeds(rank, problems)):
+        p.seed = sd
     scenes = make_scenes(problems, F, processes=max(1, min(16, _cores() - 2)))
     gen_s = time.perf_counter() - t_gen
     prec = PREC[args.precision]

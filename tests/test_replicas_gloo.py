@@ -19,7 +19,8 @@ def _rank(rank, world, port, times, q):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     import bench
     t = bench.max_over_ranks(times[rank], world, "cpu")
-    seeds = bench.replica_seeds(rank, 3)
+    from synth.workloads import mixed_problems
+    seeds = bench.replica_seeds(rank, mixed_problems(3))
     dist.barrier()
     dist.destroy_process_group()
     q.put((rank, t, seeds))
@@ -41,4 +42,4 @@ def test_two_replicas_take_the_slowest_rank_and_own_seeds():
     assert all(t == max(times) for _, t, _ in out)          # max over ranks
     assert set(out[0][2]).isdisjoint(out[1][2])             # each replica its own streams
     import bench
-    assert bench.job_throughput(world, 32 * 20, max(times)) == pytest.approx(2 * 640 / 2.5)
+    assert bench.job_throughput(world, 64 * 20, max(times)) == pytest.approx(2 * 1280 / 2.5)
