@@ -111,6 +111,13 @@ typedef struct {
                              * the usable ones), normal renormalised; valid iff the usable weight
                              * is >= 1/2. The Jacobian holds the blended point and normal fixed, as
                              * with the nearest pixel.                                            */
+  int32_t jtj;              /* Precision of the ICP term's J^T W J (Section 2, ICP paragraph):
+                             * 0 = FP32 on the SIMT pipes (default);
+                             * 1 = BF16 Jacobian rows on the tensor cores with FP32 accumulation
+                             * (warp-level mma, 16 points per product). The gradient J^T W r stays
+                             * FP32 in both, so the Gauss-Newton fixed point is the same; the step
+                             * of an iteration differs by the rounding of the Jacobian to BF16.
+                             * Handles of one batch must agree.                                   */
   int32_t ransac_o1;        /* o1 of Eq. 2 (the template side of each match) in the RANSAC:
                              * 0 = the template point at the matched pixel (default);
                              * 1 = warm start: that point warped by the handle's current warps

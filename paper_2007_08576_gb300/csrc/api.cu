@@ -477,7 +477,8 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
     const int ps = hs[i]->prm.precision == DS_PREC_FP32 ? 0 : hs[i]->prm.refine_steps;
     const int ft = hs[i]->prec_fp64 ? 0 : hs[i]->prm.factor_tc;
     if (hs[i]->prec_fp64 != fp64 || (hs[i]->prm.precision == DS_PREC_FP32) != (prec == DS_PREC_FP32) ||
-        ps != steps || ft != ftc || hs[i]->prm.solver != solver)
+        ps != steps || ft != ftc || hs[i]->prm.solver != solver ||
+        hs[i]->prm.jtj != hs[0]->prm.jtj)
       return DS_ERR_ARG;
   }
   ds_batch_s* b = new ds_batch_s();
@@ -534,6 +535,7 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   T.orb_ctas = 16;
   b->auto_factor = ftc == DS_FACTOR_AUTO;
   T.factor_tc = b->auto_factor ? 0 : ftc;
+  T.jtj = hs[0]->prm.jtj;
   T.max_tasks = max_tasks;
   T.max_nt = max_nt;
   T.words = b->d_words;
@@ -846,7 +848,7 @@ bool valid_params(const ds_params& p) {
          p.refine_steps <= 3 && p.w_orb >= 0 && p.w_angle >= 0 && p.w_rot >= 0 &&
          p.w_arap0 >= 0 && (p.factor_tc >= 0 && p.factor_tc <= DS_FACTOR_AUTO) &&
          (p.solver == 0 || p.solver == 1) && (p.assoc == 0 || p.assoc == 1) &&
-         (p.ransac_o1 == 0 || p.ransac_o1 == 1);
+         (p.ransac_o1 == 0 || p.ransac_o1 == 1) && (p.jtj == 0 || p.jtj == 1);
 }
 
 bool is_host_ptr(const void* p);
@@ -878,6 +880,7 @@ void ds_default_params(ds_params* p) {
   p->solver = 0;
   p->assoc = 0;
   p->ransac_o1 = 0;
+  p->jtj = 0;
 }
 
 const char* ds_status_str(int status) {
@@ -1219,6 +1222,7 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
     D.eps = h->prm.eps_damp;
     D.write_ref = (prec != DS_PREC_FP32 && h->prm.refine_steps > 0) ? 1 : 0;
     D.assoc = h->prm.assoc;
+    D.jtj = h->prm.jtj;
     D.tp = h->d_tp;
     D.tw = h->d_tw;
     D.seg = h->d_seg;

@@ -81,6 +81,7 @@ struct ProbDesc {
   double w_arap0, lam, eps;
   int write_ref;           // the refinement needs the FP32 system (full symmetric) besides the factor
   int assoc;               // ICP association: 0 nearest pixel, 1 bilinear blend of 4 pixels
+  int jtj;                 // ICP J^T W J: 0 FP32 SIMT, 1 BF16 on the tensor cores (FP32 accumulate)
   const float4* tp;        // sorted template points (x, y, z, bits(seg << 2 | nearest slot))
   const float4* tw;        // blend weights per sorted point (slot order)
   const int4* seg;         // node quadruple of each segment (ascending ids)
@@ -222,6 +223,7 @@ struct BatchTabs {
   int n_chol_b;
   int factor_tc;             // FP32 factorisation: 0 SIMT 64-tiles, 1 tensor cores 64-tiles,
                              // 2 tensor cores 128-blocks
+  int jtj;                   // ICP J^T W J on the tensor cores (BF16, FP32 accumulation)
   int max_tasks;             // max factorisation tasks over the problems
   int max_nt;                // max tile rows over the problems
   int* words;                // [0] factorisation head, [1..4] solve heads, [5] timeout word

@@ -292,6 +292,25 @@ __device__ __forceinline__ void slot_jac(const float* h, const NodeGPU& nd, floa
 // twelve gradient entries each. At the end of the segment each lane adds its 12 entries with
 // one atomic each; cost, weight and count go out with one atomic triple per warp. Warps never
 // wait for one another.
+// BF16 x BF16 -> FP32 warp-level tensor-core product D += A B (m16n8k16, A row-major 16 x 16,
+// B column-major 16 x 8, fragments as the PTX ISA lays them out for lane (g = lane / 4,
+// t = lane % 4)).
+__device__ __forceinline__ void mma_bf16_16x8x16(float (&d)[4], const unsigned (&a)[4],
+                                                 const unsigned (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+      "{%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+// two floats rounded to BF16 (nearest even) and packed, the first in the low half
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+  unsigned r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
+template <bool kTcJtj>
 __global__ __launch_bounds__(kTile, 2) void k_icp(const ProbDesc* const* __restrict__ descs,
                                                   const int2* __restrict__ tab) {
   const int2 wk = tab[blockIdx.x];
@@ -312,6 +331,8 @@ __global__ __launch_bounds__(kTile, 2) void k_icp(const ProbDesc* const* __restr
   double* __restrict__ acc = D.acc;
   __shared__ float sJ[kSegPerCta][32][25];
   __shared__ NodeGPU sNode[kSegPerCta][4];
+  // tensor-core path: each warp's running 24 x 24 segment sum (entries owned by fixed lanes)
+  __shared__ float sAcc[kTcJtj ? kSegPerCta : 1][kTcJtj ? 24 * 24 : 1];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool grad = lane >= 30;
   const int q = grad ? 0 : lane / 3;
@@ -321,6 +342,19 @@ __global__ __launch_bounds__(kTile, 2) void k_icp(const ProbDesc* const* __restr
   float(*rows)[25] = sJ[warp];
   NodeGPU* nd = sNode[warp];
   float cost = 0.f, wsum = 0.f, nval = 0.f;
+  const int mg = lane >> 2, mt4 = lane & 3;   // mma fragment coordinates (tensor-core path)
+  float* sacc = sAcc[kTcJtj ? warp : 0];
+  if (kTcJtj) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int row = 16 * i + mg + (e >= 2 ? 8 : 0), col = 8 * j + 2 * mt4 + (e & 1);
+          if (row < 24) sacc[row * 24 + col] = 0.f;
+        }
+  }
   for (int k = 0; k < kSegPerWarp; ++k) {
     const int sg = wk.y * kSegPerCta * kSegPerWarp + k * kSegPerCta + warp;
     if (sg >= D.S) break;
@@ -424,7 +458,58 @@ __global__ __launch_bounds__(kTile, 2) void k_icp(const ProbDesc* const* __restr
       rows[lane][24] = rt;
       __syncwarp();
       const int np = min(32, hi - c0);
-      if (!grad) {
+      if (kTcJtj) {
+        // this 32-point batch's 24 x 24 J^T W J in FP32 mma accumulators, 2 row tiles (rows
+        // 0..15, 16..31; rows >= 24 are zero) x 3 column tiles (columns 0..23), then added to the
+        // lane's own entries of the segment sum in shared memory (fixed fragment ownership, so no
+        // lane touches another's entries); rows of the points past the segment's end are zero,
+        // so whole 16-point steps are summed
+        float cm[2][3][4];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) cm[i][j][e] = 0.f;
+        for (int k0 = 0; k0 < np; k0 += 16) {
+          const float* r0 = rows[k0 + 2 * mt4];
+          const float* r1 = rows[k0 + 2 * mt4 + 1];
+          const float* r8 = rows[k0 + 2 * mt4 + 8];
+          const float* r9 = rows[k0 + 2 * mt4 + 9];
+          unsigned af[2][4];
+#pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            // A = J^T (row m = Jacobian column m, column k = point k0 + k)
+            const int m0 = 16 * i + mg, m1 = m0 + 8;
+            const bool v1 = m1 < 24;
+            af[i][0] = pack_bf16(r0[m0], r1[m0]);
+            af[i][1] = v1 ? pack_bf16(r0[m1], r1[m1]) : 0u;
+            af[i][2] = pack_bf16(r8[m0], r9[m0]);
+            af[i][3] = v1 ? pack_bf16(r8[m1], r9[m1]) : 0u;
+          }
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            // B = J (row k = point, column n = Jacobian column 8 j + n)
+            const int nn = 8 * j + mg;
+            const unsigned bf[2] = {pack_bf16(r0[nn], r1[nn]), pack_bf16(r8[nn], r9[nn])};
+#pragma unroll
+            for (int i = 0; i < 2; ++i) mma_bf16_16x8x16(cm[i][j], af[i], bf);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int row = 16 * i + mg + (e >= 2 ? 8 : 0), col = 8 * j + 2 * mt4 + (e & 1);
+              if (row < 24) sacc[row * 24 + col] += cm[i][j][e];
+            }
+        // the gradient J^T W r stays FP32: lane l < 24 sums entry l
+        if (lane < 24) {
+          for (int t = 0; t < np; ++t) a[0] += rows[t][lane] * rows[t][24];
+        }
+      } else if (!grad) {
 #pragma unroll 2
         for (int t = 0; t < np; ++t) {
           const float x0 = rows[t][ra], x1 = rows[t][ra + 1];
@@ -445,7 +530,32 @@ __global__ __launch_bounds__(kTile, 2) void k_icp(const ProbDesc* const* __restr
       }
       __syncwarp();
     }
-    if (!grad) {
+    if (kTcJtj) {
+      // the lane's entries of the segment sum: accumulator element (row, col) of tile (i, j) is
+      // row 16 i + g (+ 8 for e >= 2), column 8 j + 2 t (+ 1 for odd e); it belongs to slot-pair
+      // block (row / 6, col / 6) when that is a lower pair. Zeroed again for the next segment.
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int row = 16 * i + mg + (e >= 2 ? 8 : 0), col = 8 * j + 2 * mt4 + (e & 1);
+            const int si = row / 6, sj = col / 6;
+            if (row >= 24) continue;
+            const float v = sacc[row * 24 + col];
+            sacc[row * 24 + col] = 0.f;
+            if (si >= sj && v != 0.f)
+              atomicAdd(blk + (size_t)segbp[sg * 10 + si * (si + 1) / 2 + sj] * 36 +
+                            (row % 6) * 6 + col % 6,
+                        v);
+          }
+      if (lane < 24 && a[0] != 0.f) {
+        const int sl = lane / 6;
+        const int ndi = sl == 0 ? nn.x : sl == 1 ? nn.y : sl == 2 ? nn.z : nn.w;
+        atomicAdd(&gdata[6 * ndi + lane % 6], a[0]);
+      }
+    } else if (!grad) {
       float* dst = blk + (size_t)segbp[sg * 10 + q] * 36 + 12 * (lane % 3);
 #pragma unroll
       for (int e = 0; e < 12; ++e)
@@ -473,7 +583,10 @@ __global__ __launch_bounds__(kTile, 2) void k_icp(const ProbDesc* const* __restr
 
 void launch_icp(const BatchTabs& B, cudaStream_t s) {
   if (B.n_icp <= 0) return;
-  k_icp<<<B.n_icp, kTile, 0, s>>>(B.d, B.icp);
+  if (B.jtj)
+    k_icp<true><<<B.n_icp, kTile, 0, s>>>(B.d, B.icp);
+  else
+    k_icp<false><<<B.n_icp, kTile, 0, s>>>(B.d, B.icp);
   ++g_launches;
 }
 

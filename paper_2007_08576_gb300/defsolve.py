@@ -54,7 +54,7 @@ class DsParams(ctypes.Structure):
                 ("n_reweight", ctypes.c_int32), ("n_nearest", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("factor_tc", ctypes.c_int32),
-                ("solver", ctypes.c_int32), ("assoc", ctypes.c_int32),
+                ("solver", ctypes.c_int32), ("assoc", ctypes.c_int32), ("jtj", ctypes.c_int32),
                 ("ransac_o1", ctypes.c_int32)]
 
 
