@@ -205,6 +205,16 @@ int ds_batch_create(const ds_handle* hs, int32_t n, void* cuda_stream, ds_batch*
  * per handle (ds_get_*), and
  * ds_batch_status synchronises the batch and reports DS_ERR_TIMEOUT / DS_ERR_NOT_SPD. */
 int ds_batch_solve(ds_batch b, int32_t iters);
+/* As ds_batch_solve, on the handles p with active[p] != 0 only (active: n host bytes in the
+ * batch's handle order; at least one set; each active handle must have a submitted frame). The
+ * launches still cover the whole batch (the same captured graph is replayed for every mask);
+ * the left-out handles' work items return at once and nothing of theirs is read or written, so
+ * a long-lived batch serves any subset of its handles without new allocations or captures.
+ * Two batches listing the same handles may have solves in flight together only when their
+ * active sets are disjoint (a continuous-batching server keeps two such batches). A batch of
+ * DS_FACTOR_AUTO handles tunes on its first solve's active set. Errors as ds_batch_solve, and
+ * DS_ERR_ARG for a NULL or all-zero mask. */
+int ds_batch_solve_masked(ds_batch b, const uint8_t* active, int32_t iters);
 int ds_batch_status(ds_batch b);
 int ds_batch_destroy(ds_batch b);
 /* Phase tracing of a batch, as ds_set_tracing / ds_get_phase_times for a handle (summed over

@@ -646,10 +646,14 @@ void enqueue_solve(ds_batch_s* b, int iters) {
   trace(b, iters - 1, 3);
 }
 
-void update_desc_table(ds_batch_s* b) {
+// The batch's descriptor table for the next solve: each handle's latest frame slot, or a null
+// entry for a handle left out of the solve (active[p] == 0; active == NULL: every handle), which
+// every kernel of the solve skips.
+void update_desc_table(ds_batch_s* b, const uint8_t* active = nullptr) {
   bool changed = false;
   for (size_t p = 0; p < b->hs.size(); ++p) {
-    const ProbDesc* d = b->hs[p]->d_desc + b->hs[p]->fs;
+    const ProbDesc* d =
+        (active && !active[p]) ? nullptr : b->hs[p]->d_desc + b->hs[p]->fs;
     if (b->h_descs[p] != d) {
       b->h_descs[p] = d;
       changed = true;
@@ -665,11 +669,12 @@ void update_desc_table(ds_batch_s* b) {
   b->tab_pending[i] = true;
 }
 
-// Orders the batch stream after each handle's last solve (possibly in another batch) and its
-// pending work (submit_frame on its own stream).
-void order_after_handles(ds_batch_s* b) {
+// Orders the batch stream after each (active) handle's last solve (possibly in another batch) and
+// its pending work (submit_frame on its own stream).
+void order_after_handles(ds_batch_s* b, const uint8_t* active = nullptr) {
   cudaStream_t s = b->stream;
   for (size_t p = 0; p < b->hs.size(); ++p) {
+    if (active && !active[p]) continue;
     ds_ctx* h = b->hs[p];
     if (h->slot_pending[h->solved_fs]) cudaStreamWaitEvent(s, h->ev_slot_free[h->solved_fs], 0);
     if (h->stream != s) {
@@ -698,11 +703,11 @@ std::pair<int, int> tune_key(const ds_batch_s* b) {
 // and with 128 x 128 blocks) on synthetic SPD systems of the batch's sizes, written into the
 // factor buffers (the next solve assembles its own systems over them), and keeps the fastest.
 // Each candidate's time is the minimum over `reps` launches (CUDA events on the batch stream).
-int tune_factor(ds_batch_s* b, int reps) {
+int tune_factor(ds_batch_s* b, int reps, const uint8_t* active = nullptr) {
   cudaStream_t s = b->stream;
   BatchTabs& T = b->tabs;
-  order_after_handles(b);
-  update_desc_table(b);
+  order_after_handles(b, active);
+  update_desc_table(b, active);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     if (e0) cudaEventDestroy(e0);
@@ -738,7 +743,8 @@ int tune_factor(ds_batch_s* b, int reps) {
   cudaEventDestroy(e1);
   if (rc == DS_OK) rc = batch_words_status(b);
   // the synthetic systems are SPD; clear the pivot words anyway so that no tuning run reports
-  for (ds_ctx* h : b->hs) cudaMemsetAsync(h->d_acc + ACC_STATUS, 0, sizeof(double), s);
+  for (size_t p = 0; p < b->hs.size(); ++p)
+    if (!active || active[p]) cudaMemsetAsync(b->hs[p]->d_acc + ACC_STATUS, 0, sizeof(double), s);
   if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
     rc = DS_ERR_CUDA;
   T.factor_tc = best;
@@ -752,7 +758,7 @@ int tune_factor(ds_batch_s* b, int reps) {
   return rc;
 }
 
-int run_batch(ds_batch_s* b, int iters, bool use_graph) {
+int run_batch(ds_batch_s* b, int iters, bool use_graph, const uint8_t* active = nullptr) {
   cudaStream_t s = b->stream;
   if (b->auto_factor && !b->tuned) {
     const auto key = tune_key(b);
@@ -766,15 +772,15 @@ int run_batch(ds_batch_s* b, int iters, bool use_graph) {
       b->tabs.factor_tc = choice;
       b->tuned = true;
     } else {
-      const int rc = tune_factor(b, 2);
+      const int rc = tune_factor(b, 2, active);
       if (rc) return rc;
       std::lock_guard<std::mutex> lock(g_tune_mu);
       g_tune_cache[key] = b->tabs.factor_tc;
     }
   }
-  order_after_handles(b);
-  // the descriptor table points at each handle's latest frame slot
-  update_desc_table(b);
+  order_after_handles(b, active);
+  // the descriptor table points at each (active) handle's latest frame slot
+  update_desc_table(b, active);
   const int64_t before = g_launches;
   int64_t launched = 0;
   if (use_graph) {
@@ -825,7 +831,9 @@ int run_batch(ds_batch_s* b, int iters, bool use_graph) {
   // the slots this solve read are free again after it; the handles' later calls that touch
   // solve state wait for it (wait_solved), their next submissions only for their slot
   cudaEventRecord(b->ev_done, s);
-  for (ds_ctx* h : b->hs) {
+  for (size_t p = 0; p < b->hs.size(); ++p) {
+    if (active && !active[p]) continue;
+    ds_ctx* h = b->hs[p];
     cudaEventRecord(h->ev_slot_free[h->fs], s);
     h->slot_pending[h->fs] = true;
     h->solved_fs = h->fs;
@@ -1485,6 +1493,22 @@ int ds_batch_solve(ds_batch b, int32_t iters) {
   bool graph = !b->no_graph;
   for (ds_ctx* h : b->hs) graph = graph && h->prm.use_graph;
   return run_batch(b, iters, graph);
+}
+
+int ds_batch_solve_masked(ds_batch b, const uint8_t* active, int32_t iters) {
+  if (!b || !active || iters < 1 || iters > DS_MAX_ITERS) return DS_ERR_ARG;
+  if (b->error) return DS_ERR_CUDA;
+  if (b->stale) return DS_ERR_STATE;
+  int n_on = 0;
+  for (size_t p = 0; p < b->hs.size(); ++p) {
+    if (!active[p]) continue;
+    ++n_on;
+    if (!b->hs[p]->have_frame || b->hs[p]->N == 0) return DS_ERR_STATE;
+  }
+  if (n_on == 0) return DS_ERR_ARG;
+  bool graph = !b->no_graph;
+  for (ds_ctx* h : b->hs) graph = graph && h->prm.use_graph;
+  return run_batch(b, iters, graph, active);
 }
 
 int ds_batch_tune(ds_batch b, int32_t reps, int32_t* choice, double* ms3) {

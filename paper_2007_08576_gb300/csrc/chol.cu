@@ -447,6 +447,10 @@ __global__ __launch_bounds__(256, DS_CHOL_CTAS_PER_SM) void k_chol_dag(
     if (t >= nticket) break;
     // ticket -> (problem, task); each problem's tasks appear in their own order
     const int2 pt = tickets[t];
+    if (!descs[pt.x]) {   // not in this solve
+      __syncthreads();
+      continue;
+    }
     const LinProblem& P = descs[pt.x]->lp;
     const int4 tk = P.tasks[pt.y];
 #if defined(DS_TASK_TRACE)
@@ -785,6 +789,10 @@ __global__ __launch_bounds__(256, 1) void k_chol_tc(const ProbDesc* const* __res
     const int t = s_t;
     if (t >= nticket) break;
     const int2 pt = tickets[t];
+    if (!descs[pt.x]) {   // not in this solve
+      __syncthreads();
+      continue;
+    }
     const LinProblem& P = descs[pt.x]->lp;
     const int4 tk = P.tasks[pt.y];
 #if defined(DS_TASK_TRACE)
@@ -1246,6 +1254,10 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
     const int t = s_t;
     if (t >= nticket) break;
     const int2 pt = tickets[t];
+    if (!descs[pt.x]) {   // not in this solve
+      __syncthreads();
+      continue;
+    }
     const LinProblem& P = descs[pt.x]->lp;
     const int4 tk = P.tasks_b[pt.y];
     const bool diag = tk.y == 0;
@@ -1533,6 +1545,7 @@ template size_t chol_packed_elems<double>(int);
 // Synthetic SPD system of every problem's size, for timing the factorisation kernels (FP32
 // precisions): A_ii = n, A_ij = 1 / (2 (1 + |i - j|)^2) below the diagonal (diagonally dominant).
 __global__ void k_fill_spd(const ProbDesc* const* __restrict__ descs) {
+  if (!descs[blockIdx.y]) return;
   const LinProblem& P = descs[blockIdx.y]->lp;
   const int n = P.n;
   float* A = (float*)P.A;

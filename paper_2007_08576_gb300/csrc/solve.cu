@@ -117,6 +117,10 @@ __global__ __launch_bounds__(256) void k_trsv_dag(const ProbDesc* const* __restr
     __syncthreads();
     const int t = s_t;
     if (t >= nticket) return;
+    if (!descs[t % np]) {   // not in this solve
+      __syncthreads();
+      continue;
+    }
     const ProbDesc& PD = *descs[t % np];
     const LinProblem& P = PD.lp;
     const int2 tk = make_int2(t % np, t / np);
@@ -248,6 +252,7 @@ __device__ __forceinline__ void df_add_term(float a, float2 x, float& sh, float&
 __global__ __launch_bounds__(256) void k_residual64(const ProbDesc* const* __restrict__ descs,
                                                     const int2* __restrict__ tab) {
   const int2 w = tab[blockIdx.x];
+  if (!descs[w.x]) return;   // not in this solve
   const ProbDesc& D = *descs[w.x];
   const int n = D.n;
   const int row = w.y * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;

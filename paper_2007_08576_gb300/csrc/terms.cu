@@ -142,6 +142,7 @@ __device__ void node_update(const ProbDesc& D, int i, bool step) {
 __global__ void k_iter_end(const ProbDesc* const* __restrict__ descs, const int2* __restrict__ tab,
                            int it, int step) {
   const int2 w = tab[blockIdx.x];
+  if (!descs[w.x]) return;   // not in this solve
   const ProbDesc& D = *descs[w.x];
   if (w.y == 0 && threadIdx.x == 0) {
     double* acc = D.acc;
@@ -169,6 +170,8 @@ void launch_iter_end(const BatchTabs& B, int it, bool step, cudaStream_t s) {
 // Zeroes the data-term blocks / gradient and the factorisation / solve counters of every
 // problem, and the batch's ticket heads (not its timeout word).
 __global__ void k_iter_begin(const ProbDesc* const* __restrict__ descs, int* __restrict__ words) {
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < 5) words[threadIdx.x] = 0;
+  if (!descs[blockIdx.x]) return;   // not in this solve
   const ProbDesc& D = *descs[blockIdx.x];
   const int nth = blockDim.x * gridDim.y;
   const int t0 = blockIdx.y * blockDim.x + threadIdx.x;
@@ -180,7 +183,6 @@ __global__ void k_iter_begin(const ProbDesc* const* __restrict__ descs, int* __r
   const int nc = nt + 2 * nt * nt;
   for (int e = t0; e < nc; e += nth) D.lp.cnt[e] = 0;
   for (int e = t0; e < 2 * nt; e += nth) D.lp.flags[e] = 0;
-  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < 5) words[threadIdx.x] = 0;
 }
 
 void launch_iter_begin(const BatchTabs& B, cudaStream_t s) {
@@ -314,6 +316,7 @@ template <bool kTcJtj>
 __global__ __launch_bounds__(kTile, 2) void k_icp(const ProbDesc* const* __restrict__ descs,
                                                   const int2* __restrict__ tab) {
   const int2 wk = tab[blockIdx.x];
+  if (!descs[wk.x]) return;   // not in this solve
   const ProbDesc& D = *descs[wk.x];
   const float4* __restrict__ tp = D.tp;
   const float4* __restrict__ tw = D.tw;
@@ -594,6 +597,7 @@ void launch_icp(const BatchTabs& B, cudaStream_t s) {
 
 __global__ __launch_bounds__(128) void k_orb(const ProbDesc* const* __restrict__ descs,
                                              int ctas_per_problem) {
+  if (!descs[blockIdx.x / ctas_per_problem]) return;   // not in this solve
   const ProbDesc& D = *descs[blockIdx.x / ctas_per_problem];
   const int* __restrict__ midx = D.midx;
   const float* __restrict__ mxyz = D.mxyz;
@@ -810,6 +814,7 @@ __global__ __launch_bounds__(256) void k_arap_assemble(const ProbDesc* const* __
                                                        int first_iter, int lin_only,
                                                        int diag_only, int deferred) {
   const int2 wk = tab[blockIdx.x];
+  if (!descs[wk.x]) return;   // not in this solve
   const ProbDesc& D = *descs[wk.x];
   const PairNode* __restrict__ pn = D.pn;
   const int N = D.N;
@@ -1049,6 +1054,7 @@ template <typename T>
 __global__ __launch_bounds__(64) void k_arap_finalize(const ProbDesc* const* __restrict__ descs,
                                                       const int2* __restrict__ tab) {
   const int2 w = tab[blockIdx.x];
+  if (!descs[w.x]) return;   // not in this solve
   const ProbDesc& D = *descs[w.x];
   const int i = w.y, n = D.n;
   T* Afac = (T*)D.lp.A;
@@ -1100,6 +1106,7 @@ template <typename T>
 __global__ void k_block_jacobi(const ProbDesc* const* __restrict__ descs,
                                const int2* __restrict__ tab) {
   const int2 w = tab[blockIdx.x];
+  if (!descs[w.x]) return;   // not in this solve
   const ProbDesc& D = *descs[w.x];
   const int i = w.y * 128 + threadIdx.x;
   if (i >= D.N) return;

@@ -25,7 +25,8 @@ DS_FACTOR_AUTO = 3
 # every exported symbol of include/defsolve.h and include/defsolve_orb.h
 EXPORTS = [
     "ds_default_params", "ds_create_template", "ds_set_control_points", "ds_submit_frame",
-    "ds_solve", "ds_solve_batch", "ds_batch_create", "ds_batch_solve", "ds_batch_status",
+    "ds_solve", "ds_solve_batch", "ds_batch_create", "ds_batch_solve", "ds_batch_solve_masked",
+    "ds_batch_status",
     "ds_batch_destroy", "ds_batch_set_tracing", "ds_batch_phase_times", "ds_batch_set_graph",
     "ds_batch_tune", "ds_batch_factor_kernel", "ds_get_deformation", "ds_get_deformation64",
     "ds_set_deformation", "ds_get_inlier_mask", "ds_get_ransac", "ds_get_cost",
@@ -101,6 +102,7 @@ def lib(path: str | None = None):
         "ds_solve_batch": (i32, [ctypes.POINTER(vp), i32, i32]),
         "ds_batch_create": (i32, [ctypes.POINTER(vp), i32, vp, ctypes.POINTER(vp)]),
         "ds_batch_solve": (i32, [vp, i32]),
+        "ds_batch_solve_masked": (i32, [vp, vp, i32]),
         "ds_batch_status": (i32, [vp]),
         "ds_batch_destroy": (i32, [vp]),
         "ds_batch_set_tracing": (i32, [vp, i32]),
@@ -233,6 +235,12 @@ def ds_batch_create(handles, stream=None):
 
 def ds_batch_solve(b, iters):
     _check("ds_batch_solve", lib().ds_batch_solve(b, int(iters)))
+
+
+def ds_batch_solve_masked(b, active, iters):
+    """Solves the handles with active[p] != 0 (a length-n sequence of 0 / 1 in batch order)."""
+    m = np.ascontiguousarray(np.asarray(active, dtype=np.uint8))
+    _check("ds_batch_solve_masked", lib().ds_batch_solve_masked(b, m.ctypes.data, int(iters)))
 
 
 def ds_batch_status(b):

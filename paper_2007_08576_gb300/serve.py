@@ -14,8 +14,9 @@ arrive asynchronously; every scheduler round (``poll``)
 
 Several batches are in flight at once on their own CUDA streams (their stream sets are
 disjoint), so frames arriving while others are on the GPU are admitted into the next batch and
-their work overlaps on the device. Batch objects (and their captured graphs) are cached per
-stream composition.
+their work overlaps on the device. The GPU engine keeps two long-lived batch objects over every
+admitted stream and solves each launch's streams as a masked solve, so a launch allocates and
+captures nothing.
 
 The engine is pluggable: ``GpuEngine`` drives libdefsolve; tests use a fake engine to check the
 host logic without a GPU.
@@ -88,19 +89,24 @@ def stream_bytes(W: int, H: int, N: int, M: int, precision: int) -> int:
 
 
 class GpuEngine:
-    """libdefsolve behind the server: one handle per stream, one batch object per composition."""
+    """libdefsolve behind the server: one handle per admitted stream, and two long-lived batches
+    over all admitted handles (one per batch in flight). A launch solves the ready streams as a
+    masked solve of a free batch (ds_batch_solve_masked): the same captured graph serves every
+    subset, so launching allocates and captures nothing. The batches are rebuilt when the
+    admitted set changes."""
 
-    def __init__(self, params=None, use_graph=True, cache=32):
+    def __init__(self, params=None, use_graph=True, n_batches=2):
         import torch
         from . import build, defsolve
         build.build()
         self.d = defsolve
         self.torch = torch
         self.params = params if params is not None else defsolve.default_params(precision=2)
-        self.params.use_graph = 1
-        self.use_graph = bool(use_graph)
-        self.cache = collections.OrderedDict()
-        self.cache_cap = cache
+        self.params.use_graph = 1 if use_graph else 0
+        self.n_batches = n_batches
+        self.handles = []          # admitted solvers, in batch order
+        self.batches = []          # [batch, stream, in-flight token or None]
+        self.dirty = True
         # per stream: pinned host staging of its frames (a copy from pageable memory would make
         # the host wait for the stream's earlier work)
         self.staging = {}
@@ -109,20 +115,27 @@ class GpuEngine:
     def precision(self):
         return int(self.params.precision)
 
+    def _drop_batches(self):
+        for b, _, _ in self.batches:
+            self.d.ds_batch_destroy(b)    # waits for the batch's stream
+        self.batches = []
+        self.dirty = True
+
     def create(self, spec: StreamSpec):
         s = self.d.Solver(spec.template_depth, spec.K, spec.nodes, self.params)
         H, W = spec.template_depth.shape
         M = spec.max_matches
-        pin = lambda shape, dt: self.torch.empty(shape, dtype=dt, pin_memory=True).numpy()
         t = self.torch
+        pin = lambda shape, dt: t.empty(shape, dtype=dt, pin_memory=True).numpy()
         self.staging[id(s)] = (pin((H, W), t.float32), pin((M,), t.int32), pin((M, 3), t.float32),
                                pin((int(self.params.n_hyp),), t.int32))
+        self._drop_batches()
+        self.handles.append(s)
         return s
 
     def destroy(self, s):
-        for key in [k for k in self.cache if id(s) in k]:
-            b, _, _ = self.cache.pop(key)
-            self.d.ds_batch_destroy(b)
+        self._drop_batches()
+        self.handles = [h for h in self.handles if h is not s]
         self.staging.pop(id(s), None)
         s.close()
 
@@ -139,27 +152,29 @@ class GpuEngine:
         s.submit(dep, mi[:M], mx[:M], hy[:len(f.hyp)])
 
     def launch(self, solvers, iters):
-        key = tuple(sorted(id(s) for s in solvers))
-        if key in self.cache:
-            b, stream, ev = self.cache.pop(key)
-            # a composition seen again: capture its loop into a graph (replayed from now on)
-            self.d.ds_batch_set_graph(b, self.use_graph)
-        else:
-            stream = self.torch.cuda.Stream()
-            b = self.d.ds_batch_create([s.h for s in solvers], stream.cuda_stream)
-            self.d.ds_batch_set_graph(b, False)   # first use: direct launches, no capture cost
-            ev = None
-            while len(self.cache) >= self.cache_cap:
-                _, (ob, _, _) = self.cache.popitem(last=False)
-                self.d.ds_batch_destroy(ob)
-        self.d.ds_batch_solve(b, iters)
+        if self.dirty:
+            for _ in range(self.n_batches):
+                stream = self.torch.cuda.Stream()
+                b = self.d.ds_batch_create([h.h for h in self.handles], stream.cuda_stream)
+                self.batches.append([b, stream, None])
+            self.dirty = False
+        slot = next(x for x in self.batches if x[2] is None)
+        on = {id(h) for h in solvers}
+        mask = [1 if id(h) in on else 0 for h in self.handles]
+        self.d.ds_batch_solve_masked(slot[0], mask, iters)
         ev = self.torch.cuda.Event()
-        ev.record(stream)
-        self.cache[key] = (b, stream, ev)
-        return (key, ev)
+        ev.record(slot[1])
+        token = (slot, ev)
+        slot[2] = token
+        return token
 
     def done(self, token) -> bool:
-        return token[1].query()
+        slot, ev = token
+        if ev.query():
+            if slot[2] is token:
+                slot[2] = None
+            return True
+        return False
 
     def read(self, s):
         q, t, p = s.deformation()

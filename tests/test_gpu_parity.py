@@ -809,3 +809,55 @@ def test_factor_tuner_picks_the_fastest_and_auto_batches_stay_at_parity(d, tiny,
                             d.default_params(precision=2, factor_tc=d.DS_FACTOR_AUTO))
     assert np.abs(tpl.g + t - res.pos).max() <= POS_TOL_MM
     s.close()
+
+
+def test_masked_batch_solves_only_the_active_handles(d, tiny, mid):
+    """ds_batch_solve_masked: the active handles get the same result as solved alone, a handle
+    left out keeps its state untouched (even with a newer frame submitted), and the same batch
+    (and captured graph) then serves the complementary mask; two batches over the same handles
+    run disjoint masks in flight at once."""
+    from synth.scene import Config
+    cfg3 = Config("seq_120x90_n40", 120, 90, 40, 300, 8, 0.4, 0.5, 0.1, 8.0, 1.0, 0.3, 0.5, 1)
+    scenes = [tiny, mid, scene(cfg3, 99)]
+    p = d.default_params(precision=2)
+    alone = []
+    for sc in scenes:
+        s, st, q, t = gpu_frame(d, sc, sc.frames[0], p)
+        alone.append(t)
+        s.close()
+    solvers = []
+    for sc in scenes:
+        s = d.Solver(sc.template_depth, sc.K, sc.nodes, p)
+        fr = sc.frames[0]
+        s.submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+        solvers.append(s)
+    b = d.ds_batch_create([s.h for s in solvers])
+    d.ds_batch_solve_masked(b, [1, 0, 1], 10)
+    d.ds_batch_status(b)
+    assert np.abs(solvers[0].deformation64()[1] - alone[0]).max() <= 1e-4
+    assert np.abs(solvers[2].deformation64()[1] - alone[2]).max() <= 1e-4
+    assert np.abs(solvers[1].deformation64()[1]).max() == 0.0      # untouched: identity
+    d.ds_batch_solve_masked(b, [0, 1, 0], 10)
+    d.ds_batch_status(b)
+    assert np.abs(solvers[1].deformation64()[1] - alone[1]).max() <= 1e-4
+    with pytest.raises(d.DsError) as e:
+        d.ds_batch_solve_masked(b, [0, 0, 0], 10)
+    assert e.value.status == d.DS_ERR_ARG
+    # two batches over the same handles, disjoint masks in flight together (fresh states)
+    b2 = d.ds_batch_create([s.h for s in solvers])
+    for s, sc in zip(solvers, scenes):
+        N = len(sc.nodes)
+        d.ds_set_deformation(s.h, np.tile(np.float32([1, 0, 0, 0]), (N, 1)),
+                             np.zeros((N, 3), np.float32))
+        fr = sc.frames[0]
+        s.submit(fr.depth, fr.match_idx, fr.match_xyz, fr.hyp)
+    d.ds_batch_solve_masked(b, [1, 1, 0], 10)
+    d.ds_batch_solve_masked(b2, [0, 0, 1], 10)
+    d.ds_batch_status(b)
+    d.ds_batch_status(b2)
+    for s, t in zip(solvers, alone):
+        assert np.abs(s.deformation64()[1] - t).max() <= 1e-4
+    d.ds_batch_destroy(b)
+    d.ds_batch_destroy(b2)
+    for s in solvers:
+        s.close()
