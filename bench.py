@@ -45,8 +45,9 @@ WORKLOAD = "batched_mixed_64"
 ITERS = 10
 METRIC = "frames/s and p50/p99 frame latency vs plain GPU solve, at ≤1e-3 mm error"
 PREC = {"fp64": 0, "fp32": 1, "fp32_refine": 2}
-FACTOR = {"simt": 0, "tc64": 1, "tc128": 2, "auto": 3}   # ds_params.factor_tc
-FACTOR_NAMES = ["simt", "tc64", "tc128"]
+FACTOR = {"simt": 0, "tc64": 1, "tc128": 2, "tc128s": 3, "auto": -1}   # ds_params.factor_tc
+FACTOR_NAMES = ["simt", "tc64", "tc128", "tc128s"]     # by the tuner's kernel index
+KERNEL_NAMES = ["simt64", "tc64", "tc128_stage64k", "tc128_stage32k"]
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate per GPU (nominal)
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the dominant kernel
@@ -472,8 +473,8 @@ def run_gpu(args):
         if args.factor == "auto":
             choice, tms = d.ds_batch_tune(run.batch, 3)
             factor = FACTOR_NAMES[choice]
-            tuner = {"chosen": factor, "ms_per_factorisation": {
-                FACTOR_NAMES[k]: round(float(tms[k]), 3) for k in range(3)},
+            tuner = {"chosen": KERNEL_NAMES[choice], "ms_per_factorisation": {
+                KERNEL_NAMES[k]: round(float(tms[k]), 3) for k in range(4)},
                 "how": "each kernel on synthetic SPD systems of the batch's 64 sizes, best of 3 "
                        "launches (CUDA events); cached by batch shape"}
     else:
@@ -673,13 +674,13 @@ def run_gpu(args):
         kernel = "linearisation (k_icp + k_orb + k_arap_assemble diagonal blocks)"
     elif prec == 0:
         peak, peak_src = FP64_NOMINAL_TFLOPS, "nominal GB300 FP64 rate"
-    elif factor in ("tc64", "tc128"):
+    elif factor in ("tc64", "tc128", "tc128s"):
         bound = "tensor"
         achieved *= 3.0
         peak, peak_src = (_measured_bf16() * 1.1 / 2.25,
                           "MEASURED_PEAKS.json bf16_tflops x nominal tf32/bf16 (of measured)")
         kernel = ("k_chol_tcb (persistent 128 x 128 block Cholesky on tcgen05, all problems)"
-                  if factor == "tc128" else
+                  if factor in ("tc128", "tc128s") else
                   "k_chol_tc (persistent 64 x 64 tile Cholesky on tcgen05, all problems)")
     else:
         peak, peak_src = FP32_SIMT_TFLOPS, "152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)"
@@ -739,7 +740,8 @@ def run_gpu(args):
                        "ransac_o1": args.ransac_o1,
                        "factor": {"simt": "FP32 SIMT 64 x 64 tiles",
                                   "tc64": "tensor cores (tcgen05, 3xTF32), 64 x 64 tiles",
-                                  "tc128": "tensor cores (tcgen05, 3xTF32), 128 x 128 blocks",
+                                  "tc128": "tensor cores (tcgen05, 3xTF32), 128 x 128 blocks, 64 KB stages",
+                                  "tc128s": "tensor cores (tcgen05, 3xTF32), 128 x 128 blocks, 32 KB stages",
                                   "fp64": "FP64 SIMT 32 x 32 tiles",
                                   "none": "per-node 6 x 6 solves"}[factor],
                        "factor_tuner": tuner,
@@ -875,8 +877,8 @@ def main():
                     help="dense 6N x 6N Cholesky, or per-node 6 x 6 solves (Section 2)")
     ap.add_argument("--factor", default="auto", choices=list(FACTOR),
                     help="FP32 factorisation kernel: SIMT 64 x 64 tiles, tensor cores (tcgen05, "
-                         "3xTF32) with 64 x 64 tiles or 128 x 128 blocks, or picked by the "
-                         "library's tuner on the batch's sizes (auto)")
+                         "3xTF32) with 64 x 64 tiles or 128 x 128 blocks (64 KB or 32 KB operand "
+                         "stages), or picked by the library's tuner on the batch's sizes (auto)")
     ap.add_argument("--assoc", default="nearest", choices=["nearest", "bilinear"],
                     help="ICP association: nearest pixel or bilinear blend of 4 pixels")
     ap.add_argument("--ransac-o1", default="template", choices=["template", "warm"],

@@ -78,7 +78,7 @@ struct ds_batch_s {
   // factor kernel chosen by timing (DS_FACTOR_AUTO handles): tuned once, before the first solve
   bool auto_factor = false;
   bool tuned = false;
-  double tune_ms[3] = {-1.0, -1.0, -1.0};
+  double tune_ms[4] = {-1.0, -1.0, -1.0, -1.0};
 };
 
 struct ds_ctx {
@@ -293,6 +293,19 @@ void wait_solved(ds_ctx* h) {
 
 void destroy_batch(ds_batch_s* b);
 
+// The factor kernels the tuner chooses from, by kernel index: SIMT 64 x 64 tiles, tensor cores
+// with 64 x 64 tiles, tensor cores with 128 x 128 blocks in three 64 KB stages, and in six
+// 32 KB stages.
+constexpr int kFactorKernels = 4;
+void set_factor_kernel(BatchTabs& T, int k) {
+  static const int ftc[kFactorKernels] = {0, 1, 2, 2}, g[kFactorKernels] = {2, 2, 2, 1};
+  T.factor_tc = ftc[k];
+  T.tcb_g = g[k];
+}
+int factor_kernel_of(const BatchTabs& T) {
+  return T.factor_tc < 2 ? T.factor_tc : (T.tcb_g == 2 ? 2 : 3);
+}
+
 // The handle's batches stop running: its control points change or (leaving) it goes away, and
 // then no batch keeps a pointer to it.
 void invalidate_batches(ds_ctx* h, bool leaving) {
@@ -471,7 +484,7 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   const bool fp64 = hs[0]->prec_fp64;
   const int prec = hs[0]->prm.precision;
   const int steps = prec == DS_PREC_FP32 ? 0 : hs[0]->prm.refine_steps;
-  const int ftc = fp64 ? 0 : hs[0]->prm.factor_tc;   // DS_FACTOR_AUTO (3): tuned per batch
+  const int ftc = fp64 ? 0 : hs[0]->prm.factor_tc;   // DS_FACTOR_AUTO: tuned per batch
   const int solver = hs[0]->prm.solver;
   for (int i = 1; i < n; ++i) {
     const int ps = hs[i]->prm.precision == DS_PREC_FP32 ? 0 : hs[i]->prm.refine_steps;
@@ -534,7 +547,7 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   T.chol_b = b->d_tab + off; T.n_chol_b = (int)chol_b.size(); off += chol_b.size();
   T.orb_ctas = 16;
   b->auto_factor = ftc == DS_FACTOR_AUTO;
-  T.factor_tc = b->auto_factor ? 0 : ftc;
+  set_factor_kernel(T, b->auto_factor ? 0 : ftc);
   T.jtj = hs[0]->prm.jtj;
   T.max_tasks = max_tasks;
   T.max_nt = max_nt;
@@ -689,6 +702,7 @@ void order_after_handles(ds_batch_s* b, const uint8_t* active = nullptr) {
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, int> g_tune_cache;
 
+
 std::pair<int, int> tune_key(const ds_batch_s* b) {
   int mx = 1;
   double f = 0.0;
@@ -716,8 +730,8 @@ int tune_factor(ds_batch_s* b, int reps, const uint8_t* active = nullptr) {
   int best = 0;
   double best_ms = INFINITY;
   int rc = DS_OK;
-  for (int c = 0; c < 3 && rc == DS_OK; ++c) {
-    T.factor_tc = c;
+  for (int c = 0; c < kFactorKernels && rc == DS_OK; ++c) {
+    set_factor_kernel(T, c);
     float mn = INFINITY;
     for (int r = 0; r < reps; ++r) {
       launch_fill_spd(T, s);
@@ -747,7 +761,7 @@ int tune_factor(ds_batch_s* b, int reps, const uint8_t* active = nullptr) {
     if (!active || active[p]) cudaMemsetAsync(b->hs[p]->d_acc + ACC_STATUS, 0, sizeof(double), s);
   if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
     rc = DS_ERR_CUDA;
-  T.factor_tc = best;
+  set_factor_kernel(T, best);
   b->tuned = rc == DS_OK;
   if (b->gexec) {   // a captured loop holds the previous kernel choice
     cudaGraphExecDestroy(b->gexec);
@@ -769,13 +783,13 @@ int run_batch(ds_batch_s* b, int iters, bool use_graph, const uint8_t* active = 
       if (it != g_tune_cache.end()) choice = it->second;
     }
     if (choice >= 0) {
-      b->tabs.factor_tc = choice;
+      set_factor_kernel(b->tabs, choice);
       b->tuned = true;
     } else {
       const int rc = tune_factor(b, 2, active);
       if (rc) return rc;
       std::lock_guard<std::mutex> lock(g_tune_mu);
-      g_tune_cache[key] = b->tabs.factor_tc;
+      g_tune_cache[key] = factor_kernel_of(b->tabs);
     }
   }
   order_after_handles(b, active);
@@ -854,7 +868,7 @@ bool valid_params(const ds_params& p) {
          p.eps_damp >= 0 && p.keep_frac >= 0 && p.keep_frac <= 1 && p.sigma_blend_scale > 0 &&
          p.sigma_arap_scale > 0 && p.precision >= 0 && p.precision <= 2 && p.refine_steps >= 0 &&
          p.refine_steps <= 3 && p.w_orb >= 0 && p.w_angle >= 0 && p.w_rot >= 0 &&
-         p.w_arap0 >= 0 && (p.factor_tc >= 0 && p.factor_tc <= DS_FACTOR_AUTO) &&
+         p.w_arap0 >= 0 && (p.factor_tc >= DS_FACTOR_AUTO && p.factor_tc <= 3) &&
          (p.solver == 0 || p.solver == 1) && (p.assoc == 0 || p.assoc == 1) &&
          (p.ransac_o1 == 0 || p.ransac_o1 == 1) && (p.jtj == 0 || p.jtj == 1);
 }
@@ -1511,32 +1525,33 @@ int ds_batch_solve_masked(ds_batch b, const uint8_t* active, int32_t iters) {
   return run_batch(b, iters, graph, active);
 }
 
-int ds_batch_tune(ds_batch b, int32_t reps, int32_t* choice, double* ms3) {
+int ds_batch_tune(ds_batch b, int32_t reps, int32_t* choice, double* ms4) {
   if (!b || reps < 1 || reps > 100) return DS_ERR_ARG;
   if (b->error) return DS_ERR_CUDA;
   if (b->stale) return DS_ERR_STATE;
   if (b->fp64 || b->block_jacobi) {
     if (choice) *choice = -1;   // one kernel only: nothing to choose
-    if (ms3) ms3[0] = ms3[1] = ms3[2] = -1.0;
+    if (ms4)
+      for (int c = 0; c < kFactorKernels; ++c) ms4[c] = -1.0;
     return DS_OK;
   }
   const int rc = tune_factor(b, reps);
   if (rc) return rc;
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune_cache[tune_key(b)] = b->tabs.factor_tc;
+    g_tune_cache[tune_key(b)] = factor_kernel_of(b->tabs);
   }
-  if (choice) *choice = b->tabs.factor_tc;
-  if (ms3)
-    for (int c = 0; c < 3; ++c) ms3[c] = b->tune_ms[c];
+  if (choice) *choice = factor_kernel_of(b->tabs);
+  if (ms4)
+    for (int c = 0; c < kFactorKernels; ++c) ms4[c] = b->tune_ms[c];
   return DS_OK;
 }
 
-int ds_batch_factor_kernel(ds_batch b, int32_t* choice, double* ms3) {
+int ds_batch_factor_kernel(ds_batch b, int32_t* choice, double* ms4) {
   if (!b || !choice) return DS_ERR_ARG;
-  *choice = (b->fp64 || b->block_jacobi) ? -1 : b->tabs.factor_tc;
-  if (ms3)
-    for (int c = 0; c < 3; ++c) ms3[c] = b->tune_ms[c];
+  *choice = (b->fp64 || b->block_jacobi) ? -1 : factor_kernel_of(b->tabs);
+  if (ms4)
+    for (int c = 0; c < kFactorKernels; ++c) ms4[c] = b->tune_ms[c];
   return DS_OK;
 }
 

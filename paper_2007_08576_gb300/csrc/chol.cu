@@ -1045,45 +1045,48 @@ __global__ __launch_bounds__(256, 1) void k_chol_tc(const ProbDesc* const* __res
 // x, so each product is accurate to about 2^-21 relative: FP32 level for the refinement steps).
 // The 128 x 128 accumulator lives in tensor memory (128 lanes x 128 columns).
 //
-// Packed block slots (one per finished block (I, J), J <= I): 128 rows x 128 K values as four
-// K-chunks of 32; chunk q holds the TF32 hi part (4096 floats) then the lo part (4096 floats), each
-// in the canonical K-major layout without swizzle: core matrices of 8 rows x 4 floats (128 B),
-// element (r, m) of the chunk at ((r / 8) * 8 + m / 4) * 32 + (r % 8) * 4 + m % 4, i.e. 128 B
-// between core matrices along K and 1024 B between 8-row groups. Slot (I, J), I > J, holds L_IJ
-// (row r, K index = column); slot (J, J) holds X_JJ (row c, K index m), the B operand of C X^T.
+// Packed block slots (one per finished block (I, J), J <= I): 128 rows x 128 K values as eight
+// K sub-chunks of 16; sub-chunk q holds the TF32 hi part (2048 floats) then the lo part (2048
+// floats), each in the canonical K-major layout without swizzle: core matrices of 8 rows x 4
+// floats (128 B), element (r, m) of the sub-chunk at ((r / 8) * 4 + m / 4) * 32 + (r % 8) * 4 +
+// m % 4, i.e. 128 B between core matrices along K and 512 B between 8-row groups. Slot (I, J),
+// I > J, holds L_IJ (row r, K index = column); slot (J, J) holds X_JJ (row c, K index m), the B
+// operand of C X^T.
 //
-// Thread 0 streams the operand chunks of a product into three 64 KB shared-memory stages with
-// bulk copies (an A chunk and a B chunk of 32 KB each), issues the 12 MMAs of a chunk as soon as
-// its copies land and refills the stage of the previous chunk once that chunk's MMAs have
-// completed (tcgen05.commit on the stage's mbarrier), so the tensor pipe always has the next
-// chunk queued. The diagonal block is factored on the SIMT pipes from the accumulator in 64 x 64
-// halves (potrf_regs), with its 128 x 128 inverse by X10 = -X11 (L10 X00). An off-diagonal
-// block's C = A_IJ - acc is written to its own slot (hi / lo) and streamed back as the A operand
-// of C X_JJ^T, which goes through the same stages. The finished blocks are written to A
+// Thread 0 streams the operand sub-chunks of a product through 192 KB of shared memory in
+// stages of G sub-chunks of A and G of B (G = 2: three 64 KB stages; G = 1: six 32 KB stages;
+// the tuner times both), issues a stage's 6 G MMAs as soon as its bulk copies land and refills
+// the stage of the previous one once that stage's MMAs have completed (tcgen05.commit on the
+// stage's mbarrier), so the tensor pipe always has the next stage queued. The diagonal block is
+// factored on the SIMT pipes from the accumulator in 64 x 64 halves (potrf_regs), with its
+// 128 x 128 inverse by X10 = -X11 (L10 X00). An off-diagonal block's C = A_IJ - acc is split
+// into hi / lo parts in shared memory (128 KB, the A operand of C X_JJ^T) while X_JJ streams
+// through the remaining 64 KB in four 16 KB stages. The finished blocks are written to A
 // (row-major, for the triangular solves) and to the packed slots; the diagonal 64 x 64 inverses
 // go to Dinv for the solves.
 namespace tcb {
 
 constexpr int BS = 128;                   // block size
-constexpr int KC = 32;                    // K per chunk
-constexpr int kChunk = BS * KC;           // floats of one part (hi or lo) of a chunk
-constexpr int kSlot = 2 * BS * BS;        // floats per slot (4 chunks of hi + lo)
-constexpr unsigned kPairBytes = 2u * kChunk * 4u;   // 32 KB: hi + lo of one chunk
-constexpr int kStages = 3;
-constexpr unsigned kStageBytes = 2u * kPairBytes;   // A chunk + B chunk
-constexpr unsigned kSmem = kStages * kStageBytes;   // 192 KB
+constexpr int KS = 16;                    // K per sub-chunk
+constexpr int kPart = BS * KS;            // floats of one part (hi or lo) of a sub-chunk
+constexpr int kSub = 2 * kPart;           // floats of a sub-chunk (hi + lo)
+constexpr int kSlot = (BS / KS) * kSub;   // floats per slot (8 sub-chunks)
+constexpr unsigned kSubBytes = kSub * 4u;            // 16 KB
+constexpr unsigned kSmem = 192u * 1024u;             // stage area
+constexpr unsigned kCBytes = (BS / KS) * kSubBytes;  // 128 KB: the C operand of the OFF product
+constexpr int kXStages = 4;                          // 16 KB stages of X after the C operand
 // kind::tf32, D = F32, A = B = TF32, both K-major, N = 128, M = 128
 constexpr unsigned kIdesc =
     (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
 __host__ __device__ __forceinline__ size_t slot(int i, int j) { return (size_t)i * (i + 1) / 2 + j; }
-// offset of element (r, k) of a block (row r, K index k) in its slot (hi part; lo at + kChunk)
+// offset of element (r, k) of a block (row r, K index k) in its slot (hi part; lo at + kPart)
 __device__ __forceinline__ int soff(int r, int k) {
-  return (k >> 5) * (2 * kChunk) + (((r >> 3) * 8 + ((k & 31) >> 2)) * 32 + (r & 7) * 4 + (k & 3));
+  return (k >> 4) * kSub + (((r >> 3) * 4 + ((k & 15) >> 2)) * 32 + (r & 7) * 4 + (k & 3));
 }
 __device__ __forceinline__ uint64_t sdesc(unsigned saddr) {
   return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) |
-         ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46);
+         ((uint64_t)(512 >> 4) << 32) | ((uint64_t)1 << 46);
 }
 __device__ __forceinline__ void mma(unsigned tmem, uint64_t a, uint64_t b, unsigned acc) {
   asm volatile(
@@ -1092,13 +1095,13 @@ __device__ __forceinline__ void mma(unsigned tmem, uint64_t a, uint64_t b, unsig
       "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
       : "memory");
 }
-// D (+)= A B^T over the 32 K values of one chunk pair (A at sa, B at sb; hi then lo parts)
-__device__ __forceinline__ void mma_chunk(unsigned tmem, unsigned sa, unsigned sb, bool accumulate) {
+// D (+)= A B^T over the 16 K values of one sub-chunk pair (A at sa, B at sb; hi then lo parts)
+__device__ __forceinline__ void mma_sub(unsigned tmem, unsigned sa, unsigned sb, bool accumulate) {
 #pragma unroll
   for (int t = 0; t < 3; ++t) {
-    const unsigned ah = t == 2 ? sa + kChunk * 4u : sa, bh = t == 1 ? sb + kChunk * 4u : sb;
+    const unsigned ah = t == 2 ? sa + kPart * 4u : sa, bh = t == 1 ? sb + kPart * 4u : sb;
 #pragma unroll
-    for (int kk = 0; kk < KC / 8; ++kk)
+    for (int kk = 0; kk < KS / 8; ++kk)
       mma(tmem, sdesc(ah + 256u * kk), sdesc(bh + 256u * kk),
           (accumulate || t > 0 || kk > 0) ? 1u : 0u);
   }
@@ -1132,67 +1135,105 @@ __device__ __forceinline__ void tmem_row64(unsigned tmem, float (&v)[64]) {
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[32 + i] = h[i];
 }
-// four consecutive values (row r, K index k..k+3, k % 4 == 0) of a block into a global slot
+// four consecutive values (row r, K index k..k+3, k % 4 == 0) of a block into a slot layout,
+// in global memory (slot) or shared memory (the C operand)
 __device__ __forceinline__ void put4(float* slot, int r, int k, float a, float b, float c, float d) {
   const float ha = tc::tf32_rna(a), hb = tc::tf32_rna(b), hc = tc::tf32_rna(c),
               hd = tc::tf32_rna(d);
   const int o = soff(r, k);
   __stcg(reinterpret_cast<float4*>(slot + o), make_float4(ha, hb, hc, hd));
-  __stcg(reinterpret_cast<float4*>(slot + kChunk + o),
+  __stcg(reinterpret_cast<float4*>(slot + kPart + o),
          make_float4(tc::tf32_rna(a - ha), tc::tf32_rna(b - hb), tc::tf32_rna(c - hc),
                      tc::tf32_rna(d - hd)));
 }
+__device__ __forceinline__ void put4_smem(float* base, int r, int k, float a, float b, float c,
+                                          float d) {
+  const float ha = tc::tf32_rna(a), hb = tc::tf32_rna(b), hc = tc::tf32_rna(c),
+              hd = tc::tf32_rna(d);
+  const int o = soff(r, k);
+  *reinterpret_cast<float4*>(base + o) = make_float4(ha, hb, hc, hd);
+  *reinterpret_cast<float4*>(base + kPart + o) =
+      make_float4(tc::tf32_rna(a - ha), tc::tf32_rna(b - hb), tc::tf32_rna(c - hc),
+                  tc::tf32_rna(d - hd));
+}
 
-// Producer / MMA state of thread 0, kept across tasks so the barrier phases stay in step.
-struct Pipe {
-  unsigned cph[kStages];   // parity of the next copy completion per stage
-  int mc[kStages], mw[kStages];   // MMA commits issued / waited per stage
+// Stage ring of thread 0, kept across tasks so the barrier phases stay in step: NS stages of
+// `bytes` each at smem offset `base`; cph = parity of the next copy completion, mc / mw = MMA
+// commits issued / waited per stage.
+template <int NS>
+struct Ring {
+  unsigned long long copy[NS], mma[NS];
+  unsigned cph[NS];
+  int mc[NS], mw[NS];
 };
 
-// Thread 0: D = sum_{c < nck} A_c B_c^T, chunk pairs A_c = pa(c), B_c = pb(c) (nullptr: B = A),
-// dep(c) waited before the copies of chunk c. Every issued copy is waited exactly once and every
-// commit is waited before return (so the phases stay in step); bfin is committed after the last
-// MMA. False if a wait gave up (error word raised); the accumulator is then not meaningful.
-template <typename PA, typename PB, typename DEP>
-__device__ bool stream(unsigned tmem, unsigned char* stg, Pipe& pp, unsigned long long* bcopy,
-                       unsigned long long* bmma, unsigned long long* bfin, int nck, PA pa, PB pb,
-                       DEP dep, int* err, unsigned long long budget) {
+// Thread 0: D = sum_{c < nck} A_c B_c^T over chunks c of G sub-chunks each. A_c: from global at
+// pa(c) (G sub-chunks, contiguous) into the stage, or, with pa(c) == nullptr, resident in shared
+// memory at sa_res(c); B_c: from global at pb(c), or (pb(c) == nullptr) the stage's A. dep(c) is
+// waited before the copies of chunk c. Every issued copy is waited exactly once and every commit
+// is waited before return, so the phases stay in step; bfin is committed after the last MMA.
+// False if a wait gave up (error word raised); the accumulator is then not meaningful.
+template <int NS, int G, typename PA, typename RA, typename PB, typename DEP>
+__device__ bool stream(unsigned tmem, unsigned stg, Ring<NS>& rg, unsigned long long* bfin,
+                       int nck, PA pa, RA sa_res, PB pb, DEP dep, int* err,
+                       unsigned long long budget) {
+  constexpr unsigned kChunkBytes = G * kSubBytes;
   bool ok = true;
   int issued = 0;
   auto wait_mma = [&](int s) {
-    const bool g = mbar_wait(&bmma[s], (unsigned)(pp.mw[s] & 1), err, budget);
-    ++pp.mw[s];
+    const bool g = mbar_wait(&rg.mma[s], (unsigned)(rg.mw[s] & 1), err, budget);
+    ++rg.mw[s];
     return g;
   };
+  // stage s: [A chunk][B chunk] when A is streamed, [B chunk] otherwise
   auto issue = [&](int c) {
-    const int s = c % kStages;
-    while (pp.mw[s] < pp.mc[s])
+    const int s = c % NS;
+    while (rg.mw[s] < rg.mc[s])
       if (!wait_mma(s)) return false;   // the stage's previous MMAs are done with it
     if (!dep(c)) return false;
     fence_proxy_async_global();
     const float* a = pa(c);
     const float* b = pb(c);
-    unsigned char* d = stg + s * kStageBytes;
-    mbar_expect(&bcopy[s], b ? 2 * kPairBytes : kPairBytes);
-    bulk_load(d, a, kPairBytes, &bcopy[s]);
-    if (b) bulk_load(d + kPairBytes, b, kPairBytes, &bcopy[s]);
+    const unsigned bytes = (a ? kChunkBytes : 0u) + (b ? kChunkBytes : 0u);
+    const unsigned d = stg + s * (a ? 2u : 1u) * kChunkBytes;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                     smem_u32(&rg.copy[s])),
+                 "r"(bytes)
+                 : "memory");
+    if (a)
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+          "[%3];" ::"r"(d),
+          "l"(a), "r"(kChunkBytes), "r"(smem_u32(&rg.copy[s]))
+          : "memory");
+    if (b)
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+          "[%3];" ::"r"(d + (a ? kChunkBytes : 0u)),
+          "l"(b), "r"(kChunkBytes), "r"(smem_u32(&rg.copy[s]))
+          : "memory");
     return true;
   };
-  while (ok && issued < nck && issued < kStages) {
+  while (ok && issued < nck && issued < NS) {
     ok = issue(issued);
     if (ok) ++issued;
   }
   for (int c = 0; c < issued; ++c) {
-    const int s = c % kStages;
-    const bool got = mbar_wait(&bcopy[s], pp.cph[s], err, budget);
-    pp.cph[s] ^= 1u;
+    const int s = c % NS;
+    const bool got = mbar_wait(&rg.copy[s], rg.cph[s], err, budget);
+    rg.cph[s] ^= 1u;
     if (!got) ok = false;
     if (ok) {
       tc::fence_after();
-      const unsigned sa = smem_u32(stg + s * kStageBytes);
-      mma_chunk(tmem, sa, pb(c) ? sa + kPairBytes : sa, c > 0);
-      tc::commit(&bmma[s]);
-      ++pp.mc[s];
+      const bool sa_stream = pa(c) != nullptr, sb_stream = pb(c) != nullptr;
+      const unsigned d = stg + s * (sa_stream ? 2u : 1u) * kChunkBytes;
+      const unsigned sa = sa_stream ? d : sa_res(c);
+      const unsigned sb = sb_stream ? d + (sa_stream ? kChunkBytes : 0u) : sa;
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+        mma_sub(tmem, sa + g * kSubBytes, sb + g * kSubBytes, c > 0 || g > 0);
+      tc::commit(&rg.mma[s]);
+      ++rg.mc[s];
       if (c >= 1 && issued < nck) {   // refill the stage chunk c - 1 used
         ok = issue(issued);
         if (ok) ++issued;
@@ -1200,35 +1241,50 @@ __device__ bool stream(unsigned tmem, unsigned char* stg, Pipe& pp, unsigned lon
     }
   }
   tc::commit(bfin);
-  for (int s = 0; s < kStages; ++s)
-    while (pp.mw[s] < pp.mc[s]) wait_mma(s);
+  for (int s = 0; s < NS; ++s)
+    while (rg.mw[s] < rg.mc[s]) wait_mma(s);
   return ok;
+}
+
+template <int NS>
+__device__ __forceinline__ void ring_init(Ring<NS>& rg) {
+  for (int s = 0; s < NS; ++s) {
+    mbar_init(&rg.copy[s]);
+    mbar_init(&rg.mma[s]);
+    rg.cph[s] = 0u;
+    rg.mc[s] = rg.mw[s] = 0;
+  }
 }
 
 }  // namespace tcb
 
+// G: sub-chunks per operand per stage of the K loop (stages of 2 G x 16 KB, 6 / G of them).
+template <int G>
 __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __restrict__ descs,
                                                      const int2* __restrict__ tickets,
                                                      int nticket, int* __restrict__ head,
                                                      int* __restrict__ err,
                                                      unsigned long long budget_ns) {
   using namespace tcb;
+  constexpr int NS = 6 / G;
   constexpr int TB = 64, LDS = TB + 1, RT = 4;
   constexpr int LDC = BS + 1;
   extern __shared__ __align__(1024) unsigned char smb[];
   float* sm = reinterpret_cast<float*>(smb);
-  __shared__ __align__(8) unsigned long long bcopy[kStages], bmma[kStages], bfin;
+  __shared__ __align__(8) unsigned long long s_bfin;
   __shared__ unsigned s_tmem;
   __shared__ int s_t, s_ok, s_str;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tr = (tid / 16) * RT, tcl = (tid % 16) * RT;      // 64 x 64 register blocks
   const int arow = 32 * (warp & 3) + lane, acol = 64 * (warp >> 2);   // accumulator ownership
+  // stage rings of thread 0 (barriers and their phase counters, used by thread 0 only)
+  __shared__ __align__(8) Ring<NS> ring_k;          // K-loop stages
+  __shared__ __align__(8) Ring<kXStages> ring_x;    // X stages of the OFF product
+  unsigned long long* bfin = &s_bfin;
   if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&bcopy[s]);
-      mbar_init(&bmma[s]);
-    }
-    mbar_init(&bfin);
+    ring_init(ring_k);
+    ring_init(ring_x);
+    mbar_init(bfin);
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
@@ -1240,11 +1296,7 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
   __syncthreads();
   tc::fence_after();
   const unsigned tmem = s_tmem;
-  Pipe pp;
-  for (int s = 0; s < kStages; ++s) {
-    pp.cph[s] = 0u;
-    pp.mc[s] = pp.mw[s] = 0;
-  }
+  const unsigned stg = smem_u32(smb);
   unsigned fph = 0u;   // parity of the next bfin completion (all threads)
   // A wait that gives up raises the error word; every CTA then leaves its ticket loop (after its
   // copies and products in flight have completed), and the host reports DS_ERR_TIMEOUT.
@@ -1266,7 +1318,8 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
     int* tdone = P.cnt + nb;
     float* A = (float*)P.A;
     float* Lp = (float*)P.Lp;
-    const int nck = 4 * J;
+    constexpr int CPB = (BS / KS) / G;   // chunks per K block
+    const int nck = CPB * J;
     // ---- K loop: acc = sum_{k<J} L_Ik L_Jk^T
     if (tid == 0) {
       s_ok = *(volatile int*)err == 0;
@@ -1274,15 +1327,16 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
       if (s_str) {
         const float* si = Lp + slot(I, 0) * kSlot;
         const float* sj = Lp + slot(J, 0) * kSlot;
-        s_ok = stream(
-            tmem, smb, pp, bcopy, bmma, &bfin, nck,
-            [&](int c) { return si + (size_t)(c >> 2) * kSlot + (c & 3) * 2 * kChunk; },
-            [&](int c) -> const float* {
-              return diag ? nullptr : sj + (size_t)(c >> 2) * kSlot + (c & 3) * 2 * kChunk;
-            },
+        auto src = [&](const float* base, int c) {
+          return base + (size_t)(c / CPB) * kSlot + (c % CPB) * G * kSub;
+        };
+        s_ok = stream<NS, G>(
+            tmem, stg, ring_k, bfin, nck, [&](int c) -> const float* { return src(si, c); },
+            [&](int) { return 0u; },
+            [&](int c) -> const float* { return diag ? nullptr : src(sj, c); },
             [&](int c) {
-              if (c & 3) return true;
-              const int kb = c >> 2;
+              if (c % CPB) return true;
+              const int kb = c / CPB;
               return wait_flag(&tdone[I * nb + kb], 1, err, budget_ns) &&
                      (diag || wait_flag(&tdone[J * nb + kb], 1, err, budget_ns));
             },
@@ -1292,7 +1346,7 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
     __syncthreads();
     bool ok = s_ok;
     if (s_str) {   // thread 0 streamed the K loop and committed bfin after its last product
-      const bool got = mbar_wait(&bfin, fph, err, budget_ns);
+      const bool got = mbar_wait(bfin, fph, err, budget_ns);
       fph ^= 1u;
       ok = !__syncthreads_or(!got || !ok);
     }
@@ -1457,8 +1511,8 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
         tcb::put4(S, r, k, x4[0], x4[1], x4[2], x4[3]);
       }
     } else {
-      // ---- OFF(I, J): C = A_IJ - acc into slot (I, J), then L_IJ = C X_JJ^T
-      float* S = Lp + slot(I, J) * kSlot;
+      // ---- OFF(I, J): C = A_IJ - acc as hi / lo operand in shared memory, L_IJ = C X_JJ^T
+      float* Cs = sm;                 // 8 sub-chunks (128 KB)
       const int c0 = J * BS;
 #pragma unroll
       for (int e = 0; e < 64; e += 4) {
@@ -1473,22 +1527,23 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
           x[2] = p1.x - v[e + 2];
           x[3] = p1.y - v[e + 3];
         }
-        tcb::put4(S, arow, c, x[0], x[1], x[2], x[3]);
+        tcb::put4_smem(Cs, arow, c, x[0], x[1], x[2], x[3]);
       }
-      fence_proxy_async_global();
+      fence_proxy_async_shared();
       __syncthreads();
       if (tid == 0) {
         const float* sx = Lp + slot(J, J) * kSlot;
-        s_ok = stream(
-            tmem, smb, pp, bcopy, bmma, &bfin, 4,
-            [&](int c) { return (const float*)S + c * 2 * kChunk; },
-            [&](int c) -> const float* { return sx + c * 2 * kChunk; },
+        s_ok = stream<kXStages, 1>(
+            tmem, stg + kCBytes, ring_x, bfin, BS / KS,
+            [&](int) -> const float* { return nullptr; },
+            [&](int c) { return stg + (unsigned)c * kSubBytes; },
+            [&](int c) -> const float* { return sx + (size_t)c * kSub; },
             [&](int c) { return c > 0 || wait_flag(&pdone[J], 1, err, budget_ns); }, err,
             budget_ns);
       }
       __syncthreads();
       {
-        const bool got = mbar_wait(&bfin, fph, err, budget_ns);
+        const bool got = mbar_wait(bfin, fph, err, budget_ns);
         fph ^= 1u;
         if (__syncthreads_or(!got || !s_ok)) break;
       }
@@ -1502,6 +1557,7 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
           __stcg(reinterpret_cast<float2*>(A + (size_t)rg * n + c0 + acol + e),
                  make_float2(v[e], v[e + 1]));
       }
+      float* S = Lp + slot(I, J) * kSlot;
 #pragma unroll
       for (int e = 0; e < 64; e += 4)
         tcb::put4(S, arow, acol + e, v[e], v[e + 1], v[e + 2], v[e + 3]);
@@ -1567,11 +1623,18 @@ void launch_fill_spd(const BatchTabs& B, cudaStream_t s) {
 template <typename T>
 void launch_chol_dag(const BatchTabs& B, cudaStream_t s) {
   if (sizeof(T) == 4 && B.factor_tc == 2) {
-    static PerDevice attr_b;
-    set_smem_once(attr_b, k_chol_tcb, (int)tcb::kSmem);
     const int grid = std::min(B.n_chol_b, num_sms());
-    k_chol_tcb<<<grid, 256, tcb::kSmem, s>>>(B.d, B.chol_b, B.n_chol_b, B.words + 0, B.words + 5,
-                                             2000000000ull);
+    if (B.tcb_g == 1) {
+      static PerDevice attr_b1;
+      set_smem_once(attr_b1, k_chol_tcb<1>, (int)tcb::kSmem);
+      k_chol_tcb<1><<<grid, 256, tcb::kSmem, s>>>(B.d, B.chol_b, B.n_chol_b, B.words + 0,
+                                                  B.words + 5, 2000000000ull);
+    } else {
+      static PerDevice attr_b2;
+      set_smem_once(attr_b2, k_chol_tcb<2>, (int)tcb::kSmem);
+      k_chol_tcb<2><<<grid, 256, tcb::kSmem, s>>>(B.d, B.chol_b, B.n_chol_b, B.words + 0,
+                                                  B.words + 5, 2000000000ull);
+    }
     ++g_launches;
     return;
   }

@@ -223,6 +223,7 @@ struct BatchTabs {
   int n_chol_b;
   int factor_tc;             // FP32 factorisation: 0 SIMT 64-tiles, 1 tensor cores 64-tiles,
                              // 2 tensor cores 128-blocks
+  int tcb_g;                 // 128-block kernel: K sub-chunks of 16 per operand and stage (1, 2)
   int jtj;                   // ICP J^T W J on the tensor cores (BF16, FP32 accumulation)
   int max_tasks;             // max factorisation tasks over the problems
   int max_nt;                // max tile rows over the problems

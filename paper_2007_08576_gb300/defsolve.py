@@ -20,7 +20,7 @@ DS_OK, DS_ERR_ARG, DS_ERR_OOM, DS_ERR_BAD_INPUT, DS_ERR_NOT_SPD, DS_ERR_STATE, D
 DS_PREC_FP64, DS_PREC_FP32, DS_PREC_FP32_REFINE = 0, 1, 2
 DS_MAX_ITERS = 64
 DS_MAX_HYP = 64
-DS_FACTOR_AUTO = 3
+DS_FACTOR_AUTO = -1
 
 # every exported symbol of include/defsolve.h and include/defsolve_orb.h
 EXPORTS = [
@@ -251,17 +251,21 @@ def ds_batch_set_tracing(b, on=True):
     _check("ds_batch_set_tracing", lib().ds_batch_set_tracing(b, 1 if on else 0))
 
 
+FACTOR_KERNELS = ["simt64", "tc64", "tc128_stage64k", "tc128_stage32k"]
+
+
 def ds_batch_tune(b, reps=3):
-    """(chosen factor kernel, [ms of kernels 0, 1, 2]) after timing them on the batch's sizes."""
+    """(chosen factor kernel index, [ms of kernels 0..3]) after timing them on the batch's sizes
+    (kernel names in FACTOR_KERNELS)."""
     c = ctypes.c_int32()
-    ms = np.zeros(3, np.float64)
+    ms = np.zeros(4, np.float64)
     _check("ds_batch_tune", lib().ds_batch_tune(b, int(reps), ctypes.byref(c), _ptr(ms, np.float64)))
     return c.value, ms
 
 
 def ds_batch_factor_kernel(b):
     c = ctypes.c_int32()
-    ms = np.zeros(3, np.float64)
+    ms = np.zeros(4, np.float64)
     _check("ds_batch_factor_kernel",
            lib().ds_batch_factor_kernel(b, ctypes.byref(c), _ptr(ms, np.float64)))
     return c.value, ms

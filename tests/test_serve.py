@@ -164,7 +164,7 @@ def test_served_results_equal_alone():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("prec,ftc", [(0, 0), (1, 0), (2, 0), (2, 1), (2, 2)])
+@pytest.mark.parametrize("prec,ftc", [(0, 0), (1, 0), (2, 0), (2, 1), (2, 2), (2, 3)])
 def test_admission_estimate_covers_the_librarys_allocations(prec, ftc):
     """The admitter's per-stream estimate (stream_bytes) against the bytes the library reports
     the handle holds (ds_get_device_bytes, its own allocation count) after a full-size frame
