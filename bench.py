@@ -616,8 +616,12 @@ def run_gpu(args):
     def serve_run(rate_scale, n_frames, seed, streams):
         rng = np.random.default_rng(seed)
         rates = np.array([problems[j].rate_hz for j in streams]) * rate_scale
-        srv = Server(GpuEngine(variant_params(d, args, prec)),
-                     budget_bytes=int(0.6 * torch.cuda.mem_get_info()[0]))
+        # the served engine uses the factor kernel the headline batch's tuner chose
+        sp = variant_params(d, args, prec)
+        if tuner is not None:
+            sp.factor_tc = KERNEL_NAMES.index(tuner["chosen"])
+        srv = Server(GpuEngine(sp), budget_bytes=int(0.6 * torch.cuda.mem_get_info()[0]),
+                     max_inflight=args.max_inflight)
         for j in streams:
             sc = scenes[j]
             srv.open_stream(j, StreamSpec(sc.template_depth, sc.K, sc.nodes,
@@ -643,7 +647,11 @@ def run_gpu(args):
         return {"streams": len(streams), "offered_frames_per_s": round(float(rates.sum()), 1),
                 "frames": st["frames"], "frames_per_s": round(st["frames_per_s"], 2),
                 "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
-                "mean_batch": round(st["mean_batch"], 2), "batches": st["batches"]}
+                "mean_batch": round(st["mean_batch"], 2), "batches": st["batches"],
+                "max_inflight": args.max_inflight,
+                "mean_gpu_ms_per_batch": round(st["mean_gpu_ms_per_batch"], 3),
+                "mean_host_ms_per_launch": round(st["mean_host_ms_per_launch"], 3),
+                "mean_read_ms_per_frame": round(st["mean_read_ms_per_frame"], 4)}
 
     served = served_low = None
     if rank == 0 and args.served_frames > 0:
@@ -868,6 +876,8 @@ def main():
     ap.add_argument("--c3-frames", type=int, default=10, dest="c3_frames",
                     help="timed frames of the 640x480 / 1024-node stream alone (0: skip)")
     ap.add_argument("--served-frames", type=int, default=10000, dest="served_frames")
+    ap.add_argument("--max-inflight", type=int, default=2, dest="max_inflight",
+                    help="served loop: batches on the GPU at once (1 or 2)")
     ap.add_argument("--no-orb", action="store_true", dest="no_orb",
                     help="skip the ORB feature front-end measurement")
     ap.add_argument("--no-oracle", action="store_true", dest="no_oracle",

@@ -161,15 +161,21 @@ class GpuEngine:
         slot = next(x for x in self.batches if x[2] is None)
         on = {id(h) for h in solvers}
         mask = [1 if id(h) in on else 0 for h in self.handles]
+        e0 = self.torch.cuda.Event(enable_timing=True)
+        e0.record(slot[1])
         self.d.ds_batch_solve_masked(slot[0], mask, iters)
-        ev = self.torch.cuda.Event()
+        ev = self.torch.cuda.Event(enable_timing=True)
         ev.record(slot[1])
-        token = (slot, ev)
+        token = (slot, ev, e0)
         slot[2] = token
         return token
 
+    def gpu_ms(self, token) -> float:
+        """Device time of a completed launch (its batch stream, from the start of the solve)."""
+        return token[2].elapsed_time(token[1])
+
     def done(self, token) -> bool:
-        slot, ev = token
+        slot, ev = token[0], token[1]
         if ev.query():
             if slot[2] is token:
                 slot[2] = None
@@ -206,6 +212,9 @@ class Server:
         self.t_last = None
         self.batches = 0
         self.batch_sizes = []
+        self.gpu_ms = []          # device time of each completed batch (when the engine reports it)
+        self.host_ms = []         # host time of each launch (frame submissions + solve enqueue)
+        self.read_ms = []         # host time of each result read
 
     # -- streams
     def open_stream(self, sid, spec: StreamSpec) -> bool:
@@ -278,9 +287,13 @@ class Server:
         for token, sids, items in self.in_flight:
             if self.engine.done(token):
                 now_batch = len(sids)
+                if hasattr(self.engine, "gpu_ms"):
+                    self.gpu_ms.append(self.engine.gpu_ms(token))
                 for sid, (fut, t_arr) in zip(sids, items):
                     st = self.streams[sid]
+                    r0 = self.clock()
                     q, t, p = self.engine.read(st["solver"])
+                    self.read_ms.append((self.clock() - r0) * 1e3)
                     now = self.clock()
                     lat = now - t_arr
                     self.latencies.append(lat)
@@ -297,6 +310,7 @@ class Server:
                  if st["solver"] is not None and not st["busy"] and st["queue"]]
         ready = ready[: self.max_batch]
         if ready and len(self.in_flight) < self.max_inflight:
+            h0 = self.clock()
             solvers, items = [], []
             for sid in ready:
                 st = self.streams[sid]
@@ -307,6 +321,7 @@ class Server:
                 solvers.append(st["solver"])
                 items.append((fut, t_arr))
             token = self.engine.launch(solvers, self.iters)
+            self.host_ms.append((self.clock() - h0) * 1e3)
             self.in_flight.append((token, ready, items))
             self.batches += 1
             self.batch_sizes.append(len(ready))
@@ -329,6 +344,9 @@ class Server:
                 "p99_ms": float(np.percentile(lat, 99) * 1e3),
                 "batches": self.batches,
                 "mean_batch": float(np.mean(self.batch_sizes)) if self.batch_sizes else 0.0,
+                "mean_gpu_ms_per_batch": float(np.mean(self.gpu_ms)) if self.gpu_ms else None,
+                "mean_host_ms_per_launch": float(np.mean(self.host_ms)) if self.host_ms else None,
+                "mean_read_ms_per_frame": float(np.mean(self.read_ms)) if self.read_ms else None,
                 "device_bytes": self.used}
 
 
