@@ -186,6 +186,7 @@ def oracle_params(args):
 
 def variant_params(d, args, prec, **kw):
     """The CUDA path's ds_params for the same variant."""
+    kw.setdefault("jtj", 1 if args.jtj == "bf16" else 0)
     return d.default_params(precision=prec, factor_tc=FACTOR[args.factor],
                             solver=1 if args.solver == "block_jacobi" else 0,
                             assoc=1 if args.assoc == "bilinear" else 0,
@@ -222,7 +223,39 @@ def _oracle_frame(job):
             "seconds": dt}
 
 
-def start_oracle_pool(jobs, threads_each):
+def _oracle_stages(job):
+    """One frame of a workload timed by stage in a spawned worker (BLAS threads set by the
+    parent's environment): target preparation, RANSAC, one linearisation (ICP + ORB + dense
+    ARAP + normal equations) and one damped Cholesky solve; frame = prep + RANSAC + 10 x
+    (linearisation + solve)."""
+    cfg, seed, prm = job
+    from oracle import dqb, ransac, solver
+    from synth import make_scene
+    sc = make_scene(cfg, seed, n_frames=1)
+    f = sc.frames[0]
+    tpl = solver.setup_template(sc.template_depth, sc.K, sc.nodes, prm)
+    N = len(sc.nodes)
+    q = np.tile([1.0, 0, 0, 0], (N, 1))
+    t = np.zeros((N, 3))
+    t0 = time.perf_counter()
+    tgt = solver.prepare_target(f.depth, tpl.K)
+    t1 = time.perf_counter()
+    rs = ransac.ransac_1p(solver.ransac_o1(tpl, f.match_idx, q, t, prm), f.match_xyz, f.hyp,
+                          prm.H, prm.n_reweight, prm.keep_frac)
+    t2 = time.perf_counter()
+    orb = (f.match_idx, f.match_xyz.astype(np.float64), rs["mask"], rs["what"])
+    lin, _ = solver.linearize(tpl, tgt, q, t, orb, None, prm)
+    t3 = time.perf_counter()
+    delta = solver.cholesky_solve(solver.damp(lin.A, prm), lin.b)
+    dqb.apply_step(q, t, delta)
+    t4 = time.perf_counter()
+    st = {"prep_s": t1 - t0, "ransac_s": t2 - t1, "linearize_s": t3 - t2, "solve_s": t4 - t3}
+    frame = st["prep_s"] + st["ransac_s"] + ITERS * (st["linearize_s"] + st["solve_s"])
+    return dict({k: round(v, 4) for k, v in st.items()}, frame_s=round(frame, 3),
+                frames_per_s=round(1.0 / frame, 5))
+
+
+def start_oracle_pool(jobs, threads_each, fn=None):
     """Spawned worker processes (started before any CUDA call) solving the oracle jobs while the
     GPU runs; each worker's BLAS uses `threads_each` threads."""
     import multiprocessing as mp
@@ -238,7 +271,7 @@ def start_oracle_pool(jobs, threads_each):
                 os.environ.pop(k, None)
             else:
                 os.environ[k] = v
-    return pool, pool.map_async(_oracle_frame, jobs, chunksize=1)
+    return pool, pool.map_async(fn or _oracle_frame, jobs, chunksize=1)
 
 
 def _listed(res, H, band=1e-6):
@@ -427,14 +460,17 @@ def run_gpu(args):
     problems = mixed_problems(args.problems)
     sample = error_sample(problems)
     prm_o = oracle_params(args)
-    pool = pending = None
+    pool = pending = pool1 = pending1 = None
     c3_cfg = None
     if rank == 0 and not args.no_oracle:
         from synth import CONFIGS
         c3_cfg = CONFIGS["seq_640x480_n1024"]
         jobs = [(problems[k].cfg, problems[k].seed, prm_o, ITERS) for k in sample]
         jobs.append((c3_cfg, 2000, prm_o, ITERS))
-        pool, pending = start_oracle_pool(jobs, max(1, (_cores() - 2) // len(jobs)))
+        pool, pending = start_oracle_pool(jobs, max(1, (_cores() - 4) // len(jobs)))
+        # the single-thread oracle by stage on the single-frame and 320x240 workloads
+        st_jobs = [(CONFIGS["frame_80x60_n32"], 1000, prm_o), (CONFIGS["seq_320x240_n256"], 1000, prm_o)]
+        pool1, pending1 = start_oracle_pool(st_jobs, 1, _oracle_stages)
 
     import torch
     import torch.distributed as dist
@@ -601,16 +637,22 @@ def run_gpu(args):
     if args.c3_frames > 0:
         c3s = make_scene(CONFIGS["seq_640x480_n1024"], 2000 + 100000 * rank, n_frames=max(F, 2))
         c3 = {"workload": "seq_640x480_n1024 (6144 unknowns), one stream"}
-        for name, pr in (("fp32_refine", 2), ("fp64", 0)):
-            r3 = BatchRun(d, torch, dev, [c3s], variant_params(d, args, pr), stream)
+        c3_gpu = {}
+        for name, pr, jt in (("fp32_refine", 2, 0), ("mixed_bf16_jtj", 2, 1), ("fp64", 0, 0)):
+            r3 = BatchRun(d, torch, dev, [c3s], variant_params(d, args, pr, jtj=jt), stream)
             r3.step(0)
             torch.cuda.synchronize()
-            if name == "fp32_refine":
-                c3_gpu = gpu_result(d, r3.handles[0], c3s)
+            if pr != 0:
+                c3_gpu[name] = gpu_result(d, r3.handles[0], c3s)
             ms3, tot3, _ = timed_steps(r3, args.c3_frames, 2, flush, first=1)
             r3.close()
             c3[name] = {"frames_per_s": round(args.c3_frames / tot3, 3),
-                        "latency_ms": _stats_ms(ms3)}
+                        "latency_ms": _stats_ms(ms3),
+                        "precision": {"fp32_refine": "FP32 J^T J, FP32-level factor + 2 refinements",
+                                      "mixed_bf16_jtj": "ICP J^T J from BF16 rows on tensor cores "
+                                                        "(FP32 accumulate), FP32-level factor + 2 "
+                                                        "refinements",
+                                      "fp64": "FP32 J^T J, FP64 factor and solves + 2 refinements"}[name]}
 
     # ------------------------------------------------------------ served: Poisson arrivals
     def serve_run(rate_scale, n_frames, seed, streams):
@@ -715,7 +757,8 @@ def run_gpu(args):
                               "template size, solved in the timed batch configuration, against "
                               "the FP64 oracle (10 iterations each)"}
             if c3 is not None:
-                c3["error_vs_oracle_fp32_refine"] = _rounded(compare(c3_gpu, res[len(sample)], 2.0))
+                for name, g in c3_gpu.items():
+                    c3[name]["error_vs_oracle"] = _rounded(compare(g, res[len(sample)], 2.0))
             secs = [r["seconds"] for r in res[:len(sample)]]
             cpu = {"value": round(len(secs) / sum(secs), 5), "unit": "frames/s",
                    "cores": max(1, (_cores() - 2) // (len(sample) + 1)), "kind": "oracle",
@@ -726,6 +769,17 @@ def run_gpu(args):
                              "problems, so this overstates the oracle's rate on the whole mix",
                    "c3_frame_seconds": round(res[len(sample)]["seconds"], 2) if c3 else None}
 
+    cpu_modes = None
+    if pending1 is not None:
+        try:
+            r1 = pending1.get(timeout=args.oracle_timeout)
+            cpu_modes = {"threads": 1, "frame_80x60_n32": r1[0], "seq_320x240_n256": r1[1],
+                         "note": "FP64 oracle, one BLAS thread, in a worker process running "
+                                 "beside the GPU arm; frame = prep + RANSAC + 10 x "
+                                 "(linearisation + solve)"}
+        except Exception as e:
+            cpu_modes = {"unavailable": f"single-thread oracle did not finish: {type(e).__name__}"}
+        pool1.terminate()
     result = None
     if rank == 0:
         sizes = {}
@@ -735,9 +789,11 @@ def run_gpu(args):
             "metric": METRIC, "value": round(value, 3), "unit": "frames/s", "n_gpus": world,
             "steps": K, "warmup": W, "ms_per_step": round(float(total_s * 1e3 / K), 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f32 residuals/J^T J, f64 Cholesky, double-f32 refine residuals",
-                      "fp32": "f32",
-                      "fp32_refine": "f32 J^T J + Cholesky, double-f32 (48-bit) refine residuals"}[args.precision],
+            "dtype": ({"fp64": "f32 residuals/J^T J, f64 Cholesky, double-f32 refine residuals",
+                       "fp32": "f32",
+                       "fp32_refine": "f32 J^T J + f32-level Cholesky, double-f32 (48-bit) refine "
+                                      "residuals"}[args.precision]
+                      + ("; ICP J^T J from bf16 rows (f32 accumulate)" if args.jtj == "bf16" else "")),
             "data": "synthetic (seeded heightfields, deformation + camera motion, ray-cast depth, "
                     "matches with planted outliers)",
             "config": {"workload": WORKLOAD, "problems": n_p, "templates": sizes,
@@ -745,6 +801,7 @@ def run_gpu(args):
                                           "mean": round(float(np.mean(n_list)) / 6, 1)},
                        "outlier_rate": [0.2, 0.6], "gn_iters": ITERS, "precision": args.precision,
                        "solver": args.solver, "icp_association": args.assoc,
+                       "icp_jtj": args.jtj,
                        "ransac_o1": args.ransac_o1,
                        "factor": {"simt": "FP32 SIMT 64 x 64 tiles",
                                   "tc64": "tensor cores (tcgen05, 3xTF32), 64 x 64 tiles",
@@ -793,6 +850,7 @@ def run_gpu(args):
                          "timing": "factorisation phase per step, CUDA events in the graph"},
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
+            "cpu_oracle_single_thread": cpu_modes,
         }
     if world > 1:
         dist.barrier()
@@ -889,6 +947,8 @@ def main():
                     help="FP32 factorisation kernel: SIMT 64 x 64 tiles, tensor cores (tcgen05, "
                          "3xTF32) with 64 x 64 tiles or 128 x 128 blocks (64 KB or 32 KB operand "
                          "stages), or picked by the library's tuner on the batch's sizes (auto)")
+    ap.add_argument("--jtj", default="fp32", choices=["fp32", "bf16"],
+                    help="ICP J^T W J: FP32 SIMT, or BF16 rows on the tensor cores (FP32 accumulate)")
     ap.add_argument("--assoc", default="nearest", choices=["nearest", "bilinear"],
                     help="ICP association: nearest pixel or bilinear blend of 4 pixels")
     ap.add_argument("--ransac-o1", default="template", choices=["template", "warm"],
