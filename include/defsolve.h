@@ -95,10 +95,12 @@ typedef struct {
                              * tiles; on the tensor cores (tcgen05 kind::tf32, each product as
                              * three TF32 terms hi*hi + hi*lo + lo*hi, FP32-level accuracy) with
                              * 1 = 64 x 64 tiles, 2 = 128 x 128 blocks streamed in three 64 KB
-                             * operand stages, 3 = the same in six 32 KB stages; DS_FACTOR_AUTO
-                             * (default) = picked per batch by timing the four on the batch's
-                             * sizes at its first solve (ds_batch_tune). Ignored in DS_PREC_FP64.
-                             * Handles of one batch must agree.                                   */
+                             * operand stages, 3 = the same in six 32 KB stages, 4 / 5 = 2 / 3
+                             * with the block tasks claimed in runs of 8 per problem (a run shares
+                             * its column's operand in L2); DS_FACTOR_AUTO (default) = picked per
+                             * batch by timing the six on the batch's sizes at its first solve
+                             * (ds_batch_tune). Ignored in DS_PREC_FP64. Handles of one batch
+                             * must agree.                                                        */
   int32_t solver;           /* 0 = one Cholesky of the dense 6N x 6N damped system (default);
                              * 1 = block-Jacobi: each control point's 6 unknowns from its own 6 x 6
                              * damped diagonal block (FP64 Cholesky per node), the reading of
@@ -231,16 +233,16 @@ int ds_batch_set_graph(ds_batch b, int32_t on);
  * batch's problem sizes, written into the handles' factor buffers (no allocation; a later solve
  * assembles its own systems over them), `reps` launches each (1..100), and makes the fastest the
  * batch's kernel for its later solves, whatever factor_tc its handles carry. Kernel index =
- * the factor_tc value that selects it (0..3). *choice (may be NULL) receives the index (-1 for FP64 or
- * block-Jacobi batches, which have one kernel only), ms4 (may be NULL) the four kernels' best
+ * the factor_tc value that selects it (0..5). *choice (may be NULL) receives the index (-1 for FP64 or
+ * block-Jacobi batches, which have one kernel only), ms6 (may be NULL) the six kernels' best
  * times in ms. The choice is also cached for the process by batch shape (largest system, summed
  * n^3), where batches of DS_FACTOR_AUTO handles look it up at their first solve; without an entry
  * they tune themselves then (2 launches per kernel). Synchronises the batch stream; make the
  * first solve of an auto batch outside any stream capture. Errors: DS_ERR_ARG, DS_ERR_STATE
  * (stale batch), DS_ERR_TIMEOUT, DS_ERR_CUDA. */
-int ds_batch_tune(ds_batch b, int32_t reps, int32_t* choice, double* ms4);
-/* The batch's factor kernel index now and the tuner's last times (ms4[k] = -1: not timed). */
-int ds_batch_factor_kernel(ds_batch b, int32_t* choice, double* ms4);
+int ds_batch_tune(ds_batch b, int32_t reps, int32_t* choice, double* ms6);
+/* The batch's factor kernel index now and the tuner's last times (ms6[k] = -1: not timed). */
+int ds_batch_factor_kernel(ds_batch b, int32_t* choice, double* ms6);
 
 /* Convenience: a temporary batch over n handles, solved and synchronised. */
 int ds_solve_batch(ds_handle* hs, int32_t n, int32_t iters);

@@ -78,7 +78,7 @@ struct ds_batch_s {
   // factor kernel chosen by timing (DS_FACTOR_AUTO handles): tuned once, before the first solve
   bool auto_factor = false;
   bool tuned = false;
-  double tune_ms[4] = {-1.0, -1.0, -1.0, -1.0};
+  double tune_ms[6] = {-1.0, -1.0, -1.0, -1.0, -1.0, -1.0};
 };
 
 struct ds_ctx {
@@ -296,14 +296,20 @@ void destroy_batch(ds_batch_s* b);
 // The factor kernels the tuner chooses from, by kernel index: SIMT 64 x 64 tiles, tensor cores
 // with 64 x 64 tiles, tensor cores with 128 x 128 blocks in three 64 KB stages, and in six
 // 32 KB stages.
-constexpr int kFactorKernels = 4;
+// Indices 4 and 5 are the 128-block kernel (64 KB / 32 KB stages) with its tickets claimed in
+// runs of kClaimRun tasks per problem instead of one.
+constexpr int kFactorKernels = 6;
+constexpr int kClaimRun = 8;
 void set_factor_kernel(BatchTabs& T, int k) {
-  static const int ftc[kFactorKernels] = {0, 1, 2, 2}, g[kFactorKernels] = {2, 2, 2, 1};
+  static const int ftc[kFactorKernels] = {0, 1, 2, 2, 2, 2}, g[kFactorKernels] = {2, 2, 2, 1, 2, 1},
+                   run[kFactorKernels] = {0, 0, 0, 0, 1, 1};
   T.factor_tc = ftc[k];
   T.tcb_g = g[k];
+  T.tcb_runs = run[k];
 }
 int factor_kernel_of(const BatchTabs& T) {
-  return T.factor_tc < 2 ? T.factor_tc : (T.tcb_g == 2 ? 2 : 3);
+  if (T.factor_tc < 2) return T.factor_tc;
+  return (T.tcb_g == 2 ? 2 : 3) + (T.tcb_runs ? 2 : 0);
 }
 
 // The handle's batches stop running: its control points change or (leaving) it goes away, and
@@ -428,12 +434,14 @@ void make_chol_tasks_b(int nb, std::vector<int4>& out) {
 
 // Claim order of the factorisation tickets of a batch: problems interleaved round-robin, each
 // problem's tasks in their own (topological) order, so every task waits only on earlier tickets.
-void make_chol_tickets(const std::vector<int>& ntasks, std::vector<int2>& out) {
+// With run > 1 each problem contributes `run` consecutive tasks per turn (a run of one block
+// column's tasks shares that column's operand, which then stays in L2); still topological.
+void make_chol_tickets(const std::vector<int>& ntasks, std::vector<int2>& out, int run = 1) {
   int mx = 0;
   for (int v : ntasks) mx = std::max(mx, v);
-  for (int l = 0; l < mx; ++l)
+  for (int l = 0; l < mx; l += run)
     for (int p = 0; p < (int)ntasks.size(); ++p)
-      if (l < ntasks[p]) out.push_back(make_int2(p, l));
+      for (int k = l; k < l + run && k < ntasks[p]; ++k) out.push_back(make_int2(p, k));
 }
 
 // Events recorded while the stream is captured become event-record nodes of the graph only with
@@ -501,7 +509,7 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   b->block_jacobi = solver == 1;
   b->stream = stream;
   b->own_stream = own;
-  std::vector<int2> icp, rows, nodes, res, chol, chol_b;
+  std::vector<int2> icp, rows, nodes, res, chol, chol_b, chol_br;
   std::vector<int> ntasks(n), ntasks_b(n);
   int max_tasks = 0, max_nt = 0;
   std::vector<const ProbDesc*> descs(n);
@@ -519,8 +527,9 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   }
   make_chol_tickets(ntasks, chol);
   make_chol_tickets(ntasks_b, chol_b);
-  const size_t ntab =
-      icp.size() + rows.size() + nodes.size() + res.size() + chol.size() + chol_b.size();
+  make_chol_tickets(ntasks_b, chol_br, kClaimRun);
+  const size_t ntab = icp.size() + rows.size() + nodes.size() + res.size() + chol.size() +
+                      chol_b.size() + chol_br.size();
   int rc;
   if ((rc = dalloc(&b->d_descs, n)) || (rc = dalloc(&b->d_tab, ntab)) ||
       (rc = dalloc(&b->d_words, 8))) {
@@ -529,7 +538,7 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   }
   std::vector<int2> all;
   all.reserve(ntab);
-  for (auto* v : {&icp, &rows, &nodes, &res, &chol, &chol_b})
+  for (auto* v : {&icp, &rows, &nodes, &res, &chol, &chol_b, &chol_br})
     all.insert(all.end(), v->begin(), v->end());
   cudaMemcpy(b->d_descs, descs.data(), sizeof(void*) * n, cudaMemcpyHostToDevice);
   b->h_descs = descs;
@@ -545,6 +554,7 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   T.res = b->d_tab + off; T.n_res = (int)res.size(); off += res.size();
   T.chol = b->d_tab + off; T.n_chol = (int)chol.size(); off += chol.size();
   T.chol_b = b->d_tab + off; T.n_chol_b = (int)chol_b.size(); off += chol_b.size();
+  T.chol_br = b->d_tab + off; off += chol_br.size();
   T.orb_ctas = 16;
   b->auto_factor = ftc == DS_FACTOR_AUTO;
   set_factor_kernel(T, b->auto_factor ? 0 : ftc);
@@ -868,7 +878,7 @@ bool valid_params(const ds_params& p) {
          p.eps_damp >= 0 && p.keep_frac >= 0 && p.keep_frac <= 1 && p.sigma_blend_scale > 0 &&
          p.sigma_arap_scale > 0 && p.precision >= 0 && p.precision <= 2 && p.refine_steps >= 0 &&
          p.refine_steps <= 3 && p.w_orb >= 0 && p.w_angle >= 0 && p.w_rot >= 0 &&
-         p.w_arap0 >= 0 && (p.factor_tc >= DS_FACTOR_AUTO && p.factor_tc <= 3) &&
+         p.w_arap0 >= 0 && (p.factor_tc >= DS_FACTOR_AUTO && p.factor_tc <= 5) &&
          (p.solver == 0 || p.solver == 1) && (p.assoc == 0 || p.assoc == 1) &&
          (p.ransac_o1 == 0 || p.ransac_o1 == 1) && (p.jtj == 0 || p.jtj == 1);
 }
@@ -1525,14 +1535,14 @@ int ds_batch_solve_masked(ds_batch b, const uint8_t* active, int32_t iters) {
   return run_batch(b, iters, graph, active);
 }
 
-int ds_batch_tune(ds_batch b, int32_t reps, int32_t* choice, double* ms4) {
+int ds_batch_tune(ds_batch b, int32_t reps, int32_t* choice, double* ms6) {
   if (!b || reps < 1 || reps > 100) return DS_ERR_ARG;
   if (b->error) return DS_ERR_CUDA;
   if (b->stale) return DS_ERR_STATE;
   if (b->fp64 || b->block_jacobi) {
     if (choice) *choice = -1;   // one kernel only: nothing to choose
-    if (ms4)
-      for (int c = 0; c < kFactorKernels; ++c) ms4[c] = -1.0;
+    if (ms6)
+      for (int c = 0; c < kFactorKernels; ++c) ms6[c] = -1.0;
     return DS_OK;
   }
   const int rc = tune_factor(b, reps);
@@ -1542,16 +1552,16 @@ int ds_batch_tune(ds_batch b, int32_t reps, int32_t* choice, double* ms4) {
     g_tune_cache[tune_key(b)] = factor_kernel_of(b->tabs);
   }
   if (choice) *choice = factor_kernel_of(b->tabs);
-  if (ms4)
-    for (int c = 0; c < kFactorKernels; ++c) ms4[c] = b->tune_ms[c];
+  if (ms6)
+    for (int c = 0; c < kFactorKernels; ++c) ms6[c] = b->tune_ms[c];
   return DS_OK;
 }
 
-int ds_batch_factor_kernel(ds_batch b, int32_t* choice, double* ms4) {
+int ds_batch_factor_kernel(ds_batch b, int32_t* choice, double* ms6) {
   if (!b || !choice) return DS_ERR_ARG;
   *choice = (b->fp64 || b->block_jacobi) ? -1 : factor_kernel_of(b->tabs);
-  if (ms4)
-    for (int c = 0; c < kFactorKernels; ++c) ms4[c] = b->tune_ms[c];
+  if (ms6)
+    for (int c = 0; c < kFactorKernels; ++c) ms6[c] = b->tune_ms[c];
   return DS_OK;
 }
 

@@ -1342,6 +1342,15 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
             },
             err, budget_ns);
       }
+    } else {
+      // while thread 0 streams the K loop, the others pull this block of A (the epilogue's C =
+      // A - acc) into L2: each thread its row's 64 columns, two 128-byte lines
+      const int pr = I * BS + arow, pc = J * BS + acol;
+      if (pr < n) {
+        const float* pa = A + (size_t)pr * n + pc;
+        if (pc < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(pa));
+        if (pc + 32 < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(pa + 32));
+      }
     }
     __syncthreads();
     bool ok = s_ok;
@@ -1624,15 +1633,16 @@ template <typename T>
 void launch_chol_dag(const BatchTabs& B, cudaStream_t s) {
   if (sizeof(T) == 4 && B.factor_tc == 2) {
     const int grid = std::min(B.n_chol_b, num_sms());
+    const int2* tickets = B.tcb_runs ? B.chol_br : B.chol_b;
     if (B.tcb_g == 1) {
       static PerDevice attr_b1;
       set_smem_once(attr_b1, k_chol_tcb<1>, (int)tcb::kSmem);
-      k_chol_tcb<1><<<grid, 256, tcb::kSmem, s>>>(B.d, B.chol_b, B.n_chol_b, B.words + 0,
+      k_chol_tcb<1><<<grid, 256, tcb::kSmem, s>>>(B.d, tickets, B.n_chol_b, B.words + 0,
                                                   B.words + 5, 2000000000ull);
     } else {
       static PerDevice attr_b2;
       set_smem_once(attr_b2, k_chol_tcb<2>, (int)tcb::kSmem);
-      k_chol_tcb<2><<<grid, 256, tcb::kSmem, s>>>(B.d, B.chol_b, B.n_chol_b, B.words + 0,
+      k_chol_tcb<2><<<grid, 256, tcb::kSmem, s>>>(B.d, tickets, B.n_chol_b, B.words + 0,
                                                   B.words + 5, 2000000000ull);
     }
     ++g_launches;

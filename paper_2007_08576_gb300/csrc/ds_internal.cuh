@@ -224,6 +224,8 @@ struct BatchTabs {
   int factor_tc;             // FP32 factorisation: 0 SIMT 64-tiles, 1 tensor cores 64-tiles,
                              // 2 tensor cores 128-blocks
   int tcb_g;                 // 128-block kernel: K sub-chunks of 16 per operand and stage (1, 2)
+  int tcb_runs;              // 128-block kernel: claim order with runs of tasks per problem
+  const int2* chol_br;       // the 128-block tickets in that order (n_chol_b of them)
   int jtj;                   // ICP J^T W J on the tensor cores (BF16, FP32 accumulation)
   int max_tasks;             // max factorisation tasks over the problems
   int max_nt;                // max tile rows over the problems

@@ -251,21 +251,22 @@ def ds_batch_set_tracing(b, on=True):
     _check("ds_batch_set_tracing", lib().ds_batch_set_tracing(b, 1 if on else 0))
 
 
-FACTOR_KERNELS = ["simt64", "tc64", "tc128_stage64k", "tc128_stage32k"]
+FACTOR_KERNELS = ["simt64", "tc64", "tc128_stage64k", "tc128_stage32k", "tc128_stage64k_runs",
+                  "tc128_stage32k_runs"]
 
 
 def ds_batch_tune(b, reps=3):
-    """(chosen factor kernel index, [ms of kernels 0..3]) after timing them on the batch's sizes
+    """(chosen factor kernel index, [ms of kernels 0..5]) after timing them on the batch's sizes
     (kernel names in FACTOR_KERNELS)."""
     c = ctypes.c_int32()
-    ms = np.zeros(4, np.float64)
+    ms = np.zeros(6, np.float64)
     _check("ds_batch_tune", lib().ds_batch_tune(b, int(reps), ctypes.byref(c), _ptr(ms, np.float64)))
     return c.value, ms
 
 
 def ds_batch_factor_kernel(b):
     c = ctypes.c_int32()
-    ms = np.zeros(4, np.float64)
+    ms = np.zeros(6, np.float64)
     _check("ds_batch_factor_kernel",
            lib().ds_batch_factor_kernel(b, ctypes.byref(c), _ptr(ms, np.float64)))
     return c.value, ms

@@ -419,7 +419,8 @@ def test_bounded_waits_give_up_and_the_context_stays_usable(d, tiny):
 # ----------------------------------------------------------------------------- tensor-core factor
 
 
-@pytest.mark.parametrize("ftc", [1, 2, 3], ids=["tiles64", "blocks128", "blocks128s"])
+@pytest.mark.parametrize("ftc", [1, 2, 3, 4, 5],
+                         ids=["tiles64", "blocks128", "blocks128s", "blocks128r", "blocks128sr"])
 @pytest.mark.parametrize("prec", [1, 2])
 def test_tensor_core_factor_matches_oracle_tiny_and_ragged(d, tiny, mid, prec, ftc):
     """FP32 factorisation on tcgen05 (three TF32 terms per product): the same parity bar, with
@@ -454,7 +455,7 @@ def test_tensor_core_factor_batch_equals_simt_and_agreement_rule(d, tiny, mid):
     """An uneven batch factored on the tensor cores gives the SIMT batch's result within the
     parity tolerance; handles that disagree on the factor kernel cannot share a batch."""
     outs = {}
-    for ftc in (0, 1, 2, 3):
+    for ftc in (0, 1, 2, 3, 4, 5):
         p = d.default_params(precision=2, factor_tc=ftc)
         solvers = []
         for sc in (mid, tiny, mid):
@@ -466,7 +467,7 @@ def test_tensor_core_factor_batch_equals_simt_and_agreement_rule(d, tiny, mid):
         outs[ftc] = [s.deformation64()[1] for s in solvers]
         for s in solvers:
             s.close()
-    for ftc in (1, 2, 3):
+    for ftc in (1, 2, 3, 4, 5):
         for a, b in zip(outs[0], outs[ftc]):
             assert np.abs(a - b).max() <= POS_TOL_MM
     a = d.Solver(tiny.template_depth, tiny.K, tiny.nodes, d.default_params(precision=2))
@@ -790,7 +791,7 @@ def test_factor_tuner_picks_the_fastest_and_auto_batches_stay_at_parity(d, tiny,
         b = d.ds_batch_create([s.h for s in solvers])
         if ftc == d.DS_FACTOR_AUTO:
             choice, ms = d.ds_batch_tune(b, 2)
-            assert choice in (0, 1, 2, 3) and (ms > 0).all()
+            assert choice in range(6) and (ms > 0).all()
             assert ms[choice] == ms.min()
             assert d.ds_batch_factor_kernel(b)[0] == choice
         d.ds_batch_solve(b, 10)

@@ -73,9 +73,9 @@ def _check(d, case, p):
     return err, rel.max()
 
 
-@pytest.mark.parametrize("prec,ftc", [(2, 0), (0, 0), (2, 1), (2, 2), (2, 3), (2, -1)],
+@pytest.mark.parametrize("prec,ftc", [(2, 0), (0, 0), (2, 1), (2, 2), (2, 3), (2, 4), (2, -1)],
                          ids=["fp32_refine", "fp64", "fp32_refine_tc64", "fp32_refine_tc128",
-                              "fp32_refine_tc128s", "fp32_refine_auto"])
+                              "fp32_refine_tc128s", "fp32_refine_tc128r", "fp32_refine_auto"])
 def test_320x240_n256_all_iterations(d, c2, prec, ftc):
     _check(d, c2, d.default_params(precision=prec, factor_tc=ftc))
 
