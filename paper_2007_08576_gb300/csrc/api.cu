@@ -166,6 +166,8 @@ struct ds_ctx {
   int ntasks = 0;
   int4* d_tasks_b = nullptr;  // 128-block factorisation tasks
   int ntasks_b = 0;
+  int4* d_tasks_p = nullptr;  // the same with the block columns in pairs
+  int ntasks_p = 0;
   int nt = 0;
   bool prec_fp64 = false;
   double* d_acc = nullptr;
@@ -295,21 +297,19 @@ void destroy_batch(ds_batch_s* b);
 
 // The factor kernels the tuner chooses from, by kernel index: SIMT 64 x 64 tiles, tensor cores
 // with 64 x 64 tiles, tensor cores with 128 x 128 blocks in three 64 KB stages, and in six
-// 32 KB stages.
-// Indices 4 and 5 are the 128-block kernel (64 KB / 32 KB stages) with its tickets claimed in
-// runs of kClaimRun tasks per problem instead of one.
+// 32 KB stages; indices 4 and 5 are the 128-block kernel (64 KB / 32 KB stages of its single
+// block tasks) with its block columns taken in pairs (one stream of each row panel per pair).
 constexpr int kFactorKernels = 6;
-constexpr int kClaimRun = 8;
 void set_factor_kernel(BatchTabs& T, int k) {
   static const int ftc[kFactorKernels] = {0, 1, 2, 2, 2, 2}, g[kFactorKernels] = {2, 2, 2, 1, 2, 1},
-                   run[kFactorKernels] = {0, 0, 0, 0, 1, 1};
+                   pairs[kFactorKernels] = {0, 0, 0, 0, 1, 1};
   T.factor_tc = ftc[k];
   T.tcb_g = g[k];
-  T.tcb_runs = run[k];
+  T.tcb_pairs = pairs[k];
 }
 int factor_kernel_of(const BatchTabs& T) {
   if (T.factor_tc < 2) return T.factor_tc;
-  return (T.tcb_g == 2 ? 2 : 3) + (T.tcb_runs ? 2 : 0);
+  return (T.tcb_g == 2 ? 2 : 3) + (T.tcb_pairs ? 2 : 0);
 }
 
 // The handle's batches stop running: its control points change or (leaving) it goes away, and
@@ -335,6 +335,7 @@ void free_cp(ds_ctx* h) {
   hfree(h, h->d_gdata); hfree(h, h->d_b); hfree(h, h->d_x); hfree(h, h->d_r); hfree(h, h->d_xf);
   hfree(h, h->d_v2); hfree(h, h->d_v3); hfree(h, h->d_lcnt); hfree(h, h->d_lflags); hfree(h, h->d_tasks);
   hfree(h, h->d_tasks_b);
+  hfree(h, h->d_tasks_p);
   hfree(h, h->d_Lp);
   hfree(h, h->d_desc);
   h->N = h->n = 0;
@@ -432,16 +433,27 @@ void make_chol_tasks_b(int nb, std::vector<int4>& out) {
   make_chol_tasks(nb, out);
 }
 
+// Block tasks with the block columns taken in pairs (J0 = 2 p, J1 = J0 + 1): DIAG(J0),
+// OFF(J1, J0), DIAG(J1), then {0, 2, I, J0} for I = J1 + 1 .. nb - 1, the two blocks (I, J0) and
+// (I, J1) as one task. A lone last column is DIAG alone. Topological, like the single order.
+void make_chol_tasks_p(int nb, std::vector<int4>& out) {
+  for (int j0 = 0; j0 < nb; j0 += 2) {
+    out.push_back(make_int4(0, 0, j0, j0));
+    if (j0 + 1 >= nb) break;
+    out.push_back(make_int4(0, 1, j0 + 1, j0));
+    out.push_back(make_int4(0, 0, j0 + 1, j0 + 1));
+    for (int i = j0 + 2; i < nb; ++i) out.push_back(make_int4(0, 2, i, j0));
+  }
+}
+
 // Claim order of the factorisation tickets of a batch: problems interleaved round-robin, each
 // problem's tasks in their own (topological) order, so every task waits only on earlier tickets.
-// With run > 1 each problem contributes `run` consecutive tasks per turn (a run of one block
-// column's tasks shares that column's operand, which then stays in L2); still topological.
-void make_chol_tickets(const std::vector<int>& ntasks, std::vector<int2>& out, int run = 1) {
+void make_chol_tickets(const std::vector<int>& ntasks, std::vector<int2>& out) {
   int mx = 0;
   for (int v : ntasks) mx = std::max(mx, v);
-  for (int l = 0; l < mx; l += run)
+  for (int k = 0; k < mx; ++k)
     for (int p = 0; p < (int)ntasks.size(); ++p)
-      for (int k = l; k < l + run && k < ntasks[p]; ++k) out.push_back(make_int2(p, k));
+      if (k < ntasks[p]) out.push_back(make_int2(p, k));
 }
 
 // Events recorded while the stream is captured become event-record nodes of the graph only with
@@ -509,8 +521,8 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   b->block_jacobi = solver == 1;
   b->stream = stream;
   b->own_stream = own;
-  std::vector<int2> icp, rows, nodes, res, chol, chol_b, chol_br;
-  std::vector<int> ntasks(n), ntasks_b(n);
+  std::vector<int2> icp, rows, nodes, res, chol, chol_b, chol_p;
+  std::vector<int> ntasks(n), ntasks_b(n), ntasks_p(n);
   int max_tasks = 0, max_nt = 0;
   std::vector<const ProbDesc*> descs(n);
   for (int p = 0; p < n; ++p) {
@@ -522,14 +534,15 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
     for (int c = 0; c * 8 < h->n; ++c) res.push_back(make_int2(p, c));
     ntasks[p] = h->ntasks;
     ntasks_b[p] = h->ntasks_b;
+    ntasks_p[p] = h->ntasks_p;
     max_tasks = std::max(max_tasks, h->ntasks);
     max_nt = std::max(max_nt, h->nt);
   }
   make_chol_tickets(ntasks, chol);
   make_chol_tickets(ntasks_b, chol_b);
-  make_chol_tickets(ntasks_b, chol_br, kClaimRun);
+  make_chol_tickets(ntasks_p, chol_p);
   const size_t ntab = icp.size() + rows.size() + nodes.size() + res.size() + chol.size() +
-                      chol_b.size() + chol_br.size();
+                      chol_b.size() + chol_p.size();
   int rc;
   if ((rc = dalloc(&b->d_descs, n)) || (rc = dalloc(&b->d_tab, ntab)) ||
       (rc = dalloc(&b->d_words, 8))) {
@@ -538,7 +551,7 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   }
   std::vector<int2> all;
   all.reserve(ntab);
-  for (auto* v : {&icp, &rows, &nodes, &res, &chol, &chol_b, &chol_br})
+  for (auto* v : {&icp, &rows, &nodes, &res, &chol, &chol_b, &chol_p})
     all.insert(all.end(), v->begin(), v->end());
   cudaMemcpy(b->d_descs, descs.data(), sizeof(void*) * n, cudaMemcpyHostToDevice);
   b->h_descs = descs;
@@ -554,7 +567,7 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   T.res = b->d_tab + off; T.n_res = (int)res.size(); off += res.size();
   T.chol = b->d_tab + off; T.n_chol = (int)chol.size(); off += chol.size();
   T.chol_b = b->d_tab + off; T.n_chol_b = (int)chol_b.size(); off += chol_b.size();
-  T.chol_br = b->d_tab + off; off += chol_br.size();
+  T.chol_p = b->d_tab + off; T.n_chol_p = (int)chol_p.size(); off += chol_p.size();
   T.orb_ctas = 16;
   b->auto_factor = ftc == DS_FACTOR_AUTO;
   set_factor_kernel(T, b->auto_factor ? 0 : ftc);
@@ -1227,6 +1240,15 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
     }
     cudaMemcpy(h->d_tasks_b, tasks_b.data(), sizeof(int4) * tasks_b.size(),
                cudaMemcpyHostToDevice);
+    std::vector<int4> tasks_p;
+    make_chol_tasks_p((n + 127) / 128, tasks_p);
+    h->ntasks_p = (int)tasks_p.size();
+    if ((rc = halloc(h, &h->d_tasks_p, tasks_p.size()))) {
+      free_cp(h);
+      return rc;
+    }
+    cudaMemcpy(h->d_tasks_p, tasks_p.data(), sizeof(int4) * tasks_p.size(),
+               cudaMemcpyHostToDevice);
   }
   h->prec_fp64 = prec == DS_PREC_FP64;
   {
@@ -1296,6 +1318,7 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
     lp.ntasks = h->ntasks;
     lp.tasks_b = h->d_tasks_b;
     lp.ntasks_b = h->ntasks_b;
+    lp.tasks_p = h->d_tasks_p;
     lp.nb = (n + 127) / 128;
     lp.status = h->d_acc + ACC_STATUS;
     lp.y = h->d_v3;

@@ -1167,17 +1167,22 @@ struct Ring {
   int mc[NS], mw[NS];
 };
 
-// Thread 0: D = sum_{c < nck} A_c B_c^T over chunks c of G sub-chunks each. A_c: from global at
-// pa(c) (G sub-chunks, contiguous) into the stage, or, with pa(c) == nullptr, resident in shared
-// memory at sa_res(c); B_c: from global at pb(c), or (pb(c) == nullptr) the stage's A. dep(c) is
-// waited before the copies of chunk c. Every issued copy is waited exactly once and every commit
-// is waited before return, so the phases stay in step; bfin is committed after the last MMA.
-// False if a wait gave up (error word raised); the accumulator is then not meaningful.
-template <int NS, int G, typename PA, typename RA, typename PB, typename DEP>
-__device__ bool stream(unsigned tmem, unsigned stg, Ring<NS>& rg, unsigned long long* bfin,
-                       int nck, PA pa, RA sa_res, PB pb, DEP dep, int* err,
-                       unsigned long long budget) {
+// Thread 0: D = sum_{c < nck} A_c B_c^T over chunks c of G sub-chunks each (and, with a second
+// B operand, D2 = sum_c A_c B2_c^T into tmem2). A_c: from global at pa(c) (G sub-chunks,
+// contiguous) into the stage, or, with pa(c) == nullptr, resident in shared memory at
+// sa_res(c); B_c: from global at pb(c), or (pb(c) == nullptr) the stage's A; B2_c: from global
+// at pb2(c) when not nullptr. A stage holds up to NOPS chunks, [A][B][B2]. The first product
+// starts the accumulators afresh unless acc_first. dep(c) is waited before the copies of chunk
+// c. Every issued copy is waited exactly once and every commit is waited before return, so the
+// phases stay in step; bfin is committed after the last MMA. False if a wait gave up (error word
+// raised); the accumulators are then not meaningful.
+template <int NS, int G, int NOPS, typename PA, typename RA, typename PB, typename PB2,
+          typename DEP>
+__device__ bool stream(unsigned tmem, unsigned tmem2, unsigned stg, Ring<NS>& rg,
+                       unsigned long long* bfin, int nck, bool acc_first, PA pa, RA sa_res, PB pb,
+                       PB2 pb2, DEP dep, int* err, unsigned long long budget) {
   constexpr unsigned kChunkBytes = G * kSubBytes;
+  constexpr unsigned kStage = NOPS * kChunkBytes;
   bool ok = true;
   int issued = 0;
   auto wait_mma = [&](int s) {
@@ -1185,7 +1190,13 @@ __device__ bool stream(unsigned tmem, unsigned stg, Ring<NS>& rg, unsigned long 
     ++rg.mw[s];
     return g;
   };
-  // stage s: [A chunk][B chunk] when A is streamed, [B chunk] otherwise
+  auto copy = [&](unsigned d, const float* src, int s) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+        "[%3];" ::"r"(d),
+        "l"(src), "r"(kChunkBytes), "r"(smem_u32(&rg.copy[s]))
+        : "memory");
+  };
   auto issue = [&](int c) {
     const int s = c % NS;
     while (rg.mw[s] < rg.mc[s])
@@ -1194,24 +1205,22 @@ __device__ bool stream(unsigned tmem, unsigned stg, Ring<NS>& rg, unsigned long 
     fence_proxy_async_global();
     const float* a = pa(c);
     const float* b = pb(c);
-    const unsigned bytes = (a ? kChunkBytes : 0u) + (b ? kChunkBytes : 0u);
-    const unsigned d = stg + s * (a ? 2u : 1u) * kChunkBytes;
+    const float* b2 = pb2(c);
+    const unsigned nops = (a ? 1u : 0u) + (b ? 1u : 0u) + (b2 ? 1u : 0u);
+    unsigned d = stg + s * kStage;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
                      smem_u32(&rg.copy[s])),
-                 "r"(bytes)
+                 "r"(nops * kChunkBytes)
                  : "memory");
-    if (a)
-      asm volatile(
-          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
-          "[%3];" ::"r"(d),
-          "l"(a), "r"(kChunkBytes), "r"(smem_u32(&rg.copy[s]))
-          : "memory");
-    if (b)
-      asm volatile(
-          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
-          "[%3];" ::"r"(d + (a ? kChunkBytes : 0u)),
-          "l"(b), "r"(kChunkBytes), "r"(smem_u32(&rg.copy[s]))
-          : "memory");
+    if (a) {
+      copy(d, a, s);
+      d += kChunkBytes;
+    }
+    if (b) {
+      copy(d, b, s);
+      d += kChunkBytes;
+    }
+    if (b2) copy(d, b2, s);
     return true;
   };
   while (ok && issued < nck && issued < NS) {
@@ -1225,13 +1234,17 @@ __device__ bool stream(unsigned tmem, unsigned stg, Ring<NS>& rg, unsigned long 
     if (!got) ok = false;
     if (ok) {
       tc::fence_after();
-      const bool sa_stream = pa(c) != nullptr, sb_stream = pb(c) != nullptr;
-      const unsigned d = stg + s * (sa_stream ? 2u : 1u) * kChunkBytes;
-      const unsigned sa = sa_stream ? d : sa_res(c);
-      const unsigned sb = sb_stream ? d + (sa_stream ? kChunkBytes : 0u) : sa;
+      const bool a_st = pa(c) != nullptr, b_st = pb(c) != nullptr, b2_st = pb2(c) != nullptr;
+      const unsigned d = stg + s * kStage;
+      const unsigned sa = a_st ? d : sa_res(c);
+      const unsigned sb = b_st ? d + (a_st ? kChunkBytes : 0u) : sa;
+      const unsigned sb2 = d + ((a_st ? 1u : 0u) + (b_st ? 1u : 0u)) * kChunkBytes;
 #pragma unroll
-      for (int g = 0; g < G; ++g)
-        mma_sub(tmem, sa + g * kSubBytes, sb + g * kSubBytes, c > 0 || g > 0);
+      for (int g = 0; g < G; ++g) {
+        const bool acc = acc_first || c > 0 || g > 0;
+        mma_sub(tmem, sa + g * kSubBytes, sb + g * kSubBytes, acc);
+        if (b2_st) mma_sub(tmem2, sa + g * kSubBytes, sb2 + g * kSubBytes, acc);
+      }
       tc::commit(&rg.mma[s]);
       ++rg.mc[s];
       if (c >= 1 && issued < nck) {   // refill the stage chunk c - 1 used
@@ -1258,8 +1271,15 @@ __device__ __forceinline__ void ring_init(Ring<NS>& rg) {
 
 }  // namespace tcb
 
-// G: sub-chunks per operand per stage of the K loop (stages of 2 G x 16 KB, 6 / G of them).
-template <int G>
+// G: sub-chunks per operand per stage of the single-block K loop (stages of 2 G x 16 KB, 6 / G of
+// them). PAIRS: block columns are taken two at a time (J0 = 2 p, J1 = 2 p + 1): DIAG(J0),
+// OFF(J1, J0), DIAG(J1), then OFF2(I; J0, J1) for every row block I below, which accumulates
+// the two blocks (I, J0) and (I, J1) over k < J0 with one stream of the A operand L_Ik (two
+// accumulators, stages [L_Ik][L_J0k][L_J1k] of 48 KB), finishes (I, J0), adds the k = J0 term
+// L_IJ0 L_J1J0^T to the second accumulator from the just-finished block held in shared memory,
+// and finishes (I, J1): the row panel I is read once per two block columns instead of once per
+// column.
+template <int G, bool PAIRS>
 __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __restrict__ descs,
                                                      const int2* __restrict__ tickets,
                                                      int nticket, int* __restrict__ head,
@@ -1269,6 +1289,7 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
   constexpr int NS = 6 / G;
   constexpr int TB = 64, LDS = TB + 1, RT = 4;
   constexpr int LDC = BS + 1;
+  constexpr unsigned kTmemCols = PAIRS ? 256u : 128u;
   extern __shared__ __align__(1024) unsigned char smb[];
   float* sm = reinterpret_cast<float*>(smb);
   __shared__ __align__(8) unsigned long long s_bfin;
@@ -1278,17 +1299,19 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
   const int tr = (tid / 16) * RT, tcl = (tid % 16) * RT;      // 64 x 64 register blocks
   const int arow = 32 * (warp & 3) + lane, acol = 64 * (warp >> 2);   // accumulator ownership
   // stage rings of thread 0 (barriers and their phase counters, used by thread 0 only)
-  __shared__ __align__(8) Ring<NS> ring_k;          // K-loop stages
-  __shared__ __align__(8) Ring<kXStages> ring_x;    // X stages of the OFF product
+  __shared__ __align__(8) Ring<NS> ring_k;          // single-block K-loop stages
+  __shared__ __align__(8) Ring<kXStages> ring_x;    // stages of the products with a resident A
+  __shared__ __align__(8) Ring<4> ring_p;           // paired K-loop stages (48 KB)
   unsigned long long* bfin = &s_bfin;
   if (tid == 0) {
     ring_init(ring_k);
     ring_init(ring_x);
+    ring_init(ring_p);
     mbar_init(bfin);
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
-                     smem_u32(&s_tmem))
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s_tmem)), "r"(kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -1298,6 +1321,71 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
   const unsigned tmem = s_tmem;
   const unsigned stg = smem_u32(smb);
   unsigned fph = 0u;   // parity of the next bfin completion (all threads)
+  float* Cs = sm;      // OFF epilogue: the C (or L) operand, 8 sub-chunks (128 KB)
+  // Every thread: wait for thread 0's products (bfin) when it streamed; false if any thread saw
+  // a failure (then the CTA leaves its ticket loop).
+  auto join = [&](bool streamed) {
+    bool bad = !s_ok;
+    if (streamed) {
+      const bool got = mbar_wait(bfin, fph, err, budget_ns);
+      fph ^= 1u;
+      bad = bad || !got;
+    }
+    return !__syncthreads_or(bad);
+  };
+  // C = A_block - v as the hi / lo A operand in shared memory (rows past n are zero)
+  auto form_c = [&](const float* A, int n, int I, int Jx, const float (&v)[64]) {
+    const int rg = I * BS + arow, c0 = Jx * BS;
+#pragma unroll
+    for (int e = 0; e < 64; e += 4) {
+      const int c = acol + e;
+      float x[4] = {0.f, 0.f, 0.f, 0.f};
+      if (rg < n) {
+        const float2 p0 = __ldcg(reinterpret_cast<const float2*>(A + (size_t)rg * n + c0 + c));
+        const float2 p1 =
+            __ldcg(reinterpret_cast<const float2*>(A + (size_t)rg * n + c0 + c + 2));
+        x[0] = p0.x - v[e];
+        x[1] = p0.y - v[e + 1];
+        x[2] = p1.x - v[e + 2];
+        x[3] = p1.y - v[e + 3];
+      }
+      tcb::put4_smem(Cs, arow, c, x[0], x[1], x[2], x[3]);
+    }
+    fence_proxy_async_shared();
+  };
+  // thread 0: D (at tm) (+)= [resident A in Cs] B^T, B = 8 sub-chunks from global at src
+  auto resident_product = [&](unsigned tm, const float* src, bool acc_first, const int* flag) {
+    return stream<kXStages, 1, 1>(
+        tm, 0u, stg + kCBytes, ring_x, bfin, BS / KS, acc_first,
+        [&](int) -> const float* { return nullptr; },
+        [&](int c) { return stg + (unsigned)c * kSubBytes; },
+        [&](int c) -> const float* { return src + (size_t)c * kSub; },
+        [&](int) -> const float* { return nullptr; },
+        [&](int c) { return c > 0 || wait_flag(flag, 1, err, budget_ns); }, err, budget_ns);
+  };
+  // L block -> A (row-major) and its slot
+  auto write_block = [&](float* A, float* Lp, int n, int nb, int I, int Jx, const float (&v)[64]) {
+    const int rg = I * BS + arow;
+    if (rg < n) {
+#pragma unroll
+      for (int e = 0; e < 64; e += 2)
+        __stcg(reinterpret_cast<float2*>(A + (size_t)rg * n + Jx * BS + acol + e),
+               make_float2(v[e], v[e + 1]));
+    }
+    float* S = Lp + slot(I, Jx) * kSlot;
+#pragma unroll
+    for (int e = 0; e < 64; e += 4)
+      tcb::put4(S, arow, acol + e, v[e], v[e + 1], v[e + 2], v[e + 3]);
+  };
+  auto publish = [&](int* f) {
+    fence_proxy_async_shared();
+    fence_proxy_async_global();
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      st_release(f, 1);
+    }
+  };
   // A wait that gives up raises the error word; every CTA then leaves its ticket loop (after its
   // copies and products in flight have completed), and the host reports DS_ERR_TIMEOUT.
   for (;;) {
@@ -1311,13 +1399,100 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
       continue;
     }
     const LinProblem& P = descs[pt.x]->lp;
-    const int4 tk = P.tasks_b[pt.y];
-    const bool diag = tk.y == 0;
-    const int I = tk.z, J = tk.w, nb = P.nb, n = P.n;
+    const int4 tk = PAIRS ? P.tasks_p[pt.y] : P.tasks_b[pt.y];
+    const int nb = P.nb, n = P.n;
     int* pdone = P.cnt;
     int* tdone = P.cnt + nb;
     float* A = (float*)P.A;
     float* Lp = (float*)P.Lp;
+    if (PAIRS && tk.y == 2) {
+      // ---- OFF2(I; J0, J1): blocks (I, J0) and (I, J1)
+      const int I = tk.z, J0 = tk.w, J1 = J0 + 1;
+      const int nck = (BS / KS) * J0;
+      if (tid == 0) {
+        s_ok = *(volatile int*)err == 0;
+        s_str = s_ok && nck > 0;
+        if (s_str) {
+          auto src = [&](int row, int c) {
+            return Lp + slot(row, c >> 3) * kSlot + (size_t)(c & 7) * kSub;
+          };
+          s_ok = stream<4, 1, 3>(
+              tmem, tmem + 128u, stg, ring_p, bfin, nck, false,
+              [&](int c) -> const float* { return src(I, c); }, [&](int) { return 0u; },
+              [&](int c) -> const float* { return src(J0, c); },
+              [&](int c) -> const float* { return src(J1, c); },
+              [&](int c) {
+                if (c & 7) return true;
+                const int kb = c >> 3;
+                return wait_flag(&tdone[I * nb + kb], 1, err, budget_ns) &&
+                       wait_flag(&tdone[J0 * nb + kb], 1, err, budget_ns) &&
+                       wait_flag(&tdone[J1 * nb + kb], 1, err, budget_ns);
+              },
+              err, budget_ns);
+        }
+      } else {
+        const int pr = I * BS + arow;
+        if (pr < n) {
+          const float* pa = A + (size_t)pr * n + J0 * BS + acol;
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(pa));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(pa + 32));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(pa + BS));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(pa + BS + 32));
+        }
+      }
+      __syncthreads();
+      if (!join(s_str)) break;
+      float v[64];
+      // block (I, J0): C = A - acc0, L = C X_J0^T
+      tc::fence_after();
+      if (nck > 0) {
+        tcb::tmem_row64(tmem, v);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 64; ++e) v[e] = 0.f;
+      }
+      tc::fence_before();
+      __syncthreads();
+      form_c(A, n, I, J0, v);
+      __syncthreads();
+      if (tid == 0) s_ok = resident_product(tmem, Lp + slot(J0, J0) * kSlot, false, &pdone[J0]);
+      __syncthreads();
+      if (!join(true)) break;
+      tc::fence_after();
+      tcb::tmem_row64(tmem, v);
+      tc::fence_before();
+      __syncthreads();
+      write_block(A, Lp, n, nb, I, J0, v);
+      // the finished L_IJ0 as the resident A operand of the k = J0 term of block (I, J1)
+#pragma unroll
+      for (int e = 0; e < 64; e += 4)
+        tcb::put4_smem(Cs, arow, acol + e, v[e], v[e + 1], v[e + 2], v[e + 3]);
+      publish(&tdone[I * nb + J0]);
+      if (tid == 0)
+        s_ok = resident_product(tmem + 128u, Lp + slot(J1, J0) * kSlot, nck > 0,
+                                &tdone[J1 * nb + J0]);
+      __syncthreads();
+      if (!join(true)) break;
+      // block (I, J1): C = A - acc1, L = C X_J1^T
+      tc::fence_after();
+      tcb::tmem_row64(tmem + 128u, v);
+      tc::fence_before();
+      __syncthreads();
+      form_c(A, n, I, J1, v);
+      __syncthreads();
+      if (tid == 0) s_ok = resident_product(tmem + 128u, Lp + slot(J1, J1) * kSlot, false, &pdone[J1]);
+      __syncthreads();
+      if (!join(true)) break;
+      tc::fence_after();
+      tcb::tmem_row64(tmem + 128u, v);
+      tc::fence_before();
+      __syncthreads();
+      write_block(A, Lp, n, nb, I, J1, v);
+      publish(&tdone[I * nb + J1]);
+      continue;
+    }
+    const bool diag = tk.y == 0;
+    const int I = tk.z, J = tk.w;
     constexpr int CPB = (BS / KS) / G;   // chunks per K block
     const int nck = CPB * J;
     // ---- K loop: acc = sum_{k<J} L_Ik L_Jk^T
@@ -1330,10 +1505,11 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
         auto src = [&](const float* base, int c) {
           return base + (size_t)(c / CPB) * kSlot + (c % CPB) * G * kSub;
         };
-        s_ok = stream<NS, G>(
-            tmem, stg, ring_k, bfin, nck, [&](int c) -> const float* { return src(si, c); },
-            [&](int) { return 0u; },
+        s_ok = stream<NS, G, 2>(
+            tmem, 0u, stg, ring_k, bfin, nck, false,
+            [&](int c) -> const float* { return src(si, c); }, [&](int) { return 0u; },
             [&](int c) -> const float* { return diag ? nullptr : src(sj, c); },
+            [&](int) -> const float* { return nullptr; },
             [&](int c) {
               if (c % CPB) return true;
               const int kb = c / CPB;
@@ -1353,13 +1529,7 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
       }
     }
     __syncthreads();
-    bool ok = s_ok;
-    if (s_str) {   // thread 0 streamed the K loop and committed bfin after its last product
-      const bool got = mbar_wait(bfin, fph, err, budget_ns);
-      fph ^= 1u;
-      ok = !__syncthreads_or(!got || !ok);
-    }
-    if (!ok) break;
+    if (!join(s_str)) break;
     tc::fence_after();
     float v[64];
     if (nck > 0) {
@@ -1521,73 +1691,25 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
       }
     } else {
       // ---- OFF(I, J): C = A_IJ - acc as hi / lo operand in shared memory, L_IJ = C X_JJ^T
-      float* Cs = sm;                 // 8 sub-chunks (128 KB)
-      const int c0 = J * BS;
-#pragma unroll
-      for (int e = 0; e < 64; e += 4) {
-        const int c = acol + e;
-        float x[4] = {0.f, 0.f, 0.f, 0.f};
-        if (rg < n) {
-          const float2 p0 = __ldcg(reinterpret_cast<const float2*>(A + (size_t)rg * n + c0 + c));
-          const float2 p1 =
-              __ldcg(reinterpret_cast<const float2*>(A + (size_t)rg * n + c0 + c + 2));
-          x[0] = p0.x - v[e];
-          x[1] = p0.y - v[e + 1];
-          x[2] = p1.x - v[e + 2];
-          x[3] = p1.y - v[e + 3];
-        }
-        tcb::put4_smem(Cs, arow, c, x[0], x[1], x[2], x[3]);
-      }
-      fence_proxy_async_shared();
+      form_c(A, n, I, J, v);
       __syncthreads();
-      if (tid == 0) {
-        const float* sx = Lp + slot(J, J) * kSlot;
-        s_ok = stream<kXStages, 1>(
-            tmem, stg + kCBytes, ring_x, bfin, BS / KS,
-            [&](int) -> const float* { return nullptr; },
-            [&](int c) { return stg + (unsigned)c * kSubBytes; },
-            [&](int c) -> const float* { return sx + (size_t)c * kSub; },
-            [&](int c) { return c > 0 || wait_flag(&pdone[J], 1, err, budget_ns); }, err,
-            budget_ns);
-      }
+      if (tid == 0) s_ok = resident_product(tmem, Lp + slot(J, J) * kSlot, false, &pdone[J]);
       __syncthreads();
-      {
-        const bool got = mbar_wait(bfin, fph, err, budget_ns);
-        fph ^= 1u;
-        if (__syncthreads_or(!got || !s_ok)) break;
-      }
+      if (!join(true)) break;
       tc::fence_after();
       tcb::tmem_row64(tmem, v);
       tc::fence_before();
       __syncthreads();
-      if (rg < n) {
-#pragma unroll
-        for (int e = 0; e < 64; e += 2)
-          __stcg(reinterpret_cast<float2*>(A + (size_t)rg * n + c0 + acol + e),
-                 make_float2(v[e], v[e + 1]));
-      }
-      float* S = Lp + slot(I, J) * kSlot;
-#pragma unroll
-      for (int e = 0; e < 64; e += 4)
-        tcb::put4(S, arow, acol + e, v[e], v[e + 1], v[e + 2], v[e + 3]);
+      write_block(A, Lp, n, nb, I, J, v);
     }
-    // generic writes (shared: before the next task's copies; global: before other CTAs' copies)
-    fence_proxy_async_shared();
-    fence_proxy_async_global();
-    __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      if (diag)
-        st_release(&pdone[J], 1);
-      else
-        st_release(&tdone[I * nb + J], 1);
-    }
+    publish(diag ? &pdone[J] : &tdone[I * nb + J]);
   }
   tc::fence_before();
   __syncthreads();
   if (warp == 0) {
     tc::fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                 : "memory");
   }
 }
 
@@ -1632,19 +1754,23 @@ void launch_fill_spd(const BatchTabs& B, cudaStream_t s) {
 template <typename T>
 void launch_chol_dag(const BatchTabs& B, cudaStream_t s) {
   if (sizeof(T) == 4 && B.factor_tc == 2) {
-    const int grid = std::min(B.n_chol_b, num_sms());
-    const int2* tickets = B.tcb_runs ? B.chol_br : B.chol_b;
-    if (B.tcb_g == 1) {
-      static PerDevice attr_b1;
-      set_smem_once(attr_b1, k_chol_tcb<1>, (int)tcb::kSmem);
-      k_chol_tcb<1><<<grid, 256, tcb::kSmem, s>>>(B.d, tickets, B.n_chol_b, B.words + 0,
-                                                  B.words + 5, 2000000000ull);
-    } else {
-      static PerDevice attr_b2;
-      set_smem_once(attr_b2, k_chol_tcb<2>, (int)tcb::kSmem);
-      k_chol_tcb<2><<<grid, 256, tcb::kSmem, s>>>(B.d, tickets, B.n_chol_b, B.words + 0,
-                                                  B.words + 5, 2000000000ull);
-    }
+    const int nticket = B.tcb_pairs ? B.n_chol_p : B.n_chol_b;
+    const int2* tickets = B.tcb_pairs ? B.chol_p : B.chol_b;
+    const int grid = std::min(nticket, num_sms());
+    auto go = [&](auto kern, PerDevice& attr) {
+      set_smem_once(attr, kern, (int)tcb::kSmem);
+      kern<<<grid, 256, tcb::kSmem, s>>>(B.d, tickets, nticket, B.words + 0, B.words + 5,
+                                         2000000000ull);
+    };
+    static PerDevice attr[4];
+    if (B.tcb_pairs && B.tcb_g == 1)
+      go(k_chol_tcb<1, true>, attr[0]);
+    else if (B.tcb_pairs)
+      go(k_chol_tcb<2, true>, attr[1]);
+    else if (B.tcb_g == 1)
+      go(k_chol_tcb<1, false>, attr[2]);
+    else
+      go(k_chol_tcb<2, false>, attr[3]);
     ++g_launches;
     return;
   }

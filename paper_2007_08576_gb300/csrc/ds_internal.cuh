@@ -66,6 +66,7 @@ struct LinProblem {
   int ntasks;
   const int4* tasks_b;  // the tasks of the 128 x 128 block factorisation (tensor cores)
   int ntasks_b;
+  const int4* tasks_p;  // the same with the block columns taken in pairs
   int nb;               // 128-row blocks
   double* status;
   void* y;
@@ -224,8 +225,9 @@ struct BatchTabs {
   int factor_tc;             // FP32 factorisation: 0 SIMT 64-tiles, 1 tensor cores 64-tiles,
                              // 2 tensor cores 128-blocks
   int tcb_g;                 // 128-block kernel: K sub-chunks of 16 per operand and stage (1, 2)
-  int tcb_runs;              // 128-block kernel: claim order with runs of tasks per problem
-  const int2* chol_br;       // the 128-block tickets in that order (n_chol_b of them)
+  int tcb_pairs;             // 128-block kernel: block columns taken in pairs
+  const int2* chol_p;        // the tickets of the paired block tasks, in claim order
+  int n_chol_p;
   int jtj;                   // ICP J^T W J on the tensor cores (BF16, FP32 accumulation)
   int max_tasks;             // max factorisation tasks over the problems
   int max_nt;                // max tile rows over the problems

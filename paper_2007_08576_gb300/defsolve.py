@@ -251,8 +251,8 @@ def ds_batch_set_tracing(b, on=True):
     _check("ds_batch_set_tracing", lib().ds_batch_set_tracing(b, 1 if on else 0))
 
 
-FACTOR_KERNELS = ["simt64", "tc64", "tc128_stage64k", "tc128_stage32k", "tc128_stage64k_runs",
-                  "tc128_stage32k_runs"]
+FACTOR_KERNELS = ["simt64", "tc64", "tc128_stage64k", "tc128_stage32k", "tc128_stage64k_pairs",
+                  "tc128_stage32k_pairs"]
 
 
 def ds_batch_tune(b, reps=3):

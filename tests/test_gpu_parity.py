@@ -420,11 +420,11 @@ def test_bounded_waits_give_up_and_the_context_stays_usable(d, tiny):
 
 
 @pytest.mark.parametrize("ftc", [1, 2, 3, 4, 5],
-                         ids=["tiles64", "blocks128", "blocks128s", "blocks128r", "blocks128sr"])
+                         ids=["tiles64", "blocks128", "blocks128s", "blocks128p", "blocks128sp"])
 @pytest.mark.parametrize("prec", [1, 2])
 def test_tensor_core_factor_matches_oracle_tiny_and_ragged(d, tiny, mid, prec, ftc):
     """FP32 factorisation on tcgen05 (three TF32 terms per product): the same parity bar, with
-    64 x 64 tiles and with 128 x 128 blocks."""
+    64 x 64 tiles, with 128 x 128 blocks and with the 128-block columns taken in pairs."""
     for sc in (tiny, mid):
         fr = sc.frames[0]
         p = d.default_params(precision=prec, factor_tc=ftc)
@@ -437,7 +437,8 @@ def test_tensor_core_factor_matches_oracle_tiny_and_ragged(d, tiny, mid, prec, f
         s.close()
 
 
-@pytest.mark.parametrize("ftc", [1, 2, 3], ids=["tiles64", "blocks128", "blocks128s"])
+@pytest.mark.parametrize("ftc", [1, 2, 3, 4, 5],
+                         ids=["tiles64", "blocks128", "blocks128s", "blocks128p", "blocks128sp"])
 def test_tensor_core_factor_full_size_frame(d, ftc):
     sc = scene(CONFIGS["seq_320x240_n256"], 1000)
     fr = sc.frames[0]
