@@ -95,9 +95,11 @@ typedef struct {
                              * tiles; on the tensor cores (tcgen05 kind::tf32, each product as
                              * three TF32 terms hi*hi + hi*lo + lo*hi, FP32-level accuracy) with
                              * 1 = 64 x 64 tiles, 2 = 128 x 128 blocks streamed in three 64 KB
-                             * operand stages, 3 = the same in six 32 KB stages, 4 / 5 = 2 / 3
-                             * with the block columns taken in pairs (each row panel streamed once
-                             * per two block columns, two accumulators); DS_FACTOR_AUTO (default) = picked per
+                             * operand stages, 3 = the same in six 32 KB stages, 4 = 2 with the
+                             * block columns taken in pairs (each row panel streamed once per two
+                             * block columns, two accumulators), 5 = 128 x 128 blocks with each
+                             * task's K loop (one streaming warp, two tensor-memory accumulators)
+                             * overlapping the previous task's epilogue; DS_FACTOR_AUTO (default) = picked per
                              * batch by timing the six on the batch's sizes at its first solve
                              * (ds_batch_tune). Ignored in DS_PREC_FP64. Handles of one batch
                              * must agree.                                                        */

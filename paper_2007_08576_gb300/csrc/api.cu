@@ -297,19 +297,24 @@ void destroy_batch(ds_batch_s* b);
 
 // The factor kernels the tuner chooses from, by kernel index: SIMT 64 x 64 tiles, tensor cores
 // with 64 x 64 tiles, tensor cores with 128 x 128 blocks in three 64 KB stages, and in six
-// 32 KB stages; indices 4 and 5 are the 128-block kernel (64 KB / 32 KB stages of its single
-// block tasks) with its block columns taken in pairs (one stream of each row panel per pair).
+// 32 KB stages; 4 is the 128-block kernel (64 KB stages of its single block tasks) with its block
+// columns taken in pairs (one stream of each row panel per pair); 5 the 128-block kernel whose
+// K loops (one streaming warp, two tensor-memory accumulators) overlap the epilogues of the
+// previous tasks (eight warps).
 constexpr int kFactorKernels = 6;
 void set_factor_kernel(BatchTabs& T, int k) {
   static const int ftc[kFactorKernels] = {0, 1, 2, 2, 2, 2}, g[kFactorKernels] = {2, 2, 2, 1, 2, 1},
-                   pairs[kFactorKernels] = {0, 0, 0, 0, 1, 1};
+                   pairs[kFactorKernels] = {0, 0, 0, 0, 1, 0},
+                   pipe[kFactorKernels] = {0, 0, 0, 0, 0, 1};
   T.factor_tc = ftc[k];
   T.tcb_g = g[k];
   T.tcb_pairs = pairs[k];
+  T.tcb_pipe = pipe[k];
 }
 int factor_kernel_of(const BatchTabs& T) {
   if (T.factor_tc < 2) return T.factor_tc;
-  return (T.tcb_g == 2 ? 2 : 3) + (T.tcb_pairs ? 2 : 0);
+  if (T.tcb_pipe) return 5;
+  return T.tcb_pairs ? 4 : (T.tcb_g == 2 ? 2 : 3);
 }
 
 // The handle's batches stop running: its control points change or (leaving) it goes away, and

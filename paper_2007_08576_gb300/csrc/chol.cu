@@ -112,7 +112,17 @@ __device__ __forceinline__ double rsqrt_newton<double>(double p) {
 // zeros above the diagonal): for every pair of H x H diagonal blocks starting at s0 = 2 H g,
 // Tm = L21 X11 and X21 = -X22 Tm, with L21 = L[s0 + H.., s0..], X11 / X22 the diagonal blocks.
 // Each thread forms K consecutive outputs of a row (K = 1..4) with the shared row operand reused.
-template <typename T, int TB, int H>
+// Barrier of the threads that run the tile code: the whole block (BAR 0), or the 256 threads of
+// named barrier BAR in a block whose other warps have another role.
+template <int BAR>
+__device__ __forceinline__ void bsync() {
+  if constexpr (BAR == 0)
+    __syncthreads();
+  else
+    asm volatile("bar.sync %0, 256;" ::"n"(BAR) : "memory");
+}
+
+template <typename T, int TB, int H, int BAR = 0>
 __device__ __forceinline__ void inverse_level(const T* L, T* X, T* Tm) {
   constexpr int LDS = TB + 1, TOTAL = TB * H / 2;
   constexpr int K = TOTAL >= 1024 ? 4 : (TOTAL >= 512 ? 2 : 1);
@@ -132,7 +142,7 @@ __device__ __forceinline__ void inverse_level(const T* L, T* X, T* Tm) {
 #pragma unroll
     for (int k = 0; k < K; ++k) Tm[e + k] = v[k];
   }
-  __syncthreads();
+  bsync<BAR>();
   if (tid < NT) {
     const int e = tid * K, g = e / (H * H), r = (e % (H * H)) / H, c = e % H, s0 = 2 * H * g;
     T v[K];
@@ -147,7 +157,7 @@ __device__ __forceinline__ void inverse_level(const T* L, T* X, T* Tm) {
 #pragma unroll
     for (int k = 0; k < K; ++k) X[(s0 + H + r) * LDS + s0 + c + k] = -v[k];
   }
-  __syncthreads();
+  bsync<BAR>();
 }
 
 // Register-blocked Cholesky of a diagonal tile with its inverse. Thread (ty, tx) = (tid / 16,
@@ -163,7 +173,7 @@ __device__ __forceinline__ void inverse_level(const T* L, T* X, T* Tm) {
 // X21 = -X22 (L21 X11), for h = PB, 2 PB, 4 PB (two barriers per level). Output: L (lower part)
 // and X = L^-1 in shared memory with row stride TB + 1; X must be zero on entry. Scratch: Pt
 // (PB x (TB + 16 / sizeof(T))), Dsm (PB x PB), Tm (TB x TB / 4).
-template <typename T, int TB>
+template <typename T, int TB, int BAR = 0>
 __device__ void potrf_regs(T (&a)[TileCfg<T, TB>::RT][TileCfg<T, TB>::RT], T* L, T* X, T* Pt,
                            T* Dsm, T* Tm, int row0, double* status) {
   constexpr int RT = TileCfg<T, TB>::RT, PB = 2 * RT, NBK = TB / PB, LDS = TB + 1;
@@ -235,7 +245,7 @@ __device__ void potrf_regs(T (&a)[TileCfg<T, TB>::RT][TileCfg<T, TB>::RT], T* L,
         }
       }
     }
-    __syncthreads();
+    bsync<BAR>();
     // (2) panel below the block: threads tx = 2 kb, 2 kb + 1 (adjacent lanes), rows past the block
     if ((tx >> 1) == kb && tr >= c0 + PB) {
       const unsigned pair = 3u << (lane & 30);
@@ -265,7 +275,7 @@ __device__ void potrf_regs(T (&a)[TileCfg<T, TB>::RT][TileCfg<T, TB>::RT], T* L,
         }
       }
     }
-    __syncthreads();
+    bsync<BAR>();
     // (4) rank-PB update of the register blocks right of the panel (lower part)
     if (tc >= c0 + PB && tc <= tr + RT - 1) {
 #pragma unroll
@@ -290,9 +300,9 @@ __device__ void potrf_regs(T (&a)[TileCfg<T, TB>::RT][TileCfg<T, TB>::RT], T* L,
     }
   }
   // off-diagonal blocks of the inverse by recursive doubling (X zero above the diagonal)
-  inverse_level<T, TB, PB>(L, X, Tm);
-  inverse_level<T, TB, 2 * PB>(L, X, Tm);
-  inverse_level<T, TB, 4 * PB>(L, X, Tm);
+  inverse_level<T, TB, PB, BAR>(L, X, Tm);
+  inverse_level<T, TB, 2 * PB, BAR>(L, X, Tm);
+  inverse_level<T, TB, 4 * PB, BAR>(L, X, Tm);
   static_assert(8 * PB == TB, "three doubling levels");
 }
 
@@ -342,6 +352,9 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
     }
   }
   return true;
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
 // Orders this thread's earlier generic-proxy global writes before later async-proxy (bulk copy)
 // reads of the same data by any thread that synchronises with it.
@@ -1167,61 +1180,90 @@ struct Ring {
   int mc[NS], mw[NS];
 };
 
+// Thread 0: the copies of chunk c into its stage of the ring (A, B, B2 from global at pa(c),
+// pb(c), pb2(c) where not nullptr, in that order), after the stage's previous products are done
+// with it and dep(c) holds. False if a wait gave up (nothing of chunk c issued then).
+template <int NS, int G, int NOPS, typename PA, typename PB, typename PB2, typename DEP>
+__device__ bool issue_chunk(int c, unsigned stg, Ring<NS>& rg, PA& pa, PB& pb, PB2& pb2, DEP& dep,
+                            int* err, unsigned long long budget) {
+  constexpr unsigned kChunkBytes = G * kSubBytes;
+  constexpr unsigned kStage = NOPS * kChunkBytes;
+  const int s = c % NS;
+  while (rg.mw[s] < rg.mc[s]) {   // the stage's previous MMAs are done with it
+    const bool g = mbar_wait(&rg.mma[s], (unsigned)(rg.mw[s] & 1), err, budget);
+    ++rg.mw[s];
+    if (!g) return false;
+  }
+  if (!dep(c)) return false;   // dep(c) orders the copies after what it acquired (proxy fence)
+  const float* a = pa(c);
+  const float* b = pb(c);
+  const float* b2 = pb2(c);
+  const unsigned nops = (a ? 1u : 0u) + (b ? 1u : 0u) + (b2 ? 1u : 0u);
+  unsigned d = stg + s * kStage;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                   smem_u32(&rg.copy[s])),
+               "r"(nops * kChunkBytes)
+               : "memory");
+  auto copy = [&](unsigned dst, const float* src) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+        "[%3];" ::"r"(dst),
+        "l"(src), "r"(kChunkBytes), "r"(smem_u32(&rg.copy[s]))
+        : "memory");
+  };
+  if (a) {
+    copy(d, a);
+    d += kChunkBytes;
+  }
+  if (b) {
+    copy(d, b);
+    d += kChunkBytes;
+  }
+  if (b2) copy(d, b2);
+  return true;
+}
+
+// Thread 0: issues the first min(NS, nck) chunks of a stream ahead of its products (so that the
+// copies overlap other work of the CTA); returns how many were issued. After a failed wait the
+// copies already issued are waited for (bounded) and -1 is returned.
+template <int NS, int G, int NOPS, typename PA, typename PB, typename PB2, typename DEP>
+__device__ int prime(unsigned stg, Ring<NS>& rg, int nck, PA pa, PB pb, PB2 pb2, DEP dep,
+                     int* err, unsigned long long budget) {
+  int issued = 0;
+  while (issued < nck && issued < NS) {
+    if (!issue_chunk<NS, G, NOPS>(issued, stg, rg, pa, pb, pb2, dep, err, budget)) {
+      for (int c = 0; c < issued; ++c) {
+        mbar_wait(&rg.copy[c % NS], rg.cph[c % NS], err, budget);
+        rg.cph[c % NS] ^= 1u;
+      }
+      return -1;
+    }
+    ++issued;
+  }
+  return issued;
+}
+
 // Thread 0: D = sum_{c < nck} A_c B_c^T over chunks c of G sub-chunks each (and, with a second
 // B operand, D2 = sum_c A_c B2_c^T into tmem2). A_c: from global at pa(c) (G sub-chunks,
 // contiguous) into the stage, or, with pa(c) == nullptr, resident in shared memory at
 // sa_res(c); B_c: from global at pb(c), or (pb(c) == nullptr) the stage's A; B2_c: from global
-// at pb2(c) when not nullptr. A stage holds up to NOPS chunks, [A][B][B2]. The first product
-// starts the accumulators afresh unless acc_first. dep(c) is waited before the copies of chunk
-// c. Every issued copy is waited exactly once and every commit is waited before return, so the
-// phases stay in step; bfin is committed after the last MMA. False if a wait gave up (error word
-// raised); the accumulators are then not meaningful.
+// at pb2(c) when not nullptr. A stage holds up to NOPS chunks, [A][B][B2]. The first `pre`
+// chunks were issued by prime(). The first product starts the accumulators afresh unless
+// acc_first. dep(c) is waited before the copies of chunk c. Every issued copy is waited exactly
+// once and every commit is waited before return, so the phases stay in step; bfin is committed
+// after the last MMA. False if a wait gave up (error word raised); the accumulators are then not
+// meaningful.
 template <int NS, int G, int NOPS, typename PA, typename RA, typename PB, typename PB2,
           typename DEP>
 __device__ bool stream(unsigned tmem, unsigned tmem2, unsigned stg, Ring<NS>& rg,
-                       unsigned long long* bfin, int nck, bool acc_first, PA pa, RA sa_res, PB pb,
-                       PB2 pb2, DEP dep, int* err, unsigned long long budget) {
+                       unsigned long long* bfin, int nck, int pre, bool acc_first, PA pa,
+                       RA sa_res, PB pb, PB2 pb2, DEP dep, int* err, unsigned long long budget) {
   constexpr unsigned kChunkBytes = G * kSubBytes;
   constexpr unsigned kStage = NOPS * kChunkBytes;
   bool ok = true;
-  int issued = 0;
-  auto wait_mma = [&](int s) {
-    const bool g = mbar_wait(&rg.mma[s], (unsigned)(rg.mw[s] & 1), err, budget);
-    ++rg.mw[s];
-    return g;
-  };
-  auto copy = [&](unsigned d, const float* src, int s) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
-        "[%3];" ::"r"(d),
-        "l"(src), "r"(kChunkBytes), "r"(smem_u32(&rg.copy[s]))
-        : "memory");
-  };
+  int issued = pre;
   auto issue = [&](int c) {
-    const int s = c % NS;
-    while (rg.mw[s] < rg.mc[s])
-      if (!wait_mma(s)) return false;   // the stage's previous MMAs are done with it
-    if (!dep(c)) return false;
-    fence_proxy_async_global();
-    const float* a = pa(c);
-    const float* b = pb(c);
-    const float* b2 = pb2(c);
-    const unsigned nops = (a ? 1u : 0u) + (b ? 1u : 0u) + (b2 ? 1u : 0u);
-    unsigned d = stg + s * kStage;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
-                     smem_u32(&rg.copy[s])),
-                 "r"(nops * kChunkBytes)
-                 : "memory");
-    if (a) {
-      copy(d, a, s);
-      d += kChunkBytes;
-    }
-    if (b) {
-      copy(d, b, s);
-      d += kChunkBytes;
-    }
-    if (b2) copy(d, b2, s);
-    return true;
+    return issue_chunk<NS, G, NOPS>(c, stg, rg, pa, pb, pb2, dep, err, budget);
   };
   while (ok && issued < nck && issued < NS) {
     ok = issue(issued);
@@ -1255,7 +1297,142 @@ __device__ bool stream(unsigned tmem, unsigned tmem2, unsigned stg, Ring<NS>& rg
   }
   tc::commit(bfin);
   for (int s = 0; s < NS; ++s)
-    while (rg.mw[s] < rg.mc[s]) wait_mma(s);
+    while (rg.mw[s] < rg.mc[s]) {
+      mbar_wait(&rg.mma[s], (unsigned)(rg.mw[s] & 1), err, budget);
+      ++rg.mw[s];
+    }
+  return ok;
+}
+
+// A K-loop ring whose copies (one producer thread) and products (one consumer thread) run
+// decoupled: full[s] completes when the copies into stage s have landed, empty[s] when the
+// products that read it are done. Chunk c of a loop is the ring's (pos + c)-th use overall (pos:
+// the chunks through the ring before, counted alike by both threads). nissued / pdone: how many
+// chunks the producer issued, once it has stopped (reset before each loop).
+template <int NS>
+struct WRing {
+  unsigned long long full[NS], empty[NS];
+  int nissued, pdone;
+};
+
+template <int NS>
+__device__ __forceinline__ void wring_init(WRing<NS>& r) {
+  for (int s = 0; s < NS; ++s) {
+    mbar_init(&r.full[s]);
+    mbar_init(&r.empty[s]);
+  }
+  r.nissued = 0;
+  r.pdone = 0;
+}
+
+// Producer: for c < nck, once the stage's previous products are done and dep(c) holds, the
+// copies of chunk c (A, B, B2 from global at pa(c), pb(c), pb2(c) where not nullptr) into its
+// stage. Stops early (and says so in nissued) if a wait gives up or the error word is raised.
+template <int NS, int G, int NOPS, typename PA, typename PB, typename PB2, typename DEP>
+__device__ void ws_produce(unsigned stg, WRing<NS>& r, unsigned pos, int nck, PA pa, PB pb,
+                           PB2 pb2, DEP dep, int* err, unsigned long long budget) {
+  constexpr unsigned kChunkBytes = G * kSubBytes;
+  constexpr unsigned kStage = NOPS * kChunkBytes;
+  int c = 0;
+  if (*(volatile int*)err == 0) {
+    for (; c < nck; ++c) {
+      const unsigned q = pos + (unsigned)c, s = q % NS, g = q / NS;
+      if (g >= 1 && !mbar_wait(&r.empty[s], (g - 1) & 1u, err, budget)) break;
+      if (!dep(c)) break;
+      const float* a = pa(c);
+      const float* b = pb(c);
+      const float* b2 = pb2(c);
+      const unsigned nops = (a ? 1u : 0u) + (b ? 1u : 0u) + (b2 ? 1u : 0u);
+      unsigned d = stg + s * kStage;
+      const unsigned bar = smem_u32(&r.full[s]);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                   "r"(nops * kChunkBytes)
+                   : "memory");
+      auto copy = [&](unsigned dst, const float* src) {
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+            "[%3];" ::"r"(dst),
+            "l"(src), "r"(kChunkBytes), "r"(bar)
+            : "memory");
+      };
+      if (a) {
+        copy(d, a);
+        d += kChunkBytes;
+      }
+      if (b) {
+        copy(d, b);
+        d += kChunkBytes;
+      }
+      if (b2) copy(d, b2);
+    }
+  }
+  *(volatile int*)&r.nissued = c;
+  __threadfence_block();
+  *(volatile int*)&r.pdone = 1;
+}
+
+// Consumer: D (+)= sum_c A_c B_c^T (and D2 with B2 into tmem2) over the chunks as their copies
+// land, each stage released to the producer by a commit on empty[s]; bfin is committed after the
+// last product. If the producer stopped short, the chunks it did issue are waited for and
+// released, and false is returned (the accumulators are then not meaningful).
+template <int NS, int G, int NOPS, typename PA, typename PB, typename PB2>
+__device__ bool ws_consume(unsigned tmem, unsigned tmem2, unsigned stg, WRing<NS>& r,
+                           unsigned pos, unsigned long long* bfin, int nck, PA pa, PB pb,
+                           PB2 pb2, int* err, unsigned long long budget) {
+  constexpr unsigned kChunkBytes = G * kSubBytes;
+  constexpr unsigned kStage = NOPS * kChunkBytes;
+  const volatile int* vdone = &r.pdone;
+  const volatile int* vn = &r.nissued;
+  bool ok = true;
+  int c = 0;
+  for (; c < nck; ++c) {
+    const unsigned q = pos + (unsigned)c, s = q % NS, g = q / NS;
+    bool got = mbar_test(&r.full[s], g & 1u);
+    if (!got) {
+      const unsigned long long t0 = globaltimer();
+      for (;;) {
+        if (mbar_test(&r.full[s], g & 1u)) {
+          got = true;
+          break;
+        }
+        if (*vdone && c >= *vn) break;   // the producer stopped before chunk c
+        if (globaltimer() - t0 > budget) {
+          atomicExch(err, 1);
+          break;
+        }
+      }
+    }
+    if (!got) {
+      ok = false;
+      break;
+    }
+    tc::fence_after();
+    const bool a_st = pa(c) != nullptr, b_st = pb(c) != nullptr, b2_st = pb2(c) != nullptr;
+    const unsigned d = stg + s * kStage;
+    const unsigned sa = d;
+    const unsigned sb = b_st ? d + (a_st ? kChunkBytes : 0u) : sa;
+    const unsigned sb2 = d + ((a_st ? 1u : 0u) + (b_st ? 1u : 0u)) * kChunkBytes;
+#pragma unroll
+    for (int gg = 0; gg < G; ++gg) {
+      const bool acc = c > 0 || gg > 0;
+      mma_sub(tmem, sa + gg * kSubBytes, sb + gg * kSubBytes, acc);
+      if (b2_st) mma_sub(tmem2, sa + gg * kSubBytes, sb2 + gg * kSubBytes, acc);
+    }
+    tc::commit(&r.empty[s]);
+  }
+  if (!ok) {
+    // the producer's last word, then its chunks past c: wait for their copies, release stages
+    const unsigned long long t0 = globaltimer();
+    while (!*vdone && globaltimer() - t0 <= budget) {
+    }
+    const int n_iss = *vdone ? *vn : c;
+    for (int k = c; k < n_iss; ++k) {
+      const unsigned q = pos + (unsigned)k, s = q % NS, g = q / NS;
+      mbar_wait(&r.full[s], g & 1u, err, budget);
+      mbar_arrive(&r.empty[s]);
+    }
+  }
+  tc::commit(bfin);
   return ok;
 }
 
@@ -1294,19 +1471,19 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
   float* sm = reinterpret_cast<float*>(smb);
   __shared__ __align__(8) unsigned long long s_bfin;
   __shared__ unsigned s_tmem;
-  __shared__ int s_t, s_ok, s_str;
+  __shared__ int s_t, s_ok, s_pre;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tr = (tid / 16) * RT, tcl = (tid % 16) * RT;      // 64 x 64 register blocks
   const int arow = 32 * (warp & 3) + lane, acol = 64 * (warp >> 2);   // accumulator ownership
   // stage rings of thread 0 (barriers and their phase counters, used by thread 0 only)
-  __shared__ __align__(8) Ring<NS> ring_k;          // single-block K-loop stages
+  __shared__ __align__(8) WRing<NS> wring_k;        // single-block K-loop stages
   __shared__ __align__(8) Ring<kXStages> ring_x;    // stages of the products with a resident A
-  __shared__ __align__(8) Ring<4> ring_p;           // paired K-loop stages (48 KB)
+  __shared__ __align__(8) WRing<4> wring_p;         // paired K-loop stages (48 KB)
   unsigned long long* bfin = &s_bfin;
   if (tid == 0) {
-    ring_init(ring_k);
+    wring_init(wring_k);
     ring_init(ring_x);
-    ring_init(ring_p);
+    wring_init(wring_p);
     mbar_init(bfin);
   }
   if (warp == 0) {
@@ -1322,6 +1499,7 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
   const unsigned stg = smem_u32(smb);
   unsigned fph = 0u;   // parity of the next bfin completion (all threads)
   float* Cs = sm;      // OFF epilogue: the C (or L) operand, 8 sub-chunks (128 KB)
+  float* Tb = sm;      // a 128 x 128 FP32 block, swizzled (first 64 KB, before / after Cs is used)
   // Every thread: wait for thread 0's products (bfin) when it streamed; false if any thread saw
   // a failure (then the CTA leaves its ticket loop).
   auto join = [&](bool streamed) {
@@ -1333,49 +1511,105 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
     }
     return !__syncthreads_or(bad);
   };
-  // C = A_block - v as the hi / lo A operand in shared memory (rows past n are zero)
-  auto form_c = [&](const float* A, int n, int I, int Jx, const float (&v)[64]) {
-    const int rg = I * BS + arow, c0 = Jx * BS;
+  // Row-major 128 x 128 FP32 block in shared memory with its float4 groups permuted by row & 7:
+  // whole rows (a warp, float2 per lane) and row segments (the row's owner thread, float4) are
+  // then both conflict-free.
+  auto tpos = [](int r, int c) { return r * BS + ((((c >> 2) ^ (r & 7)) << 2) | (c & 3)); };
+  // A block (rows I BS.., columns Jx BS..) into registers with coalesced loads: warp w takes
+  // rows 16 w .. 16 w + 15, lane l columns 2 l, 2 l + 1, 64 + 2 l, 65 + 2 l (zero past n; n even)
+  auto load_rows = [&](const float* A, int n, int I, int Jx, float (&a)[64]) {
+    const int c0 = Jx * BS + 2 * lane;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int r = I * BS + 16 * warp + q;
+      float2 p0 = make_float2(0.f, 0.f), p1 = p0;
+      if (r < n) {
+        const float* row = A + (size_t)r * n;
+        if (c0 < n) p0 = __ldcg(reinterpret_cast<const float2*>(row + c0));
+        if (c0 + 64 < n) p1 = __ldcg(reinterpret_cast<const float2*>(row + c0 + 64));
+      }
+      a[4 * q] = p0.x;
+      a[4 * q + 1] = p0.y;
+      a[4 * q + 2] = p1.x;
+      a[4 * q + 3] = p1.y;
+    }
+  };
+  // the registers of load_rows -> Tb
+  auto stage_rows = [&](const float (&a)[64]) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int r = 16 * warp + q;
+      *reinterpret_cast<float2*>(Tb + tpos(r, 2 * lane)) = make_float2(a[4 * q], a[4 * q + 1]);
+      *reinterpret_cast<float2*>(Tb + tpos(r, 64 + 2 * lane)) =
+          make_float2(a[4 * q + 2], a[4 * q + 3]);
+    }
+  };
+  // C = A_block - v (A_block staged in Tb; zero on rows past n) as the hi / lo A operand in Cs;
+  // v is overwritten with C
+  auto form_c = [&](int n, int I, float (&v)[64]) {
+    const bool in = I * BS + arow < n;
 #pragma unroll
     for (int e = 0; e < 64; e += 4) {
-      const int c = acol + e;
-      float x[4] = {0.f, 0.f, 0.f, 0.f};
-      if (rg < n) {
-        const float2 p0 = __ldcg(reinterpret_cast<const float2*>(A + (size_t)rg * n + c0 + c));
-        const float2 p1 =
-            __ldcg(reinterpret_cast<const float2*>(A + (size_t)rg * n + c0 + c + 2));
-        x[0] = p0.x - v[e];
-        x[1] = p0.y - v[e + 1];
-        x[2] = p1.x - v[e + 2];
-        x[3] = p1.y - v[e + 3];
-      }
-      tcb::put4_smem(Cs, arow, c, x[0], x[1], x[2], x[3]);
+      const float4 t = *reinterpret_cast<const float4*>(Tb + tpos(arow, acol + e));
+      v[e] = in ? t.x - v[e] : 0.f;
+      v[e + 1] = in ? t.y - v[e + 1] : 0.f;
+      v[e + 2] = in ? t.z - v[e + 2] : 0.f;
+      v[e + 3] = in ? t.w - v[e + 3] : 0.f;
     }
+    __syncthreads();   // Tb read before Cs (which covers it) is written
+#pragma unroll
+    for (int e = 0; e < 64; e += 4)
+      tcb::put4_smem(Cs, arow, acol + e, v[e], v[e + 1], v[e + 2], v[e + 3]);
     fence_proxy_async_shared();
   };
-  // thread 0: D (at tm) (+)= [resident A in Cs] B^T, B = 8 sub-chunks from global at src
-  auto resident_product = [&](unsigned tm, const float* src, bool acc_first, const int* flag) {
-    return stream<kXStages, 1, 1>(
-        tm, 0u, stg + kCBytes, ring_x, bfin, BS / KS, acc_first,
-        [&](int) -> const float* { return nullptr; },
-        [&](int c) { return stg + (unsigned)c * kSubBytes; },
-        [&](int c) -> const float* { return src + (size_t)c * kSub; },
-        [&](int) -> const float* { return nullptr; },
-        [&](int c) { return c > 0 || wait_flag(flag, 1, err, budget_ns); }, err, budget_ns);
+  auto no_src = [](int) -> const float* { return nullptr; };
+  // after flags were acquired: the copies (async proxy) that follow see the data they guard
+  auto acquired = [](bool ok) {
+    fence_proxy_async_global();
+    return ok;
   };
-  // L block -> A (row-major) and its slot
-  auto write_block = [&](float* A, float* Lp, int n, int nb, int I, int Jx, const float (&v)[64]) {
-    const int rg = I * BS + arow;
-    if (rg < n) {
+  auto res_a = [&](int c) { return stg + (unsigned)c * kSubBytes; };
+  // thread 0: the first stages of D (+)= [resident A in Cs] B^T, B = 8 sub-chunks at src, issued
+  // after flag (overlapping the copies with the CTA's epilogue work); returns the count or -1
+  auto prime_product = [&](const float* src, const int* flag) {
+    return prime<kXStages, 1, 1>(
+        stg + kCBytes, ring_x, BS / KS, no_src,
+        [&](int c) -> const float* { return src + (size_t)c * kSub; }, no_src,
+        [&](int c) { return c > 0 || acquired(wait_flag(flag, 1, err, budget_ns)); }, err,
+        budget_ns);
+  };
+  // thread 0: D (at tm) (+)= [resident A in Cs] B^T, the first `pre` stages already issued
+  auto resident_product = [&](unsigned tm, const float* src, bool acc_first, const int* flag,
+                              int pre) {
+    return stream<kXStages, 1, 1>(
+        tm, 0u, stg + kCBytes, ring_x, bfin, BS / KS, pre, acc_first, no_src, res_a,
+        [&](int c) -> const float* { return src + (size_t)c * kSub; }, no_src,
+        [&](int c) { return c > 0 || acquired(wait_flag(flag, 1, err, budget_ns)); }, err,
+        budget_ns);
+  };
+  // L block v -> A (row-major, through Tb: coalesced rows) and its slot
+  auto write_block = [&](float* A, float* Lp, int n, int I, int Jx, const float (&v)[64]) {
 #pragma unroll
-      for (int e = 0; e < 64; e += 2)
-        __stcg(reinterpret_cast<float2*>(A + (size_t)rg * n + Jx * BS + acol + e),
-               make_float2(v[e], v[e + 1]));
-    }
+    for (int e = 0; e < 64; e += 4)
+      *reinterpret_cast<float4*>(Tb + tpos(arow, acol + e)) =
+          make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
     float* S = Lp + slot(I, Jx) * kSlot;
 #pragma unroll
     for (int e = 0; e < 64; e += 4)
       tcb::put4(S, arow, acol + e, v[e], v[e + 1], v[e + 2], v[e + 3]);
+    __syncthreads();
+    const int c0 = Jx * BS + 2 * lane;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int r = 16 * warp + q, rg = I * BS + r;
+      if (rg < n) {
+        float* row = A + (size_t)rg * n;
+        __stcg(reinterpret_cast<float2*>(row + c0),
+               *reinterpret_cast<const float2*>(Tb + tpos(r, 2 * lane)));
+        __stcg(reinterpret_cast<float2*>(row + c0 + 64),
+               *reinterpret_cast<const float2*>(Tb + tpos(r, 64 + 2 * lane)));
+      }
+    }
   };
   auto publish = [&](int* f) {
     fence_proxy_async_shared();
@@ -1388,8 +1622,14 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
   };
   // A wait that gives up raises the error word; every CTA then leaves its ticket loop (after its
   // copies and products in flight have completed), and the host reports DS_ERR_TIMEOUT.
+  // K loops: thread 32 issues the copies, thread 0 the products; pos_*: chunks through each ring
+  unsigned pos_k = 0u, pos_p = 0u;
   for (;;) {
-    if (tid == 0) s_t = atomicAdd(head, 1);
+    if (tid == 0) {
+      s_t = atomicAdd(head, 1);
+      wring_k.pdone = 0;
+      wring_p.pdone = 0;
+    }
     __syncthreads();
     const int t = s_t;
     if (t >= nticket) break;
@@ -1405,44 +1645,44 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
     int* tdone = P.cnt + nb;
     float* A = (float*)P.A;
     float* Lp = (float*)P.Lp;
+    float a[64];   // the task's block of A, loaded while the K loop runs
+    float v[64];   // this thread's accumulator row segment
     if (PAIRS && tk.y == 2) {
       // ---- OFF2(I; J0, J1): blocks (I, J0) and (I, J1)
       const int I = tk.z, J0 = tk.w, J1 = J0 + 1;
       const int nck = (BS / KS) * J0;
-      if (tid == 0) {
-        s_ok = *(volatile int*)err == 0;
-        s_str = s_ok && nck > 0;
-        if (s_str) {
-          auto src = [&](int row, int c) {
-            return Lp + slot(row, c >> 3) * kSlot + (size_t)(c & 7) * kSub;
-          };
-          s_ok = stream<4, 1, 3>(
-              tmem, tmem + 128u, stg, ring_p, bfin, nck, false,
-              [&](int c) -> const float* { return src(I, c); }, [&](int) { return 0u; },
-              [&](int c) -> const float* { return src(J0, c); },
-              [&](int c) -> const float* { return src(J1, c); },
+      load_rows(A, n, I, J0, a);
+      const bool str = nck > 0;
+      if (str && (tid == 0 || tid == 32)) {
+        auto src = [&](int row, int c) {
+          return Lp + slot(row, c >> 3) * kSlot + (size_t)(c & 7) * kSub;
+        };
+        auto pa = [&](int c) -> const float* { return src(I, c); };
+        auto pb = [&](int c) -> const float* { return src(J0, c); };
+        auto pb2 = [&](int c) -> const float* { return src(J1, c); };
+        if (tid == 32)
+          ws_produce<4, 1, 3>(
+              stg, wring_p, pos_p, nck, pa, pb, pb2,
               [&](int c) {
                 if (c & 7) return true;
                 const int kb = c >> 3;
-                return wait_flag(&tdone[I * nb + kb], 1, err, budget_ns) &&
-                       wait_flag(&tdone[J0 * nb + kb], 1, err, budget_ns) &&
-                       wait_flag(&tdone[J1 * nb + kb], 1, err, budget_ns);
+                return acquired(wait_flag(&tdone[I * nb + kb], 1, err, budget_ns) &&
+                                wait_flag(&tdone[J0 * nb + kb], 1, err, budget_ns) &&
+                                wait_flag(&tdone[J1 * nb + kb], 1, err, budget_ns));
               },
               err, budget_ns);
-        }
-      } else {
-        const int pr = I * BS + arow;
-        if (pr < n) {
-          const float* pa = A + (size_t)pr * n + J0 * BS + acol;
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(pa));
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(pa + 32));
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(pa + BS));
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(pa + BS + 32));
-        }
+        else
+          s_ok = ws_consume<4, 1, 3>(tmem, tmem + 128u, stg, wring_p, pos_p, bfin, nck, pa, pb,
+                                     pb2, err, budget_ns);
       }
+      if (tid == 0 && !str) s_ok = *(volatile int*)err == 0;
+      if (str) pos_p += (unsigned)nck;
       __syncthreads();
-      if (!join(s_str)) break;
-      float v[64];
+      if (!join(str)) break;
+      if (tid == 0) {   // X_J0 J0's first stages while the C operand is formed
+        s_pre = prime_product(Lp + slot(J0, J0) * kSlot, &pdone[J0]);
+        s_ok = s_pre >= 0;
+      }
       // block (I, J0): C = A - acc0, L = C X_J0^T
       tc::fence_after();
       if (nck > 0) {
@@ -1452,42 +1692,55 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
         for (int e = 0; e < 64; ++e) v[e] = 0.f;
       }
       tc::fence_before();
+      stage_rows(a);
       __syncthreads();
-      form_c(A, n, I, J0, v);
+      load_rows(A, n, I, J1, a);   // block (I, J1) of A, used after the next two products
+      form_c(n, I, v);
       __syncthreads();
-      if (tid == 0) s_ok = resident_product(tmem, Lp + slot(J0, J0) * kSlot, false, &pdone[J0]);
+      if (tid == 0 && s_ok)
+        s_ok = resident_product(tmem, Lp + slot(J0, J0) * kSlot, false, &pdone[J0], s_pre);
       __syncthreads();
-      if (!join(true)) break;
+      if (!join(s_pre >= 0)) break;
+      if (tid == 0) {   // the k = J0 term's B operand while L_IJ0 is written
+        s_pre = prime_product(Lp + slot(J1, J0) * kSlot, &tdone[J1 * nb + J0]);
+        s_ok = s_pre >= 0;
+      }
       tc::fence_after();
       tcb::tmem_row64(tmem, v);
       tc::fence_before();
-      __syncthreads();
-      write_block(A, Lp, n, nb, I, J0, v);
+      write_block(A, Lp, n, I, J0, v);
+      __syncthreads();   // Tb read before Cs (which covers it) is written
       // the finished L_IJ0 as the resident A operand of the k = J0 term of block (I, J1)
 #pragma unroll
       for (int e = 0; e < 64; e += 4)
         tcb::put4_smem(Cs, arow, acol + e, v[e], v[e + 1], v[e + 2], v[e + 3]);
       publish(&tdone[I * nb + J0]);
-      if (tid == 0)
+      if (tid == 0 && s_ok)
         s_ok = resident_product(tmem + 128u, Lp + slot(J1, J0) * kSlot, nck > 0,
-                                &tdone[J1 * nb + J0]);
+                                &tdone[J1 * nb + J0], s_pre);
       __syncthreads();
-      if (!join(true)) break;
+      if (!join(s_pre >= 0)) break;
+      if (tid == 0) {
+        s_pre = prime_product(Lp + slot(J1, J1) * kSlot, &pdone[J1]);
+        s_ok = s_pre >= 0;
+      }
       // block (I, J1): C = A - acc1, L = C X_J1^T
       tc::fence_after();
       tcb::tmem_row64(tmem + 128u, v);
       tc::fence_before();
+      stage_rows(a);
       __syncthreads();
-      form_c(A, n, I, J1, v);
+      form_c(n, I, v);
       __syncthreads();
-      if (tid == 0) s_ok = resident_product(tmem + 128u, Lp + slot(J1, J1) * kSlot, false, &pdone[J1]);
+      if (tid == 0 && s_ok)
+        s_ok = resident_product(tmem + 128u, Lp + slot(J1, J1) * kSlot, false, &pdone[J1],
+                                s_pre);
       __syncthreads();
-      if (!join(true)) break;
+      if (!join(s_pre >= 0)) break;
       tc::fence_after();
       tcb::tmem_row64(tmem + 128u, v);
       tc::fence_before();
-      __syncthreads();
-      write_block(A, Lp, n, nb, I, J1, v);
+      write_block(A, Lp, n, I, J1, v);
       publish(&tdone[I * nb + J1]);
       continue;
     }
@@ -1495,43 +1748,40 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
     const int I = tk.z, J = tk.w;
     constexpr int CPB = (BS / KS) / G;   // chunks per K block
     const int nck = CPB * J;
+    load_rows(A, n, I, J, a);
     // ---- K loop: acc = sum_{k<J} L_Ik L_Jk^T
-    if (tid == 0) {
-      s_ok = *(volatile int*)err == 0;
-      s_str = s_ok && nck > 0;
-      if (s_str) {
-        const float* si = Lp + slot(I, 0) * kSlot;
-        const float* sj = Lp + slot(J, 0) * kSlot;
-        auto src = [&](const float* base, int c) {
-          return base + (size_t)(c / CPB) * kSlot + (c % CPB) * G * kSub;
-        };
-        s_ok = stream<NS, G, 2>(
-            tmem, 0u, stg, ring_k, bfin, nck, false,
-            [&](int c) -> const float* { return src(si, c); }, [&](int) { return 0u; },
-            [&](int c) -> const float* { return diag ? nullptr : src(sj, c); },
-            [&](int) -> const float* { return nullptr; },
+    const bool str = nck > 0;
+    if (str && (tid == 0 || tid == 32)) {
+      const float* si = Lp + slot(I, 0) * kSlot;
+      const float* sj = Lp + slot(J, 0) * kSlot;
+      auto src = [&](const float* base, int c) {
+        return base + (size_t)(c / CPB) * kSlot + (c % CPB) * G * kSub;
+      };
+      auto pa = [&](int c) -> const float* { return src(si, c); };
+      auto pb = [&](int c) -> const float* { return diag ? nullptr : src(sj, c); };
+      if (tid == 32)
+        ws_produce<NS, G, 2>(
+            stg, wring_k, pos_k, nck, pa, pb, no_src,
             [&](int c) {
               if (c % CPB) return true;
               const int kb = c / CPB;
-              return wait_flag(&tdone[I * nb + kb], 1, err, budget_ns) &&
-                     (diag || wait_flag(&tdone[J * nb + kb], 1, err, budget_ns));
+              return acquired(wait_flag(&tdone[I * nb + kb], 1, err, budget_ns) &&
+                              (diag || wait_flag(&tdone[J * nb + kb], 1, err, budget_ns)));
             },
             err, budget_ns);
-      }
-    } else {
-      // while thread 0 streams the K loop, the others pull this block of A (the epilogue's C =
-      // A - acc) into L2: each thread its row's 64 columns, two 128-byte lines
-      const int pr = I * BS + arow, pc = J * BS + acol;
-      if (pr < n) {
-        const float* pa = A + (size_t)pr * n + pc;
-        if (pc < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(pa));
-        if (pc + 32 < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(pa + 32));
-      }
+      else
+        s_ok = ws_consume<NS, G, 2>(tmem, 0u, stg, wring_k, pos_k, bfin, nck, pa, pb, no_src, err,
+                                    budget_ns);
     }
+    if (tid == 0 && !str) s_ok = *(volatile int*)err == 0;
+    if (str) pos_k += (unsigned)nck;
     __syncthreads();
-    if (!join(s_str)) break;
+    if (!join(str)) break;
+    if (!diag && tid == 0) {   // X_JJ's first stages while the C operand is formed
+      s_pre = prime_product(Lp + slot(J, J) * kSlot, &pdone[J]);
+      s_ok = s_pre >= 0;
+    }
     tc::fence_after();
-    float v[64];
     if (nck > 0) {
       tcb::tmem_row64(tmem, v);
     } else {
@@ -1554,13 +1804,23 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
       float* Dsm = Pt + 8 * TileCfg<float, TB>::LDT;
       float* Tm = Dsm + 64;
       const int r0 = J * BS;
-      // lower part of C inside the matrix; identity on the padding past n; zero above
+      // the block of A (rows by warps) into Cs, then each row's owner keeps the lower part of
+      // C = A - acc inside the matrix, the identity on the padding past n and zero above
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        float* row = Cs + (16 * warp + q) * LDC;
+        row[2 * lane] = a[4 * q];
+        row[2 * lane + 1] = a[4 * q + 1];
+        row[64 + 2 * lane] = a[4 * q + 2];
+        row[65 + 2 * lane] = a[4 * q + 3];
+      }
+      __syncthreads();
 #pragma unroll
       for (int e = 0; e < 64; ++e) {
         const int c = acol + e;
         float x;
         if (rg < n && r0 + c < n)
-          x = c <= arow ? __ldcg(A + (size_t)rg * n + r0 + c) - v[e] : 0.f;
+          x = c <= arow ? Cs[arow * LDC + c] - v[e] : 0.f;
         else
           x = c == arow ? 1.f : 0.f;
         Cs[arow * LDC + c] = x;
@@ -1691,16 +1951,18 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
       }
     } else {
       // ---- OFF(I, J): C = A_IJ - acc as hi / lo operand in shared memory, L_IJ = C X_JJ^T
-      form_c(A, n, I, J, v);
+      stage_rows(a);
       __syncthreads();
-      if (tid == 0) s_ok = resident_product(tmem, Lp + slot(J, J) * kSlot, false, &pdone[J]);
+      form_c(n, I, v);
       __syncthreads();
-      if (!join(true)) break;
+      if (tid == 0 && s_ok)
+        s_ok = resident_product(tmem, Lp + slot(J, J) * kSlot, false, &pdone[J], s_pre);
+      __syncthreads();
+      if (!join(s_pre >= 0)) break;
       tc::fence_after();
       tcb::tmem_row64(tmem, v);
       tc::fence_before();
-      __syncthreads();
-      write_block(A, Lp, n, nb, I, J, v);
+      write_block(A, Lp, n, I, J, v);
     }
     publish(diag ? &pdone[J] : &tdone[I * nb + J]);
   }
@@ -1710,6 +1972,493 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
     tc::fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
                  : "memory");
+  }
+}
+
+// ----------------------------------------------------------------------------- pipelined blocks
+// The 128 x 128 block factorisation with the K loop of one task overlapping the epilogue of the
+// previous one: warp 8 (one thread) claims the tickets and streams each task's K loop into one
+// of two tensor-memory accumulators; warps 0..7 take the finished accumulators in the same order
+// and run the epilogues (DIAG: SIMT Cholesky and inverse of the block; OFF: C = A - acc and
+// L = C X^T on the tensor cores, in two K halves so that the epilogue's shared memory and the
+// K loop's stages fit side by side). Same tasks, slots, flags and results as k_chol_tcb.
+namespace tcp {
+constexpr int kThreads = 288;
+constexpr int kNS = 3;                                 // K-loop stages of 32 KB (A, B)
+constexpr int TB = 64, LDS = TB + 1;
+constexpr int kTile = TB * LDS;                        // floats of a 64 x 65 tile
+constexpr int kPt = 8 * TileCfg<float, TB>::LDT;       // potrf scratch (floats)
+constexpr int kScratch = kPt + 64 + TB * TB / 4;
+constexpr unsigned kEBytes = 104u * 1024u;             // epilogue area
+static_assert(6 * kTile * 4 + kScratch * 4 <= (int)kEBytes, "DIAG tiles fit");
+static_assert(4 * tcb::kSubBytes + 2 * tcb::kSubBytes <= kEBytes, "OFF half + X stages fit");
+constexpr unsigned kRBytes = kNS * 2 * tcb::kSubBytes;  // K-loop stages (96 KB)
+constexpr unsigned kSmem = kEBytes + kRBytes;
+}  // namespace tcp
+
+// named barrier 1 over the 256 epilogue threads, with an OR of a predicate
+__device__ __forceinline__ void ebar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ bool ebar_or(bool p) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %1, 0;\n\tbar.red.or.pred q, 1, 256, p;\n\t"
+      "selp.b32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((int)p)
+      : "memory");
+  return r != 0;
+}
+__global__ __launch_bounds__(tcp::kThreads, 1) void k_chol_tcp(
+    const ProbDesc* const* __restrict__ descs, const int2* __restrict__ tickets, int nticket,
+    int* __restrict__ head, int* __restrict__ err, unsigned long long budget_ns) {
+  using namespace tcb;
+  using tcp::TB;
+  using tcp::LDS;
+  constexpr int RT = 4;
+  extern __shared__ __align__(1024) unsigned char smb[];
+  float* sm = reinterpret_cast<float*>(smb);
+  __shared__ __align__(8) unsigned long long bar_task[2], bar_full[2], bar_empty[2], bar_efin;
+  __shared__ __align__(8) Ring<tcp::kNS> ring_k;   // streamer
+  __shared__ __align__(8) Ring<2> ring_x;          // epilogue thread 0
+  __shared__ int4 s_task[2];                       // (problem, type, I, J); type -1: no more
+  __shared__ unsigned s_tmem;
+  __shared__ int s_ok, s_pre;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&bar_task[b]);
+      mbar_init(&bar_full[b]);
+      mbar_init(&bar_empty[b]);
+    }
+    mbar_init(&bar_efin);
+    ring_init(ring_k);
+    ring_init(ring_x);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
+                     smem_u32(&s_tmem))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const unsigned tmem = s_tmem;
+  const unsigned ebase = smem_u32(smb), rbase = ebase + tcp::kEBytes;
+  auto no_src = [](int) -> const float* { return nullptr; };
+  auto acquired = [](bool ok) {
+    fence_proxy_async_global();
+    return ok;
+  };
+  if (warp == 8) {
+    // ---- streamer: claim, publish the task, K loop into accumulator u & 1
+    if (lane == 0) {
+      int u = 0;
+      auto finish = [&](int b) {
+        s_task[b] = make_int4(-1, -1, 0, 0);
+        mbar_arrive(&bar_task[b]);
+        mbar_arrive(&bar_full[b]);
+      };
+      for (;;) {
+        const int b = u & 1;
+        if (u >= 2 && !mbar_wait(&bar_empty[b], (unsigned)(((u >> 1) - 1) & 1), err, budget_ns)) {
+          finish(b);
+          break;
+        }
+        const int t = atomicAdd(head, 1);
+        if (t >= nticket || *(volatile int*)err) {
+          finish(b);
+          break;
+        }
+        const int2 pt = tickets[t];
+        if (!descs[pt.x]) continue;   // not in this solve
+        const LinProblem& P = descs[pt.x]->lp;
+        const int4 tk = P.tasks_b[pt.y];
+        const bool diag = tk.y == 0;
+        const int I = tk.z, J = tk.w, nb = P.nb;
+        const int* tdone = P.cnt + nb;
+        const float* Lp = (const float*)P.Lp;
+        s_task[b] = make_int4(pt.x, tk.y, I, J);
+        mbar_arrive(&bar_task[b]);   // release: the epilogue may load the task's block of A
+        const int nck = (BS / KS) * J;
+        if (nck == 0) {
+          mbar_arrive(&bar_full[b]);
+        } else {
+          const float* si = Lp + slot(I, 0) * kSlot;
+          const float* sj = Lp + slot(J, 0) * kSlot;
+          const bool ok = stream<tcp::kNS, 1, 2>(
+              tmem + 128u * b, 0u, rbase, ring_k, &bar_full[b], nck, 0, false,
+              [&](int c) -> const float* { return si + (size_t)(c >> 3) * kSlot + (c & 7) * kSub; },
+              [&](int) { return 0u; },
+              [&](int c) -> const float* {
+                return diag ? nullptr : sj + (size_t)(c >> 3) * kSlot + (c & 7) * kSub;
+              },
+              no_src,
+              [&](int c) {
+                if (c & 7) return true;
+                const int kb = c >> 3;
+                return acquired(wait_flag(&tdone[I * nb + kb], 1, err, budget_ns) &&
+                                (diag || wait_flag(&tdone[J * nb + kb], 1, err, budget_ns)));
+              },
+              err, budget_ns);
+          (void)ok;   // a failed wait raised the error word; the epilogue sees it
+        }
+        ++u;
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue (warps 0..7)
+    const int tr = (tid / 16) * RT, tcl = (tid % 16) * RT;               // 64 x 64 register blocks
+    const int arow = 32 * (warp & 3) + lane, acol = 64 * (warp >> 2);   // accumulator ownership
+    float* Tb = sm;       // OFF: the block of A (swizzled rows), later the block of L
+    float* Ch = sm;       // OFF: one K half of C as the hi / lo A operand (4 sub-chunks, 64 KB)
+    const unsigned xstg = ebase + 4u * kSubBytes;   // OFF: stages of X (2 x 16 KB)
+    float* C00 = sm;      // DIAG: 64 x 65 tiles of the block (C01 is not kept), then of L
+    float* C10 = C00 + tcp::kTile;
+    float* C11 = C10 + tcp::kTile;
+    float* X00 = C11 + tcp::kTile;
+    float* X11 = X00 + tcp::kTile;
+    float* Tt = X11 + tcp::kTile;   // L10 X00, then X10
+    float* Pt = Tt + tcp::kTile;
+    float* Dsm = Pt + tcp::kPt;
+    float* Tm = Dsm + 64;
+    auto tpos = [](int r, int c) { return r * BS + ((((c >> 2) ^ (r & 7)) << 2) | (c & 3)); };
+    unsigned efph = 0u;   // parity of the next bar_efin completion
+    // thread 0: the first stages of a K-half product, B = 4 sub-chunks at src (after flag)
+    auto half_prime = [&](const float* src, const int* flag) {
+      return prime<2, 1, 1>(
+          xstg, ring_x, 4, no_src, [&](int c) -> const float* { return src + (size_t)c * kSub; },
+          no_src,
+          [&](int c) {
+            return c > 0 || flag == nullptr || acquired(wait_flag(flag, 1, err, budget_ns));
+          },
+          err, budget_ns);
+    };
+    // thread 0: D (+)= [C half in Ch] B^T, the first `pre` stages already issued
+    auto half_product = [&](unsigned tm, const float* src, bool acc_first, int pre) {
+      return stream<2, 1, 1>(
+          tm, 0u, xstg, ring_x, &bar_efin, 4, pre, acc_first, no_src,
+          [&](int c) { return ebase + (unsigned)c * kSubBytes; },
+          [&](int c) -> const float* { return src + (size_t)c * kSub; }, no_src,
+          [&](int) { return true; }, err, budget_ns);
+    };
+    // every epilogue thread: wait for thread 0's product (when it streamed); false on a failure
+    auto ejoin = [&](bool streamed) {
+      bool bad = !s_ok;
+      if (streamed) {
+        const bool got = mbar_wait(&bar_efin, efph, err, budget_ns);
+        efph ^= 1u;
+        bad = bad || !got;
+      }
+      return !ebar_or(bad);
+    };
+    auto epublish = [&](int* f) {
+      fence_proxy_async_shared();
+      fence_proxy_async_global();
+      ebar();
+      if (tid == 0) {
+        __threadfence();
+        st_release(f, 1);
+      }
+    };
+    float v[64];
+    for (int e = 0;; ++e) {
+      const int b = e & 1;
+      const unsigned ph = (unsigned)((e >> 1) & 1);
+      const bool got = mbar_wait(&bar_task[b], ph, err, budget_ns);
+      const int4 tk = s_task[b];
+      if (ebar_or(!got || tk.y < 0)) break;
+      const LinProblem& P = descs[tk.x]->lp;
+      const int I = tk.z, J = tk.w, nb = P.nb, n = P.n;
+      int* pdone = P.cnt;
+      int* tdone = P.cnt + nb;
+      float* A = (float*)P.A;
+      float* Lp = (float*)P.Lp;
+      const unsigned tmb = tmem + 128u * b;
+      if (tk.y == 0) {
+        // ---- DIAG(J): block (J, J) of A into the tiles (rows by warps, coalesced)
+        const int r0 = J * BS, c0 = r0 + 2 * lane;
+#pragma unroll 4
+        for (int q = 0; q < 16; ++q) {
+          const int r = 16 * warp + q, rg = r0 + r;
+          float2 p0 = make_float2(0.f, 0.f), p1 = p0;
+          if (rg < n) {
+            const float* row = A + (size_t)rg * n;
+            if (c0 < n) p0 = __ldcg(reinterpret_cast<const float2*>(row + c0));
+            if (r >= TB && c0 + 64 < n) p1 = __ldcg(reinterpret_cast<const float2*>(row + c0 + 64));
+          }
+          float* t0 = r < TB ? C00 + r * LDS : C10 + (r - TB) * LDS;
+          t0[2 * lane] = p0.x;
+          t0[2 * lane + 1] = p0.y;
+          if (r >= TB) {
+            float* t1 = C11 + (r - TB) * LDS;
+            t1[2 * lane] = p1.x;
+            t1[2 * lane + 1] = p1.y;
+          }
+        }
+        for (int e2 = tid; e2 < tcp::kTile; e2 += 256) {
+          X00[e2] = 0.f;
+          X11[e2] = 0.f;
+        }
+        const bool okf = mbar_wait(&bar_full[b], ph, err, budget_ns);
+        if (ebar_or(!okf || *(volatile int*)err != 0)) break;
+        tc::fence_after();
+        if (J > 0) {
+          tcb::tmem_row64(tmb, v);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 64; ++q) v[q] = 0.f;
+        }
+        tc::fence_before();
+        ebar();
+        if (tid == 0) mbar_arrive(&bar_empty[b]);   // the accumulator is read
+        // C = A - acc: lower part inside the matrix, identity on the padding past n, zero above
+        const int rg = r0 + arow;
+        if (arow >= TB || acol == 0) {
+          float* tl = arow < TB ? C00 + arow * LDS : (acol == 0 ? C10 : C11) + (arow - TB) * LDS;
+#pragma unroll
+          for (int q = 0; q < 64; ++q) {
+            const int c = acol + q;
+            float x;
+            if (rg < n && r0 + c < n)
+              x = c <= arow ? tl[q] - v[q] : 0.f;
+            else
+              x = c == arow ? 1.f : 0.f;
+            tl[q] = x;
+          }
+        }
+        ebar();
+        float a[RT][RT], w[RT][RT];
+#pragma unroll
+        for (int p = 0; p < RT; ++p)
+#pragma unroll
+          for (int q = 0; q < RT; ++q) a[p][q] = C00[(tr + p) * LDS + tcl + q];
+        ebar();   // C00 read before its Cholesky factor overwrites it
+        potrf_regs<float, TB, 1>(a, C00, X00, Pt, Dsm, Tm, r0, P.status);
+        // L10 = C10 X00^T, in place
+#pragma unroll
+        for (int p = 0; p < RT; ++p)
+#pragma unroll
+          for (int q = 0; q < RT; ++q) w[p][q] = 0.f;
+        for (int m = 0; m < TB; ++m) {
+          float x[RT], y[RT];
+#pragma unroll
+          for (int p = 0; p < RT; ++p) x[p] = C10[(tr + p) * LDS + m];
+#pragma unroll
+          for (int q = 0; q < RT; ++q) y[q] = X00[(tcl + q) * LDS + m];
+#pragma unroll
+          for (int p = 0; p < RT; ++p)
+#pragma unroll
+            for (int q = 0; q < RT; ++q) w[p][q] += x[p] * y[q];
+        }
+        ebar();
+#pragma unroll
+        for (int p = 0; p < RT; ++p)
+#pragma unroll
+          for (int q = 0; q < RT; ++q) C10[(tr + p) * LDS + tcl + q] = w[p][q];
+        ebar();
+        // C11 - L10 L10^T, factored in place
+#pragma unroll
+        for (int p = 0; p < RT; ++p)
+#pragma unroll
+          for (int q = 0; q < RT; ++q) a[p][q] = C11[(tr + p) * LDS + tcl + q];
+        for (int m = 0; m < TB; ++m) {
+          float x[RT], y[RT];
+#pragma unroll
+          for (int p = 0; p < RT; ++p) x[p] = C10[(tr + p) * LDS + m];
+#pragma unroll
+          for (int q = 0; q < RT; ++q) y[q] = C10[(tcl + q) * LDS + m];
+#pragma unroll
+          for (int p = 0; p < RT; ++p)
+#pragma unroll
+            for (int q = 0; q < RT; ++q) a[p][q] -= x[p] * y[q];
+        }
+        ebar();   // C11 read before its factor overwrites it
+        potrf_regs<float, TB, 1>(a, C11, X11, Pt, Dsm, Tm, r0 + TB, P.status);
+        // T = L10 X00, then X10 = -X11 T (in place)
+#pragma unroll
+        for (int p = 0; p < RT; ++p)
+#pragma unroll
+          for (int q = 0; q < RT; ++q) w[p][q] = 0.f;
+        for (int m = 0; m < TB; ++m) {
+          float x[RT], y[RT];
+#pragma unroll
+          for (int p = 0; p < RT; ++p) x[p] = C10[(tr + p) * LDS + m];
+#pragma unroll
+          for (int q = 0; q < RT; ++q) y[q] = X00[m * LDS + tcl + q];
+#pragma unroll
+          for (int p = 0; p < RT; ++p)
+#pragma unroll
+            for (int q = 0; q < RT; ++q) w[p][q] += x[p] * y[q];
+        }
+#pragma unroll
+        for (int p = 0; p < RT; ++p)
+#pragma unroll
+          for (int q = 0; q < RT; ++q) Tt[(tr + p) * LDS + tcl + q] = w[p][q];
+        ebar();
+#pragma unroll
+        for (int p = 0; p < RT; ++p)
+#pragma unroll
+          for (int q = 0; q < RT; ++q) w[p][q] = 0.f;
+        for (int m = 0; m < TB; ++m) {
+          float x[RT], y[RT];
+#pragma unroll
+          for (int p = 0; p < RT; ++p) x[p] = X11[(tr + p) * LDS + m];
+#pragma unroll
+          for (int q = 0; q < RT; ++q) y[q] = Tt[m * LDS + tcl + q];
+#pragma unroll
+          for (int p = 0; p < RT; ++p)
+#pragma unroll
+            for (int q = 0; q < RT; ++q) w[p][q] -= x[p] * y[q];
+        }
+        ebar();
+#pragma unroll
+        for (int p = 0; p < RT; ++p)
+#pragma unroll
+          for (int q = 0; q < RT; ++q) Tt[(tr + p) * LDS + tcl + q] = w[p][q];
+        ebar();
+        // outputs: L_JJ -> A (lower, in range), X00 / X11 -> Dinv, X_JJ -> slot (J, J)
+        const int nt64 = P.nt;
+        float* D0 = (float*)P.Dinv + (size_t)(2 * J) * TB * TB;
+        for (int e2 = tid; e2 < TB * TB; e2 += 256) {
+          const int r = e2 / TB, c = e2 % TB;
+          __stcg(D0 + e2, c <= r ? X00[r * LDS + c] : 0.f);
+          if (2 * J + 1 < nt64) __stcg(D0 + TB * TB + e2, c <= r ? X11[r * LDS + c] : 0.f);
+        }
+        for (int e2 = tid; e2 < BS * BS; e2 += 256) {
+          const int r = e2 / BS, c = e2 % BS;
+          if (c > r || r0 + r >= n) continue;
+          const float l = r < TB ? C00[r * LDS + c]
+                                 : (c < TB ? C10[(r - TB) * LDS + c] : C11[(r - TB) * LDS + c - TB]);
+          __stcg(A + (size_t)(r0 + r) * n + r0 + c, l);
+        }
+        float* S = Lp + slot(J, J) * kSlot;
+        for (int e2 = tid; e2 < BS * BS / 4; e2 += 256) {
+          const int r = e2 / (BS / 4), k = 4 * (e2 % (BS / 4));
+          float x4[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int c = k + q;
+            float x = 0.f;
+            if (c <= r) {
+              if (r < TB) x = X00[r * LDS + c];
+              else if (c < TB) x = Tt[(r - TB) * LDS + c];
+              else x = X11[(r - TB) * LDS + c - TB];
+            }
+            x4[q] = x;
+          }
+          tcb::put4(S, r, k, x4[0], x4[1], x4[2], x4[3]);
+        }
+        epublish(&pdone[J]);
+        continue;
+      }
+      // ---- OFF(I, J): block (I, J) of A into Tb (its columns lie inside the matrix)
+      {
+        const int c0 = J * BS + 2 * lane;
+#pragma unroll 4
+        for (int q = 0; q < 16; ++q) {
+          const int r = 16 * warp + q, rg = I * BS + r;
+          float2 p0 = make_float2(0.f, 0.f), p1 = p0;
+          if (rg < n) {
+            const float* row = A + (size_t)rg * n;
+            p0 = __ldcg(reinterpret_cast<const float2*>(row + c0));
+            p1 = __ldcg(reinterpret_cast<const float2*>(row + c0 + 64));
+          }
+          *reinterpret_cast<float2*>(Tb + tpos(r, 2 * lane)) = p0;
+          *reinterpret_cast<float2*>(Tb + tpos(r, 64 + 2 * lane)) = p1;
+        }
+      }
+      const bool okf = mbar_wait(&bar_full[b], ph, err, budget_ns);
+      if (ebar_or(!okf || *(volatile int*)err != 0)) break;
+      tc::fence_after();
+      if (J > 0) {
+        tcb::tmem_row64(tmb, v);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 64; ++q) v[q] = 0.f;
+      }
+      tc::fence_before();
+      const float* sx = Lp + slot(J, J) * kSlot;
+      if (tid == 0) {   // X_JJ's first stages while C is formed
+        s_pre = half_prime(sx, &pdone[J]);
+        s_ok = s_pre >= 0;
+      }
+      // C = A - acc on this thread's row segment (zero on rows past n)
+      {
+        const bool in = I * BS + arow < n;
+#pragma unroll
+        for (int q = 0; q < 64; q += 4) {
+          const float4 t4 = *reinterpret_cast<const float4*>(Tb + tpos(arow, acol + q));
+          v[q] = in ? t4.x - v[q] : 0.f;
+          v[q + 1] = in ? t4.y - v[q + 1] : 0.f;
+          v[q + 2] = in ? t4.z - v[q + 2] : 0.f;
+          v[q + 3] = in ? t4.w - v[q + 3] : 0.f;
+        }
+      }
+      ebar();   // Tb read before the C half overwrites it
+      if (acol == 0) {
+#pragma unroll
+        for (int q = 0; q < 64; q += 4)
+          tcb::put4_smem(Ch, arow, q, v[q], v[q + 1], v[q + 2], v[q + 3]);
+        fence_proxy_async_shared();
+      }
+      ebar();
+      if (tid == 0 && s_ok) s_ok = half_product(tmb, sx, false, s_pre);
+      ebar();
+      if (!ejoin(s_pre >= 0)) break;
+      // second K half: X sub-chunks 4..7 against columns 64..127 of C
+      if (tid == 0) {
+        s_pre = half_prime(sx + 4 * kSub, nullptr);
+        s_ok = s_pre >= 0;
+      }
+      if (acol == TB) {
+#pragma unroll
+        for (int q = 0; q < 64; q += 4)
+          tcb::put4_smem(Ch, arow, q, v[q], v[q + 1], v[q + 2], v[q + 3]);
+        fence_proxy_async_shared();
+      }
+      ebar();
+      if (tid == 0 && s_ok) s_ok = half_product(tmb, sx + 4 * kSub, true, s_pre);
+      ebar();
+      if (!ejoin(s_pre >= 0)) break;
+      tc::fence_after();
+      tcb::tmem_row64(tmb, v);
+      tc::fence_before();
+      ebar();
+      if (tid == 0) mbar_arrive(&bar_empty[b]);   // the accumulator is free again
+      // L_IJ -> its slot, and through Tb (rows) -> A
+#pragma unroll
+      for (int q = 0; q < 64; q += 4)
+        *reinterpret_cast<float4*>(Tb + tpos(arow, acol + q)) =
+            make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+      float* S = Lp + slot(I, J) * kSlot;
+#pragma unroll
+      for (int q = 0; q < 64; q += 4)
+        tcb::put4(S, arow, acol + q, v[q], v[q + 1], v[q + 2], v[q + 3]);
+      ebar();
+      {
+        const int c0 = J * BS + 2 * lane;
+#pragma unroll 4
+        for (int q = 0; q < 16; ++q) {
+          const int r = 16 * warp + q, rg = I * BS + r;
+          if (rg < n) {
+            float* row = A + (size_t)rg * n;
+            __stcg(reinterpret_cast<float2*>(row + c0),
+                   *reinterpret_cast<const float2*>(Tb + tpos(r, 2 * lane)));
+            __stcg(reinterpret_cast<float2*>(row + c0 + 64),
+                   *reinterpret_cast<const float2*>(Tb + tpos(r, 64 + 2 * lane)));
+          }
+        }
+      }
+      epublish(&tdone[I * nb + J]);
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
   }
 }
 
@@ -1763,9 +2512,11 @@ void launch_chol_dag(const BatchTabs& B, cudaStream_t s) {
                                          2000000000ull);
     };
     static PerDevice attr[4];
-    if (B.tcb_pairs && B.tcb_g == 1)
-      go(k_chol_tcb<1, true>, attr[0]);
-    else if (B.tcb_pairs)
+    if (B.tcb_pipe) {
+      set_smem_once(attr[0], k_chol_tcp, (int)tcp::kSmem);
+      k_chol_tcp<<<grid, tcp::kThreads, tcp::kSmem, s>>>(B.d, tickets, nticket, B.words + 0,
+                                                          B.words + 5, 2000000000ull);
+    } else if (B.tcb_pairs)
       go(k_chol_tcb<2, true>, attr[1]);
     else if (B.tcb_g == 1)
       go(k_chol_tcb<1, false>, attr[2]);

@@ -226,6 +226,7 @@ struct BatchTabs {
                              // 2 tensor cores 128-blocks
   int tcb_g;                 // 128-block kernel: K sub-chunks of 16 per operand and stage (1, 2)
   int tcb_pairs;             // 128-block kernel: block columns taken in pairs
+  int tcb_pipe;              // 128-block kernel: K loops overlapping the epilogues (warp roles)
   const int2* chol_p;        // the tickets of the paired block tasks, in claim order
   int n_chol_p;
   int jtj;                   // ICP J^T W J on the tensor cores (BF16, FP32 accumulation)

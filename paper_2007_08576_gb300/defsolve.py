@@ -252,7 +252,7 @@ def ds_batch_set_tracing(b, on=True):
 
 
 FACTOR_KERNELS = ["simt64", "tc64", "tc128_stage64k", "tc128_stage32k", "tc128_stage64k_pairs",
-                  "tc128_stage32k_pairs"]
+                  "tc128_pipelined"]
 
 
 def ds_batch_tune(b, reps=3):
