@@ -1307,8 +1307,8 @@ __device__ bool stream(unsigned tmem, unsigned tmem2, unsigned stg, Ring<NS>& rg
 // A K-loop ring whose copies (one producer thread) and products (one consumer thread) run
 // decoupled: full[s] completes when the copies into stage s have landed, empty[s] when the
 // products that read it are done. Chunk c of a loop is the ring's (pos + c)-th use overall (pos:
-// the chunks through the ring before, counted alike by both threads). nissued / pdone: how many
-// chunks the producer issued, once it has stopped (reset before each loop).
+// the chunks through the ring before, counted alike by both threads). pdone / nissued: set only
+// when the producer stops short of a loop's end, with the ring position it got to.
 template <int NS>
 struct WRing {
   unsigned long long full[NS], empty[NS];
@@ -1327,7 +1327,8 @@ __device__ __forceinline__ void wring_init(WRing<NS>& r) {
 
 // Producer: for c < nck, once the stage's previous products are done and dep(c) holds, the
 // copies of chunk c (A, B, B2 from global at pa(c), pb(c), pb2(c) where not nullptr) into its
-// stage. Stops early (and says so in nissued) if a wait gives up or the error word is raised.
+// stage. Stops early (and says so in pdone / nissued) if a wait gives up or the error word is
+// raised.
 template <int NS, int G, int NOPS, typename PA, typename PB, typename PB2, typename DEP>
 __device__ void ws_produce(unsigned stg, WRing<NS>& r, unsigned pos, int nck, PA pa, PB pb,
                            PB2 pb2, DEP dep, int* err, unsigned long long budget) {
@@ -1366,9 +1367,11 @@ __device__ void ws_produce(unsigned stg, WRing<NS>& r, unsigned pos, int nck, PA
       if (b2) copy(d, b2);
     }
   }
-  *(volatile int*)&r.nissued = c;
-  __threadfence_block();
-  *(volatile int*)&r.pdone = 1;
+  if (c < nck) {
+    *(volatile int*)&r.nissued = (int)pos + c;
+    __threadfence_block();
+    *(volatile int*)&r.pdone = 1;
+  }
 }
 
 // Consumer: D (+)= sum_c A_c B_c^T (and D2 with B2 into tmem2) over the chunks as their copies
@@ -1395,7 +1398,7 @@ __device__ bool ws_consume(unsigned tmem, unsigned tmem2, unsigned stg, WRing<NS
           got = true;
           break;
         }
-        if (*vdone && c >= *vn) break;   // the producer stopped before chunk c
+        if (*vdone && (int)pos + c >= *vn) break;   // the producer stopped before chunk c
         if (globaltimer() - t0 > budget) {
           atomicExch(err, 1);
           break;
@@ -1425,7 +1428,7 @@ __device__ bool ws_consume(unsigned tmem, unsigned tmem2, unsigned stg, WRing<NS
     const unsigned long long t0 = globaltimer();
     while (!*vdone && globaltimer() - t0 <= budget) {
     }
-    const int n_iss = *vdone ? *vn : c;
+    const int n_iss = *vdone ? *vn - (int)pos : c;
     for (int k = c; k < n_iss; ++k) {
       const unsigned q = pos + (unsigned)k, s = q % NS, g = q / NS;
       mbar_wait(&r.full[s], g & 1u, err, budget);
@@ -1625,11 +1628,7 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
   // K loops: thread 32 issues the copies, thread 0 the products; pos_*: chunks through each ring
   unsigned pos_k = 0u, pos_p = 0u;
   for (;;) {
-    if (tid == 0) {
-      s_t = atomicAdd(head, 1);
-      wring_k.pdone = 0;
-      wring_p.pdone = 0;
-    }
+    if (tid == 0) s_t = atomicAdd(head, 1);
     __syncthreads();
     const int t = s_t;
     if (t >= nticket) break;
@@ -1977,13 +1976,14 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
 
 // ----------------------------------------------------------------------------- pipelined blocks
 // The 128 x 128 block factorisation with the K loop of one task overlapping the epilogue of the
-// previous one: warp 8 (one thread) claims the tickets and streams each task's K loop into one
-// of two tensor-memory accumulators; warps 0..7 take the finished accumulators in the same order
+// previous one: warp 8 (one thread) claims the tickets and issues each task's K-loop copies, warp
+// 9 (one thread) its products into one of two tensor-memory accumulators; warps 0..7 take the
+// finished accumulators in the same order
 // and run the epilogues (DIAG: SIMT Cholesky and inverse of the block; OFF: C = A - acc and
 // L = C X^T on the tensor cores, in two K halves so that the epilogue's shared memory and the
 // K loop's stages fit side by side). Same tasks, slots, flags and results as k_chol_tcb.
 namespace tcp {
-constexpr int kThreads = 288;
+constexpr int kThreads = 320;
 constexpr int kNS = 3;                                 // K-loop stages of 32 KB (A, B)
 constexpr int TB = 64, LDS = TB + 1;
 constexpr int kTile = TB * LDS;                        // floats of a 64 x 65 tile
@@ -2018,7 +2018,7 @@ __global__ __launch_bounds__(tcp::kThreads, 1) void k_chol_tcp(
   extern __shared__ __align__(1024) unsigned char smb[];
   float* sm = reinterpret_cast<float*>(smb);
   __shared__ __align__(8) unsigned long long bar_task[2], bar_full[2], bar_empty[2], bar_efin;
-  __shared__ __align__(8) Ring<tcp::kNS> ring_k;   // streamer
+  __shared__ __align__(8) WRing<tcp::kNS> wring;   // K-loop stages (producer / MMA thread)
   __shared__ __align__(8) Ring<2> ring_x;          // epilogue thread 0
   __shared__ int4 s_task[2];                       // (problem, type, I, J); type -1: no more
   __shared__ unsigned s_tmem;
@@ -2031,7 +2031,7 @@ __global__ __launch_bounds__(tcp::kThreads, 1) void k_chol_tcp(
       mbar_init(&bar_empty[b]);
     }
     mbar_init(&bar_efin);
-    ring_init(ring_k);
+    wring_init(wring);
     ring_init(ring_x);
   }
   if (warp == 0) {
@@ -2051,13 +2051,13 @@ __global__ __launch_bounds__(tcp::kThreads, 1) void k_chol_tcp(
     return ok;
   };
   if (warp == 8) {
-    // ---- streamer: claim, publish the task, K loop into accumulator u & 1
+    // ---- producer: claim, publish the task (buffer u & 1), issue its K-loop copies
     if (lane == 0) {
       int u = 0;
+      unsigned pos = 0u;
       auto finish = [&](int b) {
         s_task[b] = make_int4(-1, -1, 0, 0);
         mbar_arrive(&bar_task[b]);
-        mbar_arrive(&bar_full[b]);
       };
       for (;;) {
         const int b = u & 1;
@@ -2079,17 +2079,14 @@ __global__ __launch_bounds__(tcp::kThreads, 1) void k_chol_tcp(
         const int* tdone = P.cnt + nb;
         const float* Lp = (const float*)P.Lp;
         s_task[b] = make_int4(pt.x, tk.y, I, J);
-        mbar_arrive(&bar_task[b]);   // release: the epilogue may load the task's block of A
+        mbar_arrive(&bar_task[b]);   // release: the task to the MMA thread and the epilogue
         const int nck = (BS / KS) * J;
-        if (nck == 0) {
-          mbar_arrive(&bar_full[b]);
-        } else {
+        if (nck > 0) {
           const float* si = Lp + slot(I, 0) * kSlot;
           const float* sj = Lp + slot(J, 0) * kSlot;
-          const bool ok = stream<tcp::kNS, 1, 2>(
-              tmem + 128u * b, 0u, rbase, ring_k, &bar_full[b], nck, 0, false,
+          ws_produce<tcp::kNS, 1, 2>(
+              rbase, wring, pos, nck,
               [&](int c) -> const float* { return si + (size_t)(c >> 3) * kSlot + (c & 7) * kSub; },
-              [&](int) { return 0u; },
               [&](int c) -> const float* {
                 return diag ? nullptr : sj + (size_t)(c >> 3) * kSlot + (c & 7) * kSub;
               },
@@ -2101,9 +2098,45 @@ __global__ __launch_bounds__(tcp::kThreads, 1) void k_chol_tcp(
                                 (diag || wait_flag(&tdone[J * nb + kb], 1, err, budget_ns)));
               },
               err, budget_ns);
-          (void)ok;   // a failed wait raised the error word; the epilogue sees it
+          pos += (unsigned)nck;
+          if (*(volatile int*)&wring.pdone) {   // stopped short: no more tasks
+            finish((u + 1) & 1);
+            break;
+          }
         }
         ++u;
+      }
+    }
+    __syncwarp();
+  } else if (warp == 9) {
+    // ---- MMA thread: each published task's K loop into accumulator u & 1
+    if (lane == 0) {
+      unsigned pos = 0u;
+      for (int u = 0;; ++u) {
+        const int b = u & 1;
+        if (!mbar_wait(&bar_task[b], (unsigned)((u >> 1) & 1), err, budget_ns)) break;
+        const int4 tk = s_task[b];
+        if (tk.y < 0) break;
+        const LinProblem& P = descs[tk.x]->lp;
+        const bool diag = tk.y == 0;
+        const int I = tk.z, J = tk.w;
+        const float* Lp = (const float*)P.Lp;
+        const int nck = (BS / KS) * J;
+        if (nck == 0) {
+          mbar_arrive(&bar_full[b]);
+          continue;
+        }
+        const float* si = Lp + slot(I, 0) * kSlot;
+        const float* sj = Lp + slot(J, 0) * kSlot;
+        const bool ok = ws_consume<tcp::kNS, 1, 2>(
+            tmem + 128u * b, 0u, rbase, wring, pos, &bar_full[b], nck,
+            [&](int c) -> const float* { return si + (size_t)(c >> 3) * kSlot + (c & 7) * kSub; },
+            [&](int c) -> const float* {
+              return diag ? nullptr : sj + (size_t)(c >> 3) * kSlot + (c & 7) * kSub;
+            },
+            no_src, err, budget_ns);
+        pos += (unsigned)nck;
+        if (!ok) break;   // the error word is raised; the epilogue sees it
       }
     }
     __syncwarp();
