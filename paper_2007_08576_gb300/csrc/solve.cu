@@ -95,23 +95,27 @@ __device__ __forceinline__ void gemv_cols_pf(const T (&v)[SolveTile<T, TB>::NV],
 // rows is the solve's critical path.
 
 // Tickets per problem: [0, nt) forward rows 0..nt-1, [nt, 2nt) backward rows nt-1..0.
-// flags: [0, nt) forward row done, [nt, 2nt) backward row done. Every tile a ticket needs is
-// loaded into registers before the wait on its producer (the tiles do not depend on it), so a
-// dependency costs one flag hand-off and one 64-value vector load.
+// flags: [0, nt) forward row done, [nt, 2nt) backward row done. The tiles of L a ticket needs do
+// not depend on other tickets and stream ahead of their use (a few tiles in flight); the inputs
+// they multiply are taken a ready prefix at a time (one acquire load per tile, by as many
+// threads), so only the producers that are still running cost a hand-off each.
 // The forward tickets read the right-hand side from b (first solve) or from the refinement
 // residual r (from_r) in FP64; the backward tickets also write the solution into the FP64 x
 // (assigned, or added to it for a refinement step) and its two-float split for the residual.
 template <typename T, int TB>
-__global__ __launch_bounds__(256) void k_trsv_dag(const ProbDesc* const* __restrict__ descs,
+__global__ __launch_bounds__(256, 2) void k_trsv_dag(const ProbDesc* const* __restrict__ descs,
                                                   int np, int nticket, int solve_id, int from_r,
                                                   int assign, int* __restrict__ head,
                                                   int* __restrict__ err,
                                                   unsigned long long budget_ns) {
   constexpr int NV = SolveTile<T, TB>::NV;
+  constexpr int kPF = sizeof(T) == 8 ? 4 : 2;   // tiles of L in flight per CTA
+  constexpr int kSpan = 2048 / TB;           // tiles whose inputs fit the shared buffer
   __shared__ T acc[TB];
   __shared__ T vin[TB];
   __shared__ T part[TB][17];
-  __shared__ int s_t, s_ok;
+  __shared__ T ysm[kSpan * TB];
+  __shared__ int s_t, s_ok, s_first;
   for (;;) {
     if (threadIdx.x == 0) s_t = atomicAdd(head, 1);
     __syncthreads();
@@ -157,40 +161,98 @@ __global__ __launch_bounds__(256) void k_trsv_dag(const ProbDesc* const* __restr
                              ? (fwd ? (T)ldcg(rhs + r0 + threadIdx.x) : ldcg(y + r0 + threadIdx.x))
                              : (T)0;
     const int cnt = fwd ? i : nt - 1 - i;
-    T lv[NV];
-    if (cnt > 0) {
-      const int jt = fwd ? 0 : nt - 1;
-      const int c0 = jt * TB, nc = min(TB, n - c0);
+    // The tiles before the diagonal, in order: tile q is row tile jt(q) of this row's L (forward)
+    // or column tile of L^T (backward). Flags of the producing rows are prefix-ordered (a row is
+    // published only after it consumed its predecessor), so a ready prefix is found with one
+    // acquire load per tile, its inputs go to shared memory at once, and its tiles are consumed
+    // back to back (PF tiles of L in flight) with row partial sums kept in registers.
+    auto jtile = [&](int q) { return fwd ? q : nt - 1 - q; };
+    auto fidx = [&](int jt) { return fwd ? jt : nt + jt; };
+    auto fetch = [&](int q, T (&v)[NV]) {
+      const int jt = jtile(q), c0 = jt * TB, nc = min(TB, n - c0);
       if (fwd)
-        prefetch_rows<T, TB>(L + (size_t)r0 * n + c0, n, nr, nc, lv);
+        prefetch_rows<T, TB>(L + (size_t)r0 * n + c0, n, nr, nc, v);
       else
-        prefetch_cols<T, TB>(L + (size_t)c0 * n + r0, n, nr, nc, lv);
-    }
-    for (int q = 0; q < cnt && ok; ++q) {
-      const int jt = fwd ? q : nt - 1 - q;
-      if (threadIdx.x == 0) s_ok = wait_flag(&flag[fwd ? jt : nt + jt], solve_id, err, budget_ns);
-      __syncthreads();
-      ok = s_ok;
-      if (!ok) break;
-      const int c0 = jt * TB;
-      const int nc = min(TB, n - c0);
-      if (threadIdx.x < TB) vin[threadIdx.x] = threadIdx.x < nc ? ldcg(src + c0 + threadIdx.x) : (T)0;
-      __syncthreads();
-      T cur[NV];
+        prefetch_cols<T, TB>(L + (size_t)c0 * n + r0, n, nr, nc, v);
+    };
+    T lv[kPF][NV];
 #pragma unroll
-      for (int e = 0; e < NV; ++e) cur[e] = lv[e];
-      if (q + 1 < cnt) {  // next tile while this one is used
-        const int jn = fwd ? q + 1 : nt - 2 - q;
-        const int cn = jn * TB, ncn = min(TB, n - cn);
-        if (fwd)
-          prefetch_rows<T, TB>(L + (size_t)r0 * n + cn, n, nr, ncn, lv);
-        else
-          prefetch_cols<T, TB>(L + (size_t)cn * n + r0, n, nr, ncn, lv);
+    for (int p = 0; p < kPF; ++p)
+      if (p < cnt) fetch(p, lv[p]);
+    T ps[SolveTile<T, TB>::RS];   // forward: rows warp + 8 s; backward: ps[0] for (r, slice)
+#pragma unroll
+    for (int k = 0; k < SolveTile<T, TB>::RS; ++k) ps[k] = (T)0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cr = threadIdx.x % TB, csl = threadIdx.x / TB;
+    int done = 0;
+    while (ok && done < cnt) {
+      const int span = min(cnt - done, kSpan);
+      if (threadIdx.x == 0) s_first = span;
+      __syncthreads();
+      if ((int)threadIdx.x < span &&
+          ld_acquire(&flag[fidx(jtile(done + threadIdx.x))]) < solve_id)
+        atomicMin(&s_first, (int)threadIdx.x);
+      __syncthreads();
+      int m = done + s_first;
+      if (m == done) {   // nothing ready yet: wait for the next producer
+        if (threadIdx.x == 0)
+          s_ok = wait_flag(&flag[fidx(jtile(done))], solve_id, err, budget_ns);
+        __syncthreads();
+        ok = s_ok;
+        if (!ok) break;
+        m = done + 1;
       }
-      if (fwd)
-        gemv_rows_pf<T, TB>(cur, vin, acc, true);
-      else
-        gemv_cols_pf<T, TB>(cur, vin, acc, true, part);
+      for (int e = threadIdx.x; e < (m - done) * TB; e += blockDim.x) {
+        const int c = jtile(done + e / TB) * TB + e % TB;
+        ysm[e] = c < n ? ldcg(src + c) : (T)0;
+      }
+      __syncthreads();
+      for (int q = done; q < m; ++q) {
+        T cur[NV];
+#pragma unroll
+        for (int e = 0; e < NV; ++e) cur[e] = lv[0][e];
+#pragma unroll
+        for (int p = 0; p + 1 < kPF; ++p)
+#pragma unroll
+          for (int e = 0; e < NV; ++e) lv[p][e] = lv[p + 1][e];
+        if (q + kPF < cnt) fetch(q + kPF, lv[kPF - 1]);
+        const T* yv = ysm + (q - done) * TB;
+        if (fwd) {
+          constexpr int RS = SolveTile<T, TB>::RS, CS = SolveTile<T, TB>::CS;
+#pragma unroll
+          for (int s2 = 0; s2 < RS; ++s2)
+#pragma unroll
+            for (int t = 0; t < CS; ++t) ps[s2] += cur[s2 * CS + t] * yv[lane + 32 * t];
+        } else {
+          constexpr int SL = SolveTile<T, TB>::SL;
+#pragma unroll
+          for (int e = 0; e < NV; ++e) ps[0] += cur[e] * yv[csl + SL * e];
+        }
+      }
+      done = m;
+      __syncthreads();   // ysm is refilled next round
+    }
+    if (ok && cnt > 0) {   // acc -= the partial sums
+      if (fwd) {
+        constexpr int RS = SolveTile<T, TB>::RS;
+#pragma unroll
+        for (int s2 = 0; s2 < RS; ++s2) {
+          T sum = ps[s2];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+          if (lane == 0) acc[warp + 8 * s2] -= sum;
+        }
+      } else {
+        constexpr int SL = SolveTile<T, TB>::SL;
+        part[cr][csl] = ps[0];
+        __syncthreads();
+        if (threadIdx.x < TB) {
+          T a = (T)0;
+#pragma unroll
+          for (int q = 0; q < SL; ++q) a += part[threadIdx.x][q];
+          acc[threadIdx.x] -= a;
+        }
+      }
       __syncthreads();
     }
     if (ok) {
