@@ -433,21 +433,42 @@ void make_chol_tasks(int nt, std::vector<int4>& out) {
   }
 }
 
-// Block tasks of the 128 x 128 block factorisation, in the same column order (same encoding).
+// Block tasks of the 128 x 128 block factorisation (same encoding), column by column with a
+// lookahead of one: DIAG(j + 1) follows OFF(j + 1, j), its last dependency, ahead of the rest
+// of column j, so that the diagonal block the next column's products need is started early.
+// Every task still depends only on tasks earlier in this order.
 void make_chol_tasks_b(int nb, std::vector<int4>& out) {
-  make_chol_tasks(nb, out);
+  if (nb < 1) return;
+  out.push_back(make_int4(0, 0, 0, 0));
+  for (int j = 0; j < nb; ++j) {
+    if (j + 1 < nb) {
+      out.push_back(make_int4(0, 1, j + 1, j));
+      out.push_back(make_int4(0, 0, j + 1, j + 1));
+    }
+    for (int i = j + 2; i < nb; ++i) out.push_back(make_int4(0, 1, i, j));
+  }
 }
 
-// Block tasks with the block columns taken in pairs (J0 = 2 p, J1 = J0 + 1): DIAG(J0),
-// OFF(J1, J0), DIAG(J1), then {0, 2, I, J0} for I = J1 + 1 .. nb - 1, the two blocks (I, J0) and
-// (I, J1) as one task. A lone last column is DIAG alone. Topological, like the single order.
+// Block tasks with the block columns taken in pairs (J0 = 2 p, J1 = J0 + 1): the pair's panel
+// DIAG(J0), OFF(J1, J0), DIAG(J1), then {0, 2, I, J0} for I = J1 + 1 .. nb - 1, the two blocks
+// (I, J0) and (I, J1) as one task; a lone last column is DIAG alone. The next pair's panel
+// follows the first two of these (the rows it depends on), ahead of the others. Topological,
+// like the single order.
 void make_chol_tasks_p(int nb, std::vector<int4>& out) {
-  for (int j0 = 0; j0 < nb; j0 += 2) {
+  auto panel = [&](int j0) {
     out.push_back(make_int4(0, 0, j0, j0));
-    if (j0 + 1 >= nb) break;
-    out.push_back(make_int4(0, 1, j0 + 1, j0));
-    out.push_back(make_int4(0, 0, j0 + 1, j0 + 1));
-    for (int i = j0 + 2; i < nb; ++i) out.push_back(make_int4(0, 2, i, j0));
+    if (j0 + 1 < nb) {
+      out.push_back(make_int4(0, 1, j0 + 1, j0));
+      out.push_back(make_int4(0, 0, j0 + 1, j0 + 1));
+    }
+  };
+  if (nb < 1) return;
+  panel(0);
+  for (int j0 = 0; j0 + 1 < nb; j0 += 2) {
+    int i = j0 + 2;
+    for (; i < nb && i < j0 + 4; ++i) out.push_back(make_int4(0, 2, i, j0));
+    if (j0 + 2 < nb) panel(j0 + 2);
+    for (; i < nb; ++i) out.push_back(make_int4(0, 2, i, j0));
   }
 }
 
