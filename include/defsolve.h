@@ -302,6 +302,17 @@ int ds_get_counters(ds_handle h, int64_t* kernels_launched);
  * GPU). No synchronisation. Errors: DS_ERR_ARG (NULL). */
 int ds_get_device_bytes(ds_handle h, int64_t* bytes);
 
+/* The task order of the 128 x 128 block Cholesky factorisation (Section 2: the damped normal
+ * equations are solved by a Cholesky factorisation) of an nb x nb block matrix, as the factor
+ * kernels claim it within one problem: paired = 0 for the single-block kernels (factor_tc 2, 3
+ * and 5), 1 for the column-pair kernel (factor_tc 4). Task k is written to out[3 k .. 3 k + 2]
+ * = (type, I, J): type 0 = DIAG(J) (factor block (J, J)), 1 = OFF(I, J) (block (I, J), I > J),
+ * 2 = the two blocks (I, J) and (I, J + 1). out (host memory, caller-owned) holds cap tasks; the
+ * count is written to *ntasks (also when it exceeds cap, then nothing past cap is written).
+ * Host only, no GPU. Errors: DS_ERR_ARG (nb < 1, paired not 0 / 1, ntasks NULL, out NULL with
+ * cap > 0). */
+int ds_factor_tasks(int32_t nb, int32_t paired, int32_t* out, int32_t cap, int32_t* ntasks);
+
 /* 1-point RANSAC preselection without any allocation, for callers that cannot allocate device
  * memory (for example a host process that runs inside a pre-sized memory pool, or a real-time
  * loop where an allocation can block on a device-wide synchronisation). The paper has no

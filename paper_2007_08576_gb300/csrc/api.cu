@@ -1901,6 +1901,22 @@ int ds_get_device_bytes(ds_handle h, int64_t* bytes) {
   return DS_OK;
 }
 
+int ds_factor_tasks(int32_t nb, int32_t paired, int32_t* out, int32_t cap, int32_t* ntasks) {
+  if (nb < 1 || (paired != 0 && paired != 1) || !ntasks || (cap > 0 && !out)) return DS_ERR_ARG;
+  std::vector<int4> t;
+  if (paired)
+    make_chol_tasks_p(nb, t);
+  else
+    make_chol_tasks_b(nb, t);
+  *ntasks = (int32_t)t.size();
+  for (int k = 0; k < (int)t.size() && k < cap; ++k) {
+    out[3 * k] = t[k].y;
+    out[3 * k + 1] = t[k].z;
+    out[3 * k + 2] = t[k].w;
+  }
+  return DS_OK;
+}
+
 int ds_get_counters(ds_handle h, int64_t* kernels_launched) {
   if (!kernels_launched) return DS_ERR_ARG;
   *kernels_launched = h ? h->kernels : g_total_kernels.load();

@@ -31,7 +31,8 @@ EXPORTS = [
     "ds_batch_tune", "ds_batch_factor_kernel", "ds_get_deformation", "ds_get_deformation64",
     "ds_set_deformation", "ds_get_inlier_mask", "ds_get_ransac", "ds_get_cost",
     "ds_get_blend_table", "ds_get_frame_points", "ds_linearize", "ds_set_tracing",
-    "ds_get_phase_times", "ds_get_counters", "ds_get_device_bytes", "ds_ransac_noalloc",
+    "ds_get_phase_times", "ds_get_counters", "ds_get_device_bytes", "ds_factor_tasks",
+    "ds_ransac_noalloc",
     "ds_selftest_bounded_wait",
     "ds_destroy", "ds_status_str", "ds_version",
     "ds_orb_default_params", "ds_orb_create", "ds_orb_detect", "ds_orb_num_keypoints",
@@ -123,6 +124,7 @@ def lib(path: str | None = None):
         "ds_get_phase_times": (i32, [vp, vp]),
         "ds_get_counters": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
         "ds_get_device_bytes": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
+        "ds_factor_tasks": (i32, [i32, i32, vp, i32, ctypes.POINTER(ctypes.c_int32)]),
         "ds_ransac_noalloc": (i32, [vp, i32, i32, DsIntrinsics, vp, vp, i32, vp, i32, i32, f64,
                                     f64, vp, vp, vp, vp, vp]),
         "ds_selftest_bounded_wait": (i32, [i32, ctypes.c_int64, i32, ctypes.POINTER(f64)]),
@@ -360,6 +362,16 @@ def ds_get_device_bytes(h) -> int:
     b = ctypes.c_int64()
     _check("ds_get_device_bytes", lib().ds_get_device_bytes(h, ctypes.byref(b)))
     return b.value
+
+
+def ds_factor_tasks(nb: int, paired: bool = False) -> np.ndarray:
+    """The block factorisation's task order within one problem, rows (type, I, J)."""
+    n = ctypes.c_int32()
+    _check("ds_factor_tasks", lib().ds_factor_tasks(nb, int(paired), None, 0, ctypes.byref(n)))
+    out = np.zeros((n.value, 3), np.int32)
+    _check("ds_factor_tasks", lib().ds_factor_tasks(nb, int(paired), out.ctypes.data, n.value,
+                                                     ctypes.byref(n)))
+    return out
 
 
 def _dev_ptr(t, itemsize):
