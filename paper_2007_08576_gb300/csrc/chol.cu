@@ -1091,6 +1091,9 @@ constexpr int kXStages = 4;                          // 16 KB stages of X after 
 // kind::tf32, D = F32, A = B = TF32, both K-major, N = 128, M = 128
 constexpr unsigned kIdesc =
     (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+// the same with N = 256 (two 128-row B blocks as one operand, D over 256 TMEM columns)
+constexpr unsigned kIdesc256 =
+    (1u << 4) | (2u << 7) | (2u << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
 
 __host__ __device__ __forceinline__ size_t slot(int i, int j) { return (size_t)i * (i + 1) / 2 + j; }
 // offset of element (r, k) of a block (row r, K index k) in its slot (hi part; lo at + kPart)
@@ -1101,12 +1104,26 @@ __device__ __forceinline__ uint64_t sdesc(unsigned saddr) {
   return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) |
          ((uint64_t)(512 >> 4) << 32) | ((uint64_t)1 << 46);
 }
-__device__ __forceinline__ void mma(unsigned tmem, uint64_t a, uint64_t b, unsigned acc) {
+__device__ __forceinline__ void mma(unsigned tmem, uint64_t a, uint64_t b, unsigned acc,
+                                    unsigned idesc = kIdesc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
+}
+// D (256 columns) (+)= A [B0; B1]^T over one sub-chunk: A at sa (hi, lo parts), the two B
+// blocks interleaved at sb as [B0 hi][B1 hi][B0 lo][B1 lo] (one 256-row operand per part)
+__device__ __forceinline__ void mma_sub256(unsigned tmem, unsigned sa, unsigned sb,
+                                           bool accumulate) {
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const unsigned ah = t == 2 ? sa + kPart * 4u : sa, bh = t == 1 ? sb + kPart * 8u : sb;
+#pragma unroll
+    for (int kk = 0; kk < KS / 8; ++kk)
+      mma(tmem, sdesc(ah + 256u * kk), sdesc(bh + 256u * kk),
+          (accumulate || t > 0 || kk > 0) ? 1u : 0u, kIdesc256);
+  }
 }
 // D (+)= A B^T over the 16 K values of one sub-chunk pair (A at sa, B at sb; hi then lo parts)
 __device__ __forceinline__ void mma_sub(unsigned tmem, unsigned sa, unsigned sb, bool accumulate) {
@@ -1327,9 +1344,11 @@ __device__ __forceinline__ void wring_init(WRing<NS>& r) {
 
 // Producer: for c < nck, once the stage's previous products are done and dep(c) holds, the
 // copies of chunk c (A, B, B2 from global at pa(c), pb(c), pb2(c) where not nullptr) into its
-// stage. Stops early (and says so in pdone / nissued) if a wait gives up or the error word is
+// stage; with IL (G = 1) B and B2 go in interleaved, [B hi][B2 hi][B lo][B2 lo], as one 256-row
+// operand. Stops early (and says so in pdone / nissued) if a wait gives up or the error word is
 // raised.
-template <int NS, int G, int NOPS, typename PA, typename PB, typename PB2, typename DEP>
+template <int NS, int G, int NOPS, bool IL = false, typename PA, typename PB, typename PB2,
+          typename DEP>
 __device__ void ws_produce(unsigned stg, WRing<NS>& r, unsigned pos, int nck, PA pa, PB pb,
                            PB2 pb2, DEP dep, int* err, unsigned long long budget) {
   constexpr unsigned kChunkBytes = G * kSubBytes;
@@ -1360,11 +1379,27 @@ __device__ void ws_produce(unsigned stg, WRing<NS>& r, unsigned pos, int nck, PA
         copy(d, a);
         d += kChunkBytes;
       }
-      if (b) {
-        copy(d, b);
-        d += kChunkBytes;
+      if constexpr (IL) {
+        static_assert(G == 1, "interleaved pairs take one sub-chunk per stage");
+        constexpr unsigned kHalf = kChunkBytes / 2;
+        auto copy_half = [&](unsigned dst, const float* src) {
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+              "[%3];" ::"r"(dst),
+              "l"(src), "r"(kHalf), "r"(bar)
+              : "memory");
+        };
+        copy_half(d, b);
+        copy_half(d + kHalf, b2);
+        copy_half(d + 2 * kHalf, b + kPart);
+        copy_half(d + 3 * kHalf, b2 + kPart);
+      } else {
+        if (b) {
+          copy(d, b);
+          d += kChunkBytes;
+        }
+        if (b2) copy(d, b2);
       }
-      if (b2) copy(d, b2);
     }
   }
   if (c < nck) {
@@ -1378,7 +1413,7 @@ __device__ void ws_produce(unsigned stg, WRing<NS>& r, unsigned pos, int nck, PA
 // land, each stage released to the producer by a commit on empty[s]; bfin is committed after the
 // last product. If the producer stopped short, the chunks it did issue are waited for and
 // released, and false is returned (the accumulators are then not meaningful).
-template <int NS, int G, int NOPS, typename PA, typename PB, typename PB2>
+template <int NS, int G, int NOPS, bool IL = false, typename PA, typename PB, typename PB2>
 __device__ bool ws_consume(unsigned tmem, unsigned tmem2, unsigned stg, WRing<NS>& r,
                            unsigned pos, unsigned long long* bfin, int nck, PA pa, PB pb,
                            PB2 pb2, int* err, unsigned long long budget) {
@@ -1415,11 +1450,17 @@ __device__ bool ws_consume(unsigned tmem, unsigned tmem2, unsigned stg, WRing<NS
     const unsigned sa = d;
     const unsigned sb = b_st ? d + (a_st ? kChunkBytes : 0u) : sa;
     const unsigned sb2 = d + ((a_st ? 1u : 0u) + (b_st ? 1u : 0u)) * kChunkBytes;
+    if constexpr (IL) {
+      mma_sub256(tmem, sa, sb, c > 0);   // tmem2 = tmem + 128 holds the B2 half of D
+      (void)sb2;
+      (void)tmem2;
+    } else {
 #pragma unroll
-    for (int gg = 0; gg < G; ++gg) {
-      const bool acc = c > 0 || gg > 0;
-      mma_sub(tmem, sa + gg * kSubBytes, sb + gg * kSubBytes, acc);
-      if (b2_st) mma_sub(tmem2, sa + gg * kSubBytes, sb2 + gg * kSubBytes, acc);
+      for (int gg = 0; gg < G; ++gg) {
+        const bool acc = c > 0 || gg > 0;
+        mma_sub(tmem, sa + gg * kSubBytes, sb + gg * kSubBytes, acc);
+        if (b2_st) mma_sub(tmem2, sa + gg * kSubBytes, sb2 + gg * kSubBytes, acc);
+      }
     }
     tc::commit(&r.empty[s]);
   }
@@ -1660,7 +1701,7 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
         auto pb = [&](int c) -> const float* { return src(J0, c); };
         auto pb2 = [&](int c) -> const float* { return src(J1, c); };
         if (tid == 32)
-          ws_produce<4, 1, 3>(
+          ws_produce<4, 1, 3, true>(
               stg, wring_p, pos_p, nck, pa, pb, pb2,
               [&](int c) {
                 if (c & 7) return true;
@@ -1671,8 +1712,8 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
               },
               err, budget_ns);
         else
-          s_ok = ws_consume<4, 1, 3>(tmem, tmem + 128u, stg, wring_p, pos_p, bfin, nck, pa, pb,
-                                     pb2, err, budget_ns);
+          s_ok = ws_consume<4, 1, 3, true>(tmem, tmem + 128u, stg, wring_p, pos_p, bfin, nck, pa,
+                                           pb, pb2, err, budget_ns);
       }
       if (tid == 0 && !str) s_ok = *(volatile int*)err == 0;
       if (str) pos_p += (unsigned)nck;
