@@ -53,9 +53,9 @@ KERNEL_NAMES = ["simt64", "tc64", "tc128_stage64k", "tc128_stage32k", "tc128_sta
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate per GPU (nominal)
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the dominant kernel
-# on the headline workload, from an ncu capture (profiles/), valid only for the kernel source it
-# was taken on (first 16 hex digits of the sha256 of csrc/chol.cu + csrc/dev_util.cuh) and the
-# same workload and factor kernel; reported as null otherwise.
+# on the headline workload, by factor kernel, from an ncu capture (profiles/), valid only for the
+# kernel source it was taken on (first 16 hex digits of the sha256 of csrc/chol.cu +
+# csrc/dev_util.cuh) and the same workload; reported as null otherwise.
 FACTOR_TRAFFIC = None
 
 
@@ -107,12 +107,12 @@ def _chol_source_digest():
     return h.hexdigest()[:16]
 
 
-def _factor_traffic(workload, kernel):
+def _factor_traffic(workload, factor):
     c = FACTOR_TRAFFIC
     if (c is None or c["chol_sha256"] != _chol_source_digest() or c["workload"] != workload
-            or c["kernel"] != kernel):
+            or factor not in c["bytes"]):
         return None
-    return c["bytes"]
+    return c["bytes"][factor]
 
 
 def _dist():
@@ -732,11 +732,13 @@ def run_gpu(args):
         peak, peak_src = (_measured_bf16() * 1.1 / 2.25,
                           "MEASURED_PEAKS.json bf16_tflops x nominal tf32/bf16 (of measured)")
         kernel = ("k_chol_tcb (persistent 128 x 128 block Cholesky on tcgen05, all problems)"
-                  if factor in ("tc128", "tc128s", "tc128p", "tc128pipe") else
+                  if factor in ("tc128", "tc128s", "tc128p") else
+                  "k_chol_tcp (persistent 128 x 128 block Cholesky on tcgen05, K loops beside "
+                  "the epilogues, all problems)" if factor == "tc128pipe" else
                   "k_chol_tc (persistent 64 x 64 tile Cholesky on tcgen05, all problems)")
     else:
         peak, peak_src = FP32_SIMT_TFLOPS, "152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)"
-    traffic = _factor_traffic(WORKLOAD, kernel.split()[0]) if solver_id == 0 else None
+    traffic = _factor_traffic(WORKLOAD, factor) if solver_id == 0 else None
 
     # ------------------------------------------------------------ oracle error sample
     errors = cpu = None

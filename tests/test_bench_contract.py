@@ -53,15 +53,14 @@ def test_traffic_reported_only_for_the_captured_kernel_source_and_workload():
     c = bench.FACTOR_TRAFFIC
     try:
         bench.FACTOR_TRAFFIC = {"chol_sha256": bench._chol_source_digest(),
-                                "workload": bench.WORKLOAD, "kernel": "k_chol_dag",
-                                "bytes": 123}
-        assert bench._factor_traffic(bench.WORKLOAD, "k_chol_dag") == 123
-        assert bench._factor_traffic("seq_320x240_n256", "k_chol_dag") is None
-        assert bench._factor_traffic(bench.WORKLOAD, "k_chol_tc") is None
+                                "workload": bench.WORKLOAD, "bytes": {"tc128p": 123}}
+        assert bench._factor_traffic(bench.WORKLOAD, "tc128p") == 123
+        assert bench._factor_traffic("seq_320x240_n256", "tc128p") is None
+        assert bench._factor_traffic(bench.WORKLOAD, "tc128") is None      # another kernel
         bench.FACTOR_TRAFFIC = dict(bench.FACTOR_TRAFFIC, chol_sha256="0" * 16)   # other source
-        assert bench._factor_traffic(bench.WORKLOAD, "k_chol_dag") is None
+        assert bench._factor_traffic(bench.WORKLOAD, "tc128p") is None
         bench.FACTOR_TRAFFIC = None
-        assert bench._factor_traffic(bench.WORKLOAD, "k_chol_dag") is None
+        assert bench._factor_traffic(bench.WORKLOAD, "tc128p") is None
     finally:
         bench.FACTOR_TRAFFIC = c
 
