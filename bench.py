@@ -45,10 +45,10 @@ WORKLOAD = "batched_mixed_64"
 ITERS = 10
 METRIC = "frames/s and p50/p99 frame latency vs plain GPU solve, at ≤1e-3 mm error"
 PREC = {"fp64": 0, "fp32": 1, "fp32_refine": 2}
-FACTOR = {"simt": 0, "tc64": 1, "tc128": 2, "tc128s": 3, "tc128p": 4, "tc128pipe": 5,
+FACTOR = {"simt": 0, "tc64": 1, "tc128": 2, "tc128q": 3, "tc128p": 4, "tc128pipe": 5,
           "auto": -1}                                   # ds_params.factor_tc
-FACTOR_NAMES = ["simt", "tc64", "tc128", "tc128s", "tc128p", "tc128pipe"]   # by kernel index
-KERNEL_NAMES = ["simt64", "tc64", "tc128_stage64k", "tc128_stage32k", "tc128_stage64k_pairs",
+FACTOR_NAMES = ["simt", "tc64", "tc128", "tc128q", "tc128p", "tc128pipe"]   # by kernel index
+KERNEL_NAMES = ["simt64", "tc64", "tc128_stage64k", "tc128_quads", "tc128_stage64k_pairs",
                 "tc128_pipelined"]
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate per GPU (nominal)
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
@@ -726,13 +726,13 @@ def run_gpu(args):
         kernel = "linearisation (k_icp + k_orb + k_arap_assemble diagonal blocks)"
     elif prec == 0:
         peak, peak_src = FP64_NOMINAL_TFLOPS, "nominal GB300 FP64 rate"
-    elif factor in ("tc64", "tc128", "tc128s", "tc128p", "tc128pipe"):
+    elif factor in ("tc64", "tc128", "tc128q", "tc128p", "tc128pipe"):
         bound = "tensor"
         achieved *= 3.0
         peak, peak_src = (_measured_bf16() * 1.1 / 2.25,
                           "MEASURED_PEAKS.json bf16_tflops x nominal tf32/bf16 (of measured)")
         kernel = ("k_chol_tcb (persistent 128 x 128 block Cholesky on tcgen05, all problems)"
-                  if factor in ("tc128", "tc128s", "tc128p") else
+                  if factor in ("tc128", "tc128q", "tc128p") else
                   "k_chol_tcp (persistent 128 x 128 block Cholesky on tcgen05, K loops beside "
                   "the epilogues, all problems)" if factor == "tc128pipe" else
                   "k_chol_tc (persistent 64 x 64 tile Cholesky on tcgen05, all problems)")
@@ -810,7 +810,7 @@ def run_gpu(args):
                        "factor": {"simt": "FP32 SIMT 64 x 64 tiles",
                                   "tc64": "tensor cores (tcgen05, 3xTF32), 64 x 64 tiles",
                                   "tc128": "tensor cores (tcgen05, 3xTF32), 128 x 128 blocks, 64 KB stages",
-                                  "tc128s": "tensor cores (tcgen05, 3xTF32), 128 x 128 blocks, 32 KB stages",
+                                  "tc128q": "tensor cores (tcgen05, 3xTF32), 128 x 128 blocks, two rows x two block columns per task",
                                   "tc128p": "tensor cores (tcgen05, 3xTF32), 128 x 128 blocks in column pairs, 64 KB stages",
                                   "tc128pipe": "tensor cores (tcgen05, 3xTF32), 128 x 128 blocks, K loops overlapping the epilogues (warp roles)",
                                   "fp64": "FP64 SIMT 32 x 32 tiles",

@@ -94,15 +94,16 @@ typedef struct {
   int32_t factor_tc;        /* FP32 precisions, the factorisation kernel: 0 = FP32 SIMT pipes, 64 x 64
                              * tiles; on the tensor cores (tcgen05 kind::tf32, each product as
                              * three TF32 terms hi*hi + hi*lo + lo*hi, FP32-level accuracy) with
-                             * 1 = 64 x 64 tiles, 2 = 128 x 128 blocks streamed in three 64 KB
-                             * operand stages, 3 = the same in six 32 KB stages, 4 = 2 with the
-                             * block columns taken in pairs (each row panel streamed once per two
-                             * block columns, two accumulators), 5 = 128 x 128 blocks with each
-                             * task's K loop (one streaming warp, two tensor-memory accumulators)
-                             * overlapping the previous task's epilogue; DS_FACTOR_AUTO (default) = picked per
-                             * batch by timing the six on the batch's sizes at its first solve
-                             * (ds_batch_tune). Ignored in DS_PREC_FP64. Handles of one batch
-                             * must agree.                                                        */
+                             * 1 = 64 x 64 tiles, 2 = 128 x 128 blocks, 3 = 128 x 128 blocks with
+                             * two rows x two block columns per task (each operand block streamed
+                             * once per two products, four accumulators), 4 = 128 x 128 blocks
+                             * with the block columns taken in pairs (each row panel streamed once
+                             * per two block columns, two accumulators), 5 = 128 x 128 blocks with
+                             * each task's K loop (one streaming warp, two tensor-memory
+                             * accumulators) overlapping the previous task's epilogue;
+                             * DS_FACTOR_AUTO (default) = picked per batch by timing the six on
+                             * the batch's sizes at its first solve (ds_batch_tune). Ignored in
+                             * DS_PREC_FP64. Handles of one batch must agree.                     */
   int32_t solver;           /* 0 = one Cholesky of the dense 6N x 6N damped system (default);
                              * 1 = block-Jacobi: each control point's 6 unknowns from its own 6 x 6
                              * damped diagonal block (FP64 Cholesky per node), the reading of
@@ -304,13 +305,14 @@ int ds_get_device_bytes(ds_handle h, int64_t* bytes);
 
 /* The task order of the 128 x 128 block Cholesky factorisation (Section 2: the damped normal
  * equations are solved by a Cholesky factorisation) of an nb x nb block matrix, as the factor
- * kernels claim it within one problem: paired = 0 for the single-block kernels (factor_tc 2, 3
- * and 5), 1 for the column-pair kernel (factor_tc 4). Task k is written to out[3 k .. 3 k + 2]
- * = (type, I, J): type 0 = DIAG(J) (factor block (J, J)), 1 = OFF(I, J) (block (I, J), I > J),
- * 2 = the two blocks (I, J) and (I, J + 1). out (host memory, caller-owned) holds cap tasks; the
- * count is written to *ntasks (also when it exceeds cap, then nothing past cap is written).
- * Host only, no GPU. Errors: DS_ERR_ARG (nb < 1, paired not 0 / 1, ntasks NULL, out NULL with
- * cap > 0). */
+ * kernels claim it within one problem: paired = 0 for the single-block kernels (factor_tc 2 and
+ * 5), 1 for the column-pair kernel (factor_tc 4), 2 for the two-row two-column kernel
+ * (factor_tc 3). Task k is written to out[3 k .. 3 k + 2] = (type, I, J): type 0 = DIAG(J)
+ * (factor block (J, J)), 1 = OFF(I, J) (block (I, J), I > J), 2 = the two blocks (I, J) and
+ * (I, J + 1), 3 = the four blocks (I, J), (I, J + 1), (I + 1, J), (I + 1, J + 1). out (host
+ * memory, caller-owned) holds cap tasks; the count is written to *ntasks (also when it exceeds
+ * cap, then nothing past cap is written). Host only, no GPU. Errors: DS_ERR_ARG (nb < 1, paired
+ * not 0..2, ntasks NULL, out NULL with cap > 0). */
 int ds_factor_tasks(int32_t nb, int32_t paired, int32_t* out, int32_t cap, int32_t* ntasks);
 
 /* 1-point RANSAC preselection without any allocation, for callers that cannot allocate device

@@ -168,6 +168,8 @@ struct ds_ctx {
   int ntasks_b = 0;
   int4* d_tasks_p = nullptr;  // the same with the block columns in pairs
   int ntasks_p = 0;
+  int4* d_tasks_q = nullptr;  // the same with two rows x two block columns per task
+  int ntasks_q = 0;
   int nt = 0;
   bool prec_fp64 = false;
   double* d_acc = nullptr;
@@ -296,25 +298,27 @@ void wait_solved(ds_ctx* h) {
 void destroy_batch(ds_batch_s* b);
 
 // The factor kernels the tuner chooses from, by kernel index: SIMT 64 x 64 tiles, tensor cores
-// with 64 x 64 tiles, tensor cores with 128 x 128 blocks in three 64 KB stages, and in six
-// 32 KB stages; 4 is the 128-block kernel (64 KB stages of its single block tasks) with its block
-// columns taken in pairs (one stream of each row panel per pair); 5 the 128-block kernel whose
-// K loops (one streaming warp, two tensor-memory accumulators) overlap the epilogues of the
-// previous tasks (eight warps).
+// with 64 x 64 tiles, tensor cores with 128 x 128 blocks (64 KB K-loop stages); 3 the 128-block
+// kernel with the block columns taken in pairs and the rows below each pair also in pairs (two
+// rows x two columns per task: each operand block streamed once per two products); 4 with the
+// block columns in pairs only; 5 the 128-block kernel whose K loops (one streaming warp, two
+// tensor-memory accumulators) overlap the epilogues of the previous tasks (eight warps).
 constexpr int kFactorKernels = 6;
 void set_factor_kernel(BatchTabs& T, int k) {
-  static const int ftc[kFactorKernels] = {0, 1, 2, 2, 2, 2}, g[kFactorKernels] = {2, 2, 2, 1, 2, 1},
+  static const int ftc[kFactorKernels] = {0, 1, 2, 2, 2, 2}, g[kFactorKernels] = {2, 2, 2, 2, 2, 1},
                    pairs[kFactorKernels] = {0, 0, 0, 0, 1, 0},
+                   quad[kFactorKernels] = {0, 0, 0, 1, 0, 0},
                    pipe[kFactorKernels] = {0, 0, 0, 0, 0, 1};
   T.factor_tc = ftc[k];
   T.tcb_g = g[k];
   T.tcb_pairs = pairs[k];
+  T.tcb_quad = quad[k];
   T.tcb_pipe = pipe[k];
 }
 int factor_kernel_of(const BatchTabs& T) {
   if (T.factor_tc < 2) return T.factor_tc;
   if (T.tcb_pipe) return 5;
-  return T.tcb_pairs ? 4 : (T.tcb_g == 2 ? 2 : 3);
+  return T.tcb_pairs ? 4 : (T.tcb_quad ? 3 : 2);
 }
 
 // The handle's batches stop running: its control points change or (leaving) it goes away, and
@@ -341,6 +345,7 @@ void free_cp(ds_ctx* h) {
   hfree(h, h->d_v2); hfree(h, h->d_v3); hfree(h, h->d_lcnt); hfree(h, h->d_lflags); hfree(h, h->d_tasks);
   hfree(h, h->d_tasks_b);
   hfree(h, h->d_tasks_p);
+  hfree(h, h->d_tasks_q);
   hfree(h, h->d_Lp);
   hfree(h, h->d_desc);
   h->N = h->n = 0;
@@ -449,6 +454,34 @@ void make_chol_tasks_b(int nb, std::vector<int4>& out) {
   }
 }
 
+// Block tasks with the block columns and the rows below each column pair taken in pairs: the
+// pair's panel as below, then {0, 3, I, J0} for the rows I, I + 1 (blocks (I, J0), (I, J1),
+// (I + 1, J0), (I + 1, J1) as one task), a lone last row as {0, 2, I, J0}; the next pair's panel
+// follows the first of these (the two rows it depends on). Topological.
+void make_chol_tasks_q(int nb, std::vector<int4>& out) {
+  auto panel = [&](int j0) {
+    out.push_back(make_int4(0, 0, j0, j0));
+    if (j0 + 1 < nb) {
+      out.push_back(make_int4(0, 1, j0 + 1, j0));
+      out.push_back(make_int4(0, 0, j0 + 1, j0 + 1));
+    }
+  };
+  auto rows = [&](int i, int j0) {
+    out.push_back(make_int4(0, i + 1 < nb ? 3 : 2, i, j0));
+  };
+  if (nb < 1) return;
+  panel(0);
+  for (int j0 = 0; j0 + 1 < nb; j0 += 2) {
+    int i = j0 + 2;
+    if (i < nb) {
+      rows(i, j0);
+      i += 2;
+    }
+    if (j0 + 2 < nb) panel(j0 + 2);
+    for (; i < nb; i += 2) rows(i, j0);
+  }
+}
+
 // Block tasks with the block columns taken in pairs (J0 = 2 p, J1 = J0 + 1): the pair's panel
 // DIAG(J0), OFF(J1, J0), DIAG(J1), then {0, 2, I, J0} for I = J1 + 1 .. nb - 1, the two blocks
 // (I, J0) and (I, J1) as one task; a lone last column is DIAG alone. The next pair's panel
@@ -547,8 +580,8 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   b->block_jacobi = solver == 1;
   b->stream = stream;
   b->own_stream = own;
-  std::vector<int2> icp, rows, nodes, res, chol, chol_b, chol_p;
-  std::vector<int> ntasks(n), ntasks_b(n), ntasks_p(n);
+  std::vector<int2> icp, rows, nodes, res, chol, chol_b, chol_p, chol_q;
+  std::vector<int> ntasks(n), ntasks_b(n), ntasks_p(n), ntasks_q(n);
   int max_tasks = 0, max_nt = 0;
   std::vector<const ProbDesc*> descs(n);
   for (int p = 0; p < n; ++p) {
@@ -561,14 +594,16 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
     ntasks[p] = h->ntasks;
     ntasks_b[p] = h->ntasks_b;
     ntasks_p[p] = h->ntasks_p;
+    ntasks_q[p] = h->ntasks_q;
     max_tasks = std::max(max_tasks, h->ntasks);
     max_nt = std::max(max_nt, h->nt);
   }
   make_chol_tickets(ntasks, chol);
   make_chol_tickets(ntasks_b, chol_b);
   make_chol_tickets(ntasks_p, chol_p);
+  make_chol_tickets(ntasks_q, chol_q);
   const size_t ntab = icp.size() + rows.size() + nodes.size() + res.size() + chol.size() +
-                      chol_b.size() + chol_p.size();
+                      chol_b.size() + chol_p.size() + chol_q.size();
   int rc;
   if ((rc = dalloc(&b->d_descs, n)) || (rc = dalloc(&b->d_tab, ntab)) ||
       (rc = dalloc(&b->d_words, 8))) {
@@ -577,7 +612,7 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   }
   std::vector<int2> all;
   all.reserve(ntab);
-  for (auto* v : {&icp, &rows, &nodes, &res, &chol, &chol_b, &chol_p})
+  for (auto* v : {&icp, &rows, &nodes, &res, &chol, &chol_b, &chol_p, &chol_q})
     all.insert(all.end(), v->begin(), v->end());
   cudaMemcpy(b->d_descs, descs.data(), sizeof(void*) * n, cudaMemcpyHostToDevice);
   b->h_descs = descs;
@@ -594,6 +629,7 @@ int make_batch(ds_ctx* const* hs, int n, cudaStream_t stream, bool own, ds_batch
   T.chol = b->d_tab + off; T.n_chol = (int)chol.size(); off += chol.size();
   T.chol_b = b->d_tab + off; T.n_chol_b = (int)chol_b.size(); off += chol_b.size();
   T.chol_p = b->d_tab + off; T.n_chol_p = (int)chol_p.size(); off += chol_p.size();
+  T.chol_q = b->d_tab + off; T.n_chol_q = (int)chol_q.size(); off += chol_q.size();
   T.orb_ctas = 16;
   b->auto_factor = ftc == DS_FACTOR_AUTO;
   set_factor_kernel(T, b->auto_factor ? 0 : ftc);
@@ -1275,6 +1311,15 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
     }
     cudaMemcpy(h->d_tasks_p, tasks_p.data(), sizeof(int4) * tasks_p.size(),
                cudaMemcpyHostToDevice);
+    std::vector<int4> tasks_q;
+    make_chol_tasks_q((n + 127) / 128, tasks_q);
+    h->ntasks_q = (int)tasks_q.size();
+    if ((rc = halloc(h, &h->d_tasks_q, tasks_q.size()))) {
+      free_cp(h);
+      return rc;
+    }
+    cudaMemcpy(h->d_tasks_q, tasks_q.data(), sizeof(int4) * tasks_q.size(),
+               cudaMemcpyHostToDevice);
   }
   h->prec_fp64 = prec == DS_PREC_FP64;
   {
@@ -1345,6 +1390,7 @@ int ds_set_control_points(ds_handle h, const int32_t* pixel_index, int32_t N) {
     lp.tasks_b = h->d_tasks_b;
     lp.ntasks_b = h->ntasks_b;
     lp.tasks_p = h->d_tasks_p;
+    lp.tasks_q = h->d_tasks_q;
     lp.nb = (n + 127) / 128;
     lp.status = h->d_acc + ACC_STATUS;
     lp.y = h->d_v3;
@@ -1902,9 +1948,11 @@ int ds_get_device_bytes(ds_handle h, int64_t* bytes) {
 }
 
 int ds_factor_tasks(int32_t nb, int32_t paired, int32_t* out, int32_t cap, int32_t* ntasks) {
-  if (nb < 1 || (paired != 0 && paired != 1) || !ntasks || (cap > 0 && !out)) return DS_ERR_ARG;
+  if (nb < 1 || paired < 0 || paired > 2 || !ntasks || (cap > 0 && !out)) return DS_ERR_ARG;
   std::vector<int4> t;
-  if (paired)
+  if (paired == 2)
+    make_chol_tasks_q(nb, t);
+  else if (paired == 1)
     make_chol_tasks_p(nb, t);
   else
     make_chol_tasks_b(nb, t);

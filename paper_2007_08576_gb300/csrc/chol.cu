@@ -1480,6 +1480,98 @@ __device__ bool ws_consume(unsigned tmem, unsigned tmem2, unsigned stg, WRing<NS
   return ok;
 }
 
+// The same producer / consumer pair for two rows and two block columns: stage
+// [A0][A1][B0 hi][B1 hi][B0 lo][B1 lo] (64 KB), products A0 [B0; B1]^T into D0 (256 TMEM
+// columns at tmem) and A1 [B0; B1]^T into D1 (at tmem + 256), one N = 256 MMA per term each.
+template <int NS, typename PA, typename PA2, typename PB, typename PB2, typename DEP>
+__device__ void ws_produce4(unsigned stg, WRing<NS>& r, unsigned pos, int nck, PA pa, PA2 pa2,
+                            PB pb, PB2 pb2, DEP dep, int* err, unsigned long long budget) {
+  constexpr unsigned kStage = 4 * kSubBytes, kHalf = kSubBytes / 2;
+  int c = 0;
+  if (*(volatile int*)err == 0) {
+    for (; c < nck; ++c) {
+      const unsigned q = pos + (unsigned)c, s = q % NS, g = q / NS;
+      if (g >= 1 && !mbar_wait(&r.empty[s], (g - 1) & 1u, err, budget)) break;
+      if (!dep(c)) break;
+      const unsigned d = stg + s * kStage, bar = smem_u32(&r.full[s]);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                   "r"(kStage)
+                   : "memory");
+      auto copy = [&](unsigned dst, const float* src, unsigned bytes) {
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+            "[%3];" ::"r"(dst),
+            "l"(src), "r"(bytes), "r"(bar)
+            : "memory");
+      };
+      const float* b = pb(c);
+      const float* b2 = pb2(c);
+      copy(d, pa(c), kSubBytes);
+      copy(d + kSubBytes, pa2(c), kSubBytes);
+      copy(d + 2 * kSubBytes, b, kHalf);
+      copy(d + 2 * kSubBytes + kHalf, b2, kHalf);
+      copy(d + 3 * kSubBytes, b + kPart, kHalf);
+      copy(d + 3 * kSubBytes + kHalf, b2 + kPart, kHalf);
+    }
+  }
+  if (c < nck) {
+    *(volatile int*)&r.nissued = (int)pos + c;
+    __threadfence_block();
+    *(volatile int*)&r.pdone = 1;
+  }
+}
+
+template <int NS>
+__device__ bool ws_consume4(unsigned tmem, unsigned stg, WRing<NS>& r, unsigned pos,
+                            unsigned long long* bfin, int nck, int* err,
+                            unsigned long long budget) {
+  constexpr unsigned kStage = 4 * kSubBytes;
+  const volatile int* vdone = &r.pdone;
+  const volatile int* vn = &r.nissued;
+  bool ok = true;
+  int c = 0;
+  for (; c < nck; ++c) {
+    const unsigned q = pos + (unsigned)c, s = q % NS, g = q / NS;
+    bool got = mbar_test(&r.full[s], g & 1u);
+    if (!got) {
+      const unsigned long long t0 = globaltimer();
+      for (;;) {
+        if (mbar_test(&r.full[s], g & 1u)) {
+          got = true;
+          break;
+        }
+        if (*vdone && (int)pos + c >= *vn) break;   // the producer stopped before chunk c
+        if (globaltimer() - t0 > budget) {
+          atomicExch(err, 1);
+          break;
+        }
+      }
+    }
+    if (!got) {
+      ok = false;
+      break;
+    }
+    tc::fence_after();
+    const unsigned d = stg + s * kStage;
+    mma_sub256(tmem, d, d + 2 * kSubBytes, c > 0);
+    mma_sub256(tmem + 256u, d + kSubBytes, d + 2 * kSubBytes, c > 0);
+    tc::commit(&r.empty[s]);
+  }
+  if (!ok) {
+    const unsigned long long t0 = globaltimer();
+    while (!*vdone && globaltimer() - t0 <= budget) {
+    }
+    const int n_iss = *vdone ? *vn - (int)pos : c;
+    for (int k = c; k < n_iss; ++k) {
+      const unsigned q = pos + (unsigned)k, s = q % NS, g = q / NS;
+      mbar_wait(&r.full[s], g & 1u, err, budget);
+      mbar_arrive(&r.empty[s]);
+    }
+  }
+  tc::commit(bfin);
+  return ok;
+}
+
 template <int NS>
 __device__ __forceinline__ void ring_init(Ring<NS>& rg) {
   for (int s = 0; s < NS; ++s) {
@@ -1505,12 +1597,12 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
                                                      const int2* __restrict__ tickets,
                                                      int nticket, int* __restrict__ head,
                                                      int* __restrict__ err,
-                                                     unsigned long long budget_ns) {
+                                                     unsigned long long budget_ns, int quads) {
   using namespace tcb;
   constexpr int NS = 6 / G;
   constexpr int TB = 64, LDS = TB + 1, RT = 4;
   constexpr int LDC = BS + 1;
-  constexpr unsigned kTmemCols = PAIRS ? 256u : 128u;
+  constexpr unsigned kTmemCols = PAIRS ? 512u : 128u;
   extern __shared__ __align__(1024) unsigned char smb[];
   float* sm = reinterpret_cast<float*>(smb);
   __shared__ __align__(8) unsigned long long s_bfin;
@@ -1523,11 +1615,13 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
   __shared__ __align__(8) WRing<NS> wring_k;        // single-block K-loop stages
   __shared__ __align__(8) Ring<kXStages> ring_x;    // stages of the products with a resident A
   __shared__ __align__(8) WRing<4> wring_p;         // paired K-loop stages (48 KB)
+  __shared__ __align__(8) WRing<3> wring_q;         // K-loop stages of two rows x two columns
   unsigned long long* bfin = &s_bfin;
   if (tid == 0) {
     wring_init(wring_k);
     ring_init(ring_x);
     wring_init(wring_p);
+    wring_init(wring_q);
     mbar_init(bfin);
   }
   if (warp == 0) {
@@ -1667,7 +1761,7 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
   // A wait that gives up raises the error word; every CTA then leaves its ticket loop (after its
   // copies and products in flight have completed), and the host reports DS_ERR_TIMEOUT.
   // K loops: thread 32 issues the copies, thread 0 the products; pos_*: chunks through each ring
-  unsigned pos_k = 0u, pos_p = 0u;
+  unsigned pos_k = 0u, pos_p = 0u, pos_q = 0u;
   for (;;) {
     if (tid == 0) s_t = atomicAdd(head, 1);
     __syncthreads();
@@ -1679,7 +1773,7 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
       continue;
     }
     const LinProblem& P = descs[pt.x]->lp;
-    const int4 tk = PAIRS ? P.tasks_p[pt.y] : P.tasks_b[pt.y];
+    const int4 tk = PAIRS ? (quads ? P.tasks_q[pt.y] : P.tasks_p[pt.y]) : P.tasks_b[pt.y];
     const int nb = P.nb, n = P.n;
     int* pdone = P.cnt;
     int* tdone = P.cnt + nb;
@@ -1687,8 +1781,10 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
     float* Lp = (float*)P.Lp;
     float a[64];   // the task's block of A, loaded while the K loop runs
     float v[64];   // this thread's accumulator row segment
-    if (PAIRS && tk.y == 2) {
-      // ---- OFF2(I; J0, J1): blocks (I, J0) and (I, J1)
+    if (PAIRS && tk.y >= 2) {
+      // ---- OFF2(I; J0, J1): blocks (I, J0), (I, J1); OFF4(I; J0, J1) (type 3): the same for
+      // rows I and I + 1, each B block read once for both rows
+      const bool quad = tk.y == 3;
       const int I = tk.z, J0 = tk.w, J1 = J0 + 1;
       const int nck = (BS / KS) * J0;
       load_rows(A, n, I, J0, a);
@@ -1698,90 +1794,105 @@ __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __re
           return Lp + slot(row, c >> 3) * kSlot + (size_t)(c & 7) * kSub;
         };
         auto pa = [&](int c) -> const float* { return src(I, c); };
+        auto pa2 = [&](int c) -> const float* { return src(I + 1, c); };
         auto pb = [&](int c) -> const float* { return src(J0, c); };
         auto pb2 = [&](int c) -> const float* { return src(J1, c); };
-        if (tid == 32)
-          ws_produce<4, 1, 3, true>(
-              stg, wring_p, pos_p, nck, pa, pb, pb2,
-              [&](int c) {
-                if (c & 7) return true;
-                const int kb = c >> 3;
-                return acquired(wait_flag(&tdone[I * nb + kb], 1, err, budget_ns) &&
-                                wait_flag(&tdone[J0 * nb + kb], 1, err, budget_ns) &&
-                                wait_flag(&tdone[J1 * nb + kb], 1, err, budget_ns));
-              },
-              err, budget_ns);
-        else
-          s_ok = ws_consume<4, 1, 3, true>(tmem, tmem + 128u, stg, wring_p, pos_p, bfin, nck, pa,
-                                           pb, pb2, err, budget_ns);
+        auto dep = [&](int c) {
+          if (c & 7) return true;
+          const int kb = c >> 3;
+          return acquired(wait_flag(&tdone[I * nb + kb], 1, err, budget_ns) &&
+                          (!quad || wait_flag(&tdone[(I + 1) * nb + kb], 1, err, budget_ns)) &&
+                          wait_flag(&tdone[J0 * nb + kb], 1, err, budget_ns) &&
+                          wait_flag(&tdone[J1 * nb + kb], 1, err, budget_ns));
+        };
+        if (quad) {
+          if (tid == 32)
+            ws_produce4<3>(stg, wring_q, pos_q, nck, pa, pa2, pb, pb2, dep, err, budget_ns);
+          else
+            s_ok = ws_consume4<3>(tmem, stg, wring_q, pos_q, bfin, nck, err, budget_ns);
+        } else {
+          if (tid == 32)
+            ws_produce<4, 1, 3, true>(stg, wring_p, pos_p, nck, pa, pb, pb2, dep, err, budget_ns);
+          else
+            s_ok = ws_consume<4, 1, 3, true>(tmem, tmem + 128u, stg, wring_p, pos_p, bfin, nck,
+                                             pa, pb, pb2, err, budget_ns);
+        }
       }
       if (tid == 0 && !str) s_ok = *(volatile int*)err == 0;
-      if (str) pos_p += (unsigned)nck;
+      if (str) (quad ? pos_q : pos_p) += (unsigned)nck;
       __syncthreads();
       if (!join(str)) break;
-      if (tid == 0) {   // X_J0 J0's first stages while the C operand is formed
-        s_pre = prime_product(Lp + slot(J0, J0) * kSlot, &pdone[J0]);
-        s_ok = s_pre >= 0;
-      }
-      // block (I, J0): C = A - acc0, L = C X_J0^T
-      tc::fence_after();
-      if (nck > 0) {
-        tcb::tmem_row64(tmem, v);
-      } else {
+      // Row Ir of the pair of block columns, its accumulators at tb (J0) and tb + 128 (J1); a
+      // holds block (Ir, J0) of A on entry (and block (Ir + 1, J0) on return when next_row).
+      auto pair_rows = [&](int Ir, unsigned tb, bool next_row) {
+        if (tid == 0) {   // X_J0 J0's first stages while the C operand is formed
+          s_pre = prime_product(Lp + slot(J0, J0) * kSlot, &pdone[J0]);
+          s_ok = s_pre >= 0;
+        }
+        // block (Ir, J0): C = A - acc0, L = C X_J0^T
+        tc::fence_after();
+        if (nck > 0) {
+          tcb::tmem_row64(tb, v);
+        } else {
 #pragma unroll
-        for (int e = 0; e < 64; ++e) v[e] = 0.f;
-      }
-      tc::fence_before();
-      stage_rows(a);
-      __syncthreads();
-      load_rows(A, n, I, J1, a);   // block (I, J1) of A, used after the next two products
-      form_c(n, I, v);
-      __syncthreads();
-      if (tid == 0 && s_ok)
-        s_ok = resident_product(tmem, Lp + slot(J0, J0) * kSlot, false, &pdone[J0], s_pre);
-      __syncthreads();
-      if (!join(s_pre >= 0)) break;
-      if (tid == 0) {   // the k = J0 term's B operand while L_IJ0 is written
-        s_pre = prime_product(Lp + slot(J1, J0) * kSlot, &tdone[J1 * nb + J0]);
-        s_ok = s_pre >= 0;
-      }
-      tc::fence_after();
-      tcb::tmem_row64(tmem, v);
-      tc::fence_before();
-      write_block(A, Lp, n, I, J0, v);
-      __syncthreads();   // Tb read before Cs (which covers it) is written
-      // the finished L_IJ0 as the resident A operand of the k = J0 term of block (I, J1)
+          for (int e = 0; e < 64; ++e) v[e] = 0.f;
+        }
+        tc::fence_before();
+        stage_rows(a);
+        __syncthreads();
+        load_rows(A, n, Ir, J1, a);   // block (Ir, J1) of A, used after the next two products
+        form_c(n, Ir, v);
+        __syncthreads();
+        if (tid == 0 && s_ok)
+          s_ok = resident_product(tb, Lp + slot(J0, J0) * kSlot, false, &pdone[J0], s_pre);
+        __syncthreads();
+        if (!join(s_pre >= 0)) return false;
+        if (tid == 0) {   // the k = J0 term's B operand while L_IrJ0 is written
+          s_pre = prime_product(Lp + slot(J1, J0) * kSlot, &tdone[J1 * nb + J0]);
+          s_ok = s_pre >= 0;
+        }
+        tc::fence_after();
+        tcb::tmem_row64(tb, v);
+        tc::fence_before();
+        write_block(A, Lp, n, Ir, J0, v);
+        __syncthreads();   // Tb read before Cs (which covers it) is written
+        // the finished L_IrJ0 as the resident A operand of the k = J0 term of block (Ir, J1)
 #pragma unroll
-      for (int e = 0; e < 64; e += 4)
-        tcb::put4_smem(Cs, arow, acol + e, v[e], v[e + 1], v[e + 2], v[e + 3]);
-      publish(&tdone[I * nb + J0]);
-      if (tid == 0 && s_ok)
-        s_ok = resident_product(tmem + 128u, Lp + slot(J1, J0) * kSlot, nck > 0,
-                                &tdone[J1 * nb + J0], s_pre);
-      __syncthreads();
-      if (!join(s_pre >= 0)) break;
-      if (tid == 0) {
-        s_pre = prime_product(Lp + slot(J1, J1) * kSlot, &pdone[J1]);
-        s_ok = s_pre >= 0;
-      }
-      // block (I, J1): C = A - acc1, L = C X_J1^T
-      tc::fence_after();
-      tcb::tmem_row64(tmem + 128u, v);
-      tc::fence_before();
-      stage_rows(a);
-      __syncthreads();
-      form_c(n, I, v);
-      __syncthreads();
-      if (tid == 0 && s_ok)
-        s_ok = resident_product(tmem + 128u, Lp + slot(J1, J1) * kSlot, false, &pdone[J1],
-                                s_pre);
-      __syncthreads();
-      if (!join(s_pre >= 0)) break;
-      tc::fence_after();
-      tcb::tmem_row64(tmem + 128u, v);
-      tc::fence_before();
-      write_block(A, Lp, n, I, J1, v);
-      publish(&tdone[I * nb + J1]);
+        for (int e = 0; e < 64; e += 4)
+          tcb::put4_smem(Cs, arow, acol + e, v[e], v[e + 1], v[e + 2], v[e + 3]);
+        publish(&tdone[Ir * nb + J0]);
+        if (tid == 0 && s_ok)
+          s_ok = resident_product(tb + 128u, Lp + slot(J1, J0) * kSlot, nck > 0,
+                                  &tdone[J1 * nb + J0], s_pre);
+        __syncthreads();
+        if (!join(s_pre >= 0)) return false;
+        if (tid == 0) {
+          s_pre = prime_product(Lp + slot(J1, J1) * kSlot, &pdone[J1]);
+          s_ok = s_pre >= 0;
+        }
+        // block (Ir, J1): C = A - acc1, L = C X_J1^T
+        tc::fence_after();
+        tcb::tmem_row64(tb + 128u, v);
+        tc::fence_before();
+        stage_rows(a);
+        __syncthreads();
+        if (next_row) load_rows(A, n, Ir + 1, J0, a);   // the next row's first block of A
+        form_c(n, Ir, v);
+        __syncthreads();
+        if (tid == 0 && s_ok)
+          s_ok = resident_product(tb + 128u, Lp + slot(J1, J1) * kSlot, false, &pdone[J1],
+                                  s_pre);
+        __syncthreads();
+        if (!join(s_pre >= 0)) return false;
+        tc::fence_after();
+        tcb::tmem_row64(tb + 128u, v);
+        tc::fence_before();
+        write_block(A, Lp, n, Ir, J1, v);
+        publish(&tdone[Ir * nb + J1]);
+        return true;
+      };
+      if (!pair_rows(I, tmem, quad)) break;
+      if (quad && !pair_rows(I + 1, tmem + 256u, false)) break;
       continue;
     }
     const bool diag = tk.y == 0;
@@ -2577,20 +2688,20 @@ void launch_fill_spd(const BatchTabs& B, cudaStream_t s) {
 template <typename T>
 void launch_chol_dag(const BatchTabs& B, cudaStream_t s) {
   if (sizeof(T) == 4 && B.factor_tc == 2) {
-    const int nticket = B.tcb_pairs ? B.n_chol_p : B.n_chol_b;
-    const int2* tickets = B.tcb_pairs ? B.chol_p : B.chol_b;
+    const int nticket = B.tcb_quad ? B.n_chol_q : B.tcb_pairs ? B.n_chol_p : B.n_chol_b;
+    const int2* tickets = B.tcb_quad ? B.chol_q : B.tcb_pairs ? B.chol_p : B.chol_b;
     const int grid = std::min(nticket, num_sms());
     auto go = [&](auto kern, PerDevice& attr) {
       set_smem_once(attr, kern, (int)tcb::kSmem);
       kern<<<grid, 256, tcb::kSmem, s>>>(B.d, tickets, nticket, B.words + 0, B.words + 5,
-                                         2000000000ull);
+                                         2000000000ull, B.tcb_quad);
     };
     static PerDevice attr[4];
     if (B.tcb_pipe) {
       set_smem_once(attr[0], k_chol_tcp, (int)tcp::kSmem);
       k_chol_tcp<<<grid, tcp::kThreads, tcp::kSmem, s>>>(B.d, tickets, nticket, B.words + 0,
                                                           B.words + 5, 2000000000ull);
-    } else if (B.tcb_pairs)
+    } else if (B.tcb_pairs || B.tcb_quad)
       go(k_chol_tcb<2, true>, attr[1]);
     else if (B.tcb_g == 1)
       go(k_chol_tcb<1, false>, attr[2]);

@@ -67,6 +67,7 @@ struct LinProblem {
   const int4* tasks_b;  // the tasks of the 128 x 128 block factorisation (tensor cores)
   int ntasks_b;
   const int4* tasks_p;  // the same with the block columns taken in pairs
+  const int4* tasks_q;  // the same with the rows below each pair also taken in pairs
   int nb;               // 128-row blocks
   double* status;
   void* y;
@@ -227,6 +228,9 @@ struct BatchTabs {
   int tcb_g;                 // 128-block kernel: K sub-chunks of 16 per operand and stage (1, 2)
   int tcb_pairs;             // 128-block kernel: block columns taken in pairs
   int tcb_pipe;              // 128-block kernel: K loops overlapping the epilogues (warp roles)
+  int tcb_quad;              // 128-block kernel: two rows x two block columns per task
+  const int2* chol_q;        // the tickets of those tasks, in claim order
+  int n_chol_q;
   const int2* chol_p;        // the tickets of the paired block tasks, in claim order
   int n_chol_p;
   int jtj;                   // ICP J^T W J on the tensor cores (BF16, FP32 accumulation)

@@ -253,7 +253,7 @@ def ds_batch_set_tracing(b, on=True):
     _check("ds_batch_set_tracing", lib().ds_batch_set_tracing(b, 1 if on else 0))
 
 
-FACTOR_KERNELS = ["simt64", "tc64", "tc128_stage64k", "tc128_stage32k", "tc128_stage64k_pairs",
+FACTOR_KERNELS = ["simt64", "tc64", "tc128_stage64k", "tc128_quads", "tc128_stage64k_pairs",
                   "tc128_pipelined"]
 
 
@@ -364,8 +364,9 @@ def ds_get_device_bytes(h) -> int:
     return b.value
 
 
-def ds_factor_tasks(nb: int, paired: bool = False) -> np.ndarray:
-    """The block factorisation's task order within one problem, rows (type, I, J)."""
+def ds_factor_tasks(nb: int, paired: int = 0) -> np.ndarray:
+    """The block factorisation's task order within one problem, rows (type, I, J); paired: 0
+    single blocks, 1 column pairs, 2 two rows x two columns."""
     n = ctypes.c_int32()
     _check("ds_factor_tasks", lib().ds_factor_tasks(nb, int(paired), None, 0, ctypes.byref(n)))
     out = np.zeros((n.value, 3), np.int32)

@@ -21,8 +21,12 @@ def needs(ty, i, j):
         return ({("L", i, k) for k in range(j)} | {("L", j, k) for k in range(j)} |
                 {("D", j)})
     j1 = j + 1
-    return ({("L", i, k) for k in range(j)} | {("L", j, k) for k in range(j)} |
-            {("L", j1, k) for k in range(j)} | {("D", j), ("D", j1), ("L", j1, j)})
+    rows = [i] if ty == 2 else [i, i + 1]
+    need = ({("L", j, k) for k in range(j)} | {("L", j1, k) for k in range(j)} |
+            {("D", j), ("D", j1), ("L", j1, j)})
+    for r in rows:
+        need |= {("L", r, k) for k in range(j)}
+    return need
 
 
 def gives(ty, i, j):
@@ -30,16 +34,18 @@ def gives(ty, i, j):
         return [("D", j)]
     if ty == 1:
         return [("L", i, j)]
-    return [("L", i, j), ("L", i, j + 1)]
+    if ty == 2:
+        return [("L", i, j), ("L", i, j + 1)]
+    return [("L", i, j), ("L", i, j + 1), ("L", i + 1, j), ("L", i + 1, j + 1)]
 
 
-@pytest.mark.parametrize("paired", [0, 1])
+@pytest.mark.parametrize("paired", [0, 1, 2])
 def test_orders_are_topological_and_complete(d, paired):
     for nb in range(1, 41):
-        tasks = d.ds_factor_tasks(nb, bool(paired))
+        tasks = d.ds_factor_tasks(nb, paired)
         have, made = set(), []
         for ty, i, j in tasks.tolist():
-            assert ty in ((0, 1, 2) if paired else (0, 1))
+            assert ty in ((0, 1), (0, 1, 2), (0, 1, 2, 3))[paired]
             missing = needs(ty, i, j) - have
             assert not missing, (nb, (ty, i, j), sorted(missing)[:3])
             for g in gives(ty, i, j):
@@ -65,7 +71,7 @@ def test_bad_arguments(d):
         d.ds_factor_tasks(0)
     import ctypes
     n = ctypes.c_int32()
-    assert d.lib().ds_factor_tasks(4, 2, None, 0, ctypes.byref(n)) == d.DS_ERR_ARG
+    assert d.lib().ds_factor_tasks(4, 3, None, 0, ctypes.byref(n)) == d.DS_ERR_ARG
     assert d.lib().ds_factor_tasks(4, 0, None, 5, ctypes.byref(n)) == d.DS_ERR_ARG
     assert d.lib().ds_factor_tasks(4, 0, None, 0, None) == d.DS_ERR_ARG
     assert d.lib().ds_factor_tasks(4, 0, None, 0, ctypes.byref(n)) == 0 and n.value == 10

@@ -420,7 +420,7 @@ def test_bounded_waits_give_up_and_the_context_stays_usable(d, tiny):
 
 
 @pytest.mark.parametrize("ftc", [1, 2, 3, 4, 5],
-                         ids=["tiles64", "blocks128", "blocks128s", "blocks128p", "blocks128pipe"])
+                         ids=["tiles64", "blocks128", "blocks128q", "blocks128p", "blocks128pipe"])
 @pytest.mark.parametrize("prec", [1, 2])
 def test_tensor_core_factor_matches_oracle_tiny_and_ragged(d, tiny, mid, prec, ftc):
     """FP32 factorisation on tcgen05 (three TF32 terms per product): the same parity bar, with
@@ -438,7 +438,7 @@ def test_tensor_core_factor_matches_oracle_tiny_and_ragged(d, tiny, mid, prec, f
 
 
 @pytest.mark.parametrize("ftc", [1, 2, 3, 4, 5],
-                         ids=["tiles64", "blocks128", "blocks128s", "blocks128p", "blocks128pipe"])
+                         ids=["tiles64", "blocks128", "blocks128q", "blocks128p", "blocks128pipe"])
 def test_tensor_core_factor_full_size_frame(d, ftc):
     sc = scene(CONFIGS["seq_320x240_n256"], 1000)
     fr = sc.frames[0]

@@ -76,7 +76,7 @@ def _check(d, case, p):
 @pytest.mark.parametrize("prec,ftc", [(2, 0), (0, 0), (2, 1), (2, 2), (2, 3), (2, 4), (2, 5),
                                       (2, -1)],
                          ids=["fp32_refine", "fp64", "fp32_refine_tc64", "fp32_refine_tc128",
-                              "fp32_refine_tc128s", "fp32_refine_tc128p", "fp32_refine_tc128pipe",
+                              "fp32_refine_tc128q", "fp32_refine_tc128p", "fp32_refine_tc128pipe",
                               "fp32_refine_auto"])
 def test_320x240_n256_all_iterations(d, c2, prec, ftc):
     _check(d, c2, d.default_params(precision=prec, factor_tc=ftc))
@@ -84,7 +84,7 @@ def test_320x240_n256_all_iterations(d, c2, prec, ftc):
 
 @pytest.mark.parametrize("prec,ftc", [(2, 0), (0, 0), (2, 1), (2, 2), (2, 3), (2, 4), (2, 5)],
                          ids=["fp32_refine", "fp64", "fp32_refine_tc64", "fp32_refine_tc128",
-                              "fp32_refine_tc128s", "fp32_refine_tc128p", "fp32_refine_tc128pipe"])
+                              "fp32_refine_tc128q", "fp32_refine_tc128p", "fp32_refine_tc128pipe"])
 def test_640x480_n1024_all_iterations(d, c3, prec, ftc):
     _check(d, c3, d.default_params(precision=prec, factor_tc=ftc))
 
