@@ -1584,14 +1584,19 @@ __device__ __forceinline__ void ring_init(Ring<NS>& rg) {
 
 }  // namespace tcb
 
+// Every K loop runs on two threads: thread 32 issues the bulk copies of the operand stages,
+// thread 0 the MMAs, linked by full / empty mbarriers per stage (WRing).
 // G: sub-chunks per operand per stage of the single-block K loop (stages of 2 G x 16 KB, 6 / G of
 // them). PAIRS: block columns are taken two at a time (J0 = 2 p, J1 = 2 p + 1): DIAG(J0),
 // OFF(J1, J0), DIAG(J1), then OFF2(I; J0, J1) for every row block I below, which accumulates
-// the two blocks (I, J0) and (I, J1) over k < J0 with one stream of the A operand L_Ik (two
-// accumulators, stages [L_Ik][L_J0k][L_J1k] of 48 KB), finishes (I, J0), adds the k = J0 term
-// L_IJ0 L_J1J0^T to the second accumulator from the just-finished block held in shared memory,
-// and finishes (I, J1): the row panel I is read once per two block columns instead of once per
-// column.
+// the two blocks (I, J0) and (I, J1) over k < J0 with one stream of the A operand L_Ik (stages
+// [L_Ik][L_J0k, L_J1k interleaved] of 48 KB, one N = 256 MMA per term into 256 TMEM columns),
+// finishes (I, J0), adds the k = J0 term L_IJ0 L_J1J0^T to the second accumulator from the
+// just-finished block held in shared memory, and finishes (I, J1): the row panel I is read once
+// per two block columns instead of once per column. With quads (the task list of two rows x two
+// columns), OFF4(I; J0, J1) does the same for the rows I and I + 1 at once (stages
+// [L_Ik][L_I+1,k][L_J0k, L_J1k] of 64 KB, four accumulators over all 512 TMEM columns), so that
+// the column panels are also read once per two rows.
 template <int G, bool PAIRS>
 __global__ __launch_bounds__(256, 1) void k_chol_tcb(const ProbDesc* const* __restrict__ descs,
                                                      const int2* __restrict__ tickets,
