@@ -56,7 +56,8 @@ FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x ma
 # on the headline workload, by factor kernel, from an ncu capture (profiles/), valid only for the
 # kernel source it was taken on (first 16 hex digits of the sha256 of csrc/chol.cu +
 # csrc/dev_util.cuh) and the same workload; reported as null otherwise.
-FACTOR_TRAFFIC = None
+FACTOR_TRAFFIC = {"chol_sha256": "b7a4547769ca80bc", "workload": "batched_mixed_64",
+                  "bytes": {"tc128q": 47389573120 + 6035021568}}
 
 
 def max_over_ranks(x, world, dev):
