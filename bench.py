@@ -665,7 +665,8 @@ def run_gpu(args):
         sp = variant_params(d, args, prec)
         if tuner is not None:
             sp.factor_tc = KERNEL_NAMES.index(tuner["chosen"])
-        srv = Server(GpuEngine(sp), budget_bytes=int(0.6 * torch.cuda.mem_get_info()[0]),
+        srv = Server(GpuEngine(sp, n_batches=max(2, args.max_inflight)),
+                     budget_bytes=int(0.6 * torch.cuda.mem_get_info()[0]),
                      max_inflight=args.max_inflight)
         for j in streams:
             sc = scenes[j]

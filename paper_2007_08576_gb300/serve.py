@@ -201,6 +201,10 @@ class Server:
         # batches on the GPU at once: frames that arrive meanwhile wait and join the next batch,
         # so batches grow with the load instead of splitting into many small concurrent ones
         self.max_inflight = max_inflight
+        slots = getattr(engine, "n_batches", None)
+        if slots is not None and slots < max_inflight:
+            raise ValueError(f"the engine keeps {slots} batches, fewer than max_inflight = "
+                             f"{max_inflight}")
         self.clock = clock
         self.used = 0
         self.streams = {}                 # sid -> dict(spec, solver, queue, busy, bytes)

@@ -248,3 +248,12 @@ def test_accounting_follows_the_engines_reported_bytes():
     srv.drain()
     srv.close_stream("a")
     assert srv.used == 0
+
+
+def test_inflight_cap_needs_as_many_engine_batches():
+    """A server may not keep more batches on the GPU than its engine has batch slots."""
+    eng = FakeEngine()
+    eng.n_batches = 2
+    Server(eng, budget_bytes=1 << 40, max_inflight=2)
+    with pytest.raises(ValueError):
+        Server(eng, budget_bytes=1 << 40, max_inflight=3)
