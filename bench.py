@@ -697,7 +697,10 @@ def run_gpu(args):
                 "max_inflight": args.max_inflight,
                 "mean_gpu_ms_per_batch": round(st["mean_gpu_ms_per_batch"], 3),
                 "mean_host_ms_per_launch": round(st["mean_host_ms_per_launch"], 3),
-                "mean_read_ms_per_frame": round(st["mean_read_ms_per_frame"], 4)}
+                "mean_read_ms_per_frame": round(st["mean_read_ms_per_frame"], 4),
+                "full_batches": st["full_batches"] and {
+                    k: (round(v, 2) if isinstance(v, float) else v)
+                    for k, v in st["full_batches"].items()}}
 
     served = served_low = None
     if rank == 0 and args.served_frames > 0:

@@ -217,6 +217,7 @@ class Server:
         self.batches = 0
         self.batch_sizes = []
         self.gpu_ms = []          # device time of each completed batch (when the engine reports it)
+        self.done_batches = []    # (frames, device ms) of each completed batch, when reported
         self.host_ms = []         # host time of each launch (frame submissions + solve enqueue)
         self.read_ms = []         # host time of each result read
 
@@ -292,7 +293,9 @@ class Server:
             if self.engine.done(token):
                 now_batch = len(sids)
                 if hasattr(self.engine, "gpu_ms"):
-                    self.gpu_ms.append(self.engine.gpu_ms(token))
+                    g = self.engine.gpu_ms(token)
+                    self.gpu_ms.append(g)
+                    self.done_batches.append((now_batch, g))
                 for sid, (fut, t_arr) in zip(sids, items):
                     st = self.streams[sid]
                     r0 = self.clock()
@@ -351,7 +354,18 @@ class Server:
                 "mean_gpu_ms_per_batch": float(np.mean(self.gpu_ms)) if self.gpu_ms else None,
                 "mean_host_ms_per_launch": float(np.mean(self.host_ms)) if self.host_ms else None,
                 "mean_read_ms_per_frame": float(np.mean(self.read_ms)) if self.read_ms else None,
-                "device_bytes": self.used}
+                "device_bytes": self.used, "full_batches": self._full_batches()}
+
+    def _full_batches(self):
+        """The batches that carried every admitted stream (the load the server saturates at): how
+        many, and their frames per second of device time."""
+        if not self.done_batches:
+            return None
+        top = max(n for n, _ in self.done_batches)
+        full = [(n, g) for n, g in self.done_batches if n == top]
+        ms = sum(g for _, g in full)
+        return {"size": top, "batches": len(full),
+                "frames_per_s_device": sum(n for n, _ in full) / (ms * 1e-3) if ms > 0 else None}
 
 
 def poisson_schedule(rng: np.random.Generator, rates_hz, n_total: int):

@@ -257,3 +257,23 @@ def test_inflight_cap_needs_as_many_engine_batches():
     Server(eng, budget_bytes=1 << 40, max_inflight=2)
     with pytest.raises(ValueError):
         Server(eng, budget_bytes=1 << 40, max_inflight=3)
+
+
+def test_full_batch_rate_from_device_times():
+    class Timed(FakeEngine):
+        def gpu_ms(self, tok):
+            return 10.0 * len(tok["ids"])
+
+    eng = Timed(delay=1)
+    srv = Server(eng, budget_bytes=1 << 40, max_inflight=1)
+    for s in "abc":
+        srv.open_stream(s, _spec())
+    for s in "abc":
+        srv.submit(s, _frame())
+    srv.poll()                                   # batch of 3
+    srv.drain()
+    srv.submit("a", _frame())
+    srv.drain()                                  # batch of 1
+    fb = srv.stats()["full_batches"]
+    assert fb["size"] == 3 and fb["batches"] == 1
+    assert fb["frames_per_s_device"] == pytest.approx(3 / 0.030)
