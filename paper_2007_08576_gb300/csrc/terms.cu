@@ -288,10 +288,14 @@ __device__ __forceinline__ void slot_jac(const float* h, const NodeGPU& nd, floa
 // warp w takes segments base + w + 8 k, k < kSegPerWarp. The segment's 4 node transforms are
 // staged in the warp's shared memory. The lanes take 32 of the segment's points at a time: each
 // forms its point's association, Tukey weight and sqrt-weighted Jacobian row (24 entries, plus
-// the weighted residual) and stages it in the warp's shared rows; then every lane accumulates 12
-// fixed entries of the segment's 384 outputs over those points. Lanes 0..29 own two rows of one
-// 6 x 6 slot-pair block (block l / 3, rows 2 (l % 3) and 2 (l % 3) + 1), lanes 30 and 31 own
-// twelve gradient entries each. At the end of the segment each lane adds its 12 entries with
+// the weighted residual) and stages it in the warp's shared block, column-major (column e of
+// point t at [e][t], so that four consecutive points of a column are one 16-byte load); then
+// every lane accumulates 12 fixed entries of the segment's 384 outputs over those points, four
+// points per step (points past the segment's end were staged as zeros). While a batch is
+// worked on, the next batch's template points are prefetched into L2, and the target point and
+// normal of a pixel are loaded together. Lanes 0..29 own two rows of one 6 x 6 slot-pair block
+// (block l / 3, rows 2 (l % 3) and 2 (l % 3) + 1), lanes 30 and 31 own twelve gradient entries
+// each. At the end of the segment each lane adds its 12 entries with
 // one atomic each; cost, weight and count go out with one atomic triple per warp. Warps never
 // wait for one another.
 // BF16 x BF16 -> FP32 warp-level tensor-core product D += A B (m16n8k16, A row-major 16 x 16,
@@ -332,7 +336,10 @@ __global__ __launch_bounds__(kTile, 2) void k_icp(const ProbDesc* const* __restr
   float* __restrict__ blk = D.blk;
   float* __restrict__ gdata = D.gdata;
   double* __restrict__ acc = D.acc;
-  __shared__ float sJ[kSegPerCta][32][25];
+  // point stride of a staged column: 16-byte rows for the FP32 path's 4-point loads; 8-byte
+  // rows for the tensor-core path's point pairs (which also holds the segment sums)
+  constexpr int kJS = kTcJtj ? 34 : 36;
+  __shared__ __align__(16) float sJ[kSegPerCta][25][kJS];
   __shared__ NodeGPU sNode[kSegPerCta][4];
   // tensor-core path: each warp's running 24 x 24 segment sum (entries owned by fixed lanes)
   __shared__ float sAcc[kTcJtj ? kSegPerCta : 1][kTcJtj ? 24 * 24 : 1];
@@ -342,7 +349,7 @@ __global__ __launch_bounds__(kTile, 2) void k_icp(const ProbDesc* const* __restr
   const int ra = 6 * kSlotPairI(q) + 2 * (lane % 3);   // this lane's two Jacobian rows
   const int cb = 6 * kSlotPairJ(q);                    // and the partner slot's columns
   const int g0 = (lane - 30) * 12;                     // gradient entries of lanes 30, 31
-  float(*rows)[25] = sJ[warp];
+  float(*cols)[kJS] = sJ[warp];
   NodeGPU* nd = sNode[warp];
   float cost = 0.f, wsum = 0.f, nval = 0.f;
   const int mg = lane >> 2, mt4 = lane & 3;   // mma fragment coordinates (tensor-core path)
@@ -375,10 +382,12 @@ __global__ __launch_bounds__(kTile, 2) void k_icp(const ProbDesc* const* __restr
     for (int e = 0; e < 12; ++e) a[e] = 0.f;
     for (int c0 = lo; c0 < hi; c0 += 32) {
       const int pidx = c0 + lane;
-      float Jt[24];
-#pragma unroll
-      for (int i = 0; i < 24; ++i) Jt[i] = 0.f;
+      if (pidx + 32 < hi) {   // the next batch's template point and weights, into L2
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(tp + pidx + 32));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(tw + pidx + 32));
+      }
       float rt = 0.f;
+      bool staged = false;   // the point's Jacobian row is in the staging block
       if (pidx < hi) {
         const float4 pa = tp[pidx];
         const int near = __float_as_int(pa.w) & 3;
@@ -398,8 +407,8 @@ __global__ __launch_bounds__(kTile, 2) void k_icp(const ProbDesc* const* __restr
             if (pu >= 0.f && pu < (float)W && pv >= 0.f && pv < (float)H) {
               const int pix = (int)pv * W + (int)pu;
               const float4 tq = tgt_pt[pix];
+              const float4 n4 = tgt_nrm[pix];
               if (tq.w > 0.f) {
-                const float4 n4 = tgt_nrm[pix];
                 tqv = {tq.x, tq.y, tq.z};
                 n = {n4.x, n4.y, n4.z};
                 assoc_ok = true;
@@ -420,8 +429,8 @@ __global__ __launch_bounds__(kTile, 2) void k_icp(const ProbDesc* const* __restr
               if (cu >= 0.f && cu <= (float)(W - 1) && cv >= 0.f && cv <= (float)(H - 1)) {
                 const int pc = (int)cv * W + (int)cu;
                 const float4 Xc = tgt_pt[pc];
+                const float4 Nc = tgt_nrm[pc];
                 if (Xc.w > 0.f) {
-                  const float4 Nc = tgt_nrm[pc];
                   ws += wc[c4];
                   qs = add(qs, mul({Xc.x, Xc.y, Xc.z}, wc[c4]));
                   ns = add(ns, mul({Nc.x, Nc.y, Nc.z}, wc[c4]));
@@ -448,17 +457,24 @@ __global__ __launch_bounds__(kTile, 2) void k_icp(const ProbDesc* const* __restr
             float h[8];
             dir_grad(n, p, B, h);
 #pragma unroll
-            for (int s = 0; s < 4; ++s)
-              slot_jac(h, nd[s], alp[s] * B.sgn[s] * sig, &Jt[6 * s]);
+            for (int s = 0; s < 4; ++s) {
+              float J6[6];
+              slot_jac(h, nd[s], alp[s] * B.sgn[s] * sig, J6);
+#pragma unroll
+              for (int i = 0; i < 6; ++i) cols[6 * s + i][lane] = J6[i];
+            }
             rt = sig * r;
+            staged = true;
           } else {
             cost += cc6;
           }
         }
       }
+      if (!staged) {
 #pragma unroll
-      for (int i = 0; i < 24; ++i) rows[lane][i] = Jt[i];
-      rows[lane][24] = rt;
+        for (int i = 0; i < 24; ++i) cols[i][lane] = 0.f;
+      }
+      cols[24][lane] = rt;
       __syncwarp();
       const int np = min(32, hi - c0);
       if (kTcJtj) {
@@ -475,26 +491,28 @@ __global__ __launch_bounds__(kTile, 2) void k_icp(const ProbDesc* const* __restr
 #pragma unroll
             for (int e = 0; e < 4; ++e) cm[i][j][e] = 0.f;
         for (int k0 = 0; k0 < np; k0 += 16) {
-          const float* r0 = rows[k0 + 2 * mt4];
-          const float* r1 = rows[k0 + 2 * mt4 + 1];
-          const float* r8 = rows[k0 + 2 * mt4 + 8];
-          const float* r9 = rows[k0 + 2 * mt4 + 9];
+          // entries (point k0 + 2 t4 + {0, 1}) and (point k0 + 2 t4 + {8, 9}) of a column
+          const int t0 = k0 + 2 * mt4;
+          auto pair = [&](int m, int t) {
+            const float2 v = *reinterpret_cast<const float2*>(&cols[m][t]);
+            return pack_bf16(v.x, v.y);
+          };
           unsigned af[2][4];
 #pragma unroll
           for (int i = 0; i < 2; ++i) {
             // A = J^T (row m = Jacobian column m, column k = point k0 + k)
             const int m0 = 16 * i + mg, m1 = m0 + 8;
             const bool v1 = m1 < 24;
-            af[i][0] = pack_bf16(r0[m0], r1[m0]);
-            af[i][1] = v1 ? pack_bf16(r0[m1], r1[m1]) : 0u;
-            af[i][2] = pack_bf16(r8[m0], r9[m0]);
-            af[i][3] = v1 ? pack_bf16(r8[m1], r9[m1]) : 0u;
+            af[i][0] = pair(m0, t0);
+            af[i][1] = v1 ? pair(m1, t0) : 0u;
+            af[i][2] = pair(m0, t0 + 8);
+            af[i][3] = v1 ? pair(m1, t0 + 8) : 0u;
           }
 #pragma unroll
           for (int j = 0; j < 3; ++j) {
             // B = J (row k = point, column n = Jacobian column 8 j + n)
             const int nn = 8 * j + mg;
-            const unsigned bf[2] = {pack_bf16(r0[nn], r1[nn]), pack_bf16(r8[nn], r9[nn])};
+            const unsigned bf[2] = {pair(nn, t0), pair(nn, t0 + 8)};
 #pragma unroll
             for (int i = 0; i < 2; ++i) mma_bf16_16x8x16(cm[i][j], af[i], bf);
           }
@@ -510,25 +528,37 @@ __global__ __launch_bounds__(kTile, 2) void k_icp(const ProbDesc* const* __restr
             }
         // the gradient J^T W r stays FP32: lane l < 24 sums entry l
         if (lane < 24) {
-          for (int t = 0; t < np; ++t) a[0] += rows[t][lane] * rows[t][24];
+          for (int t = 0; t < np; ++t) a[0] += cols[lane][t] * cols[24][t];
         }
       } else if (!grad) {
-#pragma unroll 2
-        for (int t = 0; t < np; ++t) {
-          const float x0 = rows[t][ra], x1 = rows[t][ra + 1];
+        // four points per step, in point order (the points past np add exact zeros)
+        for (int t = 0; t < np; t += 4) {
+          const float4 x0 = *reinterpret_cast<const float4*>(&cols[ra][t]);
+          const float4 x1 = *reinterpret_cast<const float4*>(&cols[ra + 1][t]);
 #pragma unroll
           for (int cc = 0; cc < 6; ++cc) {
-            const float y = rows[t][cb + cc];
-            a[cc] += x0 * y;
-            a[6 + cc] += x1 * y;
+            const float4 y = *reinterpret_cast<const float4*>(&cols[cb + cc][t]);
+            a[cc] += x0.x * y.x;
+            a[6 + cc] += x1.x * y.x;
+            a[cc] += x0.y * y.y;
+            a[6 + cc] += x1.y * y.y;
+            a[cc] += x0.z * y.z;
+            a[6 + cc] += x1.z * y.z;
+            a[cc] += x0.w * y.w;
+            a[6 + cc] += x1.w * y.w;
           }
         }
       } else {
-#pragma unroll 2
-        for (int t = 0; t < np; ++t) {
-          const float rr = rows[t][24];
+        for (int t = 0; t < np; t += 4) {
+          const float4 rr = *reinterpret_cast<const float4*>(&cols[24][t]);
 #pragma unroll
-          for (int e = 0; e < 12; ++e) a[e] += rows[t][g0 + e] * rr;
+          for (int e = 0; e < 12; ++e) {
+            const float4 x = *reinterpret_cast<const float4*>(&cols[g0 + e][t]);
+            a[e] += x.x * rr.x;
+            a[e] += x.y * rr.y;
+            a[e] += x.z * rr.z;
+            a[e] += x.w * rr.w;
+          }
         }
       }
       __syncwarp();
