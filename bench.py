@@ -696,7 +696,9 @@ def run_gpu(args):
                 "mean_batch": round(st["mean_batch"], 2), "batches": st["batches"],
                 "max_inflight": args.max_inflight,
                 "mean_gpu_ms_per_batch": round(st["mean_gpu_ms_per_batch"], 3),
+                "min_fill": srv.min_fill,
                 "mean_host_ms_per_launch": round(st["mean_host_ms_per_launch"], 3),
+                "mean_host_ms_per_submit": round(st["mean_host_ms_per_submit"], 3),
                 "mean_read_ms_per_frame": round(st["mean_read_ms_per_frame"], 4),
                 "full_batches": st["full_batches"] and {
                     k: (round(v, 2) if isinstance(v, float) else v)

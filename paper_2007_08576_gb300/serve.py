@@ -7,16 +7,22 @@ arrive asynchronously; every scheduler round (``poll``)
   1. completes the batches whose GPU work has finished (results read to the host, futures
      resolved, latency = result on the host - arrival),
   2. admits waiting streams while the device-memory budget allows,
-  3. launches one batch over every admitted stream that has a queued frame and is not already in
-     flight (the streams' frames are submitted, then one batched Gauss-Newton solve covers all of
-     them), unless max_inflight batches are already on the GPU: then the ready frames wait and
-     join the next batch.
+  3. stages the next queued frame of every admitted stream that has none staged: the frame is
+     submitted at once (copy to the device, frame preparation and RANSAC on the stream's own CUDA
+     stream), into the frame slot its in-flight solve does not read, so this work overlaps the
+     batch already on the GPU,
+  4. launches one batch (one batched Gauss-Newton solve) over every admitted stream that has a
+     staged frame and is not in flight, if no batch is on the GPU, or if fewer than max_inflight
+     are and the ready streams make up at least min_fill of the admitted ones; otherwise the
+     ready frames wait and join the next batch. Under load this keeps the batches full (two
+     half-size groups taking turns would each pay a whole solve's fixed cost), while a burst
+     still gets a batch of its own beside the running one.
 
-Several batches are in flight at once on their own CUDA streams (their stream sets are
-disjoint), so frames arriving while others are on the GPU are admitted into the next batch and
-their work overlaps on the device. The GPU engine keeps two long-lived batch objects over every
-admitted stream and solves each launch's streams as a masked solve, so a launch allocates and
-captures nothing.
+Batches in flight together run on their own CUDA streams (their stream sets are disjoint), so
+frames arriving while others are on the GPU are admitted into the next batch and their work
+overlaps on the device. The GPU engine keeps two long-lived batch objects over every admitted
+stream and solves each launch's streams as a masked solve, so a launch allocates and captures
+nothing.
 
 The engine is pluggable: ``GpuEngine`` drives libdefsolve; tests use a fake engine to check the
 host logic without a GPU.
@@ -107,9 +113,11 @@ class GpuEngine:
         self.handles = []          # admitted solvers, in batch order
         self.batches = []          # [batch, stream, in-flight token or None]
         self.dirty = True
-        # per stream: pinned host staging of its frames (a copy from pageable memory would make
-        # the host wait for the stream's earlier work)
+        # per stream: two sets of pinned host staging of its frames, used in turn (a copy from
+        # pageable memory would make the host wait for the stream's earlier work), and which set
+        # the next frame takes
         self.staging = {}
+        self.turn = {}
 
     @property
     def precision(self):
@@ -127,8 +135,10 @@ class GpuEngine:
         M = spec.max_matches
         t = self.torch
         pin = lambda shape, dt: t.empty(shape, dtype=dt, pin_memory=True).numpy()
-        self.staging[id(s)] = (pin((H, W), t.float32), pin((M,), t.int32), pin((M, 3), t.float32),
-                               pin((int(self.params.n_hyp),), t.int32))
+        self.staging[id(s)] = [(pin((H, W), t.float32), pin((M,), t.int32),
+                                pin((M, 3), t.float32), pin((int(self.params.n_hyp),), t.int32))
+                               for _ in range(2)]
+        self.turn[id(s)] = 0
         self._drop_batches()
         self.handles.append(s)
         return s
@@ -137,13 +147,17 @@ class GpuEngine:
         self._drop_batches()
         self.handles = [h for h in self.handles if h is not s]
         self.staging.pop(id(s), None)
+        self.turn.pop(id(s), None)
         s.close()
 
     def submit(self, s, f: FrameIn):
-        """Copies the frame into the stream's pinned staging and submits it from there. The
-        staging is free again: the server submits a stream's next frame only after the batch
-        that read its previous one has completed, and that batch ran after the copies."""
-        dep, mi, mx, hy = self.staging[id(s)]
+        """Copies the frame into one of the stream's two pinned staging sets and submits it
+        from there (its copies to the device are asynchronous). The set is free again: the server
+        keeps at most one frame staged and one in flight per stream, so the frame that used this
+        set two submissions ago has been solved, after its copies."""
+        k = self.turn[id(s)]
+        self.turn[id(s)] = 1 - k
+        dep, mi, mx, hy = self.staging[id(s)][k]
         M = len(f.match_idx)
         np.copyto(dep, f.depth)
         np.copyto(mi[:M], f.match_idx)
@@ -193,7 +207,7 @@ class GpuEngine:
 
 class Server:
     def __init__(self, engine, budget_bytes: int, iters: int = 10, max_batch: int = 64,
-                 max_inflight: int = 2, clock=time.perf_counter):
+                 max_inflight: int = 2, min_fill: float = 0.6, clock=time.perf_counter):
         self.engine = engine
         self.budget = int(budget_bytes)
         self.iters = iters
@@ -201,6 +215,9 @@ class Server:
         # batches on the GPU at once: frames that arrive meanwhile wait and join the next batch,
         # so batches grow with the load instead of splitting into many small concurrent ones
         self.max_inflight = max_inflight
+        # share of the admitted streams that must be ready before a batch is launched beside
+        # one already on the GPU (0: launch whenever a batch slot is free)
+        self.min_fill = float(min_fill)
         slots = getattr(engine, "n_batches", None)
         if slots is not None and slots < max_inflight:
             raise ValueError(f"the engine keeps {slots} batches, fewer than max_inflight = "
@@ -218,7 +235,8 @@ class Server:
         self.batch_sizes = []
         self.gpu_ms = []          # device time of each completed batch (when the engine reports it)
         self.done_batches = []    # (frames, device ms) of each completed batch, when reported
-        self.host_ms = []         # host time of each launch (frame submissions + solve enqueue)
+        self.host_ms = []         # host time of each launch (the batched solve's enqueue)
+        self.submit_ms = []       # host time of each frame submission (staging)
         self.read_ms = []         # host time of each result read
 
     # -- streams
@@ -232,15 +250,15 @@ class Server:
         if nbytes > self.budget:
             raise ValueError(f"stream {sid} needs {nbytes} B, more than the whole budget")
         self.streams[sid] = dict(spec=spec, solver=None, queue=collections.deque(), busy=False,
-                                 bytes=nbytes)
+                                 staged=None, bytes=nbytes)
         self.waiting.append(sid)
         self._admit()
         return self.streams[sid]["solver"] is not None
 
     def close_stream(self, sid):
         st = self.streams[sid]
-        if st["busy"]:
-            raise RuntimeError(f"stream {sid} has a frame in flight")
+        if st["busy"] or st["staged"] is not None:
+            raise RuntimeError(f"stream {sid} has a frame in flight or staged")
         for fut, _, _ in st["queue"]:
             fut.cancel()
         if st["solver"] is not None:
@@ -313,30 +331,45 @@ class Server:
                 still.append((token, sids, items))
         self.in_flight = still
         self._admit()
+        self._stage()
         ready = [sid for sid, st in self.streams.items()
-                 if st["solver"] is not None and not st["busy"] and st["queue"]]
+                 if st["staged"] is not None and not st["busy"]]
         ready = ready[: self.max_batch]
-        if ready and len(self.in_flight) < self.max_inflight:
+        admitted = sum(1 for st in self.streams.values() if st["solver"] is not None)
+        if ready and len(self.in_flight) < self.max_inflight and (
+                not self.in_flight or len(ready) >= self.min_fill * admitted):
             h0 = self.clock()
             solvers, items = [], []
             for sid in ready:
                 st = self.streams[sid]
-                fut, t_arr, frame = st["queue"].popleft()
-                self.engine.submit(st["solver"], frame)
-                self._account(st)
+                items.append(st["staged"])
+                st["staged"] = None
                 st["busy"] = True
                 solvers.append(st["solver"])
-                items.append((fut, t_arr))
             token = self.engine.launch(solvers, self.iters)
             self.host_ms.append((self.clock() - h0) * 1e3)
             self.in_flight.append((token, ready, items))
             self.batches += 1
             self.batch_sizes.append(len(ready))
+            self._stage()       # the launched streams' next frames overlap their solve
         return n_done
 
+    def _stage(self):
+        """Submits the next queued frame of every admitted stream that has none staged (one
+        frame staged and one in flight per stream at most: the handle's two frame slots)."""
+        for st in self.streams.values():
+            if st["solver"] is None or st["staged"] is not None or not st["queue"]:
+                continue
+            fut, t_arr, frame = st["queue"].popleft()
+            h0 = self.clock()
+            self.engine.submit(st["solver"], frame)
+            self.submit_ms.append((self.clock() - h0) * 1e3)
+            self._account(st)
+            st["staged"] = (fut, t_arr)
+
     def pending(self) -> int:
-        return sum(len(st["queue"]) for st in self.streams.values()) + sum(
-            len(s) for _, s, _ in self.in_flight)
+        return sum(len(st["queue"]) + (st["staged"] is not None)
+                   for st in self.streams.values()) + sum(len(s) for _, s, _ in self.in_flight)
 
     def drain(self, idle_sleep=0.0):
         while self.pending():
@@ -353,6 +386,7 @@ class Server:
                 "mean_batch": float(np.mean(self.batch_sizes)) if self.batch_sizes else 0.0,
                 "mean_gpu_ms_per_batch": float(np.mean(self.gpu_ms)) if self.gpu_ms else None,
                 "mean_host_ms_per_launch": float(np.mean(self.host_ms)) if self.host_ms else None,
+                "mean_host_ms_per_submit": float(np.mean(self.submit_ms)) if self.submit_ms else None,
                 "mean_read_ms_per_frame": float(np.mean(self.read_ms)) if self.read_ms else None,
                 "device_bytes": self.used, "full_batches": self._full_batches()}
 

@@ -8,7 +8,10 @@ from paper_2007_08576_gb300.serve import (FrameIn, Server, StreamSpec, poisson_s
 
 
 class FakeEngine:
-    """Completes a launched batch after `delay` polls; 'solves' by counting frames."""
+    """Completes a launched batch after `delay` polls; 'solves' by counting frames. Models the
+    library's two frame slots per handle: a solve takes the latest submitted frame, a stream has
+    at most one solve in flight, and a frame may be submitted while one is (into the other
+    slot), but never two frames beyond the last launched one."""
 
     precision = 2
 
@@ -19,7 +22,7 @@ class FakeEngine:
         self.live = set()
 
     def create(self, spec):
-        s = {"frames": 0, "spec": spec}
+        s = {"frames": 0, "submitted": 0, "launched": 0, "spec": spec}
         self.live.add(id(s))
         return s
 
@@ -27,16 +30,26 @@ class FakeEngine:
         self.live.discard(id(s))
 
     def submit(self, s, f):
-        s["frames"] += 1
+        assert s["submitted"] == s["launched"], "a frame submitted over an unsolved one"
+        s["submitted"] += 1
 
     def launch(self, solvers, iters):
-        tok = {"left": self.delay, "ids": [id(s) for s in solvers]}
+        for s in solvers:
+            assert s["launched"] == s["frames"], "a second solve of a stream in flight"
+            assert s["submitted"] > s["launched"], "a solve without a new frame"
+            s["launched"] = s["submitted"]
+        tok = {"left": self.delay, "ids": [id(s) for s in solvers], "solvers": solvers,
+               "upto": [s["submitted"] for s in solvers]}
         self.launches.append(tok)
         return tok
 
     def done(self, tok):
         tok["left"] -= 1
-        return tok["left"] < 0
+        if tok["left"] < 0:
+            for s, u in zip(tok["solvers"], tok["upto"]):
+                s["frames"] = u
+            return True
+        return False
 
     def read(self, s):
         N = len(s["spec"].nodes)
@@ -71,7 +84,7 @@ def test_admission_by_memory_budget():
 
 def test_continuous_batching_overlaps_and_keeps_order():
     eng = FakeEngine(delay=3)
-    srv = Server(eng, budget_bytes=1 << 40)
+    srv = Server(eng, budget_bytes=1 << 40, min_fill=0.0)
     for s in "abcd":
         srv.open_stream(s, _spec())
     f1 = [srv.submit(s, _frame()) for s in "ab"]
@@ -277,3 +290,57 @@ def test_full_batch_rate_from_device_times():
     fb = srv.stats()["full_batches"]
     assert fb["size"] == 3 and fb["batches"] == 1
     assert fb["frames_per_s_device"] == pytest.approx(3 / 0.030)
+
+
+def test_next_frame_is_staged_while_the_previous_solves():
+    """A stream's next frame is submitted (its copies, preparation and RANSAC start) while its
+    previous frame's solve is on the GPU; the solve of the new frame waits for that one, and the
+    results come out in order."""
+    eng = FakeEngine(delay=3)
+    srv = Server(eng, budget_bytes=1 << 40)
+    srv.open_stream("a", _spec())
+    f1 = srv.submit("a", _frame())
+    srv.poll()                                       # staged and launched
+    s = srv.streams["a"]["solver"]
+    assert s["submitted"] == 1 and s["launched"] == 1
+    f2 = srv.submit("a", _frame())
+    f3 = srv.submit("a", _frame())
+    srv.poll()                                       # frame 2 staged beside the running solve
+    assert s["submitted"] == 2 and s["launched"] == 1 and len(eng.launches) == 1
+    assert srv.streams["a"]["staged"] is not None and len(srv.streams["a"]["queue"]) == 1
+    srv.drain()
+    assert [f.result().t[0, 0] for f in (f1, f2, f3)] == [1.0, 2.0, 3.0]
+    assert len(eng.launches) == 3
+
+
+def test_batches_beside_a_running_one_need_min_fill():
+    """With a batch on the GPU, a second one is launched only when the ready streams make up at
+    least min_fill of the admitted ones; otherwise they wait and go out with the first batch's
+    streams as one full batch."""
+    eng = FakeEngine(delay=2)
+    srv = Server(eng, budget_bytes=1 << 40, max_inflight=2, min_fill=0.6)
+    for sid in "abcde":
+        srv.open_stream(sid, _spec())
+    for sid in "ab":
+        srv.submit(sid, _frame())
+    srv.poll()                                       # nothing on the GPU: a, b go at once
+    assert len(eng.launches) == 1
+    for sid in "cd":
+        srv.submit(sid, _frame())
+    srv.poll()                                       # 2 ready < 0.6 x 5: they wait
+    assert len(eng.launches) == 1
+    for sid in "ab":
+        srv.submit(sid, _frame())
+    srv.drain()
+    assert len(eng.launches) == 2 and len(eng.launches[1]["ids"]) == 4
+    srv2 = Server(FakeEngine(delay=2), budget_bytes=1 << 40, max_inflight=2, min_fill=0.6)
+    for sid in "abcde":
+        srv2.open_stream(sid, _spec())
+    srv2.submit("a", _frame())
+    srv2.poll()
+    for sid in "bcd":
+        srv2.submit(sid, _frame())
+    srv2.poll()                                      # 3 ready >= 0.6 x 5: a second batch
+    assert len(srv2.in_flight) == 2
+    srv2.drain()
+    assert srv2.stats()["frames"] == 4
