@@ -344,3 +344,35 @@ def test_batches_beside_a_running_one_need_min_fill():
     assert len(srv2.in_flight) == 2
     srv2.drain()
     assert srv2.stats()["frames"] == 4
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_schedules_keep_the_slot_discipline_and_order(seed):
+    """Random arrivals, batch delays, fill rules and in-flight caps: the fake engine asserts the
+    library's slot model on every submission and launch (one frame staged and one in flight per
+    stream at most, a solve only over a new frame), every frame completes, and each stream's
+    results come out in arrival order."""
+    rng = np.random.default_rng(seed)
+    eng = FakeEngine(delay=int(rng.integers(1, 5)))
+    eng.n_batches = 2
+    srv = Server(eng, budget_bytes=1 << 40, max_inflight=int(rng.integers(1, 3)),
+                 min_fill=float(rng.choice([0.0, 0.3, 0.6, 1.0])))
+    sids = list(range(int(rng.integers(2, 7))))
+    for sid in sids:
+        srv.open_stream(sid, _spec())
+    futs = {sid: [] for sid in sids}
+    for _ in range(60):
+        for sid in sids:
+            if rng.random() < 0.3:
+                futs[sid].append(srv.submit(sid, _frame()))
+        for _ in range(int(rng.integers(0, 3))):
+            srv.poll()
+    srv.drain()
+    total = 0
+    for sid in sids:
+        got = [f.result().t[0, 0] for f in futs[sid]]
+        assert got == [float(k + 1) for k in range(len(got))]
+        total += len(got)
+    st = srv.stats()
+    assert st["frames"] == total and srv.pending() == 0
+    assert all(not s["busy"] and s["staged"] is None for s in srv.streams.values())
