@@ -1004,3 +1004,77 @@ def test_arap_pair_weights_closed_form():
     d2 = np.array([[0, 9, 16, 2], [9, 0, 25, 5], [16, 25, 0, 10], [2, 5, 10, 0]], dtype=float)
     want = np.exp(-d2 / s2) * (1 - np.eye(4))
     assert np.abs(tpl.wpair - want).max() < 1e-16
+
+
+# ----------------------------------------------------------------------------- cost vs its normal equations
+
+
+def test_right_hand_side_is_the_negative_cost_gradient(tiny):
+    """Eq. 1 and its normal equations (A17: every term r^2 / 2 near zero, the Tukey rho for ICP):
+    with w_ARAP fixed, the preselected ORB weights constant and the association unchanged by
+    the step, b = -sum W J^T r is exactly minus the gradient of the reported cost in the
+    (dtheta, dt) step coordinates. Central differences of the cost through the state update on
+    random coordinates; a weight applied to the rows but not to the cost (or squared in one of
+    them), a dropped 1/2 or a flipped residual sign breaks the equality."""
+    sc, tpl = tiny
+    prm = solver.Params()
+    rng = np.random.default_rng(21)
+    N = tpl.g.shape[0]
+    q, t = random_state(rng, N, rot=0.02, trans=0.5)
+    f = sc.frames[0]
+    tgt = solver.prepare_target(f.depth, tpl.K)
+    midx = np.asarray(f.match_idx[:60], dtype=np.int64)
+    o2 = np.asarray(f.match_xyz[:60], dtype=np.float64)
+    what = rng.uniform(0.5, 1.0, len(midx))
+    orb = (midx, o2, np.ones(len(midx), dtype=bool), what)
+    lin, w_arap = solver.linearize(tpl, tgt, q, t, orb, None, prm)
+    assert lin.cost_icp > 0 and lin.cost_orb > 0 and lin.cost_arap > 0
+
+    def cost_at(delta):
+        qa, ta = dqb.apply_step(q, t, delta)
+        la, _ = solver.linearize(tpl, tgt, qa, ta, orb, w_arap, prm)
+        return la.cost, la
+
+    h = 1e-6
+    coords = rng.choice(6 * N, size=24, replace=False)
+    g_fd = np.zeros(len(coords))
+    for k, j in enumerate(coords):
+        e = np.zeros(6 * N)
+        e[j] = h
+        cp, lp = cost_at(e)
+        cm, lm = cost_at(-e)
+        # the step must not move any point to another pixel, nor across a Tukey cut
+        assert np.array_equal(lp.pix, lin.pix) and np.array_equal(lm.pix, lin.pix)
+        assert np.array_equal(lp.icp_valid, lin.icp_valid)
+        g_fd[k] = (cp - cm) / (2 * h)
+    err = np.abs(g_fd + lin.b[coords]).max() / np.abs(lin.b).max()
+    assert err < 1e-6, err
+
+
+def test_orb_rows_hand_computed():
+    """Section 2.1, last paragraph, and Eq. 1's ORB term: r_k = x'(j_k) - o2_k, row weight
+    w_ORB omega_k with omega_k = the RANSAC weight for a preselected match and the ramp
+    1 - d / (5H) clamped to [0, 1] otherwise; cost 1/2 sum w_ORB omega_k |r_k|^2."""
+    H, w_orb = 2.0, 10.0
+    xk = np.array([[0.0, 0.0, 100.0], [5.0, 5.0, 100.0], [1.0, 0.0, 90.0], [3.0, 3.0, 95.0]])
+    o2 = xk + np.array([[1.0, 2.0, 2.0],      # d = 3, preselected, RANSAC weight 0.7
+                        [0.0, 0.0, 4.0],      # d = 4, not preselected: 1 - 4/10 = 0.6
+                        [0.0, 12.0, 0.0],     # d = 12 > 5H: weight 0
+                        [0.0, 0.0, 0.0]])     # d = 0, not preselected: weight 1
+    mask = np.array([True, False, False, False])
+    what = np.array([0.7, 0.9, 0.9, 0.9])
+    rng = np.random.default_rng(3)
+    Jk = rng.normal(size=(4, 3, 4, 6))
+    nidk = np.array([[0, 1, 2, 3], [4, 5, 6, 7], [1, 3, 5, 7], [2, 4, 6, 0]])
+    rows, cost, om_sum = terms.orb_rows(xk, Jk, nidk, o2, mask, what, H, w_orb)
+    om = np.array([0.7, 0.6, 0.0, 1.0])
+    assert np.allclose(rows.r, -(o2 - xk).reshape(-1), rtol=0, atol=1e-15)
+    assert np.allclose(rows.W, np.repeat(w_orb * om, 3), rtol=0, atol=1e-15)
+    assert cost == pytest.approx(0.5 * w_orb * (0.7 * 9 + 0.6 * 16 + 0.0 * 144 + 1.0 * 0), rel=1e-14)
+    assert om_sum == pytest.approx(2.3, rel=1e-14)
+    # row 3 k + a holds component a of match k's warp Jacobian, on its 4 nodes' 6 columns
+    for k in range(4):
+        for a in range(3):
+            assert np.array_equal(rows.cols[3 * k + a],
+                                  (6 * nidk[k][:, None] + np.arange(6)).reshape(-1))
+            assert np.array_equal(rows.vals[3 * k + a], Jk[k, a].reshape(-1))
