@@ -336,8 +336,9 @@ __global__ __launch_bounds__(kTile, 2) void k_icp(const ProbDesc* const* __restr
   float* __restrict__ blk = D.blk;
   float* __restrict__ gdata = D.gdata;
   double* __restrict__ acc = D.acc;
-  // point stride of a staged column: 16-byte rows for the FP32 path's 4-point loads; 8-byte
-  // rows for the tensor-core path's point pairs (which also holds the segment sums)
+  // point stride of a staged column: a multiple of 4 floats for the FP32 path's 4-point loads;
+  // a multiple of 2 for the tensor-core path's point pairs, whose segment sums below must also
+  // fit in the 48 KB of static shared memory
   constexpr int kJS = kTcJtj ? 34 : 36;
   __shared__ __align__(16) float sJ[kSegPerCta][25][kJS];
   __shared__ NodeGPU sNode[kSegPerCta][4];
