@@ -116,6 +116,25 @@ def _factor_traffic(workload, factor):
     return c["bytes"][factor]
 
 
+def _phase_rooflines(phase_ms, sum_n2, points, iters, refine_steps, hbm_gbs):
+    """HBM fractions of the two bandwidth-bound phases of an fp32_refine step, from their
+    CUDA-event times and their algorithmic bytes: per iteration the linearisation writes the full
+    FP32 rows of the refinement matrix and the factor copy's lower part (6 sum n^2 B) and reads
+    64 B per template point; the solves read the lower FP32 factor once per direction in each
+    of the 1 + refine_steps solves (4 sum n^2 B each) and every refinement residual reads the
+    full matrix once (4 sum n^2 B)."""
+    lin_b = iters * (6.0 * sum_n2 + 64.0 * points)
+    sol_b = iters * 4.0 * sum_n2 * ((1 + refine_steps) + refine_steps)
+    out = {}
+    for name, b, ms in (("linearize", lin_b, phase_ms[0]), ("solve_refine", sol_b, phase_ms[2])):
+        gbs = b / (ms * 1e-3) / 1e9
+        out[name] = {"bytes_per_step": int(b), "achieved_gbs": round(gbs, 1),
+                     "peak_gbs": hbm_gbs, "frac": round(gbs / hbm_gbs, 4)}
+    out["peak_source"] = "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    out["timing"] = "phase times per step, CUDA events in the graph"
+    return out
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -746,6 +765,14 @@ def run_gpu(args):
     else:
         peak, peak_src = FP32_SIMT_TFLOPS, "152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)"
     traffic = _factor_traffic(WORKLOAD, factor) if solver_id == 0 else None
+    phase_roof = None
+    if solver_id == 0 and prec == 2:
+        try:
+            pts = sum(int((sc.template_depth > 0).sum()) for sc in scenes)
+            phase_roof = _phase_rooflines(phase, float(sum(x * x for x in n_list)), pts, ITERS,
+                                          int(prm.refine_steps), _measured_hbm())
+        except Exception as e:   # a diagnostic: its failure must not cost the line
+            phase_roof = {"unavailable": f"{type(e).__name__}: {e}"}
 
     # ------------------------------------------------------------ oracle error sample
     errors = cpu = None
@@ -847,6 +874,7 @@ def run_gpu(args):
                                   "solve_refine": round(phase[2], 4), "update": round(phase[3], 4)},
             "e2e": {"value": round(job_throughput(world, n_p * K, e2e_tot), 3), "unit": "frames/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "phase_roofline": phase_roof,
             "gpu_launches": int(launches),
             "gpu_launches_per_step": round(launches_per_step, 1),
             "roofline": {"bound": bound, "kernel": kernel,

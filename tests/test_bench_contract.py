@@ -87,3 +87,20 @@ def test_error_sample_and_comparison():
     c = bench.compare(gpu, ref, 2.0)
     assert abs(c["max_err_mm"] - 3e-4) < 1e-15 and abs(c["cost_rel_err"] - 1e-4) < 1e-12
     assert c["mask_bits_differing"] == 1     # match 1 sits in the band around H, match 2 counts
+
+
+def test_phase_rooflines_count_the_algorithmic_bytes():
+    """The bench line's phase HBM fractions: per iteration the linearisation moves 6 sum n^2 B of
+    matrix writes plus 64 B per template point, the solves 4 sum n^2 B per solve (1 + refinement
+    steps) and per refinement residual."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench._phase_rooflines([40.0, 130.0, 50.0, 0.3], sum_n2=1e9, points=8e6, iters=10,
+                               refine_steps=2, hbm_gbs=6000.0)
+    lin = 10 * (6e9 + 64 * 8e6)
+    sol = 10 * 4e9 * 5
+    assert r["linearize"]["bytes_per_step"] == int(lin)
+    assert r["solve_refine"]["bytes_per_step"] == int(sol)
+    assert abs(r["linearize"]["achieved_gbs"] - lin / 0.040 / 1e9) < 0.1
+    assert abs(r["solve_refine"]["frac"] - sol / 0.050 / 1e9 / 6000.0) < 1e-4
+    json.dumps(r)
