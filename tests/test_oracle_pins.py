@@ -1078,3 +1078,42 @@ def test_orb_rows_hand_computed():
             assert np.array_equal(rows.cols[3 * k + a],
                                   (6 * nidk[k][:, None] + np.arange(6)).reshape(-1))
             assert np.array_equal(rows.vals[3 * k + a], Jk[k, a].reshape(-1))
+
+
+# ----------------------------------------------------------------------------- damping and the update
+
+
+def test_damping_touches_only_the_diagonal():
+    """Reading A1: A + lambda (diag(A) + eps) with lambda = 1e-4, eps = 1e-9; the off-diagonal
+    entries are left as they are."""
+    prm = solver.Params()
+    A = np.array([[4.0, 1.0, -2.0], [1.0, 9.0, 0.5], [-2.0, 0.5, 0.0]])
+    Ad = solver.damp(A, prm)
+    assert prm.lam == 1e-4 and prm.eps == 1e-9
+    want = A.copy()
+    for i, a in enumerate([4.0, 9.0, 0.0]):
+        want[i, i] = a + 1e-4 * (a + 1e-9)
+    assert np.array_equal(Ad, want)
+    assert np.array_equal(A, [[4.0, 1.0, -2.0], [1.0, 9.0, 0.5], [-2.0, 0.5, 0.0]])  # not in place
+
+
+def test_state_update_is_left_multiplicative_in_the_global_frame():
+    """Reading A3: the step's rotation acts in the global frame, R <- exp([dtheta]x) R (the
+    quaternion exp(dtheta / 2) multiplied on the left), normalised onto q_w >= 0, and the
+    translation adds. A node turned 90 degrees about x, then stepped 90 degrees about z, has
+    R = Rz(90) Rx(90), not Rx(90) Rz(90); a step that takes q_w below zero comes back with the
+    opposite sign (the same rotation)."""
+    s = math.sqrt(0.5)
+    q = np.array([[s, s, 0.0, 0.0]])                       # Rx(90 deg)
+    t = np.array([[1.0, 2.0, 3.0]])
+    qn, tn = dqb.apply_step(q, t, np.array([0.0, 0.0, math.pi / 2, 0.5, -1.0, 2.0]))
+    Rz = np.array([[0.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+    Rx = np.array([[1.0, 0.0, 0.0], [0.0, 0.0, -1.0], [0.0, 1.0, 0.0]])
+    assert np.allclose(rotmat(qn[0]), Rz @ Rx, atol=1e-14)
+    assert not np.allclose(rotmat(qn[0]), Rx @ Rz, atol=1e-3)
+    assert np.allclose(qn[0], [0.5, 0.5, 0.5, 0.5], atol=1e-15)
+    assert np.array_equal(tn, [[1.5, 1.0, 5.0]])
+    # 270 degrees about z from the identity: exp gives q_w = cos(135 deg) < 0, flipped back
+    qf, _ = dqb.apply_step(np.array([[1.0, 0.0, 0.0, 0.0]]), np.zeros((1, 3)),
+                           np.array([0.0, 0.0, 1.5 * math.pi, 0.0, 0.0, 0.0]))
+    assert qf[0, 0] > 0 and np.allclose(qf[0], [s, 0.0, 0.0, -s], atol=1e-15)
