@@ -372,9 +372,17 @@ class Server:
                    for st in self.streams.values()) + sum(len(s) for _, s, _ in self.in_flight)
 
     def drain(self, idle_sleep=0.0):
+        """Polls until every queued frame is done. Raises RuntimeError instead of spinning when
+        the only frames left belong to streams still waiting for admission while nothing is on
+        the GPU: no batch will complete to free memory for them (close a stream first)."""
         while self.pending():
             if self.poll() == 0 and idle_sleep:
                 time.sleep(idle_sleep)
+            if not self.in_flight and not any(
+                    st["solver"] is not None and (st["queue"] or st["staged"] is not None)
+                    for st in self.streams.values()) and self.pending():
+                raise RuntimeError("frames left only on streams waiting for device memory; "
+                                   "close a stream to admit them")
 
     def stats(self) -> dict:
         lat = np.array(self.latencies) if self.latencies else np.zeros(1)

@@ -376,3 +376,21 @@ def test_random_schedules_keep_the_slot_discipline_and_order(seed):
     st = srv.stats()
     assert st["frames"] == total and srv.pending() == 0
     assert all(not s["busy"] and s["staged"] is None for s in srv.streams.values())
+
+
+def test_drain_refuses_to_spin_on_streams_that_cannot_be_admitted():
+    """Frames of a stream that waits for device memory, with nothing on the GPU to free any:
+    drain raises instead of polling forever; once a stream is closed the waiting one is admitted
+    and its frames complete."""
+    one = stream_bytes(80, 60, 32, 200, 2)
+    srv = Server(FakeEngine(), budget_bytes=int(1.5 * one))
+    srv.open_stream("a", _spec())
+    assert not srv.open_stream("b", _spec())
+    fa = srv.submit("a", _frame())
+    fb = srv.submit("b", _frame())
+    with pytest.raises(RuntimeError):
+        srv.drain()
+    assert fa.done() and not fb.done()
+    srv.close_stream("a")
+    srv.drain()
+    assert fb.result().t[0, 0] == 1.0
